@@ -1,0 +1,190 @@
+"""Pins for the oracle's Algorithms 1-4 against what the paper and the mathematics fix:
+exact recovery, the stated equivalences, Eckart-Young, range inclusion (Lemma 4), Lemma 2,
+the pass and vector counts, and the expected-error bounds (Lemma 1, eqs. mn11/mn12, Thm 6)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import algorithms as al
+from oracle import bounds, norms
+from oracle import quaternion as Q
+from oracle.qr import qr
+from oracle.qsvd import singular_values
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lowrank(m, n, r, seed):
+    B = synth.gaussian_qmat(seed, m, r)
+    C = synth.gaussian_qmat(seed + 1, r, n)
+    return Q.qmatmul(B, C)
+
+
+def _omega(n, ell, seed):
+    return synth.gaussian_qmat(seed, n, ell)
+
+
+def _proj(Qm):
+    return Q.qmatmul(Qm, Q.qH(Qm))
+
+
+@pytest.mark.parametrize("algo,v", [("alg2", 2), ("alg2", 3), ("alg2", 5), ("alg4", 4), ("alg4", 5)])
+def test_exact_recovery_of_rank_r(algo, v):
+    A = _lowrank(40, 30, 6, 100)
+    k, p = 6, 2
+    res = al.run(algo, A, k, p, v, _omega(30, k + p, 7))
+    err = norms.lowrank_error(A, res.U, res.S, res.V)
+    assert err <= 1e-12 * norms.spectral_norm(A)
+    np.testing.assert_allclose(res.S, singular_values(A)[:k], rtol=1e-11)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_alg2_even_equals_alg1(q):
+    """Section 3: for v = 2(q+1), Algorithm 2 reduces to Algorithm 1."""
+    P = synth.config_slow_decay(60, 50, 8, 4, 2, seed=3)
+    r1 = al.alg1_classical(P.A, 8, 4, q, P.Omega)
+    r2 = al.alg2_arbitrary_pass(P.A, 8, 4, 2 * q + 2, P.Omega)
+    np.testing.assert_allclose(r2.Q1, r1.Q1, atol=1e-10)
+    np.testing.assert_allclose(r2.R, r1.R, atol=1e-10)
+    np.testing.assert_allclose(r2.S, r1.S, rtol=1e-10)
+    np.testing.assert_allclose(_proj(r2.U), _proj(r1.U), atol=1e-9)
+
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_alg4_below_four_views_equals_alg2(v):
+    """Section 6: Algorithm 4 reduces to Algorithm 2 when v < 4."""
+    P = synth.config_slow_decay(60, 50, 8, 4, v, seed=4)
+    r2 = al.alg2_arbitrary_pass(P.A, 8, 4, v, P.Omega)
+    r4 = al.alg4_block_flexible(P.A, 8, 4, v, P.Omega)
+    np.testing.assert_allclose(r4.S, r2.S, rtol=1e-10)
+    np.testing.assert_allclose(_proj(r4.Q1), _proj(r2.Q1), atol=1e-10)
+    np.testing.assert_allclose(_proj(r4.Q2), _proj(r2.Q2), atol=1e-10)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_alg4_even_spans_alg3_range(q):
+    """Section 5: for v = 2(q+1), Algorithm 4 reduces to Algorithm 3 (same Krylov range)."""
+    P = synth.config_slow_decay(70, 60, 5, 3, 2, seed=5)
+    r3 = al.alg3_block_classical(P.A, 5, 3, q, P.Omega)
+    r4 = al.alg4_block_flexible(P.A, 5, 3, 2 * q + 2, P.Omega)
+    np.testing.assert_allclose(_proj(r4.Q1), _proj(r3.Q1), atol=1e-8)
+    np.testing.assert_allclose(r4.S, r3.S, rtol=1e-8)
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_eckart_young_and_projection_floor(v):
+    P = synth.config_slow_decay(50, 40, 6, 3, v, seed=6)
+    res = al.alg2_arbitrary_pass(P.A, 6, 3, v, P.Omega)
+    s = P.sigma
+    assert norms.lowrank_error(P.A, res.U, res.S, res.V) >= s[6] * (1 - 1e-12)
+    assert norms.range_error(P.A, res.Q1) >= s[9] * (1 - 1e-12)
+    assert norms.corange_error(P.A, res.Q2) >= s[9] * (1 - 1e-12)
+    assert np.all(res.S <= s[:6] * (1 + 1e-12))                  # Ritz values interlace
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_untruncated_reconstruction_identity(v):
+    """Before truncation (k = ell): even v gives Q1 Q1^H X, odd v gives X Q2 Q2^H exactly."""
+    P = synth.config_slow_decay(40, 30, 6, 2, v, seed=8)
+    res = al.alg2_arbitrary_pass(P.A, 8, 0, v, P.Omega)
+    full = Q.qmatmul(res.U * res.S, Q.qH(res.V))
+    want = Q.qmatmul(_proj(res.Q1), P.A) if v % 2 == 0 else Q.qmatmul(P.A, _proj(res.Q2))
+    np.testing.assert_allclose(full, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("v", [4, 6])
+def test_lemma4_range_inclusion(v):
+    """Lemma 4: the stacked Krylov basis contains the last power sample, so its projection
+    error is no larger than Algorithm 2's with the same Omega and v."""
+    P = synth.config_slow_decay(80, 70, 6, 2, v, seed=9)
+    r2 = al.alg2_arbitrary_pass(P.A, 6, 2, v, P.Omega)
+    r4 = al.alg4_block_flexible(P.A, 6, 2, v, P.Omega)
+    assert norms.range_error(P.A, r4.Q1) <= norms.range_error(P.A, r2.Q1) * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_lemma2_inequality(q):
+    P = synth.config_slow_decay(30, 25, 4, 2, 2, seed=10)
+    X = P.A
+    XHX = Q.qmatmul(Q.qH(X), X)
+    Z = P.Omega
+    Zq = Q.qeye(25)
+    for _ in range(q):
+        Zq = Q.qmatmul(XHX, Zq)
+    Q2, _ = qr(Q.qmatmul(Zq, Z))
+    M = Q.qeye(25) - _proj(Q2)
+    lhs = norms.spectral_norm(Q.qmatmul(X, M)) ** (2 * q)
+    rhs = norms.spectral_norm(Q.qmatmul(Zq, M))
+    assert lhs <= rhs * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 6, 7])
+def test_pass_and_vector_counts(v):
+    g = json.load(open(os.path.join(GOLD, "paper_counts.json")))
+    P = synth.config_slow_decay(30, 24, 3, 2, v, seed=11)
+    ell = 5
+    r2 = al.alg2_arbitrary_pass(P.A, 3, 2, v, P.Omega)
+    r4 = al.alg4_block_flexible(P.A, 3, 2, v, P.Omega)
+    env = {"v": v, "ell": ell, "floor": math.floor}
+    assert r2.passes == eval(g["alg2_passes"], {}, env)
+    assert r4.passes == eval(g["alg4_passes"], {}, env)
+    assert r2.columns == eval(g["alg2_columns"], {}, env)
+    assert r4.columns == eval(g["alg4_columns"], {}, env)
+    assert r2.trace == ["X" if i % 2 == 0 else "XH" for i in range(v)]
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_classical_pass_counts(q):
+    g = json.load(open(os.path.join(GOLD, "paper_counts.json")))
+    P = synth.config_slow_decay(30, 24, 3, 2, 2, seed=12)
+    assert al.alg1_classical(P.A, 3, 2, q, P.Omega).passes == eval(g["alg1_passes"], {}, {"q": q})
+    assert al.alg3_block_classical(P.A, 3, 2, q, P.Omega).passes == eval(g["alg3_passes"], {}, {"q": q})
+
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_side_choice_consistent(v):
+    P = synth.config_slow_decay(30, 45, 5, 3, v, seed=13)
+    assert al.default_side(30, 45, 2) == "XH" and al.default_side(30, 45, 3) == "X"
+    res = al.run("alg2", P.A, 5, 3, v, synth.gaussian_qmat(5, 30, 8), side="XH")
+    assert res.U.shape == (4, 30, 5) and res.V.shape == (4, 45, 5)
+    np.testing.assert_allclose(Q.qmatmul(Q.qH(res.U), res.U), Q.qeye(5), atol=1e-12)
+    np.testing.assert_allclose(Q.qmatmul(Q.qH(res.V), res.V), Q.qeye(5), atol=1e-12)
+    assert norms.lowrank_error(P.A, res.U, res.S, res.V) < 3 * P.sigma[5]
+
+
+def test_known_spectrum_recovered_with_enough_passes():
+    """Config 1: sigma_i = 0.5^i plus 1e-6 noise; with 6 passes the top k values match the
+    constructed ones within the noise norm (Weyl's inequality)."""
+    P = synth.config1()
+    res = al.alg2_arbitrary_pass(P.A, P.k, P.p, 6, P.Omega)
+    nn = 1e-6 * (math.sqrt(4 * 256) + math.sqrt(4 * 192)) * 1.5
+    assert np.all(np.abs(res.S - P.sigma) <= nn)
+
+
+def test_expected_error_bounds_and_decay():
+    """Mean errors over 60 seeds respect Lemma 1 / eq. mn11 / mn12 / Theorem 6 and decrease
+    with the number of passes (Theorem 3's exponential decay)."""
+    P = synth.config_slow_decay(48, 40, 4, 2, 2, seed=14)
+    k, p, ell = 4, 2, 6
+    sig = P.sigma
+    means = {}
+    for v in (2, 3, 4, 5):
+        e1, e2, e4 = [], [], []
+        for s in range(60):
+            Om = synth.gaussian_qmat(1000 + s, 40, ell)
+            r = al.alg2_arbitrary_pass(P.A, k, p, v, Om)
+            e1.append(norms.range_error(P.A, r.Q1))
+            e2.append(norms.corange_error(P.A, r.Q2))
+            r4 = al.alg4_block_flexible(P.A, k, p, v, Om)
+            e4.append(norms.range_error(P.A, r4.Q1) if v % 2 == 0 else norms.corange_error(P.A, r4.Q2))
+        b1, b2 = bounds.mn11_12(sig, k, p, v)
+        assert np.mean(e1) <= b1 and np.mean(e2) <= b2
+        assert np.mean(e4) <= bounds.theorem6(sig, k, p, v)
+        means[v] = (np.mean(e1), np.mean(e2))
+    assert means[4][0] < means[2][0] and means[5][1] < means[3][1]
+    assert bounds.lemma1(sig, k, p, 0) == bounds.mn11_12(sig, k, p, 2)[0]
+    assert bounds.corollary5(sig, k, p) == bounds.lemma4(sig, k, p, 0)
