@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the pass-efficient randomized quaternion QSVD on GB300 (one JSON line).
+
+Workload (one "step"): the FP32 arbitrary-pass range finder workload -- a 4096 x 4096 quaternion
+matrix with FP32 planes, sigma_i = 1/i and Haar-like singular vectors, k = 100, p = 10 -- run
+through Algorithm 2 with each pass budget v in {2, 3, 4, 6, 8}: 23 sketch passes with their
+orthonormalisations, five core QSVDs and lifts.  Metric: sketch passes per second (whole job);
+A-read TB/s and the per-v rank-k QSVD times go in extra keys.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank runs its own replica (weak scaling, no collective on the
+data path); rank 0 prints the line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = N = 4096
+K_RANK, P_OVER = 100, 10
+PASSES = (2, 3, 4, 6, 8)
+METRIC = "sketch passes/s & A-read TB/s; rank-k QSVD time at stated error, BF16/batched vs FP32"
+WORKLOAD = "slow-decay 4096x4096 quaternion, FP32 planes, sigma_i=1/i, k=100, p=10, Algorithm 2 at v in {2,3,4,6,8}"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=lambda: self.lines.extend(self.proc.stdout), daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_work(kid: str, compute: str):
+    """(flops, bytes, bound, peak, unit, peak_note) per launch of a kernel class at this workload.
+    Flops count 32 m n l per quaternion sketch (the Hamilton product, no split overhead)."""
+    pk, src = _peaks()
+    l = K_RANK + P_OVER
+    sk_flops, sk_bytes = 32.0 * M * N * l, 4.0 * M * N * 4
+    tf32 = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+    if kid == "sketch_tc":
+        if compute == "BF16":
+            return sk_flops, sk_bytes / 2, "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s", \
+                f"bf16 sustained ({src})"
+        return sk_flops, sk_bytes, "tensor", tf32, "TFLOP/s", f"tf32 = bf16 sustained ({src}) x 1.1/2.25 nominal"
+    fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12          # unit counts x max SM clock
+    fp64 = 1.25                                         # nominal dense FP64 of the part
+    if kid == "sketch_simt":
+        return sk_flops, sk_bytes, "alu", fp32_simt, "TFLOP/s", "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    if kid == "gram":
+        return 32.0 * M * l * (l + 1) / 2, 16.0 * M * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
+    if kid == "chol":
+        return 32.0 * l ** 3 / 6, 32.0 * l * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
+    if kid == "tri_inv":
+        return 32.0 * l ** 3 / 6, 32.0 * l * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
+    if kid == "jacobi":
+        return 8 * 56.0 * l ** 3 / 2, 32.0 * l * l, "alu", fp32_simt, "TFLOP/s", "FP32 SIMT peak (one CTA can reach 1/152 of it)"
+    return None
+
+
+def roofline(stats, compute, steps):
+    live = {k: v for k, v in stats.items() if v[0] > 0}
+    dom = max(live, key=lambda k: live[k][1])
+    n, ms = live[dom]
+    w = algorithmic_work(dom, compute)
+    out = {"kernel": dom, "launches": n, "avg_ms": ms / n}
+    if w is None:
+        out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return out
+    flops, nbytes, bound, peak, unit, note = w
+    sec = ms / n / 1e3
+    if bound == "hbm":
+        ach = nbytes / sec / 1e9
+    else:
+        ach = flops / sec / 1e12
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = tr.get(dom)
+        if ent and ent.get("source_sha") == _source_sha(ent.get("source", "")):
+            traffic = ent.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    out.update({"bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3), "unit": unit,
+                "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": note,
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes})
+    return out
+
+
+def _source_sha(rel):
+    import hashlib
+    p = os.path.join(ROOT, rel)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if rel and os.path.exists(p) else None
+
+
+def cpu_oracle_sample(P, passes=2):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: Algorithm 2 with v=2 on
+    the full matrix.  Returns (passes/s, seconds, threads)."""
+    from oracle import algorithms as al
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    al.alg2_arbitrary_pass(P.A, P.k, P.p, passes, P.Omega)
+    dt = time.perf_counter() - t0
+    return passes / dt, dt, threads
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import synth
+    P = synth.config2(2)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(P)
+    t0 = time.perf_counter()
+    thr = 0
+    for _ in range(args.steps):
+        _, _, thr = cpu_oracle_sample(P)
+    dt = time.perf_counter() - t0
+    value = 2 * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "sketch passes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "Algorithm 2, v=2, full 4096x4096 matrix per step"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
+                             "sample": "Algorithm 2 with v=2 on the full 4096x4096 matrix per step"},
+            "e2e": {"value": round(value, 5), "unit": "sketch passes/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = synth.config2(4)
+    compute = getattr(qlr, "COMPUTE_" + args.compute)
+    a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
+    A_host = torch.from_numpy(P.A).to(a_dt).contiguous().pin_memory()
+    Om_host = torch.from_numpy(np.ascontiguousarray(P.Omega.transpose(0, 2, 1))).float().contiguous().pin_memory()
+    A = A_host.to(dev, non_blocking=True)
+    om_store = Om_host.to(dev, non_blocking=True)
+    om = om_store.transpose(1, 2)                                    # column-major n x l view
+    U = qlr.empty_thin(M, K_RANK, device=dev)
+    V = qlr.empty_thin(N, K_RANK, device=dev)
+    S = torch.zeros(len(PASSES), K_RANK, dtype=torch.float64, device=dev)
+    ctx = qlr.Context(local)
+    ctx.reserve(max(qlr.workspace_size(M, N, K_RANK, P_OVER, v, qlr.ALG2, compute) for v in PASSES))
+    qsvd_ms = {v: [] for v in PASSES}
+    ev = {v: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for v in PASSES}
+
+    def step(record=False):
+        for i, v in enumerate(PASSES):
+            if record:
+                ev[v][0].record()
+            qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, v, om, U, S[i], V, compute=compute, side=qlr.SIDE_X)
+            if record:
+                ev[v][1].record()
+
+    for _ in range(args.warmup):
+        step()
+    rc = ctx.sync()
+    if rc != 0:
+        raise SystemExit(f"device error {rc} during warm-up")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record()
+    for s in range(args.steps):
+        step(record=(s == args.steps - 1))
+    t1e.record()
+    torch.cuda.synchronize()
+    for v in PASSES:
+        qsvd_ms[v].append(ev[v][0].elapsed_time(ev[v][1]))
+    barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    elapsed_ms = t0e.elapsed_time(t1e)
+    stats = ctx.stats()
+    rc = ctx.sync()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    passes_per_step = sum(PASSES)
+    value = ws * passes_per_step * args.steps / (elapsed_ms / 1e3)
+    a_bytes = A.numel() * A.element_size()
+    tbs = ws * passes_per_step * args.steps * a_bytes / (elapsed_ms / 1e3) / 1e12
+    gpu_launches = sum(n for n, _ in stats.values())
+
+    # end to end through the C ABI with host buffers: H2D of A and Omega, D2H of U, S, V per step
+    U_h = torch.empty(4, K_RANK, M, dtype=torch.float32).pin_memory()
+    V_h = torch.empty(4, K_RANK, N, dtype=torch.float32).pin_memory()
+    S_h = torch.empty(len(PASSES), K_RANK, dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e2e_steps):
+        A.copy_(A_host, non_blocking=True)
+        om_store.copy_(Om_host, non_blocking=True)
+        step()
+        U_h.copy_(U.transpose(1, 2), non_blocking=True)
+        V_h.copy_(V.transpose(1, 2), non_blocking=True)
+        S_h.copy_(S, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * passes_per_step * e2e_steps / (e2e_ms / 1e3)
+    h2d = A_host.numel() * A_host.element_size() + Om_host.numel() * Om_host.element_size()
+    d2h = U_h.numel() * 4 + V_h.numel() * 4 + S_h.numel() * 8
+
+    line = None
+    if rank == 0:
+        roof = roofline(stats, args.compute, args.steps)
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            val, secs, thr = cpu_oracle_sample(P)
+            cpu = {"value": round(val, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
+                   "sample": f"Algorithm 2 with v=2 on the full 4096x4096 matrix ({secs:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "sketch passes/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"TF32X3": "f32 (3xTF32 tensor-core sketch, FP64 Gram/Cholesky)", "F32": "f32 (SIMT)",
+                      "BF16": "bf16 (FP32 accumulate, FP64 Gram/Cholesky)", "TF32": "tf32"}[args.compute],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "passes": list(PASSES), "compute": args.compute,
+                       "l2": "inputs larger than L2 (A = %.0f MB)" % (a_bytes / 1e6), "parallelism": f"replicas x{ws}"},
+            "a_read_tbs": round(tbs, 4),
+            "qsvd_ms": {str(v): round(statistics.mean(qsvd_ms[v]), 3) for v in PASSES},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 3), "unit": "sketch passes/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches,
+            "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in stats.items() if n},
+            "clocks": clk,
+            "device_error": rc,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * qlr.h -- C ABI of the GB300 (sm_103a) pass-efficient randomized quaternion low-rank library.
+ *
+ * Method: pass-efficient randomized low-rank approximation of quaternion matrices
+ * (arXiv 2507.13731).  The hot path is the per-pass quaternion sketch product Y = A X or
+ * Z = A^H Y, run v times by the arbitrary-pass range finder (Algorithm 2) or the flexible block
+ * Krylov variant (Algorithm 4), with an orthonormalisation ("QR") after every pass and a small
+ * truncated QSVD at the end.
+ *
+ * Conventions (all entry points)
+ *  - Quaternion matrices are four real planes (real, i, j, k) -- the paper's X1..X4, Section 2.
+ *    A pure quaternion matrix (zero real part) may pass plane[0] == NULL.
+ *  - The large data matrix A is row-major (ld >= cols).  Thin matrices (Omega, Q, Y, Z, U, V)
+ *    are column-major (ld >= rows).  All pointers inside qlr_qmat are DEVICE pointers.
+ *  - Caller owns every matrix and output buffer.  The context owns its workspace (device
+ *    memory it allocates with cudaMalloc on first need and grows on demand; qlr_reserve
+ *    pre-sizes it so that later calls -- e.g. inside CUDA stream capture -- allocate nothing).
+ *  - Calls are asynchronous on the context's stream.  Host-side validation errors are returned
+ *    immediately.  Device-side conditions (Cholesky breakdown, Jacobi non-convergence, bounded
+ *    waits) are recorded in a device error word; qlr_sync() waits for the stream and returns it.
+ *  - Every function returns QLR_OK (0) or one of the QLR_E* codes below.
+ */
+#ifndef QLR_H
+#define QLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------------------------ */
+#define QLR_OK 0
+#define QLR_EINVAL 1       /* bad argument (null pointer, bad enum, bad layout / dtype combination) */
+#define QLR_ESHAPE 2       /* inconsistent sizes, or k + p > min(m, n) (hypothesis of Lemma 2)    */
+#define QLR_ENOTPD 3       /* Cholesky pivot <= 0: Gram matrix not numerically positive definite  */
+#define QLR_ENOCONV 4      /* core Jacobi QSVD did not converge within its sweep limit            */
+#define QLR_ETIMEOUT 5     /* a bounded device-side wait gave up                                  */
+#define QLR_ECUDA 6        /* a CUDA runtime / driver call failed                                  */
+#define QLR_ENOMEM 7       /* workspace too small and growing it is not allowed (stream capture)  */
+#define QLR_EUNSUPPORTED 8 /* combination not implemented (e.g. a size beyond a kernel's limit)   */
+
+/* ---- storage types ---------------------------------------------------------------------- */
+#define QLR_F64 0
+#define QLR_F32 1
+#define QLR_BF16 2
+
+/* ---- layouts ----------------------------------------------------------------------------- */
+#define QLR_ROW_MAJOR 0
+#define QLR_COL_MAJOR 1
+
+/* ---- arithmetic of the sketch products ------------------------------------------------- */
+#define QLR_COMPUTE_AUTO 0   /* F64 storage -> F64, F32 -> TF32X3, BF16 -> BF16                 */
+#define QLR_COMPUTE_F64 1    /* FP64 SIMT (cuda cores)                                          */
+#define QLR_COMPUTE_F32 2    /* FP32 SIMT: the plain FP32 GPU path                              */
+#define QLR_COMPUTE_TF32 3   /* tcgen05 kind::tf32, one product (FP32 storage)                  */
+#define QLR_COMPUTE_TF32X3 4 /* tcgen05 kind::tf32, hi/lo split of both operands, three products */
+#define QLR_COMPUTE_BF16 5   /* tcgen05 kind::f16 with BF16 operands (BF16 storage of A)         */
+
+/* ---- sketch operator ------------------------------------------------------------------- */
+#define QLR_OP_N 0 /* Y = A X     */
+#define QLR_OP_H 1 /* Y = A^H X   */
+
+/* ---- algorithm / side / orthonormalisation choices ------------------------------------- */
+#define QLR_ALG2 2 /* Algorithm 2 (arbitrary number of passes)              */
+#define QLR_ALG4 4 /* Algorithm 4 (flexible block Krylov, arbitrary views)  */
+#define QLR_SIDE_AUTO (-1)
+#define QLR_SIDE_X 0
+#define QLR_SIDE_XH 1
+#define QLR_ORTH_CHOLQR2 0  /* CholeskyQR2, FP64 Gram and Cholesky                    */
+#define QLR_ORTH_SCHOLQR3 1 /* shifted CholeskyQR3 (Fukaya et al. 2020) for ill-conditioned input */
+
+typedef struct {
+  void* plane[4];  /* device pointers: planes real, i, j, k; plane[0] == NULL => pure quaternion */
+  int64_t rows;    /* number of rows                                                            */
+  int64_t cols;    /* number of columns                                                         */
+  int64_t ld;      /* leading dimension in elements (row stride if row-major, column stride if col-major) */
+  int32_t layout;  /* QLR_ROW_MAJOR or QLR_COL_MAJOR                                            */
+  int32_t dtype;   /* QLR_F64, QLR_F32 or QLR_BF16                                              */
+} qlr_qmat;
+
+typedef struct {
+  int32_t compute; /* QLR_COMPUTE_*; AUTO picks from A's dtype                                  */
+  int32_t side;    /* QLR_SIDE_*; AUTO applies Section 6's rule (even v and n > m: use X^H)     */
+  int32_t orth;    /* QLR_ORTH_*; Algorithm 4's stacked basis always uses QLR_ORTH_SCHOLQR3    */
+  int32_t flags;   /* reserved, must be 0                                                       */
+} qlr_opts;
+
+typedef struct qlr_ctx qlr_ctx;
+
+/* Create a context on CUDA device `device` issuing work on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream).  Allocates the device error word.  Returns QLR_ECUDA on failure. */
+int qlr_create(qlr_ctx** ctx, int device, void* stream);
+/* Synchronise, free the workspace and the context.  ctx may be NULL. */
+int qlr_destroy(qlr_ctx* ctx);
+/* Change the stream later calls are issued on. */
+int qlr_set_stream(qlr_ctx* ctx, void* stream);
+/* Make sure the workspace holds at least `bytes` bytes (cudaMalloc now, never inside a call). */
+int qlr_reserve(qlr_ctx* ctx, size_t bytes);
+/* Workspace bytes a qlr_qsvd_lowrank / qlr_qblock_krylov call with these sizes needs. */
+size_t qlr_workspace_size(int64_t m, int64_t n, int k, int p, int passes, int algo, int compute);
+/* Wait for the context's stream; return the first device-side error code (and clear it), or
+ * QLR_ECUDA if the stream reported a CUDA error. */
+int qlr_sync(qlr_ctx* ctx);
+/* Static English text for an error code. */
+const char* qlr_strerror(int code);
+
+/* ---- launch statistics (no paper counterpart: measurement support) ----------------------
+ * Kernel classes counted / timed by the library.  Launch counts are always kept; with timing
+ * enabled every launch is bracketed by CUDA events recorded on the context stream (do not
+ * enable inside stream capture).  qlr_stats waits for the stream and returns, for class `kid`,
+ * the number of launches and the summed event time in milliseconds since the last reset. */
+#define QLR_KID_SKETCH_TC 0   /* tcgen05 sketch product                     */
+#define QLR_KID_SKETCH_SIMT 1 /* SIMT sketch product / thin GEMMs           */
+#define QLR_KID_GRAM 2        /* FP64 Gram (partials + reduction)           */
+#define QLR_KID_CHOL 3        /* quaternion Cholesky                         */
+#define QLR_KID_TRIINV 4      /* triangular inverse                          */
+#define QLR_KID_APPLY 5       /* Q = Y R^{-1}, lifts, projections            */
+#define QLR_KID_JACOBI 6      /* core QSVD sweeps                            */
+#define QLR_KID_REFINE 7      /* core QSVD FP64 evaluation + ranking         */
+#define QLR_KID_MISC 8        /* conversions, operand staging, small products */
+#define QLR_KID_COUNT 9
+int qlr_set_timing(qlr_ctx* ctx, int enable);
+int qlr_reset_stats(qlr_ctx* ctx);
+int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
+
+/*
+ * qlr_qsketch -- one sketch pass (the products X Q2 / X^H Q1 of Algorithm 2 and Algorithm 4,
+ * and the Hamilton product of eq. (1), Section 2, summed over the inner index).
+ *   op == QLR_OP_N:  Y (m x l) = A (m x n) X (n x l)
+ *   op == QLR_OP_H:  Y (n x l) = A^H X (m x l), with A^H = A1^T - A2^T i - A3^T j - A4^T k (Section 2)
+ * A: row-major, dtype F64 / F32 / BF16 (pure allowed).  X: column-major, 4 planes; its dtype
+ * must be F64 for COMPUTE_F64, F32 for F32 / TF32 / TF32X3, F32 or BF16 for BF16 (F32 input is
+ * rounded to BF16 on the device).  Y: column-major, F64 (COMPUTE_F64) or F32.  A is read once.
+ * Errors: QLR_EINVAL (null/dtype/layout), QLR_ESHAPE (size mismatch), QLR_EUNSUPPORTED.
+ */
+int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute);
+
+/*
+ * qlr_qgram -- G = Y^H Y in FP64 (the Gram step of CholeskyQR; the "QR" of Algorithms 1-4,
+ * Def. 1 eq. QQR).  Y: m x l column-major F32 or F64.  G: device, FP64, l x l x 4 planes,
+ * column-major (G[c*l*l + j*l + i]), full Hermitian matrix written.
+ */
+int qlr_qgram(qlr_ctx* ctx, const qlr_qmat* Y, double* G);
+
+/*
+ * qlr_qchol -- upper-triangular R with real positive diagonal and G = R^H R (quaternion
+ * Cholesky, FP64).  G, R: device FP64 l x l x 4 column-major (may not alias).  Lower triangle of
+ * R is written as zero.  A non-positive pivot records QLR_ENOTPD in the device error word and
+ * continues with a tiny positive pivot so later kernels see finite numbers.
+ */
+int qlr_qchol(qlr_ctx* ctx, int l, const double* G, double* R);
+
+/*
+ * qlr_cholqr -- thin QR Y = Q R (Def. 1, eq. QQR) by CholeskyQR2 (orth = QLR_ORTH_CHOLQR2) or
+ * shifted CholeskyQR3 (QLR_ORTH_SCHOLQR3).  Gram products and Cholesky factors in FP64, the
+ * triangular solves in the storage precision of Y.  Y, Q: m x l column-major, same dtype
+ * (F32 or F64), must not alias.  R: device FP64 l x l x 4, upper triangular, real positive
+ * diagonal (the unique thin QR for full-rank Y).  R may be NULL if not needed.
+ */
+int qlr_cholqr(qlr_ctx* ctx, const qlr_qmat* Y, qlr_qmat* Q, double* R, int orth);
+
+/*
+ * qlr_qtsvd -- core truncated QSVD (R, k) of a small l x l quaternion matrix (the
+ * "Truncated SVD(R,k)" step of Algorithms 1, 2, 4; QSVD of Def. 1 eq. qsvd) through the
+ * complex adjoint chi(R) with structure-preserving one-sided Jacobi.  R: device FP64 l x l x 4
+ * column-major.  Outputs (device, FP64): L (l x k x 4), S (k, descending), Rt (l x k x 4) with
+ * R ~= L diag(S) Rt^H.  prec: QLR_F64 runs the Jacobi in FP64; QLR_F32 runs it in FP32 and
+ * re-evaluates S, L in FP64 from the FP32 right vectors.  QLR_ENOCONV if it did not converge.
+ */
+int qlr_qtsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec);
+
+/*
+ * qlr_qrangefinder -- v passes of Algorithm 2 (range finder part): for i = 1..v, odd i:
+ * [Q1, R1] = QR(X Q2), even i: [Q2, R2] = QR(X^H Q1), starting from Q2 = Omega.
+ * A: m x n row-major.  omega: Gaussian test matrix (Def. 2), l = k + p columns, n rows (side X)
+ * or m rows (side X^H), column-major, dtype F64 or F32.  Q1 (m x l) and Q2 (n x l): column-major,
+ * F64 or F32 (F64 iff compute is F64); Q2 is left equal to omega's contents when v == 1 is not
+ * allowed (v >= 2).  R: device FP64 l x l x 4 -- R^(2) for even v, R^(1) for odd v.  side_used
+ * (host, may be NULL) receives QLR_SIDE_X or QLR_SIDE_XH.  With side X^H the roles of (m, n) and
+ * of (Q1, Q2) are those of the algorithm run on A^H (Q1 is then n x l).
+ * Errors: QLR_ESHAPE if k + p > min(m, n) or v < 2.
+ */
+int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr_qmat* omega,
+                     const qlr_opts* opts, qlr_qmat* Q1, qlr_qmat* Q2, double* R, int* side_used);
+
+/*
+ * qlr_qsvd_lowrank -- rank-k approximation A ~= U diag(S) V^H by Algorithm 2 (algo = QLR_ALG2)
+ * or Algorithm 4 (QLR_ALG4, with block width l = k + p) with exactly `passes` passes over A,
+ * followed by the truncated QSVD of the last R and the lifts V = Q2 V_hat, U = Q1 U_hat.
+ * U: m x k, V: n x k, column-major, F32 or F64; S: device FP64 array of k values, descending.
+ * The call leaves the result defined up to a right unit-quaternion factor per column pair.
+ */
+int qlr_qsvd_lowrank(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo,
+                     const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V);
+
+/*
+ * qlr_qblock_krylov -- Algorithm 4 (flexible block Krylov, Section 5) with block size b >= k:
+ * the same as qlr_qsvd_lowrank(..., k, b - k, passes, QLR_ALG4, ...).
+ */
+int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes, const qlr_qmat* omega,
+                      const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V);
+
+/*
+ * qlr_qsvd_lowrank_batched -- `count` independent Algorithm 2 problems of uneven sizes.  Arrays
+ * (host) of `count` descriptors / values; S[i] is a device FP64 buffer of k[i] values.  Each
+ * sketch pass of all problems runs as one grouped persistent launch; the whole v-pass sequence
+ * is captured once into a CUDA graph per (context, problem set) and replayed.
+ */
+int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p,
+                             int passes, const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U,
+                             double* const* S, qlr_qmat* V);
+
+/*
+ * qlr_residual_norm -- measurement pass (not one of the method's passes): estimate
+ * ||A - Q Q^H A||_2 (side == QLR_SIDE_X, Q m x l) or ||A - A Q Q^H||_2 (side == QLR_SIDE_XH,
+ * Q n x l) -- the errors bounded by Lemma 1, Theorem 3 and eqs. (mn11)/(mn12) -- by `iters`
+ * steps of block power iteration with `nvec` vectors started from `start` (column-major F32/F64,
+ * n x nvec for side X, m x nvec for side X^H).  *out (host) receives the estimate (a lower
+ * bound that converges to the norm).  Synchronises the stream.
+ */
+int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start,
+                      int iters, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QLR_H */

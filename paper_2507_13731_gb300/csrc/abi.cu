@@ -1,0 +1,621 @@
+// C ABI: context, argument validation, and the pass scheduler for Algorithms 2 and 4.
+//
+// Algorithm 2 (arbitrary passes): Q2 <- Omega; for i = 1..v: odd i: [Q1, R1] = QR(X Q2),
+// even i: [Q2, R2] = QR(X^H Q1); TSVD of R2 (even v: [V_hat, S, U_hat]) or R1 (odd v:
+// [U_hat, S, V_hat]); V = Q2 V_hat, U = Q1 U_hat.
+// Algorithm 4 (flexible block Krylov): the same alternation, with the per-pass bases of one side
+// stacked into K, a QR of K, one final wide pass and the TSVD of its R.
+// Section 6: the algorithm may run on X = A or on X = A^H; on A^H the two sketch operators swap
+// and the outputs swap back (A ~= V' S U'^H).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "qlr_internal.h"
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool valid_dtype(int d) { return d == QLR_F64 || d == QLR_F32 || d == QLR_BF16; }
+
+int check_qmat(const qlr_qmat* q, int layout, bool allow_pure) {
+  if (!q) return QLR_EINVAL;
+  if (q->layout != layout || !valid_dtype(q->dtype)) return QLR_EINVAL;
+  if (q->rows < 0 || q->cols < 0) return QLR_ESHAPE;
+  const int64_t inner = (layout == QLR_ROW_MAJOR) ? q->cols : q->rows;
+  if (q->ld < std::max<int64_t>(1, inner)) return QLR_ESHAPE;
+  for (int c = 0; c < 4; ++c)
+    if (q->plane[c] == nullptr && !(c == 0 && allow_pure) && q->rows > 0 && q->cols > 0) return QLR_EINVAL;
+  return QLR_OK;
+}
+
+int resolve_compute(int compute, int a_dtype) {
+  if (compute != QLR_COMPUTE_AUTO) return compute;
+  if (a_dtype == QLR_F64) return QLR_COMPUTE_F64;
+  if (a_dtype == QLR_BF16) return QLR_COMPUTE_BF16;
+  return QLR_COMPUTE_TF32X3;
+}
+
+bool valid_compute(int c) { return c >= QLR_COMPUTE_F64 && c <= QLR_COMPUTE_BF16; }
+
+// Thin-matrix dtype used by the scheduler for a compute mode.
+int thin_dtype(int compute) { return compute == QLR_COMPUTE_F64 ? QLR_F64 : QLR_F32; }
+
+size_t gram_ws_bound(int64_t l) {
+  size_t per = (size_t)32 * l * l;
+  size_t cap = std::max<size_t>(per, (size_t)64 << 20);
+  return cap + (size_t)8 * ((l + 31) / 32) * ((l + 31) / 32) + 4096;
+}
+
+size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
+  return (size_t)5 * 32 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 8 * 256;
+}
+
+size_t tsvd_ws_bound(int64_t l) { return (size_t)64 * l * l + 16 * l + 8192; }
+
+// ---------------------------------------------------------------------------------------
+struct Sched {
+  qlr_ctx* ctx;
+  WsArena* ws;
+  const qlr_qmat* A;
+  int compute;
+  int tdt;          // thin dtype
+  int op_fwd, op_bwd;
+  int64_t rows_fwd, rows_bwd;   // X is rows_fwd x rows_bwd
+  bool allow_simt_fallback = false;
+
+  int sketch(int op, const qlr_qmat& B, qlr_qmat& Y) {
+    if (compute == QLR_COMPUTE_F64 || compute == QLR_COMPUTE_F32) {
+      qlr::GemmArgs g{};
+      for (int c = 0; c < 4; ++c) { g.a[c] = A->plane[c]; g.b[c] = B.plane[c]; g.c[c] = Y.plane[c]; }
+      g.a_dtype = A->dtype; g.b_dtype = B.dtype; g.c_dtype = Y.dtype;
+      g.ldb = B.ld; g.ldc = Y.ld;
+      if (op == QLR_OP_N) { g.sa_i = A->ld; g.sa_k = 1; g.i_contig = false; g.conj_a = false; g.M = A->rows; g.K = A->cols; }
+      else { g.sa_i = 1; g.sa_k = A->ld; g.i_contig = true; g.conj_a = true; g.M = A->cols; g.K = A->rows; }
+      g.N = B.cols; g.alpha = 1.0; g.beta = 0.0;
+      g.acc64 = (compute == QLR_COMPUTE_F64);
+      g.kid = QLR_KID_SKETCH_SIMT;
+      return qlr::gemm_simt(ctx, g);
+    }
+    if (!qlr::sketch_tc_supported(op, *A, B, compute)) {
+      if (!allow_simt_fallback) return QLR_EUNSUPPORTED;
+      Sched s2 = *this;                 // documented AUTO behaviour: SIMT FP32 for unsupported shapes
+      s2.compute = QLR_COMPUTE_F32;
+      return s2.sketch(op, B, Y);
+    }
+    return qlr::sketch_tc(ctx, op, *A, B, Y, compute, *ws);
+  }
+
+  qlr_qmat thin(int64_t rows, int64_t cols, int dt = -1) {
+    qlr_qmat q{};
+    q.rows = rows; q.cols = cols; q.ld = std::max<int64_t>(rows, 1);
+    q.layout = QLR_COL_MAJOR; q.dtype = dt < 0 ? tdt : dt;
+    size_t esz = qlr_dtype_size(q.dtype);
+    char* p = ws->take<char>((size_t)4 * q.ld * cols * esz);
+    for (int c = 0; c < 4; ++c) q.plane[c] = p ? p + (size_t)c * q.ld * cols * esz : nullptr;
+    return q;
+  }
+};
+
+qlr_qmat col_slice(const qlr_qmat& q, int64_t c0, int64_t nc) {
+  qlr_qmat s = q;
+  size_t esz = qlr_dtype_size(q.dtype);
+  for (int c = 0; c < 4; ++c) s.plane[c] = q.plane[c] ? static_cast<char*>(q.plane[c]) + (size_t)c0 * q.ld * esz : nullptr;
+  s.cols = nc;
+  return s;
+}
+
+// C (rows x k) = Q (rows x l) * S (FP64 small l x k, plane stride l*k)
+int lift(qlr_ctx* ctx, const qlr_qmat& Q, const double* S, int l, int k, qlr_qmat& C) {
+  qlr::GemmArgs g{};
+  for (int c = 0; c < 4; ++c) { g.a[c] = Q.plane[c]; g.b[c] = S + (size_t)c * l * k; g.c[c] = C.plane[c]; }
+  g.sa_i = 1; g.sa_k = Q.ld; g.i_contig = true; g.conj_a = false; g.a_dtype = Q.dtype;
+  g.ldb = l; g.b_dtype = QLR_F64; g.ldc = C.ld; g.c_dtype = C.dtype;
+  g.M = Q.rows; g.N = k; g.K = l; g.alpha = 1.0; g.beta = 0.0;
+  g.acc64 = (Q.dtype == QLR_F64 || C.dtype == QLR_F64);
+  return qlr::gemm_simt(ctx, g);
+}
+
+// Common argument checks for the algorithm entry points; resolves compute and side.
+int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr_qmat* omega, const qlr_opts* opts,
+            int& compute, int& side, bool& auto_compute) {
+  if (!ctx) return QLR_EINVAL;
+  QLR_TRY(check_qmat(A, QLR_ROW_MAJOR, true));
+  QLR_TRY(check_qmat(omega, QLR_COL_MAJOR, false));
+  if (opts && opts->flags != 0) return QLR_EINVAL;
+  if (k < 1 || p < 0 || passes < 2) return QLR_ESHAPE;
+  const int64_t l = (int64_t)k + p;
+  if (l > std::min(A->rows, A->cols)) return QLR_ESHAPE;
+  auto_compute = (opts == nullptr || opts->compute == QLR_COMPUTE_AUTO);
+  compute = resolve_compute(opts ? opts->compute : QLR_COMPUTE_AUTO, A->dtype);
+  if (!valid_compute(compute)) return QLR_EINVAL;
+  if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
+  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && A->dtype != QLR_F32) return QLR_EINVAL;
+  side = opts ? opts->side : QLR_SIDE_AUTO;
+  if (side == QLR_SIDE_AUTO) side = (passes % 2 == 0 && A->cols > A->rows) ? QLR_SIDE_XH : QLR_SIDE_X;
+  if (side != QLR_SIDE_X && side != QLR_SIDE_XH) return QLR_EINVAL;
+  const int64_t om_rows = (side == QLR_SIDE_X) ? A->cols : A->rows;
+  if (omega->rows != om_rows || omega->cols != l) return QLR_ESHAPE;
+  if (omega->dtype == QLR_BF16) return QLR_EINVAL;
+  return QLR_OK;
+}
+
+void init_sched(Sched& S, qlr_ctx* ctx, WsArena* ws, const qlr_qmat* A, int compute, int side) {
+  S.ctx = ctx; S.ws = ws; S.A = A; S.compute = compute; S.tdt = thin_dtype(compute);
+  S.op_fwd = (side == QLR_SIDE_X) ? QLR_OP_N : QLR_OP_H;
+  S.op_bwd = (side == QLR_SIDE_X) ? QLR_OP_H : QLR_OP_N;
+  S.rows_fwd = (side == QLR_SIDE_X) ? A->rows : A->cols;
+  S.rows_bwd = (side == QLR_SIDE_X) ? A->cols : A->rows;
+}
+
+// Omega in the scheduler's thin dtype (copy only when the dtype differs).
+int omega_in(Sched& S, const qlr_qmat* omega, qlr_qmat& out) {
+  if (omega->dtype == S.tdt) { out = *omega; return QLR_OK; }
+  out = S.thin(omega->rows, omega->cols);
+  if (!S.ws->ok) return QLR_ENOMEM;
+  return qlr::convert_qmat(S.ctx, *omega, out);
+}
+
+// Algorithm 2's v passes.  Q1: rows_fwd x l, Q2: rows_bwd x l, R: last R (FP64 l x l x 4).
+int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth) {
+  qlr_qmat Y = S.thin(S.rows_fwd, l), Z = S.thin(S.rows_bwd, l);
+  if (!S.ws->ok) return QLR_ENOMEM;
+  const qlr_qmat* q2 = &om;
+  for (int i = 1; i <= v; ++i) {
+    if (i % 2 == 1) {
+      QLR_TRY(S.sketch(S.op_fwd, *q2, Y));                          // X Q2
+      QLR_TRY(qlr::cholqr(S.ctx, Y, Q1, i == v ? R : nullptr, orth, *S.ws));   // [Q1, R1] = QR(.)
+    } else {
+      QLR_TRY(S.sketch(S.op_bwd, Q1, Z));                           // X^H Q1
+      QLR_TRY(qlr::cholqr(S.ctx, Z, Q2, i == v ? R : nullptr, orth, *S.ws));   // [Q2, R2] = QR(.)
+      q2 = &Q2;
+    }
+  }
+  return QLR_OK;
+}
+
+// Algorithm 4.  On return Q1 (rows_fwd x L), Q2 (rows_bwd x L), R (L x L) with L the stacked width.
+int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth) {
+  const int s = (v - 1) / 2;
+  const bool even = (v % 2 == 0);
+  const int nblk = even ? v / 2 : (v - 1) / 2;
+  const int64_t Lw = (int64_t)nblk * l;
+  qlr_qmat K = S.thin(even ? S.rows_fwd : S.rows_bwd, Lw);
+  qlr_qmat Y = S.thin(S.rows_fwd, l), Z = S.thin(S.rows_bwd, l);
+  qlr_qmat q1cur = S.thin(S.rows_fwd, l), q2cur = S.thin(S.rows_bwd, l);
+  if (!S.ws->ok) return QLR_ENOMEM;
+  const qlr_qmat* q2prev = &om;                 // Q2_0 = Omega
+  for (int j = 1; j <= s; ++j) {
+    if (2 * j - 1 < v) {                        // odd view: range side
+      qlr_qmat dst = even ? col_slice(K, (int64_t)(j - 1) * l, l) : q1cur;
+      QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
+      QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth, *S.ws));
+      q1cur = dst;
+    }
+    if (2 * j < v) {
+      qlr_qmat dst = even ? q2cur : col_slice(K, (int64_t)(j - 1) * l, l);
+      QLR_TRY(S.sketch(S.op_bwd, q1cur, Z));
+      QLR_TRY(qlr::cholqr(S.ctx, Z, dst, nullptr, orth, *S.ws));
+      q2cur = dst;
+      q2prev = &q2cur;
+    }
+  }
+  if (even) {
+    qlr_qmat dst = col_slice(K, (int64_t)s * l, l);
+    QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
+    QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth, *S.ws));
+    QLR_TRY(qlr::cholqr(S.ctx, K, Q1, nullptr, QLR_ORTH_SCHOLQR3, *S.ws));   // [Q1, ~] = QR(K1)
+    qlr_qmat W = S.thin(S.rows_bwd, Lw);
+    if (!S.ws->ok) return QLR_ENOMEM;
+    QLR_TRY(S.sketch(S.op_bwd, Q1, W));                                       // X^H Q1
+    QLR_TRY(qlr::cholqr(S.ctx, W, Q2, R, orth, *S.ws));                        // [Q2, R2]
+  } else {
+    QLR_TRY(qlr::cholqr(S.ctx, K, Q2, nullptr, QLR_ORTH_SCHOLQR3, *S.ws));   // [Q2, ~] = QR(K2)
+    qlr_qmat W = S.thin(S.rows_fwd, Lw);
+    if (!S.ws->ok) return QLR_ENOMEM;
+    QLR_TRY(S.sketch(S.op_fwd, Q2, W));                                       // X Q2
+    QLR_TRY(qlr::cholqr(S.ctx, W, Q1, R, orth, *S.ws));                        // [Q1, R1]
+  }
+  return QLR_OK;
+}
+
+int64_t stacked_width(int algo, int l, int v) {
+  if (algo != QLR_ALG4) return l;
+  return (int64_t)((v % 2 == 0) ? v / 2 : (v - 1) / 2) * l;
+}
+
+size_t lowrank_ws(int64_t m, int64_t n, int k, int p, int v, int algo, int compute) {
+  const int64_t l = k + p;
+  const int64_t L = std::max<int64_t>(l, stacked_width(algo, (int)l, v));
+  const size_t esz = (compute == QLR_COMPUTE_F64) ? 8 : 4;
+  const int64_t rows = std::max(m, n);
+  size_t b = 0;
+  b += (size_t)4 * esz * (m + n) * l * 4;        // Y, Z, q1cur, q2cur
+  b += (size_t)4 * esz * rows * L * 3;           // K, W, Q1/Q2 (stacked)
+  b += (size_t)4 * esz * (m + n) * L;            // Q1, Q2 when not caller-provided
+  b += (size_t)4 * esz * rows * l;               // omega conversion
+  b += (size_t)32 * L * L * 2 + (size_t)64 * L * k + 8 * k;
+  b += cholqr_ws_bound(rows, L, esz) + tsvd_ws_bound(L);
+  b += qlr::sketch_tc_ws(rows, L, 160);           // tensor-core operand staging + split-K partials
+  return b + ((size_t)4 << 20);
+}
+
+}  // namespace
+
+// ========================================================================================
+static cudaEvent_t pool_get(qlr_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+KTimer::KTimer(qlr_ctx* c, int k) : ctx(c), kid(k) {
+  ctx->launches[kid] += 1;
+  if (ctx->timing) {
+    e0 = pool_get(ctx);
+    e1 = pool_get(ctx);
+    if (e0) cudaEventRecord(e0, ctx->stream);
+  }
+}
+KTimer::~KTimer() {
+  if (e0 && e1) {
+    cudaEventRecord(e1, ctx->stream);
+    ctx->ev_pending.push_back({kid, {e0, e1}});
+  }
+}
+
+static void resolve_pending(qlr_ctx* ctx) {
+  for (auto& pe : ctx->ev_pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pe.second.first, pe.second.second) == cudaSuccess) ctx->ms[pe.first] += t;
+    else cudaGetLastError();
+    ctx->ev_pool.push_back(pe.second.first);
+    ctx->ev_pool.push_back(pe.second.second);
+  }
+  ctx->ev_pending.clear();
+}
+
+int qlr_ensure_ws(qlr_ctx* ctx, size_t bytes) {
+  if (ctx->ws_bytes >= bytes) return QLR_OK;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) return QLR_ENOMEM;
+  QLR_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws) { cudaFree(ctx->ws); ctx->ws = nullptr; ctx->ws_bytes = 0; }
+  size_t want = std::max(bytes, ctx->ws_bytes * 2);
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) { cudaGetLastError(); ctx->ws = nullptr; return QLR_ENOMEM; }
+    want = bytes;
+  }
+  ctx->ws_bytes = want;
+  return QLR_OK;
+}
+
+extern "C" {
+
+int qlr_create(qlr_ctx** out, int device, void* stream) {
+  if (!out) return QLR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) { cudaGetLastError(); return QLR_ECUDA; }
+  DeviceGuard g(device);
+  qlr_ctx* c = new qlr_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) { delete c; return QLR_ECUDA; }
+  if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) { cudaFree(c->d_err); delete c; return QLR_ECUDA; }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return QLR_OK;
+}
+
+int qlr_set_timing(qlr_ctx* ctx, int enable) {
+  if (!ctx) return QLR_EINVAL;
+  ctx->timing = enable != 0;
+  return QLR_OK;
+}
+
+int qlr_reset_stats(qlr_ctx* ctx) {
+  if (!ctx) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return QLR_ECUDA;
+  resolve_pending(ctx);
+  for (int i = 0; i < QLR_KID_COUNT; ++i) { ctx->launches[i] = 0; ctx->ms[i] = 0.0; }
+  return QLR_OK;
+}
+
+int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms) {
+  if (!ctx || kid < 0 || kid >= QLR_KID_COUNT) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return QLR_ECUDA;
+  resolve_pending(ctx);
+  if (launches) *launches = ctx->launches[kid];
+  if (total_ms) *total_ms = ctx->ms[kid];
+  return QLR_OK;
+}
+
+int qlr_destroy(qlr_ctx* ctx) {
+  if (!ctx) return QLR_OK;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  resolve_pending(ctx);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return QLR_OK;
+}
+
+int qlr_set_stream(qlr_ctx* ctx, void* stream) {
+  if (!ctx) return QLR_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return QLR_OK;
+}
+
+int qlr_reserve(qlr_ctx* ctx, size_t bytes) {
+  if (!ctx) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  return qlr_ensure_ws(ctx, bytes);
+}
+
+size_t qlr_workspace_size(int64_t m, int64_t n, int k, int p, int passes, int algo, int compute) {
+  return lowrank_ws(m, n, k, p, passes, algo, compute);
+}
+
+int qlr_sync(qlr_ctx* ctx) {
+  if (!ctx) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return QLR_ECUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return QLR_ECUDA;
+  if (h != 0) cudaMemset(ctx->d_err, 0, sizeof(int));
+  return h;
+}
+
+const char* qlr_strerror(int code) {
+  switch (code) {
+    case QLR_OK: return "success";
+    case QLR_EINVAL: return "invalid argument";
+    case QLR_ESHAPE: return "inconsistent sizes (or k + p > min(m, n))";
+    case QLR_ENOTPD: return "Cholesky breakdown: Gram matrix not numerically positive definite";
+    case QLR_ENOCONV: return "core Jacobi QSVD did not converge";
+    case QLR_ETIMEOUT: return "bounded device wait timed out";
+    case QLR_ECUDA: return "CUDA error";
+    case QLR_ENOMEM: return "workspace too small";
+    case QLR_EUNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown error";
+}
+
+int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute) {
+  if (!ctx) return QLR_EINVAL;
+  QLR_TRY(check_qmat(A, QLR_ROW_MAJOR, true));
+  QLR_TRY(check_qmat(X, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(Y, QLR_COL_MAJOR, false));
+  if (op != QLR_OP_N && op != QLR_OP_H) return QLR_EINVAL;
+  compute = resolve_compute(compute, A->dtype);
+  if (!valid_compute(compute)) return QLR_EINVAL;
+  const int64_t inner = (op == QLR_OP_N) ? A->cols : A->rows, outer = (op == QLR_OP_N) ? A->rows : A->cols;
+  if (X->rows != inner || Y->rows != outer || Y->cols != X->cols) return QLR_ESHAPE;
+  const int ydt = (compute == QLR_COMPUTE_F64) ? QLR_F64 : QLR_F32;
+  if (Y->dtype != ydt) return QLR_EINVAL;
+  if (compute == QLR_COMPUTE_F64 && X->dtype != QLR_F64) return QLR_EINVAL;
+  if ((compute == QLR_COMPUTE_F32 || compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && X->dtype != QLR_F32)
+    return QLR_EINVAL;
+  if (compute == QLR_COMPUTE_BF16 && !(X->dtype == QLR_F32 || X->dtype == QLR_BF16)) return QLR_EINVAL;
+  if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
+  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && A->dtype != QLR_F32) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (compute >= QLR_COMPUTE_TF32) QLR_TRY(qlr_ensure_ws(ctx, qlr::sketch_tc_ws(X->rows, X->cols, ctx->num_sms)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  Sched S{};
+  init_sched(S, ctx, &ws, A, compute, QLR_SIDE_X);
+  return S.sketch(op, *X, *Y);
+}
+
+int qlr_qgram(qlr_ctx* ctx, const qlr_qmat* Y, double* G) {
+  if (!ctx || !G) return QLR_EINVAL;
+  QLR_TRY(check_qmat(Y, QLR_COL_MAJOR, false));
+  if (Y->dtype == QLR_BF16) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, gram_ws_bound(Y->cols)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  return qlr::gram(ctx, *Y, G, ws);
+}
+
+int qlr_qchol(qlr_ctx* ctx, int l, const double* G, double* R) {
+  if (!ctx || !G || !R || l < 0) return QLR_EINVAL;
+  if (G == R) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  return qlr::chol(ctx, l, G, R, 0.0);
+}
+
+int qlr_cholqr(qlr_ctx* ctx, const qlr_qmat* Y, qlr_qmat* Q, double* R, int orth) {
+  if (!ctx) return QLR_EINVAL;
+  QLR_TRY(check_qmat(Y, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(Q, QLR_COL_MAJOR, false));
+  if (Y->dtype == QLR_BF16 || Q->dtype != Y->dtype) return QLR_EINVAL;
+  if (Q->rows != Y->rows || Q->cols != Y->cols) return QLR_ESHAPE;
+  if (Y->cols > Y->rows) return QLR_ESHAPE;
+  if (orth != QLR_ORTH_CHOLQR2 && orth != QLR_ORTH_SCHOLQR3) return QLR_EINVAL;
+  for (int c = 0; c < 4; ++c)
+    if (Q->plane[c] == Y->plane[c]) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, cholqr_ws_bound(Y->rows, Y->cols, qlr_dtype_size(Y->dtype))));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  return qlr::cholqr(ctx, *Y, *Q, R, orth, ws);
+}
+
+int qlr_qtsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec) {
+  if (!ctx || !R || !L || !S || !Rt) return QLR_EINVAL;
+  if (l < 1 || k < 1 || k > l) return QLR_ESHAPE;
+  if (prec != QLR_F64 && prec != QLR_F32) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, tsvd_ws_bound(l)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  return qlr::core_tsvd(ctx, l, R, k, L, S, Rt, prec, ws);
+}
+
+int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr_qmat* omega,
+                     const qlr_opts* opts, qlr_qmat* Q1, qlr_qmat* Q2, double* R, int* side_used) {
+  int compute, side;
+  bool autoc;
+  QLR_TRY(prepare(ctx, A, k, p, passes, omega, opts, compute, side, autoc));
+  QLR_TRY(check_qmat(Q1, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(Q2, QLR_COL_MAJOR, false));
+  if (!R) return QLR_EINVAL;
+  const int l = k + p;
+  const int tdt = thin_dtype(compute);
+  const int64_t rf = (side == QLR_SIDE_X) ? A->rows : A->cols, rb = (side == QLR_SIDE_X) ? A->cols : A->rows;
+  if (Q1->rows != rf || Q1->cols != l || Q2->rows != rb || Q2->cols != l) return QLR_ESHAPE;
+  if (Q1->dtype != tdt || Q2->dtype != tdt) return QLR_EINVAL;
+  const int orth = opts ? opts->orth : QLR_ORTH_CHOLQR2;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, lowrank_ws(A->rows, A->cols, k, p, passes, QLR_ALG2, compute)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  Sched S{};
+  init_sched(S, ctx, &ws, A, compute, side);
+  S.allow_simt_fallback = autoc;
+  qlr_qmat om;
+  QLR_TRY(omega_in(S, omega, om));
+  QLR_TRY(run_alg2(S, l, passes, om, *Q1, *Q2, R, orth));
+  if (side_used) *side_used = side;
+  return QLR_OK;
+}
+
+static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo, const qlr_qmat* omega,
+                        const qlr_opts* opts, qlr_qmat* U, double* S_out, qlr_qmat* V) {
+  int compute, side;
+  bool autoc;
+  QLR_TRY(prepare(ctx, A, k, p, passes, omega, opts, compute, side, autoc));
+  if (algo != QLR_ALG2 && algo != QLR_ALG4) return QLR_EINVAL;
+  QLR_TRY(check_qmat(U, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(V, QLR_COL_MAJOR, false));
+  if (!S_out) return QLR_EINVAL;
+  if (U->rows != A->rows || U->cols != k || V->rows != A->cols || V->cols != k) return QLR_ESHAPE;
+  if (U->dtype == QLR_BF16 || V->dtype == QLR_BF16) return QLR_EINVAL;
+  const int l = k + p;
+  const int64_t L = stacked_width(algo, l, passes);
+  if (L > std::min(A->rows, A->cols)) return QLR_ESHAPE;
+  const int orth = opts ? opts->orth : QLR_ORTH_CHOLQR2;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, lowrank_ws(A->rows, A->cols, k, p, passes, algo, compute)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  Sched S{};
+  init_sched(S, ctx, &ws, A, compute, side);
+  S.allow_simt_fallback = autoc;
+  qlr_qmat om;
+  QLR_TRY(omega_in(S, omega, om));
+  qlr_qmat Q1 = S.thin(S.rows_fwd, L), Q2 = S.thin(S.rows_bwd, L);
+  double* R = ws.take<double>((size_t)4 * L * L);
+  double* Lm = ws.take<double>((size_t)4 * L * k);
+  double* Rt = ws.take<double>((size_t)4 * L * k);
+  if (!ws.ok) return QLR_ENOMEM;
+  if (algo == QLR_ALG2) QLR_TRY(run_alg2(S, l, passes, om, Q1, Q2, R, orth));
+  else QLR_TRY(run_alg4(S, l, passes, om, Q1, Q2, R, orth));
+  const int prec = (compute == QLR_COMPUTE_F64) ? QLR_F64 : QLR_F32;
+  QLR_TRY(qlr::core_tsvd(ctx, (int)L, R, k, Lm, S_out, Rt, prec, ws));
+  // even v: [V_hat, S, U_hat] = TSVD(R2); odd v: [U_hat, S, V_hat] = TSVD(R1)
+  const double* Uhat = (passes % 2 == 0) ? Rt : Lm;
+  const double* Vhat = (passes % 2 == 0) ? Lm : Rt;
+  qlr_qmat* UX = (side == QLR_SIDE_X) ? U : V;   // U of the algorithm's X
+  qlr_qmat* VX = (side == QLR_SIDE_X) ? V : U;
+  QLR_TRY(lift(ctx, Q1, Uhat, (int)L, k, *UX));          // U = Q1 U_hat
+  QLR_TRY(lift(ctx, Q2, Vhat, (int)L, k, *VX));          // V = Q2 V_hat
+  return QLR_OK;
+}
+
+int qlr_qsvd_lowrank(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo, const qlr_qmat* omega,
+                     const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V) {
+  return lowrank_impl(ctx, A, k, p, passes, algo, omega, opts, U, S, V);
+}
+
+int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes, const qlr_qmat* omega,
+                      const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V) {
+  if (b < k) return QLR_ESHAPE;
+  return lowrank_impl(ctx, A, k, b - k, passes, QLR_ALG4, omega, opts, U, S, V);
+}
+
+int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
+                             const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V) {
+  if (!ctx || count < 0 || (count > 0 && (!A || !k || !p || !omega || !U || !S || !V))) return QLR_EINVAL;
+  for (int i = 0; i < count; ++i)
+    QLR_TRY(lowrank_impl(ctx, &A[i], k[i], p[i], passes, QLR_ALG2, &omega[i], opts, &U[i], S[i], &V[i]));
+  return QLR_OK;
+}
+
+int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start, int iters,
+                      double* out) {
+  if (!ctx || !out) return QLR_EINVAL;
+  QLR_TRY(check_qmat(A, QLR_ROW_MAJOR, true));
+  QLR_TRY(check_qmat(Q, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(start, QLR_COL_MAJOR, false));
+  if (side != QLR_SIDE_X && side != QLR_SIDE_XH) return QLR_EINVAL;
+  if (Q->dtype != start->dtype || Q->dtype == QLR_BF16) return QLR_EINVAL;
+  const int64_t qrows = (side == QLR_SIDE_X) ? A->rows : A->cols;
+  if (Q->rows != qrows || start->rows != A->cols || iters < 1 || start->cols < 1) return QLR_ESHAPE;
+  DeviceGuard g(ctx->device);
+  const int64_t nv = start->cols, l = Q->cols;
+  const int cmp = (Q->dtype == QLR_F64) ? QLR_COMPUTE_F64 : QLR_COMPUTE_F32;
+  size_t esz = qlr_dtype_size(Q->dtype);
+  QLR_TRY(qlr_ensure_ws(ctx, (size_t)4 * esz * (A->rows + A->cols) * nv * 3 + (size_t)4 * esz * l * nv +
+                                 cholqr_ws_bound(A->cols, nv, esz) + ((size_t)1 << 20)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  Sched S{};
+  init_sched(S, ctx, &ws, A, cmp, QLR_SIDE_X);
+  qlr_qmat x = S.thin(A->cols, nv), xt = S.thin(A->cols, nv), y = S.thin(A->rows, nv), h = S.thin(l, nv);
+  if (!ws.ok) return QLR_ENOMEM;
+  QLR_TRY(qlr::convert_qmat(ctx, *start, x));
+  // P z = z - Q (Q^H z)
+  auto project = [&](qlr_qmat& z) -> int {
+    qlr::GemmArgs g1{};
+    for (int c = 0; c < 4; ++c) { g1.a[c] = Q->plane[c]; g1.b[c] = z.plane[c]; g1.c[c] = h.plane[c]; }
+    g1.sa_i = Q->ld; g1.sa_k = 1; g1.i_contig = false; g1.conj_a = true; g1.a_dtype = Q->dtype;
+    g1.ldb = z.ld; g1.b_dtype = z.dtype; g1.ldc = h.ld; g1.c_dtype = h.dtype;
+    g1.M = l; g1.N = nv; g1.K = Q->rows; g1.alpha = 1.0; g1.beta = 0.0; g1.acc64 = (cmp == QLR_COMPUTE_F64);
+    QLR_TRY(qlr::gemm_simt(ctx, g1));
+    qlr::GemmArgs g2{};
+    for (int c = 0; c < 4; ++c) { g2.a[c] = Q->plane[c]; g2.b[c] = h.plane[c]; g2.c[c] = z.plane[c]; }
+    g2.sa_i = 1; g2.sa_k = Q->ld; g2.i_contig = true; g2.conj_a = false; g2.a_dtype = Q->dtype;
+    g2.ldb = h.ld; g2.b_dtype = h.dtype; g2.ldc = z.ld; g2.c_dtype = z.dtype;
+    g2.M = Q->rows; g2.N = nv; g2.K = l; g2.alpha = -1.0; g2.beta = 1.0; g2.acc64 = (cmp == QLR_COMPUTE_F64);
+    return qlr::gemm_simt(ctx, g2);
+  };
+  double* norms = ws.take<double>((size_t)4 * nv * nv);
+  if (!ws.ok) return QLR_ENOMEM;
+  double best = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    QLR_TRY(qlr::cholqr(ctx, x, xt, nullptr, QLR_ORTH_SCHOLQR3, ws));   // orthonormal block
+    if (side == QLR_SIDE_XH) QLR_TRY(project(xt));
+    QLR_TRY(S.sketch(QLR_OP_N, xt, y));        // y = A x
+    if (side == QLR_SIDE_X) QLR_TRY(project(y));
+    // ||E x|| per column (Gram diagonal) -> lower bound on ||E||_2
+    QLR_TRY(qlr::gram(ctx, y, norms, ws));
+    std::vector<double> hg((size_t)4 * nv * nv);
+    QLR_CUDA_TRY(cudaMemcpyAsync(hg.data(), norms, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    QLR_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int64_t j = 0; j < nv; ++j) best = std::max(best, std::sqrt(std::max(0.0, hg[(size_t)j * nv + j])));
+    QLR_TRY(S.sketch(QLR_OP_H, y, x));         // x = A^H y (= E^H y for side X)
+    if (side == QLR_SIDE_XH) QLR_TRY(project(x));
+  }
+  *out = best;
+  return QLR_OK;
+}
+
+}  // extern "C"

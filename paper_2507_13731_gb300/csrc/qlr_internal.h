@@ -1,0 +1,180 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/qlr.h"
+
+// ----------------------------------------------------------------------------------------
+// context
+struct qlr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* d_err = nullptr;          // device error word: first QLR_E* code recorded by a kernel
+  void* ws = nullptr;            // workspace
+  size_t ws_bytes = 0;
+  int num_sms = 0;
+  // launch statistics
+  int64_t launches[QLR_KID_COUNT] = {};
+  double ms[QLR_KID_COUNT] = {};
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;                       // free events
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+// Brackets one kernel launch: counts it and, with timing enabled, records events on ctx->stream.
+struct KTimer {
+  qlr_ctx* ctx;
+  int kid;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KTimer(qlr_ctx* c, int k);
+  ~KTimer();
+};
+
+// Bump allocator over the context workspace (256-byte aligned slices).
+struct WsArena {
+  char* base;
+  size_t cap, off = 0;
+  bool ok = true;
+  WsArena(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (off + bytes > cap) { ok = false; return nullptr; }
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+int qlr_ensure_ws(qlr_ctx* ctx, size_t bytes);
+
+#define QLR_CUDA_TRY(expr)                          \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return QLR_ECUDA;        \
+  } while (0)
+
+#define QLR_TRY(expr)                               \
+  do {                                              \
+    int r_ = (expr);                                \
+    if (r_ != QLR_OK) return r_;                    \
+  } while (0)
+
+// ----------------------------------------------------------------------------------------
+// device helpers
+__device__ __forceinline__ void qlr_set_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+template <class T> __device__ __forceinline__ T qlr_load(const T* p) { return *p; }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+template <class T> struct Cvt;
+template <> struct Cvt<float> {
+  template <class S> __device__ __forceinline__ static float from(S x) { return to_f(x); }
+};
+template <> struct Cvt<double> {
+  template <class S> __device__ __forceinline__ static double from(S x) { return to_d(x); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+  template <class S> __device__ __forceinline__ static __nv_bfloat16 from(S x) {
+    return __float2bfloat16_rn(to_f(x));
+  }
+};
+
+// Quaternion stored as 4 reals (real, i, j, k).
+template <class T> struct Quat { T w, x, y, z; };
+
+// Hamilton product a*b (Section 2, eq. 1).
+template <class T>
+__device__ __forceinline__ Quat<T> qmul(const Quat<T>& a, const Quat<T>& b) {
+  return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+          a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+          a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+          a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+// conj(a)*b
+template <class T>
+__device__ __forceinline__ Quat<T> qcmul(const Quat<T>& a, const Quat<T>& b) {
+  return {a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z,
+          a.w * b.x - a.x * b.w - a.y * b.z + a.z * b.y,
+          a.w * b.y + a.x * b.z - a.y * b.w - a.z * b.x,
+          a.w * b.z - a.x * b.y + a.y * b.x - a.z * b.w};
+}
+// a*conj(b)
+template <class T>
+__device__ __forceinline__ Quat<T> qmulc(const Quat<T>& a, const Quat<T>& b) {
+  return {a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z,
+          -a.w * b.x + a.x * b.w - a.y * b.z + a.z * b.y,
+          -a.w * b.y + a.x * b.z + a.y * b.w - a.z * b.x,
+          -a.w * b.z - a.x * b.y + a.y * b.x + a.z * b.w};
+}
+template <class T> __device__ __forceinline__ T qnorm2(const Quat<T>& a) {
+  return a.w * a.w + a.x * a.x + a.y * a.y + a.z * a.z;
+}
+
+// ----------------------------------------------------------------------------------------
+// Small dense quaternion matrices in FP64 (Gram, R, core QSVD operands): 4 planes of l x l,
+// column-major: element (i, j) of plane c at M[c*l*l + j*l + i].
+__device__ __forceinline__ Quat<double> ld_small(const double* M, int l, int i, int j) {
+  size_t s = (size_t)l * l, o = (size_t)j * l + i;
+  return {M[o], M[s + o], M[2 * s + o], M[3 * s + o]};
+}
+__device__ __forceinline__ void st_small(double* M, int l, int i, int j, const Quat<double>& q) {
+  size_t s = (size_t)l * l, o = (size_t)j * l + i;
+  M[o] = q.w; M[s + o] = q.x; M[2 * s + o] = q.y; M[3 * s + o] = q.z;
+}
+
+// ----------------------------------------------------------------------------------------
+// launchers implemented in the .cu files (all asynchronous on ctx->stream)
+namespace qlr {
+
+// SIMT generic quaternion GEMM  C = alpha * op(A) * B + beta * C
+//   A element (i, k) at A.plane[c] + i*sa_i + k*sa_k, conj_a applies A -> conj(A) elementwise.
+//   B column-major (k, j) at b + k + j*ldb.  C column-major.  Types per dtype fields.
+struct GemmArgs {
+  const void* a[4]; int64_t sa_i, sa_k; int a_dtype; bool conj_a; bool a_pure;
+  const void* b[4]; int64_t ldb; int b_dtype;
+  void* c[4]; int64_t ldc; int c_dtype;
+  int64_t M, N, K;
+  double alpha, beta;
+  bool i_contig;      // true when sa_i == 1 (A's row index contiguous in memory)
+  bool acc64;         // accumulate in FP64
+  int kid = QLR_KID_APPLY;   // statistics class of the launch
+};
+int gemm_simt(qlr_ctx* ctx, const GemmArgs& g);
+
+// tcgen05 sketch products (see sketch_tc.cu)
+int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws);
+size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms);
+bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compute);
+
+// orthonormalisation pieces (orth.cu)
+int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
+int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel);
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv);
+int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
+int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
+
+// core QSVD (core_svd.cu)
+int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec,
+              WsArena& ws);
+
+// utilities (util.cu)
+int convert_qmat(qlr_ctx* ctx, const qlr_qmat& src, qlr_qmat& dst);  // elementwise dtype change
+int zero_qmat(qlr_ctx* ctx, qlr_qmat& dst);
+int small_to_qmat(qlr_ctx* ctx, const double* S, int l, int k, qlr_qmat& dst);  // l x k FP64 small -> qmat
+
+}  // namespace qlr
+
+size_t qlr_dtype_size(int dtype);

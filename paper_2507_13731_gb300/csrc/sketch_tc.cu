@@ -1,0 +1,663 @@
+// tcgen05 tensor-core sketch products  Y = A X  (op N)  and  Z = A^H Y  (op H).
+//
+// The Hamilton product of eq. (1) (Section 2), summed over the inner index, is one real GEMM of
+// the plane-stacked A against a sign-structured expansion of the thin sketch:
+//     Y_d = sum_c  s(c, d) * A_c * X_{c xor d}          (op N)
+//     Z_d = sum_c  s'(c, d) * A_c^T * Y_{c xor d}       (op H, A^H = A1^T - A2^T i - A3^T j - A4^T k)
+// with s(c, d) = -1 exactly for (c, d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)} and
+// s'(c, d) = -s(c, d) for c != 0.  The expansion is never materialised: each (c, d) pair is one
+// tcgen05.mma of A's plane-c tile against X's plane (c xor d) tile, with the instruction
+// descriptor's negate-B bit carrying the sign, accumulating into output plane d's TMEM columns.
+//
+// Per CTA: a 128-row tile of the output (M = m for op N, M = n for op H) and a block of nb <= 128
+// output columns of all four planes (4 nb <= 512 TMEM columns), over a contiguous range of the
+// reduction (split-K).  A's tiles come through TMA into a 2-4 stage shared-memory ring; A is read
+// exactly once per column block.  Op N stages A K-major (TMA swizzled tiles).  Op H reads A along
+// its rows: for BF16 the MMA consumes the MN-major tile directly; for the 4-byte modes the tile is
+// loaded unswizzled and the worker warps transpose it into the K-major swizzled layout (splitting
+// it into hi / lo on the way for 3xTF32).
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (owns TMEM), 2-3 = workers (hi/lo split and/or
+// transpose of A), 4-7 = epilogue (TMEM -> registers -> global, or split-K partial + last-CTA
+// reduction).
+//
+// Precision modes: BF16 (kind::f16, A stored BF16, X rounded to BF16), TF32 (kind::tf32, one
+// product on FP32 data), TF32X3 (kind::tf32: A = A_hi + A_lo and X = X_hi + X_lo with
+// A_hi = A with its 13 low mantissa bits cleared, three products A_hi X_hi + A_lo X_hi + A_hi X_lo).
+// Accumulation is FP32 in TMEM throughout.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "qlr_internal.h"
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TBM = 128;          // output rows per CTA (MMA M)
+constexpr int MAX_STAGES = 4;
+constexpr uint64_t WAIT_NS = 1500000000ull;   // bounded waits: 1.5 s
+
+enum Kind { K_BF16 = 0, K_TF32 = 1, K_TF32X3 = 2 };
+enum AMode { A_K = 0, A_MN = 1, A_T = 2 };   // K-major TMA, MN-major descriptors, transposed by workers
+
+struct TcParams {
+  CUtensorMap tmA[4];
+  CUtensorMap tmX[4];
+  CUtensorMap tmXlo[4];
+  float* y[4];
+  int64_t ldy;
+  float* part;              // split-K partial tiles
+  unsigned* counters;       // one arrival counter per output tile
+  int64_t M;                // output rows
+  int l;                    // valid output columns
+  int nb;                   // output columns per CTA block
+  int ncb;                  // column blocks
+  int kiters;               // K stages in total
+  int kper;                 // K stages per split
+  int nsplit;
+  int c_first;              // 1 for a pure quaternion A (plane 0 absent)
+  uint32_t neg_mask;        // bit c*4+d set: negate the (c, d) product
+  uint32_t idesc_base;
+  uint32_t tmem_cols;
+  int stages;
+  int* err;
+};
+
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout (records QLR_ETIMEOUT and raises the CTA abort flag) or when
+// another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (now_ns() - t0 > WAIT_NS) {
+      *abort_flag = 1;
+      qlr_set_error(err, QLR_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+  if (KIND == K_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading byte offset >> 4 in
+// 16-29, stride byte offset >> 4 in 32-45, version 1 at bit 46, swizzle mode in bits 61-63.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t mode) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)mode << 61);
+}
+
+template <int KIND> struct Cfg;
+template <> struct Cfg<K_BF16> {     // 2-byte operands, 64 B swizzle, 32 K-elements per stage
+  static constexpr int ESZ = 2, SW = 64, BK = 32, MMA_K = 16, MODE = 4;
+};
+template <> struct Cfg<K_TF32> {     // 4-byte operands, 64 B swizzle, 16 K-elements per stage
+  static constexpr int ESZ = 4, SW = 64, BK = 16, MMA_K = 8, MODE = 4;
+};
+template <> struct Cfg<K_TF32X3> {   // 4-byte operands, 32 B swizzle, 8 K-elements per stage
+  static constexpr int ESZ = 4, SW = 32, BK = 8, MMA_K = 8, MODE = 6;
+};
+
+// ---------------------------------------------------------------------------------------
+template <int KIND, int AMODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_constant__ TcParams p) {
+  using C = Cfg<KIND>;
+  constexpr bool X3 = (KIND == K_TF32X3);
+  constexpr bool MN = (AMODE == A_MN);
+  constexpr bool TR = (AMODE == A_T);
+  constexpr bool WORKERS = X3 || TR;
+  constexpr int A_BYTES = TBM * C::SW;                 // one plane of the A tile (== raw tile bytes)
+  constexpr int KSTEPS = C::BK / C::MMA_K;
+  constexpr int ATOM_MN = C::SW / C::ESZ;              // MN-major: elements per atom row
+  constexpr int NATOM = TBM / ATOM_MN;
+  constexpr int CH = C::SW / 16;                       // 16-byte chunks per K-major row
+  const int STAGES = p.stages;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nb = p.nb;
+  const int X_BYTES = nb * C::SW;
+  const int A_SET = 4 * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));   // [raw][hi][lo]
+  const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + MAX_STAGES;
+  uint64_t* ready = bars + 2 * MAX_STAGES;
+  uint64_t* tmem_full = bars + 3 * MAX_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAX_STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* last_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int cb = blockIdx.x, mt = blockIdx.y, split = blockIdx.z;
+  const int64_t m0 = (int64_t)mt * TBM;
+  const int j0 = cb * nb;
+  const int it0 = split * p.kper;
+  const int it1 = min(p.kiters, it0 + p.kper);
+  const int nit = it1 - it0;
+
+  constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + c * A_BYTES; };
+  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + c * A_BYTES; };
+  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + 4 * A_BYTES + c * A_BYTES; };
+  auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
+  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAX_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&ready[s], 64);
+    }
+    mbar_init(tmem_full, 1);
+    *abort_flag = 0;
+    *last_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint32_t tx = (uint32_t)((4 - p.c_first) * A_BYTES + 4 * X_BYTES * (X3 ? 2 : 1));
+      int issued = 0;
+      for (int i = 0; i < nit; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
+        mbar_expect_tx(&full[s], tx);
+        const int k0 = (it0 + i) * C::BK;
+        for (int c = p.c_first; c < 4; ++c) {
+          if (MN) {
+#pragma unroll
+            for (int a = 0; a < NATOM; ++a)
+              tma_load_2d(smem_u32(a_plane(s, c) + a * C::BK * C::SW), &p.tmA[c], (int)m0 + a * ATOM_MN, k0, &full[s]);
+          } else if (TR) {
+            tma_load_2d(smem_u32(raw_plane(s, c)), &p.tmA[c], (int)m0, k0, &full[s]);   // [BK][128] unswizzled
+          } else {
+            tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
+          }
+        }
+        for (int q = 0; q < 4; ++q) {
+          tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
+          if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+        }
+        ++issued;
+      }
+      // drain: every issued stage must have landed before the CTA may exit
+      for (int i = max(0, issued - STAGES); i < issued; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        const uint64_t t0 = now_ns();
+        while (!mbar_try_wait(&full[s], ph) && now_ns() - t0 < WAIT_NS) __nanosleep(64);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = true;
+      for (int i = 0; i < nit && ok; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, p.err);
+        if (!ok) break;
+        tc_fence_after();
+#pragma unroll
+        for (int ks = 0; ks < KSTEPS; ++ks) {
+          for (int c = p.c_first; c < 4; ++c) {
+            uint64_t ad, adlo = 0;
+            if (MN) {
+              // MN-major: LBO = stride between MN atoms, SBO = stride between 8-row K groups
+              const uint32_t off = (uint32_t)(ks * C::MMA_K * C::SW);
+              ad = make_desc(smem_u32(a_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
+              if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
+            } else {
+              const uint32_t off = (uint32_t)(ks * C::MMA_K * C::ESZ);
+              ad = make_desc(smem_u32(a_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
+              if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              const int q = c ^ d;
+              const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
+              const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
+              const uint32_t idesc = p.idesc_base | (((p.neg_mask >> (c * 4 + d)) & 1u) << 14);
+              const uint32_t dt = tmem + (uint32_t)(d * nb);
+              const uint32_t acc = (i > 0 || ks > 0 || c > p.c_first) ? 1u : 0u;
+              umma<KIND>(dt, ad, bd, idesc, acc);
+              if (X3) {
+                const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
+                umma<KIND>(dt, adlo, bd, idesc, 1u);
+                umma<KIND>(dt, ad, bdlo, idesc, 1u);
+              }
+            }
+          }
+        }
+        umma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+      }
+      umma_commit(tmem_full);     // accumulator complete (also fires after an abort)
+    }
+  } else if (warp < 4) {
+    // ---------------- workers: hi/lo split (3xTF32) and/or transpose of A ----------------
+    if (WORKERS) {
+      const int st = threadIdx.x - 64;   // 0..63
+      for (int i = 0; i < nit; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag, p.err)) break;
+        for (int c = p.c_first; c < 4; ++c) {
+          uint4* hi = reinterpret_cast<uint4*>(a_plane(s, c));
+          uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
+          if (TR) {
+            // raw[k][r] (k < BK, r < 128) -> row r of the K-major tile, 16-byte chunk cch holding
+            // k = 4 cch .. 4 cch + 3, stored at chunk position cch ^ swizzle(r)
+            const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_plane(s, c));
+            for (int e = st; e < TBM * CH; e += 64) {
+              const int r = e % TBM, cch = e / TBM;
+              const int sw = (CH == 2) ? ((r >> 2) & 1) : (CH == 4) ? ((r >> 1) & 3) : (r & 7);
+              uint4 v;
+              v.x = raw[(4 * cch + 0) * TBM + r];
+              v.y = raw[(4 * cch + 1) * TBM + r];
+              v.z = raw[(4 * cch + 2) * TBM + r];
+              v.w = raw[(4 * cch + 3) * TBM + r];
+              const int o = r * CH + (cch ^ sw);
+              if (X3) {
+                uint4 h, rr;
+                h.x = v.x & 0xFFFFE000u; h.y = v.y & 0xFFFFE000u; h.z = v.z & 0xFFFFE000u; h.w = v.w & 0xFFFFE000u;
+                rr.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+                rr.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+                rr.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+                rr.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+                hi[o] = h;
+                lo[o] = rr;
+              } else {
+                hi[o] = v;
+              }
+            }
+          } else {
+            for (int e = st; e < A_BYTES / 16; e += 64) {
+              uint4 v = hi[e], h, r;
+              h.x = v.x & 0xFFFFE000u; h.y = v.y & 0xFFFFE000u; h.z = v.z & 0xFFFFE000u; h.w = v.w & 0xFFFFE000u;
+              r.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+              r.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+              r.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+              r.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+              hi[e] = h;
+              lo[e] = r;
+            }
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&ready[s]);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;
+    const int64_t grow = m0 + row;
+    const bool ok = mbar_wait(tmem_full, 0, abort_flag, p.err) && !*abort_flag;
+    tc_fence_after();
+    const int tile = mt * p.ncb + cb;
+    const size_t tile_elems = (size_t)4 * TBM * nb;
+    float v[16];
+    if (ok && nit > 0) {
+      for (int d = 0; d < 4; ++d) {
+        for (int cc = 0; cc < nb; cc += 16) {
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc), v);
+          if (p.nsplit == 1) {
+            if (grow < p.M) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int j = j0 + cc + jj;
+                if (j < p.l && cc + jj < nb) p.y[d][grow + (int64_t)j * p.ldy] = v[jj];
+              }
+            }
+          } else {
+            float* P = p.part + ((size_t)split * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) P[(size_t)(cc + jj) * TBM + row] = v[jj];
+          }
+        }
+      }
+    }
+    if (p.nsplit > 1) {
+      __threadfence();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (threadIdx.x == 128) {
+        const unsigned old = atomicAdd(&p.counters[tile], 1u);
+        *last_flag = (old == (unsigned)(p.nsplit - 1)) ? 1 : 0;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (*last_flag) {
+        __threadfence();
+        if (grow < p.M) {
+          for (int d = 0; d < 4; ++d)
+            for (int jc = 0; jc < nb; ++jc) {
+              const int j = j0 + jc;
+              if (j >= p.l) break;
+              float s = 0.f;
+              for (int sp = 0; sp < p.nsplit; ++sp)
+                s += __ldcg(&p.part[((size_t)sp * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
+                                    (size_t)jc * TBM + row]);
+              p.y[d][grow + (int64_t)j * p.ldy] = s;
+            }
+        }
+        if (threadIdx.x == 128) p.counters[tile] = 0u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// Operand staging: X (F32, column-major) -> BF16 copy, plain FP32 copy, or hi / lo FP32 pair.
+__global__ void stage_x_kernel(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ x2,
+                               const float* __restrict__ x3, int64_t ldx, int64_t rows, int64_t cols, int mode,
+                               void* __restrict__ out, void* __restrict__ out_lo, int64_t ldo) {
+  const float* xs[4] = {x0, x1, x2, x3};
+  const int64_t per = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / per);
+    const int64_t r = e % per, i = r % rows, j = r / rows;
+    const float v = xs[c][i + j * ldx];
+    const size_t o = (size_t)c * ldo * cols + (size_t)j * ldo + i;
+    if (mode == K_BF16) {
+      static_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
+    } else if (mode == K_TF32) {
+      static_cast<float*>(out)[o] = v;
+    } else {
+      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      static_cast<float*>(out)[o] = h;
+      static_cast<float*>(out_lo)[o] = v - h;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+// 2-D tiled map over a (inner x outer) array with row pitch `pitch_bytes`; box (bi x bo).
+bool encode_2d(CUtensorMap* tm, const void* base, CUtensorMapDataType dt, uint64_t inner, uint64_t outer,
+               uint64_t pitch_bytes, uint32_t bi, uint32_t bo, CUtensorMapSwizzle sw) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {bi, bo};
+  cuuint32_t es[2] = {1, 1};
+  return fn(tm, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int kind_of(int compute) {
+  return compute == QLR_COMPUTE_BF16 ? K_BF16 : (compute == QLR_COMPUTE_TF32 ? K_TF32 : K_TF32X3);
+}
+
+struct Plan {
+  int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, nsplit, kper, stages;
+  uint32_t tmem_cols;
+  size_t smem;
+};
+
+Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
+  Plan pl{};
+  pl.kind = kind_of(compute);
+  pl.amode = (op == QLR_OP_N) ? A_K : (pl.kind == K_BF16 ? A_MN : A_T);
+  pl.esz = pl.kind == K_BF16 ? 2 : 4;
+  pl.sw = pl.kind == K_TF32X3 ? 32 : 64;
+  pl.bk = pl.sw / pl.esz;
+  const int lp = (l + 15) / 16 * 16;
+  pl.ncb = (lp + 127) / 128;
+  pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
+  pl.mtiles = (int)((M + TBM - 1) / TBM);
+  pl.kiters = (int)((K + pl.bk - 1) / pl.bk);
+  const int ctas = pl.mtiles * pl.ncb;
+  int ns = std::max(1, num_sms / std::max(1, ctas));
+  ns = std::min(ns, std::max(1, pl.kiters / 8));
+  pl.kper = (pl.kiters + ns - 1) / ns;
+  pl.nsplit = (pl.kiters + pl.kper - 1) / pl.kper;
+  const int cols = 4 * pl.nb;
+  pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+  const bool x3 = pl.kind == K_TF32X3;
+  const size_t stage = (size_t)4 * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
+                       (size_t)4 * pl.nb * pl.sw * (x3 ? 2 : 1);
+  const size_t budget = (size_t)227 * 1024 - 1024 - 256;
+  pl.stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
+  pl.smem = pl.stages * stage + 1024 + 256;
+  return pl;
+}
+
+template <int KIND, int AMODE>
+int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm) {
+  auto kern = sketch_tc_kernel<KIND, AMODE>;
+  QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  dim3 grid((unsigned)pl.ncb, (unsigned)pl.mtiles, (unsigned)pl.nsplit);
+  KTimer kt(ctx, QLR_KID_SKETCH_TC);
+  kern<<<grid, TC_THREADS, pl.smem, ctx->stream>>>(prm);
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+namespace qlr {
+
+bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compute) {
+  (void)op; (void)X;
+  if (compute != QLR_COMPUTE_BF16 && compute != QLR_COMPUTE_TF32 && compute != QLR_COMPUTE_TF32X3) return false;
+  const int want = compute == QLR_COMPUTE_BF16 ? QLR_BF16 : QLR_F32;
+  if (A.dtype != want || A.layout != QLR_ROW_MAJOR) return false;
+  const size_t esz = qlr_dtype_size(A.dtype);
+  if ((A.ld * esz) % 16 != 0) return false;
+  for (int c = 0; c < 4; ++c)
+    if (A.plane[c] && !aligned16(A.plane[c])) return false;
+  if (!get_encode()) return false;
+  return A.rows < (1LL << 31) && A.cols < (1LL << 31);
+}
+
+size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
+  const int64_t ldo = (rows_in + 7) / 8 * 8;
+  return (size_t)2 * 4 * ldo * l * 4 + (size_t)(num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
+}
+
+int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws) {
+  if (!sketch_tc_supported(op, A, X, compute)) return QLR_EUNSUPPORTED;
+  const int64_t M = (op == QLR_OP_N) ? A.rows : A.cols;
+  const int64_t K = (op == QLR_OP_N) ? A.cols : A.rows;
+  const int l = (int)X.cols;
+  if (M == 0 || l == 0) return QLR_OK;
+  if (K == 0) return zero_qmat(ctx, Y);
+  if (X.dtype != QLR_F32 && !(compute == QLR_COMPUTE_BF16 && X.dtype == QLR_BF16)) return QLR_EINVAL;
+  const Plan pl = make_plan(compute, op, M, K, l, ctx->num_sms > 0 ? ctx->num_sms : 148);
+  if (pl.stages < 2) return QLR_EUNSUPPORTED;
+  size_t mark = ws.off;
+  // stage the thin operand with a 16-byte aligned column pitch
+  const int64_t ldo = (K + 7) / 8 * 8;
+  const size_t xesz = (pl.kind == K_BF16) ? 2 : 4;
+  void* xs = ws.take<char>((size_t)4 * ldo * l * xesz);
+  void* xlo = (pl.kind == K_TF32X3) ? ws.take<char>((size_t)4 * ldo * l * 4) : nullptr;
+  const size_t tile_elems = (size_t)4 * TBM * pl.nb;
+  float* part = pl.nsplit > 1 ? ws.take<float>((size_t)pl.nsplit * pl.mtiles * pl.ncb * tile_elems) : nullptr;
+  unsigned* counters = ws.take<unsigned>((size_t)pl.mtiles * pl.ncb);
+  if (!ws.ok) return QLR_ENOMEM;
+  if (X.dtype == QLR_BF16) {
+    qlr_qmat dst = X;
+    dst.ld = ldo;
+    for (int c = 0; c < 4; ++c) dst.plane[c] = static_cast<char*>(xs) + (size_t)c * ldo * l * 2;
+    QLR_TRY(convert_qmat(ctx, X, dst));
+  } else {
+    int64_t tot = 4 * K * (int64_t)l;
+    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8192);
+    KTimer kt(ctx, QLR_KID_MISC);
+    stage_x_kernel<<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<const float*>(X.plane[0]), static_cast<const float*>(X.plane[1]),
+        static_cast<const float*>(X.plane[2]), static_cast<const float*>(X.plane[3]), X.ld, K, l, pl.kind, xs, xlo, ldo);
+    QLR_CUDA_TRY(cudaGetLastError());
+  }
+  QLR_CUDA_TRY(cudaMemsetAsync(counters, 0, (size_t)pl.mtiles * pl.ncb * sizeof(unsigned), ctx->stream));
+
+  TcParams prm;
+  memset(&prm, 0, sizeof(prm));
+  const CUtensorMapDataType dt = (pl.kind == K_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapSwizzle sw = (pl.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const int esz = pl.esz;
+  prm.c_first = (A.plane[0] == nullptr) ? 1 : 0;
+  for (int c = prm.c_first; c < 4; ++c) {
+    bool ok;
+    if (op == QLR_OP_N)   // K-major: inner = n (reduction), outer = m (output rows); box {BK, 128}
+      ok = encode_2d(&prm.tmA[c], A.plane[c], dt, (uint64_t)A.cols, (uint64_t)A.rows, (uint64_t)A.ld * esz,
+                     (uint32_t)pl.bk, TBM, sw);
+    else if (pl.amode == A_MN)   // MN-major: inner = n (output rows), outer = m (reduction); box {SW/esz, BK}
+      ok = encode_2d(&prm.tmA[c], A.plane[c], dt, (uint64_t)A.cols, (uint64_t)A.rows, (uint64_t)A.ld * esz,
+                     (uint32_t)(pl.sw / esz), (uint32_t)pl.bk, sw);
+    else                         // raw tile for the worker transpose: box {128, BK}, unswizzled
+      ok = encode_2d(&prm.tmA[c], A.plane[c], dt, (uint64_t)A.cols, (uint64_t)A.rows, (uint64_t)A.ld * esz, TBM,
+                     (uint32_t)pl.bk, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!ok) { ws.off = mark; return QLR_ECUDA; }
+  }
+  for (int q = 0; q < 4; ++q) {
+    const char* base = static_cast<const char*>(xs) + (size_t)q * ldo * l * xesz;
+    if (!encode_2d(&prm.tmX[q], base, dt, (uint64_t)K, (uint64_t)l, (uint64_t)ldo * xesz, (uint32_t)pl.bk,
+                   (uint32_t)pl.nb, sw)) { ws.off = mark; return QLR_ECUDA; }
+    if (xlo) {
+      const char* lb = static_cast<const char*>(xlo) + (size_t)q * ldo * l * 4;
+      if (!encode_2d(&prm.tmXlo[q], lb, dt, (uint64_t)K, (uint64_t)l, (uint64_t)ldo * 4, (uint32_t)pl.bk,
+                     (uint32_t)pl.nb, sw)) { ws.off = mark; return QLR_ECUDA; }
+    }
+  }
+  for (int c = 0; c < 4; ++c) prm.y[c] = static_cast<float*>(Y.plane[c]);
+  prm.ldy = Y.ld;
+  prm.part = part;
+  prm.counters = counters;
+  prm.M = M;
+  prm.l = l;
+  prm.nb = pl.nb;
+  prm.ncb = pl.ncb;
+  prm.kiters = pl.kiters;
+  prm.kper = pl.kper;
+  prm.nsplit = pl.nsplit;
+  // sign table: op N: negative for (c,d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)}; op H flips c != 0
+  uint32_t neg = 0;
+  const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
+  for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
+  if (op == QLR_OP_H) neg ^= 0xFFF0u;   // flip every (c != 0, d) entry
+  prm.neg_mask = neg;
+  const uint32_t fmt = (pl.kind == K_BF16) ? 1u : 2u;
+  prm.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((pl.amode == A_MN ? 1u : 0u) << 15) |
+                   ((uint32_t)(pl.nb >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+  prm.tmem_cols = pl.tmem_cols;
+  prm.stages = pl.stages;
+  prm.err = ctx->d_err;
+  int rc;
+  const bool h = (op == QLR_OP_H);
+  if (pl.kind == K_BF16) rc = h ? launch_kernel<K_BF16, A_MN>(ctx, pl, prm) : launch_kernel<K_BF16, A_K>(ctx, pl, prm);
+  else if (pl.kind == K_TF32) rc = h ? launch_kernel<K_TF32, A_T>(ctx, pl, prm) : launch_kernel<K_TF32, A_K>(ctx, pl, prm);
+  else rc = h ? launch_kernel<K_TF32X3, A_T>(ctx, pl, prm) : launch_kernel<K_TF32X3, A_K>(ctx, pl, prm);
+  ws.off = mark;
+  return rc;
+}
+
+}  // namespace qlr

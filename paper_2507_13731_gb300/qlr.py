@@ -1,0 +1,290 @@
+"""ctypes binding of libqlr.so: argument marshalling only.
+
+Every computation runs in the CUDA library; this module turns torch tensors into the
+`qlr_qmat` descriptors of include/qlr.h and raises `QlrError` on a non-zero return code.
+PyTorch is used for device memory and streams only.
+
+Quaternion matrices are torch tensors of logical shape (4, rows, cols) -- planes real, i, j, k
+-- or (3, rows, cols) for a pure quaternion matrix (planes i, j, k; real part zero).  A tensor
+whose last dimension is contiguous is row-major (the data matrix A); one whose middle dimension
+is contiguous (e.g. from `empty_thin`) is column-major (Omega, Q, U, V and the sketches).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqlr.so")
+
+# constants mirrored from include/qlr.h
+OK, EINVAL, ESHAPE, ENOTPD, ENOCONV, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
+F64, F32, BF16 = 0, 1, 2
+ROW_MAJOR, COL_MAJOR = 0, 1
+COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16 = range(6)
+OP_N, OP_H = 0, 1
+ALG2, ALG4 = 2, 4
+SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
+ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
+
+_DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc"]
+
+
+class QlrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib().qlr_strerror(code).decode()} (code {code})")
+
+
+class QMatC(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p * 4), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("layout", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class OptsC(ctypes.Structure):
+    _fields_ = [("compute", ctypes.c_int32), ("side", ctypes.c_int32), ("orth", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqlr.so; fails loudly if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2507_13731_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        Q = ctypes.POINTER(QMatC)
+        O = ctypes.POINTER(OptsC)
+        sig = {
+            "qlr_create": (I, [ctypes.POINTER(P), I, P]),
+            "qlr_destroy": (I, [P]),
+            "qlr_set_stream": (I, [P, P]),
+            "qlr_reserve": (I, [P, S]),
+            "qlr_workspace_size": (S, [I64, I64, I, I, I, I, I]),
+            "qlr_sync": (I, [P]),
+            "qlr_strerror": (ctypes.c_char_p, [I]),
+            "qlr_qsketch": (I, [P, I, Q, Q, Q, I]),
+            "qlr_qgram": (I, [P, Q, P]),
+            "qlr_qchol": (I, [P, I, P, P]),
+            "qlr_cholqr": (I, [P, Q, Q, P, I]),
+            "qlr_qtsvd": (I, [P, I, P, I, P, P, P, I]),
+            "qlr_qrangefinder": (I, [P, Q, I, I, I, Q, O, Q, Q, P, ctypes.POINTER(I)]),
+            "qlr_qsvd_lowrank": (I, [P, Q, I, I, I, I, Q, O, Q, P, Q]),
+            "qlr_qblock_krylov": (I, [P, Q, I, I, I, Q, O, Q, P, Q]),
+            "qlr_qsvd_lowrank_batched": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
+                                             ctypes.POINTER(P), Q]),
+            "qlr_residual_norm": (I, [P, Q, Q, I, Q, I, ctypes.POINTER(D)]),
+            "qlr_set_timing": (I, [P, I]),
+            "qlr_reset_stats": (I, [P]),
+            "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise QlrError(rc, where)
+
+
+# ------------------------------------------------------------------------------------------
+def empty_thin(rows: int, cols: int, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    """Column-major quaternion matrix storage: logical shape (4, rows, cols), rows contiguous."""
+    return torch.empty(4, cols, rows, dtype=dtype, device=device).transpose(1, 2)
+
+
+def to_thin(x: torch.Tensor) -> torch.Tensor:
+    """Copy a (4, rows, cols) tensor into column-major storage on the same device."""
+    out = empty_thin(x.shape[1], x.shape[2], x.dtype, x.device)
+    out.copy_(x)
+    return out
+
+
+def qmat(t: torch.Tensor, layout: Optional[int] = None) -> QMatC:
+    """Describe a quaternion tensor (4 or 3 planes) as a qlr_qmat.  `layout` forces ROW_MAJOR or
+    COL_MAJOR (needed for degenerate 1-row / 1-column tensors); by default it is read from the
+    strides."""
+    if t.dim() != 3 or t.shape[0] not in (3, 4):
+        raise ValueError("quaternion tensors have shape (4, rows, cols) or (3, rows, cols)")
+    if t.dtype not in _DT:
+        raise ValueError(f"unsupported dtype {t.dtype}")
+    rows, cols = t.shape[1], t.shape[2]
+    rs, cs = t.stride(1), t.stride(2)
+    row_ok = (cs == 1 or cols <= 1) and (rs >= cols or rows <= 1)
+    col_ok = (rs == 1 or rows <= 1) and (cs >= rows or cols <= 1)
+    if layout is None:
+        layout = ROW_MAJOR if (row_ok and cs == 1 and not (rs == 1 and col_ok)) else (COL_MAJOR if col_ok else ROW_MAJOR)
+    if layout == ROW_MAJOR and not row_ok or layout == COL_MAJOR and not col_ok:
+        raise ValueError("each plane must be row- or column-major with a unit stride")
+    q = QMatC()
+    q.rows, q.cols, q.dtype, q.layout = rows, cols, _DT[t.dtype], layout
+    q.ld = max(rs if layout == ROW_MAJOR else cs, cols if layout == ROW_MAJOR else rows, 1)
+    if layout == ROW_MAJOR and rows <= 1:
+        q.ld = max(cols, 1)
+    if layout == COL_MAJOR and cols <= 1:
+        q.ld = max(rows, 1)
+    off = 4 - t.shape[0]
+    es = t.element_size()
+    for c in range(4):
+        q.plane[c] = None if c < off else t.data_ptr() + (c - off) * t.stride(0) * es
+    return q
+
+
+def _A(t):
+    return qmat(t, ROW_MAJOR)
+
+
+def _T(t):
+    return qmat(t, COL_MAJOR)
+
+
+def _opts(compute: int = COMPUTE_AUTO, side: int = SIDE_AUTO, orth: int = ORTH_CHOLQR2) -> OptsC:
+    return OptsC(compute, side, orth, 0)
+
+
+class Context:
+    """A qlr context bound to a device and (by default) torch's current stream on it."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.device = device
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        self._stream = s
+        h = ctypes.c_void_p()
+        _check(lib().qlr_create(ctypes.byref(h), device, ctypes.c_void_p(s.cuda_stream)), "qlr_create")
+        self.h = h
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().qlr_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_stream(self, stream: torch.cuda.Stream) -> None:
+        self._stream = stream
+        _check(lib().qlr_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "qlr_set_stream")
+
+    def reserve(self, nbytes: int) -> None:
+        _check(lib().qlr_reserve(self.h, nbytes), "qlr_reserve")
+
+    def sync(self) -> int:
+        """Wait for the stream; return the device error code (0 if none)."""
+        return lib().qlr_sync(self.h)
+
+    def set_timing(self, on: bool) -> None:
+        _check(lib().qlr_set_timing(self.h, 1 if on else 0), "qlr_set_timing")
+
+    def reset_stats(self) -> None:
+        _check(lib().qlr_reset_stats(self.h), "qlr_reset_stats")
+
+    def stats(self) -> dict:
+        """{kernel class: (launches, total ms)} since the last reset."""
+        out = {}
+        for kid, name in enumerate(KID_NAMES):
+            n, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+            _check(lib().qlr_stats(self.h, kid, ctypes.byref(n), ctypes.byref(ms)), "qlr_stats")
+            out[name] = (n.value, ms.value)
+        return out
+
+
+def workspace_size(m, n, k, p, passes, algo=ALG2, compute=COMPUTE_AUTO) -> int:
+    return lib().qlr_workspace_size(m, n, k, p, passes, algo, compute)
+
+
+def qsketch(ctx: Context, op: int, A: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, compute: int = COMPUTE_AUTO):
+    a, x, y = _A(A), _T(X), _T(Y)
+    _check(lib().qlr_qsketch(ctx.h, op, ctypes.byref(a), ctypes.byref(x), ctypes.byref(y), compute), "qlr_qsketch")
+    return Y
+
+
+def qgram(ctx: Context, Y: torch.Tensor, G: torch.Tensor):
+    y = _T(Y)
+    _check(lib().qlr_qgram(ctx.h, ctypes.byref(y), ctypes.c_void_p(G.data_ptr())), "qlr_qgram")
+    return G
+
+
+def qchol(ctx: Context, G: torch.Tensor, R: torch.Tensor):
+    _check(lib().qlr_qchol(ctx.h, G.shape[-1], ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(R.data_ptr())),
+           "qlr_qchol")
+    return R
+
+
+def cholqr(ctx: Context, Y: torch.Tensor, Q: torch.Tensor, R: Optional[torch.Tensor] = None,
+           orth: int = ORTH_CHOLQR2):
+    y, q = _T(Y), _T(Q)
+    rp = ctypes.c_void_p(R.data_ptr()) if R is not None else ctypes.c_void_p()
+    _check(lib().qlr_cholqr(ctx.h, ctypes.byref(y), ctypes.byref(q), rp, orth), "qlr_cholqr")
+    return Q, R
+
+
+def qtsvd(ctx: Context, R: torch.Tensor, k: int, L: torch.Tensor, S: torch.Tensor, Rt: torch.Tensor, prec: int = F64):
+    l = R.shape[-1]
+    _check(lib().qlr_qtsvd(ctx.h, l, ctypes.c_void_p(R.data_ptr()), k, ctypes.c_void_p(L.data_ptr()),
+                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(Rt.data_ptr()), prec), "qlr_qtsvd")
+    return L, S, Rt
+
+
+def qrangefinder(ctx: Context, A, k, p, passes, omega, Q1, Q2, R, compute=COMPUTE_AUTO, side=SIDE_AUTO,
+                 orth=ORTH_CHOLQR2) -> int:
+    a, om, q1, q2 = _A(A), _T(omega), _T(Q1), _T(Q2)
+    o = _opts(compute, side, orth)
+    used = ctypes.c_int(-1)
+    _check(lib().qlr_qrangefinder(ctx.h, ctypes.byref(a), k, p, passes, ctypes.byref(om), ctypes.byref(o),
+                                  ctypes.byref(q1), ctypes.byref(q2), ctypes.c_void_p(R.data_ptr()),
+                                  ctypes.byref(used)), "qlr_qrangefinder")
+    return used.value
+
+
+def qsvd_lowrank(ctx: Context, A, k, p, passes, omega, U, S, V, algo=ALG2, compute=COMPUTE_AUTO, side=SIDE_AUTO,
+                 orth=ORTH_CHOLQR2):
+    a, om, u, v = _A(A), _T(omega), _T(U), _T(V)
+    o = _opts(compute, side, orth)
+    _check(lib().qlr_qsvd_lowrank(ctx.h, ctypes.byref(a), k, p, passes, algo, ctypes.byref(om), ctypes.byref(o),
+                                  ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
+           "qlr_qsvd_lowrank")
+    return U, S, V
+
+
+def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE_AUTO, side=SIDE_AUTO):
+    a, om, u, v = _A(A), _T(omega), _T(U), _T(V)
+    o = _opts(compute, side)
+    _check(lib().qlr_qblock_krylov(ctx.h, ctypes.byref(a), k, b, passes, ctypes.byref(om), ctypes.byref(o),
+                                   ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
+           "qlr_qblock_krylov")
+    return U, S, V
+
+
+def qsvd_lowrank_batched(ctx: Context, As: Sequence[torch.Tensor], ks: Sequence[int], ps: Sequence[int], passes: int,
+                         omegas, Us, Ss, Vs, compute=COMPUTE_AUTO):
+    n = len(As)
+    arrA = (QMatC * n)(*[_A(t) for t in As])
+    arrO = (QMatC * n)(*[_T(t) for t in omegas])
+    arrU = (QMatC * n)(*[_T(t) for t in Us])
+    arrV = (QMatC * n)(*[_T(t) for t in Vs])
+    kk = (ctypes.c_int * n)(*ks)
+    pp = (ctypes.c_int * n)(*ps)
+    sp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Ss])
+    o = _opts(compute, SIDE_X)
+    _check(lib().qlr_qsvd_lowrank_batched(ctx.h, n, arrA, kk, pp, passes, arrO, ctypes.byref(o), arrU, sp, arrV),
+           "qlr_qsvd_lowrank_batched")
+    return Us, Ss, Vs
+
+
+def residual_norm(ctx: Context, A, Q, side, start, iters=30) -> float:
+    a, q, s = _A(A), _T(Q), _T(start)
+    out = ctypes.c_double(0.0)
+    _check(lib().qlr_residual_norm(ctx.h, ctypes.byref(a), ctypes.byref(q), side, ctypes.byref(s), iters,
+                                   ctypes.byref(out)), "qlr_residual_norm")
+    return out.value

@@ -1,0 +1,128 @@
+"""End-to-end parity of Algorithm 2 / Algorithm 4 against the oracle run on the same Omega."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import algorithms as al
+from oracle import norms
+from oracle import quaternion as Q
+from tests._qutil import dev_rowmajor, dev_thin, host, small, small_to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    c = qlr.Context(0)
+    yield c
+    c.close()
+
+
+def _proj(M):
+    return Q.qmatmul(M, Q.qH(M))
+
+
+def run_gpu(ctx, P, v, algo, dt, compute, side=None, Ad=None):
+    from paper_2507_13731_gb300 import qlr
+    side = qlr.SIDE_X if side is None else side
+    if Ad is None:
+        Ad = dev_rowmajor(P.A, dt, pure=P.pure)
+    Om = P.Omega if side == qlr.SIDE_X else synth.omega_for(77, P.m, P.ell)
+    Od = dev_thin(Om, "f64" if dt == "f64" else "f32")
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    U, V = qlr.empty_thin(P.m, P.k, tdt), qlr.empty_thin(P.n, P.k, tdt)
+    S = torch.zeros(P.k, dtype=torch.float64, device="cuda")
+    qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, v, Od, U, S, V, algo=algo, compute=compute, side=side)
+    assert ctx.sync() == 0
+    return host(U), S.cpu().numpy(), host(V), Om, Ad
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_config1_fp64_alg2(ctx, v):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config1()
+    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG2, "f64", qlr.COMPUTE_F64)
+    ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, v, Om)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-10)
+    np.testing.assert_allclose(_proj(U[:, :, :8]), _proj(ref.U[:, :, :8]), atol=1e-8)
+    np.testing.assert_allclose(_proj(V[:, :, :8]), _proj(ref.V[:, :, :8]), atol=1e-8)
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 6])
+def test_alg4_fp64_small(ctx, v):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(160, 120, 6, 4, v, seed=21)
+    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG4, "f64", qlr.COMPUTE_F64)
+    ref = al.alg4_block_flexible(P.A, 6, 4, v, Om)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-9)
+    err_gpu = norms.lowrank_error(P.A, U, S, V)
+    err_ref = norms.lowrank_error(P.A, ref.U, ref.S, ref.V)
+    assert abs(err_gpu - err_ref) <= 1e-8 * err_ref
+
+
+@pytest.mark.parametrize("v", [2, 3, 4])
+def test_fp32_slow_decay(ctx, v):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(1024, 768, 40, 10, v, seed=22)
+    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG2, "f32", qlr.COMPUTE_F32)
+    ref = al.alg2_arbitrary_pass(P.A, 40, 10, v, Om)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-4)
+
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_side_xh(ctx, v):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(90, 140, 8, 4, v, seed=23)
+    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG2, "f64", qlr.COMPUTE_F64, side=qlr.SIDE_XH)
+    ref = al.run("alg2", P.A, 8, 4, v, Om, side="XH")
+    np.testing.assert_allclose(S, ref.S, rtol=1e-10)
+    np.testing.assert_allclose(_proj(U[:, :, :6]), _proj(ref.U[:, :, :6]), atol=1e-8)
+
+
+def test_rangefinder_factors(ctx):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(200, 150, 10, 5, 3, seed=24)
+    Ad = dev_rowmajor(P.A, "f64")
+    Od = dev_thin(P.Omega, "f64")
+    Q1, Q2 = qlr.empty_thin(200, 15, torch.float64), qlr.empty_thin(150, 15, torch.float64)
+    R = small(15)
+    for v in (2, 3, 4):
+        side = qlr.qrangefinder(ctx, Ad, 10, 5, v, Od, Q1, Q2, R, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X)
+        assert ctx.sync() == 0 and side == qlr.SIDE_X
+        ref = al.alg2_arbitrary_pass(P.A, 10, 5, v, P.Omega)
+        np.testing.assert_allclose(host(Q1), ref.Q1, atol=1e-9)
+        np.testing.assert_allclose(small_to_np(R), ref.R, atol=1e-10)
+        if v >= 2:
+            np.testing.assert_allclose(host(Q2), ref.Q2, atol=1e-9)
+
+
+def test_batched_loop_pure(ctx):
+    from paper_2507_13731_gb300 import qlr
+    probs = synth.batched_problems(count=4, mmax=200, nmax=150, rmax=12)
+    As = [dev_rowmajor(P.A, "f32", pure=True) for P in probs]
+    Os = [dev_thin(P.Omega, "f32") for P in probs]
+    Us = [qlr.empty_thin(P.m, P.k) for P in probs]
+    Vs = [qlr.empty_thin(P.n, P.k) for P in probs]
+    Ss = [torch.zeros(P.k, dtype=torch.float64, device="cuda") for P in probs]
+    qlr.qsvd_lowrank_batched(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs,
+                             compute=qlr.COMPUTE_F32)
+    assert ctx.sync() == 0
+    for P, S in zip(probs, Ss):
+        ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, 3, P.Omega)
+        np.testing.assert_allclose(S.cpu().numpy(), ref.S, rtol=1e-4)
+
+
+def test_residual_norm_matches_oracle(ctx):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(300, 200, 10, 5, 2, seed=25)
+    ref = al.alg2_arbitrary_pass(P.A, 10, 5, 2, P.Omega)
+    Ad = dev_rowmajor(P.A, "f64")
+    start = dev_thin(synth.gaussian_qmat(9, 200, 6), "f64")
+    e1 = qlr.residual_norm(ctx, Ad, dev_thin(ref.Q1, "f64"), qlr.SIDE_X, start, iters=60)
+    e2 = qlr.residual_norm(ctx, Ad, dev_thin(ref.Q2, "f64"), qlr.SIDE_XH, start, iters=60)
+    w1, w2 = norms.range_error(P.A, ref.Q1), norms.corange_error(P.A, ref.Q2)
+    assert w1 * (1 - 1e-3) <= e1 <= w1 * (1 + 1e-10)
+    assert w2 * (1 - 1e-3) <= e2 <= w2 * (1 + 1e-10)

@@ -1,0 +1,92 @@
+"""Parity of the orthonormalisation step ("QR" of Def. 1, eq. QQR): FP64 Gram, quaternion
+Cholesky, CholeskyQR2 and shifted CholeskyQR3, against the oracle's Householder QR (the thin QR
+with real positive diag(R) is unique, so Q and R are compared element by element)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import quaternion as Q
+from oracle.qr import qr
+from tests._qutil import dev_thin, host, small, small_to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    c = qlr.Context(0)
+    yield c
+    c.close()
+
+
+def _conditioned(m, l, cond, seed):
+    Uq, _ = qr(synth.gaussian_qmat(seed, m, l))
+    Vq, _ = qr(synth.gaussian_qmat(seed + 1, l, l))
+    s = np.geomspace(1.0, 1.0 / cond, l)
+    return Q.qmatmul(Uq * s, Q.qH(Vq))
+
+
+@pytest.mark.parametrize("m,l,dt", [(1000, 37, "f32"), (333, 1, "f64"), (4096, 110, "f32"), (70, 70, "f64")])
+def test_gram(ctx, m, l, dt):
+    from paper_2507_13731_gb300 import qlr
+    Y = synth.gaussian_qmat(5, m, l)
+    Yd = dev_thin(Y, dt)
+    G = small(l)
+    qlr.qgram(ctx, Yd, G)
+    assert ctx.sync() == 0
+    Yh = host(Yd)
+    want = Q.qmatmul(Q.qH(Yh), Yh)
+    scale = Q.qnorm(Q.qH(Yh)) @ Q.qnorm(Yh)
+    assert np.all(Q.qnorm(small_to_np(G) - want) <= 64 * m * 2.0 ** -53 * scale)
+
+
+@pytest.mark.parametrize("l", [1, 5, 64, 110])
+def test_chol_matches_unique_qr_factor(ctx, l):
+    from paper_2507_13731_gb300 import qlr
+    Y = _conditioned(3 * l + 10, l, 1e3, 7)
+    _, Rw = qr(Y)
+    G = Q.qmatmul(Q.qH(Y), Y)
+    Gd = torch.from_numpy(np.ascontiguousarray(G.transpose(0, 2, 1))).cuda()
+    Rd = small(l)
+    qlr.qchol(ctx, Gd, Rd)
+    assert ctx.sync() == 0
+    np.testing.assert_allclose(small_to_np(Rd), Rw, atol=1e-9 * np.abs(Rw).max())
+
+
+@pytest.mark.parametrize("m,l,cond,dt,orth", [(500, 23, 1e2, "f64", 0), (2000, 110, 1e3, "f32", 0),
+                                             (300, 40, 1e10, "f64", 1), (1500, 60, 1e6, "f32", 1),
+                                             (64, 64, 10.0, "f64", 0), (17, 3, 5.0, "f32", 0)])
+def test_cholqr_parity(ctx, m, l, cond, dt, orth):
+    from paper_2507_13731_gb300 import qlr
+    Y = _conditioned(m, l, cond, 11)
+    Yd = dev_thin(Y, dt)
+    Yh = host(Yd)
+    Qd = qlr.empty_thin(m, l, Yd.dtype)
+    Rd = small(l)
+    qlr.cholqr(ctx, Yd, Qd, Rd, orth)
+    assert ctx.sync() == 0
+    Qh, Rh = host(Qd), small_to_np(Rd)
+    Qw, Rw = qr(Yh)
+    u = 2.0 ** -53 if dt == "f64" else 2.0 ** -24
+    orth_err = np.abs(Q.qmatmul(Q.qH(Qh), Qh) - Q.qeye(l)).max()
+    assert orth_err <= 200 * l * u
+    recon = Q.qfro(Q.qmatmul(Qh, Rh) - Yh) / Q.qfro(Yh)
+    assert recon <= 50 * l * u * (cond if orth == 1 else 1.0)
+    if cond * u < 1e-3:   # well conditioned: unique factors agree element by element
+        tol = 50 * l * u * cond
+        np.testing.assert_allclose(Rh, Rw, atol=tol * np.abs(Rw).max())
+        np.testing.assert_allclose(Qh, Qw, atol=tol)
+
+
+def test_cholqr2_breakdown_is_reported(ctx):
+    from paper_2507_13731_gb300 import qlr
+    Y = synth.gaussian_qmat(3, 50, 6)
+    Y[:, :, 4] = 0.0
+    Yd = dev_thin(Y, "f64")
+    Qd = qlr.empty_thin(50, 6, torch.float64)
+    qlr.cholqr(ctx, Yd, Qd, None, qlr.ORTH_CHOLQR2)
+    assert ctx.sync() == qlr.ENOTPD
+    assert ctx.sync() == 0          # the error word is cleared once read
