@@ -198,6 +198,48 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_driver(args):
+    """Small driver for ncu captures: the bench workload's A and Omega, then `warmup + steps`
+    calls of one sketch pass (--only sketch --op N|H) or one QSVD with --passes v (--only qsvd).
+    Prints one JSON line with the mean CUDA-event time of the timed calls."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    P = synth.config2(args.passes)
+    compute = getattr(qlr, "COMPUTE_" + args.compute)
+    a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
+    A = torch.from_numpy(P.A).to(a_dt).cuda().contiguous()
+    om = qlr.to_thin(torch.from_numpy(P.Omega).float().cuda())
+    ctx = qlr.Context(0)
+    U, V = qlr.empty_thin(M, K_RANK), qlr.empty_thin(N, K_RANK)
+    S = torch.zeros(K_RANK, dtype=torch.float64, device="cuda")
+    Y = qlr.empty_thin(M, K_RANK + P_OVER)
+    op = qlr.OP_N if args.op == "N" else qlr.OP_H
+
+    def call():
+        if args.only == "sketch":
+            qlr.qsketch(ctx, op, A, om, Y, compute)
+        else:
+            qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, args.passes, om, U, S, V, compute=compute, side=qlr.SIDE_X)
+
+    for _ in range(args.warmup):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    rc = ctx.sync()
+    print(json.dumps({"only": args.only, "op": args.op, "passes": args.passes, "compute": args.compute,
+                      "ms_per_call": e0.elapsed_time(e1) / args.steps, "device_error": rc}), flush=True)
+    ctx.close()
+    return 0 if rc == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,8 +248,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["sketch", "qsvd"], default=None,
+                    help="profiling driver: time only sketch passes or single QSVDs (for ncu captures)")
+    ap.add_argument("--op", choices=["N", "H"], default="N")
+    ap.add_argument("--passes", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.only:
+        return profile_driver(args)
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

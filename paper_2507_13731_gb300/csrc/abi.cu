@@ -62,7 +62,7 @@ size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
   return (size_t)5 * 32 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 8 * 256;
 }
 
-size_t tsvd_ws_bound(int64_t l) { return (size_t)64 * l * l + 16 * l + 8192; }
+size_t tsvd_ws_bound(int64_t l) { return qlr::core_tsvd_ws((int)l) + 16384; }
 
 // ---------------------------------------------------------------------------------------
 struct Sched {
@@ -443,7 +443,9 @@ int qlr_qchol(qlr_ctx* ctx, int l, const double* G, double* R) {
   if (!ctx || !G || !R || l < 0) return QLR_EINVAL;
   if (G == R) return QLR_EINVAL;
   DeviceGuard g(ctx->device);
-  return qlr::chol(ctx, l, G, R, 0.0);
+  QLR_TRY(qlr_ensure_ws(ctx, (size_t)40 * l * l + 65536));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  return qlr::chol(ctx, l, G, R, 0.0, ws);
 }
 
 int qlr_cholqr(qlr_ctx* ctx, const qlr_qmat* Y, qlr_qmat* Q, double* R, int orth) {

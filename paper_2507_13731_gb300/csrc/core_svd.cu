@@ -12,11 +12,17 @@
 // pair.  At convergence W = U diag(sigma); each quaternion singular value of R is one of the
 // doubled singular values of chi(R).
 //
-// The right rotations are accumulated into V (R V = U diag(sigma)), so both vector sets are
-// orthonormal to the working precision.  Precision: the sweeps run in T (float or double); a final
+// The right rotations make up V (R V = U diag(sigma)).  The sweep kernel works on W alone (in
+// shared memory when it fits) and logs every rotation (c, s, mu); a second kernel replays the log
+// on V = I.  The rows of V transform independently under right rotations, so the replay runs
+// row-parallel on many SMs.  Both vector sets are orthonormal to the working precision.  Precision: the sweeps run in T (float or double); a final
 // FP64 step evaluates every kept singular value as the two-sided Rayleigh quotient
 // sigma = Re(u^H R v) / (|u| |v|) from the FP64 R, whose error is second order in the vectors'.
+#include <cooperative_groups.h>
+
 #include "qlr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -53,19 +59,14 @@ __device__ __forceinline__ void rr_pair(int lp, int r, int i, int& p, int& q) {
 
 template <class T>
 __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R, int l, T* __restrict__ Wout,
-                                                     T* __restrict__ Vout, bool w_smem, bool v_smem, int max_sweeps,
-                                                     T tol, T* __restrict__ sig_out, int* __restrict__ sweeps_out,
-                                                     int* err) {
+                                                     bool w_smem, int max_sweeps, T tol, T* __restrict__ sig_out,
+                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot;
   T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
-  T* V = v_smem ? reinterpret_cast<T*>(smem_raw) + (w_smem ? 4 * (size_t)l * l : 0) : Vout;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
   const size_t ll = (size_t)l * l;
-  for (size_t e = t; e < 4 * ll; e += JT) {
-    W[e] = (T)R[e];
-    V[e] = (e < ll && (e % l) == (e / l)) ? (T)1 : (T)0;   // V = I
-  }
+  for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
   __syncthreads();
   const int lp = l + (l & 1);
   int sweep = 0;
@@ -90,21 +91,23 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
         a = warp_sum(a); b = warp_sum(b);
         g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
         T gn = sqrt(qnorm2(g));
-        if (!(gn > tol * sqrt(a * b)) || gn == (T)0) continue;
+        T* lg = rlog + (((size_t)sweep * (lp - 1) + r) * (lp / 2) + pi) * 6;
+        if (!(gn > tol * sqrt(a * b)) || gn == (T)0) {
+          if (lane == 0) { lg[0] = (T)1; lg[1] = (T)0; lg[2] = (T)1; lg[3] = lg[4] = lg[5] = (T)0; }
+          continue;
+        }
         if (lane == 0) s_rot = 1;
         Quat<T> mu = {g.w / gn, g.x / gn, g.y / gn, g.z / gn};
         T zeta = (b - a) / (2 * gn);
         T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
         T c = (T)1 / sqrt((T)1 + tt * tt), s = c * tt;
+        if (lane == 0) { lg[0] = c; lg[1] = s; lg[2] = mu.w; lg[3] = mu.x; lg[4] = mu.y; lg[5] = mu.z; }
         for (int i = lane; i < l; i += 32) {
           Quat<T> wp = ldw(W, l, i, p), wq = qmulc(ldw(W, l, i, q), mu);   // w_q mu*
           Quat<T> np = {c * wp.w - s * wq.w, c * wp.x - s * wq.x, c * wp.y - s * wq.y, c * wp.z - s * wq.z};
           Quat<T> nq = {s * wp.w + c * wq.w, s * wp.x + c * wq.x, s * wp.y + c * wq.y, s * wp.z + c * wq.z};
           stw(W, l, i, p, np);
           stw(W, l, i, q, nq);
-          Quat<T> vp = ldw(V, l, i, p), vq = qmulc(ldw(V, l, i, q), mu);
-          stw(V, l, i, p, {c * vp.w - s * vq.w, c * vp.x - s * vq.x, c * vp.y - s * vq.y, c * vp.z - s * vq.z});
-          stw(V, l, i, q, {s * vp.w + c * vq.w, s * vp.x + c * vq.x, s * vp.y + c * vq.y, s * vp.z + c * vq.z});
         }
       }
       __syncthreads();
@@ -129,10 +132,229 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
     }
   }
   __syncthreads();
-  for (size_t e = t; e < 4 * ll; e += JT) {
-    if (w_smem) Wout[e] = W[e];
-    if (v_smem) Vout[e] = V[e];
+  if (w_smem)
+    for (size_t e = t; e < 4 * ll; e += JT) Wout[e] = W[e];
+}
+
+// Replay the logged rotations on V = I, one warp per row of V (rows are independent under right
+// rotations); the pairs of one round are disjoint, so the lanes apply them concurrently.
+template <class T>
+__global__ void __launch_bounds__(128) jacobi_replay_kernel(int l, const T* __restrict__ rlog, const int* __restrict__ nsweeps,
+                                                             T* __restrict__ Vout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int row = blockIdx.x * 4 + warp;
+  T* vr = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 4 * l;   // this row: 4 planes x l
+  if (row >= l) return;
+  for (int j = lane; j < l; j += 32) {
+    vr[j] = (j == row) ? (T)1 : (T)0;
+    vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
   }
+  __syncwarp();
+  const int lp = l + (l & 1);
+  const int ns = *nsweeps;
+  for (int sw = 0; sw < ns; ++sw) {
+    for (int r = 0; r < lp - 1; ++r) {
+      const T* lg0 = rlog + (((size_t)sw * (lp - 1) + r) * (lp / 2)) * 6;
+      for (int pi = lane; pi < lp / 2; pi += 32) {
+        int p, q;
+        rr_pair(lp, r, pi, p, q);
+        if (p >= l || q >= l) continue;
+        const T* lg = lg0 + (size_t)pi * 6;
+        const T c = lg[0], s = lg[1];
+        if (s == (T)0) continue;
+        const Quat<T> mu = {lg[2], lg[3], lg[4], lg[5]};
+        Quat<T> vp = {vr[p], vr[l + p], vr[2 * l + p], vr[3 * l + p]};
+        Quat<T> vq = qmulc(Quat<T>{vr[q], vr[l + q], vr[2 * l + q], vr[3 * l + q]}, mu);
+        vr[p] = c * vp.w - s * vq.w; vr[l + p] = c * vp.x - s * vq.x; vr[2 * l + p] = c * vp.y - s * vq.y; vr[3 * l + p] = c * vp.z - s * vq.z;
+        vr[q] = s * vp.w + c * vq.w; vr[l + q] = s * vp.x + c * vq.x; vr[2 * l + q] = s * vp.y + c * vq.y; vr[3 * l + q] = s * vp.z + c * vq.z;
+      }
+      __syncwarp();
+    }
+  }
+  const size_t ll = (size_t)l * l;
+  for (int j = lane; j < l; j += 32)
+    for (int c = 0; c < 4; ++c) Vout[c * ll + (size_t)j * l + row] = vr[(size_t)c * l + j];
+}
+
+// ---------------------------------------------------------------------------------------
+// Cluster block Jacobi for larger l: the l columns of W are split into NB = 2 * P blocks
+// (P = cluster size).  A sweep is NB - 1 block rounds; in block round br, CTA p takes the block
+// pair rr_pair(NB, br, p) (disjoint across CTAs), loads the union of the two blocks into shared
+// memory, runs one local round-robin sweep over its columns and writes them back; a cluster
+// barrier ends the round.  W stays in global memory (L2).  Every local round is one "stage" of
+// the rotation log: P x BW records (p, q, c, s, mu), disjoint columns, identity-padded, so the
+// replay can apply a whole stage in parallel.
+constexpr int JP = 8;                 // cluster size
+constexpr int JB_THREADS = 256;
+constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4)
+
+template <class T>
+__global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
+                                                                   T* __restrict__ W, int max_sweeps, T tol,
+                                                                   T* __restrict__ rlog, int* __restrict__ flags,
+                                                                   int* __restrict__ sweeps_out, T* __restrict__ sig_out,
+                                                                   int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);          // [4][l][2 bw]  (plane, row, local column)
+  cg::cluster_group cluster = cg::this_cluster();
+  const int p = (int)cluster.block_rank();
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JB_THREADS / 32;
+  const size_t ll = (size_t)l * l;
+  const int NB = 2 * JP;
+  const int U = 2 * bw;                           // local columns
+  const int stages_per_sweep = (NB - 1) * (U - 1);
+  const int stage_cap = JP * bw;
+  for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)R[e];
+  if (p == 0)
+    for (int i = t; i < max_sweeps; i += JB_THREADS) flags[i] = 0;
+  __threadfence();
+  cluster.sync();
+  int sweep = 0;
+  bool converged = (l < 2);
+  __shared__ int s_rot;
+  __shared__ int gcol[64];
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    if (t == 0) s_rot = 0;
+    for (int br = 0; br < NB - 1; ++br) {
+      int ba, bb;
+      rr_pair(NB, br, p, ba, bb);
+      // global column of each local slot (or -1)
+      if (t < U) {
+        const int blk = (t < bw) ? ba : bb, off = (t < bw) ? t : t - bw;
+        const int g = blk * bw + off;
+        gcol[t] = (g < l) ? g : -1;
+      }
+      __syncthreads();
+      for (int e = t; e < 4 * l * U; e += JB_THREADS) {
+        const int c = e / (l * U), rem = e % (l * U), row = rem / U, lc = rem % U;
+        const int g = gcol[lc];
+        S[e] = (g >= 0) ? W[c * ll + (size_t)g * l + row] : (T)0;
+      }
+      __syncthreads();
+      for (int lr = 0; lr < U - 1; ++lr) {
+        T* lg_stage = rlog + ((size_t)sweep * stages_per_sweep + (size_t)br * (U - 1) + lr) * stage_cap * REC;
+        for (int pi = warp; pi < bw; pi += nwarps) {
+          int a, b;
+          rr_pair(U, lr, pi, a, b);
+          T* lg = lg_stage + ((size_t)p * bw + pi) * REC;
+          const int ga = gcol[a], gb = gcol[b];
+          if (ga < 0 || gb < 0) {
+            if (lane == 0) { lg[0] = (T)-1; lg[1] = (T)-1; lg[2] = (T)1; lg[3] = (T)0; }
+            continue;
+          }
+          T aa = 0, bb2 = 0;
+          Quat<T> g = {0, 0, 0, 0};
+          for (int i = lane; i < l; i += 32) {
+            Quat<T> wp = {S[((size_t)0 * l + i) * U + a], S[((size_t)1 * l + i) * U + a], S[((size_t)2 * l + i) * U + a],
+                          S[((size_t)3 * l + i) * U + a]};
+            Quat<T> wq = {S[((size_t)0 * l + i) * U + b], S[((size_t)1 * l + i) * U + b], S[((size_t)2 * l + i) * U + b],
+                          S[((size_t)3 * l + i) * U + b]};
+            aa += qnorm2(wp);
+            bb2 += qnorm2(wq);
+            Quat<T> pr = qcmul(wp, wq);
+            g.w += pr.w; g.x += pr.x; g.y += pr.y; g.z += pr.z;
+          }
+          aa = warp_sum(aa); bb2 = warp_sum(bb2);
+          g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
+          const T gn = sqrt(qnorm2(g));
+          if (!(gn > tol * sqrt(aa * bb2)) || gn == (T)0) {
+            if (lane == 0) { lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = (T)1; lg[3] = (T)0; }
+            continue;
+          }
+          if (lane == 0) s_rot = 1;
+          const Quat<T> mu = {g.w / gn, g.x / gn, g.y / gn, g.z / gn};
+          const T zeta = (bb2 - aa) / (2 * gn);
+          const T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          const T c = (T)1 / sqrt((T)1 + tt * tt), sn = c * tt;
+          if (lane == 0) {
+            lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = c; lg[3] = sn;
+            lg[4] = mu.w; lg[5] = mu.x; lg[6] = mu.y; lg[7] = mu.z;
+          }
+          for (int i = lane; i < l; i += 32) {
+            const size_t o0 = ((size_t)0 * l + i) * U, o1 = ((size_t)1 * l + i) * U, o2 = ((size_t)2 * l + i) * U,
+                         o3 = ((size_t)3 * l + i) * U;
+            Quat<T> wp = {S[o0 + a], S[o1 + a], S[o2 + a], S[o3 + a]};
+            Quat<T> wq = qmulc(Quat<T>{S[o0 + b], S[o1 + b], S[o2 + b], S[o3 + b]}, mu);
+            S[o0 + a] = c * wp.w - sn * wq.w; S[o1 + a] = c * wp.x - sn * wq.x;
+            S[o2 + a] = c * wp.y - sn * wq.y; S[o3 + a] = c * wp.z - sn * wq.z;
+            S[o0 + b] = sn * wp.w + c * wq.w; S[o1 + b] = sn * wp.x + c * wq.x;
+            S[o2 + b] = sn * wp.y + c * wq.y; S[o3 + b] = sn * wp.z + c * wq.z;
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = t; e < 4 * l * U; e += JB_THREADS) {
+        const int c = e / (l * U), rem = e % (l * U), row = rem / U, lc = rem % U;
+        const int g = gcol[lc];
+        if (g >= 0) W[c * ll + (size_t)g * l + row] = S[e];
+      }
+      __threadfence();
+      cluster.sync();
+    }
+    if (t == 0 && s_rot) atomicOr(&flags[sweep], 1);
+    __threadfence();
+    cluster.sync();
+    converged = (*(volatile int*)&flags[sweep] == 0);
+    cluster.sync();
+  }
+  if (p == 0 && t == 0) {
+    *sweeps_out = sweep;
+    if (!converged) qlr_set_error(err, QLR_ENOCONV);
+  }
+  // column norms and normalisation: CTA p handles columns p, p + P, ...
+  for (int j = p * nwarps + warp; j < l; j += JP * nwarps) {
+    T a = 0;
+    for (int i = lane; i < l; i += 32) a += qnorm2(ldw(W, l, i, j));
+    a = sqrt(warp_sum(a));
+    if (lane == 0) sig_out[j] = a;
+    const T inv = a > (T)0 ? (T)1 / a : (T)0;
+    for (int i = lane; i < l; i += 32) {
+      Quat<T> w = ldw(W, l, i, j);
+      stw(W, l, i, j, {w.w * inv, w.x * inv, w.y * inv, w.z * inv});
+    }
+  }
+}
+
+// Replay of the staged rotation log on V = I, one warp per row; the records of a stage touch
+// disjoint columns, so the lanes apply them concurrently.
+template <class T>
+__global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw, const T* __restrict__ rlog,
+                                                                   const int* __restrict__ nsweeps, T* __restrict__ Vout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int row = blockIdx.x * 4 + warp;
+  T* vr = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 4 * l;
+  if (row >= l) return;
+  for (int j = lane; j < l; j += 32) {
+    vr[j] = (j == row) ? (T)1 : (T)0;
+    vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
+  }
+  __syncwarp();
+  const int U = 2 * bw;
+  const size_t nst = (size_t)(*nsweeps) * (2 * JP - 1) * (U - 1);
+  const int cap = JP * bw;
+  for (size_t st = 0; st < nst; ++st) {
+    const T* lg0 = rlog + st * cap * REC;
+    for (int k = lane; k < cap; k += 32) {
+      const T* lg = lg0 + (size_t)k * REC;
+      const T sn = lg[3];
+      if (sn == (T)0) continue;
+      const int pp = (int)lg[0], qq = (int)lg[1];
+      const T c = lg[2];
+      const Quat<T> mu = {lg[4], lg[5], lg[6], lg[7]};
+      Quat<T> vp = {vr[pp], vr[l + pp], vr[2 * l + pp], vr[3 * l + pp]};
+      Quat<T> vq = qmulc(Quat<T>{vr[qq], vr[l + qq], vr[2 * l + qq], vr[3 * l + qq]}, mu);
+      vr[pp] = c * vp.w - sn * vq.w; vr[l + pp] = c * vp.x - sn * vq.x; vr[2 * l + pp] = c * vp.y - sn * vq.y;
+      vr[3 * l + pp] = c * vp.z - sn * vq.z;
+      vr[qq] = sn * vp.w + c * vq.w; vr[l + qq] = sn * vp.x + c * vq.x; vr[2 * l + qq] = sn * vp.y + c * vq.y;
+      vr[3 * l + qq] = sn * vp.z + c * vq.z;
+    }
+    __syncwarp();
+  }
+  const size_t ll = (size_t)l * l;
+  for (int j = lane; j < l; j += 32)
+    for (int c = 0; c < 4; ++c) Vout[c * ll + (size_t)j * l + row] = vr[(size_t)c * l + j];
 }
 
 // Rank of each column by descending sigma (ties broken by index): order[rank] = column.  A NaN
@@ -206,25 +428,80 @@ __global__ void __launch_bounds__(256) refine_kernel(const double* __restrict__ 
 
 namespace qlr {
 
+constexpr int JMAX_SWEEPS = 30;
+constexpr int JBLOCK_MIN_L = 48;     // from this size on, the cluster block Jacobi is used
+
+size_t jacobi_log_floats(int l) {
+  if (l >= JBLOCK_MIN_L) {
+    const int bw = (l + 2 * JP - 1) / (2 * JP), U = 2 * bw;
+    return (size_t)JMAX_SWEEPS * (2 * JP - 1) * (U - 1) * JP * bw * REC + REC;
+  }
+  const int lp = l + (l & 1);
+  return (size_t)JMAX_SWEEPS * (lp - 1) * (lp / 2) * 6 + 6;
+}
+
 template <class T>
 static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, WsArena& ws) {
   const size_t ll4 = (size_t)4 * l * l;
   T* W = ws.take<T>(ll4);
   T* V = ws.take<T>(ll4);
+  T* rlog = ws.take<T>(jacobi_log_floats(l));
   T* sig = ws.take<T>(l);
   int* order = ws.take<int>(l);
   int* sweeps = ws.take<int>(1);
+  int* flags = ws.take<int>(JMAX_SWEEPS);
   if (!ws.ok) return QLR_ENOMEM;
-  const size_t one = ll4 * sizeof(T);
-  const bool w_smem = one <= 200 * 1024;
-  const bool v_smem = w_smem && 2 * one <= 200 * 1024;
-  const size_t smem = (w_smem ? one : 0) + (v_smem ? one : 0);
-  if (smem > 0)
-    QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const T eps = (sizeof(T) == 4) ? (T)5.9604645e-08 : (T)1.1102230246251565e-16;
   const T tol = (T)8 * eps * (T)sqrt((double)l);   // above the rounding noise of the dot products
-  { KTimer kt(ctx, QLR_KID_JACOBI);
-  jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, V, w_smem, v_smem, 60, tol, sig, sweeps, ctx->d_err); }
+  if (l >= JBLOCK_MIN_L) {
+    const int bw = (l + 2 * JP - 1) / (2 * JP);
+    const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
+    if (smem > 220 * 1024) return QLR_EUNSUPPORTED;
+    QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(JP, 1, 1);
+    cfg.blockDim = dim3(JB_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = JP;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+      KTimer kt(ctx, QLR_KID_JACOBI);
+      QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_block_kernel<T>, R, l, bw, W, (int)JMAX_SWEEPS, tol, rlog, flags,
+                                      sweeps, sig, ctx->d_err));
+    }
+    {
+      KTimer kt(ctx, QLR_KID_JACOBI);
+      const size_t rs = (size_t)4 * 4 * l * sizeof(T);
+      if (rs > 48 * 1024)
+        QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+      jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, rlog, sweeps, V);
+      QLR_CUDA_TRY(cudaGetLastError());
+    }
+  } else {
+    const size_t one = ll4 * sizeof(T);
+    const bool w_smem = one <= 220 * 1024;
+    const size_t smem = w_smem ? one : 0;
+    if (smem > 0)
+      QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      KTimer kt(ctx, QLR_KID_JACOBI);
+      jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err);
+    }
+    QLR_CUDA_TRY(cudaGetLastError());
+    {
+      KTimer kt(ctx, QLR_KID_JACOBI);
+      const size_t rs = (size_t)4 * 4 * l * sizeof(T);
+      if (rs > 48 * 1024)
+        QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+      jacobi_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, rlog, sweeps, V);
+    }
+  }
   QLR_CUDA_TRY(cudaGetLastError());
   { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); }
   QLR_CUDA_TRY(cudaGetLastError());
@@ -234,6 +511,10 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
+}
+
+size_t core_tsvd_ws(int l) {
+  return (size_t)2 * 4 * l * l * 8 + jacobi_log_floats(l) * 8 + (size_t)16 * l + JMAX_SWEEPS * 4 + 8 * 256;
 }
 
 int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec, WsArena& ws) {

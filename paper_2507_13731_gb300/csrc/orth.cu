@@ -94,107 +94,6 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunks,
   if (i != j) st_small(G, l, j, i, {s.w, -s.x, -s.y, -s.z});
 }
 
-// ---------------------------------------------------------------------------------------
-// Right-looking quaternion Cholesky G = R^H R in FP64, one CTA.  R is worked in place (upper
-// triangle).  shift_coef > 0 adds shift_coef * trace(G) to the diagonal first (shifted CholQR).
-__global__ void __launch_bounds__(1024) chol_kernel(const double* __restrict__ G, double* __restrict__ R, int l,
-                                                     double shift_coef, int* err) {
-  __shared__ double s_piv, s_shift;
-  const int t = threadIdx.x, nt = blockDim.x;
-  const size_t ll = (size_t)l * l;
-  if (t == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < l; ++i) tr += G[(size_t)i * l + i];
-    s_shift = shift_coef * tr;
-  }
-  for (size_t e = t; e < ll; e += nt) {
-    int i = (int)(e % l), j = (int)(e / l);
-    for (int c = 0; c < 4; ++c) R[c * ll + e] = (i <= j) ? G[c * ll + e] : 0.0;
-  }
-  __syncthreads();
-  for (int i = t; i < l; i += nt) R[(size_t)i * l + i] += s_shift;
-  __syncthreads();
-  double maxdiag = 0.0;
-  for (int i = 0; i < l; ++i) maxdiag = fmax(maxdiag, R[(size_t)i * l + i]);
-  for (int j = 0; j < l; ++j) {
-    if (t == 0) {
-      double d2 = R[(size_t)j * l + j];
-      if (!(d2 > 0.0)) {
-        qlr_set_error(err, QLR_ENOTPD);
-        d2 = fmax(maxdiag, 1.0) * 1e-300;
-      }
-      double d = sqrt(d2);
-      s_piv = d;
-      R[(size_t)j * l + j] = d;
-      R[ll + (size_t)j * l + j] = 0.0;
-      R[2 * ll + (size_t)j * l + j] = 0.0;
-      R[3 * ll + (size_t)j * l + j] = 0.0;
-    }
-    __syncthreads();
-    const double inv = 1.0 / s_piv;
-    for (int k = j + 1 + t; k < l; k += nt) {
-      size_t o = (size_t)k * l + j;
-      for (int c = 0; c < 4; ++c) R[c * ll + o] *= inv;
-    }
-    __syncthreads();
-    // trailing update of the upper triangle: R[i][k] -= conj(R[j][i]) R[j][k], j < i <= k
-    const int rem = l - j - 1;
-    const int64_t npairs = (int64_t)rem * (rem + 1) / 2;
-    for (int64_t p = t; p < npairs; p += nt) {
-      // map p -> (ii, kk) with 0 <= ii <= kk < rem, column-major over the upper triangle
-      int kk = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-      while ((int64_t)kk * (kk + 1) / 2 > p) --kk;
-      while ((int64_t)(kk + 1) * (kk + 2) / 2 <= p) ++kk;
-      int ii = (int)(p - (int64_t)kk * (kk + 1) / 2);
-      int i = j + 1 + ii, k = j + 1 + kk;
-      Quat<double> a = ld_small(R, l, j, i), b = ld_small(R, l, j, k), r = ld_small(R, l, i, k);
-      Quat<double> pr = qcmul(a, b);
-      r.w -= pr.w; r.x -= pr.x; r.y -= pr.y; r.z -= pr.z;
-      st_small(R, l, i, k, r);
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Inverse of an upper-triangular quaternion matrix with real diagonal: one warp per column,
-// back substitution x_i = -(sum_{t=i+1..j} R_it x_t) / R_ii.
-constexpr int TI_WARPS = 4, TI_MAXL = 512;
-
-__global__ void __launch_bounds__(32 * TI_WARPS) tri_inv_kernel(const double* __restrict__ R, double* __restrict__ X, int l) {
-  extern __shared__ double sx[];  // TI_WARPS * 4 * l
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int j = blockIdx.x * TI_WARPS + warp;
-  if (j >= l) return;
-  double* x = sx + (size_t)warp * 4 * l;
-  for (int i = lane; i < l; i += 32) x[i] = x[l + i] = x[2 * l + i] = x[3 * l + i] = 0.0;
-  __syncwarp();
-  if (lane == 0) x[j] = 1.0 / R[(size_t)j * l + j];
-  __syncwarp();
-  for (int i = j - 1; i >= 0; --i) {
-    Quat<double> s = {0, 0, 0, 0};
-    for (int t = i + 1 + lane; t <= j; t += 32) {
-      Quat<double> p = qmul(ld_small(R, l, i, t), Quat<double>{x[t], x[l + t], x[2 * l + t], x[3 * l + t]});
-      s.w += p.w; s.x += p.x; s.y += p.y; s.z += p.z;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-      s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
-    }
-    if (lane == 0) {
-      double inv = -1.0 / R[(size_t)i * l + i];
-      x[i] = s.w * inv; x[l + i] = s.x * inv; x[2 * l + i] = s.y * inv; x[3 * l + i] = s.z * inv;
-    }
-    __syncwarp();
-  }
-  const size_t ll = (size_t)l * l;
-  for (int i = lane; i < l; i += 32)
-    for (int c = 0; c < 4; ++c) X[c * ll + (size_t)j * l + i] = x[(size_t)c * l + i];
-}
-
 // C = A B for small l x l quaternion matrices (FP64), A and B upper triangular.
 __global__ void small_matmul_kernel(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
                                     int l) {
@@ -209,11 +108,416 @@ __global__ void small_matmul_kernel(const double* __restrict__ A, const double* 
   st_small(C, l, i, j, s);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// FP64-class Gram of FP32 data on the FP32 pipes (GB300 runs FP64 at 1/64 of the FP32 rate).
+// The real symmetric W = Yh^T Yh of the plane-stacked Yh = [Y0 Y1 Y2 Y3] (m x 4l) is accumulated
+// in double-FP32: every product a*b is split exactly into hi + lo with an FMA, hi is added with
+// a branch-free two-sum (Knuth) into (S, C), lo goes into C.  The result S + C has a relative
+// error of about 2^-48 of sum |a b|.  Upper 64 x 64 tiles only; row chunks give partial sums
+// that a second kernel adds in FP64 and combines into the quaternion Gram:
+//   G0 = W00 + W11 + W22 + W33,  G1 = W01 - W10 - W23 + W32,
+//   G2 = W02 + W13 - W20 - W31,  G3 = W03 - W12 + W21 - W30   (W_cd = Y_c^T Y_d).
+constexpr int WT = 64, WR = 16;
+
+// The _rn intrinsics keep the compiler from contracting these steps into FMAs.
+__device__ __forceinline__ void df_add(float& S, float& C, float a, float b) {
+  const float hi = __fmul_rn(a, b);
+  const float lo = fmaf(a, b, -hi);
+  const float s = __fadd_rn(S, hi);
+  const float v = __fsub_rn(s, S);
+  const float e = __fadd_rn(__fsub_rn(S, __fsub_rn(s, v)), __fsub_rn(hi, v));
+  S = s;
+  C = __fadd_rn(C, __fadd_rn(e, lo));
+}
+
+__global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
+                                                               const float* __restrict__ y2, const float* __restrict__ y3,
+                                                               int64_t m, int l, int64_t ld, int64_t rows_per_chunk,
+                                                               const int2* __restrict__ tiles, double* __restrict__ part) {
+  __shared__ float Ya[WR][WT];
+  __shared__ float Yb[WR][WT];
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const int2 tile = tiles[blockIdx.x];
+  const int I0 = tile.x * WT, J0 = tile.y * WT;
+  const int L4 = 4 * l;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r_end = min(m, r_begin + rows_per_chunk);
+  const float* yp[4] = {y0, y1, y2, y3};
+  float S[4][4], C[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) S[a][b] = C[a][b] = 0.f;
+  // loader mapping: 256 threads x 4 loads = 16 rows x 64 columns per operand
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += WR) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int rr = t % WR, cc = t / WR + 16 * h;
+      const int64_t gr = r0 + rr;
+      float va = 0.f, vb = 0.f;
+      if (gr < r_end) {
+        const int Ia = I0 + cc, Ib = J0 + cc;
+        if (Ia < L4) va = yp[Ia / l][gr + (int64_t)(Ia % l) * ld];
+        if (Ib < L4) vb = yp[Ib / l][gr + (int64_t)(Ib % l) * ld];
+      }
+      Ya[rr][cc] = va;
+      Yb[rr][cc] = vb;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int rr = 0; rr < WR; ++rr) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = Ya[rr][tx + 16 * q]; b[q] = Yb[rr][ty + 16 * q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int z = 0; z < 4; ++z) df_add(S[x][z], C[x][z], a[x], b[z]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (size_t)blockIdx.y * L4 * L4;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int I = I0 + tx + 16 * x, J = J0 + ty + 16 * z;
+      if (I < L4 && J < L4) P[(size_t)J * L4 + I] = (double)S[x][z] + (double)C[x][z];
+    }
+}
+
+__device__ __forceinline__ double w_at(const double* __restrict__ part, int nchunks, int L4, int I, int J) {
+  if ((I / WT) > (J / WT)) { int t = I; I = J; J = t; }     // only upper tiles were computed
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * L4 * L4 + (size_t)J * L4 + I];
+  return s;
+}
+
+__global__ void gram_df_combine_kernel(const double* __restrict__ part, int nchunks, int l, double* __restrict__ G) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)l * l) return;
+  const int i = (int)(idx % l), j = (int)(idx / l);
+  if (i > j) return;
+  const int L4 = 4 * l;
+  double w[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) w[c][d] = w_at(part, nchunks, L4, c * l + i, d * l + j);
+  Quat<double> g;
+  g.w = w[0][0] + w[1][1] + w[2][2] + w[3][3];
+  g.x = w[0][1] - w[1][0] - w[2][3] + w[3][2];
+  g.y = w[0][2] + w[1][3] - w[2][0] - w[3][1];
+  g.z = w[0][3] - w[1][2] + w[2][1] - w[3][0];
+  if (i == j) g.x = g.y = g.z = 0.0;
+  st_small(G, l, i, j, g);
+  if (i != j) st_small(G, l, j, i, {g.w, -g.x, -g.y, -g.z});
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Blocked right-looking quaternion Cholesky in FP64 over many SMs.  Wm holds the upper triangle
+// of the working matrix (initially G, plus the shift); R receives the factor.  For each panel
+// [j0, j0 + CB): (1) one CTA factors the diagonal block and inverts it; (2) the panel rows
+// R[j0:j1, k] = R_jj^{-H} Wm[j0:j1, k] are formed column-parallel; (3) the trailing upper
+// triangle is updated tile-parallel: Wm[i, k] -= sum_t conj(R[t, i]) R[t, k].
+constexpr int CB = 16;      // panel width
+constexpr int CT = 8;       // trailing-update tile
+
+__global__ void chol_init_kernel(const double* __restrict__ G, double* __restrict__ Wm, double* __restrict__ R, int l,
+                                 double shift_coef) {
+  __shared__ double s_tr;
+  const size_t ll = (size_t)l * l;
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < l; ++i) tr += G[(size_t)i * l + i];
+    s_tr = shift_coef * tr;
+  }
+  __syncthreads();
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ll; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % l), j = (int)(e / l);
+    for (int c = 0; c < 4; ++c) {
+      Wm[c * ll + e] = (i <= j) ? G[c * ll + e] + ((c == 0 && i == j) ? s_tr : 0.0) : 0.0;
+      R[c * ll + e] = 0.0;
+    }
+  }
+}
+
+// Factor the diagonal block [j0, j0+b) of Wm into R (upper, real positive diagonal) and write its
+// inverse into Dinv (b x b x 4, column-major).
+__global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm, double* __restrict__ R, int l, int j0,
+                                                         int b, double* __restrict__ Dinv, int* err) {
+  __shared__ double D[4][CB][CB];
+  __shared__ double X[4][CB][CB];
+  __shared__ double piv;
+  const int t = threadIdx.x;
+  const size_t ll = (size_t)l * l;
+  for (int e = t; e < CB * CB; e += blockDim.x) {
+    const int i = e % CB, j = e / CB;
+    for (int c = 0; c < 4; ++c) {
+      D[c][i][j] = (i < b && j < b && i <= j) ? Wm[c * ll + (size_t)(j0 + j) * l + j0 + i] : 0.0;
+      X[c][i][j] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (t == 0) {
+      double d2 = D[0][j][j];
+      if (!(d2 > 0.0)) {
+        qlr_set_error(err, QLR_ENOTPD);
+        d2 = 1e-300;
+      }
+      piv = sqrt(d2);
+      D[0][j][j] = piv;
+      D[1][j][j] = D[2][j][j] = D[3][j][j] = 0.0;
+    }
+    __syncthreads();
+    const double inv = 1.0 / piv;
+    for (int k = j + 1 + t; k < b; k += blockDim.x)
+      for (int c = 0; c < 4; ++c) D[c][j][k] *= inv;
+    __syncthreads();
+    for (int e = t; e < CB * CB; e += blockDim.x) {
+      const int i = e % CB, k = e / CB;
+      if (i > j && i <= k && k < b) {
+        Quat<double> a = {D[0][j][i], D[1][j][i], D[2][j][i], D[3][j][i]};
+        Quat<double> bb = {D[0][j][k], D[1][j][k], D[2][j][k], D[3][j][k]};
+        Quat<double> pr = qcmul(a, bb);
+        D[0][i][k] -= pr.w; D[1][i][k] -= pr.x; D[2][i][k] -= pr.y; D[3][i][k] -= pr.z;
+      }
+    }
+    __syncthreads();
+  }
+  // inverse X = D^{-1} by column-oriented back substitution on all right-hand sides at once:
+  // for i = b-1 .. 0: X[i, :] = Y[i, :] / d_i, then Y[0:i, :] -= D[0:i, i] X[i, :]   (Y starts as I)
+  for (int e = t; e < CB * CB; e += blockDim.x) {
+    const int i = e % CB, j = e / CB;
+    X[0][i][j] = (i == j && i < b) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int i = b - 1; i >= 0; --i) {
+    const double dinv = 1.0 / D[0][i][i];
+    if (t < b) {           // row i of X: scale (only columns j >= i are non-zero)
+      const int j = t;
+      X[0][i][j] *= dinv; X[1][i][j] *= dinv; X[2][i][j] *= dinv; X[3][i][j] *= dinv;
+    }
+    __syncthreads();
+    for (int e = t; e < i * b; e += blockDim.x) {   // rows r < i, all columns j
+      const int r = e % i, j = e / i;
+      Quat<double> pr = qmul(Quat<double>{D[0][r][i], D[1][r][i], D[2][r][i], D[3][r][i]},
+                             Quat<double>{X[0][i][j], X[1][i][j], X[2][i][j], X[3][i][j]});
+      X[0][r][j] -= pr.w; X[1][r][j] -= pr.x; X[2][r][j] -= pr.y; X[3][r][j] -= pr.z;
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    for (int c = 0; c < 4; ++c) {
+      R[c * ll + (size_t)(j0 + j) * l + j0 + i] = (i <= j) ? D[c][i][j] : 0.0;
+      Dinv[(size_t)c * b * b + (size_t)j * b + i] = (i <= j) ? X[c][i][j] : 0.0;
+    }
+  }
+}
+
+// Panel rows: R[j0+r, k] = sum_{s <= r} conj(Dinv[s, r]) Wm[j0+s, k], one warp per column k >= j1.
+__global__ void chol_panel_kernel(const double* __restrict__ Wm, double* __restrict__ R, int l, int j0, int b,
+                                  const double* __restrict__ Dinv) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int j1 = j0 + b;
+  const int k = j1 + warp;
+  if (k >= l || lane >= b) return;
+  const size_t ll = (size_t)l * l, bb = (size_t)b * b;
+  const int r = lane;
+  Quat<double> acc = {0, 0, 0, 0};
+  for (int sidx = 0; sidx <= r; ++sidx) {
+    Quat<double> dv = {Dinv[(size_t)r * b + sidx], Dinv[bb + (size_t)r * b + sidx], Dinv[2 * bb + (size_t)r * b + sidx],
+                       Dinv[3 * bb + (size_t)r * b + sidx]};
+    const size_t o = (size_t)k * l + j0 + sidx;
+    Quat<double> w = {Wm[o], Wm[ll + o], Wm[2 * ll + o], Wm[3 * ll + o]};
+    Quat<double> pr = qcmul(dv, w);
+    acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+  }
+  const size_t o = (size_t)k * l + j0 + r;
+  R[o] = acc.w; R[ll + o] = acc.x; R[2 * ll + o] = acc.y; R[3 * ll + o] = acc.z;
+}
+
+// Trailing update of the upper triangle: Wm[i, k] -= sum_{t in panel} conj(R[t, i]) R[t, k].
+__global__ void __launch_bounds__(64) chol_update_kernel(double* __restrict__ Wm, const double* __restrict__ R, int l,
+                                                          int j0, int b, const int2* __restrict__ tiles) {
+  __shared__ double Pi[4][CB][CT];
+  __shared__ double Pk[4][CB][CT];
+  const int j1 = j0 + b;
+  const int2 tl = tiles[blockIdx.x];
+  const int i0 = j1 + tl.x * CT, k0 = j1 + tl.y * CT;
+  const size_t ll = (size_t)l * l;
+  const int t = threadIdx.x;
+  for (int e = t; e < CB * CT; e += blockDim.x) {
+    const int r = e % CB, c0 = e / CB;
+    for (int c = 0; c < 4; ++c) {
+      Pi[c][r][c0] = (r < b && i0 + c0 < l) ? R[c * ll + (size_t)(i0 + c0) * l + j0 + r] : 0.0;
+      Pk[c][r][c0] = (r < b && k0 + c0 < l) ? R[c * ll + (size_t)(k0 + c0) * l + j0 + r] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int ii = t % CT, kk = t / CT;
+  const int i = i0 + ii, k = k0 + kk;
+  if (i >= l || k >= l || i > k) return;
+  Quat<double> acc = {0, 0, 0, 0};
+  for (int r = 0; r < b; ++r) {
+    Quat<double> pr = qcmul(Quat<double>{Pi[0][r][ii], Pi[1][r][ii], Pi[2][r][ii], Pi[3][r][ii]},
+                            Quat<double>{Pk[0][r][kk], Pk[1][r][kk], Pk[2][r][kk], Pk[3][r][kk]});
+    acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+  }
+  const size_t o = (size_t)k * l + i;
+  Wm[o] -= acc.w; Wm[ll + o] -= acc.x; Wm[2 * ll + o] -= acc.y; Wm[3 * ll + o] -= acc.z;
+}
+
+// Inverse of an upper-triangular quaternion matrix, one CTA per column j (back substitution
+// with block-wide dot products).
+__global__ void __launch_bounds__(256) tri_inv_col_kernel(const double* __restrict__ R, double* __restrict__ X, int l) {
+  extern __shared__ double xs[];   // 4 * l
+  __shared__ double red[4][8];
+  const int j = blockIdx.x, t = threadIdx.x, lane = t % 32, warp = t / 32, nw = blockDim.x / 32;
+  const size_t ll = (size_t)l * l;
+  for (int i = t; i < l; i += blockDim.x) xs[i] = xs[l + i] = xs[2 * l + i] = xs[3 * l + i] = 0.0;
+  __syncthreads();
+  if (t == 0) xs[j] = 1.0 / R[(size_t)j * l + j];
+  __syncthreads();
+  for (int i = j - 1; i >= 0; --i) {
+    Quat<double> sacc = {0, 0, 0, 0};
+    for (int q = i + 1 + t; q <= j; q += blockDim.x) {
+      Quat<double> pr = qmul(ld_small(R, l, i, q), Quat<double>{xs[q], xs[l + q], xs[2 * l + q], xs[3 * l + q]});
+      sacc.w += pr.w; sacc.x += pr.x; sacc.y += pr.y; sacc.z += pr.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sacc.w += __shfl_xor_sync(0xffffffffu, sacc.w, o);
+      sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+      sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+      sacc.z += __shfl_xor_sync(0xffffffffu, sacc.z, o);
+    }
+    if (lane == 0) { red[0][warp] = sacc.w; red[1][warp] = sacc.x; red[2][warp] = sacc.y; red[3][warp] = sacc.z; }
+    __syncthreads();
+    if (t == 0) {
+      Quat<double> s = {0, 0, 0, 0};
+      for (int w = 0; w < nw; ++w) { s.w += red[0][w]; s.x += red[1][w]; s.y += red[2][w]; s.z += red[3][w]; }
+      const double ninv = -1.0 / R[(size_t)i * l + i];
+      xs[i] = s.w * ninv; xs[l + i] = s.x * ninv; xs[2 * l + i] = s.y * ninv; xs[3 * l + i] = s.z * ninv;
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < l; i += blockDim.x)
+    for (int c = 0; c < 4; ++c) X[c * ll + (size_t)j * l + i] = xs[(size_t)c * l + i];
+}
+
+
+// Inverse of the upper-triangular R from its diagonal-block inverses (Dinv_I, one per panel of
+// width CB): column j of X = R^{-1} by block back substitution, one CTA per column:
+//   x_J = Dinv_J e_j,   x_I = -Dinv_I (sum_{q in blocks I+1..J} R[I, q] x_q)   for I = J-1 .. 0.
+__global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __restrict__ R, const double* __restrict__ Dinv,
+                                                               double* __restrict__ X, int l) {
+  extern __shared__ double xs[];          // 4 * l
+  __shared__ double tpart[4][CB][16];     // partial sums: row r of the block, 16 q-chunks
+  __shared__ double tsum[4][CB];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const size_t ll = (size_t)l * l;
+  const int J = j / CB;
+  for (int i = t; i < l; i += blockDim.x) xs[i] = xs[l + i] = xs[2 * l + i] = xs[3 * l + i] = 0.0;
+  __syncthreads();
+  {   // x_J = Dinv_J[:, j - J*CB]
+    const int bJ = min(CB, l - J * CB), jj = j - J * CB;
+    const double* D = Dinv + (size_t)J * 4 * CB * CB;
+    const size_t bb = (size_t)bJ * bJ;
+    if (t < bJ && t <= jj) {
+      const size_t o = (size_t)jj * bJ + t;
+      xs[J * CB + t] = D[o]; xs[l + J * CB + t] = D[bb + o]; xs[2 * l + J * CB + t] = D[2 * bb + o];
+      xs[3 * l + J * CB + t] = D[3 * bb + o];
+    }
+  }
+  __syncthreads();
+  for (int I = J - 1; I >= 0; --I) {
+    const int i0 = I * CB, q0 = (I + 1) * CB;
+    // T[r] = sum_{q = q0 .. j} R[i0 + r, q] x_q : thread (r, chunk) with 16 chunks per row
+    {
+      const int r = t % CB, ch = t / CB;   // CB * 16 = 256 threads
+      Quat<double> acc = {0, 0, 0, 0};
+      for (int q = q0 + ch; q <= j; q += 16) {
+        Quat<double> pr = qmul(ld_small(R, l, i0 + r, q), Quat<double>{xs[q], xs[l + q], xs[2 * l + q], xs[3 * l + q]});
+        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+      }
+      tpart[0][r][ch] = acc.w; tpart[1][r][ch] = acc.x; tpart[2][r][ch] = acc.y; tpart[3][r][ch] = acc.z;
+    }
+    __syncthreads();
+    if (t < 4 * CB) {
+      const int c = t / CB, r = t % CB;
+      double sacc = 0.0;
+      for (int ch = 0; ch < 16; ++ch) sacc += tpart[c][r][ch];
+      tsum[c][r] = sacc;
+    }
+    __syncthreads();
+    // x_I = -Dinv_I T   (Dinv_I upper triangular, CB x CB)
+    if (t < CB) {
+      const int r = t;
+      const double* D = Dinv + (size_t)I * 4 * CB * CB;
+      const size_t bb = (size_t)CB * CB;
+      Quat<double> acc = {0, 0, 0, 0};
+      for (int q = r; q < CB; ++q) {
+        const size_t o = (size_t)q * CB + r;
+        Quat<double> pr = qmul(Quat<double>{D[o], D[bb + o], D[2 * bb + o], D[3 * bb + o]},
+                               Quat<double>{tsum[0][q], tsum[1][q], tsum[2][q], tsum[3][q]});
+        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+      }
+      xs[i0 + r] = -acc.w; xs[l + i0 + r] = -acc.x; xs[2 * l + i0 + r] = -acc.y; xs[3 * l + i0 + r] = -acc.z;
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < l; i += blockDim.x)
+    for (int c = 0; c < 4; ++c) X[c * ll + (size_t)j * l + i] = xs[(size_t)c * l + i];
+}
+
 }  // namespace
 
 namespace qlr {
 
+static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
+  const int l = (int)Y.cols;
+  const int64_t m = Y.rows;
+  const int L4 = 4 * l;
+  const int nt = (L4 + WT - 1) / WT;
+  std::vector<int2> tiles;
+  for (int b = 0; b < nt; ++b)
+    for (int a = 0; a <= b; ++a) tiles.push_back(make_int2(a, b));
+  const int target = 3 * (ctx->num_sms > 0 ? ctx->num_sms : 148);
+  int64_t chunks = (target + (int64_t)tiles.size() - 1) / (int64_t)tiles.size();
+  chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (m + 63) / 64));
+  chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, ((int64_t)64 << 20) / ((int64_t)8 * L4 * L4)));
+  int64_t rpc = ((m + chunks - 1) / chunks + WR - 1) / WR * WR;
+  chunks = (m + rpc - 1) / rpc;
+  size_t mark = ws.off;
+  int2* d_tiles = ws.take<int2>(tiles.size());
+  double* part = ws.take<double>((size_t)chunks * L4 * L4);
+  if (!ws.ok) return QLR_ENOMEM;
+  QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+  {
+    KTimer kt(ctx, QLR_KID_GRAM);
+    dim3 grid((unsigned)tiles.size(), (unsigned)chunks);
+    gram_df_partial_kernel<<<grid, 256, 0, ctx->stream>>>(
+        static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
+        static_cast<const float*>(Y.plane[3]), m, l, Y.ld, rpc, d_tiles, part);
+    QLR_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    KTimer kt(ctx, QLR_KID_GRAM);
+    const int64_t tot = (int64_t)l * l;
+    gram_df_combine_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(part, (int)chunks, l, G);
+    QLR_CUDA_TRY(cudaGetLastError());
+  }
+  ws.off = mark;
+  return QLR_OK;
+}
+
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
+  if (Y.dtype == QLR_F32 && Y.cols > 0 && Y.rows > 0) return gram_df32(ctx, Y, G, ws);
   const int l = (int)Y.cols;
   const int64_t m = Y.rows;
   if (l == 0) return QLR_OK;
@@ -255,21 +559,56 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   return QLR_OK;
 }
 
-int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef) {
+int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsArena& ws, double* Dinv_all) {
   if (l == 0) return QLR_OK;
+  const size_t ll4 = (size_t)4 * l * l;
+  size_t mark = ws.off;
+  double* Wm = ws.take<double>(ll4);
+  const int npan = (l + CB - 1) / CB;
+  if (Dinv_all == nullptr) Dinv_all = ws.take<double>((size_t)npan * 4 * CB * CB);
+  const int nbt = (l + CT - 1) / CT;
+  std::vector<int2> all;
+  for (int b2 = 0; b2 < nbt; ++b2)
+    for (int a2 = 0; a2 <= b2; ++a2) all.push_back(make_int2(a2, b2));
+  int2* d_tiles = ws.take<int2>(all.size());
+  if (!ws.ok) return QLR_ENOMEM;
+  QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
   KTimer kt(ctx, QLR_KID_CHOL);
-  chol_kernel<<<1, 1024, 0, ctx->stream>>>(G, R, l, shift_coef, ctx->d_err);
+  chol_init_kernel<<<std::max(1, std::min(64, (int)((ll4 / 4 + 255) / 256))), 256, 0, ctx->stream>>>(G, Wm, R, l, shift_coef);
   QLR_CUDA_TRY(cudaGetLastError());
+  for (int j0 = 0; j0 < l; j0 += CB) {
+    const int b = std::min(CB, l - j0);
+    double* Dinv = Dinv_all + (size_t)(j0 / CB) * 4 * CB * CB;
+    chol_diag_kernel<<<1, 256, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, ctx->d_err);
+    QLR_CUDA_TRY(cudaGetLastError());
+    const int rem = l - j0 - b;
+    if (rem <= 0) break;
+    chol_panel_kernel<<<(rem * 32 + 127) / 128, 128, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv);
+    QLR_CUDA_TRY(cudaGetLastError());
+    // tiles of the trailing triangle (tile coordinates relative to j0 + b); the tile list is the
+    // prefix of the full upper-tile list with both coordinates < ceil(rem / CT)
+    const int nt = (rem + CT - 1) / CT;
+    const int ntiles = nt * (nt + 1) / 2;
+    chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, d_tiles);
+    QLR_CUDA_TRY(cudaGetLastError());
+  }
+  ws.off = mark;
   return QLR_OK;
 }
 
-int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv) {
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all) {
   if (l == 0) return QLR_OK;
-  if (l > TI_MAXL) return QLR_EUNSUPPORTED;
-  size_t smem = (size_t)TI_WARPS * 4 * l * sizeof(double);
-  if (smem > 48 * 1024) QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   KTimer kt(ctx, QLR_KID_TRIINV);
-  tri_inv_kernel<<<(l + TI_WARPS - 1) / TI_WARPS, 32 * TI_WARPS, smem, ctx->stream>>>(R, Rinv, l);
+  const size_t smem = (size_t)4 * l * sizeof(double);
+  if (Dinv_all) {
+    if (smem > 48 * 1024)
+      QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tri_inv_blocked_kernel<<<l, 256, smem, ctx->stream>>>(R, Dinv_all, Rinv, l);
+  } else {
+    if (smem > 48 * 1024)
+      QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tri_inv_col_kernel<<<l, 256, smem, ctx->stream>>>(R, Rinv, l);
+  }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
@@ -311,6 +650,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
   double* P1 = ws.take<double>(ll4);
   double* P2 = ws.take<double>(ll4);
   double* Rinv = ws.take<double>(ll4);
+  double* Dinv_all = ws.take<double>((size_t)((l + CB - 1) / CB) * 4 * CB * CB);
   char* tbuf = ws.take<char>((size_t)4 * m * l * esz);
   if (!ws.ok) return QLR_ENOMEM;
   qlr_qmat T = Y;
@@ -333,8 +673,8 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     qlr_qmat& dst = const_cast<qlr_qmat&>(*seq[s + 1]);
     double* Rcur = (s == 0) ? Rprod : Rs;
     QLR_TRY(gram(ctx, src, G, ws));
-    QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0));
-    QLR_TRY(tri_inv(ctx, l, Rcur, Rinv));
+    QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all));
+    QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
     QLR_TRY(apply_rinv(ctx, src, Rinv, dst));
     if (s > 0) {   // R_total <- R_s * R_total
       QLR_TRY(small_matmul(ctx, l, Rs, Rprod, Rnext));

@@ -161,14 +161,15 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 
 // orthonormalisation pieces (orth.cu)
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
-int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel);
-int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv);
+int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr);
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr);
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
 
 // core QSVD (core_svd.cu)
 int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec,
               WsArena& ws);
+size_t core_tsvd_ws(int l);
 
 // utilities (util.cu)
 int convert_qmat(qlr_ctx* ctx, const qlr_qmat& src, qlr_qmat& dst);  // elementwise dtype change
