@@ -223,6 +223,30 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
 int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start,
                       int iters, double* out);
 
+/*
+ * qlr_qsketch_noalloc -- the tensor-core sketch product of qlr_qsketch (same op, operands, layouts
+ * and results, compute QLR_COMPUTE_TF32, QLR_COMPUTE_TF32X3 or QLR_COMPUTE_BF16) for callers that
+ * cannot allocate device memory.  The paper has no counterpart; this is a deployment convenience.
+ * Who cannot allocate: cudaMalloc may synchronise the whole device and takes a driver-wide lock,
+ * so latency-critical serving loops keep it out of their steady state, and some host applications
+ * give all device memory to their own pool allocator and forbid other allocations; neither can
+ * create a qlr context (which allocates its error word and workspace).
+ * No context: the call runs on `stream` (a cudaStream_t, NULL = legacy default stream) of the
+ * current device and takes all scratch memory from one fixed 32 MiB device array compiled into the
+ * library (every GPU that loads it keeps those 32 MiB until the process exits).  It calls no
+ * cudaMalloc / cudaFree.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make the first call on each device before any stream capture.
+ * The array is shared by all calls on a device and keeps the previous call's contents; each call
+ * clears the parts that must start at zero.  Calls that overlap on the GPU (other streams or
+ * threads) race on the array: serialise them.  `err` (device int, may be NULL) receives
+ * QLR_ETIMEOUT if a bounded device wait gives up.
+ * Errors: QLR_EINVAL / QLR_ESHAPE as qlr_qsketch; QLR_EUNSUPPORTED for a row pitch of A that is not
+ * a multiple of 16 bytes; QLR_ENOMEM when the operands need more scratch than the 32 MiB array
+ * (the staged thin operand alone needs 32 bytes per quaternion entry of X for TF32X3, 8 for BF16).
+ */
+int qlr_qsketch_noalloc(void* stream, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute,
+                        int* err);
+
 #ifdef __cplusplus
 }
 #endif

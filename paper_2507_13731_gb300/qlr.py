@@ -85,6 +85,7 @@ def lib():
             "qlr_set_timing": (I, [P, I]),
             "qlr_reset_stats": (I, [P]),
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
+            "qlr_qsketch_noalloc": (I, [P, I, Q, Q, Q, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -206,6 +207,18 @@ def workspace_size(m, n, k, p, passes, algo=ALG2, compute=COMPUTE_AUTO) -> int:
 def qsketch(ctx: Context, op: int, A: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, compute: int = COMPUTE_AUTO):
     a, x, y = _A(A), _T(X), _T(Y)
     _check(lib().qlr_qsketch(ctx.h, op, ctypes.byref(a), ctypes.byref(x), ctypes.byref(y), compute), "qlr_qsketch")
+    return Y
+
+
+def qsketch_noalloc(op: int, A: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, compute: int,
+                    stream: Optional[torch.cuda.Stream] = None, err: Optional[torch.Tensor] = None):
+    """qlr_qsketch_noalloc: the tensor-core sketch product without a context and without any
+    device allocation (scratch comes from the library's fixed device array); see include/qlr.h."""
+    a, x, y = _A(A), _T(X), _T(Y)
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    ep = ctypes.c_void_p(err.data_ptr()) if err is not None else ctypes.c_void_p()
+    _check(lib().qlr_qsketch_noalloc(ctypes.c_void_p(s.cuda_stream), op, ctypes.byref(a), ctypes.byref(x),
+                                     ctypes.byref(y), compute, ep), "qlr_qsketch_noalloc")
     return Y
 
 
