@@ -59,7 +59,7 @@ size_t gram_ws_bound(int64_t l) {
 }
 
 size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
-  return (size_t)5 * 32 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 8 * 256;
+  return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 16 * 256;
 }
 
 size_t tsvd_ws_bound(int64_t l) { return qlr::core_tsvd_ws((int)l) + 16384; }

@@ -19,6 +19,8 @@
 // FP64 step evaluates every kept singular value as the two-sided Rayleigh quotient
 // sigma = Re(u^H R v) / (|u| |v|) from the FP64 R, whose error is second order in the vectors'.
 #include <cooperative_groups.h>
+#include <cstdio>
+#include <cstdlib>
 
 #include "qlr_internal.h"
 
@@ -503,6 +505,12 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     }
   }
   QLR_CUDA_TRY(cudaGetLastError());
+  if (std::getenv("QLR_DEBUG_JACOBI")) {   // diagnostics only: synchronises the stream
+    int hs = -1;
+    cudaMemcpyAsync(&hs, sweeps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    std::fprintf(stderr, "qlr jacobi: l=%d sweeps=%d %s\n", l, hs, l >= JBLOCK_MIN_L ? "cluster" : "single-CTA");
+  }
   { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); }
   QLR_CUDA_TRY(cudaGetLastError());
   const size_t rsm = (size_t)8 * l * sizeof(double);

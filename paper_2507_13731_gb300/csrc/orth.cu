@@ -187,14 +187,23 @@ __global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __res
     }
 }
 
-__device__ __forceinline__ double w_at(const double* __restrict__ part, int nchunks, int L4, int I, int J) {
-  if ((I / WT) > (J / WT)) { int t = I; I = J; J = t; }     // only upper tiles were computed
-  double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * L4 * L4 + (size_t)J * L4 + I];
-  return s;
+// Sum the chunk partials of W (upper tiles) in a fixed order, coalesced, into part[0].
+__global__ void gram_df_reduce_kernel(double* __restrict__ part, int nchunks, int L4) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L4 * L4) return;
+  const int I = (int)(e % L4), J = (int)(e / L4);
+  if ((I / WT) > (J / WT)) return;
+  double s = part[e];
+  for (int c = 1; c < nchunks; ++c) s += part[(size_t)c * L4 * L4 + e];
+  part[e] = s;
 }
 
-__global__ void gram_df_combine_kernel(const double* __restrict__ part, int nchunks, int l, double* __restrict__ G) {
+__device__ __forceinline__ double w_at(const double* __restrict__ W, int L4, int I, int J) {
+  if ((I / WT) > (J / WT)) { int t = I; I = J; J = t; }     // only upper tiles were computed
+  return W[(size_t)J * L4 + I];
+}
+
+__global__ void gram_df_combine_kernel(const double* __restrict__ part, int l, double* __restrict__ G) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)l * l) return;
   const int i = (int)(idx % l), j = (int)(idx / l);
@@ -204,7 +213,7 @@ __global__ void gram_df_combine_kernel(const double* __restrict__ part, int nchu
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int d = 0; d < 4; ++d) w[c][d] = w_at(part, nchunks, L4, c * l + i, d * l + j);
+    for (int d = 0; d < 4; ++d) w[c][d] = w_at(part, L4, c * l + i, d * l + j);
   Quat<double> g;
   g.w = w[0][0] + w[1][1] + w[2][2] + w[3][3];
   g.x = w[0][1] - w[1][0] - w[2][3] + w[3][2];
@@ -226,8 +235,9 @@ constexpr int CB = 16;      // panel width
 constexpr int CT = 8;       // trailing-update tile
 
 __global__ void chol_init_kernel(const double* __restrict__ G, double* __restrict__ Wm, double* __restrict__ R, int l,
-                                 double shift_coef) {
+                                 double shift_coef, const int* run_if) {
   __shared__ double s_tr;
+  if (run_if && *run_if == 0) return;
   const size_t ll = (size_t)l * l;
   if (threadIdx.x == 0) {
     double tr = 0.0;
@@ -247,7 +257,8 @@ __global__ void chol_init_kernel(const double* __restrict__ G, double* __restric
 // Factor the diagonal block [j0, j0+b) of Wm into R (upper, real positive diagonal) and write its
 // inverse into Dinv (b x b x 4, column-major).
 __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm, double* __restrict__ R, int l, int j0,
-                                                         int b, double* __restrict__ Dinv, int* err) {
+                                                         int b, double* __restrict__ Dinv, int* err, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   __shared__ double D[4][CB][CB];
   __shared__ double X[4][CB][CB];
   __shared__ double piv;
@@ -321,7 +332,8 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm,
 
 // Panel rows: R[j0+r, k] = sum_{s <= r} conj(Dinv[s, r]) Wm[j0+s, k], one warp per column k >= j1.
 __global__ void chol_panel_kernel(const double* __restrict__ Wm, double* __restrict__ R, int l, int j0, int b,
-                                  const double* __restrict__ Dinv) {
+                                  const double* __restrict__ Dinv, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   const int j1 = j0 + b;
   const int k = j1 + warp;
@@ -343,7 +355,9 @@ __global__ void chol_panel_kernel(const double* __restrict__ Wm, double* __restr
 
 // Trailing update of the upper triangle: Wm[i, k] -= sum_{t in panel} conj(R[t, i]) R[t, k].
 __global__ void __launch_bounds__(64) chol_update_kernel(double* __restrict__ Wm, const double* __restrict__ R, int l,
-                                                          int j0, int b, const int2* __restrict__ tiles) {
+                                                          int j0, int b, const int2* __restrict__ tiles,
+                                                          const int* run_if) {
+  if (run_if && *run_if == 0) return;
   __shared__ double Pi[4][CB][CT];
   __shared__ double Pk[4][CB][CT];
   const int j1 = j0 + b;
@@ -415,7 +429,8 @@ __global__ void __launch_bounds__(256) tri_inv_col_kernel(const double* __restri
 // width CB): column j of X = R^{-1} by block back substitution, one CTA per column:
 //   x_J = Dinv_J e_j,   x_I = -Dinv_I (sum_{q in blocks I+1..J} R[I, q] x_q)   for I = J-1 .. 0.
 __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __restrict__ R, const double* __restrict__ Dinv,
-                                                               double* __restrict__ X, int l) {
+                                                               double* __restrict__ X, int l, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   extern __shared__ double xs[];          // 4 * l
   __shared__ double tpart[4][CB][16];     // partial sums: row r of the block, 16 q-chunks
   __shared__ double tsum[4][CB];
@@ -475,6 +490,104 @@ __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __re
     for (int c = 0; c < 4; ++c) X[c * ll + (size_t)j * l + i] = xs[(size_t)c * l + i];
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Second CholeskyQR step by series.  After the first step Q' = Y R1^{-1} is orthonormal up to
+// E = Q'^H Q' - I with |E| of order u32 kappa(Y).  The Cholesky factor of I + E is I + F with F
+// upper triangular and real diagonal; (I + F)^H (I + F) = I + E is equivalent to
+// F = Phi(E - F^H F), Phi(X) = strict upper part of X plus half its (real) diagonal, a fixed point
+// reached by iterating from F = Phi(E) (the error shrinks like |E|^(n+1)).  The inverse is
+// (I + F)^{-1} = I - F + F^2 - ..., evaluated as X <- I - F X.  Each step is a triangular product
+// spread over all SMs in FP64 -- no serial pivots.  The init kernel raises `use_chol` when
+// l * max|E_ij| exceeds SERIES_MAX; the blocked Cholesky kernels then run instead (they are
+// predicated on that flag, so no host synchronisation is needed).
+constexpr double SERIES_MAX = 5e-3;
+constexpr int SERIES_ITERS = 6, NEUMANN_ITERS = 7, SPLIT = 4;
+
+__global__ void series_init_kernel(const double* __restrict__ G, double* __restrict__ E, double* __restrict__ F, int l,
+                                   unsigned long long* __restrict__ emax_bits) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)l * l) return;
+  const int i = (int)(idx % l), j = (int)(idx / l);
+  Quat<double> e = ld_small(G, l, i, j);
+  if (i == j) e.w -= 1.0;
+  st_small(E, l, i, j, e);
+  Quat<double> f = {0, 0, 0, 0};
+  if (i < j) f = e;
+  else if (i == j) f.w = 0.5 * e.w;
+  st_small(F, l, i, j, f);
+  const double mx = fmax(fmax(fabs(e.w), fabs(e.x)), fmax(fabs(e.y), fabs(e.z)));
+  atomicMax(emax_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void series_decide_kernel(const unsigned long long* __restrict__ emax_bits, int l, int* use_chol) {
+  const double emax = __longlong_as_double((long long)*emax_bits);
+  *use_chol = (!(emax * l <= SERIES_MAX)) ? 1 : 0;
+}
+
+// out(i, j) for i <= j with SPLIT threads per entry:
+//   mode 0 (series):  Phi(E - F^H F)(i, j),  (F^H F)_ij = sum_{t <= i} conj(F_ti) F_tj
+//   mode 1 (Neumann): delta_ij - (F X)_ij,     (F X)_ij  = sum_{i <= t <= j} F_it X_tj
+__global__ void __launch_bounds__(128) series_step_kernel(const double* __restrict__ E, const double* __restrict__ F,
+                                                           const double* __restrict__ X, double* __restrict__ out, int l,
+                                                           int mode, const int2* __restrict__ entries, int nentries) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ent = gt / SPLIT;
+  const int part = (int)(gt % SPLIT);
+  const bool valid = ent < nentries;
+  Quat<double> acc = {0, 0, 0, 0};
+  int i = 0, j = 0;
+  if (valid) {
+    i = entries[ent].x;
+    j = entries[ent].y;
+    if (mode == 0) {
+      for (int t = part; t <= i; t += SPLIT) {
+        Quat<double> pr = qcmul(ld_small(F, l, t, i), ld_small(F, l, t, j));
+        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+      }
+    } else {
+      for (int t = i + part; t <= j; t += SPLIT) {
+        Quat<double> pr = qmul(ld_small(F, l, i, t), ld_small(X, l, t, j));
+        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = SPLIT / 2; o > 0; o >>= 1) {
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+  }
+  if (!valid || part != 0) return;
+  Quat<double> r;
+  if (mode == 0) {
+    Quat<double> e = ld_small(E, l, i, j);
+    if (i < j) r = {e.w - acc.w, e.x - acc.x, e.y - acc.y, e.z - acc.z};
+    else r = {0.5 * (e.w - acc.w), 0.0, 0.0, 0.0};
+  } else {
+    r = {(i == j ? 1.0 : 0.0) - acc.w, -acc.x, -acc.y, -acc.z};
+  }
+  st_small(out, l, i, j, r);
+}
+
+// R2 = I + F (full matrix written; lower part zero)
+__global__ void series_form_kernel(const double* __restrict__ F, double* __restrict__ R2, int l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)l * l) return;
+  const int i = (int)(idx % l), j = (int)(idx / l);
+  Quat<double> f = (i <= j) ? ld_small(F, l, i, j) : Quat<double>{0, 0, 0, 0};
+  if (i == j) f.w += 1.0;
+  st_small(R2, l, i, j, f);
+}
+
+__global__ void fill_identity_kernel(double* __restrict__ X, int l) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)l * l) return;
+  const int i = (int)(idx % l), j = (int)(idx / l);
+  st_small(X, l, i, j, {i == j ? 1.0 : 0.0, 0.0, 0.0, 0.0});
+}
+
 }  // namespace
 
 namespace qlr {
@@ -508,8 +621,10 @@ static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   }
   {
     KTimer kt(ctx, QLR_KID_GRAM);
+    const int64_t tw = (int64_t)L4 * L4;
+    if (chunks > 1) gram_df_reduce_kernel<<<(unsigned)((tw + 255) / 256), 256, 0, ctx->stream>>>(part, (int)chunks, L4);
     const int64_t tot = (int64_t)l * l;
-    gram_df_combine_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(part, (int)chunks, l, G);
+    gram_df_combine_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(part, l, G);
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
@@ -559,7 +674,8 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   return QLR_OK;
 }
 
-int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsArena& ws, double* Dinv_all) {
+int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsArena& ws, double* Dinv_all,
+         const int* run_if) {
   if (l == 0) return QLR_OK;
   const size_t ll4 = (size_t)4 * l * l;
   size_t mark = ws.off;
@@ -574,36 +690,36 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
   if (!ws.ok) return QLR_ENOMEM;
   QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
   KTimer kt(ctx, QLR_KID_CHOL);
-  chol_init_kernel<<<std::max(1, std::min(64, (int)((ll4 / 4 + 255) / 256))), 256, 0, ctx->stream>>>(G, Wm, R, l, shift_coef);
+  chol_init_kernel<<<std::max(1, std::min(64, (int)((ll4 / 4 + 255) / 256))), 256, 0, ctx->stream>>>(G, Wm, R, l, shift_coef, run_if);
   QLR_CUDA_TRY(cudaGetLastError());
   for (int j0 = 0; j0 < l; j0 += CB) {
     const int b = std::min(CB, l - j0);
     double* Dinv = Dinv_all + (size_t)(j0 / CB) * 4 * CB * CB;
-    chol_diag_kernel<<<1, 256, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, ctx->d_err);
+    chol_diag_kernel<<<1, 256, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, ctx->d_err, run_if);
     QLR_CUDA_TRY(cudaGetLastError());
     const int rem = l - j0 - b;
     if (rem <= 0) break;
-    chol_panel_kernel<<<(rem * 32 + 127) / 128, 128, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv);
+    chol_panel_kernel<<<(rem * 32 + 127) / 128, 128, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, run_if);
     QLR_CUDA_TRY(cudaGetLastError());
     // tiles of the trailing triangle (tile coordinates relative to j0 + b); the tile list is the
     // prefix of the full upper-tile list with both coordinates < ceil(rem / CT)
     const int nt = (rem + CT - 1) / CT;
     const int ntiles = nt * (nt + 1) / 2;
-    chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, d_tiles);
+    chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, d_tiles, run_if);
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
   return QLR_OK;
 }
 
-int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all) {
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all, const int* run_if) {
   if (l == 0) return QLR_OK;
   KTimer kt(ctx, QLR_KID_TRIINV);
   const size_t smem = (size_t)4 * l * sizeof(double);
   if (Dinv_all) {
     if (smem > 48 * 1024)
       QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tri_inv_blocked_kernel<<<l, 256, smem, ctx->stream>>>(R, Dinv_all, Rinv, l);
+    tri_inv_blocked_kernel<<<l, 256, smem, ctx->stream>>>(R, Dinv_all, Rinv, l, run_if);
   } else {
     if (smem > 48 * 1024)
       QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -636,6 +752,53 @@ static int apply_rinv(qlr_ctx* ctx, const qlr_qmat& Y, const double* Rinv, qlr_q
   g.alpha = 1.0; g.beta = 0.0;
   g.acc64 = (Y.dtype == QLR_F64);
   return gemm_simt(ctx, g);
+}
+
+// Cholesky factor R2 = I + F of a near-identity Gram matrix G and its inverse by series; sets
+// *use_chol_out to a device flag that is non-zero when G is too far from I for the series.
+static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, double* R2inv, WsArena& ws,
+                         int** use_chol_out) {
+  const size_t ll4 = (size_t)4 * l * l;
+  double* E = ws.take<double>(ll4);
+  double* Fa = ws.take<double>(ll4);
+  double* Fb = ws.take<double>(ll4);
+  double* Xa = ws.take<double>(ll4);
+  double* Xb = ws.take<double>(ll4);
+  unsigned long long* emax = ws.take<unsigned long long>(1);
+  int* use_chol = ws.take<int>(1);
+  const int nent = l * (l + 1) / 2;
+  int2* ent = ws.take<int2>(nent);
+  if (!ws.ok) return QLR_ENOMEM;
+  std::vector<int2> he;
+  he.reserve(nent);
+  for (int j = 0; j < l; ++j)
+    for (int i = 0; i <= j; ++i) he.push_back(make_int2(i, j));
+  QLR_CUDA_TRY(cudaMemcpyAsync(ent, he.data(), he.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+  QLR_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), ctx->stream));
+  KTimer kt(ctx, QLR_KID_CHOL);
+  const int64_t tot = (int64_t)l * l;
+  const unsigned gsq = (unsigned)((tot + 127) / 128);
+  const unsigned gst = (unsigned)(((int64_t)nent * SPLIT + 127) / 128);
+  series_init_kernel<<<gsq, 128, 0, ctx->stream>>>(G, E, Fa, l, emax);
+  series_decide_kernel<<<1, 1, 0, ctx->stream>>>(emax, l, use_chol);
+  double* Fc = Fa;
+  double* Fn = Fb;
+  for (int it = 0; it < SERIES_ITERS; ++it) {
+    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, ent, nent);
+    std::swap(Fc, Fn);
+  }
+  series_form_kernel<<<gsq, 128, 0, ctx->stream>>>(Fc, R2, l);
+  fill_identity_kernel<<<gsq, 128, 0, ctx->stream>>>(Xa, l);
+  double* Xc = Xa;
+  double* Xn = Xb;
+  for (int it = 0; it < NEUMANN_ITERS; ++it) {
+    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, (it == NEUMANN_ITERS - 1) ? R2inv : Xn, l, 1, ent,
+                                                   nent);
+    std::swap(Xc, Xn);
+  }
+  QLR_CUDA_TRY(cudaGetLastError());
+  *use_chol_out = use_chol;
+  return QLR_OK;
 }
 
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws) {
@@ -673,8 +836,15 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     qlr_qmat& dst = const_cast<qlr_qmat&>(*seq[s + 1]);
     double* Rcur = (s == 0) ? Rprod : Rs;
     QLR_TRY(gram(ctx, src, G, ws));
-    QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all));
-    QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
+    if (s == 1 && orth == QLR_ORTH_CHOLQR2) {
+      int* use_chol = nullptr;
+      QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol));
+      QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol));     // only if the series test failed
+      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, use_chol));
+    } else {
+      QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all));
+      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
+    }
     QLR_TRY(apply_rinv(ctx, src, Rinv, dst));
     if (s > 0) {   // R_total <- R_s * R_total
       QLR_TRY(small_matmul(ctx, l, Rs, Rprod, Rnext));

@@ -161,8 +161,10 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 
 // orthonormalisation pieces (orth.cu)
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
-int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr);
-int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr);
+int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
+         const int* run_if = nullptr);
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr,
+            const int* run_if = nullptr);
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
 

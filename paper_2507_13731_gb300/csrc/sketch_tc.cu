@@ -417,14 +417,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
         __threadfence();
         if (grow < p.M) {
           for (int d = 0; d < 4; ++d)
-            for (int jc = 0; jc < nb; ++jc) {
-              const int j = j0 + jc;
-              if (j >= p.l) break;
-              float s = 0.f;
-              for (int sp = 0; sp < p.nsplit; ++sp)
-                s += __ldcg(&p.part[((size_t)sp * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
-                                    (size_t)jc * TBM + row]);
-              p.y[d][grow + (int64_t)j * p.ldy] = s;
+            for (int jc0 = 0; jc0 < nb; jc0 += 16) {
+              float acc[16];
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
+              for (int sp = 0; sp < p.nsplit; ++sp) {
+                const float* P = p.part + ((size_t)sp * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
+                                 (size_t)jc0 * TBM + row;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) acc[jj] += __ldcg(P + (size_t)jj * TBM);   // 16 loads in flight
+              }
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int j = j0 + jc0 + jj;
+                if (jc0 + jj < nb && j < p.l) p.y[d][grow + (int64_t)j * p.ldy] = acc[jj];
+              }
             }
         }
         if (threadIdx.x == 128) p.counters[tile] = 0u;

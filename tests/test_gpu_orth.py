@@ -58,8 +58,11 @@ def test_chol_matches_unique_qr_factor(ctx, l):
 
 @pytest.mark.parametrize("m,l,cond,dt,orth", [(500, 23, 1e2, "f64", 0), (2000, 110, 1e3, "f32", 0),
                                              (300, 40, 1e10, "f64", 1), (1500, 60, 1e6, "f32", 1),
-                                             (64, 64, 10.0, "f64", 0), (17, 3, 5.0, "f32", 0)])
+                                             (64, 64, 10.0, "f64", 0), (17, 3, 5.0, "f32", 0),
+                                             (2000, 40, 3e4, "f32", 0), (3000, 110, 3e2, "f32", 0)])
 def test_cholqr_parity(ctx, m, l, cond, dt, orth):
+    """CholeskyQR2's second step uses the series factorisation when Q'^H Q' is close to I and the
+    blocked Cholesky otherwise (the 3e4-conditioned FP32 case); both must give the unique QR."""
     from paper_2507_13731_gb300 import qlr
     Y = _conditioned(m, l, cond, 11)
     Yd = dev_thin(Y, dt)
