@@ -191,6 +191,12 @@ constexpr int JP = 8;                 // cluster size
 constexpr int JB_THREADS = 256;
 constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4)
 
+// Stage index of local round lr in block round br: block round 0 runs the full round-robin over
+// the 2 bw columns of its block pair (U - 1 rounds, covering the pairs inside each block); later
+// block rounds only pair columns across the two blocks (bw rounds: a_i with b_{(i + lr) mod bw}).
+__host__ __device__ __forceinline__ int jb_stages_per_sweep(int bw) { return (2 * bw - 1) + (2 * JP - 2) * bw; }
+__host__ __device__ __forceinline__ int jb_stage(int br, int lr, int bw) { return br == 0 ? lr : (2 * bw - 1) + (br - 1) * bw + lr; }
+
 template <class T>
 __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
                                                                    T* __restrict__ W, int max_sweeps, T tol,
@@ -198,14 +204,14 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
                                                                    int* __restrict__ sweeps_out, T* __restrict__ sig_out,
                                                                    int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);          // [4][l][2 bw]  (plane, row, local column)
+  T* S = reinterpret_cast<T*>(smem_raw);          // [4][2 bw][l]: plane, local column, row
   cg::cluster_group cluster = cg::this_cluster();
   const int p = (int)cluster.block_rank();
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JB_THREADS / 32;
   const size_t ll = (size_t)l * l;
   const int NB = 2 * JP;
-  const int U = 2 * bw;                           // local columns
-  const int stages_per_sweep = (NB - 1) * (U - 1);
+  const int U = 2 * bw;
+  const int sps = jb_stages_per_sweep(bw);
   const int stage_cap = JP * bw;
   for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)R[e];
   if (p == 0)
@@ -216,42 +222,44 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
   bool converged = (l < 2);
   __shared__ int s_rot;
   __shared__ int gcol[64];
+  auto col = [&](int c, int lc) { return S + ((size_t)c * U + lc) * l; };
   for (; sweep < max_sweeps && !converged; ++sweep) {
     if (t == 0) s_rot = 0;
     for (int br = 0; br < NB - 1; ++br) {
       int ba, bb;
       rr_pair(NB, br, p, ba, bb);
-      // global column of each local slot (or -1)
       if (t < U) {
         const int blk = (t < bw) ? ba : bb, off = (t < bw) ? t : t - bw;
         const int g = blk * bw + off;
         gcol[t] = (g < l) ? g : -1;
       }
       __syncthreads();
-      for (int e = t; e < 4 * l * U; e += JB_THREADS) {
-        const int c = e / (l * U), rem = e % (l * U), row = rem / U, lc = rem % U;
+      for (int e = t; e < 4 * U * l; e += JB_THREADS) {
+        const int c = e / (U * l), rem = e % (U * l), lc = rem / l, row = rem % l;
         const int g = gcol[lc];
         S[e] = (g >= 0) ? W[c * ll + (size_t)g * l + row] : (T)0;
       }
       __syncthreads();
-      for (int lr = 0; lr < U - 1; ++lr) {
-        T* lg_stage = rlog + ((size_t)sweep * stages_per_sweep + (size_t)br * (U - 1) + lr) * stage_cap * REC;
+      const int nlr = (br == 0) ? U - 1 : bw;
+      for (int lr = 0; lr < nlr; ++lr) {
+        T* lg_stage = rlog + ((size_t)sweep * sps + jb_stage(br, lr, bw)) * stage_cap * REC;
         for (int pi = warp; pi < bw; pi += nwarps) {
           int a, b;
-          rr_pair(U, lr, pi, a, b);
+          if (br == 0) rr_pair(U, lr, pi, a, b);
+          else { a = pi; b = bw + (pi + lr) % bw; }
           T* lg = lg_stage + ((size_t)p * bw + pi) * REC;
           const int ga = gcol[a], gb = gcol[b];
           if (ga < 0 || gb < 0) {
             if (lane == 0) { lg[0] = (T)-1; lg[1] = (T)-1; lg[2] = (T)1; lg[3] = (T)0; }
             continue;
           }
+          const T* a0 = col(0, a); const T* a1 = col(1, a); const T* a2 = col(2, a); const T* a3 = col(3, a);
+          const T* b0 = col(0, b); const T* b1 = col(1, b); const T* b2 = col(2, b); const T* b3 = col(3, b);
           T aa = 0, bb2 = 0;
           Quat<T> g = {0, 0, 0, 0};
           for (int i = lane; i < l; i += 32) {
-            Quat<T> wp = {S[((size_t)0 * l + i) * U + a], S[((size_t)1 * l + i) * U + a], S[((size_t)2 * l + i) * U + a],
-                          S[((size_t)3 * l + i) * U + a]};
-            Quat<T> wq = {S[((size_t)0 * l + i) * U + b], S[((size_t)1 * l + i) * U + b], S[((size_t)2 * l + i) * U + b],
-                          S[((size_t)3 * l + i) * U + b]};
+            Quat<T> wp = {a0[i], a1[i], a2[i], a3[i]};
+            Quat<T> wq = {b0[i], b1[i], b2[i], b3[i]};
             aa += qnorm2(wp);
             bb2 += qnorm2(wq);
             Quat<T> pr = qcmul(wp, wq);
@@ -265,29 +273,30 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
             continue;
           }
           if (lane == 0) s_rot = 1;
-          const Quat<T> mu = {g.w / gn, g.x / gn, g.y / gn, g.z / gn};
-          const T zeta = (bb2 - aa) / (2 * gn);
+          const T ign = (T)1 / gn;
+          const Quat<T> mu = {g.w * ign, g.x * ign, g.y * ign, g.z * ign};
+          const T zeta = (bb2 - aa) * ((T)0.5 * ign);
           const T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
           const T c = (T)1 / sqrt((T)1 + tt * tt), sn = c * tt;
           if (lane == 0) {
             lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = c; lg[3] = sn;
             lg[4] = mu.w; lg[5] = mu.x; lg[6] = mu.y; lg[7] = mu.z;
           }
+          T* A0 = col(0, a); T* A1 = col(1, a); T* A2 = col(2, a); T* A3 = col(3, a);
+          T* B0 = col(0, b); T* B1 = col(1, b); T* B2 = col(2, b); T* B3 = col(3, b);
           for (int i = lane; i < l; i += 32) {
-            const size_t o0 = ((size_t)0 * l + i) * U, o1 = ((size_t)1 * l + i) * U, o2 = ((size_t)2 * l + i) * U,
-                         o3 = ((size_t)3 * l + i) * U;
-            Quat<T> wp = {S[o0 + a], S[o1 + a], S[o2 + a], S[o3 + a]};
-            Quat<T> wq = qmulc(Quat<T>{S[o0 + b], S[o1 + b], S[o2 + b], S[o3 + b]}, mu);
-            S[o0 + a] = c * wp.w - sn * wq.w; S[o1 + a] = c * wp.x - sn * wq.x;
-            S[o2 + a] = c * wp.y - sn * wq.y; S[o3 + a] = c * wp.z - sn * wq.z;
-            S[o0 + b] = sn * wp.w + c * wq.w; S[o1 + b] = sn * wp.x + c * wq.x;
-            S[o2 + b] = sn * wp.y + c * wq.y; S[o3 + b] = sn * wp.z + c * wq.z;
+            Quat<T> wp = {A0[i], A1[i], A2[i], A3[i]};
+            Quat<T> wq = qmulc(Quat<T>{B0[i], B1[i], B2[i], B3[i]}, mu);
+            A0[i] = c * wp.w - sn * wq.w; A1[i] = c * wp.x - sn * wq.x;
+            A2[i] = c * wp.y - sn * wq.y; A3[i] = c * wp.z - sn * wq.z;
+            B0[i] = sn * wp.w + c * wq.w; B1[i] = sn * wp.x + c * wq.x;
+            B2[i] = sn * wp.y + c * wq.y; B3[i] = sn * wp.z + c * wq.z;
           }
         }
         __syncthreads();
       }
-      for (int e = t; e < 4 * l * U; e += JB_THREADS) {
-        const int c = e / (l * U), rem = e % (l * U), row = rem / U, lc = rem % U;
+      for (int e = t; e < 4 * U * l; e += JB_THREADS) {
+        const int c = e / (U * l), rem = e % (U * l), lc = rem / l, row = rem % l;
         const int g = gcol[lc];
         if (g >= 0) W[c * ll + (size_t)g * l + row] = S[e];
       }
@@ -304,7 +313,6 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
     *sweeps_out = sweep;
     if (!converged) qlr_set_error(err, QLR_ENOCONV);
   }
-  // column norms and normalisation: CTA p handles columns p, p + P, ...
   for (int j = p * nwarps + warp; j < l; j += JP * nwarps) {
     T a = 0;
     for (int i = lane; i < l; i += 32) a += qnorm2(ldw(W, l, i, j));
@@ -333,18 +341,33 @@ __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw,
     vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
   }
   __syncwarp();
-  const int U = 2 * bw;
-  const size_t nst = (size_t)(*nsweeps) * (2 * JP - 1) * (U - 1);
+  const size_t nst = (size_t)(*nsweeps) * jb_stages_per_sweep(bw);
   const int cap = JP * bw;
+  constexpr int KMAX = 4;   // records per lane and stage (cap <= 128)
+  T cur[KMAX][REC], nxt[KMAX][REC];
+  auto fetch = [&](size_t st, T (&buf)[KMAX][REC]) {
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u) {
+      const int k = lane + 32 * u;
+      if (st < nst && k < cap) {
+        const T* lg = rlog + (st * cap + k) * REC;
+#pragma unroll
+        for (int f = 0; f < REC; ++f) buf[u][f] = __ldg(lg + f);
+      } else {
+        buf[u][3] = (T)0;
+      }
+    }
+  };
+  fetch(0, cur);
   for (size_t st = 0; st < nst; ++st) {
-    const T* lg0 = rlog + st * cap * REC;
-    for (int k = lane; k < cap; k += 32) {
-      const T* lg = lg0 + (size_t)k * REC;
-      const T sn = lg[3];
+    fetch(st + 1, nxt);                       // next stage's records in flight while this one applies
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u) {
+      const T sn = cur[u][3];
       if (sn == (T)0) continue;
-      const int pp = (int)lg[0], qq = (int)lg[1];
-      const T c = lg[2];
-      const Quat<T> mu = {lg[4], lg[5], lg[6], lg[7]};
+      const int pp = (int)cur[u][0], qq = (int)cur[u][1];
+      const T c = cur[u][2];
+      const Quat<T> mu = {cur[u][4], cur[u][5], cur[u][6], cur[u][7]};
       Quat<T> vp = {vr[pp], vr[l + pp], vr[2 * l + pp], vr[3 * l + pp]};
       Quat<T> vq = qmulc(Quat<T>{vr[qq], vr[l + qq], vr[2 * l + qq], vr[3 * l + qq]}, mu);
       vr[pp] = c * vp.w - sn * vq.w; vr[l + pp] = c * vp.x - sn * vq.x; vr[2 * l + pp] = c * vp.y - sn * vq.y;
@@ -353,6 +376,10 @@ __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw,
       vr[3 * l + qq] = sn * vp.z + c * vq.z;
     }
     __syncwarp();
+#pragma unroll
+    for (int u = 0; u < KMAX; ++u)
+#pragma unroll
+      for (int f = 0; f < REC; ++f) cur[u][f] = nxt[u][f];
   }
   const size_t ll = (size_t)l * l;
   for (int j = lane; j < l; j += 32)
@@ -433,13 +460,19 @@ namespace qlr {
 constexpr int JMAX_SWEEPS = 30;
 constexpr int JBLOCK_MIN_L = 48;     // from this size on, the cluster block Jacobi is used
 
+// The cluster block Jacobi holds two column blocks per CTA in shared memory and gives each replay
+// lane at most four records per stage; larger cores run the single-CTA sweep.
+static bool use_block_jacobi(int l, size_t esz) {
+  const int bw = (l + 2 * JP - 1) / (2 * JP);
+  return l >= JBLOCK_MIN_L && (size_t)4 * l * 2 * bw * esz <= 220 * 1024 && JP * bw <= 128;
+}
+
 size_t jacobi_log_floats(int l) {
-  if (l >= JBLOCK_MIN_L) {
-    const int bw = (l + 2 * JP - 1) / (2 * JP), U = 2 * bw;
-    return (size_t)JMAX_SWEEPS * (2 * JP - 1) * (U - 1) * JP * bw * REC + REC;
-  }
+  const int bw = (l + 2 * JP - 1) / (2 * JP);
+  const size_t blk = (size_t)JMAX_SWEEPS * jb_stages_per_sweep(bw) * JP * bw * REC + REC;
   const int lp = l + (l & 1);
-  return (size_t)JMAX_SWEEPS * (lp - 1) * (lp / 2) * 6 + 6;
+  const size_t one = (size_t)JMAX_SWEEPS * (lp - 1) * (lp / 2) * 6 + 6;
+  return blk > one ? blk : one;
 }
 
 template <class T>
@@ -455,10 +488,10 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   if (!ws.ok) return QLR_ENOMEM;
   const T eps = (sizeof(T) == 4) ? (T)5.9604645e-08 : (T)1.1102230246251565e-16;
   const T tol = (T)8 * eps * (T)sqrt((double)l);   // above the rounding noise of the dot products
-  if (l >= JBLOCK_MIN_L) {
+  const bool blockj = use_block_jacobi(l, sizeof(T));
+  if (blockj) {
     const int bw = (l + 2 * JP - 1) / (2 * JP);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
-    if (smem > 220 * 1024) return QLR_EUNSUPPORTED;
     QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(JP, 1, 1);
@@ -509,7 +542,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     int hs = -1;
     cudaMemcpyAsync(&hs, sweeps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
-    std::fprintf(stderr, "qlr jacobi: l=%d sweeps=%d %s\n", l, hs, l >= JBLOCK_MIN_L ? "cluster" : "single-CTA");
+    std::fprintf(stderr, "qlr jacobi: l=%d sweeps=%d %s\n", l, hs, blockj ? "cluster" : "single-CTA");
   }
   { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); }
   QLR_CUDA_TRY(cudaGetLastError());
