@@ -70,6 +70,12 @@ extern "C" {
 #define QLR_SIDE_XH 1
 #define QLR_ORTH_CHOLQR2 0  /* CholeskyQR2, FP64 Gram and Cholesky                    */
 #define QLR_ORTH_SCHOLQR3 1 /* shifted CholeskyQR3 (Fukaya et al. 2020) for ill-conditioned input */
+/* opts.flags bit: run opts.orth at every pass, as Algorithms 2 and 4 write it.  Without it, a basis
+ * that only feeds the next pass (Algorithm 2's passes 1..v-2, the blocks Algorithm 4 stacks or
+ * discards) gets one shifted CholeskyQR step: its R is never used and the next product depends only
+ * on its column space, so the result is the same in exact arithmetic.  The QR factors whose Q or R
+ * reach U, S, V always use opts.orth. */
+#define QLR_FLAG_QR_EVERY_PASS 1
 
 typedef struct {
   void* plane[4];  /* device pointers: planes real, i, j, k; plane[0] == NULL => pure quaternion */
@@ -84,7 +90,7 @@ typedef struct {
   int32_t compute; /* QLR_COMPUTE_*; AUTO picks from A's dtype                                  */
   int32_t side;    /* QLR_SIDE_*; AUTO applies Section 6's rule (even v and n > m: use X^H)     */
   int32_t orth;    /* QLR_ORTH_*; Algorithm 4's stacked basis always uses QLR_ORTH_SCHOLQR3    */
-  int32_t flags;   /* reserved, must be 0                                                       */
+  int32_t flags;   /* 0 or QLR_FLAG_QR_EVERY_PASS                                               */
 } qlr_opts;
 
 typedef struct qlr_ctx qlr_ctx;

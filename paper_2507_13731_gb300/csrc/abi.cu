@@ -133,7 +133,7 @@ int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr
   if (!ctx) return QLR_EINVAL;
   QLR_TRY(check_qmat(A, QLR_ROW_MAJOR, true));
   QLR_TRY(check_qmat(omega, QLR_COL_MAJOR, false));
-  if (opts && opts->flags != 0) return QLR_EINVAL;
+  if (opts && (opts->flags & ~QLR_FLAG_QR_EVERY_PASS) != 0) return QLR_EINVAL;
   if (k < 1 || p < 0 || passes < 2) return QLR_ESHAPE;
   const int64_t l = (int64_t)k + p;
   if (l > std::min(A->rows, A->cols)) return QLR_ESHAPE;
@@ -167,18 +167,25 @@ int omega_in(Sched& S, const qlr_qmat* omega, qlr_qmat& out) {
   return qlr::convert_qmat(S.ctx, *omega, out);
 }
 
+// Orthonormalisation of a basis that only feeds the next pass: opts.orth when every pass should
+// run it, else one shifted CholeskyQR step (same column space, R discarded).
+int mid_orth(const qlr_opts* opts, int orth) {
+  return (opts && (opts->flags & QLR_FLAG_QR_EVERY_PASS)) ? orth : qlr::ORTH_SPAN;
+}
+
 // Algorithm 2's v passes.  Q1: rows_fwd x l, Q2: rows_bwd x l, R: last R (FP64 l x l x 4).
-int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth) {
+// Passes 1..v-2 only feed the next pass; passes v-1 and v give Q1, Q2 and R.
+int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth, int orth_mid) {
   qlr_qmat Y = S.thin(S.rows_fwd, l), Z = S.thin(S.rows_bwd, l);
   if (!S.ws->ok) return QLR_ENOMEM;
   const qlr_qmat* q2 = &om;
   for (int i = 1; i <= v; ++i) {
     if (i % 2 == 1) {
       QLR_TRY(S.sketch(S.op_fwd, *q2, Y));                          // X Q2
-      QLR_TRY(qlr::cholqr(S.ctx, Y, Q1, i == v ? R : nullptr, orth, *S.ws));   // [Q1, R1] = QR(.)
+      QLR_TRY(qlr::cholqr(S.ctx, Y, Q1, i == v ? R : nullptr, i >= v - 1 ? orth : orth_mid, *S.ws));   // [Q1, R1] = QR(.)
     } else {
       QLR_TRY(S.sketch(S.op_bwd, Q1, Z));                           // X^H Q1
-      QLR_TRY(qlr::cholqr(S.ctx, Z, Q2, i == v ? R : nullptr, orth, *S.ws));   // [Q2, R2] = QR(.)
+      QLR_TRY(qlr::cholqr(S.ctx, Z, Q2, i == v ? R : nullptr, i >= v - 1 ? orth : orth_mid, *S.ws));   // [Q2, R2] = QR(.)
       q2 = &Q2;
     }
   }
@@ -186,7 +193,8 @@ int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
 }
 
 // Algorithm 4.  On return Q1 (rows_fwd x L), Q2 (rows_bwd x L), R (L x L) with L the stacked width.
-int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth) {
+// The per-view blocks are stacked into K (re-orthonormalised as a whole) or only feed the next view.
+int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth, int orth_mid) {
   const int s = (v - 1) / 2;
   const bool even = (v % 2 == 0);
   const int nblk = even ? v / 2 : (v - 1) / 2;
@@ -200,13 +208,13 @@ int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
     if (2 * j - 1 < v) {                        // odd view: range side
       qlr_qmat dst = even ? col_slice(K, (int64_t)(j - 1) * l, l) : q1cur;
       QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
-      QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth, *S.ws));
+      QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth_mid, *S.ws));
       q1cur = dst;
     }
     if (2 * j < v) {
       qlr_qmat dst = even ? q2cur : col_slice(K, (int64_t)(j - 1) * l, l);
       QLR_TRY(S.sketch(S.op_bwd, q1cur, Z));
-      QLR_TRY(qlr::cholqr(S.ctx, Z, dst, nullptr, orth, *S.ws));
+      QLR_TRY(qlr::cholqr(S.ctx, Z, dst, nullptr, orth_mid, *S.ws));
       q2cur = dst;
       q2prev = &q2cur;
     }
@@ -214,7 +222,7 @@ int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
   if (even) {
     qlr_qmat dst = col_slice(K, (int64_t)s * l, l);
     QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
-    QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth, *S.ws));
+    QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth_mid, *S.ws));
     QLR_TRY(qlr::cholqr(S.ctx, K, Q1, nullptr, QLR_ORTH_SCHOLQR3, *S.ws));   // [Q1, ~] = QR(K1)
     qlr_qmat W = S.thin(S.rows_bwd, Lw);
     if (!S.ws->ok) return QLR_ENOMEM;
@@ -496,7 +504,7 @@ int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, 
   S.allow_simt_fallback = autoc;
   qlr_qmat om;
   QLR_TRY(omega_in(S, omega, om));
-  QLR_TRY(run_alg2(S, l, passes, om, *Q1, *Q2, R, orth));
+  QLR_TRY(run_alg2(S, l, passes, om, *Q1, *Q2, R, orth, mid_orth(opts, orth)));
   if (side_used) *side_used = side;
   return QLR_OK;
 }
@@ -529,8 +537,8 @@ static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passe
   double* Lm = ws.take<double>((size_t)4 * L * k);
   double* Rt = ws.take<double>((size_t)4 * L * k);
   if (!ws.ok) return QLR_ENOMEM;
-  if (algo == QLR_ALG2) QLR_TRY(run_alg2(S, l, passes, om, Q1, Q2, R, orth));
-  else QLR_TRY(run_alg4(S, l, passes, om, Q1, Q2, R, orth));
+  if (algo == QLR_ALG2) QLR_TRY(run_alg2(S, l, passes, om, Q1, Q2, R, orth, mid_orth(opts, orth)));
+  else QLR_TRY(run_alg4(S, l, passes, om, Q1, Q2, R, orth, mid_orth(opts, orth)));
   const int prec = (compute == QLR_COMPUTE_F64) ? QLR_F64 : QLR_F32;
   QLR_TRY(qlr::core_tsvd(ctx, (int)L, R, k, Lm, S_out, Rt, prec, ws));
   // even v: [V_hat, S, U_hat] = TSVD(R2); odd v: [U_hat, S, V_hat] = TSVD(R1)

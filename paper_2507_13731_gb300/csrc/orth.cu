@@ -7,6 +7,15 @@
 
 namespace {
 
+// Position (a, b), a <= b, of entry e in the column-by-column listing of an upper triangle
+// (0,0), (0,1), (1,1), (0,2), ...: b is the largest integer with b (b + 1) / 2 <= e.
+__device__ __forceinline__ int2 upper_tri_entry(int e) {
+  int b = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (b > 0 && b * (b + 1) / 2 > e) --b;
+  while ((b + 1) * (b + 2) / 2 <= e) ++b;
+  return make_int2(e - b * (b + 1) / 2, b);
+}
+
 // ---------------------------------------------------------------------------------------
 // Gram partial sums: part[chunk] = sum over the chunk's rows r of conj(y_ri) y_rj, for tiles
 // (ti <= tj) of the upper triangle.  32 x 32 quaternion tiles, 256 threads, 2 x 2 per thread.
@@ -16,11 +25,11 @@ template <class TY>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const TY* __restrict__ y0, const TY* __restrict__ y1,
                                                            const TY* __restrict__ y2, const TY* __restrict__ y3,
                                                            int64_t m, int l, int64_t ld, int64_t rows_per_chunk,
-                                                           const int2* __restrict__ tiles, double* __restrict__ part) {
+                                                           double* __restrict__ part) {
   __shared__ double Yi[4][GR][GT + 1];
   __shared__ double Yj[4][GR][GT + 1];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int2 tile = tiles[blockIdx.x];
+  const int2 tile = upper_tri_entry((int)blockIdx.x);
   const int i0 = tile.x * GT, j0 = tile.y * GT;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
   const int64_t r_end = min(m, r_begin + rows_per_chunk);
@@ -134,11 +143,11 @@ __device__ __forceinline__ void df_add(float& S, float& C, float a, float b) {
 __global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
                                                                const float* __restrict__ y2, const float* __restrict__ y3,
                                                                int64_t m, int l, int64_t ld, int64_t rows_per_chunk,
-                                                               const int2* __restrict__ tiles, double* __restrict__ part) {
+                                                               double* __restrict__ part) {
   __shared__ float Ya[WR][WT];
   __shared__ float Yb[WR][WT];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int2 tile = tiles[blockIdx.x];
+  const int2 tile = upper_tri_entry((int)blockIdx.x);
   const int I0 = tile.x * WT, J0 = tile.y * WT;
   const int L4 = 4 * l;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
@@ -258,10 +267,13 @@ __global__ void chol_init_kernel(const double* __restrict__ G, double* __restric
 // inverse into Dinv (b x b x 4, column-major).
 __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm, double* __restrict__ R, int l, int j0,
                                                          int b, double* __restrict__ Dinv, int* err, const int* run_if) {
+  // FP64 issues at a small fraction of the FP32 rate, so every FP64 instruction here is issued by
+  // warps whose lanes all carry work: the active (row, column) pairs of each step are enumerated
+  // densely, and pivots and their reciprocals are computed once.
   if (run_if && *run_if == 0) return;
   __shared__ double D[4][CB][CB];
   __shared__ double X[4][CB][CB];
-  __shared__ double piv;
+  __shared__ double rpiv[CB];
   const int t = threadIdx.x;
   const size_t ll = (size_t)l * l;
   for (int e = t; e < CB * CB; e += blockDim.x) {
@@ -279,42 +291,43 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm,
         qlr_set_error(err, QLR_ENOTPD);
         d2 = 1e-300;
       }
-      piv = sqrt(d2);
+      const double piv = sqrt(d2);
       D[0][j][j] = piv;
       D[1][j][j] = D[2][j][j] = D[3][j][j] = 0.0;
+      rpiv[j] = 1.0 / piv;
     }
     __syncthreads();
-    const double inv = 1.0 / piv;
-    for (int k = j + 1 + t; k < b; k += blockDim.x)
-      for (int c = 0; c < 4; ++c) D[c][j][k] *= inv;
+    const int n = b - j - 1;                  // row j right of the pivot: n entries x 4 planes
+    if (t < 4 * n) {
+      const int c = t / n, k = j + 1 + t % n;
+      D[c][j][k] *= rpiv[j];
+    }
     __syncthreads();
-    for (int e = t; e < CB * CB; e += blockDim.x) {
-      const int i = e % CB, k = e / CB;
-      if (i > j && i <= k && k < b) {
-        Quat<double> a = {D[0][j][i], D[1][j][i], D[2][j][i], D[3][j][i]};
-        Quat<double> bb = {D[0][j][k], D[1][j][k], D[2][j][k], D[3][j][k]};
-        Quat<double> pr = qcmul(a, bb);
-        D[0][i][k] -= pr.w; D[1][i][k] -= pr.x; D[2][i][k] -= pr.y; D[3][i][k] -= pr.z;
-      }
+    // trailing update D[i][k] -= conj(D[j][i]) D[j][k] for j < i <= k < b: n (n + 1) / 2 pairs
+    const int npairs = n * (n + 1) / 2;
+    for (int e = t; e < npairs; e += blockDim.x) {
+      const int2 ik = upper_tri_entry(e);
+      const int i = j + 1 + ik.x, k = j + 1 + ik.y;
+      Quat<double> pr = qcmul(Quat<double>{D[0][j][i], D[1][j][i], D[2][j][i], D[3][j][i]},
+                              Quat<double>{D[0][j][k], D[1][j][k], D[2][j][k], D[3][j][k]});
+      D[0][i][k] -= pr.w; D[1][i][k] -= pr.x; D[2][i][k] -= pr.y; D[3][i][k] -= pr.z;
     }
     __syncthreads();
   }
   // inverse X = D^{-1} by column-oriented back substitution on all right-hand sides at once:
-  // for i = b-1 .. 0: X[i, :] = Y[i, :] / d_i, then Y[0:i, :] -= D[0:i, i] X[i, :]   (Y starts as I)
-  for (int e = t; e < CB * CB; e += blockDim.x) {
-    const int i = e % CB, j = e / CB;
-    X[0][i][j] = (i == j && i < b) ? 1.0 : 0.0;
-  }
+  // for i = b-1 .. 0: X[i, i:] = Y[i, i:] / d_i, then Y[0:i, i:] -= D[0:i, i] X[i, i:]  (Y starts as I;
+  // row i of X is zero left of the diagonal)
+  for (int e = t; e < b; e += blockDim.x) X[0][e][e] = 1.0;
   __syncthreads();
   for (int i = b - 1; i >= 0; --i) {
-    const double dinv = 1.0 / D[0][i][i];
-    if (t < b) {           // row i of X: scale (only columns j >= i are non-zero)
-      const int j = t;
-      X[0][i][j] *= dinv; X[1][i][j] *= dinv; X[2][i][j] *= dinv; X[3][i][j] *= dinv;
+    const int w = b - i;
+    if (t < 4 * w) {
+      const int c = t / w, j = i + t % w;
+      X[c][i][j] *= rpiv[i];
     }
     __syncthreads();
-    for (int e = t; e < i * b; e += blockDim.x) {   // rows r < i, all columns j
-      const int r = e % i, j = e / i;
+    for (int e = t; e < i * w; e += blockDim.x) {   // rows r < i, columns j >= i
+      const int r = e % i, j = i + e / i;
       Quat<double> pr = qmul(Quat<double>{D[0][r][i], D[1][r][i], D[2][r][i], D[3][r][i]},
                              Quat<double>{X[0][i][j], X[1][i][j], X[2][i][j], X[3][i][j]});
       X[0][r][j] -= pr.w; X[1][r][j] -= pr.x; X[2][r][j] -= pr.y; X[3][r][j] -= pr.z;
@@ -355,13 +368,12 @@ __global__ void chol_panel_kernel(const double* __restrict__ Wm, double* __restr
 
 // Trailing update of the upper triangle: Wm[i, k] -= sum_{t in panel} conj(R[t, i]) R[t, k].
 __global__ void __launch_bounds__(64) chol_update_kernel(double* __restrict__ Wm, const double* __restrict__ R, int l,
-                                                          int j0, int b, const int2* __restrict__ tiles,
-                                                          const int* run_if) {
+                                                          int j0, int b, const int* run_if) {
   if (run_if && *run_if == 0) return;
   __shared__ double Pi[4][CB][CT];
   __shared__ double Pk[4][CB][CT];
   const int j1 = j0 + b;
-  const int2 tl = tiles[blockIdx.x];
+  const int2 tl = upper_tri_entry((int)blockIdx.x);
   const int i0 = j1 + tl.x * CT, k0 = j1 + tl.y * CT;
   const size_t ll = (size_t)l * l;
   const int t = threadIdx.x;
@@ -498,10 +510,13 @@ __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __re
 // F = Phi(E - F^H F), Phi(X) = strict upper part of X plus half its (real) diagonal, a fixed point
 // reached by iterating from F = Phi(E) (the error shrinks like |E|^(n+1)).  The inverse is
 // (I + F)^{-1} = I - F + F^2 - ..., evaluated as X <- I - F X.  Each step is a triangular product
-// spread over all SMs in FP64 -- no serial pivots.  The init kernel raises `use_chol` when
+// spread over all SMs in FP64 -- no serial pivots.  Both iterations contract with rate of order
+// |E|, so a step whose predecessor changed no entry by more than SERIES_TOL (far below the FP64
+// resolution of I + F) only copies its input forward.  The init kernel raises `use_chol` when
 // l * max|E_ij| exceeds SERIES_MAX; the blocked Cholesky kernels then run instead (they are
 // predicated on that flag, so no host synchronisation is needed).
 constexpr double SERIES_MAX = 5e-3;
+constexpr double SERIES_TOL = 1e-18;
 constexpr int SERIES_ITERS = 6, NEUMANN_ITERS = 7, SPLIT = 4;
 
 __global__ void series_init_kernel(const double* __restrict__ G, double* __restrict__ E, double* __restrict__ F, int l,
@@ -528,24 +543,38 @@ __global__ void series_decide_kernel(const unsigned long long* __restrict__ emax
 // out(i, j) for i <= j with SPLIT threads per entry:
 //   mode 0 (series):  Phi(E - F^H F)(i, j),  (F^H F)_ij = sum_{t <= i} conj(F_ti) F_tj
 //   mode 1 (Neumann): delta_ij - (F X)_ij,     (F X)_ij  = sum_{i <= t <= j} F_it X_tj
+// The largest change against the step's input (F in mode 0, X in mode 1) goes to *delta; when
+// the previous step's change *prev_delta is at most SERIES_TOL the input is copied unchanged.
 __global__ void __launch_bounds__(128) series_step_kernel(const double* __restrict__ E, const double* __restrict__ F,
                                                            const double* __restrict__ X, double* __restrict__ out, int l,
-                                                           int mode, const int2* __restrict__ entries, int nentries) {
+                                                           int mode, int nentries,
+                                                           const unsigned long long* __restrict__ prev_delta,
+                                                           unsigned long long* __restrict__ delta) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ent = gt / SPLIT;
   const int part = (int)(gt % SPLIT);
   const bool valid = ent < nentries;
-  Quat<double> acc = {0, 0, 0, 0};
+  const double* in = (mode == 0) ? F : X;
   int i = 0, j = 0;
   if (valid) {
-    i = entries[ent].x;
-    j = entries[ent].y;
+    const int2 ij = upper_tri_entry((int)ent);
+    i = ij.x;
+    j = ij.y;
+  }
+  if (prev_delta && __longlong_as_double((long long)*prev_delta) <= SERIES_TOL) {
+    if (valid && part == 0) st_small(out, l, i, j, ld_small(in, l, i, j));
+    return;
+  }
+  Quat<double> acc = {0, 0, 0, 0};
+  if (valid) {
     if (mode == 0) {
+#pragma unroll 4
       for (int t = part; t <= i; t += SPLIT) {
         Quat<double> pr = qcmul(ld_small(F, l, t, i), ld_small(F, l, t, j));
         acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
       }
     } else {
+#pragma unroll 4
       for (int t = i + part; t <= j; t += SPLIT) {
         Quat<double> pr = qmul(ld_small(F, l, i, t), ld_small(X, l, t, j));
         acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
@@ -559,16 +588,24 @@ __global__ void __launch_bounds__(128) series_step_kernel(const double* __restri
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
   }
-  if (!valid || part != 0) return;
-  Quat<double> r;
-  if (mode == 0) {
-    Quat<double> e = ld_small(E, l, i, j);
-    if (i < j) r = {e.w - acc.w, e.x - acc.x, e.y - acc.y, e.z - acc.z};
-    else r = {0.5 * (e.w - acc.w), 0.0, 0.0, 0.0};
-  } else {
-    r = {(i == j ? 1.0 : 0.0) - acc.w, -acc.x, -acc.y, -acc.z};
+  double ch = 0.0;
+  if (valid && part == 0) {
+    Quat<double> r;
+    if (mode == 0) {
+      Quat<double> e = ld_small(E, l, i, j);
+      if (i < j) r = {e.w - acc.w, e.x - acc.x, e.y - acc.y, e.z - acc.z};
+      else r = {0.5 * (e.w - acc.w), 0.0, 0.0, 0.0};
+    } else {
+      r = {(i == j ? 1.0 : 0.0) - acc.w, -acc.x, -acc.y, -acc.z};
+    }
+    const Quat<double> o = ld_small(in, l, i, j);
+    ch = fmax(fmax(fabs(r.w - o.w), fabs(r.x - o.x)), fmax(fabs(r.y - o.y), fabs(r.z - o.z)));
+    st_small(out, l, i, j, r);
   }
-  st_small(out, l, i, j, r);
+  // warp maximum, one atomic per warp (non-negative doubles order like their bit patterns)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(delta, (unsigned long long)__double_as_longlong(ch));
 }
 
 // R2 = I + F (full matrix written; lower part zero)
@@ -597,26 +634,22 @@ static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   const int64_t m = Y.rows;
   const int L4 = 4 * l;
   const int nt = (L4 + WT - 1) / WT;
-  std::vector<int2> tiles;
-  for (int b = 0; b < nt; ++b)
-    for (int a = 0; a <= b; ++a) tiles.push_back(make_int2(a, b));
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int target = 3 * (ctx->num_sms > 0 ? ctx->num_sms : 148);
-  int64_t chunks = (target + (int64_t)tiles.size() - 1) / (int64_t)tiles.size();
+  int64_t chunks = (target + ntiles - 1) / ntiles;
   chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (m + 63) / 64));
   chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, ((int64_t)64 << 20) / ((int64_t)8 * L4 * L4)));
   int64_t rpc = ((m + chunks - 1) / chunks + WR - 1) / WR * WR;
   chunks = (m + rpc - 1) / rpc;
   size_t mark = ws.off;
-  int2* d_tiles = ws.take<int2>(tiles.size());
   double* part = ws.take<double>((size_t)chunks * L4 * L4);
   if (!ws.ok) return QLR_ENOMEM;
-  QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
   {
     KTimer kt(ctx, QLR_KID_GRAM);
-    dim3 grid((unsigned)tiles.size(), (unsigned)chunks);
+    dim3 grid((unsigned)ntiles, (unsigned)chunks);
     gram_df_partial_kernel<<<grid, 256, 0, ctx->stream>>>(
         static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
-        static_cast<const float*>(Y.plane[3]), m, l, Y.ld, rpc, d_tiles, part);
+        static_cast<const float*>(Y.plane[3]), m, l, Y.ld, rpc, part);
     QLR_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -637,11 +670,9 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   const int64_t m = Y.rows;
   if (l == 0) return QLR_OK;
   const int nt = (l + GT - 1) / GT;
-  std::vector<int2> tiles;
-  for (int b = 0; b < nt; ++b)
-    for (int a = 0; a <= b; ++a) tiles.push_back(make_int2(a, b));
+  const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   int target = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 148);
-  int64_t chunks = (target + (int64_t)tiles.size() - 1) / (int64_t)tiles.size();
+  int64_t chunks = (target + ntiles - 1) / ntiles;
   chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, (m + 63) / 64));
   chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, ((int64_t)64 << 20) / ((int64_t)32 * l * l)));
   int64_t rpc = ((m + chunks - 1) / chunks + GR - 1) / GR * GR;
@@ -649,20 +680,18 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   chunks = (m + rpc - 1) / rpc;
   if (chunks == 0) chunks = 1;
   size_t mark = ws.off;
-  int2* d_tiles = ws.take<int2>(tiles.size());
   double* part = ws.take<double>((size_t)chunks * 4 * l * l);
   if (!ws.ok) return QLR_ENOMEM;
-  QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
-  dim3 grid((unsigned)tiles.size(), (unsigned)chunks);
+  dim3 grid((unsigned)ntiles, (unsigned)chunks);
   KTimer kt(ctx, QLR_KID_GRAM);
   if (Y.dtype == QLR_F64) {
     const double* p[4];
     for (int c = 0; c < 4; ++c) p[c] = static_cast<const double*>(Y.plane[c]);
-    gram_partial_kernel<double><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, d_tiles, part);
+    gram_partial_kernel<double><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, part);
   } else if (Y.dtype == QLR_F32) {
     const float* p[4];
     for (int c = 0; c < 4; ++c) p[c] = static_cast<const float*>(Y.plane[c]);
-    gram_partial_kernel<float><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, d_tiles, part);
+    gram_partial_kernel<float><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, part);
   } else {
     return QLR_EINVAL;
   }
@@ -682,13 +711,7 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
   double* Wm = ws.take<double>(ll4);
   const int npan = (l + CB - 1) / CB;
   if (Dinv_all == nullptr) Dinv_all = ws.take<double>((size_t)npan * 4 * CB * CB);
-  const int nbt = (l + CT - 1) / CT;
-  std::vector<int2> all;
-  for (int b2 = 0; b2 < nbt; ++b2)
-    for (int a2 = 0; a2 <= b2; ++a2) all.push_back(make_int2(a2, b2));
-  int2* d_tiles = ws.take<int2>(all.size());
   if (!ws.ok) return QLR_ENOMEM;
-  QLR_CUDA_TRY(cudaMemcpyAsync(d_tiles, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
   KTimer kt(ctx, QLR_KID_CHOL);
   chol_init_kernel<<<std::max(1, std::min(64, (int)((ll4 / 4 + 255) / 256))), 256, 0, ctx->stream>>>(G, Wm, R, l, shift_coef, run_if);
   QLR_CUDA_TRY(cudaGetLastError());
@@ -701,11 +724,10 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     if (rem <= 0) break;
     chol_panel_kernel<<<(rem * 32 + 127) / 128, 128, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, run_if);
     QLR_CUDA_TRY(cudaGetLastError());
-    // tiles of the trailing triangle (tile coordinates relative to j0 + b); the tile list is the
-    // prefix of the full upper-tile list with both coordinates < ceil(rem / CT)
+    // tiles (a <= b) of the trailing triangle, coordinates relative to j0 + b
     const int nt = (rem + CT - 1) / CT;
     const int ntiles = nt * (nt + 1) / 2;
-    chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, d_tiles, run_if);
+    chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, run_if);
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
@@ -764,17 +786,12 @@ static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, doubl
   double* Fb = ws.take<double>(ll4);
   double* Xa = ws.take<double>(ll4);
   double* Xb = ws.take<double>(ll4);
-  unsigned long long* emax = ws.take<unsigned long long>(1);
+  unsigned long long* emax = ws.take<unsigned long long>(1 + SERIES_ITERS + NEUMANN_ITERS);
+  unsigned long long* deltas = emax + 1;
   int* use_chol = ws.take<int>(1);
   const int nent = l * (l + 1) / 2;
-  int2* ent = ws.take<int2>(nent);
   if (!ws.ok) return QLR_ENOMEM;
-  std::vector<int2> he;
-  he.reserve(nent);
-  for (int j = 0; j < l; ++j)
-    for (int i = 0; i <= j; ++i) he.push_back(make_int2(i, j));
-  QLR_CUDA_TRY(cudaMemcpyAsync(ent, he.data(), he.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
-  QLR_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), ctx->stream));
+  QLR_CUDA_TRY(cudaMemsetAsync(emax, 0, (1 + SERIES_ITERS + NEUMANN_ITERS) * sizeof(unsigned long long), ctx->stream));
   KTimer kt(ctx, QLR_KID_CHOL);
   const int64_t tot = (int64_t)l * l;
   const unsigned gsq = (unsigned)((tot + 127) / 128);
@@ -784,16 +801,18 @@ static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, doubl
   double* Fc = Fa;
   double* Fn = Fb;
   for (int it = 0; it < SERIES_ITERS; ++it) {
-    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, ent, nent);
+    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, nent, it ? deltas + it - 1 : nullptr,
+                                                     deltas + it);
     std::swap(Fc, Fn);
   }
   series_form_kernel<<<gsq, 128, 0, ctx->stream>>>(Fc, R2, l);
   fill_identity_kernel<<<gsq, 128, 0, ctx->stream>>>(Xa, l);
   double* Xc = Xa;
   double* Xn = Xb;
+  unsigned long long* nd = deltas + SERIES_ITERS;
   for (int it = 0; it < NEUMANN_ITERS; ++it) {
-    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, (it == NEUMANN_ITERS - 1) ? R2inv : Xn, l, 1, ent,
-                                                   nent);
+    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, (it == NEUMANN_ITERS - 1) ? R2inv : Xn, l, 1, nent,
+                                                     it ? nd + it - 1 : nullptr, nd + it);
     std::swap(Xc, Xn);
   }
   QLR_CUDA_TRY(cudaGetLastError());
@@ -821,14 +840,15 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
   T.layout = QLR_COL_MAJOR;
   for (int c = 0; c < 4; ++c) T.plane[c] = tbuf + (size_t)c * m * l * esz;
 
-  // CholeskyQR2: Y -> T -> Q.  Shifted CholeskyQR3: Y -> Q -> T -> Q.
-  const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : 2;
+  // CholeskyQR2: Y -> T -> Q.  Shifted CholeskyQR3: Y -> Q -> T -> Q.  Span only: Y -> Q (shifted).
+  const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : (orth == ORTH_SPAN) ? 1 : 2;
+  const qlr_qmat* seq1[2] = {&Y, &Q};
   const qlr_qmat* seq2[3] = {&Y, &T, &Q};
   const qlr_qmat* seq3[4] = {&Y, &Q, &T, &Q};
-  const qlr_qmat* const* seq = (steps == 3) ? seq3 : seq2;
+  const qlr_qmat* const* seq = (steps == 3) ? seq3 : (steps == 1) ? seq1 : seq2;
   // shift s = 11 (m l + l (l + 1)) u ||Y||_2^2 with u = 2^-53 (FP64 Gram and Cholesky);
   // ||Y||_2^2 is bounded by trace(G), which the Cholesky kernel multiplies in.
-  const double shift = (orth == QLR_ORTH_SCHOLQR3) ? 11.0 * ((double)m * l + (double)l * (l + 1)) * 1.1102230246251565e-16 : 0.0;
+  const double shift = (orth == QLR_ORTH_SCHOLQR3 || orth == ORTH_SPAN) ? 11.0 * ((double)m * l + (double)l * (l + 1)) * 1.1102230246251565e-16 : 0.0;
   double* Rprod = P1;
   double* Rnext = P2;
   for (int s = 0; s < steps; ++s) {

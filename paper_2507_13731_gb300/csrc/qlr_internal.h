@@ -139,6 +139,10 @@ __device__ __forceinline__ void st_small(double* M, int l, int i, int j, const Q
 // launchers implemented in the .cu files (all asynchronous on ctx->stream)
 namespace qlr {
 
+// Internal orthonormalisation mode of cholqr(): one shifted CholeskyQR step, for bases of which
+// only the column space is used.
+constexpr int ORTH_SPAN = 16;
+
 // SIMT generic quaternion GEMM  C = alpha * op(A) * B + beta * C
 //   A element (i, k) at A.plane[c] + i*sa_i + k*sa_k, conj_a applies A -> conj(A) elementwise.
 //   B column-major (k, j) at b + k + j*ldb.  C column-major.  Types per dtype fields.

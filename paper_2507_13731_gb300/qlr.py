@@ -29,6 +29,7 @@ OP_N, OP_H = 0, 1
 ALG2, ALG4 = 2, 4
 SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
 ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
+FLAG_QR_EVERY_PASS = 1
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc"]
@@ -151,8 +152,9 @@ def _T(t):
     return qmat(t, COL_MAJOR)
 
 
-def _opts(compute: int = COMPUTE_AUTO, side: int = SIDE_AUTO, orth: int = ORTH_CHOLQR2) -> OptsC:
-    return OptsC(compute, side, orth, 0)
+def _opts(compute: int = COMPUTE_AUTO, side: int = SIDE_AUTO, orth: int = ORTH_CHOLQR2,
+          qr_every_pass: bool = False) -> OptsC:
+    return OptsC(compute, side, orth, FLAG_QR_EVERY_PASS if qr_every_pass else 0)
 
 
 class Context:
@@ -250,9 +252,9 @@ def qtsvd(ctx: Context, R: torch.Tensor, k: int, L: torch.Tensor, S: torch.Tenso
 
 
 def qrangefinder(ctx: Context, A, k, p, passes, omega, Q1, Q2, R, compute=COMPUTE_AUTO, side=SIDE_AUTO,
-                 orth=ORTH_CHOLQR2) -> int:
+                 orth=ORTH_CHOLQR2, qr_every_pass=False) -> int:
     a, om, q1, q2 = _A(A), _T(omega), _T(Q1), _T(Q2)
-    o = _opts(compute, side, orth)
+    o = _opts(compute, side, orth, qr_every_pass)
     used = ctypes.c_int(-1)
     _check(lib().qlr_qrangefinder(ctx.h, ctypes.byref(a), k, p, passes, ctypes.byref(om), ctypes.byref(o),
                                   ctypes.byref(q1), ctypes.byref(q2), ctypes.c_void_p(R.data_ptr()),
@@ -261,18 +263,19 @@ def qrangefinder(ctx: Context, A, k, p, passes, omega, Q1, Q2, R, compute=COMPUT
 
 
 def qsvd_lowrank(ctx: Context, A, k, p, passes, omega, U, S, V, algo=ALG2, compute=COMPUTE_AUTO, side=SIDE_AUTO,
-                 orth=ORTH_CHOLQR2):
+                 orth=ORTH_CHOLQR2, qr_every_pass=False):
     a, om, u, v = _A(A), _T(omega), _T(U), _T(V)
-    o = _opts(compute, side, orth)
+    o = _opts(compute, side, orth, qr_every_pass)
     _check(lib().qlr_qsvd_lowrank(ctx.h, ctypes.byref(a), k, p, passes, algo, ctypes.byref(om), ctypes.byref(o),
                                   ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
            "qlr_qsvd_lowrank")
     return U, S, V
 
 
-def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE_AUTO, side=SIDE_AUTO):
+def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE_AUTO, side=SIDE_AUTO,
+                  qr_every_pass=False):
     a, om, u, v = _A(A), _T(omega), _T(U), _T(V)
-    o = _opts(compute, side)
+    o = _opts(compute, side, ORTH_CHOLQR2, qr_every_pass)
     _check(lib().qlr_qblock_krylov(ctx.h, ctypes.byref(a), k, b, passes, ctypes.byref(om), ctypes.byref(o),
                                    ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
            "qlr_qblock_krylov")

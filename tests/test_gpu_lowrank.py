@@ -7,6 +7,7 @@ import synth
 from oracle import algorithms as al
 from oracle import norms
 from oracle import quaternion as Q
+from oracle.qsvd import singular_values
 from tests._qutil import dev_rowmajor, dev_thin, host, small, small_to_np
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +52,27 @@ def test_config1_fp64_alg2(ctx, v):
     np.testing.assert_allclose(_proj(V[:, :, :8]), _proj(ref.V[:, :, :8]), atol=1e-8)
 
 
+@pytest.mark.parametrize("algo", ["alg2", "alg4"])
+@pytest.mark.parametrize("v", [4, 7])
+def test_qr_every_pass_flag(ctx, algo, v):
+    """Both settings of QLR_FLAG_QR_EVERY_PASS give the oracle's singular values to 1e-10 and the
+    same rank-k subspaces: the intermediate bases differ only by l x l rotations."""
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(300, 220, 12, 6, v, seed=26)
+    Ad = dev_rowmajor(P.A, "f64")
+    Od = dev_thin(P.Omega, "f64")
+    a = qlr.ALG2 if algo == "alg2" else qlr.ALG4
+    ref = (al.alg2_arbitrary_pass if algo == "alg2" else al.alg4_block_flexible)(P.A, 12, 6, v, P.Omega)
+    for every in (True, False):
+        U, V = qlr.empty_thin(300, 12, torch.float64), qlr.empty_thin(220, 12, torch.float64)
+        S = torch.zeros(12, dtype=torch.float64, device="cuda")
+        qlr.qsvd_lowrank(ctx, Ad, 12, 6, v, Od, U, S, V, algo=a, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X,
+                         qr_every_pass=every)
+        assert ctx.sync() == 0
+        np.testing.assert_allclose(S.cpu().numpy(), ref.S, rtol=1e-10)
+        np.testing.assert_allclose(_proj(host(U)[:, :, :8]), _proj(ref.U[:, :, :8]), atol=1e-8)
+
+
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 6])
 def test_alg4_fp64_small(ctx, v):
     from paper_2507_13731_gb300 import qlr
@@ -82,21 +104,35 @@ def test_side_xh(ctx, v):
     np.testing.assert_allclose(_proj(U[:, :, :6]), _proj(ref.U[:, :, :6]), atol=1e-8)
 
 
-def test_rangefinder_factors(ctx):
+@pytest.mark.parametrize("every_pass", [True, False])
+def test_rangefinder_factors(ctx, every_pass):
+    """With a QR at every pass the factors equal the oracle's; by default the bases that only feed
+    the next pass get one shifted CholeskyQR step, so Q1, Q2, R equal the oracle's up to unitary
+    l x l rotations: same projectors, same singular values of R, same defining relation."""
     from paper_2507_13731_gb300 import qlr
     P = synth.config_slow_decay(200, 150, 10, 5, 3, seed=24)
     Ad = dev_rowmajor(P.A, "f64")
     Od = dev_thin(P.Omega, "f64")
     Q1, Q2 = qlr.empty_thin(200, 15, torch.float64), qlr.empty_thin(150, 15, torch.float64)
     R = small(15)
-    for v in (2, 3, 4):
-        side = qlr.qrangefinder(ctx, Ad, 10, 5, v, Od, Q1, Q2, R, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X)
+    for v in (2, 3, 4, 5):
+        side = qlr.qrangefinder(ctx, Ad, 10, 5, v, Od, Q1, Q2, R, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X,
+                                qr_every_pass=every_pass)
         assert ctx.sync() == 0 and side == qlr.SIDE_X
         ref = al.alg2_arbitrary_pass(P.A, 10, 5, v, P.Omega)
-        np.testing.assert_allclose(host(Q1), ref.Q1, atol=1e-9)
-        np.testing.assert_allclose(small_to_np(R), ref.R, atol=1e-10)
-        if v >= 2:
-            np.testing.assert_allclose(host(Q2), ref.Q2, atol=1e-9)
+        q1, q2, r = host(Q1), host(Q2), small_to_np(R)
+        if every_pass or v == 2:
+            np.testing.assert_allclose(q1, ref.Q1, atol=1e-9)
+            np.testing.assert_allclose(r, ref.R, atol=1e-10)
+            np.testing.assert_allclose(q2, ref.Q2, atol=1e-9)
+            continue
+        for q, rq in ((q1, ref.Q1), (q2, ref.Q2)):
+            np.testing.assert_allclose(Q.qmatmul(q, Q.qH(q)), Q.qmatmul(rq, Q.qH(rq)), atol=1e-9)
+        np.testing.assert_allclose(singular_values(r), singular_values(ref.R), rtol=1e-10, atol=1e-12)
+        # odd v: X Q2 = Q1 R1; even v: X^H Q1 = Q2 R2
+        lhs = Q.qmatmul(P.A, q2) if v % 2 else Q.qmatmul(Q.qH(P.A), q1)
+        rhs = Q.qmatmul(q1, r) if v % 2 else Q.qmatmul(q2, r)
+        np.testing.assert_allclose(lhs, rhs, atol=1e-9)
 
 
 def test_batched_loop_pure(ctx):
