@@ -197,8 +197,18 @@ constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4
 __host__ __device__ __forceinline__ int jb_stages_per_sweep(int bw) { return (2 * bw - 1) + (2 * JP - 2) * bw; }
 __host__ __device__ __forceinline__ int jb_stage(int br, int lr, int bw) { return br == 0 ? lr : (2 * bw - 1) + (br - 1) * bw + lr; }
 
-template <class T>
-__global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
+// Reciprocal and reciprocal square root for the rotation parameters: the hardware approximations
+// in float (a few ulp; every rotation is logged and replayed exactly as applied, and the singular
+// values are re-evaluated in FP64 at the end), correctly rounded in double.
+__device__ __forceinline__ float jrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jrsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float jrcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double jrcp(double x) { return 1.0 / x; }
+
+// Rows per lane RPL: the two columns of a pair stay in registers between the dot products and
+// the rotation (l <= 32 RPL).
+template <class T, int RPL>
+__global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
                                                                    T* __restrict__ W, int max_sweeps, T tol,
                                                                    T* __restrict__ rlog, int* __restrict__ flags,
                                                                    int* __restrict__ sweeps_out, T* __restrict__ sig_out,
@@ -213,6 +223,7 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
   const int U = 2 * bw;
   const int sps = jb_stages_per_sweep(bw);
   const int stage_cap = JP * bw;
+  const T tol2 = tol * tol;
   for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)R[e];
   if (p == 0)
     for (int i = t; i < max_sweeps; i += JB_THREADS) flags[i] = 0;
@@ -234,10 +245,23 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
         gcol[t] = (g < l) ? g : -1;
       }
       __syncthreads();
-      for (int e = t; e < 4 * U * l; e += JB_THREADS) {
-        const int c = e / (U * l), rem = e % (U * l), lc = rem / l, row = rem % l;
+      for (int lc = warp; lc < U; lc += nwarps) {   // one warp per local column, coalesced rows
         const int g = gcol[lc];
-        S[e] = (g >= 0) ? W[c * ll + (size_t)g * l + row] : (T)0;
+        T v[4][RPL];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            v[c][u] = (g >= 0 && i < l) ? W[c * ll + (size_t)g * l + i] : (T)0;
+          }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < l) col(c, lc)[i] = v[c][u];
+          }
       }
       __syncthreads();
       const int nlr = (br == 0) ? U - 1 : bw;
@@ -253,52 +277,70 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
             if (lane == 0) { lg[0] = (T)-1; lg[1] = (T)-1; lg[2] = (T)1; lg[3] = (T)0; }
             continue;
           }
-          const T* a0 = col(0, a); const T* a1 = col(1, a); const T* a2 = col(2, a); const T* a3 = col(3, a);
-          const T* b0 = col(0, b); const T* b1 = col(1, b); const T* b2 = col(2, b); const T* b3 = col(3, b);
+          T* A0 = col(0, a); T* A1 = col(1, a); T* A2 = col(2, a); T* A3 = col(3, a);
+          T* B0 = col(0, b); T* B1 = col(1, b); T* B2 = col(2, b); T* B3 = col(3, b);
+          Quat<T> wp[RPL], wq[RPL];
           T aa = 0, bb2 = 0;
           Quat<T> g = {0, 0, 0, 0};
-          for (int i = lane; i < l; i += 32) {
-            Quat<T> wp = {a0[i], a1[i], a2[i], a3[i]};
-            Quat<T> wq = {b0[i], b1[i], b2[i], b3[i]};
-            aa += qnorm2(wp);
-            bb2 += qnorm2(wq);
-            Quat<T> pr = qcmul(wp, wq);
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < l) {
+              wp[u] = {A0[i], A1[i], A2[i], A3[i]};
+              wq[u] = {B0[i], B1[i], B2[i], B3[i]};
+            } else {
+              wp[u] = {0, 0, 0, 0};
+              wq[u] = {0, 0, 0, 0};
+            }
+            aa += qnorm2(wp[u]);
+            bb2 += qnorm2(wq[u]);
+            const Quat<T> pr = qcmul(wp[u], wq[u]);
             g.w += pr.w; g.x += pr.x; g.y += pr.y; g.z += pr.z;
           }
           aa = warp_sum(aa); bb2 = warp_sum(bb2);
           g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
-          const T gn = sqrt(qnorm2(g));
-          if (!(gn > tol * sqrt(aa * bb2)) || gn == (T)0) {
+          const T gn2 = qnorm2(g);
+          if (!(gn2 > (tol2 * aa) * bb2)) {      // pair already orthogonal to the tolerance
             if (lane == 0) { lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = (T)1; lg[3] = (T)0; }
             continue;
           }
           if (lane == 0) s_rot = 1;
-          const T ign = (T)1 / gn;
+          const T ign = jrsqrt(gn2);
           const Quat<T> mu = {g.w * ign, g.x * ign, g.y * ign, g.z * ign};
           const T zeta = (bb2 - aa) * ((T)0.5 * ign);
-          const T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          const T c = (T)1 / sqrt((T)1 + tt * tt), sn = c * tt;
+          const T az = fabs(zeta);
+          const T x = (T)1 + az * az;
+          const T den = (az < (T)1e18) ? az + x * jrsqrt(x) : (T)2 * az;
+          const T tt = (zeta >= 0 ? (T)1 : (T)-1) * jrcp(den);
+          const T c = jrsqrt((T)1 + tt * tt), sn = c * tt;
           if (lane == 0) {
             lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = c; lg[3] = sn;
             lg[4] = mu.w; lg[5] = mu.x; lg[6] = mu.y; lg[7] = mu.z;
           }
-          T* A0 = col(0, a); T* A1 = col(1, a); T* A2 = col(2, a); T* A3 = col(3, a);
-          T* B0 = col(0, b); T* B1 = col(1, b); T* B2 = col(2, b); T* B3 = col(3, b);
-          for (int i = lane; i < l; i += 32) {
-            Quat<T> wp = {A0[i], A1[i], A2[i], A3[i]};
-            Quat<T> wq = qmulc(Quat<T>{B0[i], B1[i], B2[i], B3[i]}, mu);
-            A0[i] = c * wp.w - sn * wq.w; A1[i] = c * wp.x - sn * wq.x;
-            A2[i] = c * wp.y - sn * wq.y; A3[i] = c * wp.z - sn * wq.z;
-            B0[i] = sn * wp.w + c * wq.w; B1[i] = sn * wp.x + c * wq.x;
-            B2[i] = sn * wp.y + c * wq.y; B3[i] = sn * wp.z + c * wq.z;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < l) {
+              const Quat<T> q = qmulc(wq[u], mu);
+              A0[i] = c * wp[u].w - sn * q.w; A1[i] = c * wp[u].x - sn * q.x;
+              A2[i] = c * wp[u].y - sn * q.y; A3[i] = c * wp[u].z - sn * q.z;
+              B0[i] = sn * wp[u].w + c * q.w; B1[i] = sn * wp[u].x + c * q.x;
+              B2[i] = sn * wp[u].y + c * q.y; B3[i] = sn * wp[u].z + c * q.z;
+            }
           }
         }
         __syncthreads();
       }
-      for (int e = t; e < 4 * U * l; e += JB_THREADS) {
-        const int c = e / (U * l), rem = e % (U * l), lc = rem / l, row = rem % l;
+      for (int lc = warp; lc < U; lc += nwarps) {
         const int g = gcol[lc];
-        if (g >= 0) W[c * ll + (size_t)g * l + row] = S[e];
+        if (g < 0) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < l) W[c * ll + (size_t)g * l + i] = col(c, lc)[i];
+          }
       }
       __threadfence();
       cluster.sync();
@@ -326,61 +368,95 @@ __global__ void __launch_bounds__(JB_THREADS) jacobi_block_kernel(const double* 
   }
 }
 
-// Replay of the staged rotation log on V = I, one warp per row; the records of a stage touch
-// disjoint columns, so the lanes apply them concurrently.
+// Replay of the staged rotation log on V = I, one warp per row of V.  The log is read in chunks
+// of RCH stages that the CTA's four warps share: each chunk is copied to shared memory with
+// cp.async while the previous one is applied.
+constexpr int RCH = 8;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <class T>
+__device__ __forceinline__ void ld_rec(const T* r, T (&v)[REC]) {
+#pragma unroll
+  for (int f = 0; f < REC; ++f) v[f] = r[f];
+}
+template <>
+__device__ __forceinline__ void ld_rec<float>(const float* r, float (&v)[REC]) {
+  const float4 a = reinterpret_cast<const float4*>(r)[0], b = reinterpret_cast<const float4*>(r)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+size_t jb_replay_smem(int l, int bw, size_t esz) {
+  return (size_t)2 * RCH * JP * bw * REC * esz + (size_t)4 * 4 * l * esz;
+}
+
 template <class T>
 __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw, const T* __restrict__ rlog,
                                                                    const int* __restrict__ nsweeps, T* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int row = blockIdx.x * 4 + warp;
-  T* vr = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 4 * l;
-  if (row >= l) return;
-  for (int j = lane; j < l; j += 32) {
-    vr[j] = (j == row) ? (T)1 : (T)0;
-    vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
-  }
-  __syncwarp();
-  const size_t nst = (size_t)(*nsweeps) * jb_stages_per_sweep(bw);
   const int cap = JP * bw;
-  constexpr int KMAX = 4;   // records per lane and stage (cap <= 128)
-  T cur[KMAX][REC], nxt[KMAX][REC];
-  auto fetch = [&](size_t st, T (&buf)[KMAX][REC]) {
-#pragma unroll
-    for (int u = 0; u < KMAX; ++u) {
-      const int k = lane + 32 * u;
-      if (st < nst && k < cap) {
-        const T* lg = rlog + (st * cap + k) * REC;
-#pragma unroll
-        for (int f = 0; f < REC; ++f) buf[u][f] = __ldg(lg + f);
-      } else {
-        buf[u][3] = (T)0;
+  const size_t stage_elems = (size_t)cap * REC;
+  T* logbuf = reinterpret_cast<T*>(smem_raw);                    // [2][RCH][cap][REC]
+  T* vr = logbuf + 2 * RCH * stage_elems + (size_t)warp * 4 * l;  // this warp's row of V, 4 planes
+  const int row = blockIdx.x * 4 + warp;
+  const bool active = row < l;
+  if (active)
+    for (int j = lane; j < l; j += 32) {
+      vr[j] = (j == row) ? (T)1 : (T)0;
+      vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
+    }
+  const size_t nst = (size_t)(*nsweeps) * jb_stages_per_sweep(bw);
+  const size_t nchunks = (nst + RCH - 1) / RCH;
+  auto stage_chunk = [&](size_t ch) {
+    const size_t s0 = ch * RCH;
+    const size_t ns = (nst - s0 < (size_t)RCH) ? nst - s0 : (size_t)RCH;
+    const size_t bytes = ns * stage_elems * sizeof(T);
+    const char* src = reinterpret_cast<const char*>(rlog + s0 * stage_elems);
+    char* dst = reinterpret_cast<char*>(logbuf + (ch & 1) * RCH * stage_elems);
+    for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16) cp_async16(dst + o, src + o);
+    cp_async_commit();
+  };
+  if (nchunks > 0) stage_chunk(0);
+  for (size_t ch = 0; ch < nchunks; ++ch) {
+    if (ch + 1 < nchunks) {
+      stage_chunk(ch + 1);     // fills the other buffer, released by the barrier that ended chunk ch - 1
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const T* lb = logbuf + (ch & 1) * RCH * stage_elems;
+    const int ns = (int)((nst - ch * RCH < (size_t)RCH) ? nst - ch * RCH : (size_t)RCH);
+    if (active) {
+      for (int st = 0; st < ns; ++st) {
+        for (int k = lane; k < cap; k += 32) {
+          T r[REC];
+          ld_rec(lb + ((size_t)st * cap + k) * REC, r);
+          const T sn = r[3];
+          if (sn == (T)0) continue;
+          const int pp = (int)r[0], qq = (int)r[1];
+          const T c = r[2];
+          const Quat<T> mu = {r[4], r[5], r[6], r[7]};
+          const Quat<T> vp = {vr[pp], vr[l + pp], vr[2 * l + pp], vr[3 * l + pp]};
+          const Quat<T> vq = qmulc(Quat<T>{vr[qq], vr[l + qq], vr[2 * l + qq], vr[3 * l + qq]}, mu);
+          vr[pp] = c * vp.w - sn * vq.w; vr[l + pp] = c * vp.x - sn * vq.x; vr[2 * l + pp] = c * vp.y - sn * vq.y;
+          vr[3 * l + pp] = c * vp.z - sn * vq.z;
+          vr[qq] = sn * vp.w + c * vq.w; vr[l + qq] = sn * vp.x + c * vq.x; vr[2 * l + qq] = sn * vp.y + c * vq.y;
+          vr[3 * l + qq] = sn * vp.z + c * vq.z;
+        }
+        __syncwarp();
       }
     }
-  };
-  fetch(0, cur);
-  for (size_t st = 0; st < nst; ++st) {
-    fetch(st + 1, nxt);                       // next stage's records in flight while this one applies
-#pragma unroll
-    for (int u = 0; u < KMAX; ++u) {
-      const T sn = cur[u][3];
-      if (sn == (T)0) continue;
-      const int pp = (int)cur[u][0], qq = (int)cur[u][1];
-      const T c = cur[u][2];
-      const Quat<T> mu = {cur[u][4], cur[u][5], cur[u][6], cur[u][7]};
-      Quat<T> vp = {vr[pp], vr[l + pp], vr[2 * l + pp], vr[3 * l + pp]};
-      Quat<T> vq = qmulc(Quat<T>{vr[qq], vr[l + qq], vr[2 * l + qq], vr[3 * l + qq]}, mu);
-      vr[pp] = c * vp.w - sn * vq.w; vr[l + pp] = c * vp.x - sn * vq.x; vr[2 * l + pp] = c * vp.y - sn * vq.y;
-      vr[3 * l + pp] = c * vp.z - sn * vq.z;
-      vr[qq] = sn * vp.w + c * vq.w; vr[l + qq] = sn * vp.x + c * vq.x; vr[2 * l + qq] = sn * vp.y + c * vq.y;
-      vr[3 * l + qq] = sn * vp.z + c * vq.z;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < KMAX; ++u)
-#pragma unroll
-      for (int f = 0; f < REC; ++f) cur[u][f] = nxt[u][f];
+    __syncthreads();
   }
+  if (!active) return;
   const size_t ll = (size_t)l * l;
   for (int j = lane; j < l; j += 32)
     for (int c = 0; c < 4; ++c) Vout[c * ll + (size_t)j * l + row] = vr[(size_t)c * l + j];
@@ -464,7 +540,7 @@ constexpr int JBLOCK_MIN_L = 48;     // from this size on, the cluster block Jac
 // lane at most four records per stage; larger cores run the single-CTA sweep.
 static bool use_block_jacobi(int l, size_t esz) {
   const int bw = (l + 2 * JP - 1) / (2 * JP);
-  return l >= JBLOCK_MIN_L && (size_t)4 * l * 2 * bw * esz <= 220 * 1024 && JP * bw <= 128;
+  return l >= JBLOCK_MIN_L && l <= 256 && (size_t)4 * l * 2 * bw * esz <= 220 * 1024 && JP * bw <= 128;
 }
 
 size_t jacobi_log_floats(int l) {
@@ -492,7 +568,8 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   if (blockj) {
     const int bw = (l + 2 * JP - 1) / (2 * JP);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
-    QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = (l <= 128) ? jacobi_block_kernel<T, 4> : jacobi_block_kernel<T, 8>;
+    QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(JP, 1, 1);
     cfg.blockDim = dim3(JB_THREADS, 1, 1);
@@ -507,12 +584,12 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     cfg.numAttrs = 1;
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
-      QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_block_kernel<T>, R, l, bw, W, (int)JMAX_SWEEPS, tol, rlog, flags,
-                                      sweeps, sig, ctx->d_err));
+      QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, R, l, bw, W, (int)JMAX_SWEEPS, tol, rlog, flags, sweeps, sig,
+                                      ctx->d_err));
     }
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
-      const size_t rs = (size_t)4 * 4 * l * sizeof(T);
+      const size_t rs = jb_replay_smem(l, bw, sizeof(T));
       if (rs > 48 * 1024)
         QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
       jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, rlog, sweeps, V);

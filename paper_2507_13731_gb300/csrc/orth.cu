@@ -3,7 +3,12 @@
 // Q' = Y R1^{-1}, then once more on Q'; R = R2 R1.  Shifted CholeskyQR3 (Fukaya, Kannan,
 // Nakatsukasa, Zhang and Yamamoto, SISC 2020) adds s I to the first Gram matrix so the
 // Cholesky factorisation exists for ill-conditioned input (Algorithm 4's stacked basis).
+#include <cooperative_groups.h>
+#include <mutex>
+
 #include "qlr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -104,19 +109,42 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunks,
 }
 
 // C = A B for small l x l quaternion matrices (FP64), A and B upper triangular.
-__global__ void small_matmul_kernel(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
-                                    int l) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)l * l) return;
-  int i = (int)(idx % l), j = (int)(idx / l);
-  Quat<double> s = {0, 0, 0, 0};
-  for (int t = i; t <= j; ++t) {
-    Quat<double> p = qmul(ld_small(A, l, i, t), ld_small(B, l, t, j));
-    s.w += p.w; s.x += p.x; s.y += p.y; s.z += p.z;
-  }
-  st_small(C, l, i, j, s);
-}
+constexpr int MM_SPLIT = 8;   // lanes sharing one output entry of small_matmul_kernel
 
+__global__ void __launch_bounds__(128) small_matmul_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                            double* __restrict__ C, int l) {
+  // C = A B for upper-triangular A, B: only entries i <= j, each the sum over i <= t <= j split
+  // across MM_SPLIT lanes so the FP64 work is spread evenly over all SMs; C's lower part is zero.
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ent = gt / MM_SPLIT;
+  const int part = (int)(gt % MM_SPLIT);
+  const int64_t nent = (int64_t)l * (l + 1) / 2;
+  const bool valid = ent < nent;
+  int i = 0, j = 0;
+  if (valid) {
+    const int2 ij = upper_tri_entry((int)ent);
+    i = ij.x;
+    j = ij.y;
+  }
+  Quat<double> s = {0, 0, 0, 0};
+  if (valid) {
+#pragma unroll 4
+    for (int t = i + part; t <= j; t += MM_SPLIT) {
+      const Quat<double> p = qmul(ld_small(A, l, i, t), ld_small(B, l, t, j));
+      s.w += p.w; s.x += p.x; s.y += p.y; s.z += p.z;
+    }
+  }
+#pragma unroll
+  for (int o = MM_SPLIT / 2; o > 0; o >>= 1) {
+    s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+  }
+  if (!valid || part != 0) return;
+  st_small(C, l, i, j, s);
+  if (i < j) st_small(C, l, j, i, Quat<double>{0, 0, 0, 0});
+}
 
 // ---------------------------------------------------------------------------------------
 // FP64-class Gram of FP32 data on the FP32 pipes (GB300 runs FP64 at 1/64 of the FP32 rate).
@@ -340,6 +368,203 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm,
       R[c * ll + (size_t)(j0 + j) * l + j0 + i] = (i <= j) ? D[c][i][j] : 0.0;
       Dinv[(size_t)c * b * b + (size_t)j * b + i] = (i <= j) ? X[c][i][j] : 0.0;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Cholesky factorisation of the whole l x l FP64 Gram in one thread-block cluster (NC CTAs,
+// 8 or 16).  FP64 runs at a small fraction of the FP32 rate on every SM, so the work has to be
+// spread over several SMs, and a chain of one launch per block column spends most of its time
+// between kernels.  Here the upper triangle stays in shared memory, column k owned by CTA k mod NC
+// (rows 0..k, quaternions stored plane-interleaved).  Column step j: every CTA reads row j from
+// the owners through distributed shared memory and scales it by 1/r_jj (this is row j of R),
+// updates row j + 1 of its columns, and the owner of column j + 1 takes that pivot; the CTAs then
+// arrive at the cluster barrier and do the rest of the rank-1 update (rows >= j + 2) before
+// waiting on it, so the bulk FP64 work overlaps the barrier (other CTAs only read row j + 1 next).  At the end each CTA inverts some of
+// the CB x CB diagonal blocks of R for the blocked triangular inverse.
+constexpr int CC_THREADS = 256;
+
+__host__ __device__ __forceinline__ int cc_nown(int l, int nc, int c) { return c < l ? (l - c + nc - 1) / nc : 0; }
+// Offset (in quaternions) of the first stored row of column k = c + idx * nc in CTA c.
+__host__ __device__ __forceinline__ int cc_colstart(int nc, int c, int idx) { return idx * (c + 1) + nc * idx * (idx - 1) / 2; }
+__host__ __device__ __forceinline__ size_t cc_smem(int l, int nc) {
+  int mx = 0;
+  for (int c = 0; c < nc; ++c) {
+    const int n = cc_nown(l, nc, c);
+    const int tot = cc_colstart(nc, c, n);
+    mx = tot > mx ? tot : mx;
+  }
+  return (size_t)mx * 32 + (size_t)l * 32 + (size_t)2 * l * 8;   // columns, gathered row, pivots
+}
+
+__device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
+
+// X = D^{-1} for an upper-triangular b x b quaternion block D with real positive diagonal (dense
+// lanes, column-oriented back substitution on all right-hand sides; X starts as the identity).
+__device__ void cc_block_inverse(double (&D)[4][CB][CB], double (&X)[4][CB][CB], double* rpiv, int b) {
+  const int t = threadIdx.x;
+  for (int e = t; e < CB * CB; e += blockDim.x) {
+    const int i = e % CB, j = e / CB;
+    X[0][i][j] = (i == j && i < b) ? 1.0 : 0.0;
+    X[1][i][j] = X[2][i][j] = X[3][i][j] = 0.0;
+  }
+  if (t < b) rpiv[t] = 1.0 / D[0][t][t];
+  __syncthreads();
+  for (int i = b - 1; i >= 0; --i) {
+    const int w = b - i;
+    if (t < 4 * w) {
+      const int c = t / w, j = i + t % w;
+      X[c][i][j] *= rpiv[i];
+    }
+    __syncthreads();
+    for (int e = t; e < i * w; e += blockDim.x) {
+      const int r = e % i, j = i + e / i;
+      Quat<double> pr = qmul(Quat<double>{D[0][r][i], D[1][r][i], D[2][r][i], D[3][r][i]},
+                             Quat<double>{X[0][i][j], X[1][i][j], X[2][i][j], X[3][i][j]});
+      X[0][r][j] -= pr.w; X[1][r][j] -= pr.x; X[2][r][j] -= pr.y; X[3][r][j] -= pr.z;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const double* __restrict__ G, double* __restrict__ R,
+                                                                     double* __restrict__ Dinv_all, int l, double shift_coef,
+                                                                     int* err, const int* run_if) {
+  if (run_if && *run_if == 0) return;           // the same decision in every CTA of the cluster
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int nc = (int)cluster.num_blocks();
+  const int c = (int)cluster.block_rank();
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = CC_THREADS / 32;
+  const size_t ll = (size_t)l * l;
+  const int nown = cc_nown(l, nc, c);
+  double4* Wc = reinterpret_cast<double4*>(smem_raw);                  // own columns
+  const int wtot = cc_colstart(nc, c, nown);
+  int mxtot = 0;
+  for (int cc = 0; cc < nc; ++cc) mxtot = max(mxtot, cc_colstart(nc, cc, cc_nown(l, nc, cc)));
+  double4* g = Wc + mxtot;                                               // gathered row of R
+  double* s_piv = reinterpret_cast<double*>(g + l);
+  double* s_rpiv = s_piv + l;
+  (void)wtot;
+
+  // shift s = shift_coef * trace(G) on the diagonal
+  __shared__ double s_shift;
+  if (warp == 0) {
+    double tr = 0.0;
+    for (int i = lane; i < l; i += 32) tr += G[(size_t)i * l + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (lane == 0) s_shift = shift_coef * tr;
+  }
+  __syncthreads();
+  for (int idx = warp; idx < nown; idx += nwarps) {
+    const int k = c + idx * nc;
+    double4* col = Wc + cc_colstart(nc, c, idx);
+    for (int i = lane; i <= k; i += 32) {
+      const size_t o = (size_t)k * l + i;
+      double4 q = make_double4(G[o], G[ll + o], G[2 * ll + o], G[3 * ll + o]);
+      if (i == k) q.x += s_shift;
+      col[i] = q;
+    }
+    for (int i = k + 1 + lane; i < l; i += 32)   // lower part of R is zero
+      for (int cp = 0; cp < 4; ++cp) R[cp * ll + (size_t)k * l + i] = 0.0;
+  }
+  __syncthreads();
+  auto take_pivot = [&](int j) {               // owner of column j, one thread
+    const int idx = j / nc;
+    double d = Wc[cc_colstart(nc, c, idx) + j].x;
+    if (!(d > 0.0)) {
+      qlr_set_error(err, QLR_ENOTPD);
+      d = 1e-300;
+    }
+    const double piv = sqrt(d);
+    s_piv[j] = piv;
+    s_rpiv[j] = 1.0 / piv;
+    const size_t o = (size_t)j * l + j;
+    R[o] = piv; R[ll + o] = 0.0; R[2 * ll + o] = 0.0; R[3 * ll + o] = 0.0;
+  };
+  if (c == 0 && t == 0 && l > 0) take_pivot(0);
+  cluster.sync();
+
+  for (int j = 0; j < l; ++j) {
+    const int oj = j % nc;
+    const double rp = *cluster.map_shared_rank(s_rpiv + j, oj);
+    // row j of R: g[i] = W[j][i] / r_jj for i > j, read from each column's owner
+    for (int i = j + 1 + t; i < l; i += CC_THREADS) {
+      const int oi = i % nc, idx = i / nc;
+      const double4 q = *cluster.map_shared_rank(Wc + cc_colstart(nc, oi, idx) + j, oi);
+      const double4 r = make_double4(q.x * rp, q.y * rp, q.z * rp, q.w * rp);
+      g[i] = r;
+      if (oi == c) {
+        const size_t o = (size_t)i * l + j;
+        R[o] = r.x; R[ll + o] = r.y; R[2 * ll + o] = r.z; R[3 * ll + o] = r.w;
+      }
+    }
+    __syncthreads();
+    // look-ahead: row j + 1 of the own columns k >= j + 1, then the next pivot
+    const int j1 = j + 1;
+    if (j1 < l) {
+      const double4 gi = g[j1];
+      const int idx0 = (j1 - c + nc - 1) / nc;   // first own column index with k >= j + 1
+      for (int idx = idx0 + t; idx < nown; idx += CC_THREADS) {
+        const int k = c + idx * nc;
+        const double4 gk = g[k];
+        double4& w = Wc[cc_colstart(nc, c, idx) + j1];
+        const Quat<double> pr = qcmul(Quat<double>{gi.x, gi.y, gi.z, gi.w}, Quat<double>{gk.x, gk.y, gk.z, gk.w});
+        w.x -= pr.w; w.y -= pr.x; w.z -= pr.y; w.w -= pr.z;
+      }
+      __syncthreads();
+      if (c == j1 % nc && t == 0) take_pivot(j1);
+    }
+    __syncwarp();
+    cluster_arrive_release();
+    // bulk of the rank-1 update: rows j + 2 .. k of the own columns k >= j + 2
+    const int j2 = j + 2;
+    if (j2 < l) {
+      const int idx0 = (j2 - c + nc - 1) / nc;
+      for (int idx = idx0 + warp; idx < nown; idx += nwarps) {
+        const int k = c + idx * nc;
+        const double4 gk = g[k];
+        const Quat<double> qk = {gk.x, gk.y, gk.z, gk.w};
+        double4* col = Wc + cc_colstart(nc, c, idx);
+        for (int i = j2 + lane; i <= k; i += 32) {
+          const double4 gi = g[i];
+          const Quat<double> pr = qcmul(Quat<double>{gi.x, gi.y, gi.z, gi.w}, qk);
+          double4 w = col[i];
+          w.x -= pr.w; w.y -= pr.x; w.z -= pr.y; w.w -= pr.z;
+          col[i] = w;
+        }
+      }
+    }
+    // the barrier completes once every thread has arrived, not once every thread has finished
+    // its share of the bulk update: the CTA's own threads must finish reading g and writing the
+    // columns before any of them starts the next step
+    __syncthreads();
+    cluster_wait_acquire();
+  }
+  __threadfence();
+  cluster.sync();
+  // inverses of the diagonal blocks (block J = rows / columns [J CB, J CB + b))
+  __shared__ double D[4][CB][CB];
+  __shared__ double X[4][CB][CB];
+  __shared__ double rpv[CB];
+  const int nblk = (l + CB - 1) / CB;
+  for (int J = c; J < nblk; J += nc) {
+    const int j0 = J * CB, b = min(CB, l - j0);
+    for (int e = t; e < CB * CB; e += blockDim.x) {
+      const int i = e % CB, jj = e / CB;
+      for (int cp = 0; cp < 4; ++cp)
+        D[cp][i][jj] = (i < b && jj < b && i <= jj) ? __ldcg(R + cp * ll + (size_t)(j0 + jj) * l + j0 + i) : 0.0;
+    }
+    __syncthreads();
+    cc_block_inverse(D, X, rpv, b);
+    double* Dinv = Dinv_all + (size_t)J * 4 * CB * CB;
+    for (int e = t; e < b * b; e += blockDim.x) {
+      const int i = e % b, jj = e / b;
+      for (int cp = 0; cp < 4; ++cp) Dinv[(size_t)cp * b * b + (size_t)jj * b + i] = (i <= jj) ? X[cp][i][jj] : 0.0;
+    }
+    __syncthreads();
   }
 }
 
@@ -703,10 +928,71 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   return QLR_OK;
 }
 
+// Cluster size for chol_cluster_kernel at this shared-memory size: 16 (non-portable) when the
+// device can co-schedule it, else 8; 0 when neither fits.
+static int cluster_chol_size(int device, int l) {
+  static std::mutex mu;
+  static std::vector<std::pair<int64_t, int>> cache;   // (device << 32 | l) -> cluster size
+  std::lock_guard<std::mutex> lk(mu);
+  const int64_t key = ((int64_t)device << 32) | (uint32_t)l;
+  for (const auto& e : cache)
+    if (e.first == key) return e.second;
+  const bool allowed =
+      cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  cudaGetLastError();
+  int pick = 0;
+  for (int nc : {16, 8}) {
+    if (nc == 16 && !allowed) continue;
+    const size_t smem = cc_smem(l, nc);
+    if (smem > 200 * 1024) continue;
+    if (cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc, 1, 1);
+    cfg.blockDim = dim3(CC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, chol_cluster_kernel, &cfg) == cudaSuccess && ncl > 0) {
+      pick = nc;
+      break;
+    }
+    cudaGetLastError();
+  }
+  cache.emplace_back(key, pick);
+  return pick;
+}
+
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsArena& ws, double* Dinv_all,
          const int* run_if) {
   if (l == 0) return QLR_OK;
   const size_t ll4 = (size_t)4 * l * l;
+  const int nc = (l > CB) ? cluster_chol_size(ctx->device, l) : 0;
+  if (nc > 0 && Dinv_all != nullptr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc, 1, 1);
+    cfg.blockDim = dim3(CC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = cc_smem(l, nc);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    KTimer kt(ctx, QLR_KID_CHOL);
+    QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, chol_cluster_kernel, G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if));
+    return QLR_OK;
+  }
   size_t mark = ws.off;
   double* Wm = ws.take<double>(ll4);
   const int npan = (l + CB - 1) / CB;
@@ -752,9 +1038,9 @@ int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Di
 }
 
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C) {
-  int64_t tot = (int64_t)l * l;
+  const int64_t thr = (int64_t)l * (l + 1) / 2 * MM_SPLIT;
   KTimer kt(ctx, QLR_KID_MISC);
-  small_matmul_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(A, B, C, l);
+  small_matmul_kernel<<<(unsigned)((thr + 127) / 128), 128, 0, ctx->stream>>>(A, B, C, l);
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
