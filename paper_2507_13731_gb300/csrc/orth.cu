@@ -376,11 +376,12 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(double* __restrict__ Wm,
 // 8 or 16).  FP64 runs at a small fraction of the FP32 rate on every SM, so the work has to be
 // spread over several SMs, and a chain of one launch per block column spends most of its time
 // between kernels.  Here the upper triangle stays in shared memory, column k owned by CTA k mod NC
-// (rows 0..k, quaternions stored plane-interleaved).  Column step j: every CTA reads row j from
-// the owners through distributed shared memory and scales it by 1/r_jj (this is row j of R),
-// updates row j + 1 of its columns, and the owner of column j + 1 takes that pivot; the CTAs then
-// arrive at the cluster barrier and do the rest of the rank-1 update (rows >= j + 2) before
-// waiting on it, so the bulk FP64 work overlaps the barrier (other CTAs only read row j + 1 next).  At the end each CTA inverts some of
+// (rows 0..k, quaternions stored plane-interleaved).  Column step j: every CTA scales row j, which
+// the column owners pushed into its shared memory during step j - 1, by 1/r_jj (this is row j of
+// R); it then updates row j + 1 of its own columns and pushes those entries to every CTA through
+// distributed shared memory, and the owner of column j + 1 takes and pushes that pivot.  The CTAs
+// then arrive at the cluster barrier and do the rest of the rank-1 update (rows >= j + 2) before
+// waiting on it, so the bulk FP64 work overlaps the barrier and no remote load sits on the path.  At the end each CTA inverts some of
 // the CB x CB diagonal blocks of R for the blocked triangular inverse.
 constexpr int CC_THREADS = 256;
 
@@ -394,7 +395,7 @@ __host__ __device__ __forceinline__ size_t cc_smem(int l, int nc) {
     const int tot = cc_colstart(nc, c, n);
     mx = tot > mx ? tot : mx;
   }
-  return (size_t)mx * 32 + (size_t)l * 32 + (size_t)2 * l * 8;   // columns, gathered row, pivots
+  return (size_t)mx * 32 + (size_t)4 * l * 32 + (size_t)l * 8;   // columns, h, three pushed rows, pivots
 }
 
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
@@ -428,6 +429,26 @@ __device__ void cc_block_inverse(double (&D)[4][CB][CB], double (&X)[4][CB][CB],
   }
 }
 
+// w - conj(a) b for quaternions stored as (real, i, j, k) in double4, four fused multiply-adds
+// per component.
+__device__ __forceinline__ double4 qcfms(double4 w, const double4 a, const double4 b) {
+  w.x = fma(-a.x, b.x, w.x); w.x = fma(-a.y, b.y, w.x); w.x = fma(-a.z, b.z, w.x); w.x = fma(-a.w, b.w, w.x);
+  w.y = fma(-a.x, b.y, w.y); w.y = fma(a.y, b.x, w.y);  w.y = fma(a.z, b.w, w.y);  w.y = fma(-a.w, b.z, w.y);
+  w.z = fma(-a.x, b.z, w.z); w.z = fma(-a.y, b.w, w.z); w.z = fma(a.z, b.x, w.z);  w.z = fma(a.w, b.y, w.z);
+  w.w = fma(-a.x, b.w, w.w); w.w = fma(a.y, b.z, w.w);  w.w = fma(-a.z, b.y, w.w); w.w = fma(a.w, b.x, w.w);
+  return w;
+}
+
+// 1 / sqrt(d) in FP64: the FP32 hardware estimate refined by two Newton-Raphson steps
+// y <- y (3 - d y^2) / 2 (each squares the relative error: 2^-22 -> 2^-43 -> below FP64 rounding).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  y = y * fma(-0.5 * d * y, y, 1.5);
+  y = y * fma(-0.5 * d * y, y, 1.5);
+  return y;
+}
+
 __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const double* __restrict__ G, double* __restrict__ R,
                                                                      double* __restrict__ Dinv_all, int l, double shift_coef,
                                                                      int* err, const int* run_if) {
@@ -439,14 +460,16 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = CC_THREADS / 32;
   const size_t ll = (size_t)l * l;
   const int nown = cc_nown(l, nc, c);
-  double4* Wc = reinterpret_cast<double4*>(smem_raw);                  // own columns
-  const int wtot = cc_colstart(nc, c, nown);
   int mxtot = 0;
   for (int cc = 0; cc < nc; ++cc) mxtot = max(mxtot, cc_colstart(nc, cc, cc_nown(l, nc, cc)));
-  double4* g = Wc + mxtot;                                               // gathered row of R
-  double* s_piv = reinterpret_cast<double*>(g + l);
-  double* s_rpiv = s_piv + l;
-  (void)wtot;
+  double4* Wc = reinterpret_cast<double4*>(smem_raw);       // own columns (rows 0..k)
+  double4* g = Wc + mxtot;                                    // h_k of the own columns (below)
+  // [3][l]: rows j of W pushed by the column owners.  Step j reads buffer j mod 3 and fills
+  // (j + 1) mod 3 in the other CTAs, one of which may still be in step j - 1's bulk update
+  // (reading (j - 1) mod 3) -- never further behind, since it has arrived at step j - 1's barrier.
+  double4* rowbuf = g + l;
+  double* s_rp = reinterpret_cast<double*>(rowbuf + 3 * l);   // 1 / r_jj, pushed by the pivot owner
+  cluster.sync();   // every CTA of the cluster is running before any distributed shared memory access
 
   // shift s = shift_coef * trace(G) on the diagonal
   __shared__ double s_shift;
@@ -466,82 +489,98 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
       double4 q = make_double4(G[o], G[ll + o], G[2 * ll + o], G[3 * ll + o]);
       if (i == k) q.x += s_shift;
       col[i] = q;
+      if (i == 0 && k > 0)                         // row 0 to every CTA
+        for (int r = 0; r < nc; ++r) *cluster.map_shared_rank(rowbuf + k, r) = q;
     }
     for (int i = k + 1 + lane; i < l; i += 32)   // lower part of R is zero
       for (int cp = 0; cp < 4; ++cp) R[cp * ll + (size_t)k * l + i] = 0.0;
   }
   __syncthreads();
+  // R is built in place: once row j has been pushed, W[j][k] of an own column is dead and its slot
+  // takes R[j][k]; R goes to global memory once at the end, so the barrier's release does not
+  // wait on global stores.
   auto take_pivot = [&](int j) {               // owner of column j, one thread
-    const int idx = j / nc;
-    double d = Wc[cc_colstart(nc, c, idx) + j].x;
+    double4& wjj = Wc[cc_colstart(nc, c, j / nc) + j];
+    double d = wjj.x;
     if (!(d > 0.0)) {
       qlr_set_error(err, QLR_ENOTPD);
       d = 1e-300;
     }
-    const double piv = sqrt(d);
-    s_piv[j] = piv;
-    s_rpiv[j] = 1.0 / piv;
-    const size_t o = (size_t)j * l + j;
-    R[o] = piv; R[ll + o] = 0.0; R[2 * ll + o] = 0.0; R[3 * ll + o] = 0.0;
+    const double rp = rsqrt_newton(d);
+    for (int r = 0; r < nc; ++r) *cluster.map_shared_rank(s_rp + j, r) = rp;
+    wjj = make_double4(d * rp, 0.0, 0.0, 0.0);
   };
   if (c == 0 && t == 0 && l > 0) take_pivot(0);
   cluster.sync();
 
+  // With the raw pushed row W[j][.] and h_k = W[j][k] / r_jj^2 for the own columns, the rank-1
+  // update is W[i][k] -= conj(W[j][i]) h_k: only the CTA's own entries of row j are scaled.
+  double4* h = g;
   for (int j = 0; j < l; ++j) {
-    const int oj = j % nc;
-    const double rp = *cluster.map_shared_rank(s_rpiv + j, oj);
-    // row j of R: g[i] = W[j][i] / r_jj for i > j, read from each column's owner
-    for (int i = j + 1 + t; i < l; i += CC_THREADS) {
-      const int oi = i % nc, idx = i / nc;
-      const double4 q = *cluster.map_shared_rank(Wc + cc_colstart(nc, oi, idx) + j, oi);
-      const double4 r = make_double4(q.x * rp, q.y * rp, q.z * rp, q.w * rp);
-      g[i] = r;
-      if (oi == c) {
-        const size_t o = (size_t)i * l + j;
-        R[o] = r.x; R[ll + o] = r.y; R[2 * ll + o] = r.z; R[3 * ll + o] = r.w;
-      }
+    const double rp = s_rp[j], rp2 = rp * rp;
+    const double4* row = rowbuf + (j % 3) * l;
+    const int j1 = j + 1;
+    const int idx0 = (j1 - c + nc - 1) / nc;   // first own column index with k >= j + 1
+    const int nact = nown - idx0;
+    if (t < nact) {                            // R[j][k], h_k and the look-ahead row j + 1
+      const int idx = idx0 + t, k = c + idx * nc;
+      const double4 q = row[k];
+      double4* col = Wc + cc_colstart(nc, c, idx);
+      col[j] = make_double4(q.x * rp, q.y * rp, q.z * rp, q.w * rp);
+      const double4 hk = make_double4(q.x * rp2, q.y * rp2, q.z * rp2, q.w * rp2);
+      h[k] = hk;
+      col[j1] = qcfms(col[j1], row[j1], hk);
     }
     __syncthreads();
-    // look-ahead: row j + 1 of the own columns k >= j + 1, then the next pivot
-    const int j1 = j + 1;
     if (j1 < l) {
-      const double4 gi = g[j1];
-      const int idx0 = (j1 - c + nc - 1) / nc;   // first own column index with k >= j + 1
-      for (int idx = idx0 + t; idx < nown; idx += CC_THREADS) {
-        const int k = c + idx * nc;
-        const double4 gk = g[k];
-        double4& w = Wc[cc_colstart(nc, c, idx) + j1];
-        const Quat<double> pr = qcmul(Quat<double>{gi.x, gi.y, gi.z, gi.w}, Quat<double>{gk.x, gk.y, gk.z, gk.w});
-        w.x -= pr.w; w.y -= pr.x; w.z -= pr.y; w.w -= pr.z;
-      }
-      __syncthreads();
       if (c == j1 % nc && t == 0) take_pivot(j1);
+      double4* nrow = rowbuf + (j1 % 3) * l;
+      for (int e = t; e < nact * nc; e += CC_THREADS) {   // push row j + 1 of the own columns
+        const int idx = idx0 + e / nc, r = e % nc, k = c + idx * nc;
+        if (k > j1) *cluster.map_shared_rank(nrow + k, r) = Wc[cc_colstart(nc, c, idx) + j1];
+      }
     }
     __syncwarp();
     cluster_arrive_release();
-    // bulk of the rank-1 update: rows j + 2 .. k of the own columns k >= j + 2
+    // bulk of the rank-1 update: rows j + 2 .. k of the own columns k >= j + 2, the (column, row)
+    // items numbered consecutively over all threads so FP64 warps run full.  Column m (from the
+    // first one, k_0 >= j + 2) has L_0 + m nc rows; item e lies in the column m with
+    // P(m) <= e < P(m + 1), P(m) = m L_0 + nc m (m - 1) / 2.
     const int j2 = j + 2;
     if (j2 < l) {
-      const int idx0 = (j2 - c + nc - 1) / nc;
-      for (int idx = idx0 + warp; idx < nown; idx += nwarps) {
-        const int k = c + idx * nc;
-        const double4 gk = g[k];
-        const Quat<double> qk = {gk.x, gk.y, gk.z, gk.w};
-        double4* col = Wc + cc_colstart(nc, c, idx);
-        for (int i = j2 + lane; i <= k; i += 32) {
-          const double4 gi = g[i];
-          const Quat<double> pr = qcmul(Quat<double>{gi.x, gi.y, gi.z, gi.w}, qk);
-          double4 w = col[i];
-          w.x -= pr.w; w.y -= pr.x; w.z -= pr.y; w.w -= pr.z;
-          col[i] = w;
+      const int jdx0 = (j2 - c + nc - 1) / nc;
+      const int ncol = nown - jdx0;
+      if (ncol > 0) {
+        const int L0 = c + jdx0 * nc - j2 + 1;
+        const int total = ncol * L0 + nc * ncol * (ncol - 1) / 2;
+        const float hb = (float)L0 - 0.5f * (float)nc;
+        for (int e = t; e < total; e += CC_THREADS) {
+          int m = (int)((-hb + sqrtf(hb * hb + 2.0f * (float)nc * (float)e)) / (float)nc);
+          m = max(0, min(m, ncol - 1));
+          while (m > 0 && m * L0 + nc * m * (m - 1) / 2 > e) --m;
+          while (m + 1 < ncol && (m + 1) * L0 + nc * (m + 1) * m / 2 <= e) ++m;
+          const int i = j2 + e - (m * L0 + nc * m * (m - 1) / 2);
+          const int idx = jdx0 + m, k = c + idx * nc;
+          double4& w = Wc[cc_colstart(nc, c, idx) + i];
+          w = qcfms(w, row[i], h[k]);
         }
       }
     }
     // the barrier completes once every thread has arrived, not once every thread has finished
-    // its share of the bulk update: the CTA's own threads must finish reading g and writing the
+    // its share of the bulk update: the CTA's own threads must finish reading h and writing the
     // columns before any of them starts the next step
     __syncthreads();
     cluster_wait_acquire();
+  }
+  cluster.sync();   // last distributed shared memory access done before any CTA moves on
+  for (int idx = warp; idx < nown; idx += nwarps) {
+    const int k = c + idx * nc;
+    const double4* col = Wc + cc_colstart(nc, c, idx);
+    for (int i = lane; i <= k; i += 32) {
+      const double4 r = col[i];
+      const size_t o = (size_t)k * l + i;
+      R[o] = r.x; R[ll + o] = r.y; R[2 * ll + o] = r.z; R[3 * ll + o] = r.w;
+    }
   }
   __threadfence();
   cluster.sync();
