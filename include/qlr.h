@@ -76,6 +76,9 @@ extern "C" {
  * on its column space, so the result is the same in exact arithmetic.  The QR factors whose Q or R
  * reach U, S, V always use opts.orth. */
 #define QLR_FLAG_QR_EVERY_PASS 1
+/* opts.flags bit for batch plans: enqueue every kernel on each run instead of replaying the
+ * CUDA graph captured at creation (ignored by the single-problem calls). */
+#define QLR_FLAG_NO_GRAPH 2
 
 typedef struct {
   void* plane[4];  /* device pointers: planes real, i, j, k; plane[0] == NULL => pure quaternion */
@@ -90,7 +93,7 @@ typedef struct {
   int32_t compute; /* QLR_COMPUTE_*; AUTO picks from A's dtype                                  */
   int32_t side;    /* QLR_SIDE_*; AUTO applies Section 6's rule (even v and n > m: use X^H)     */
   int32_t orth;    /* QLR_ORTH_*; Algorithm 4's stacked basis always uses QLR_ORTH_SCHOLQR3    */
-  int32_t flags;   /* 0 or QLR_FLAG_QR_EVERY_PASS                                               */
+  int32_t flags;   /* 0 or a combination of QLR_FLAG_QR_EVERY_PASS and QLR_FLAG_NO_GRAPH        */
 } qlr_opts;
 
 typedef struct qlr_ctx qlr_ctx;
@@ -209,14 +212,48 @@ int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes,
                       const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V);
 
 /*
- * qlr_qsvd_lowrank_batched -- `count` independent Algorithm 2 problems of uneven sizes.  Arrays
- * (host) of `count` descriptors / values; S[i] is a device FP64 buffer of k[i] values.  Each
- * sketch pass of all problems runs as one grouped persistent launch; the whole v-pass sequence
- * is captured once into a CUDA graph per (context, problem set) and replayed.
+ * qlr_qsvd_lowrank_batched -- `count` independent Algorithm 2 problems of uneven sizes (the
+ * paper's patches / frames setting).  Arrays (host) of `count` descriptors / values; S[i] is a
+ * device FP64 buffer of k[i] values; every problem runs on the side X.  When every A[i] is BF16
+ * (or FP32 with a TF32 compute mode) with a 16-byte multiple row pitch and 16-byte aligned planes,
+ * Omega[i], U[i], V[i] are FP32, the call builds a batch plan (below) without tuning or graph,
+ * runs it once and frees it; otherwise it loops over qlr_qsvd_lowrank.
  */
 int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p,
                              int passes, const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U,
                              double* const* S, qlr_qmat* V);
+
+/*
+ * Batch plans: the batched Algorithm 2 above, planned once and run many times.
+ *
+ * qlr_batch_create -- checks and plans `count` problems (conditions as above; compute AUTO means
+ * BF16 for BF16 A and 3xTF32 for FP32 A; side must be AUTO or X).  Each sketch pass of all the
+ * problems is one grouped tensor-core launch over every output tile (plus one grouped staging
+ * launch); the per-problem orthonormalisations, core QSVDs and lifts run on up to 32 side
+ * streams forked from and joined to the context stream.  At creation the plan allocates its
+ * device memory (cudaMalloc), times the two tile orders of the grouped sketch and keeps the
+ * faster (the autotuner), runs the whole sequence once (its results are valid), and captures it
+ * into a CUDA graph unless opts.flags has QLR_FLAG_NO_GRAPH.  The pointers in A, omega, U, S, V
+ * are baked into the plan: later runs read and write the same buffers.
+ * qlr_batch_run -- enqueues one run on the context stream (asynchronous; errors of the device
+ * side show in qlr_sync).  qlr_batch_info -- plan facts.  qlr_batch_destroy -- synchronises and
+ * frees the plan (b may be NULL).
+ */
+typedef struct qlr_batch qlr_batch;
+typedef struct {
+  int32_t lanes;           /* side streams                                              */
+  int32_t graph;           /* 1 when runs replay the captured CUDA graph               */
+  int32_t tile_order;      /* grouped sketch tile order chosen: 0 problem order, 1 longest first */
+  int32_t sketch_launches; /* grouped launches per run (staging + sketch per pass)     */
+  float tune_ms[2];        /* autotuner: N + H sketch time of each tile order (ms)    */
+  int64_t launches_per_run;/* kernels launched per run (all streams)                  */
+} qlr_batch_stats;
+int qlr_batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
+                     const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V,
+                     qlr_batch** out);
+int qlr_batch_run(qlr_batch* b);
+int qlr_batch_info(const qlr_batch* b, qlr_batch_stats* st);
+int qlr_batch_destroy(qlr_batch* b);
 
 /*
  * qlr_residual_norm -- measurement pass (not one of the method's passes): estimate

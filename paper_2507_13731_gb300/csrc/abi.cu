@@ -13,6 +13,25 @@
 
 #include "qlr_internal.h"
 
+namespace qlr {
+size_t gram_ws_bound(int64_t l) {
+  size_t per = (size_t)32 * l * l;
+  size_t cap = std::max<size_t>(per, (size_t)64 << 20);
+  return cap + (size_t)8 * ((l + 31) / 32) * ((l + 31) / 32) + 4096;
+}
+
+size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
+  return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 16 * 256;
+}
+
+size_t tsvd_ws_bound(int64_t l) { return core_tsvd_ws((int)l) + 16384; }
+
+}  // namespace qlr
+
+using qlr::cholqr_ws_bound;
+using qlr::gram_ws_bound;
+using qlr::tsvd_ws_bound;
+
 namespace {
 
 struct DeviceGuard {
@@ -51,18 +70,6 @@ bool valid_compute(int c) { return c >= QLR_COMPUTE_F64 && c <= QLR_COMPUTE_BF16
 
 // Thin-matrix dtype used by the scheduler for a compute mode.
 int thin_dtype(int compute) { return compute == QLR_COMPUTE_F64 ? QLR_F64 : QLR_F32; }
-
-size_t gram_ws_bound(int64_t l) {
-  size_t per = (size_t)32 * l * l;
-  size_t cap = std::max<size_t>(per, (size_t)64 << 20);
-  return cap + (size_t)8 * ((l + 31) / 32) * ((l + 31) / 32) + 4096;
-}
-
-size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
-  return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 16 * 256;
-}
-
-size_t tsvd_ws_bound(int64_t l) { return qlr::core_tsvd_ws((int)l) + 16384; }
 
 // ---------------------------------------------------------------------------------------
 struct Sched {
@@ -133,7 +140,7 @@ int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr
   if (!ctx) return QLR_EINVAL;
   QLR_TRY(check_qmat(A, QLR_ROW_MAJOR, true));
   QLR_TRY(check_qmat(omega, QLR_COL_MAJOR, false));
-  if (opts && (opts->flags & ~QLR_FLAG_QR_EVERY_PASS) != 0) return QLR_EINVAL;
+  if (opts && (opts->flags & ~(QLR_FLAG_QR_EVERY_PASS | QLR_FLAG_NO_GRAPH)) != 0) return QLR_EINVAL;
   if (k < 1 || p < 0 || passes < 2) return QLR_ESHAPE;
   const int64_t l = (int64_t)k + p;
   if (l > std::min(A->rows, A->cols)) return QLR_ESHAPE;
@@ -565,6 +572,11 @@ int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes,
 int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
                              const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V) {
   if (!ctx || count < 0 || (count > 0 && (!A || !k || !p || !omega || !U || !S || !V))) return QLR_EINVAL;
+  if (count == 0) return QLR_OK;
+  qlr_batch* b = nullptr;
+  const int rc = qlr::batch_create(ctx, count, A, k, p, passes, omega, opts, U, S, V, false, false, &b);
+  if (rc == QLR_OK) return qlr_batch_destroy(b);   // the plan's creation ran it once
+  if (rc != QLR_EUNSUPPORTED && rc != QLR_EINVAL) return rc;
   for (int i = 0; i < count; ++i)
     QLR_TRY(lowrank_impl(ctx, &A[i], k[i], p[i], passes, QLR_ALG2, &omega[i], opts, &U[i], S[i], &V[i]));
   return QLR_OK;

@@ -564,7 +564,8 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   if (!ws.ok) return QLR_ENOMEM;
   const T eps = (sizeof(T) == 4) ? (T)5.9604645e-08 : (T)1.1102230246251565e-16;
   const T tol = (T)8 * eps * (T)sqrt((double)l);   // above the rounding noise of the dot products
-  const bool blockj = use_block_jacobi(l, sizeof(T));
+  // many concurrent small problems: one CTA each (the cluster form spends 8 SMs on one problem)
+  const bool blockj = use_block_jacobi(l, sizeof(T)) && !(ctx->small_mode && ll4 * sizeof(T) <= 220 * 1024);
   if (blockj) {
     const int bw = (l + 2 * JP - 1) / (2 * JP);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
@@ -590,8 +591,8 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
       const size_t rs = jb_replay_smem(l, bw, sizeof(T));
-      if (rs > 48 * 1024)
-        QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+      // static shared memory comes on top of the dynamic size: always opt in
+      QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
       jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, rlog, sweeps, V);
       QLR_CUDA_TRY(cudaGetLastError());
     }
@@ -609,8 +610,8 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
       const size_t rs = (size_t)4 * 4 * l * sizeof(T);
-      if (rs > 48 * 1024)
-        QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
+      // static shared memory comes on top of the dynamic size: always opt in
+      QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
       jacobi_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, rlog, sweeps, V);
     }
   }
@@ -624,8 +625,8 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); }
   QLR_CUDA_TRY(cudaGetLastError());
   const size_t rsm = (size_t)8 * l * sizeof(double);
-  if (rsm > 48 * 1024)
-    QLR_CUDA_TRY(cudaFuncSetAttribute(refine_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+  // static shared memory comes on top of the dynamic size: always opt in
+  QLR_CUDA_TRY(cudaFuncSetAttribute(refine_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
   { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;

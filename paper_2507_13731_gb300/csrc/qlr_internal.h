@@ -17,6 +17,9 @@ struct qlr_ctx {
   void* ws = nullptr;            // workspace
   size_t ws_bytes = 0;
   int num_sms = 0;
+  // Throughput mode for many concurrent small problems (batch lanes): small factorisations run in
+  // one CTA each instead of spreading one problem over a cluster of SMs.
+  bool small_mode = false;
   // launch statistics
   int64_t launches[QLR_KID_COUNT] = {};
   double ms[QLR_KID_COUNT] = {};
@@ -52,10 +55,15 @@ struct WsArena {
 
 int qlr_ensure_ws(qlr_ctx* ctx, size_t bytes);
 
-#define QLR_CUDA_TRY(expr)                          \
-  do {                                              \
-    cudaError_t e_ = (expr);                        \
-    if (e_ != cudaSuccess) return QLR_ECUDA;        \
+// Failing CUDA calls are reported on stderr when QLR_DEBUG_CUDA is set in the environment.
+void qlr_report_cuda(cudaError_t e, const char* expr, const char* file, int line);
+#define QLR_CUDA_TRY(expr)                                        \
+  do {                                                            \
+    cudaError_t e_ = (expr);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      qlr_report_cuda(e_, #expr, __FILE__, __LINE__);             \
+      return QLR_ECUDA;                                           \
+    }                                                             \
   } while (0)
 
 #define QLR_TRY(expr)                               \
@@ -163,6 +171,22 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms);
 bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compute);
 
+// Grouped tensor-core sketch over many problems (one launch for the staging of every X and one
+// for every output tile).  The plan lives in caller-provided device memory (`dev`, sized by
+// sketch_tc_grouped_bytes) and is reused by every run; `order` 1 schedules the tiles with the
+// longest reduction first, 0 in problem order.
+struct GroupedSketch {
+  int kind = 0, amode = 0, count = 0, nitems = 0, stage_grid_x = 0;
+  size_t smem = 0;
+  void* d_probs = nullptr;
+  int4* d_items = nullptr;
+  void* d_stage = nullptr;
+};
+size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_qmat* X, int compute);
+int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, const qlr_qmat* X, const qlr_qmat* Y,
+                           int compute, int order, char* dev, size_t bytes, GroupedSketch& gs);
+int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs);
+
 // orthonormalisation pieces (orth.cu)
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
@@ -176,6 +200,16 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
 int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec,
               WsArena& ws);
 size_t core_tsvd_ws(int l);
+
+// workspace bounds (abi.cu)
+size_t gram_ws_bound(int64_t l);
+size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz);
+size_t tsvd_ws_bound(int64_t l);
+
+// batch plans (batch.cu): tune = run the tile-order autotuner, use_graph = capture a CUDA graph
+int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
+                 const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V,
+                 bool tune, bool use_graph, qlr_batch** out);
 
 // utilities (util.cu)
 int convert_qmat(qlr_ctx* ctx, const qlr_qmat& src, qlr_qmat& dst);  // elementwise dtype change

@@ -173,8 +173,10 @@ template <> struct Cfg<K_TF32X3> {   // 4-byte operands, 32 B swizzle, 8 K-eleme
 };
 
 // ---------------------------------------------------------------------------------------
+// One output tile: column block cb, row tile mt, reduction slice `split` (mtiles row tiles).
 template <int KIND, int AMODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_constant__ TcParams p) {
+__device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, const int mt, const int split,
+                                            const int mtiles) {
   using C = Cfg<KIND>;
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
@@ -203,7 +205,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
   volatile int* last_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int cb = blockIdx.x, mt = blockIdx.y, split = blockIdx.z;
   const int64_t m0 = (int64_t)mt * TBM;
   const int j0 = cb * nb;
   const int it0 = split * p.kper;
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
               }
             }
           } else {
-            float* P = p.part + ((size_t)split * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
+            float* P = p.part + ((size_t)split * mtiles * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) P[(size_t)(cc + jj) * TBM + row] = v[jj];
           }
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
               for (int sp = 0; sp < p.nsplit; ++sp) {
-                const float* P = p.part + ((size_t)sp * gridDim.y * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
+                const float* P = p.part + ((size_t)sp * mtiles * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
                                  (size_t)jc0 * TBM + row;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) acc[jj] += __ldcg(P + (size_t)jj * TBM);   // 16 loads in flight
@@ -444,6 +445,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
   if (warp == 1) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+template <int KIND, int AMODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_constant__ TcParams p) {
+  sketch_tile<KIND, AMODE>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.y);
+}
+
+// Grouped launch over many problems: CTA b computes the tile items[b] = (problem, row tile,
+// column block) with that problem's parameters (tensor maps in global memory, 64-byte aligned).
+template <int KIND, int AMODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const TcParams* __restrict__ probs,
+                                                                          const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const TcParams& p = probs[it.x];
+  if (threadIdx.x == 0) {   // the TMA-issuing thread: tensor maps written before the launch
+    for (int c = p.c_first; c < 4; ++c)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmA[c]) : "memory");
+    for (int q = 0; q < 4; ++q) {
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmX[q]) : "memory");
+      if (KIND == K_TF32X3)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmXlo[q]) : "memory");
+    }
+  }
+  sketch_tile<KIND, AMODE>(p, it.z, it.y, 0, 1);
+}
+
+// Grouped operand staging: problem blockIdx.y's X (FP32, column-major) into its staged buffer.
+struct StageArg {
+  const float* x[4];
+  int64_t ldx, rows, cols, ldo;
+  void* out;
+  void* out_lo;
+};
+
+__global__ void stage_x_grouped_kernel(const StageArg* __restrict__ args, int mode) {
+  const StageArg a = args[blockIdx.y];
+  const int64_t per = a.rows * a.cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * per; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / per);
+    const int64_t r = e % per, i = r % a.rows, j = r / a.rows;
+    const float v = a.x[c][i + j * a.ldx];
+    const size_t o = (size_t)c * a.ldo * a.cols + (size_t)j * a.ldo + i;
+    if (mode == K_BF16) {
+      static_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(v);
+    } else if (mode == K_TF32) {
+      static_cast<float*>(a.out)[o] = v;
+    } else {
+      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      static_cast<float*>(a.out)[o] = h;
+      static_cast<float*>(a.out_lo)[o] = v - h;
+    }
   }
 }
 
@@ -563,6 +616,192 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
     if (A.plane[c] && !aligned16(A.plane[c])) return false;
   if (!get_encode()) return false;
   return A.rows < (1LL << 31) && A.cols < (1LL << 31);
+}
+
+// ---------------------------------------------------------------------------------------
+// Grouped form.
+namespace {
+struct GDims {
+  int64_t M, K;
+  int l, nb, ncb, mtiles, kiters;
+  int64_t ldo;
+};
+GDims gdims(int op, const qlr_qmat& A, const qlr_qmat& X, const Plan& base) {
+  GDims g{};
+  g.M = (op == QLR_OP_N) ? A.rows : A.cols;
+  g.K = (op == QLR_OP_N) ? A.cols : A.rows;
+  g.l = (int)X.cols;
+  const int lp = (g.l + 15) / 16 * 16;
+  g.ncb = (lp + 127) / 128;
+  g.nb = ((lp + g.ncb - 1) / g.ncb + 15) / 16 * 16;
+  g.mtiles = (int)((g.M + TBM - 1) / TBM);
+  g.kiters = (int)((g.K + base.bk - 1) / base.bk);
+  g.ldo = (g.K + 7) / 8 * 8;
+  return g;
+}
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_qmat* X, int compute) {
+  const Plan base = make_plan(compute, op, 1, 1, 16, 1);
+  const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
+  size_t b = align256((size_t)count * sizeof(TcParams)) + align256((size_t)count * sizeof(StageArg));
+  size_t items = 0;
+  for (int i = 0; i < count; ++i) {
+    const GDims g = gdims(op, A[i], X[i], base);
+    items += (size_t)g.mtiles * g.ncb;
+    b += align256((size_t)4 * g.ldo * g.l * xesz) * (base.kind == K_TF32X3 ? 2 : 1);
+  }
+  return b + align256(items * sizeof(int4)) + 4096;
+}
+
+int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, const qlr_qmat* X, const qlr_qmat* Y,
+                           int compute, int order, char* dev, size_t bytes, GroupedSketch& gs) {
+  if (count <= 0) return QLR_EINVAL;
+  const Plan base = make_plan(compute, op, 1, 1, 16, 1);
+  const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
+  const bool x3 = base.kind == K_TF32X3;
+  std::vector<GDims> dims(count);
+  int max_nb = 16;
+  for (int i = 0; i < count; ++i) {
+    if (!sketch_tc_supported(op, A[i], X[i], compute)) return QLR_EUNSUPPORTED;
+    dims[i] = gdims(op, A[i], X[i], base);
+    const GDims& g = dims[i];
+    if (g.M <= 0 || g.K <= 0 || g.l <= 0) return QLR_ESHAPE;
+    if (X[i].dtype != QLR_F32 || X[i].layout != QLR_COL_MAJOR || X[i].rows != g.K) return QLR_EINVAL;
+    if (Y[i].dtype != QLR_F32 || Y[i].layout != QLR_COL_MAJOR || Y[i].rows != g.M || Y[i].cols != g.l) return QLR_ESHAPE;
+    max_nb = std::max(max_nb, g.nb);
+  }
+  const size_t stage = (size_t)4 * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
+                       (size_t)4 * max_nb * base.sw * (x3 ? 2 : 1);
+  const size_t budget = (size_t)227 * 1024 - 1024 - 256;
+  const int stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
+  if (stages < 2) return QLR_EUNSUPPORTED;
+  const int cols = 4 * max_nb;
+  const uint32_t tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+
+  // device layout: params | stage args | items | staged X buffers
+  char* cur = dev;
+  auto take = [&](size_t n) { char* r = cur; cur += align256(n); return r; };
+  TcParams* d_probs = reinterpret_cast<TcParams*>(take((size_t)count * sizeof(TcParams)));
+  StageArg* d_stage = reinterpret_cast<StageArg*>(take((size_t)count * sizeof(StageArg)));
+  size_t nitems = 0;
+  for (const auto& g : dims) nitems += (size_t)g.mtiles * g.ncb;
+  int4* d_items = reinterpret_cast<int4*>(take(nitems * sizeof(int4)));
+
+  std::vector<TcParams> hp(count);
+  std::vector<StageArg> hs(count);
+  std::vector<int4> hi;
+  hi.reserve(nitems);
+  const CUtensorMapDataType dt = (base.kind == K_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapSwizzle sw = (base.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+  uint32_t neg = 0;
+  const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
+  for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
+  if (op == QLR_OP_H) neg ^= 0xFFF0u;
+  const uint32_t fmt = (base.kind == K_BF16) ? 1u : 2u;
+  int max_stage_blocks = 1;
+  for (int i = 0; i < count; ++i) {
+    const GDims& g = dims[i];
+    const qlr_qmat& a = A[i];
+    TcParams& prm = hp[i];
+    memset(&prm, 0, sizeof(prm));
+    char* xs = take((size_t)4 * g.ldo * g.l * xesz);
+    char* xlo = x3 ? take((size_t)4 * g.ldo * g.l * 4) : nullptr;
+    if ((size_t)(cur - dev) > bytes) return QLR_ENOMEM;
+    prm.c_first = (a.plane[0] == nullptr) ? 1 : 0;
+    for (int c = prm.c_first; c < 4; ++c) {
+      bool ok;
+      if (op == QLR_OP_N)
+        ok = encode_2d(&prm.tmA[c], a.plane[c], dt, (uint64_t)a.cols, (uint64_t)a.rows, (uint64_t)a.ld * base.esz,
+                       (uint32_t)base.bk, TBM, sw);
+      else if (base.amode == A_MN)
+        ok = encode_2d(&prm.tmA[c], a.plane[c], dt, (uint64_t)a.cols, (uint64_t)a.rows, (uint64_t)a.ld * base.esz,
+                       (uint32_t)(base.sw / base.esz), (uint32_t)base.bk, sw);
+      else
+        ok = encode_2d(&prm.tmA[c], a.plane[c], dt, (uint64_t)a.cols, (uint64_t)a.rows, (uint64_t)a.ld * base.esz, TBM,
+                       (uint32_t)base.bk, CU_TENSOR_MAP_SWIZZLE_NONE);
+      if (!ok) return QLR_ECUDA;
+    }
+    for (int q = 0; q < 4; ++q) {
+      if (!encode_2d(&prm.tmX[q], xs + (size_t)q * g.ldo * g.l * xesz, dt, (uint64_t)g.K, (uint64_t)g.l,
+                     (uint64_t)g.ldo * xesz, (uint32_t)base.bk, (uint32_t)g.nb, sw))
+        return QLR_ECUDA;
+      if (xlo && !encode_2d(&prm.tmXlo[q], xlo + (size_t)q * g.ldo * g.l * 4, dt, (uint64_t)g.K, (uint64_t)g.l,
+                            (uint64_t)g.ldo * 4, (uint32_t)base.bk, (uint32_t)g.nb, sw))
+        return QLR_ECUDA;
+    }
+    for (int c = 0; c < 4; ++c) prm.y[c] = static_cast<float*>(Y[i].plane[c]);
+    prm.ldy = Y[i].ld;
+    prm.M = g.M;
+    prm.l = g.l;
+    prm.nb = g.nb;
+    prm.ncb = g.ncb;
+    prm.kiters = g.kiters;
+    prm.kper = g.kiters;
+    prm.nsplit = 1;
+    prm.neg_mask = neg;
+    prm.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((base.amode == A_MN ? 1u : 0u) << 15) |
+                     ((uint32_t)(g.nb >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+    prm.tmem_cols = tmem_cols;
+    prm.stages = stages;
+    prm.err = ctx->d_err;
+    StageArg& sa = hs[i];
+    for (int c = 0; c < 4; ++c) sa.x[c] = static_cast<const float*>(X[i].plane[c]);
+    sa.ldx = X[i].ld;
+    sa.rows = g.K;
+    sa.cols = g.l;
+    sa.ldo = g.ldo;
+    sa.out = xs;
+    sa.out_lo = xlo;
+    max_stage_blocks = std::max<int>(max_stage_blocks, (int)std::min<int64_t>((4 * g.K * g.l + 255) / 256, 64));
+    for (int mt = 0; mt < g.mtiles; ++mt)
+      for (int cb = 0; cb < g.ncb; ++cb) hi.push_back(make_int4(i, mt, cb, 0));
+  }
+  if (order == 1)
+    std::stable_sort(hi.begin(), hi.end(), [&](const int4& a, const int4& b) { return dims[a.x].K > dims[b.x].K; });
+  // ordered on the context stream before any launch that reads them (a plain cudaMemcpy from
+  // pageable memory may still be in flight when it returns and is not ordered with that stream)
+  QLR_CUDA_TRY(cudaMemcpyAsync(d_probs, hp.data(), hp.size() * sizeof(TcParams), cudaMemcpyHostToDevice, ctx->stream));
+  QLR_CUDA_TRY(cudaMemcpyAsync(d_stage, hs.data(), hs.size() * sizeof(StageArg), cudaMemcpyHostToDevice, ctx->stream));
+  QLR_CUDA_TRY(cudaMemcpyAsync(d_items, hi.data(), hi.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  QLR_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  gs.kind = base.kind;
+  gs.amode = base.amode;
+  gs.count = count;
+  gs.nitems = (int)hi.size();
+  gs.stage_grid_x = max_stage_blocks;
+  gs.smem = stages * stage + 1024 + 256;
+  gs.d_probs = d_probs;
+  gs.d_items = d_items;
+  gs.d_stage = d_stage;
+  return QLR_OK;
+}
+
+namespace {
+template <int KIND, int AMODE>
+int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
+  auto kern = sketch_tc_grouped_kernel<KIND, AMODE>;
+  QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
+  KTimer kt(ctx, QLR_KID_SKETCH_TC);
+  kern<<<(unsigned)gs.nitems, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items);
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
+}  // namespace
+
+int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
+  if (gs.nitems == 0) return QLR_OK;
+  {
+    KTimer kt(ctx, QLR_KID_MISC);
+    stage_x_grouped_kernel<<<dim3((unsigned)gs.stage_grid_x, (unsigned)gs.count), 256, 0, ctx->stream>>>(
+        static_cast<const StageArg*>(gs.d_stage), gs.kind);
+    QLR_CUDA_TRY(cudaGetLastError());
+  }
+  const bool n = (gs.amode == A_K);
+  if (gs.kind == K_BF16) return n ? launch_grouped<K_BF16, A_K>(ctx, gs) : launch_grouped<K_BF16, A_MN>(ctx, gs);
+  if (gs.kind == K_TF32) return n ? launch_grouped<K_TF32, A_K>(ctx, gs) : launch_grouped<K_TF32, A_T>(ctx, gs);
+  return n ? launch_grouped<K_TF32X3, A_K>(ctx, gs) : launch_grouped<K_TF32X3, A_T>(ctx, gs);
 }
 
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {

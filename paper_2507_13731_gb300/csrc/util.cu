@@ -1,5 +1,13 @@
 // Elementwise helpers on quaternion matrices: dtype conversion / copy, zero fill.
+#include <cstdio>
+#include <cstdlib>
+
 #include "qlr_internal.h"
+
+void qlr_report_cuda(cudaError_t e, const char* expr, const char* file, int line) {
+  static const bool on = std::getenv("QLR_DEBUG_CUDA") != nullptr;
+  if (on) std::fprintf(stderr, "qlr: %s failed at %s:%d: %s\n", expr, file, line, cudaGetErrorString(e));
+}
 
 size_t qlr_dtype_size(int dtype) {
   switch (dtype) {

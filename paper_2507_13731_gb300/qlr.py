@@ -30,6 +30,7 @@ ALG2, ALG4 = 2, 4
 SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
 ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
 FLAG_QR_EVERY_PASS = 1
+FLAG_NO_GRAPH = 2
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc"]
@@ -49,6 +50,12 @@ class QMatC(ctypes.Structure):
 class OptsC(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int32), ("side", ctypes.c_int32), ("orth", ctypes.c_int32),
                 ("flags", ctypes.c_int32)]
+
+
+class BatchStatsC(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("graph", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("sketch_launches", ctypes.c_int32), ("tune_ms", ctypes.c_float * 2),
+                ("launches_per_run", ctypes.c_int64)]
 
 
 _lib = None
@@ -87,6 +94,11 @@ def lib():
             "qlr_reset_stats": (I, [P]),
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
             "qlr_qsketch_noalloc": (I, [P, I, Q, Q, Q, I, P]),
+            "qlr_batch_create": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
+                                     ctypes.POINTER(P), Q, ctypes.POINTER(P)]),
+            "qlr_batch_run": (I, [P]),
+            "qlr_batch_info": (I, [P, ctypes.POINTER(BatchStatsC)]),
+            "qlr_batch_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -296,6 +308,60 @@ def qsvd_lowrank_batched(ctx: Context, As: Sequence[torch.Tensor], ks: Sequence[
     _check(lib().qlr_qsvd_lowrank_batched(ctx.h, n, arrA, kk, pp, passes, arrO, ctypes.byref(o), arrU, sp, arrV),
            "qlr_qsvd_lowrank_batched")
     return Us, Ss, Vs
+
+
+class Batch:
+    """A batch plan: Algorithm 2 over many problems, planned (and autotuned, graph-captured) once,
+    run many times on the context's stream.  The buffers passed here are the ones every run uses."""
+
+    def __init__(self, ctx: Context, As, ks, ps, passes: int, omegas, Us, Ss, Vs, compute=COMPUTE_AUTO,
+                 graph: bool = True, qr_every_pass: bool = False):
+        n = len(As)
+        self._keep = (As, omegas, Us, Ss, Vs)
+        arrA = (QMatC * n)(*[_A(t) for t in As])
+        arrO = (QMatC * n)(*[_T(t) for t in omegas])
+        arrU = (QMatC * n)(*[_T(t) for t in Us])
+        arrV = (QMatC * n)(*[_T(t) for t in Vs])
+        kk = (ctypes.c_int * n)(*ks)
+        pp = (ctypes.c_int * n)(*ps)
+        sp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Ss])
+        o = _opts(compute, SIDE_X, ORTH_CHOLQR2, qr_every_pass)
+        if not graph:
+            o.flags |= FLAG_NO_GRAPH
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        _check(lib().qlr_batch_create(ctx.h, n, arrA, kk, pp, passes, arrO, ctypes.byref(o), arrU, sp, arrV,
+                                      ctypes.byref(self.h)), "qlr_batch_create")
+
+    def run(self) -> None:
+        _check(lib().qlr_batch_run(self.h), "qlr_batch_run")
+
+    def info(self) -> dict:
+        st = BatchStatsC()
+        _check(lib().qlr_batch_info(self.h, ctypes.byref(st)), "qlr_batch_info")
+        return {"lanes": st.lanes, "graph": bool(st.graph), "tile_order": st.tile_order,
+                "sketch_launches": st.sketch_launches, "tune_ms": [st.tune_ms[0], st.tune_ms[1]],
+                "launches_per_run": st.launches_per_run}
+
+    def close(self) -> None:
+        if self.h:
+            lib().qlr_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def empty_rowmajor(rows: int, cols: int, planes: int = 4, dtype=torch.bfloat16, device="cuda") -> torch.Tensor:
+    """Row-major quaternion storage (planes, rows, cols) whose row pitch is a multiple of 16 bytes, the
+    tensor-core sketch's requirement (the pitch is padded, the view has exactly `cols` columns)."""
+    esz = torch.empty(0, dtype=dtype).element_size()
+    per = 16 // esz
+    ld = (cols + per - 1) // per * per
+    return torch.empty(planes, rows, ld, dtype=dtype, device=device)[:, :, :cols]
 
 
 def residual_norm(ctx: Context, A, Q, side, start, iters=30) -> float:

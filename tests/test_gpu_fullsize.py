@@ -111,19 +111,30 @@ def _config4_ref():
 
 def test_config5_batched_bf16_sampled(ctx):
     """512 pure matrices of uneven sizes (64..1024 x 64..768), rank 8..64 plus noise, k = r,
-    p = 8, v = 3, BF16 storage; every matrix runs on the GPU, 24 sampled ones against the oracle."""
+    p = 8, v = 3, BF16 storage with a 16-byte row pitch: one batch plan (grouped tensor-core
+    sketch per pass, CUDA graph), every matrix on the GPU, 24 sampled ones against the oracle;
+    a replay of the graph reproduces the first run."""
     from paper_2507_13731_gb300 import qlr
     probs = synth.batched_problems()
-    As = [dev_rowmajor(P.A, "bf16", pure=True) for P in probs]
+    As = []
+    for P in probs:
+        t = qlr.empty_rowmajor(P.m, P.n, 3, torch.bfloat16)
+        t.copy_(torch.from_numpy(np.ascontiguousarray(P.A[1:])).to(torch.bfloat16))
+        As.append(t)
     Os = [dev_thin(P.Omega, "f32") for P in probs]
     Us = [qlr.empty_thin(P.m, P.k) for P in probs]
     Vs = [qlr.empty_thin(P.n, P.k) for P in probs]
     Ss = [torch.zeros(P.k, dtype=torch.float64, device="cuda") for P in probs]
-    qlr.qsvd_lowrank_batched(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs,
-                             compute=qlr.COMPUTE_AUTO)
+    b = qlr.Batch(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs)
     assert ctx.sync() == 0
+    first = [s.clone() for s in Ss]
+    b.run()
+    assert ctx.sync() == 0
+    for s, f in zip(Ss, first):
+        np.testing.assert_allclose(s.cpu().numpy(), f.cpu().numpy(), rtol=1e-12, atol=0)
     rng = np.random.default_rng(5)
     for i in rng.choice(len(probs), 24, replace=False):
         P = probs[i]
         ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, 3, P.Omega)
         np.testing.assert_allclose(Ss[i].cpu().numpy(), ref.S, rtol=2e-2, err_msg=f"problem {i}")
+    b.close()
