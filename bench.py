@@ -160,6 +160,72 @@ def cpu_oracle_sample(P, passes=2):
     return passes / dt, dt, threads
 
 
+BATCH_WORKLOAD = ("512 pure quaternion matrices, m ~ U{64..1024}, n ~ U{64..768}, rank r ~ U{8..64} plus "
+                  "N(0,(1e-3)^2) noise on the i,j,k planes, k=r, p=8, Algorithm 2 with v=3, BF16 storage (16-byte row pitch)")
+
+
+def batched_leg(dev, steps=5):
+    """The batched workload: one batch plan (grouped tensor-core sketch per pass, per-problem
+    orthonormalisation lanes, CUDA graph, tile-order autotuner) against the plain FP32 comparator,
+    a loop of per-problem calls with FP32 storage and the FP32 SIMT sketch."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import qlr
+    probs = synth.batched_problems()
+    ctx = qlr.Context(dev.index or 0)
+    As, Af = [], []
+    for P in probs:
+        t = qlr.empty_rowmajor(P.m, P.n, 3, torch.bfloat16, device=dev)
+        src = torch.from_numpy(np.ascontiguousarray(P.A[1:]))
+        t.copy_(src.to(torch.bfloat16))
+        As.append(t)
+        Af.append(src.float().to(dev))
+    Os = [qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev)) for P in probs]
+    Us = [qlr.empty_thin(P.m, P.k, device=dev) for P in probs]
+    Vs = [qlr.empty_thin(P.n, P.k, device=dev) for P in probs]
+    Ss = [torch.zeros(P.k, dtype=torch.float64, device=dev) for P in probs]
+    ks, ps = [P.k for P in probs], [P.p for P in probs]
+    b = qlr.Batch(ctx, As, ks, ps, 3, Os, Us, Ss, Vs)
+    info = b.info()
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    plan_ms = e0.elapsed_time(e1) / steps
+    rc = ctx.sync()
+    qlr.qsvd_lowrank_batched(ctx, Af, ks, ps, 3, Os, Us, Ss, Vs, compute=qlr.COMPUTE_F32)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(2):
+        qlr.qsvd_lowrank_batched(ctx, Af, ks, ps, 3, Os, Us, Ss, Vs, compute=qlr.COMPUTE_F32)
+    e1.record()
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / 2
+    rc = rc or ctx.sync()
+    pk, src = _peaks()
+    a_bytes = sum(3 * P.m * P.n * 2 for P in probs)
+    pass_ms = info["tune_ms"][info["tile_order"]] / 2
+    hbm = a_bytes / (pass_ms / 1e3) / 1e9
+    b.close()
+    ctx.close()
+    return {"workload": BATCH_WORKLOAD, "plan_ms": round(plan_ms, 3),
+            "problems_per_s": round(len(probs) / (plan_ms / 1e3), 1), "loop_fp32_ms": round(loop_ms, 3),
+            "speedup_vs_fp32_loop": round(loop_ms / plan_ms, 2),
+            "grouped_sketch": {"ms_per_pass": round(pass_ms, 4), "a_bytes_per_pass": a_bytes,
+                               "hbm_gbs": round(hbm, 1), "peak_gbs": pk.get("hbm_gbs"),
+                               "frac": round(hbm / pk.get("hbm_gbs", 6800.0), 4), "peak_source": src},
+            "graph": info["graph"], "lanes": info["lanes"], "tile_order": info["tile_order"],
+            "autotune_ms": [round(x, 4) for x in info["tune_ms"]], "launches_per_run": info["launches_per_run"],
+            "device_error": rc}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,6 +314,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
     ap.add_argument("--only", choices=["sketch", "qsvd"], default=None,
                     help="profiling driver: time only sketch passes or single QSVDs (for ncu captures)")
     ap.add_argument("--op", choices=["N", "H"], default="N")
@@ -370,6 +437,9 @@ def main():
     if rank == 0:
         roof = roofline(stats, args.compute, args.steps)
         cpu = None
+        batched = None
+        if ws == 1 and not args.no_batched:
+            batched = batched_leg(dev)
         if ws == 1 and not args.no_cpu_baseline:
             val, secs, thr = cpu_oracle_sample(P)
             cpu = {"value": round(val, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
@@ -390,6 +460,7 @@ def main():
             "e2e": {"value": round(e2e_value, 3), "unit": "sketch passes/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
+            "batched": batched,
             "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in stats.items() if n},
             "clocks": clk,
             "device_error": rc,

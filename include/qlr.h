@@ -229,7 +229,7 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  * qlr_batch_create -- checks and plans `count` problems (conditions as above; compute AUTO means
  * BF16 for BF16 A and 3xTF32 for FP32 A; side must be AUTO or X).  Each sketch pass of all the
  * problems is one grouped tensor-core launch over every output tile (plus one grouped staging
- * launch); the per-problem orthonormalisations, core QSVDs and lifts run on up to 32 side
+ * launch); the per-problem orthonormalisations, core QSVDs and lifts run on up to 128 side
  * streams forked from and joined to the context stream.  At creation the plan allocates its
  * device memory (cudaMalloc), times the two tile orders of the grouped sketch and keeps the
  * faster (the autotuner), runs the whole sequence once (its results are valid), and captures it

@@ -280,8 +280,15 @@ static cudaEvent_t pool_get(qlr_ctx* ctx) {
   return e;
 }
 
+static thread_local KTimer* tl_ktimer = nullptr;
+
+void qlr_count_launch() {
+  if (tl_ktimer) tl_ktimer->count += 1;
+}
+
 KTimer::KTimer(qlr_ctx* c, int k) : ctx(c), kid(k) {
-  ctx->launches[kid] += 1;
+  prev = tl_ktimer;
+  tl_ktimer = this;
   if (ctx->timing) {
     e0 = pool_get(ctx);
     e1 = pool_get(ctx);
@@ -289,6 +296,8 @@ KTimer::KTimer(qlr_ctx* c, int k) : ctx(c), kid(k) {
   }
 }
 KTimer::~KTimer() {
+  tl_ktimer = prev;
+  ctx->launches[kid] += count;
   if (e0 && e1) {
     cudaEventRecord(e1, ctx->stream);
     ctx->ev_pending.push_back({kid, {e0, e1}});

@@ -45,6 +45,10 @@ struct qlr_batch {
 
 namespace {
 
+// Side streams: enough that the per-problem chains of small, latency-bound kernels fill the GPU
+// (the hardware runs up to 128 kernels at once).
+constexpr int kMaxLanes = 128;
+
 struct DevGuard {
   int prev = -1;
   explicit DevGuard(int dev) {
@@ -237,7 +241,7 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   b->compute = compute;
   b->orth = orth;
   b->mid = (opts && (opts->flags & QLR_FLAG_QR_EVERY_PASS)) ? orth : ORTH_SPAN;
-  b->lanes = std::min(count, 32);
+  b->lanes = std::min(count, kMaxLanes);
   b->main_ctx.device = ctx->device;
   b->main_ctx.stream = ctx->stream;
   b->main_ctx.d_err = ctx->d_err;

@@ -587,6 +587,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
       KTimer kt(ctx, QLR_KID_JACOBI);
       QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, R, l, bw, W, (int)JMAX_SWEEPS, tol, rlog, flags, sweeps, sig,
                                       ctx->d_err));
+      qlr_count_launch();
     }
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
@@ -594,6 +595,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
       // static shared memory comes on top of the dynamic size: always opt in
       QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
       jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, rlog, sweeps, V);
+      qlr_count_launch();
       QLR_CUDA_TRY(cudaGetLastError());
     }
   } else {
@@ -605,6 +607,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
       jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err);
+      qlr_count_launch();
     }
     QLR_CUDA_TRY(cudaGetLastError());
     {
@@ -613,6 +616,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
       // static shared memory comes on top of the dynamic size: always opt in
       QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
       jacobi_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, rlog, sweeps, V);
+      qlr_count_launch();
     }
   }
   QLR_CUDA_TRY(cudaGetLastError());
@@ -622,12 +626,12 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     cudaStreamSynchronize(ctx->stream);
     std::fprintf(stderr, "qlr jacobi: l=%d sweeps=%d %s\n", l, hs, blockj ? "cluster" : "single-CTA");
   }
-  { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); }
+  { KTimer kt(ctx, QLR_KID_REFINE); rank_kernel<T><<<(l + 127) / 128, 128, 0, ctx->stream>>>(sig, l, order); qlr_count_launch(); }
   QLR_CUDA_TRY(cudaGetLastError());
   const size_t rsm = (size_t)8 * l * sizeof(double);
   // static shared memory comes on top of the dynamic size: always opt in
   QLR_CUDA_TRY(cudaFuncSetAttribute(refine_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-  { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); }
+  { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); qlr_count_launch(); }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }

@@ -138,6 +138,7 @@ void launch(const qlr::GemmArgs& g, cudaStream_t s) {
     if (g.conj_a) gemm_simt_kernel<TAcc, false, true><<<grid, NT, 0, s>>>(g);
     else gemm_simt_kernel<TAcc, false, false><<<grid, NT, 0, s>>>(g);
   }
+  qlr_count_launch();
 }
 
 }  // namespace

@@ -1004,14 +1004,19 @@ static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
     gram_df_partial_kernel<<<grid, 256, 0, ctx->stream>>>(
         static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
         static_cast<const float*>(Y.plane[3]), m, l, Y.ld, rpc, part);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
   {
     KTimer kt(ctx, QLR_KID_GRAM);
     const int64_t tw = (int64_t)L4 * L4;
-    if (chunks > 1) gram_df_reduce_kernel<<<(unsigned)((tw + 255) / 256), 256, 0, ctx->stream>>>(part, (int)chunks, L4);
+    if (chunks > 1) {
+      gram_df_reduce_kernel<<<(unsigned)((tw + 255) / 256), 256, 0, ctx->stream>>>(part, (int)chunks, L4);
+      qlr_count_launch();
+    }
     const int64_t tot = (int64_t)l * l;
     gram_df_combine_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(part, l, G);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
@@ -1042,16 +1047,19 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
     const double* p[4];
     for (int c = 0; c < 4; ++c) p[c] = static_cast<const double*>(Y.plane[c]);
     gram_partial_kernel<double><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, part);
+    qlr_count_launch();
   } else if (Y.dtype == QLR_F32) {
     const float* p[4];
     for (int c = 0; c < 4; ++c) p[c] = static_cast<const float*>(Y.plane[c]);
     gram_partial_kernel<float><<<grid, 256, 0, ctx->stream>>>(p[0], p[1], p[2], p[3], m, l, Y.ld, rpc, part);
+    qlr_count_launch();
   } else {
     return QLR_EINVAL;
   }
   QLR_CUDA_TRY(cudaGetLastError());
   int64_t tot = (int64_t)l * l;
   gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(part, (int)chunks, l, G);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   ws.off = mark;  // partials are dead once the reduction is enqueued (stream order)
   return QLR_OK;
@@ -1109,6 +1117,7 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     QLR_CUDA_TRY(cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KTimer kt(ctx, QLR_KID_CHOL);
     chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
     return QLR_OK;
   }
@@ -1128,6 +1137,7 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     cfg.numAttrs = 1;
     KTimer kt(ctx, QLR_KID_CHOL);
     QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, chol_cluster_kernel, G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if));
+    qlr_count_launch();
     return QLR_OK;
   }
   size_t mark = ws.off;
@@ -1137,20 +1147,24 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
   if (!ws.ok) return QLR_ENOMEM;
   KTimer kt(ctx, QLR_KID_CHOL);
   chol_init_kernel<<<std::max(1, std::min(64, (int)((ll4 / 4 + 255) / 256))), 256, 0, ctx->stream>>>(G, Wm, R, l, shift_coef, run_if);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   for (int j0 = 0; j0 < l; j0 += CB) {
     const int b = std::min(CB, l - j0);
     double* Dinv = Dinv_all + (size_t)(j0 / CB) * 4 * CB * CB;
     chol_diag_kernel<<<1, 256, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, ctx->d_err, run_if);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
     const int rem = l - j0 - b;
     if (rem <= 0) break;
     chol_panel_kernel<<<(rem * 32 + 127) / 128, 128, 0, ctx->stream>>>(Wm, R, l, j0, b, Dinv, run_if);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
     // tiles (a <= b) of the trailing triangle, coordinates relative to j0 + b
     const int nt = (rem + CT - 1) / CT;
     const int ntiles = nt * (nt + 1) / 2;
     chol_update_kernel<<<ntiles, 64, 0, ctx->stream>>>(Wm, R, l, j0, b, run_if);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
@@ -1165,10 +1179,12 @@ int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Di
     // static shared memory comes on top of the dynamic size: always opt in
     QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tri_inv_blocked_kernel<<<l, 256, smem, ctx->stream>>>(R, Dinv_all, Rinv, l, run_if);
+    qlr_count_launch();
   } else {
     // static shared memory comes on top of the dynamic size: always opt in
     QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tri_inv_col_kernel<<<l, 256, smem, ctx->stream>>>(R, Rinv, l);
+    qlr_count_launch();
   }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
@@ -1178,6 +1194,7 @@ int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* 
   const int64_t thr = (int64_t)l * (l + 1) / 2 * MM_SPLIT;
   KTimer kt(ctx, QLR_KID_MISC);
   small_matmul_kernel<<<(unsigned)((thr + 127) / 128), 128, 0, ctx->stream>>>(A, B, C, l);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
@@ -1220,22 +1237,28 @@ static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, doubl
   const unsigned gsq = (unsigned)((tot + 127) / 128);
   const unsigned gst = (unsigned)(((int64_t)nent * SPLIT + 127) / 128);
   series_init_kernel<<<gsq, 128, 0, ctx->stream>>>(G, E, Fa, l, emax);
+  qlr_count_launch();
   series_decide_kernel<<<1, 1, 0, ctx->stream>>>(emax, l, use_chol);
+  qlr_count_launch();
   double* Fc = Fa;
   double* Fn = Fb;
   for (int it = 0; it < SERIES_ITERS; ++it) {
     series_step_kernel<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, nent, it ? deltas + it - 1 : nullptr,
                                                      deltas + it);
+    qlr_count_launch();
     std::swap(Fc, Fn);
   }
   series_form_kernel<<<gsq, 128, 0, ctx->stream>>>(Fc, R2, l);
+  qlr_count_launch();
   fill_identity_kernel<<<gsq, 128, 0, ctx->stream>>>(Xa, l);
+  qlr_count_launch();
   double* Xc = Xa;
   double* Xn = Xb;
   unsigned long long* nd = deltas + SERIES_ITERS;
   for (int it = 0; it < NEUMANN_ITERS; ++it) {
     series_step_kernel<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, (it == NEUMANN_ITERS - 1) ? R2inv : Xn, l, 1, nent,
                                                      it ? nd + it - 1 : nullptr, nd + it);
+    qlr_count_launch();
     std::swap(Xc, Xn);
   }
   QLR_CUDA_TRY(cudaGetLastError());

@@ -28,14 +28,19 @@ struct qlr_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
 };
 
-// Brackets one kernel launch: counts it and, with timing enabled, records events on ctx->stream.
+// Brackets the launches of one kernel class: with timing enabled it records events on
+// ctx->stream around them; the launches themselves are counted by qlr_count_launch() after each
+// one (added to the innermost live KTimer of the calling thread when it closes).
 struct KTimer {
   qlr_ctx* ctx;
   int kid;
+  int count = 0;
+  KTimer* prev = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   KTimer(qlr_ctx* c, int k);
   ~KTimer();
 };
+void qlr_count_launch();
 
 // Bump allocator over the context workspace (256-byte aligned slices).
 struct WsArena {

@@ -595,6 +595,7 @@ int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm) {
   dim3 grid((unsigned)pl.ncb, (unsigned)pl.mtiles, (unsigned)pl.nsplit);
   KTimer kt(ctx, QLR_KID_SKETCH_TC);
   kern<<<grid, TC_THREADS, pl.smem, ctx->stream>>>(prm);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
@@ -785,6 +786,7 @@ int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
   QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
   KTimer kt(ctx, QLR_KID_SKETCH_TC);
   kern<<<(unsigned)gs.nitems, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
@@ -796,6 +798,7 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
     KTimer kt(ctx, QLR_KID_MISC);
     stage_x_grouped_kernel<<<dim3((unsigned)gs.stage_grid_x, (unsigned)gs.count), 256, 0, ctx->stream>>>(
         static_cast<const StageArg*>(gs.d_stage), gs.kind);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
   const bool n = (gs.amode == A_K);
@@ -841,6 +844,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
     stage_x_kernel<<<blocks, 256, 0, ctx->stream>>>(
         static_cast<const float*>(X.plane[0]), static_cast<const float*>(X.plane[1]),
         static_cast<const float*>(X.plane[2]), static_cast<const float*>(X.plane[3]), X.ld, K, l, pl.kind, xs, xlo, ldo);
+    qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
   QLR_CUDA_TRY(cudaMemsetAsync(counters, 0, (size_t)pl.mtiles * pl.ncb * sizeof(unsigned), ctx->stream));

@@ -38,6 +38,7 @@ int launch_convert(qlr_ctx* ctx, const void* s, int64_t lds, void* d, int64_t ld
   KTimer kt(ctx, QLR_KID_MISC);
   convert_kernel<S, D><<<blocks, 256, 0, ctx->stream>>>(static_cast<const S*>(s), lds, static_cast<D*>(d), ldd, inner,
                                                          outer);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
