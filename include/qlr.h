@@ -231,10 +231,11 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  * problems is one grouped tensor-core launch over every output tile (plus one grouped staging
  * launch); the per-problem orthonormalisations, core QSVDs and lifts run on up to 128 side
  * streams forked from and joined to the context stream.  At creation the plan allocates its
- * device memory (cudaMalloc), times the two tile orders of the grouped sketch and keeps the
- * faster (the autotuner), runs the whole sequence once (its results are valid), and captures it
- * into a CUDA graph unless opts.flags has QLR_FLAG_NO_GRAPH.  The pointers in A, omega, U, S, V
- * are baked into the plan: later runs read and write the same buffers.
+ * device memory (cudaMalloc), times four variants of the grouped sketch (tile order x one CTA per
+ * tile or persistent CTAs) and keeps the fastest (the autotuner), runs the whole sequence once
+ * (its results are valid), and captures it into a CUDA graph unless opts.flags has
+ * QLR_FLAG_NO_GRAPH.  The pointers in A, omega, U, S, V are baked into the plan: later runs read
+ * and write the same buffers.
  * qlr_batch_run -- enqueues one run on the context stream (asynchronous; errors of the device
  * side show in qlr_sync).  qlr_batch_info -- plan facts.  qlr_batch_destroy -- synchronises and
  * frees the plan (b may be NULL).
@@ -243,9 +244,10 @@ typedef struct qlr_batch qlr_batch;
 typedef struct {
   int32_t lanes;           /* side streams                                              */
   int32_t graph;           /* 1 when runs replay the captured CUDA graph               */
-  int32_t tile_order;      /* grouped sketch tile order chosen: 0 problem order, 1 longest first */
+  int32_t tile_order;      /* grouped sketch variant chosen: bit 0 tiles with the longest reduction
+                              first (else problem order), bit 1 persistent CTAs (else one per tile) */
   int32_t sketch_launches; /* grouped launches per run (staging + sketch per pass)     */
-  float tune_ms[2];        /* autotuner: N + H sketch time of each tile order (ms)    */
+  float tune_ms[4];        /* autotuner: N + H sketch time of each variant (ms)       */
   int64_t launches_per_run;/* kernels launched per run (all streams)                  */
 } qlr_batch_stats;
 int qlr_batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,

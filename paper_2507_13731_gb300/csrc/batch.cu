@@ -8,6 +8,7 @@
 // sequence is captured once into a CUDA graph and replayed by every run.  At plan time a small
 // autotuner times the grouped sketch's tile orders and keeps the faster one.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -38,8 +39,8 @@ struct qlr_batch {
   void* dev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int order = 1;
-  float tune_ms[2] = {0.f, 0.f};
+  int order = 1;                            // chosen grouped-sketch variant (bit 0 order, bit 1 persistent)
+  float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
   int64_t launches_per_run = 0;
 };
 
@@ -160,13 +161,15 @@ int plan_sketches(qlr_batch* b, int order) {
   return QLR_OK;
 }
 
-// Autotuner: time the two sketch orders (passes N and H, best of three after a warm-up).
+// Autotuner: time the grouped sketch variants -- tile order (problem order / longest reduction
+// first) x schedule (one CTA per tile / one persistent CTA per SM) -- on passes N and H, best of
+// three after a warm-up, and keep the fastest.
 int autotune(qlr_batch* b) {
   cudaEvent_t e0, e1;
   QLR_CUDA_TRY(cudaEventCreate(&e0));
   QLR_CUDA_TRY(cudaEventCreate(&e1));
   int rc = QLR_OK;
-  for (int order = 0; order < 2 && rc == QLR_OK; ++order) {
+  for (int order = 0; order < 4 && rc == QLR_OK; ++order) {
     rc = plan_sketches(b, order);
     if (rc != QLR_OK) break;
     float best = 1e30f;
@@ -185,7 +188,7 @@ int autotune(qlr_batch* b) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   QLR_TRY(rc);
-  b->order = (b->tune_ms[1] <= b->tune_ms[0]) ? 1 : 0;
+  b->order = (int)(std::min_element(b->tune_ms, b->tune_ms + 4) - b->tune_ms);
   return plan_sketches(b, b->order);
 }
 
@@ -311,7 +314,14 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
     lc.num_sms = std::max(4, 2 * ctx->num_sms / b->lanes);
     lc.small_mode = true;
   }
-  if (rc == QLR_OK) rc = tune ? autotune(b) : plan_sketches(b, 1);
+  // QLR_BATCH_VARIANT=0..3 in the environment fixes the grouped sketch variant (no tuning)
+  const char* force = std::getenv("QLR_BATCH_VARIANT");
+  if (rc == QLR_OK && force && force[0] >= '0' && force[0] <= '3' && force[1] == 0) {
+    b->order = force[0] - '0';
+    rc = plan_sketches(b, b->order);
+  } else if (rc == QLR_OK) {
+    rc = tune ? autotune(b) : plan_sketches(b, b->order);
+  }
   // one eager run: every lazily configured kernel attribute is set before any capture
   if (rc == QLR_OK) rc = enqueue(b);
   if (rc == QLR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = QLR_ECUDA;
@@ -362,8 +372,7 @@ extern "C" int qlr_batch_info(const qlr_batch* b, qlr_batch_stats* st) {
   st->lanes = b->lanes;
   st->graph = b->exec ? 1 : 0;
   st->tile_order = b->order;
-  st->tune_ms[0] = b->tune_ms[0];
-  st->tune_ms[1] = b->tune_ms[1];
+  for (int i = 0; i < 4; ++i) st->tune_ms[i] = b->tune_ms[i];
   st->sketch_launches = 2 * b->passes;
   st->launches_per_run = b->launches_per_run;
   return QLR_OK;

@@ -178,10 +178,13 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 
 // Grouped tensor-core sketch over many problems (one launch for the staging of every X and one
 // for every output tile).  The plan lives in caller-provided device memory (`dev`, sized by
-// sketch_tc_grouped_bytes) and is reused by every run; `order` 1 schedules the tiles with the
-// longest reduction first, 0 in problem order.
+// sketch_tc_grouped_bytes) and is reused by every run.  `variant` bit 0: schedule the tiles with
+// the longest reduction first (else in problem order); bit 1: one persistent CTA per SM walking
+// the tile list (else one CTA per tile).
 struct GroupedSketch {
   int kind = 0, amode = 0, count = 0, nitems = 0, stage_grid_x = 0;
+  int persistent = 0, grid = 0, nb_max = 0, nacc = 1, stages = 0;
+  uint32_t tmem_cols = 0;
   size_t smem = 0;
   void* d_probs = nullptr;
   int4* d_items = nullptr;
@@ -189,7 +192,7 @@ struct GroupedSketch {
 };
 size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_qmat* X, int compute);
 int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, const qlr_qmat* X, const qlr_qmat* Y,
-                           int compute, int order, char* dev, size_t bytes, GroupedSketch& gs);
+                           int compute, int variant, char* dev, size_t bytes, GroupedSketch& gs);
 int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs);
 
 // orthonormalisation pieces (orth.cu)

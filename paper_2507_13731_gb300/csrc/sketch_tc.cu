@@ -472,6 +472,278 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const 
   sketch_tile<KIND, AMODE>(p, it.z, it.y, 0, 1);
 }
 
+// Persistent grouped form: gridDim.x CTAs (one per SM) walk the item list, CTA b taking items
+// b, b + gridDim.x, ...  The TMA ring, the worker and MMA stage counters run on across items, and
+// the accumulator is double-buffered in TMEM when two fit (nacc = 2): the epilogue drains item t
+// while the MMA warp already accumulates item t + 1 and the producer streams A for the next ones.
+// Shared-memory stages are laid out for the widest column block (nb_max); every problem's tiles
+// use its own nb <= nb_max.
+template <int KIND, int AMODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    sketch_tc_persistent_kernel(const TcParams* __restrict__ probs, const int4* __restrict__ items, int nitems,
+                                int nb_max, int nacc, int stages, uint32_t tmem_cols, int* err) {
+  using C = Cfg<KIND>;
+  constexpr bool X3 = (KIND == K_TF32X3);
+  constexpr bool MN = (AMODE == A_MN);
+  constexpr bool TR = (AMODE == A_T);
+  constexpr bool WORKERS = X3 || TR;
+  constexpr int A_BYTES = TBM * C::SW;
+  constexpr int KSTEPS = C::BK / C::MMA_K;
+  constexpr int ATOM_MN = C::SW / C::ESZ;
+  constexpr int NATOM = TBM / ATOM_MN;
+  constexpr int CH = C::SW / 16;
+  const int STAGES = stages;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int X_BYTES = nb_max * C::SW;
+  const int A_SET = 4 * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
+  const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + MAX_STAGES;
+  uint64_t* ready = bars + 2 * MAX_STAGES;
+  uint64_t* acc_full = bars + 3 * MAX_STAGES;        // [2]
+  uint64_t* acc_empty = bars + 3 * MAX_STAGES + 2;   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAX_STAGES + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int my_items = (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + c * A_BYTES; };
+  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + c * A_BYTES; };
+  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + 4 * A_BYTES + c * A_BYTES; };
+  auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
+  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAX_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&ready[s], 64);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 128);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int t = 0; t < my_items && ok; ++t) {
+        const int4 it = items[blockIdx.x + t * gridDim.x];
+        const TcParams& p = probs[it.x];
+        for (int c = p.c_first; c < 4; ++c)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmA[c]) : "memory");
+        for (int q = 0; q < 4; ++q) {
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmX[q]) : "memory");
+          if (X3) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmXlo[q]) : "memory");
+        }
+        const int64_t m0 = (int64_t)it.y * TBM;
+        const int j0 = it.z * p.nb;
+        const uint32_t tx = (uint32_t)((4 - p.c_first) * A_BYTES + 4 * p.nb * C::SW * (X3 ? 2 : 1));
+        for (int i = 0; i < p.kiters; ++i, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) { ok = false; break; }
+          mbar_expect_tx(&full[s], tx);
+          const int k0 = i * C::BK;
+          for (int c = p.c_first; c < 4; ++c) {
+            if (MN) {
+#pragma unroll
+              for (int a = 0; a < NATOM; ++a)
+                tma_load_2d(smem_u32(a_plane(s, c) + a * C::BK * C::SW), &p.tmA[c], (int)m0 + a * ATOM_MN, k0, &full[s]);
+            } else if (TR) {
+              tma_load_2d(smem_u32(raw_plane(s, c)), &p.tmA[c], (int)m0, k0, &full[s]);
+            } else {
+              tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
+            }
+          }
+          for (int q = 0; q < 4; ++q) {
+            tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
+            if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+          }
+        }
+      }
+      // drain: every issued stage must have landed before the CTA may exit
+      for (int i = max(0, g - STAGES); i < g; ++i) {
+        const int s = i % STAGES;
+        const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        const uint64_t t0 = now_ns();
+        while (!mbar_try_wait(&full[s], ph) && now_ns() - t0 < WAIT_NS) __nanosleep(64);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int t = 0; t < my_items && ok; ++t) {
+        const int4 it = items[blockIdx.x + t * gridDim.x];
+        const TcParams& p = probs[it.x];
+        const int a = t % nacc;
+        if (t >= nacc) {
+          ok = mbar_wait(&acc_empty[a], (uint32_t)((t / nacc) - 1) & 1u, abort_flag, err);
+          if (!ok) break;
+          tc_fence_after();
+        }
+        const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
+        for (int i = 0; i < p.kiters; ++i, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, err);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ++ks) {
+            for (int c = p.c_first; c < 4; ++c) {
+              uint64_t ad, adlo = 0;
+              if (MN) {
+                const uint32_t off = (uint32_t)(ks * C::MMA_K * C::SW);
+                ad = make_desc(smem_u32(a_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
+                if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
+              } else {
+                const uint32_t off = (uint32_t)(ks * C::MMA_K * C::ESZ);
+                ad = make_desc(smem_u32(a_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
+                if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
+              }
+#pragma unroll
+              for (int d = 0; d < 4; ++d) {
+                const int q = c ^ d;
+                const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
+                const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
+                const uint32_t idesc = p.idesc_base | (((p.neg_mask >> (c * 4 + d)) & 1u) << 14);
+                const uint32_t dt = acc_base + (uint32_t)(d * p.nb);
+                const uint32_t acc = (i > 0 || ks > 0 || c > p.c_first) ? 1u : 0u;
+                umma<KIND>(dt, ad, bd, idesc, acc);
+                if (X3) {
+                  const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
+                  umma<KIND>(dt, adlo, bd, idesc, 1u);
+                  umma<KIND>(dt, ad, bdlo, idesc, 1u);
+                }
+              }
+            }
+          }
+          umma_commit(&empty[s]);
+        }
+        umma_commit(&acc_full[a]);   // accumulator of item t complete (also after an abort)
+      }
+    }
+  } else if (warp < 4) {
+    // ---------------- workers: hi/lo split (3xTF32) and/or transpose of A ----------------
+    if (WORKERS) {
+      const int st = threadIdx.x - 64;
+      int g = 0;
+      bool ok = true;
+      for (int t = 0; t < my_items && ok; ++t) {
+        const int4 it = items[blockIdx.x + t * gridDim.x];
+        const TcParams& p = probs[it.x];
+        for (int i = 0; i < p.kiters; ++i, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag, err)) { ok = false; break; }
+          for (int c = p.c_first; c < 4; ++c) {
+            uint4* hi = reinterpret_cast<uint4*>(a_plane(s, c));
+            uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
+            if (TR) {
+              const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_plane(s, c));
+              for (int e = st; e < TBM * CH; e += 64) {
+                const int r = e % TBM, cch = e / TBM;
+                const int sw = (CH == 2) ? ((r >> 2) & 1) : (CH == 4) ? ((r >> 1) & 3) : (r & 7);
+                uint4 v;
+                v.x = raw[(4 * cch + 0) * TBM + r];
+                v.y = raw[(4 * cch + 1) * TBM + r];
+                v.z = raw[(4 * cch + 2) * TBM + r];
+                v.w = raw[(4 * cch + 3) * TBM + r];
+                const int o = r * CH + (cch ^ sw);
+                if (X3) {
+                  uint4 h, rr;
+                  h.x = v.x & 0xFFFFE000u; h.y = v.y & 0xFFFFE000u; h.z = v.z & 0xFFFFE000u; h.w = v.w & 0xFFFFE000u;
+                  rr.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+                  rr.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+                  rr.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+                  rr.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+                  hi[o] = h;
+                  lo[o] = rr;
+                } else {
+                  hi[o] = v;
+                }
+              }
+            } else {
+              for (int e = st; e < A_BYTES / 16; e += 64) {
+                uint4 v = hi[e], h, r;
+                h.x = v.x & 0xFFFFE000u; h.y = v.y & 0xFFFFE000u; h.z = v.z & 0xFFFFE000u; h.w = v.w & 0xFFFFE000u;
+                r.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(h.x));
+                r.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(h.y));
+                r.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(h.z));
+                r.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(h.w));
+                hi[e] = h;
+                lo[e] = r;
+              }
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&ready[s]);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    float v[16];
+    for (int t = 0; t < my_items; ++t) {
+      const int4 it = items[blockIdx.x + t * gridDim.x];
+      const TcParams& p = probs[it.x];
+      const int a = t % nacc;
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(t / nacc) & 1u, abort_flag, err) && !*abort_flag;
+      tc_fence_after();
+      if (!ok) break;
+      const int64_t grow = (int64_t)it.y * TBM + row;
+      const int j0 = it.z * p.nb;
+      const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
+      for (int d = 0; d < 4; ++d) {
+        for (int cc = 0; cc < p.nb; cc += 16) {
+          tmem_ld16(acc_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * p.nb + cc), v);
+          if (grow < p.M) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = j0 + cc + jj;
+              if (j < p.l && cc + jj < p.nb) p.y[d][grow + (int64_t)j * p.ldy] = v[jj];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[a]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
 // Grouped operand staging: problem blockIdx.y's X (FP32, column-major) into its staged buffer.
 struct StageArg {
   const float* x[4];
@@ -657,7 +929,8 @@ size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_q
 }
 
 int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, const qlr_qmat* X, const qlr_qmat* Y,
-                           int compute, int order, char* dev, size_t bytes, GroupedSketch& gs) {
+                           int compute, int variant, char* dev, size_t bytes, GroupedSketch& gs) {
+  const int order = variant & 1;
   if (count <= 0) return QLR_EINVAL;
   const Plan base = make_plan(compute, op, 1, 1, 16, 1);
   const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
@@ -771,6 +1044,15 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   gs.amode = base.amode;
   gs.count = count;
   gs.nitems = (int)hi.size();
+  gs.persistent = (variant >> 1) & 1;
+  gs.nb_max = max_nb;
+  gs.nacc = (2 * 4 * max_nb <= 512) ? 2 : 1;
+  gs.stages = stages;
+  {
+    const int pc = gs.nacc * 4 * max_nb;
+    gs.tmem_cols = pc <= 32 ? 32 : pc <= 64 ? 64 : pc <= 128 ? 128 : pc <= 256 ? 256 : 512;
+  }
+  gs.grid = std::min(gs.nitems, ctx->num_sms > 0 ? ctx->num_sms : 148);
   gs.stage_grid_x = max_stage_blocks;
   gs.smem = stages * stage + 1024 + 256;
   gs.d_probs = d_probs;
@@ -782,6 +1064,17 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
 namespace {
 template <int KIND, int AMODE>
 int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
+  if (gs.persistent) {
+    auto pk = sketch_tc_persistent_kernel<KIND, AMODE>;
+    QLR_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
+    KTimer kt(ctx, QLR_KID_SKETCH_TC);
+    pk<<<(unsigned)gs.grid, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items,
+                                                               gs.nitems, gs.nb_max, gs.nacc, gs.stages, gs.tmem_cols,
+                                                               ctx->d_err);
+    qlr_count_launch();
+    QLR_CUDA_TRY(cudaGetLastError());
+    return QLR_OK;
+  }
   auto kern = sketch_tc_grouped_kernel<KIND, AMODE>;
   QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
   KTimer kt(ctx, QLR_KID_SKETCH_TC);

@@ -54,7 +54,7 @@ class OptsC(ctypes.Structure):
 
 class BatchStatsC(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("graph", ctypes.c_int32), ("tile_order", ctypes.c_int32),
-                ("sketch_launches", ctypes.c_int32), ("tune_ms", ctypes.c_float * 2),
+                ("sketch_launches", ctypes.c_int32), ("tune_ms", ctypes.c_float * 4),
                 ("launches_per_run", ctypes.c_int64)]
 
 
@@ -340,7 +340,7 @@ class Batch:
         st = BatchStatsC()
         _check(lib().qlr_batch_info(self.h, ctypes.byref(st)), "qlr_batch_info")
         return {"lanes": st.lanes, "graph": bool(st.graph), "tile_order": st.tile_order,
-                "sketch_launches": st.sketch_launches, "tune_ms": [st.tune_ms[0], st.tune_ms[1]],
+                "sketch_launches": st.sketch_launches, "tune_ms": list(st.tune_ms),
                 "launches_per_run": st.launches_per_run}
 
     def close(self) -> None:
