@@ -59,16 +59,22 @@ __device__ __forceinline__ void rr_pair(int lp, int r, int i, int& p, int& q) {
   }
 }
 
+// Vout != nullptr (W in shared memory and room for V next to it): the rotations are applied to
+// V = I in place as well, and neither the log nor the replay is needed.
 template <class T>
 __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R, int l, T* __restrict__ Wout,
                                                      bool w_smem, int max_sweeps, T tol, T* __restrict__ sig_out,
-                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err) {
+                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err,
+                                                     T* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot;
   T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
   const size_t ll = (size_t)l * l;
+  T* Vs = Vout ? reinterpret_cast<T*>(smem_raw) + 4 * ll : nullptr;
   for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
+  if (Vs)
+    for (size_t e = t; e < 4 * ll; e += JT) Vs[e] = (e < ll && e % (l + 1) == 0) ? (T)1 : (T)0;
   __syncthreads();
   const int lp = l + (l & 1);
   int sweep = 0;
@@ -93,9 +99,9 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
         a = warp_sum(a); b = warp_sum(b);
         g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
         T gn = sqrt(qnorm2(g));
-        T* lg = rlog + (((size_t)sweep * (lp - 1) + r) * (lp / 2) + pi) * 6;
+        T* lg = Vs ? nullptr : rlog + (((size_t)sweep * (lp - 1) + r) * (lp / 2) + pi) * 6;
         if (!(gn > tol * sqrt(a * b)) || gn == (T)0) {
-          if (lane == 0) { lg[0] = (T)1; lg[1] = (T)0; lg[2] = (T)1; lg[3] = lg[4] = lg[5] = (T)0; }
+          if (lane == 0 && lg) { lg[0] = (T)1; lg[1] = (T)0; lg[2] = (T)1; lg[3] = lg[4] = lg[5] = (T)0; }
           continue;
         }
         if (lane == 0) s_rot = 1;
@@ -103,13 +109,18 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
         T zeta = (b - a) / (2 * gn);
         T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
         T c = (T)1 / sqrt((T)1 + tt * tt), s = c * tt;
-        if (lane == 0) { lg[0] = c; lg[1] = s; lg[2] = mu.w; lg[3] = mu.x; lg[4] = mu.y; lg[5] = mu.z; }
+        if (lane == 0 && lg) { lg[0] = c; lg[1] = s; lg[2] = mu.w; lg[3] = mu.x; lg[4] = mu.y; lg[5] = mu.z; }
         for (int i = lane; i < l; i += 32) {
           Quat<T> wp = ldw(W, l, i, p), wq = qmulc(ldw(W, l, i, q), mu);   // w_q mu*
           Quat<T> np = {c * wp.w - s * wq.w, c * wp.x - s * wq.x, c * wp.y - s * wq.y, c * wp.z - s * wq.z};
           Quat<T> nq = {s * wp.w + c * wq.w, s * wp.x + c * wq.x, s * wp.y + c * wq.y, s * wp.z + c * wq.z};
           stw(W, l, i, p, np);
           stw(W, l, i, q, nq);
+          if (Vs) {                              // the same right rotation on V
+            Quat<T> vp = ldw(Vs, l, i, p), vq = qmulc(ldw(Vs, l, i, q), mu);
+            stw(Vs, l, i, p, {c * vp.w - s * vq.w, c * vp.x - s * vq.x, c * vp.y - s * vq.y, c * vp.z - s * vq.z});
+            stw(Vs, l, i, q, {s * vp.w + c * vq.w, s * vp.x + c * vq.x, s * vp.y + c * vq.y, s * vp.z + c * vq.z});
+          }
         }
       }
       __syncthreads();
@@ -136,6 +147,8 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
   __syncthreads();
   if (w_smem)
     for (size_t e = t; e < 4 * ll; e += JT) Wout[e] = W[e];
+  if (Vs)
+    for (size_t e = t; e < 4 * ll; e += JT) Vout[e] = Vs[e];
 }
 
 // Replay the logged rotations on V = I, one warp per row of V (rows are independent under right
@@ -601,16 +614,19 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   } else {
     const size_t one = ll4 * sizeof(T);
     const bool w_smem = one <= 220 * 1024;
-    const size_t smem = w_smem ? one : 0;
+    // many concurrent small problems: V accumulated in place (no log, no replay launch)
+    const bool vin = ctx->small_mode && 2 * one <= 220 * 1024;
+    const size_t smem = vin ? 2 * one : (w_smem ? one : 0);
     if (smem > 0)
       QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
-      jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err);
+      jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err,
+                                                     vin ? V : nullptr);
       qlr_count_launch();
     }
     QLR_CUDA_TRY(cudaGetLastError());
-    {
+    if (!vin) {
       KTimer kt(ctx, QLR_KID_JACOBI);
       const size_t rs = (size_t)4 * 4 * l * sizeof(T);
       // static shared memory comes on top of the dynamic size: always opt in

@@ -611,16 +611,22 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
 // Whole Cholesky factorisation of a small Gram (l <= CS_MAX_L) in one CTA, for many concurrent
 // small problems: the upper triangle packed by columns in shared memory (column k at offset
 // k (k + 1) / 2, rows 0..k, plane-interleaved), right-looking with the rank-1 updates' (row,
-// column) pairs enumerated densely over all threads; then the CB x CB diagonal-block inverses.
+// column) pairs enumerated densely over all threads.  Then either the CB x CB diagonal-block
+// inverses (for the blocked triangular inverse) or, with Rinv != nullptr (l <= CS_INV_MAX_L), the
+// whole inverse by column-oriented back substitution in a second packed triangle.
 constexpr int CS_THREADS = 512;
 constexpr int CS_MAX_L = 96;
+constexpr int CS_INV_MAX_L = 80;
 
 __global__ void __launch_bounds__(CS_THREADS, 1) chol_single_kernel(const double* __restrict__ G, double* __restrict__ R,
                                                                     double* __restrict__ Dinv_all, int l,
-                                                                    double shift_coef, int* err, const int* run_if) {
+                                                                    double shift_coef, int* err, const int* run_if,
+                                                                    double* __restrict__ Rinv) {
   if (run_if && *run_if == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double4* W = reinterpret_cast<double4*>(smem_raw);
+  double* rpv_all = reinterpret_cast<double*>(W + l * (l + 1) / 2);     // 1 / r_jj, l values
+  double4* Xp = reinterpret_cast<double4*>(rpv_all + ((l + 3) / 4) * 4);  // packed inverse (Rinv only)
   __shared__ double s_shift, s_rp;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32;
   const size_t ll = (size_t)l * l;
@@ -651,6 +657,7 @@ __global__ void __launch_bounds__(CS_THREADS, 1) chol_single_kernel(const double
       }
       const double rp = rsqrt_newton(d);
       s_rp = rp;
+      rpv_all[j] = rp;
       at(j, j) = make_double4(d * rp, 0.0, 0.0, 0.0);
     }
     __syncthreads();
@@ -674,6 +681,39 @@ __global__ void __launch_bounds__(CS_THREADS, 1) chol_single_kernel(const double
     const int i = e % l, k = e / l;
     const double4 r = (i <= k) ? at(i, k) : make_double4(0.0, 0.0, 0.0, 0.0);
     R[e] = r.x; R[ll + e] = r.y; R[2 * ll + e] = r.z; R[3 * ll + e] = r.w;
+  }
+  if (Rinv) {
+    // X = R^{-1}: for i = l-1 .. 0, X[i, i:] = Y[i, i:] / r_ii, then Y[0:i, i:] -= R[0:i, i] X[i, i:]
+    // (Y starts as the identity; row i of X is zero left of the diagonal)
+    auto xt = [&](int i, int k) -> double4& { return Xp[k * (k + 1) / 2 + i]; };
+    for (int e = t; e < ntri; e += CS_THREADS) {
+      const int2 ik = upper_tri_entry(e);
+      Xp[e] = make_double4(ik.x == ik.y ? 1.0 : 0.0, 0.0, 0.0, 0.0);
+    }
+    __syncthreads();
+    for (int i = l - 1; i >= 0; --i) {
+      const int w = l - i;
+      const double rp = rpv_all[i];
+      for (int e = t; e < w; e += CS_THREADS) {
+        double4& x = xt(i, i + e);
+        x = make_double4(x.x * rp, x.y * rp, x.z * rp, x.w * rp);
+      }
+      __syncthreads();
+      for (int e = t; e < i * w; e += CS_THREADS) {   // rows r < i, columns j >= i
+        const int r = e % i, j = i + e / i;
+        const double4 a = at(r, i), b = xt(i, j);
+        const Quat<double> pr = qmul(Quat<double>{a.x, a.y, a.z, a.w}, Quat<double>{b.x, b.y, b.z, b.w});
+        double4& x = xt(r, j);
+        x.x -= pr.w; x.y -= pr.x; x.z -= pr.y; x.w -= pr.z;
+      }
+      __syncthreads();
+    }
+    for (int e = t; e < (int)ll; e += CS_THREADS) {
+      const int i = e % l, k = e / l;
+      const double4 r = (i <= k) ? xt(i, k) : make_double4(0.0, 0.0, 0.0, 0.0);
+      Rinv[e] = r.x; Rinv[ll + e] = r.y; Rinv[2 * ll + e] = r.z; Rinv[3 * ll + e] = r.w;
+    }
+    return;
   }
   __shared__ double D[4][CB][CB];
   __shared__ double X[4][CB][CB];
@@ -1113,10 +1153,11 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
   if (l == 0) return QLR_OK;
   const size_t ll4 = (size_t)4 * l * l;
   if (ctx->small_mode && l <= CS_MAX_L && Dinv_all != nullptr) {
-    const size_t smem = (size_t)l * (l + 1) / 2 * 32;   // plus 16.5 KB static: always opt in
+    const size_t smem = (size_t)l * (l + 1) / 2 * 32 + (size_t)(l + 3) / 4 * 32;   // + 16.5 KB static: opt in
     QLR_CUDA_TRY(cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KTimer kt(ctx, QLR_KID_CHOL);
-    chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if);
+    chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if,
+                                                             nullptr);
     qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
     return QLR_OK;
@@ -1168,6 +1209,18 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
+  return QLR_OK;
+}
+
+// Small problems in throughput mode: factor and invert in one single-CTA launch.
+static int chol_inv_small(qlr_ctx* ctx, int l, const double* G, double* R, double* Rinv, double shift_coef) {
+  const size_t tri = (size_t)l * (l + 1) / 2 * 32;
+  const size_t smem = 2 * tri + (size_t)(l + 3) / 4 * 32;   // + 16.5 KB static: opt in
+  QLR_CUDA_TRY(cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTimer kt(ctx, QLR_KID_CHOL);
+  chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, nullptr, l, shift_coef, ctx->d_err, nullptr, Rinv);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
 
@@ -1302,7 +1355,9 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     qlr_qmat& dst = const_cast<qlr_qmat&>(*seq[s + 1]);
     double* Rcur = (s == 0) ? Rprod : Rs;
     QLR_TRY(gram(ctx, src, G, ws));
-    if (s == 1 && orth == QLR_ORTH_CHOLQR2 && !(ctx->small_mode && l <= CS_MAX_L)) {
+    if (ctx->small_mode && l <= CS_INV_MAX_L) {
+      QLR_TRY(chol_inv_small(ctx, l, G, Rcur, Rinv, (s == 0) ? shift : 0.0));
+    } else if (s == 1 && orth == QLR_ORTH_CHOLQR2 && !(ctx->small_mode && l <= CS_MAX_L)) {
       int* use_chol = nullptr;
       QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol));
       QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol));     // only if the series test failed
