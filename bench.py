@@ -264,12 +264,52 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def batch_driver(args):
+    """--only batch: the batched workload's plan (built once), then `warmup + steps` runs;
+    QLR_BATCH_VARIANT=0..3 fixes the grouped sketch variant.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    probs = synth.batched_problems()
+    ctx = qlr.Context(0)
+    As = []
+    for P in probs:
+        t = qlr.empty_rowmajor(P.m, P.n, 3, torch.bfloat16)
+        t.copy_(torch.from_numpy(np.ascontiguousarray(P.A[1:])).to(torch.bfloat16))
+        As.append(t)
+    Os = [qlr.to_thin(torch.from_numpy(P.Omega).float().cuda()) for P in probs]
+    Us = [qlr.empty_thin(P.m, P.k) for P in probs]
+    Vs = [qlr.empty_thin(P.n, P.k) for P in probs]
+    Ss = [torch.zeros(P.k, dtype=torch.float64, device="cuda") for P in probs]
+    b = qlr.Batch(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs)
+    for _ in range(args.warmup):
+        b.run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    rc = ctx.sync()
+    print(json.dumps({"only": "batch", "ms_per_run": e0.elapsed_time(e1) / args.steps, "info": b.info(),
+                      "device_error": rc}), flush=True)
+    b.close()
+    ctx.close()
+    return 0 if rc == 0 else 1
+
+
 def profile_driver(args):
     """Small driver for ncu captures: the bench workload's A and Omega, then `warmup + steps`
     calls of one sketch pass (--only sketch --op N|H) or one QSVD with --passes v (--only qsvd).
     Prints one JSON line with the mean CUDA-event time of the timed calls."""
     import numpy as np
     import torch
+
+    if args.only == "batch":
+        return batch_driver(args)
 
     import synth
     from paper_2507_13731_gb300 import build, qlr
@@ -315,8 +355,8 @@ def main():
     ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
-    ap.add_argument("--only", choices=["sketch", "qsvd"], default=None,
-                    help="profiling driver: time only sketch passes or single QSVDs (for ncu captures)")
+    ap.add_argument("--only", choices=["sketch", "qsvd", "batch"], default=None,
+                    help="profiling driver: time only sketch passes, single QSVDs or batch runs (for ncu captures)")
     ap.add_argument("--op", choices=["N", "H"], default="N")
     ap.add_argument("--passes", type=int, default=4)
     args = ap.parse_args()

@@ -129,7 +129,8 @@ const char* qlr_strerror(int code);
 #define QLR_KID_JACOBI 6      /* core QSVD sweeps                            */
 #define QLR_KID_REFINE 7      /* core QSVD FP64 evaluation + ranking         */
 #define QLR_KID_MISC 8        /* conversions, operand staging, small products */
-#define QLR_KID_COUNT 9
+#define QLR_KID_SERIES 9      /* CholeskyQR2 second step by series (factor and inverse) */
+#define QLR_KID_COUNT 10
 int qlr_set_timing(qlr_ctx* ctx, int enable);
 int qlr_reset_stats(qlr_ctx* ctx);
 int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);

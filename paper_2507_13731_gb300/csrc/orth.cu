@@ -1285,7 +1285,7 @@ static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, doubl
   const int nent = l * (l + 1) / 2;
   if (!ws.ok) return QLR_ENOMEM;
   QLR_CUDA_TRY(cudaMemsetAsync(emax, 0, (1 + SERIES_ITERS + NEUMANN_ITERS) * sizeof(unsigned long long), ctx->stream));
-  KTimer kt(ctx, QLR_KID_CHOL);
+  KTimer kt(ctx, QLR_KID_SERIES);
   const int64_t tot = (int64_t)l * l;
   const unsigned gsq = (unsigned)((tot + 127) / 128);
   const unsigned gst = (unsigned)(((int64_t)nent * SPLIT + 127) / 128);

@@ -33,7 +33,7 @@ FLAG_QR_EVERY_PASS = 1
 FLAG_NO_GRAPH = 2
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
-KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc"]
+KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series"]
 
 
 class QlrError(RuntimeError):
