@@ -226,6 +226,22 @@ def batched_leg(dev, steps=5):
             "device_error": rc}
 
 
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest of the ranks' values (the whole job is as slow as its slowest replica)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, elapsed_ms: float) -> float:
+    """Units processed by all replicas per second, timed by the slowest one."""
+    return ws * units_per_rank / (elapsed_ms / 1e3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -434,13 +450,9 @@ def main():
     elapsed_ms = t0e.elapsed_time(t1e)
     stats = ctx.stats()
     rc = ctx.sync()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
     passes_per_step = sum(PASSES)
-    value = ws * passes_per_step * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_rate(passes_per_step * args.steps, ws, elapsed_ms)
     a_bytes = A.numel() * A.element_size()
     tbs = ws * passes_per_step * args.steps * a_bytes / (elapsed_ms / 1e3) / 1e12
     gpu_launches = sum(n for n, _ in stats.values())
@@ -464,12 +476,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * passes_per_step * e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+    e2e_value = whole_job_rate(passes_per_step * e2e_steps, ws, e2e_ms)
     h2d = A_host.numel() * A_host.element_size() + Om_host.numel() * Om_host.element_size()
     d2h = U_h.numel() * 4 + V_h.numel() * 4 + S_h.numel() * 8
 

@@ -65,6 +65,29 @@ struct TcParams {
   int* err;
 };
 
+// The scalar part of TcParams, copied into registers once: with the parameters in global memory
+// (grouped launches), every asm statement with a memory clobber and every store of the output
+// would otherwise force the fields to be reloaded.
+struct TcScalars {
+  float *y0, *y1, *y2, *y3;                // output planes (selected without an indexed array)
+  int64_t ldy;
+  float* part;
+  unsigned* counters;
+  int64_t M;
+  int l, nb, ncb, kiters, kper, nsplit, c_first, stages;
+  uint32_t neg_mask, idesc_base, tmem_cols;
+  int* err;
+  __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
+};
+__device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
+  TcScalars v;
+  v.y0 = p.y[0]; v.y1 = p.y[1]; v.y2 = p.y[2]; v.y3 = p.y[3];
+  v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
+  v.kiters = p.kiters; v.kper = p.kper; v.nsplit = p.nsplit; v.c_first = p.c_first; v.stages = p.stages;
+  v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
+  return v;
+}
+
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -142,6 +165,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// 16 consecutive TMEM columns of this warp's 32 lanes; the registers are valid only after
+// tmem_wait_ld(), so several loads can be in flight before one wait.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -178,6 +212,7 @@ template <int KIND, int AMODE>
 __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, const int mt, const int split,
                                             const int mtiles) {
   using C = Cfg<KIND>;
+  const TcScalars pv = tc_scalars(p);
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
   constexpr bool TR = (AMODE == A_T);
@@ -187,11 +222,11 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   constexpr int ATOM_MN = C::SW / C::ESZ;              // MN-major: elements per atom row
   constexpr int NATOM = TBM / ATOM_MN;
   constexpr int CH = C::SW / 16;                       // 16-byte chunks per K-major row
-  const int STAGES = p.stages;
+  const int STAGES = pv.stages;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int nb = p.nb;
+  const int nb = pv.nb;
   const int X_BYTES = nb * C::SW;
   const int A_SET = 4 * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));   // [raw][hi][lo]
   const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
@@ -207,8 +242,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t m0 = (int64_t)mt * TBM;
   const int j0 = cb * nb;
-  const int it0 = split * p.kper;
-  const int it1 = min(p.kiters, it0 + p.kper);
+  const int it0 = split * pv.kper;
+  const int it1 = min(pv.kiters, it0 + pv.kper);
   const int nit = it1 - it0;
 
   constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
@@ -232,7 +267,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(p.tmem_cols)
+                 "r"(pv.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -244,15 +279,15 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const uint32_t tx = (uint32_t)((4 - p.c_first) * A_BYTES + 4 * X_BYTES * (X3 ? 2 : 1));
+      const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + 4 * X_BYTES * (X3 ? 2 : 1));
       int issued = 0;
       for (int i = 0; i < nit; ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, pv.err)) break;
         mbar_expect_tx(&full[s], tx);
         const int k0 = (it0 + i) * C::BK;
-        for (int c = p.c_first; c < 4; ++c) {
+        for (int c = pv.c_first; c < 4; ++c) {
           if (MN) {
 #pragma unroll
             for (int a = 0; a < NATOM; ++a)
@@ -284,12 +319,12 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
       for (int i = 0; i < nit && ok; ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-        ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, p.err);
+        ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, pv.err);
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
         for (int ks = 0; ks < KSTEPS; ++ks) {
-          for (int c = p.c_first; c < 4; ++c) {
+          for (int c = pv.c_first; c < 4; ++c) {
             uint64_t ad, adlo = 0;
             if (MN) {
               // MN-major: LBO = stride between MN atoms, SBO = stride between 8-row K groups
@@ -306,9 +341,9 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
               const int q = c ^ d;
               const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
               const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-              const uint32_t idesc = p.idesc_base | (((p.neg_mask >> (c * 4 + d)) & 1u) << 14);
+              const uint32_t idesc = pv.idesc_base | (((pv.neg_mask >> (c * 4 + d)) & 1u) << 14);
               const uint32_t dt = tmem + (uint32_t)(d * nb);
-              const uint32_t acc = (i > 0 || ks > 0 || c > p.c_first) ? 1u : 0u;
+              const uint32_t acc = (i > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
               umma<KIND>(dt, ad, bd, idesc, acc);
               if (X3) {
                 const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
@@ -329,8 +364,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
       for (int i = 0; i < nit; ++i) {
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph, abort_flag, p.err)) break;
-        for (int c = p.c_first; c < 4; ++c) {
+        if (!mbar_wait(&full[s], ph, abort_flag, pv.err)) break;
+        for (int c = pv.c_first; c < 4; ++c) {
           uint4* hi = reinterpret_cast<uint4*>(a_plane(s, c));
           uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
           if (TR) {
@@ -381,49 +416,58 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row = q * 32 + lane;
     const int64_t grow = m0 + row;
-    const bool ok = mbar_wait(tmem_full, 0, abort_flag, p.err) && !*abort_flag;
+    const bool ok = mbar_wait(tmem_full, 0, abort_flag, pv.err) && !*abort_flag;
     tc_fence_after();
-    const int tile = mt * p.ncb + cb;
+    const int tile = mt * pv.ncb + cb;
     const size_t tile_elems = (size_t)4 * TBM * nb;
     float v[16];
     if (ok && nit > 0) {
       for (int d = 0; d < 4; ++d) {
-        for (int cc = 0; cc < nb; cc += 16) {
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc), v);
-          if (p.nsplit == 1) {
-            if (grow < p.M) {
+        for (int cc = 0; cc < nb; cc += (pv.nsplit == 1 ? 32 : 16)) {
+          if (pv.nsplit == 1) {
+            // two loads in flight per wait (nb is a multiple of 16)
+            uint32_t r0[16], r1[16];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
+            tmem_ld16_issue(ta, r0);
+            if (cc + 16 < nb) tmem_ld16_issue(ta + 16, r1);
+            tmem_wait_ld();
+            if (grow < pv.M) {
+              float* yd = pv.y(d) + grow;
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj) {
+              for (int jj = 0; jj < 32; ++jj) {
                 const int j = j0 + cc + jj;
-                if (j < p.l && cc + jj < nb) p.y[d][grow + (int64_t)j * p.ldy] = v[jj];
+                if (j < pv.l && cc + jj < nb) yd[(int64_t)j * pv.ldy] = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
               }
             }
-          } else {
-            float* P = p.part + ((size_t)split * mtiles * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
+            continue;
+          }
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc), v);
+          {
+            float* P = pv.part + ((size_t)split * mtiles * pv.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) P[(size_t)(cc + jj) * TBM + row] = v[jj];
           }
         }
       }
     }
-    if (p.nsplit > 1) {
+    if (pv.nsplit > 1) {
       __threadfence();
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (threadIdx.x == 128) {
-        const unsigned old = atomicAdd(&p.counters[tile], 1u);
-        *last_flag = (old == (unsigned)(p.nsplit - 1)) ? 1 : 0;
+        const unsigned old = atomicAdd(&pv.counters[tile], 1u);
+        *last_flag = (old == (unsigned)(pv.nsplit - 1)) ? 1 : 0;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (*last_flag) {
         __threadfence();
-        if (grow < p.M) {
+        if (grow < pv.M) {
           for (int d = 0; d < 4; ++d)
             for (int jc0 = 0; jc0 < nb; jc0 += 16) {
               float acc[16];
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
-              for (int sp = 0; sp < p.nsplit; ++sp) {
-                const float* P = p.part + ((size_t)sp * mtiles * p.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
+              for (int sp = 0; sp < pv.nsplit; ++sp) {
+                const float* P = pv.part + ((size_t)sp * mtiles * pv.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
                                  (size_t)jc0 * TBM + row;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) acc[jj] += __ldcg(P + (size_t)jj * TBM);   // 16 loads in flight
@@ -431,11 +475,11 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) {
                 const int j = j0 + jc0 + jj;
-                if (jc0 + jj < nb && j < p.l) p.y[d][grow + (int64_t)j * p.ldy] = acc[jj];
+                if (jc0 + jj < nb && j < pv.l) pv.y(d)[grow + (int64_t)j * pv.ldy] = acc[jj];
               }
             }
         }
-        if (threadIdx.x == 128) p.counters[tile] = 0u;
+        if (threadIdx.x == 128) pv.counters[tile] = 0u;
       }
     }
   }
@@ -444,7 +488,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(pv.tmem_cols) : "memory");
   }
 }
 
@@ -550,22 +594,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
         const TcParams& p = probs[it.x];
-        for (int c = p.c_first; c < 4; ++c)
+        const TcScalars pv = tc_scalars(p);
+        for (int c = pv.c_first; c < 4; ++c)
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmA[c]) : "memory");
         for (int q = 0; q < 4; ++q) {
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmX[q]) : "memory");
           if (X3) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmXlo[q]) : "memory");
         }
         const int64_t m0 = (int64_t)it.y * TBM;
-        const int j0 = it.z * p.nb;
-        const uint32_t tx = (uint32_t)((4 - p.c_first) * A_BYTES + 4 * p.nb * C::SW * (X3 ? 2 : 1));
-        for (int i = 0; i < p.kiters; ++i, ++g) {
+        const int j0 = it.z * pv.nb;
+        const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + 4 * pv.nb * C::SW * (X3 ? 2 : 1));
+        for (int i = 0; i < pv.kiters; ++i, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) { ok = false; break; }
           mbar_expect_tx(&full[s], tx);
           const int k0 = i * C::BK;
-          for (int c = p.c_first; c < 4; ++c) {
+          for (int c = pv.c_first; c < 4; ++c) {
             if (MN) {
 #pragma unroll
               for (int a = 0; a < NATOM; ++a)
@@ -598,6 +643,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
         const TcParams& p = probs[it.x];
+        const TcScalars pv = tc_scalars(p);
         const int a = t % nacc;
         if (t >= nacc) {
           ok = mbar_wait(&acc_empty[a], (uint32_t)((t / nacc) - 1) & 1u, abort_flag, err);
@@ -605,7 +651,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
         }
         const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
-        for (int i = 0; i < p.kiters; ++i, ++g) {
+        for (int i = 0; i < pv.kiters; ++i, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
           ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, err);
@@ -613,7 +659,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
 #pragma unroll
           for (int ks = 0; ks < KSTEPS; ++ks) {
-            for (int c = p.c_first; c < 4; ++c) {
+            for (int c = pv.c_first; c < 4; ++c) {
               uint64_t ad, adlo = 0;
               if (MN) {
                 const uint32_t off = (uint32_t)(ks * C::MMA_K * C::SW);
@@ -629,9 +675,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int q = c ^ d;
                 const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
                 const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-                const uint32_t idesc = p.idesc_base | (((p.neg_mask >> (c * 4 + d)) & 1u) << 14);
-                const uint32_t dt = acc_base + (uint32_t)(d * p.nb);
-                const uint32_t acc = (i > 0 || ks > 0 || c > p.c_first) ? 1u : 0u;
+                const uint32_t idesc = pv.idesc_base | (((pv.neg_mask >> (c * 4 + d)) & 1u) << 14);
+                const uint32_t dt = acc_base + (uint32_t)(d * pv.nb);
+                const uint32_t acc = (i > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
                 umma<KIND>(dt, ad, bd, idesc, acc);
                 if (X3) {
                   const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
@@ -655,11 +701,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
         const TcParams& p = probs[it.x];
-        for (int i = 0; i < p.kiters; ++i, ++g) {
+        const TcScalars pv = tc_scalars(p);
+        for (int i = 0; i < pv.kiters; ++i, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
           if (!mbar_wait(&full[s], ph, abort_flag, err)) { ok = false; break; }
-          for (int c = p.c_first; c < 4; ++c) {
+          for (int c = pv.c_first; c < 4; ++c) {
             uint4* hi = reinterpret_cast<uint4*>(a_plane(s, c));
             uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
             if (TR) {
@@ -712,21 +759,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = 0; t < my_items; ++t) {
       const int4 it = items[blockIdx.x + t * gridDim.x];
       const TcParams& p = probs[it.x];
+      const TcScalars pv = tc_scalars(p);
       const int a = t % nacc;
       const bool ok = mbar_wait(&acc_full[a], (uint32_t)(t / nacc) & 1u, abort_flag, err) && !*abort_flag;
       tc_fence_after();
       if (!ok) break;
       const int64_t grow = (int64_t)it.y * TBM + row;
-      const int j0 = it.z * p.nb;
+      const int j0 = it.z * pv.nb;
       const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
       for (int d = 0; d < 4; ++d) {
-        for (int cc = 0; cc < p.nb; cc += 16) {
-          tmem_ld16(acc_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * p.nb + cc), v);
-          if (grow < p.M) {
+        for (int cc = 0; cc < pv.nb; cc += 32) {
+          uint32_t r0[16], r1[16];
+          const uint32_t ta = acc_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * pv.nb + cc);
+          tmem_ld16_issue(ta, r0);
+          if (cc + 16 < pv.nb) tmem_ld16_issue(ta + 16, r1);
+          tmem_wait_ld();
+          if (grow < pv.M) {
+            float* yd = pv.y(d) + grow;
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
+            for (int jj = 0; jj < 32; ++jj) {
               const int j = j0 + cc + jj;
-              if (j < p.l && cc + jj < p.nb) p.y[d][grow + (int64_t)j * p.ldy] = v[jj];
+              if (j < pv.l && cc + jj < pv.nb) yd[(int64_t)j * pv.ldy] = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
             }
           }
         }
