@@ -21,7 +21,8 @@ size_t gram_ws_bound(int64_t l) {
 }
 
 size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
-  return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * rows * l * esz + gram_ws_bound(l) + 16 * 256;
+  return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * (rows + 4) * l * esz + (size_t)16 * l * l +
+         gram_ws_bound(l) + 16 * 256;
 }
 
 size_t tsvd_ws_bound(int64_t l) { return core_tsvd_ws((int)l) + 16384; }
@@ -104,9 +105,11 @@ struct Sched {
     return qlr::sketch_tc(ctx, op, *A, B, Y, compute, *ws);
   }
 
+  // column pitch a multiple of 4 elements (16 bytes in FP32): the tensor-core thin x small
+  // products read these through TMA
   qlr_qmat thin(int64_t rows, int64_t cols, int dt = -1) {
     qlr_qmat q{};
-    q.rows = rows; q.cols = cols; q.ld = std::max<int64_t>(rows, 1);
+    q.rows = rows; q.cols = cols; q.ld = std::max<int64_t>((rows + 3) / 4 * 4, 1);
     q.layout = QLR_COL_MAJOR; q.dtype = dt < 0 ? tdt : dt;
     size_t esz = qlr_dtype_size(q.dtype);
     char* p = ws->take<char>((size_t)4 * q.ld * cols * esz);
@@ -121,17 +124,6 @@ qlr_qmat col_slice(const qlr_qmat& q, int64_t c0, int64_t nc) {
   for (int c = 0; c < 4; ++c) s.plane[c] = q.plane[c] ? static_cast<char*>(q.plane[c]) + (size_t)c0 * q.ld * esz : nullptr;
   s.cols = nc;
   return s;
-}
-
-// C (rows x k) = Q (rows x l) * S (FP64 small l x k, plane stride l*k)
-int lift(qlr_ctx* ctx, const qlr_qmat& Q, const double* S, int l, int k, qlr_qmat& C) {
-  qlr::GemmArgs g{};
-  for (int c = 0; c < 4; ++c) { g.a[c] = Q.plane[c]; g.b[c] = S + (size_t)c * l * k; g.c[c] = C.plane[c]; }
-  g.sa_i = 1; g.sa_k = Q.ld; g.i_contig = true; g.conj_a = false; g.a_dtype = Q.dtype;
-  g.ldb = l; g.b_dtype = QLR_F64; g.ldc = C.ld; g.c_dtype = C.dtype;
-  g.M = Q.rows; g.N = k; g.K = l; g.alpha = 1.0; g.beta = 0.0;
-  g.acc64 = (Q.dtype == QLR_F64 || C.dtype == QLR_F64);
-  return qlr::gemm_simt(ctx, g);
 }
 
 // Common argument checks for the algorithm entry points; resolves compute and side.
@@ -256,10 +248,10 @@ size_t lowrank_ws(int64_t m, int64_t n, int k, int p, int v, int algo, int compu
   const size_t esz = (compute == QLR_COMPUTE_F64) ? 8 : 4;
   const int64_t rows = std::max(m, n);
   size_t b = 0;
-  b += (size_t)4 * esz * (m + n) * l * 4;        // Y, Z, q1cur, q2cur
-  b += (size_t)4 * esz * rows * L * 3;           // K, W, Q1/Q2 (stacked)
-  b += (size_t)4 * esz * (m + n) * L;            // Q1, Q2 when not caller-provided
-  b += (size_t)4 * esz * rows * l;               // omega conversion
+  b += (size_t)4 * esz * (m + n + 8) * l * 4;    // Y, Z, q1cur, q2cur (pitch padded to 4 rows)
+  b += (size_t)4 * esz * (rows + 4) * L * 3;     // K, W, Q1/Q2 (stacked)
+  b += (size_t)4 * esz * (m + n + 8) * L;        // Q1, Q2 when not caller-provided
+  b += (size_t)4 * esz * (rows + 4) * l;         // omega conversion
   b += (size_t)32 * L * L * 2 + (size_t)64 * L * k + 8 * k;
   b += cholqr_ws_bound(rows, L, esz) + tsvd_ws_bound(L);
   b += qlr::sketch_tc_ws(rows, L, 160);           // tensor-core operand staging + split-K partials
@@ -562,8 +554,8 @@ static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passe
   const double* Vhat = (passes % 2 == 0) ? Lm : Rt;
   qlr_qmat* UX = (side == QLR_SIDE_X) ? U : V;   // U of the algorithm's X
   qlr_qmat* VX = (side == QLR_SIDE_X) ? V : U;
-  QLR_TRY(lift(ctx, Q1, Uhat, (int)L, k, *UX));          // U = Q1 U_hat
-  QLR_TRY(lift(ctx, Q2, Vhat, (int)L, k, *VX));          // V = Q2 V_hat
+  QLR_TRY(qlr::thin_times_small(ctx, Q1, Uhat, (int)L, k, *UX, ws));   // U = Q1 U_hat
+  QLR_TRY(qlr::thin_times_small(ctx, Q2, Vhat, (int)L, k, *VX, ws));   // V = Q2 V_hat
   return QLR_OK;
 }
 

@@ -72,10 +72,12 @@ int check_q(const qlr_qmat* q, int layout, int dtype, bool allow_pure) {
   return QLR_OK;
 }
 
+// Column-major FP32 thin matrix with a 16-byte multiple column pitch (the tensor-core thin x
+// small products read it through TMA).
 qlr_qmat thin_at(char*& cur, int64_t rows, int64_t cols) {
   qlr_qmat q{};
-  q.rows = rows; q.cols = cols; q.ld = rows; q.layout = QLR_COL_MAJOR; q.dtype = QLR_F32;
-  const size_t plane = (size_t)rows * cols * 4;
+  q.rows = rows; q.cols = cols; q.ld = (rows + 3) / 4 * 4; q.layout = QLR_COL_MAJOR; q.dtype = QLR_F32;
+  const size_t plane = (size_t)q.ld * cols * 4;
   for (int c = 0; c < 4; ++c) q.plane[c] = cur + (size_t)c * plane;
   cur += (4 * plane + 255) / 256 * 256;
   return q;
@@ -85,17 +87,6 @@ double* small_at(char*& cur, size_t doubles) {
   double* p = reinterpret_cast<double*>(cur);
   cur += (doubles * 8 + 255) / 256 * 256;
   return p;
-}
-
-// C (rows x k) = Q (rows x l) * S (FP64 small l x k, plane stride l*k)
-int lift(qlr_ctx* ctx, const qlr_qmat& Q, const double* S, int l, int k, qlr_qmat& C) {
-  qlr::GemmArgs g{};
-  for (int c = 0; c < 4; ++c) { g.a[c] = Q.plane[c]; g.b[c] = S + (size_t)c * l * k; g.c[c] = C.plane[c]; }
-  g.sa_i = 1; g.sa_k = Q.ld; g.i_contig = true; g.conj_a = false; g.a_dtype = Q.dtype;
-  g.ldb = l; g.b_dtype = QLR_F64; g.ldc = C.ld; g.c_dtype = C.dtype;
-  g.M = Q.rows; g.N = k; g.K = l; g.alpha = 1.0; g.beta = 0.0;
-  g.acc64 = false;
-  return qlr::gemm_simt(ctx, g);
 }
 
 const qlr::GroupedSketch& plan_of(const qlr_batch* b, int pass) {
@@ -126,8 +117,8 @@ int enqueue(qlr_batch* b) {
         // even v: [V_hat, S, U_hat] = TSVD(R2); odd v: [U_hat, S, V_hat] = TSVD(R1)
         const double* Uhat = (v % 2 == 0) ? P.Rt : P.Lm;
         const double* Vhat = (v % 2 == 0) ? P.Lm : P.Rt;
-        QLR_TRY(lift(lc, P.Q1, Uhat, P.l, P.k, P.U));
-        QLR_TRY(lift(lc, P.Q2, Vhat, P.l, P.k, P.V));
+        QLR_TRY(qlr::thin_times_small(lc, P.Q1, Uhat, P.l, P.k, P.U, ws));
+        QLR_TRY(qlr::thin_times_small(lc, P.Q2, Vhat, P.l, P.k, P.V, ws));
       }
     }
     for (int L = 0; L < b->lanes; ++L) {
@@ -256,7 +247,8 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   int64_t maxl = 0;
   for (int j = 0; j < count; ++j) {
     const int64_t m = A[j].rows, n = A[j].cols, l = k[j] + p[j];
-    bytes += 2 * ((4 * (size_t)m * l * 4 + 255) / 256 * 256) + 2 * ((4 * (size_t)n * l * 4 + 255) / 256 * 256);
+    const int64_t mp = (m + 3) / 4 * 4, np = (n + 3) / 4 * 4;
+    bytes += 2 * ((4 * (size_t)mp * l * 4 + 255) / 256 * 256) + 2 * ((4 * (size_t)np * l * 4 + 255) / 256 * 256);
     bytes += ((size_t)4 * l * l * 8 + 255) / 256 * 256 + 2 * (((size_t)4 * l * k[j] * 8 + 255) / 256 * 256);
     lane_need = std::max(lane_need, cholqr_ws_bound(std::max(m, n), l, 4) + tsvd_ws_bound(l));
     maxl = std::max(maxl, l);

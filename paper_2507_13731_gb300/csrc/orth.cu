@@ -1253,20 +1253,8 @@ int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* 
 }
 
 // Q = Y * Rinv (Rinv FP64 small, column-major, l x l)
-static int apply_rinv(qlr_ctx* ctx, const qlr_qmat& Y, const double* Rinv, qlr_qmat& Q) {
-  GemmArgs g{};
-  for (int c = 0; c < 4; ++c) {
-    g.a[c] = Y.plane[c];
-    g.b[c] = Rinv + (size_t)c * Y.cols * Y.cols;
-    g.c[c] = Q.plane[c];
-  }
-  g.sa_i = 1; g.sa_k = Y.ld; g.a_dtype = Y.dtype; g.conj_a = false; g.i_contig = true;
-  g.ldb = Y.cols; g.b_dtype = QLR_F64;
-  g.ldc = Q.ld; g.c_dtype = Q.dtype;
-  g.M = Y.rows; g.N = Y.cols; g.K = Y.cols;
-  g.alpha = 1.0; g.beta = 0.0;
-  g.acc64 = (Y.dtype == QLR_F64);
-  return gemm_simt(ctx, g);
+static int apply_rinv(qlr_ctx* ctx, const qlr_qmat& Y, const double* Rinv, qlr_qmat& Q, WsArena& ws) {
+  return thin_times_small(ctx, Y, Rinv, (int)Y.cols, (int)Y.cols, Q, ws);
 }
 
 // Cholesky factor R2 = I + F of a near-identity Gram matrix G and its inverse by series; sets
@@ -1332,12 +1320,13 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
   double* P2 = ws.take<double>(ll4);
   double* Rinv = ws.take<double>(ll4);
   double* Dinv_all = ws.take<double>((size_t)((l + CB - 1) / CB) * 4 * CB * CB);
-  char* tbuf = ws.take<char>((size_t)4 * m * l * esz);
+  const int64_t tld = (m + 3) / 4 * 4;   // 16-byte multiple pitch (tensor-core thin products)
+  char* tbuf = ws.take<char>((size_t)4 * tld * l * esz);
   if (!ws.ok) return QLR_ENOMEM;
   qlr_qmat T = Y;
-  T.ld = m;
+  T.ld = tld;
   T.layout = QLR_COL_MAJOR;
-  for (int c = 0; c < 4; ++c) T.plane[c] = tbuf + (size_t)c * m * l * esz;
+  for (int c = 0; c < 4; ++c) T.plane[c] = tbuf + (size_t)c * tld * l * esz;
 
   // CholeskyQR2: Y -> T -> Q.  Shifted CholeskyQR3: Y -> Q -> T -> Q.  Span only: Y -> Q (shifted).
   const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : (orth == ORTH_SPAN) ? 1 : 2;
@@ -1366,7 +1355,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
       QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all));
       QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
     }
-    QLR_TRY(apply_rinv(ctx, src, Rinv, dst));
+    QLR_TRY(apply_rinv(ctx, src, Rinv, dst, ws));
     if (s > 0) {   // R_total <- R_s * R_total
       QLR_TRY(small_matmul(ctx, l, Rs, Rprod, Rnext));
       double* sw = Rprod; Rprod = Rnext; Rnext = sw;

@@ -221,6 +221,8 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
 
 // utilities (util.cu)
 int convert_qmat(qlr_ctx* ctx, const qlr_qmat& src, qlr_qmat& dst);  // elementwise dtype change
+// C (rows x k) = T (rows x l, column-major) * S (FP64 l x k, column-major planes) (thin.cu)
+int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws);
 int zero_qmat(qlr_ctx* ctx, qlr_qmat& dst);
 int small_to_qmat(qlr_ctx* ctx, const double* S, int l, int k, qlr_qmat& dst);  // l x k FP64 small -> qmat
 

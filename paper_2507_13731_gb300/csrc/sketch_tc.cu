@@ -914,11 +914,11 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
 }
 
 template <int KIND, int AMODE>
-int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm) {
+int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm, int kid) {
   auto kern = sketch_tc_kernel<KIND, AMODE>;
   QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   dim3 grid((unsigned)pl.ncb, (unsigned)pl.mtiles, (unsigned)pl.nsplit);
-  KTimer kt(ctx, QLR_KID_SKETCH_TC);
+  KTimer kt(ctx, kid);
   kern<<<grid, TC_THREADS, pl.smem, ctx->stream>>>(prm);
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
@@ -1160,6 +1160,7 @@ size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
 
 int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws) {
   if (!sketch_tc_supported(op, A, X, compute)) return QLR_EUNSUPPORTED;
+  if (op != QLR_OP_N && op != QLR_OP_H) return QLR_EINVAL;
   const int64_t M = (op == QLR_OP_N) ? A.rows : A.cols;
   const int64_t K = (op == QLR_OP_N) ? A.cols : A.rows;
   const int l = (int)X.cols;
@@ -1248,10 +1249,11 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.stages = pl.stages;
   prm.err = ctx->d_err;
   int rc;
-  const bool h = (op == QLR_OP_H);
-  if (pl.kind == K_BF16) rc = h ? launch_kernel<K_BF16, A_MN>(ctx, pl, prm) : launch_kernel<K_BF16, A_K>(ctx, pl, prm);
-  else if (pl.kind == K_TF32) rc = h ? launch_kernel<K_TF32, A_T>(ctx, pl, prm) : launch_kernel<K_TF32, A_K>(ctx, pl, prm);
-  else rc = h ? launch_kernel<K_TF32X3, A_T>(ctx, pl, prm) : launch_kernel<K_TF32X3, A_K>(ctx, pl, prm);
+  const bool h = (op != QLR_OP_N);
+  const int kid = QLR_KID_SKETCH_TC;
+  if (pl.kind == K_BF16) rc = h ? launch_kernel<K_BF16, A_MN>(ctx, pl, prm, kid) : launch_kernel<K_BF16, A_K>(ctx, pl, prm, kid);
+  else if (pl.kind == K_TF32) rc = h ? launch_kernel<K_TF32, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32, A_K>(ctx, pl, prm, kid);
+  else rc = h ? launch_kernel<K_TF32X3, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32X3, A_K>(ctx, pl, prm, kid);
   ws.off = mark;
   return rc;
 }
