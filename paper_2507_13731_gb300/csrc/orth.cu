@@ -395,7 +395,7 @@ __host__ __device__ __forceinline__ size_t cc_smem(int l, int nc) {
     const int tot = cc_colstart(nc, c, n);
     mx = tot > mx ? tot : mx;
   }
-  return (size_t)mx * 32 + (size_t)4 * l * 32 + (size_t)l * 8;   // columns, h, three pushed rows, pivots
+  return (size_t)mx * 32 + (size_t)4 * l * 32 + 64;   // columns, h, three receive slots, pivots, mbarriers
 }
 
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
@@ -439,14 +439,61 @@ __device__ __forceinline__ double4 qcfms(double4 w, const double4 a, const doubl
   return w;
 }
 
-// 1 / sqrt(d) in FP64: the FP32 hardware estimate refined by two Newton-Raphson steps
-// y <- y (3 - d y^2) / 2 (each squares the relative error: 2^-22 -> 2^-43 -> below FP64 rounding).
-__device__ __forceinline__ double rsqrt_newton(double d) {
+// 1 / sqrt(d) in FP64: the FP32 hardware estimate refined by Newton-Raphson steps
+// y <- y (3 - d y^2) / 2, each squaring the relative error (2^-22 -> 2^-43 -> below FP64
+// rounding).  FP64 instructions are slow on this part and the pivot sits on the Cholesky's
+// critical path, so the factorisation takes one step (relative error ~2^-43 ~ 1e-13, a uniform
+// scaling of row j of R and column j of its inverse) and the other uses take two.
+__device__ __forceinline__ double rsqrt_newton(double d, int steps = 2) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
   double y = (double)rsqrtf((float)d);
   y = y * fma(-0.5 * d * y, y, 1.5);
-  y = y * fma(-0.5 * d * y, y, 1.5);
+  if (steps > 1) y = y * fma(-0.5 * d * y, y, 1.5);
   return y;
+}
+
+// Distributed shared memory data flow: st.async writes into another CTA's shared memory and
+// completes bytes on that CTA's mbarrier; the receiver waits on its own mbarrier phase.
+__device__ __forceinline__ uint32_t cc_smem32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cc_remote(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cc_st_async2(uint32_t raddr, double a, double b, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr), "d"(a),
+               "d"(b), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void cc_st_async1(uint32_t raddr, double a, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(raddr), "d"(a),
+               "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void cc_arm(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cc_smem32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait on a phase (1.5 s); false on timeout (QLR_ETIMEOUT recorded).
+__device__ __forceinline__ bool cc_wait(uint64_t* bar, uint32_t parity, int* err) {
+  const uint32_t a = cc_smem32(bar);
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    uint64_t now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (it == 0) t0 = now;
+    else if (now - t0 > 1500000000ull) {
+      qlr_set_error(err, QLR_ETIMEOUT);
+      return false;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const double* __restrict__ G, double* __restrict__ R,
@@ -463,13 +510,20 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
   int mxtot = 0;
   for (int cc = 0; cc < nc; ++cc) mxtot = max(mxtot, cc_colstart(nc, cc, cc_nown(l, nc, cc)));
   double4* Wc = reinterpret_cast<double4*>(smem_raw);       // own columns (rows 0..k)
-  double4* g = Wc + mxtot;                                    // h_k of the own columns (below)
-  // [3][l]: rows j of W pushed by the column owners.  Step j reads buffer j mod 3 and fills
-  // (j + 1) mod 3 in the other CTAs, one of which may still be in step j - 1's bulk update
-  // (reading (j - 1) mod 3) -- never further behind, since it has arrived at step j - 1's barrier.
-  double4* rowbuf = g + l;
-  double* s_rp = reinterpret_cast<double*>(rowbuf + 3 * l);   // 1 / r_jj, pushed by the pivot owner
+  double4* h = Wc + mxtot;                                    // h_k of the own columns (below)
+  // Three receive slots: slot j mod 3 gets row j of W (entries k > j) from the column owners and
+  // 1 / r_jj from the pivot owner during step j - 1, with an mbarrier counting the bytes.  A CTA
+  // can only start step j once every CTA has pushed its part of row j (made after its step j - 1
+  // look-ahead, hence after its step j - 2 bulk), so a slot is never written while still read.
+  double4* slot_row = h + l;                                  // [3][l]
+  double* slot_rp = reinterpret_cast<double*>(slot_row + 3 * l);   // [3] (+ padding)
+  uint64_t* slot_bar = reinterpret_cast<uint64_t*>(slot_rp + 4);   // [3]
+  auto bytes_of = [&](int j) -> uint32_t { return (uint32_t)(8 + 32 * (l - j - 1)); };
   cluster.sync();   // every CTA of the cluster is running before any distributed shared memory access
+  if (t == 0) {
+    for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cc_smem32(&slot_bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
   // shift s = shift_coef * trace(G) on the diagonal
   __shared__ double s_shift;
@@ -489,59 +543,101 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
       double4 q = make_double4(G[o], G[ll + o], G[2 * ll + o], G[3 * ll + o]);
       if (i == k) q.x += s_shift;
       col[i] = q;
-      if (i == 0 && k > 0)                         // row 0 to every CTA
-        for (int r = 0; r < nc; ++r) *cluster.map_shared_rank(rowbuf + k, r) = q;
     }
     for (int i = k + 1 + lane; i < l; i += 32)   // lower part of R is zero
       for (int cp = 0; cp < 4; ++cp) R[cp * ll + (size_t)k * l + i] = 0.0;
   }
   __syncthreads();
+  cluster.sync();   // every mbarrier initialised before any remote completion
+  if (t == 0)
+    for (int s = 0; s < 3 && s < l; ++s) cc_arm(&slot_bar[s], bytes_of(s));
+
   // R is built in place: once row j has been pushed, W[j][k] of an own column is dead and its slot
-  // takes R[j][k]; R goes to global memory once at the end, so the barrier's release does not
-  // wait on global stores.
-  auto take_pivot = [&](int j) {               // owner of column j, one thread
+  // takes R[j][k]; R goes to global memory once at the end.
+  // Pivot of column j by its owner (one thread): R[j][j] and 1 / r_jj to every CTA's slot.
+  auto take_pivot = [&](int j) {
     double4& wjj = Wc[cc_colstart(nc, c, j / nc) + j];
     double d = wjj.x;
     if (!(d > 0.0)) {
       qlr_set_error(err, QLR_ENOTPD);
       d = 1e-300;
     }
-    const double rp = rsqrt_newton(d);
-    for (int r = 0; r < nc; ++r) *cluster.map_shared_rank(s_rp + j, r) = rp;
+    const double rp = rsqrt_newton(d, 1);
+    const int s = j % 3;
+    const uint32_t la = cc_smem32(&slot_rp[s]), lb = cc_smem32(&slot_bar[s]);
+    for (int r = 0; r < nc; ++r) cc_st_async1(cc_remote(la, r), rp, cc_remote(lb, r));
     wjj = make_double4(d * rp, 0.0, 0.0, 0.0);
   };
+  // Entries k > j of row j of the own columns to every CTA's slot (items e < ncol * nc).
+  auto push_row = [&](int j) {
+    const int s = j % 3;
+    const int idx0 = (j + 1 - c + nc - 1) / nc;   // first own column with k > j
+    const int ncol = nown - idx0;
+    const uint32_t lb = cc_smem32(&slot_bar[s]);
+    for (int e = t; e < ncol * nc; e += CC_THREADS) {
+      const int idx = idx0 + e / nc, r = e % nc, k = c + idx * nc;
+      const double4 w = Wc[cc_colstart(nc, c, idx) + j];
+      const uint32_t la = cc_smem32(&slot_row[s * l + k]);
+      const uint32_t ra = cc_remote(la, r), rb = cc_remote(lb, r);
+      cc_st_async2(ra, w.x, w.y, rb);
+      cc_st_async2(ra + 16, w.z, w.w, rb);
+    }
+  };
   if (c == 0 && t == 0 && l > 0) take_pivot(0);
-  cluster.sync();
+  if (l > 1) push_row(0);
 
-  // With the raw pushed row W[j][.] and h_k = W[j][k] / r_jj^2 for the own columns, the rank-1
-  // update is W[i][k] -= conj(W[j][i]) h_k: only the CTA's own entries of row j are scaled.
-  double4* h = g;
-  for (int j = 0; j < l; ++j) {
-    const double rp = s_rp[j], rp2 = rp * rp;
-    const double4* row = rowbuf + (j % 3) * l;
+  bool ok = true;
+  for (int j = 0; j < l && ok; ++j) {
+    const int s = j % 3;
+    ok = cc_wait(&slot_bar[s], (uint32_t)(j / 3) & 1u, err);
+    if (!ok) break;
+    const double rp = slot_rp[s];
+    const double4* row = slot_row + s * l;
     const int j1 = j + 1;
     const int idx0 = (j1 - c + nc - 1) / nc;   // first own column index with k >= j + 1
     const int nact = nown - idx0;
-    if (t < nact) {                            // R[j][k], h_k and the look-ahead row j + 1
-      const int idx = idx0 + t, k = c + idx * nc;
-      const double4 q = row[k];
-      double4* col = Wc + cc_colstart(nc, c, idx);
-      col[j] = make_double4(q.x * rp, q.y * rp, q.z * rp, q.w * rp);
-      const double4 hk = make_double4(q.x * rp2, q.y * rp2, q.z * rp2, q.w * rp2);
-      h[k] = hk;
-      col[j1] = qcfms(col[j1], row[j1], hk);
+    // look-ahead row j + 1 (on the critical path of every step): one lane per quaternion
+    // component of each own column, so each FP64 instruction serves up to eight columns --
+    // h_k = W[j][k] / r_jj^2 component-wise, the other three components by shuffles, then
+    // W[j+1][k] -= conj(W[j][j+1]) h_k for this lane's component
+    const int nlane = 32 * ((4 * nact + 31) / 32);   // whole warps: every lane takes part in the shuffles
+    if (t < nlane) {
+      const int ci = t >> 2, comp = t & 3;
+      const bool act = ci < nact;
+      const int idx = idx0 + (act ? ci : 0), k = c + idx * nc;
+      const double rp2 = rp * rp;
+      const double* qk = reinterpret_cast<const double*>(&row[act ? k : j1]);
+      const double hc = qk[comp] * rp2;
+      const int base = (t & 31) & ~3;
+      const double h0 = __shfl_sync(0xffffffffu, hc, base + 0), h1 = __shfl_sync(0xffffffffu, hc, base + 1);
+      const double h2 = __shfl_sync(0xffffffffu, hc, base + 2), h3 = __shfl_sync(0xffffffffu, hc, base + 3);
+      if (act) {
+        reinterpret_cast<double*>(&h[k])[comp] = hc;
+        const double4 a = row[j1];
+        double* wp = reinterpret_cast<double*>(&Wc[cc_colstart(nc, c, idx) + j1]) + comp;
+        double w = *wp;
+        if (comp == 0) {
+          w = fma(-a.x, h0, w); w = fma(-a.y, h1, w); w = fma(-a.z, h2, w); w = fma(-a.w, h3, w);
+        } else if (comp == 1) {
+          w = fma(-a.x, h1, w); w = fma(a.y, h0, w); w = fma(a.z, h3, w); w = fma(-a.w, h2, w);
+        } else if (comp == 2) {
+          w = fma(-a.x, h2, w); w = fma(-a.y, h3, w); w = fma(a.z, h0, w); w = fma(a.w, h1, w);
+        } else {
+          w = fma(-a.x, h3, w); w = fma(a.y, h2, w); w = fma(-a.z, h1, w); w = fma(a.w, h0, w);
+        }
+        *wp = w;
+      }
     }
     __syncthreads();
     if (j1 < l) {
       if (c == j1 % nc && t == 0) take_pivot(j1);
-      double4* nrow = rowbuf + (j1 % 3) * l;
-      for (int e = t; e < nact * nc; e += CC_THREADS) {   // push row j + 1 of the own columns
-        const int idx = idx0 + e / nc, r = e % nc, k = c + idx * nc;
-        if (k > j1) *cluster.map_shared_rank(nrow + k, r) = Wc[cc_colstart(nc, c, idx) + j1];
-      }
+      push_row(j1);
     }
-    __syncwarp();
-    cluster_arrive_release();
+    if (t < nact) {                            // R[j][k] of the own columns (off the critical path)
+      const int k = c + (idx0 + t) * nc;
+      const double4 q = row[k];
+      Wc[cc_colstart(nc, c, idx0 + t) + j] = make_double4(q.x * rp, q.y * rp, q.z * rp, q.w * rp);
+    }
     // bulk of the rank-1 update: rows j + 2 .. k of the own columns k >= j + 2, the (column, row)
     // items numbered consecutively over all threads so FP64 warps run full.  Column m (from the
     // first one, k_0 >= j + 2) has L_0 + m nc rows; item e lies in the column m with
@@ -566,11 +662,8 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
         }
       }
     }
-    // the barrier completes once every thread has arrived, not once every thread has finished
-    // its share of the bulk update: the CTA's own threads must finish reading h and writing the
-    // columns before any of them starts the next step
-    __syncthreads();
-    cluster_wait_acquire();
+    __syncthreads();                           // slot s and h are free again
+    if (t == 0 && j + 3 < l) cc_arm(&slot_bar[s], bytes_of(j + 3));
   }
   cluster.sync();   // last distributed shared memory access done before any CTA moves on
   for (int idx = warp; idx < nown; idx += nwarps) {
@@ -725,6 +818,273 @@ __global__ void __launch_bounds__(CS_THREADS, 1) chol_single_kernel(const double
       const int i = e % CB, jj = e / CB;
       const double4 q = (i < b && jj < b && i <= jj) ? at(j0 + i, j0 + jj) : make_double4(0.0, 0.0, 0.0, 0.0);
       D[0][i][jj] = q.x; D[1][i][jj] = q.y; D[2][i][jj] = q.z; D[3][i][jj] = q.w;
+    }
+    __syncthreads();
+    cc_block_inverse(D, X, rpv, b);
+    double* Dinv = Dinv_all + (size_t)J * 4 * CB * CB;
+    for (int e = t; e < b * b; e += blockDim.x) {
+      const int i = e % b, jj = e / b;
+      for (int cp = 0; cp < 4; ++cp) Dinv[(size_t)cp * b * b + (size_t)jj * b + i] = (i <= jj) ? X[cp][i][jj] : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// The same cluster Cholesky in double-FP32 arithmetic (an unevaluated sum hi + lo of two floats,
+// about 48 significant bits), for Grams of FP32 sketches, which the Gram kernel already forms in
+// double-FP32: the factorisation then matches the Gram's precision, while every step runs on the
+// FP32 pipes (FP64 instructions issue slowly here and a dependent one takes ~200 cycles, which
+// put the FP64 column step's look-ahead and pivot near 3000 cycles).  The operations are Knuth's
+// two-sum and the fused-multiply-add exact product (Dekker), renormalised after each operation;
+// 1 / sqrt uses the FP32 estimate and two Newton-Raphson steps in double-FP32.
+struct d32 {
+  float h, l;
+};
+__device__ __forceinline__ d32 d32_add(d32 a, d32 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ d32 d32_mul(d32 a, d32 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ d32 d32_neg(d32 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ d32 d32_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double d32_to(d32 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ d32 d32_rsqrt(d32 d) {
+  d32 y = {rsqrtf(d.h), 0.f};
+  for (int it = 0; it < 2; ++it) {   // y <- y + y (1 - d y^2) / 2
+    const d32 r = d32_add({1.f, 0.f}, d32_neg(d32_mul(d32_mul(d, y), y)));
+    y = d32_add(y, d32_mul(y, {0.5f * r.h, 0.5f * r.l}));
+  }
+  return y;
+}
+// A quaternion of double-FP32 numbers: components (real, i, j, k) of the high and low parts.
+struct dq {
+  float4 h, l;
+};
+__device__ __forceinline__ d32 dq_get(const dq& q, int c) {
+  return {reinterpret_cast<const float*>(&q.h)[c], reinterpret_cast<const float*>(&q.l)[c]};
+}
+__device__ __forceinline__ void dq_set(dq& q, int c, d32 v) {
+  reinterpret_cast<float*>(&q.h)[c] = v.h;
+  reinterpret_cast<float*>(&q.l)[c] = v.l;
+}
+// Component c of w - conj(a) b (the signs of conj(a) b per component).
+__device__ __forceinline__ d32 dq_cfms_comp(d32 w, const d32 (&a)[4], const d32 (&b)[4], int c) {
+  auto sub = [&](d32 x, d32 p, d32 q) { return d32_add(x, d32_neg(d32_mul(p, q))); };
+  auto add = [&](d32 x, d32 p, d32 q) { return d32_add(x, d32_mul(p, q)); };
+  if (c == 0) { w = sub(w, a[0], b[0]); w = sub(w, a[1], b[1]); w = sub(w, a[2], b[2]); return sub(w, a[3], b[3]); }
+  if (c == 1) { w = sub(w, a[0], b[1]); w = add(w, a[1], b[0]); w = add(w, a[2], b[3]); return sub(w, a[3], b[2]); }
+  if (c == 2) { w = sub(w, a[0], b[2]); w = sub(w, a[1], b[3]); w = add(w, a[2], b[0]); return add(w, a[3], b[1]); }
+  w = sub(w, a[0], b[3]); w = add(w, a[1], b[2]); w = sub(w, a[2], b[1]); return add(w, a[3], b[0]);
+}
+__device__ __forceinline__ dq dq_cfms(dq w, const dq& a, const dq& b) {
+  d32 av[4], bv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { av[c] = dq_get(a, c); bv[c] = dq_get(b, c); }
+  dq r;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dq_set(r, c, dq_cfms_comp(dq_get(w, c), av, bv, c));
+  return r;
+}
+__device__ __forceinline__ void cc_st_async4f(uint32_t raddr, float4 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(raddr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void cc_st_async2f(uint32_t raddr, float a, float b, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr), "f"(a),
+               "f"(b), "r"(rbar)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_df_kernel(const double* __restrict__ G, double* __restrict__ R,
+                                                                        double* __restrict__ Dinv_all, int l,
+                                                                        double shift_coef, int* err, const int* run_if) {
+  if (run_if && *run_if == 0) return;           // the same decision in every CTA of the cluster
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int nc = (int)cluster.num_blocks();
+  const int c = (int)cluster.block_rank();
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = CC_THREADS / 32;
+  const size_t ll = (size_t)l * l;
+  const int nown = cc_nown(l, nc, c);
+  int mxtot = 0;
+  for (int cc = 0; cc < nc; ++cc) mxtot = max(mxtot, cc_colstart(nc, cc, cc_nown(l, nc, cc)));
+  dq* Wc = reinterpret_cast<dq*>(smem_raw);                  // own columns (rows 0..k)
+  dq* h = Wc + mxtot;                                         // h_k of the own columns
+  dq* slot_row = h + l;                                       // [3][l] received rows (see the FP64 kernel)
+  d32* slot_rp = reinterpret_cast<d32*>(slot_row + 3 * l);   // [3] (+ padding)
+  uint64_t* slot_bar = reinterpret_cast<uint64_t*>(slot_rp + 4);   // [3]
+  auto bytes_of = [&](int j) -> uint32_t { return (uint32_t)(8 + 32 * (l - j - 1)); };
+  cluster.sync();   // every CTA of the cluster is running before any distributed shared memory access
+  if (t == 0) {
+    for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cc_smem32(&slot_bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __shared__ double s_shift;
+  if (warp == 0) {
+    double tr = 0.0;
+    for (int i = lane; i < l; i += 32) tr += G[(size_t)i * l + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (lane == 0) s_shift = shift_coef * tr;
+  }
+  __syncthreads();
+  for (int idx = warp; idx < nown; idx += nwarps) {
+    const int k = c + idx * nc;
+    dq* col = Wc + cc_colstart(nc, c, idx);
+    for (int i = lane; i <= k; i += 32) {
+      const size_t o = (size_t)k * l + i;
+      dq q;
+      for (int cp = 0; cp < 4; ++cp) dq_set(q, cp, d32_from(G[cp * ll + o] + ((cp == 0 && i == k) ? s_shift : 0.0)));
+      col[i] = q;
+    }
+    for (int i = k + 1 + lane; i < l; i += 32)   // lower part of R is zero
+      for (int cp = 0; cp < 4; ++cp) R[cp * ll + (size_t)k * l + i] = 0.0;
+  }
+  __syncthreads();
+  cluster.sync();   // every mbarrier initialised before any remote completion
+  if (t == 0)
+    for (int s = 0; s < 3 && s < l; ++s) cc_arm(&slot_bar[s], bytes_of(s));
+
+  auto take_pivot = [&](int j) {               // owner of column j, one thread
+    dq& wjj = Wc[cc_colstart(nc, c, j / nc) + j];
+    d32 d = dq_get(wjj, 0);
+    if (!(d.h > 0.f)) {
+      qlr_set_error(err, QLR_ENOTPD);
+      d = {1e-30f, 0.f};
+    }
+    const d32 rp = d32_rsqrt(d);
+    const int s = j % 3;
+    const uint32_t la = cc_smem32(&slot_rp[s]), lb = cc_smem32(&slot_bar[s]);
+    for (int r = 0; r < nc; ++r) cc_st_async2f(cc_remote(la, r), rp.h, rp.l, cc_remote(lb, r));
+    const d32 piv = d32_mul(d, rp);
+    dq z;
+    z.h = make_float4(piv.h, 0.f, 0.f, 0.f);
+    z.l = make_float4(piv.l, 0.f, 0.f, 0.f);
+    wjj = z;
+  };
+  auto push_row = [&](int j) {
+    const int s = j % 3;
+    const int idx0 = (j + 1 - c + nc - 1) / nc;
+    const int ncol = nown - idx0;
+    const uint32_t lb = cc_smem32(&slot_bar[s]);
+    for (int e = t; e < ncol * nc; e += CC_THREADS) {
+      const int idx = idx0 + e / nc, r = e % nc, k = c + idx * nc;
+      const dq w = Wc[cc_colstart(nc, c, idx) + j];
+      const uint32_t ra = cc_remote(cc_smem32(&slot_row[s * l + k]), r), rb = cc_remote(lb, r);
+      cc_st_async4f(ra, w.h, rb);
+      cc_st_async4f(ra + 16, w.l, rb);
+    }
+  };
+  if (c == 0 && t == 0 && l > 0) take_pivot(0);
+  if (l > 1) push_row(0);
+
+  bool ok = true;
+  for (int j = 0; j < l && ok; ++j) {
+    const int s = j % 3;
+    ok = cc_wait(&slot_bar[s], (uint32_t)(j / 3) & 1u, err);
+    if (!ok) break;
+    const d32 rp = slot_rp[s];
+    const dq* row = slot_row + s * l;
+    const int j1 = j + 1;
+    const int idx0 = (j1 - c + nc - 1) / nc;
+    const int nact = nown - idx0;
+    // look-ahead row j + 1, one lane per quaternion component of each own column (see the FP64 kernel)
+    const int nlane = 32 * ((4 * nact + 31) / 32);
+    if (t < nlane) {
+      const int ci = t >> 2, comp = t & 3;
+      const bool act = ci < nact;
+      const int idx = idx0 + (act ? ci : 0), k = c + idx * nc;
+      const d32 rp2 = d32_mul(rp, rp);
+      const d32 hc = d32_mul(dq_get(row[act ? k : j1], comp), rp2);
+      const int base = (t & 31) & ~3;
+      d32 hv[4], av[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        hv[q].h = __shfl_sync(0xffffffffu, hc.h, base + q);
+        hv[q].l = __shfl_sync(0xffffffffu, hc.l, base + q);
+      }
+      if (act) {
+        dq_set(h[k], comp, hc);
+        const dq a = row[j1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) av[q] = dq_get(a, q);
+        dq& w = Wc[cc_colstart(nc, c, idx) + j1];
+        dq_set(w, comp, dq_cfms_comp(dq_get(w, comp), av, hv, comp));
+      }
+    }
+    __syncthreads();
+    if (j1 < l) {
+      if (c == j1 % nc && t == 0) take_pivot(j1);
+      push_row(j1);
+    }
+    if (t < nact) {                            // R[j][k] of the own columns
+      const int k = c + (idx0 + t) * nc;
+      const dq q = row[k];
+      dq r;
+      for (int cp = 0; cp < 4; ++cp) dq_set(r, cp, d32_mul(dq_get(q, cp), rp));
+      Wc[cc_colstart(nc, c, idx0 + t) + j] = r;
+    }
+    const int j2 = j + 2;
+    if (j2 < l) {
+      const int jdx0 = (j2 - c + nc - 1) / nc;
+      const int ncol = nown - jdx0;
+      if (ncol > 0) {
+        const int L0 = c + jdx0 * nc - j2 + 1;
+        const int total = ncol * L0 + nc * ncol * (ncol - 1) / 2;
+        const float hb = (float)L0 - 0.5f * (float)nc;
+        for (int e = t; e < total; e += CC_THREADS) {
+          int m = (int)((-hb + sqrtf(hb * hb + 2.0f * (float)nc * (float)e)) / (float)nc);
+          m = max(0, min(m, ncol - 1));
+          while (m > 0 && m * L0 + nc * m * (m - 1) / 2 > e) --m;
+          while (m + 1 < ncol && (m + 1) * L0 + nc * (m + 1) * m / 2 <= e) ++m;
+          const int i = j2 + e - (m * L0 + nc * m * (m - 1) / 2);
+          const int idx = jdx0 + m, k = c + idx * nc;
+          dq& w = Wc[cc_colstart(nc, c, idx) + i];
+          w = dq_cfms(w, row[i], h[k]);
+        }
+      }
+    }
+    __syncthreads();
+    if (t == 0 && j + 3 < l) cc_arm(&slot_bar[s], bytes_of(j + 3));
+  }
+  cluster.sync();   // last distributed shared memory access done before any CTA moves on
+  for (int idx = warp; idx < nown; idx += nwarps) {
+    const int k = c + idx * nc;
+    const dq* col = Wc + cc_colstart(nc, c, idx);
+    for (int i = lane; i <= k; i += 32) {
+      const dq r = col[i];
+      const size_t o = (size_t)k * l + i;
+      for (int cp = 0; cp < 4; ++cp) R[cp * ll + o] = d32_to(dq_get(r, cp));
+    }
+  }
+  __threadfence();
+  cluster.sync();
+  __shared__ double D[4][CB][CB];
+  __shared__ double X[4][CB][CB];
+  __shared__ double rpv[CB];
+  const int nblk = (l + CB - 1) / CB;
+  for (int J = c; J < nblk; J += nc) {
+    const int j0 = J * CB, b = min(CB, l - j0);
+    for (int e = t; e < CB * CB; e += blockDim.x) {
+      const int i = e % CB, jj = e / CB;
+      for (int cp = 0; cp < 4; ++cp)
+        D[cp][i][jj] = (i < b && jj < b && i <= jj) ? __ldcg(R + cp * ll + (size_t)(j0 + jj) * l + j0 + i) : 0.0;
     }
     __syncthreads();
     cc_block_inverse(D, X, rpv, b);
@@ -1115,14 +1475,16 @@ static int cluster_chol_size(int device, int l) {
   for (const auto& e : cache)
     if (e.first == key) return e.second;
   const bool allowed =
-      cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+      cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(chol_cluster_df_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   cudaGetLastError();
   int pick = 0;
   for (int nc : {16, 8}) {
     if (nc == 16 && !allowed) continue;
     const size_t smem = cc_smem(l, nc);
     if (smem > 200 * 1024) continue;
-    if (cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+    if (cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(chol_cluster_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -1149,7 +1511,7 @@ static int cluster_chol_size(int device, int l) {
 }
 
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsArena& ws, double* Dinv_all,
-         const int* run_if) {
+         const int* run_if, bool df) {
   if (l == 0) return QLR_OK;
   const size_t ll4 = (size_t)4 * l * l;
   if (ctx->small_mode && l <= CS_MAX_L && Dinv_all != nullptr) {
@@ -1177,7 +1539,8 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     KTimer kt(ctx, QLR_KID_CHOL);
-    QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, chol_cluster_kernel, G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if));
+    QLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, df ? chol_cluster_df_kernel : chol_cluster_kernel, G, R, Dinv_all, l, shift_coef,
+                                    ctx->d_err, run_if));
     qlr_count_launch();
     return QLR_OK;
   }
@@ -1330,6 +1693,8 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
 
   // CholeskyQR2: Y -> T -> Q.  Shifted CholeskyQR3: Y -> Q -> T -> Q.  Span only: Y -> Q (shifted).
   const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : (orth == ORTH_SPAN) ? 1 : 2;
+  // FP32 sketches: the Gram is double-FP32, and the Cholesky runs in the same arithmetic
+  const bool df = (Y.dtype == QLR_F32);
   const qlr_qmat* seq1[2] = {&Y, &Q};
   const qlr_qmat* seq2[3] = {&Y, &T, &Q};
   const qlr_qmat* seq3[4] = {&Y, &Q, &T, &Q};
@@ -1349,10 +1714,10 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     } else if (s == 1 && orth == QLR_ORTH_CHOLQR2 && !(ctx->small_mode && l <= CS_MAX_L)) {
       int* use_chol = nullptr;
       QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol));
-      QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol));     // only if the series test failed
+      QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol, df));     // only if the series test failed
       QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, use_chol));
     } else {
-      QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all));
+      QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all, nullptr, df));
       QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
     }
     QLR_TRY(apply_rinv(ctx, src, Rinv, dst, ws));

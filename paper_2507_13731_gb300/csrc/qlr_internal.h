@@ -198,7 +198,7 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs);
 // orthonormalisation pieces (orth.cu)
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
-         const int* run_if = nullptr);
+         const int* run_if = nullptr, bool df = false);
 int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr,
             const int* run_if = nullptr);
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
