@@ -395,7 +395,7 @@ __host__ __device__ __forceinline__ size_t cc_smem(int l, int nc) {
     const int tot = cc_colstart(nc, c, n);
     mx = tot > mx ? tot : mx;
   }
-  return (size_t)mx * 32 + (size_t)4 * l * 32 + 64;   // columns, h, three receive slots, pivots, mbarriers
+  return (size_t)mx * 32 + (size_t)4 * l * 32 + 128;   // columns, h, three receive slots, pivots, mbarriers
 }
 
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
@@ -927,9 +927,9 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_df_kernel(const do
   dq* Wc = reinterpret_cast<dq*>(smem_raw);                  // own columns (rows 0..k)
   dq* h = Wc + mxtot;                                         // h_k of the own columns
   dq* slot_row = h + l;                                       // [3][l] received rows (see the FP64 kernel)
-  d32* slot_rp = reinterpret_cast<d32*>(slot_row + 3 * l);   // [3] (+ padding)
-  uint64_t* slot_bar = reinterpret_cast<uint64_t*>(slot_rp + 4);   // [3]
-  auto bytes_of = [&](int j) -> uint32_t { return (uint32_t)(8 + 32 * (l - j - 1)); };
+  d32* slot_rp = reinterpret_cast<d32*>(slot_row + 3 * l);   // [3][2]: 1 / r_jj and its square
+  uint64_t* slot_bar = reinterpret_cast<uint64_t*>(slot_rp + 6);   // [3]
+  auto bytes_of = [&](int j) -> uint32_t { return (uint32_t)(16 + 32 * (l - j - 1)); };
   cluster.sync();   // every CTA of the cluster is running before any distributed shared memory access
   if (t == 0) {
     for (int s = 0; s < 3; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cc_smem32(&slot_bar[s])) : "memory");
@@ -961,22 +961,34 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_df_kernel(const do
   if (t == 0)
     for (int s = 0; s < 3 && s < l; ++s) cc_arm(&slot_bar[s], bytes_of(s));
 
-  auto take_pivot = [&](int j) {               // owner of column j, one thread
-    dq& wjj = Wc[cc_colstart(nc, c, j / nc) + j];
-    d32 d = dq_get(wjj, 0);
-    if (!(d.h > 0.f)) {
-      qlr_set_error(err, QLR_ENOTPD);
-      d = {1e-30f, 0.f};
+  // Pivot of column j from its (updated) diagonal d, computed by one lane (`me`) of a full warp:
+  // R[j][j] in place, and (1 / r_jj, 1 / r_jj^2) to every CTA's slot, one lane per CTA.
+  auto take_pivot = [&](int j, d32 d, bool me) {
+    d32 rp = {0.f, 0.f}, rp2 = {0.f, 0.f};
+    if (me) {
+      if (!(d.h > 0.f)) {
+        qlr_set_error(err, QLR_ENOTPD);
+        d = {1e-30f, 0.f};
+      }
+      rp = d32_rsqrt(d);
+      rp2 = d32_mul(rp, rp);
+      const d32 piv = d32_mul(d, rp);
+      dq z;
+      z.h = make_float4(piv.h, 0.f, 0.f, 0.f);
+      z.l = make_float4(piv.l, 0.f, 0.f, 0.f);
+      Wc[cc_colstart(nc, c, j / nc) + j] = z;
     }
-    const d32 rp = d32_rsqrt(d);
-    const int s = j % 3;
-    const uint32_t la = cc_smem32(&slot_rp[s]), lb = cc_smem32(&slot_bar[s]);
-    for (int r = 0; r < nc; ++r) cc_st_async2f(cc_remote(la, r), rp.h, rp.l, cc_remote(lb, r));
-    const d32 piv = d32_mul(d, rp);
-    dq z;
-    z.h = make_float4(piv.h, 0.f, 0.f, 0.f);
-    z.l = make_float4(piv.l, 0.f, 0.f, 0.f);
-    wjj = z;
+    const unsigned src = __ffs(__ballot_sync(0xffffffffu, me)) - 1;
+    rp.h = __shfl_sync(0xffffffffu, rp.h, src); rp.l = __shfl_sync(0xffffffffu, rp.l, src);
+    rp2.h = __shfl_sync(0xffffffffu, rp2.h, src); rp2.l = __shfl_sync(0xffffffffu, rp2.l, src);
+    const int ln = threadIdx.x & 31;
+    if (ln < nc) {
+      const int s = j % 3;
+      const uint32_t rb = cc_remote(cc_smem32(&slot_bar[s]), ln);
+      const uint32_t ra = cc_remote(cc_smem32(&slot_rp[2 * s]), ln);
+      cc_st_async2f(ra, rp.h, rp.l, rb);
+      cc_st_async2f(ra + 8, rp2.h, rp2.l, rb);
+    }
   };
   auto push_row = [&](int j) {
     const int s = j % 3;
@@ -991,7 +1003,7 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_df_kernel(const do
       cc_st_async4f(ra + 16, w.l, rb);
     }
   };
-  if (c == 0 && t == 0 && l > 0) take_pivot(0);
+  if (c == 0 && warp == 0 && l > 0) take_pivot(0, dq_get(Wc[0], 0), lane == 0);
   if (l > 1) push_row(0);
 
   bool ok = true;
@@ -999,40 +1011,46 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_df_kernel(const do
     const int s = j % 3;
     ok = cc_wait(&slot_bar[s], (uint32_t)(j / 3) & 1u, err);
     if (!ok) break;
-    const d32 rp = slot_rp[s];
+    const d32 rp = slot_rp[2 * s], rp2 = slot_rp[2 * s + 1];
     const dq* row = slot_row + s * l;
     const int j1 = j + 1;
     const int idx0 = (j1 - c + nc - 1) / nc;
     const int nact = nown - idx0;
-    // look-ahead row j + 1, one lane per quaternion component of each own column (see the FP64 kernel)
+    // look-ahead row j + 1, one lane per quaternion component of each own column: h_k =
+    // W[j][k] / r_jj^2 (all four components, independent products), the four signed products
+    // of this lane's component of conj(W[j][j+1]) h_k summed as a tree, subtracted from W[j+1][k].
+    // The lane holding the diagonal of column j + 1 takes the pivot at once.
     const int nlane = 32 * ((4 * nact + 31) / 32);
+    const bool own_next = (j1 < l && c == j1 % nc);
     if (t < nlane) {
       const int ci = t >> 2, comp = t & 3;
       const bool act = ci < nact;
       const int idx = idx0 + (act ? ci : 0), k = c + idx * nc;
-      const d32 rp2 = d32_mul(rp, rp);
-      const d32 hc = d32_mul(dq_get(row[act ? k : j1], comp), rp2);
-      const int base = (t & 31) & ~3;
-      d32 hv[4], av[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        hv[q].h = __shfl_sync(0xffffffffu, hc.h, base + q);
-        hv[q].l = __shfl_sync(0xffffffffu, hc.l, base + q);
-      }
+      d32 piv_d = {0.f, 0.f};
       if (act) {
-        dq_set(h[k], comp, hc);
-        const dq a = row[j1];
+        // component `comp` of conj(a) h is sum_q (-1)^neg(comp, q) a_q h_{comp xor q}, with the
+        // negative (comp, q) pairs the set bits of 0xAC60 at 4 comp + q
+        const dq* qk = &row[k];
+        const dq* ap = &row[j1];
+        d32 p[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) av[q] = dq_get(a, q);
+        for (int q = 0; q < 4; ++q) {
+          const d32 hq = d32_mul(dq_get(*qk, comp ^ q), rp2);
+          if (q == 0) dq_set(h[k], comp, hq);
+          const d32 aq = dq_get(*ap, q);
+          const float sgn = ((0xAC60u >> (4 * comp + q)) & 1u) ? -1.f : 1.f;
+          p[q] = d32_mul({sgn * aq.h, sgn * aq.l}, hq);
+        }
+        const d32 sum = d32_add(d32_add(p[0], p[1]), d32_add(p[2], p[3]));
         dq& w = Wc[cc_colstart(nc, c, idx) + j1];
-        dq_set(w, comp, dq_cfms_comp(dq_get(w, comp), av, hv, comp));
+        const d32 nv = d32_add(dq_get(w, comp), d32_neg(sum));
+        dq_set(w, comp, nv);
+        piv_d = nv;
       }
+      if (own_next && warp == 0) take_pivot(j1, piv_d, act && k == j1 && comp == 0);
     }
     __syncthreads();
-    if (j1 < l) {
-      if (c == j1 % nc && t == 0) take_pivot(j1);
-      push_row(j1);
-    }
+    if (j1 < l) push_row(j1);
     if (t < nact) {                            // R[j][k] of the own columns
       const int k = c + (idx0 + t) * nc;
       const dq q = row[k];
