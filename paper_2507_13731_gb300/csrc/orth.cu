@@ -1214,13 +1214,17 @@ __global__ void __launch_bounds__(256) tri_inv_col_kernel(const double* __restri
 //   x_J = Dinv_J e_j,   x_I = -Dinv_I (sum_{q in blocks I+1..J} R[I, q] x_q)   for I = J-1 .. 0.
 __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __restrict__ R, const double* __restrict__ Dinv,
                                                                double* __restrict__ X, int l, const int* run_if) {
+  // Column j of X = R^{-1} by block back substitution, x_I = -Dinv_I sum_{q > block I} R[I, q] x_q.
+  // FP64 results take ~200 cycles each on this part, so every sum is a shuffle tree over 16 lanes
+  // (depth 4) instead of a serial chain: lane ch of row r's half-warp takes q = q0 + ch, q0 + ch +
+  // 16, ...; the 16 x 16 triangular product with Dinv_I runs as lane (r, q).
   if (run_if && *run_if == 0) return;
   extern __shared__ double xs[];          // 4 * l
-  __shared__ double tpart[4][CB][16];     // partial sums: row r of the block, 16 q-chunks
   __shared__ double tsum[4][CB];
   const int j = blockIdx.x, t = threadIdx.x;
   const size_t ll = (size_t)l * l;
   const int J = j / CB;
+  const int r = t >> 4, ch = t & 15;      // 16 rows x 16 lanes = 256 threads
   for (int i = t; i < l; i += blockDim.x) xs[i] = xs[l + i] = xs[2 * l + i] = xs[3 * l + i] = 0.0;
   __syncthreads();
   {   // x_J = Dinv_J[:, j - J*CB]
@@ -1236,37 +1240,39 @@ __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __re
   __syncthreads();
   for (int I = J - 1; I >= 0; --I) {
     const int i0 = I * CB, q0 = (I + 1) * CB;
-    // T[r] = sum_{q = q0 .. j} R[i0 + r, q] x_q : thread (r, chunk) with 16 chunks per row
+    Quat<double> acc = {0, 0, 0, 0};
+    for (int q = q0 + ch; q <= j; q += 16) {
+      const Quat<double> pr = qmul(ld_small(R, l, i0 + r, q), Quat<double>{xs[q], xs[l + q], xs[2 * l + q], xs[3 * l + q]});
+      acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {      // the 16 lanes of row r are one half-warp
+      acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    }
+    if (ch == 0) { tsum[0][r] = acc.w; tsum[1][r] = acc.x; tsum[2][r] = acc.y; tsum[3][r] = acc.z; }
+    __syncthreads();
+    // x_I[r] = -sum_{q >= r} Dinv_I[r][q] T[q]: lane (r, q)
     {
-      const int r = t % CB, ch = t / CB;   // CB * 16 = 256 threads
-      Quat<double> acc = {0, 0, 0, 0};
-      for (int q = q0 + ch; q <= j; q += 16) {
-        Quat<double> pr = qmul(ld_small(R, l, i0 + r, q), Quat<double>{xs[q], xs[l + q], xs[2 * l + q], xs[3 * l + q]});
-        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
-      }
-      tpart[0][r][ch] = acc.w; tpart[1][r][ch] = acc.x; tpart[2][r][ch] = acc.y; tpart[3][r][ch] = acc.z;
-    }
-    __syncthreads();
-    if (t < 4 * CB) {
-      const int c = t / CB, r = t % CB;
-      double sacc = 0.0;
-      for (int ch = 0; ch < 16; ++ch) sacc += tpart[c][r][ch];
-      tsum[c][r] = sacc;
-    }
-    __syncthreads();
-    // x_I = -Dinv_I T   (Dinv_I upper triangular, CB x CB)
-    if (t < CB) {
-      const int r = t;
       const double* D = Dinv + (size_t)I * 4 * CB * CB;
       const size_t bb = (size_t)CB * CB;
-      Quat<double> acc = {0, 0, 0, 0};
-      for (int q = r; q < CB; ++q) {
+      const int q = ch;
+      Quat<double> pr = {0, 0, 0, 0};
+      if (q >= r) {
         const size_t o = (size_t)q * CB + r;
-        Quat<double> pr = qmul(Quat<double>{D[o], D[bb + o], D[2 * bb + o], D[3 * bb + o]},
-                               Quat<double>{tsum[0][q], tsum[1][q], tsum[2][q], tsum[3][q]});
-        acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+        pr = qmul(Quat<double>{D[o], D[bb + o], D[2 * bb + o], D[3 * bb + o]},
+                  Quat<double>{tsum[0][q], tsum[1][q], tsum[2][q], tsum[3][q]});
       }
-      xs[i0 + r] = -acc.w; xs[l + i0 + r] = -acc.x; xs[2 * l + i0 + r] = -acc.y; xs[3 * l + i0 + r] = -acc.z;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        pr.w += __shfl_xor_sync(0xffffffffu, pr.w, o);
+        pr.x += __shfl_xor_sync(0xffffffffu, pr.x, o);
+        pr.y += __shfl_xor_sync(0xffffffffu, pr.y, o);
+        pr.z += __shfl_xor_sync(0xffffffffu, pr.z, o);
+      }
+      if (ch == 0) { xs[i0 + r] = -pr.w; xs[l + i0 + r] = -pr.x; xs[2 * l + i0 + r] = -pr.y; xs[3 * l + i0 + r] = -pr.z; }
     }
     __syncthreads();
   }
