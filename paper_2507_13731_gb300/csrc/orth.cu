@@ -109,7 +109,7 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunks,
 }
 
 // C = A B for small l x l quaternion matrices (FP64), A and B upper triangular.
-constexpr int MM_SPLIT = 8;   // lanes sharing one output entry of small_matmul_kernel
+constexpr int MM_SPLIT = 16;   // lanes sharing one output entry of small_matmul_kernel
 
 __global__ void __launch_bounds__(128) small_matmul_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                             double* __restrict__ C, int l) {
@@ -1295,7 +1295,8 @@ __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __re
 // predicated on that flag, so no host synchronisation is needed).
 constexpr double SERIES_MAX = 5e-3;
 constexpr double SERIES_TOL = 1e-18;
-constexpr int SERIES_ITERS = 6, NEUMANN_ITERS = 7, SPLIT = 4;
+constexpr int SERIES_ITERS = 6, NEUMANN_ITERS = 7;
+constexpr int SPLIT = 16;   // lanes per entry: FP64 sums as short per-lane chains plus a shuffle tree
 
 __global__ void series_init_kernel(const double* __restrict__ G, double* __restrict__ E, double* __restrict__ F, int l,
                                    unsigned long long* __restrict__ emax_bits) {
