@@ -217,7 +217,7 @@ int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes,
  * paper's patches / frames setting).  Arrays (host) of `count` descriptors / values; S[i] is a
  * device FP64 buffer of k[i] values; every problem runs on the side X.  When every A[i] is BF16
  * (or FP32 with a TF32 compute mode) with a 16-byte multiple row pitch and 16-byte aligned planes,
- * Omega[i], U[i], V[i] are FP32, the call builds a batch plan (below) without tuning or graph,
+ * Omega[i], U[i], V[i] are FP32 and k[i] + p[i] <= 80, the call builds a batch plan (below) without tuning or graph,
  * runs it once and frees it; otherwise it loops over qlr_qsvd_lowrank.
  */
 int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p,
@@ -227,11 +227,14 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
 /*
  * Batch plans: the batched Algorithm 2 above, planned once and run many times.
  *
- * qlr_batch_create -- checks and plans `count` problems (conditions as above; compute AUTO means
- * BF16 for BF16 A and 3xTF32 for FP32 A; side must be AUTO or X).  Each sketch pass of all the
- * problems is one grouped tensor-core launch over every output tile (plus one grouped staging
- * launch); the per-problem orthonormalisations, core QSVDs and lifts run on up to 128 side
- * streams forked from and joined to the context stream.  At creation the plan allocates its
+ * qlr_batch_create -- checks and plans `count` problems (conditions as above, and l = k + p <= 80
+ * for every problem, else QLR_EUNSUPPORTED; compute AUTO means BF16 for BF16 A and 3xTF32 for
+ * FP32 A; side must be AUTO or X).  Every step runs as one grouped launch over all the problems:
+ * each sketch pass is one grouped tensor-core launch over every output tile (plus one grouped
+ * staging launch); each CholeskyQR step is a grouped Gram (double-FP32), a grouped Cholesky
+ * (double-FP32, one CTA per problem, also forming R^{-1} and the running product of the R
+ * factors in FP32) and a grouped thin x small product; the core QSVDs (FP32 one-sided Jacobi,
+ * sigma from the converged column norms) and the lifts are one launch each.  At creation the plan allocates its
  * device memory (cudaMalloc), times four variants of the grouped sketch (tile order x one CTA per
  * tile or persistent CTAs) and keeps the fastest (the autotuner), runs the whole sequence once
  * (its results are valid), and captures it into a CUDA graph unless opts.flags has
@@ -243,7 +246,7 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  */
 typedef struct qlr_batch qlr_batch;
 typedef struct {
-  int32_t lanes;           /* side streams                                              */
+  int32_t lanes;           /* streams a run uses (1: every step is one grouped launch) */
   int32_t graph;           /* 1 when runs replay the captured CUDA graph               */
   int32_t tile_order;      /* grouped sketch variant chosen: bit 0 tiles with the longest reduction
                               first (else problem order), bit 1 persistent CTAs (else one per tile) */

@@ -1,12 +1,15 @@
 // Batched Algorithm 2 over many independent problems (image patches / frames of uneven sizes).
 //
-// One plan per problem set.  Every pass is one grouped tensor-core sketch launch over all the
-// problems' output tiles (sketch_tc.cu), preceded by one grouped staging launch of their thin
-// operands.  Between passes the per-problem orthonormalisations (and after the last pass the core
-// QSVDs and lifts) run on a set of side streams ("lanes"), problems dealt round-robin, so that
-// the many small latency-bound kernels of different problems overlap on the GPU.  The whole
-// sequence is captured once into a CUDA graph and replayed by every run.  At plan time a small
-// autotuner times the grouped sketch's tile orders and keeps the faster one.
+// One plan per problem set, and one launch per step for all the problems: every sketch pass is
+// a grouped tensor-core launch over all the problems' output tiles (sketch_tc.cu), preceded by
+// one grouped staging launch of their thin operands; every orthonormalisation step is a grouped
+// Gram launch (with its combine), a grouped double-FP32 Cholesky launch (one CTA per problem,
+// which also forms R^{-1} and the running product of the R factors) and a grouped thin x small
+// product; after the last pass one grouped Jacobi launch computes every core QSVD and one
+// grouped product lifts all U and V.  A run is a few dozen launches, whatever the problem count,
+// and each launch spreads the problems' CTAs over the whole GPU.  The sequence is captured once
+// into a CUDA graph and replayed by every run.  At plan time a small autotuner times the grouped
+// sketch's tile orders and keeps the faster one.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -14,28 +17,47 @@
 
 #include "qlr_internal.h"
 
+namespace {
+
+// One orthonormalisation step of one pass (device tables, one entry per problem).
+struct StepTables {
+  const qlr::GramGroupArgs* gram = nullptr;
+  const qlr::CholGroupArgs* chol = nullptr;
+  const qlr::GemmArgs* apply = nullptr;
+};
+
+}  // namespace
+
 struct qlr_batch {
   struct Prob {
-    qlr_qmat A, om, U, V, Y, Z, Q1, Q2;
+    qlr_qmat A, om, U, V, Y, Z, Q1, Q2, T;
     double* S;
-    double *R, *Lm, *Rt;
+    float2* W;        // Gram tiles (double-FP32 pairs)
+    float* G;         // Gram, double-FP32 upper triangle
+    float* Rinv;      // R^{-1} of the current step (FP32)
+    float* Rp[2];     // running products of the last pass's R factors (FP32)
+    float* Uh;        // core QSVD: left vectors (l x k)
+    float* Vh;        // core QSVD: right vectors (l x k)
     int k, p, l;
   };
   qlr_ctx* ctx = nullptr;
-  qlr_ctx main_ctx;                         // issues the grouped launches, untimed: on ctx->stream, or
+  qlr_ctx main_ctx;                         // issues the launches, untimed: on ctx->stream, or
                                             // on cap_stream while the graph is captured
   cudaStream_t cap_stream = nullptr;        // capture needs a stream other than the legacy default
-  int count = 0, passes = 0, compute = 0, orth = 0, mid = 0, lanes = 0;
+  int count = 0, passes = 0, compute = 0, orth = 0, mid = 0, lmax = 0;
   std::vector<Prob> pr;
-  std::vector<cudaStream_t> ls;
-  std::vector<qlr_ctx> lctx;
-  std::vector<char*> lws;
-  size_t lws_bytes = 0;
-  cudaEvent_t fork_ev = nullptr;
-  std::vector<cudaEvent_t> join_ev;
   qlr::GroupedSketch gs[3];                 // (N, Omega -> Y), (H, Q1 -> Z), (N, Q2 -> Y)
   char* gdev[3] = {nullptr, nullptr, nullptr};
   size_t gbytes[3] = {0, 0, 0};
+  std::vector<std::vector<StepTables>> steps;   // [pass - 1][step]
+  const int4* gram_items[2] = {nullptr, nullptr};   // [0]: rows m (odd passes), [1]: rows n
+  const int4* comb_items[2] = {nullptr, nullptr};
+  const int4* apply_items[2] = {nullptr, nullptr};
+  int n_gram[2] = {0, 0}, n_comb[2] = {0, 0}, n_apply[2] = {0, 0};
+  const qlr::JacobiGroupArgs* jac = nullptr;
+  const qlr::GemmArgs* lift = nullptr;
+  const int4* lift_items = nullptr;
+  int n_lift = 0;
   void* dev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -45,10 +67,6 @@ struct qlr_batch {
 };
 
 namespace {
-
-// Side streams: enough that the per-problem chains of small, latency-bound kernels fill the GPU
-// (the hardware runs up to 128 kernels at once).
-constexpr int kMaxLanes = 128;
 
 struct DevGuard {
   int prev = -1;
@@ -72,67 +90,67 @@ int check_q(const qlr_qmat* q, int layout, int dtype, bool allow_pure) {
   return QLR_OK;
 }
 
-// Column-major FP32 thin matrix with a 16-byte multiple column pitch (the tensor-core thin x
-// small products read it through TMA).
+size_t rup(size_t b) { return (b + 255) / 256 * 256; }
+
+// Column-major FP32 thin matrix with a 16-byte multiple column pitch (TMA reads it as the next
+// pass's sketch operand).
 qlr_qmat thin_at(char*& cur, int64_t rows, int64_t cols) {
   qlr_qmat q{};
   q.rows = rows; q.cols = cols; q.ld = (rows + 3) / 4 * 4; q.layout = QLR_COL_MAJOR; q.dtype = QLR_F32;
   const size_t plane = (size_t)q.ld * cols * 4;
   for (int c = 0; c < 4; ++c) q.plane[c] = cur + (size_t)c * plane;
-  cur += (4 * plane + 255) / 256 * 256;
+  cur += rup(4 * plane);
   return q;
 }
 
-double* small_at(char*& cur, size_t doubles) {
-  double* p = reinterpret_cast<double*>(cur);
-  cur += (doubles * 8 + 255) / 256 * 256;
+template <class T>
+T* take(char*& cur, size_t count) {
+  T* p = reinterpret_cast<T*>(cur);
+  cur += rup(count * sizeof(T));
   return p;
 }
+
+qlr::GemmArgs thin_small_args(const qlr_qmat& T, const float* S, int l, int k, const qlr_qmat& C) {
+  qlr::GemmArgs g{};
+  for (int c = 0; c < 4; ++c) {
+    g.a[c] = T.plane[c];
+    g.b[c] = S + (size_t)c * l * k;
+    g.c[c] = C.plane[c];
+  }
+  g.sa_i = 1; g.sa_k = T.ld; g.a_dtype = QLR_F32; g.conj_a = false; g.a_pure = false; g.i_contig = true;
+  g.ldb = l; g.b_dtype = QLR_F32;
+  g.ldc = C.ld; g.c_dtype = QLR_F32;
+  g.M = T.rows; g.N = k; g.K = l;
+  g.alpha = 1.0; g.beta = 0.0;
+  g.acc64 = false;
+  return g;
+}
+
+int orth_steps(int orth) { return orth == QLR_ORTH_SCHOLQR3 ? 3 : (orth == qlr::ORTH_SPAN ? 1 : 2); }
 
 const qlr::GroupedSketch& plan_of(const qlr_batch* b, int pass) {
   return pass == 1 ? b->gs[0] : (pass % 2 == 0 ? b->gs[1] : b->gs[2]);
 }
 
-// The whole batched QSVD, enqueued on main_ctx.stream (and the lanes, forked from and joined to it).
+// The whole batched QSVD, enqueued on main_ctx.stream.
 int enqueue(qlr_batch* b) {
   const int v = b->passes;
-  cudaStream_t ms = b->main_ctx.stream;
-  int64_t launches = 0;
+  qlr_ctx* mc = &b->main_ctx;
+  std::fill(std::begin(mc->launches), std::end(mc->launches), 0);
   for (int i = 1; i <= v; ++i) {
-    QLR_TRY(qlr::sketch_tc_grouped_run(&b->main_ctx, plan_of(b, i)));
-    launches += 2;
-    QLR_CUDA_TRY(cudaEventRecord(b->fork_ev, ms));
-    for (int L = 0; L < b->lanes; ++L) QLR_CUDA_TRY(cudaStreamWaitEvent(b->ls[L], b->fork_ev, 0));
-    for (int j = 0; j < b->count; ++j) {
-      const int L = j % b->lanes;
-      qlr_ctx* lc = &b->lctx[L];
-      WsArena ws(b->lws[L], b->lws_bytes);
-      qlr_batch::Prob& P = b->pr[j];
-      const int orth = (i >= v - 1) ? b->orth : b->mid;
-      if (i % 2 == 1) QLR_TRY(qlr::cholqr(lc, P.Y, P.Q1, i == v ? P.R : nullptr, orth, ws));
-      else QLR_TRY(qlr::cholqr(lc, P.Z, P.Q2, i == v ? P.R : nullptr, orth, ws));
-      if (i == v) {
-        ws.off = 0;
-        QLR_TRY(qlr::core_tsvd(lc, P.l, P.R, P.k, P.Lm, P.S, P.Rt, QLR_F32, ws));
-        // even v: [V_hat, S, U_hat] = TSVD(R2); odd v: [U_hat, S, V_hat] = TSVD(R1)
-        const double* Uhat = (v % 2 == 0) ? P.Rt : P.Lm;
-        const double* Vhat = (v % 2 == 0) ? P.Lm : P.Rt;
-        QLR_TRY(qlr::thin_times_small(lc, P.Q1, Uhat, P.l, P.k, P.U, ws));
-        QLR_TRY(qlr::thin_times_small(lc, P.Q2, Vhat, P.l, P.k, P.V, ws));
-      }
-    }
-    for (int L = 0; L < b->lanes; ++L) {
-      QLR_CUDA_TRY(cudaEventRecord(b->join_ev[L], b->ls[L]));
-      QLR_CUDA_TRY(cudaStreamWaitEvent(ms, b->join_ev[L], 0));
+    QLR_TRY(qlr::sketch_tc_grouped_run(mc, plan_of(b, i)));
+    const int par = (i % 2 == 1) ? 0 : 1;
+    for (const StepTables& st : b->steps[i - 1]) {
+      QLR_TRY(qlr::gram_df_grouped(mc, st.gram, b->gram_items[par], b->n_gram[par], b->comb_items[par], b->n_comb[par]));
+      QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
+      QLR_TRY(qlr::gemm_simt_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
   }
-  int64_t lane_launches = 0;
-  for (auto& lc : b->lctx) {
-    for (int kk = 0; kk < QLR_KID_COUNT; ++kk) lane_launches += lc.launches[kk];
-    std::fill(std::begin(lc.launches), std::end(lc.launches), 0);
-  }
-  std::fill(std::begin(b->main_ctx.launches), std::end(b->main_ctx.launches), 0);
-  b->launches_per_run = launches + lane_launches;
+  QLR_TRY(qlr::jacobi_grouped(mc, b->jac, b->count, b->lmax));
+  QLR_TRY(qlr::gemm_simt_grouped(mc, b->lift, b->lift_items, b->n_lift));
+  int64_t n = 0;
+  for (int kk = 0; kk < QLR_KID_COUNT; ++kk) n += mc->launches[kk];
+  b->launches_per_run = n;
   return QLR_OK;
 }
 
@@ -186,14 +204,137 @@ int autotune(qlr_batch* b) {
 void release(qlr_batch* b) {
   if (!b) return;
   if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
-  for (auto s : b->ls) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  for (auto e : b->join_ev) cudaEventDestroy(e);
   if (b->dev) cudaFree(b->dev);
   delete b;
+}
+
+// Host images of the device tables, appended to one byte buffer (256-byte aligned entries).
+struct TableBuf {
+  std::vector<char> host;
+  std::vector<size_t> offs;
+  template <class T>
+  void add(const std::vector<T>& v) {
+    const size_t off = rup(host.size());
+    host.resize(off + rup(v.size() * sizeof(T) + 1));
+    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+    offs.push_back(off);
+  }
+};
+
+// Lays out every problem's buffers from `base` (returns the bytes used) and records the host
+// images of the step tables in tb, in the order batch_create reads them back.
+size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const qlr_qmat* omega, qlr_qmat* U,
+              double* const* S, qlr_qmat* V, char* base, TableBuf& tb) {
+  using namespace qlr;
+  const int count = b->count, passes = b->passes;
+  char* cur = base;
+  for (int j = 0; j < count; ++j) {
+    qlr_batch::Prob& P = b->pr[j];
+    P.A = A[j]; P.om = omega[j]; P.U = U[j]; P.V = V[j]; P.S = S[j];
+    P.k = k[j]; P.p = p[j]; P.l = k[j] + p[j];
+    const int64_t m = A[j].rows, n = A[j].cols;
+    P.Y = thin_at(cur, m, P.l);
+    P.Q1 = thin_at(cur, m, P.l);
+    P.Z = thin_at(cur, n, P.l);
+    P.Q2 = thin_at(cur, n, P.l);
+    P.T = thin_at(cur, std::max(m, n), P.l);
+    P.W = take<float2>(cur, (size_t)16 * P.l * P.l);
+    P.G = take<float>(cur, (size_t)8 * P.l * P.l);
+    P.Rinv = take<float>(cur, (size_t)4 * P.l * P.l);
+    P.Rp[0] = take<float>(cur, (size_t)4 * P.l * P.l);
+    P.Rp[1] = take<float>(cur, (size_t)4 * P.l * P.l);
+    P.Uh = take<float>(cur, (size_t)4 * P.l * P.k);
+    P.Vh = take<float>(cur, (size_t)4 * P.l * P.k);
+  }
+  // items: Gram tiles, combine blocks and product tiles for row count m (odd passes) or n, the
+  // problems with the most rows first (their CTAs run longest)
+  for (int par = 0; par < 2; ++par) {
+    std::vector<int4> gi, ci, ai;
+    std::vector<int> heavy(count);
+    for (int j = 0; j < count; ++j) heavy[j] = j;
+    auto rows_of = [&](int j) { return par == 0 ? b->pr[j].A.rows : b->pr[j].A.cols; };
+    std::stable_sort(heavy.begin(), heavy.end(), [&](int x, int y) { return rows_of(x) > rows_of(y); });
+    for (int j : heavy) {
+      const qlr_batch::Prob& P = b->pr[j];
+      const int64_t rows = par == 0 ? P.A.rows : P.A.cols;
+      gram_grouped_items(rows, P.l, j, gi, ci);
+      gemm_grouped_items(rows, P.l, j, ai);
+    }
+    b->n_gram[par] = (int)gi.size();
+    b->n_comb[par] = (int)ci.size();
+    b->n_apply[par] = (int)ai.size();
+    tb.add(gi);
+    tb.add(ci);
+    tb.add(ai);
+  }
+  // steps of every pass: Y (odd) or Z (even) -> Q1 or Q2, through T
+  for (int i = 1; i <= passes; ++i) {
+    const int o = (i >= passes - 1) ? b->orth : b->mid;
+    const int ns = orth_steps(o);
+    for (int s = 0; s < ns; ++s) {
+      std::vector<GramGroupArgs> ga(count);
+      std::vector<CholGroupArgs> ca(count);
+      std::vector<GemmArgs> aa(count);
+      for (int j = 0; j < count; ++j) {
+        qlr_batch::Prob& P = b->pr[j];
+        const qlr_qmat& src = (i % 2 == 1) ? P.Y : P.Z;
+        const qlr_qmat& dst = (i % 2 == 1) ? P.Q1 : P.Q2;
+        qlr_qmat T = P.T;
+        T.rows = dst.rows;
+        T.ld = dst.ld;
+        // 1 step: src -> dst; 2: src -> T -> dst; 3: src -> dst -> T -> dst
+        const qlr_qmat* seq[4] = {&src, &dst, nullptr, nullptr};
+        if (ns == 2) { seq[1] = &T; seq[2] = &dst; }
+        if (ns == 3) { seq[2] = &T; seq[3] = &dst; }
+        const qlr_qmat& from = *seq[s];
+        const qlr_qmat& to = *seq[s + 1];
+        GramGroupArgs& G = ga[j];
+        for (int c = 0; c < 4; ++c) G.y[c] = static_cast<const float*>(from.plane[c]);
+        G.ld = from.ld; G.m = from.rows; G.l = P.l; G.W = P.W; G.G = P.G;
+        CholGroupArgs& C = ca[j];
+        C.G = P.G;
+        C.Rinv = P.Rinv;
+        C.l = P.l;
+        // shifted first step (span steps, shifted CholeskyQR3): s = 11 (m l + l (l + 1)) u trace(G),
+        // u = 2^-48 for the double-FP32 Gram and Cholesky
+        const bool shifted = (s == 0) && (o == QLR_ORTH_SCHOLQR3 || o == ORTH_SPAN);
+        C.shift_coef = shifted ? (float)(11.0 * ((double)from.rows * P.l + (double)P.l * (P.l + 1)) * 3.552713678800501e-15)
+                               : 0.f;
+        // the last pass keeps R = R_s ... R_0 for the core QSVD
+        C.Rout = (i == passes) ? P.Rp[s % 2] : nullptr;
+        C.Rprev = (i == passes && s > 0) ? P.Rp[(s - 1) % 2] : nullptr;
+        aa[j] = thin_small_args(from, P.Rinv, P.l, P.l, to);
+        aa[j].b_upper = true;   // R^{-1} is upper triangular
+      }
+      tb.add(ga);
+      tb.add(ca);
+      tb.add(aa);
+    }
+  }
+  // core QSVDs and lifts U = Q1 U_hat, V = Q2 V_hat; even v: [V_hat, S, U_hat] = TSVD(R2),
+  // odd v: [U_hat, S, V_hat] = TSVD(R1)
+  const int nlast = orth_steps(b->orth);
+  std::vector<JacobiGroupArgs> ja(count);
+  std::vector<GemmArgs> la(2 * count);
+  std::vector<int4> li;
+  for (int j = 0; j < count; ++j) {
+    qlr_batch::Prob& P = b->pr[j];
+    ja[j] = {P.Rp[(nlast - 1) % 2], P.Uh, P.Vh, P.S, P.l, P.k};
+    const float* Uhat = (passes % 2 == 0) ? P.Vh : P.Uh;
+    const float* Vhat = (passes % 2 == 0) ? P.Uh : P.Vh;
+    la[j] = thin_small_args(P.Q1, Uhat, P.l, P.k, P.U);
+    la[count + j] = thin_small_args(P.Q2, Vhat, P.l, P.k, P.V);
+    gemm_grouped_items(P.A.rows, P.k, j, li);
+  }
+  for (int j = 0; j < count; ++j) gemm_grouped_items(b->pr[j].A.cols, b->pr[j].k, count + j, li);
+  b->n_lift = (int)li.size();
+  tb.add(ja);
+  tb.add(la);
+  tb.add(li);
+  return (size_t)(cur - base);
 }
 
 }  // namespace
@@ -215,6 +356,7 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   const int orth = opts ? opts->orth : QLR_ORTH_CHOLQR2;
   if (orth != QLR_ORTH_CHOLQR2 && orth != QLR_ORTH_SCHOLQR3) return QLR_EINVAL;
   if (opts && (opts->flags & QLR_FLAG_NO_GRAPH)) use_graph = false;
+  int lmax = 0;
   for (int j = 0; j < count; ++j) {
     QLR_TRY(check_q(&A[j], QLR_ROW_MAJOR, adt, true));
     const int l = k[j] + p[j];
@@ -225,7 +367,9 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
     if (omega[j].rows != A[j].cols || omega[j].cols != l) return QLR_ESHAPE;
     if (U[j].rows != A[j].rows || U[j].cols != k[j] || V[j].rows != A[j].cols || V[j].cols != k[j]) return QLR_ESHAPE;
     if (!S[j]) return QLR_EINVAL;
+    if (l > kBatchMaxL) return QLR_EUNSUPPORTED;
     if (!qlr::sketch_tc_supported(QLR_OP_N, A[j], omega[j], compute)) return QLR_EUNSUPPORTED;
+    lmax = std::max(lmax, l);
   }
   DevGuard g(ctx->device);
   qlr_batch* b = new qlr_batch();
@@ -235,25 +379,13 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   b->compute = compute;
   b->orth = orth;
   b->mid = (opts && (opts->flags & QLR_FLAG_QR_EVERY_PASS)) ? orth : ORTH_SPAN;
-  b->lanes = std::min(count, kMaxLanes);
+  b->lmax = lmax;
   b->main_ctx.device = ctx->device;
   b->main_ctx.stream = ctx->stream;
   b->main_ctx.d_err = ctx->d_err;
   b->main_ctx.num_sms = ctx->num_sms;
   b->pr.resize(count);
 
-  // sizes: per-problem thin and small buffers, the three grouped plans, the lane workspaces
-  size_t bytes = 0, lane_need = 0;
-  int64_t maxl = 0;
-  for (int j = 0; j < count; ++j) {
-    const int64_t m = A[j].rows, n = A[j].cols, l = k[j] + p[j];
-    const int64_t mp = (m + 3) / 4 * 4, np = (n + 3) / 4 * 4;
-    bytes += 2 * ((4 * (size_t)mp * l * 4 + 255) / 256 * 256) + 2 * ((4 * (size_t)np * l * 4 + 255) / 256 * 256);
-    bytes += ((size_t)4 * l * l * 8 + 255) / 256 * 256 + 2 * (((size_t)4 * l * k[j] * 8 + 255) / 256 * 256);
-    lane_need = std::max(lane_need, cholqr_ws_bound(std::max(m, n), l, 4) + tsvd_ws_bound(l));
-    maxl = std::max(maxl, l);
-  }
-  (void)maxl;
   // thin operands of the grouped plans are described before their buffers exist: sizes only
   std::vector<qlr_qmat> Av(A, A + count), Xn(count), Xh(count);
   for (int j = 0; j < count; ++j) {
@@ -266,45 +398,53 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   }
   b->gbytes[0] = b->gbytes[2] = sketch_tc_grouped_bytes(QLR_OP_N, count, Av.data(), Xn.data(), compute);
   b->gbytes[1] = sketch_tc_grouped_bytes(QLR_OP_H, count, Av.data(), Xh.data(), compute);
-  b->lws_bytes = (lane_need + 255) / 256 * 256;
-  const size_t total = bytes + b->gbytes[0] + b->gbytes[1] + b->gbytes[2] + (size_t)b->lanes * b->lws_bytes + 4096;
+  // a dry layout from a dummy base gives the sizes of the buffers and of the tables
+  size_t bytes = 0, tbytes = 0;
+  {
+    TableBuf dry;
+    char* dummy = reinterpret_cast<char*>((uintptr_t)256);
+    bytes = rup(layout(b, A, k, p, omega, U, S, V, dummy, dry));
+    tbytes = rup(dry.host.size());
+  }
+  const size_t total = bytes + rup(b->gbytes[0]) + rup(b->gbytes[1]) + rup(b->gbytes[2]) + tbytes;
   if (cudaMalloc(&b->dev, total) != cudaSuccess) {
     cudaGetLastError();
     release(b);
     return QLR_ENOMEM;
   }
-  char* cur = static_cast<char*>(b->dev);
-  for (int j = 0; j < count; ++j) {
-    qlr_batch::Prob& P = b->pr[j];
-    P.A = A[j]; P.om = omega[j]; P.U = U[j]; P.V = V[j]; P.S = S[j];
-    P.k = k[j]; P.p = p[j]; P.l = k[j] + p[j];
-    P.Y = thin_at(cur, A[j].rows, P.l);
-    P.Q1 = thin_at(cur, A[j].rows, P.l);
-    P.Z = thin_at(cur, A[j].cols, P.l);
-    P.Q2 = thin_at(cur, A[j].cols, P.l);
-    P.R = small_at(cur, (size_t)4 * P.l * P.l);
-    P.Lm = small_at(cur, (size_t)4 * P.l * P.k);
-    P.Rt = small_at(cur, (size_t)4 * P.l * P.k);
-  }
-  for (int s = 0; s < 3; ++s) { b->gdev[s] = cur; cur += (b->gbytes[s] + 255) / 256 * 256; }
-  for (int L = 0; L < b->lanes; ++L) { b->lws.push_back(cur); cur += b->lws_bytes; }
-  int rc = cudaMemsetAsync(b->dev, 0, bytes, ctx->stream) == cudaSuccess ? QLR_OK : QLR_ECUDA;
-
-  // lanes: streams, untimed contexts sharing the error word, an even share of the SMs
-  b->lctx.resize(b->lanes);
-  b->join_ev.resize(b->lanes, nullptr);
-  if (rc == QLR_OK && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) rc = QLR_ECUDA;
-  for (int L = 0; L < b->lanes && rc == QLR_OK; ++L) {
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { rc = QLR_ECUDA; break; }
-    b->ls.push_back(s);
-    if (cudaEventCreateWithFlags(&b->join_ev[L], cudaEventDisableTiming) != cudaSuccess) { rc = QLR_ECUDA; break; }
-    qlr_ctx& lc = b->lctx[L];
-    lc.device = ctx->device;
-    lc.stream = s;
-    lc.d_err = ctx->d_err;
-    lc.num_sms = std::max(4, 2 * ctx->num_sms / b->lanes);
-    lc.small_mode = true;
+  char* base = static_cast<char*>(b->dev);
+  TableBuf tb;
+  layout(b, A, k, p, omega, U, S, V, base, tb);
+  char* cur = base + bytes;
+  for (int s = 0; s < 3; ++s) { b->gdev[s] = cur; cur += rup(b->gbytes[s]); }
+  char* tdev = cur;
+  int rc = QLR_OK;
+  if (cudaMemsetAsync(b->dev, 0, bytes, ctx->stream) != cudaSuccess) rc = QLR_ECUDA;
+  if (rc == QLR_OK && cudaMemcpyAsync(tdev, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    rc = QLR_ECUDA;
+  if (rc == QLR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = QLR_ECUDA;   // tb is pageable
+  if (rc == QLR_OK) {
+    size_t q = 0;
+    auto next = [&]() { return tdev + tb.offs[q++]; };
+    for (int par = 0; par < 2; ++par) {
+      b->gram_items[par] = reinterpret_cast<const int4*>(next());
+      b->comb_items[par] = reinterpret_cast<const int4*>(next());
+      b->apply_items[par] = reinterpret_cast<const int4*>(next());
+    }
+    b->steps.resize(passes);
+    for (int i = 1; i <= passes; ++i) {
+      const int ns = orth_steps((i >= passes - 1) ? b->orth : b->mid);
+      for (int s = 0; s < ns; ++s) {
+        StepTables st;
+        st.gram = reinterpret_cast<const GramGroupArgs*>(next());
+        st.chol = reinterpret_cast<const CholGroupArgs*>(next());
+        st.apply = reinterpret_cast<const GemmArgs*>(next());
+        b->steps[i - 1].push_back(st);
+      }
+    }
+    b->jac = reinterpret_cast<const JacobiGroupArgs*>(next());
+    b->lift = reinterpret_cast<const GemmArgs*>(next());
+    b->lift_items = reinterpret_cast<const int4*>(next());
   }
   // QLR_BATCH_VARIANT=0..3 in the environment fixes the grouped sketch variant (no tuning)
   const char* force = std::getenv("QLR_BATCH_VARIANT");
@@ -361,7 +501,7 @@ extern "C" int qlr_batch_run(qlr_batch* b) {
 
 extern "C" int qlr_batch_info(const qlr_batch* b, qlr_batch_stats* st) {
   if (!b || !st) return QLR_EINVAL;
-  st->lanes = b->lanes;
+  st->lanes = 1;
   st->graph = b->exec ? 1 : 0;
   st->tile_order = b->order;
   for (int i = 0; i < 4; ++i) st->tune_ms[i] = b->tune_ms[i];

@@ -59,23 +59,40 @@ __device__ __forceinline__ void rr_pair(int lp, int r, int i, int& p, int& q) {
   }
 }
 
-// Vout != nullptr (W in shared memory and room for V next to it): the rotations are applied to
-// V = I in place as well, and neither the log nor the replay is needed.
+// Reciprocal and reciprocal square root for the rotation parameters: the hardware approximations
+// in float (a few ulp; every rotation is applied to W and V, or logged and replayed, exactly as
+// computed, so the vectors stay orthonormal to the working precision), correctly rounded in
+// double.
+__device__ __forceinline__ float jrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double jrsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float jrcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double jrcp(double x) { return 1.0 / x; }
+
+// Rotation parameters of a column pair (alpha = |w_p|^2, beta = |w_q|^2, gamma = w_p^H w_q with
+// |gamma|^2 = gn2 > 0): mu = gamma / |gamma| and the real Jacobi rotation (c, s) that
+// orthogonalises (w_p, w_q mu*): t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// zeta = (beta - alpha) / (2 |gamma|), c = 1 / sqrt(1 + t^2), s = c t.
 template <class T>
-__global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R, int l, T* __restrict__ Wout,
-                                                     bool w_smem, int max_sweeps, T tol, T* __restrict__ sig_out,
-                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err,
-                                                     T* __restrict__ Vout) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void jacobi_rotation(T alpha, T beta, const Quat<T>& g, T gn2, Quat<T>& mu, T& c, T& s) {
+  const T ign = jrsqrt(gn2);
+  mu = {g.w * ign, g.x * ign, g.y * ign, g.z * ign};
+  const T zeta = (beta - alpha) * ((T)0.5 * ign);
+  const T az = fabs(zeta);
+  const T x = (T)1 + az * az;
+  const T den = (az < (T)1e18) ? az + x * jrsqrt(x) : (T)2 * az;
+  const T tt = (zeta >= 0 ? (T)1 : (T)-1) * jrcp(den);
+  c = jrsqrt((T)1 + tt * tt);
+  s = c * tt;
+}
+
+// Cyclic (round-robin) one-sided Jacobi sweeps by one CTA of JT threads on W (l x l, planes of
+// l * l, column-major), with the same right rotations applied to Vs when it is set; otherwise
+// every rotation is logged to rlog.  Returns the number of sweeps run; *converged is set when
+// the last sweep rotated no pair.
+template <class T>
+__device__ int jacobi_sweeps(T* W, T* Vs, int l, int max_sweeps, T tol, T* rlog, bool* converged_out) {
   __shared__ int s_rot;
-  T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
-  const size_t ll = (size_t)l * l;
-  T* Vs = Vout ? reinterpret_cast<T*>(smem_raw) + 4 * ll : nullptr;
-  for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
-  if (Vs)
-    for (size_t e = t; e < 4 * ll; e += JT) Vs[e] = (e < ll && e % (l + 1) == 0) ? (T)1 : (T)0;
-  __syncthreads();
   const int lp = l + (l & 1);
   int sweep = 0;
   bool converged = (l < 2);
@@ -98,17 +115,16 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
         }
         a = warp_sum(a); b = warp_sum(b);
         g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
-        T gn = sqrt(qnorm2(g));
+        const T gn2 = qnorm2(g);
         T* lg = Vs ? nullptr : rlog + (((size_t)sweep * (lp - 1) + r) * (lp / 2) + pi) * 6;
-        if (!(gn > tol * sqrt(a * b)) || gn == (T)0) {
+        if (!(gn2 > (tol * tol * a) * b)) {      // pair already orthogonal to the tolerance
           if (lane == 0 && lg) { lg[0] = (T)1; lg[1] = (T)0; lg[2] = (T)1; lg[3] = lg[4] = lg[5] = (T)0; }
           continue;
         }
         if (lane == 0) s_rot = 1;
-        Quat<T> mu = {g.w / gn, g.x / gn, g.y / gn, g.z / gn};
-        T zeta = (b - a) / (2 * gn);
-        T tt = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-        T c = (T)1 / sqrt((T)1 + tt * tt), s = c * tt;
+        Quat<T> mu;
+        T c, s;
+        jacobi_rotation(a, b, g, gn2, mu, c, s);
         if (lane == 0 && lg) { lg[0] = c; lg[1] = s; lg[2] = mu.w; lg[3] = mu.x; lg[4] = mu.y; lg[5] = mu.z; }
         for (int i = lane; i < l; i += 32) {
           Quat<T> wp = ldw(W, l, i, p), wq = qmulc(ldw(W, l, i, q), mu);   // w_q mu*
@@ -128,6 +144,28 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
     converged = (s_rot == 0);
     __syncthreads();
   }
+  *converged_out = converged;
+  return sweep;
+}
+
+// Vout != nullptr (W in shared memory and room for V next to it): the rotations are applied to
+// V = I in place as well, and neither the log nor the replay is needed.
+template <class T>
+__global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R, int l, T* __restrict__ Wout,
+                                                     bool w_smem, int max_sweeps, T tol, T* __restrict__ sig_out,
+                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err,
+                                                     T* __restrict__ Vout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
+  const size_t ll = (size_t)l * l;
+  T* Vs = Vout ? reinterpret_cast<T*>(smem_raw) + 4 * ll : nullptr;
+  for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
+  if (Vs)
+    for (size_t e = t; e < 4 * ll; e += JT) Vs[e] = (e < ll && e % (l + 1) == 0) ? (T)1 : (T)0;
+  __syncthreads();
+  bool converged = false;
+  const int sweep = jacobi_sweeps<T>(W, Vs, l, max_sweeps, tol, rlog, &converged);
   if (t == 0) {
     *sweeps_out = sweep;
     if (!converged) qlr_set_error(err, QLR_ENOCONV);
@@ -149,6 +187,69 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
     for (size_t e = t; e < 4 * ll; e += JT) Wout[e] = W[e];
   if (Vs)
     for (size_t e = t; e < 4 * ll; e += JT) Vout[e] = Vs[e];
+}
+
+template <class T>
+__device__ __forceinline__ T rank_key(T x) { return isnan(x) ? -INFINITY : x; }
+
+// Batch plans: one CTA per problem, W = R and V = I in shared memory (FP32).  After the sweeps
+// sigma_j = |w_j| and u_j = w_j / sigma_j; the k largest sigma (descending, ties by column) go to
+// S and their u, v columns to U, V.  Without the FP64 Rayleigh step of the single-problem path:
+// the plan's sketches and bases are BF16 / FP32, and the column norms carry the FP32 accuracy of
+// the rotated columns.
+__global__ void __launch_bounds__(JT) jacobi_grouped_kernel(const qlr::JacobiGroupArgs* __restrict__ args,
+                                                            int max_sweeps, int* err) {
+  const qlr::JacobiGroupArgs& a = args[blockIdx.x];
+  const int l = a.l, k = a.k;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t ll = (size_t)l * l;
+  float* W = reinterpret_cast<float*>(smem_raw);
+  float* Vs = W + 4 * ll;
+  float* sig = Vs + 4 * ll;
+  int* ord = reinterpret_cast<int*>(sig + l);
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
+  const float* R = a.R;
+  for (size_t e = t; e < 4 * ll; e += JT) {
+    W[e] = R[e];
+    Vs[e] = (e < ll && e % (l + 1) == 0) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float tol = 8.f * 5.9604645e-08f * sqrtf((float)l);   // above the rounding noise of the dot products
+  bool converged = false;
+  jacobi_sweeps<float>(W, Vs, l, max_sweeps, tol, nullptr, &converged);
+  if (t == 0 && !converged) qlr_set_error(err, QLR_ENOCONV);
+  for (int j = warp; j < l; j += nwarps) {
+    float s2 = 0.f;
+    for (int i = lane; i < l; i += 32) s2 += qnorm2(ldw(W, l, i, j));
+    s2 = sqrtf(warp_sum(s2));
+    if (lane == 0) sig[j] = s2;
+    const float inv = s2 > 0.f ? 1.f / s2 : 0.f;
+    for (int i = lane; i < l; i += 32) {
+      const Quat<float> w = ldw(W, l, i, j);
+      stw(W, l, i, j, {w.w * inv, w.x * inv, w.y * inv, w.z * inv});
+    }
+  }
+  __syncthreads();
+  for (int j = t; j < l; j += JT) {
+    const float sj = rank_key(sig[j]);
+    int rank = 0;
+    for (int i = 0; i < l; ++i) {
+      const float si = rank_key(sig[i]);
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    ord[rank] = j;
+  }
+  __syncthreads();
+  for (int r = t; r < k; r += JT) a.S[r] = (double)sig[ord[r]];
+  const size_t lk = (size_t)l * k;
+  float* U = a.U;
+  float* V = a.V;
+  for (size_t e = t; e < 4 * lk; e += JT) {
+    const int c = (int)(e / lk), r = (int)((e % lk) / l), i = (int)(e % l);
+    const size_t src = (size_t)c * ll + (size_t)ord[r] * l + i;
+    U[e] = W[src];
+    V[e] = Vs[src];
+  }
 }
 
 // Replay the logged rotations on V = I, one warp per row of V (rows are independent under right
@@ -210,13 +311,6 @@ constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4
 __host__ __device__ __forceinline__ int jb_stages_per_sweep(int bw) { return (2 * bw - 1) + (2 * JP - 2) * bw; }
 __host__ __device__ __forceinline__ int jb_stage(int br, int lr, int bw) { return br == 0 ? lr : (2 * bw - 1) + (br - 1) * bw + lr; }
 
-// Reciprocal and reciprocal square root for the rotation parameters: the hardware approximations
-// in float (a few ulp; every rotation is logged and replayed exactly as applied, and the singular
-// values are re-evaluated in FP64 at the end), correctly rounded in double.
-__device__ __forceinline__ float jrsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double jrsqrt(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ float jrcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double jrcp(double x) { return 1.0 / x; }
 
 // Rows per lane RPL: the two columns of a pair stay in registers between the dot products and
 // the rotation (l <= 32 RPL).
@@ -318,14 +412,9 @@ __global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const doubl
             continue;
           }
           if (lane == 0) s_rot = 1;
-          const T ign = jrsqrt(gn2);
-          const Quat<T> mu = {g.w * ign, g.x * ign, g.y * ign, g.z * ign};
-          const T zeta = (bb2 - aa) * ((T)0.5 * ign);
-          const T az = fabs(zeta);
-          const T x = (T)1 + az * az;
-          const T den = (az < (T)1e18) ? az + x * jrsqrt(x) : (T)2 * az;
-          const T tt = (zeta >= 0 ? (T)1 : (T)-1) * jrcp(den);
-          const T c = jrsqrt((T)1 + tt * tt), sn = c * tt;
+          Quat<T> mu;
+          T c, sn;
+          jacobi_rotation(aa, bb2, g, gn2, mu, c, sn);
           if (lane == 0) {
             lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = c; lg[3] = sn;
             lg[4] = mu.w; lg[5] = mu.x; lg[6] = mu.y; lg[7] = mu.z;
@@ -477,8 +566,6 @@ __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw,
 
 // Rank of each column by descending sigma (ties broken by index): order[rank] = column.  A NaN
 // sigma sorts last, so the keys are totally ordered and `order` is always a permutation.
-template <class T>
-__device__ __forceinline__ T rank_key(T x) { return isnan(x) ? -INFINITY : x; }
 
 template <class T>
 __global__ void rank_kernel(const T* __restrict__ sig, int l, int* __restrict__ order) {
@@ -648,6 +735,20 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   // static shared memory comes on top of the dynamic size: always opt in
   QLR_CUDA_TRY(cudaFuncSetAttribute(refine_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
   { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); qlr_count_launch(); }
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
+
+size_t jacobi_grouped_smem(int lmax) { return (size_t)2 * 4 * lmax * lmax * 4 + (size_t)lmax * 8 + 64; }
+
+int jacobi_grouped(qlr_ctx* ctx, const JacobiGroupArgs* d_args, int count, int lmax) {
+  if (count <= 0) return QLR_OK;
+  if (lmax > kBatchMaxL) return QLR_EUNSUPPORTED;
+  const size_t smem = jacobi_grouped_smem(lmax);
+  QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTimer kt(ctx, QLR_KID_JACOBI);
+  jacobi_grouped_kernel<<<count, JT, smem, ctx->stream>>>(d_args, JMAX_SWEEPS, ctx->d_err);
+  qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }

@@ -18,15 +18,16 @@ __device__ __forceinline__ TAcc load_elem(const void* p, int64_t idx, int dt) {
   return (TAcc)__bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
 }
 
+// One BM x BN output tile (row tile bx, column tile by) of C.
 template <class TAcc, bool I_CONTIG, bool CONJ>
-__global__ void __launch_bounds__(NT) gemm_simt_kernel(qlr::GemmArgs g) {
+__device__ __forceinline__ void gemm_simt_tile(const qlr::GemmArgs& g, int64_t bx, int64_t by) {
   // one element of padding for 4-byte types (bank conflicts); none for doubles (48 KB static limit)
   constexpr int PAD = sizeof(TAcc) == 4 ? 1 : 0;
   __shared__ TAcc As[4][BK][BM + PAD];
   __shared__ TAcc Bs[4][BK][BN + PAD];
   const int t = threadIdx.x;
   const int tx = t % 16, ty = t / 16;
-  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  const int64_t i0 = bx * BM, j0 = by * BN;
 
   Quat<TAcc> acc[4][2];
 #pragma unroll
@@ -76,11 +77,13 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(qlr::GemmArgs g) {
     }
   };
 
+  // rows of an upper-triangular B below the column tile's last column are zero
+  const int64_t kend = g.b_upper ? min(g.K, j0 + BN) : g.K;
   load_tile(0);
-  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+  for (int64_t k0 = 0; k0 < kend; k0 += BK) {
     store_tile();
     __syncthreads();
-    if (k0 + BK < g.K) load_tile(k0 + BK);   // prefetch next tile into registers
+    if (k0 + BK < kend) load_tile(k0 + BK);   // prefetch next tile into registers
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       Quat<TAcc> a[4], b[2];
@@ -128,6 +131,18 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(qlr::GemmArgs g) {
     }
 }
 
+template <class TAcc, bool I_CONTIG, bool CONJ>
+__global__ void __launch_bounds__(NT) gemm_simt_kernel(qlr::GemmArgs g) {
+  gemm_simt_tile<TAcc, I_CONTIG, CONJ>(g, blockIdx.x, blockIdx.y);
+}
+
+// Many independent products in one launch (batch plans): item (problem, row tile, column tile).
+__global__ void __launch_bounds__(NT) gemm_simt_grouped_kernel(const qlr::GemmArgs* __restrict__ args,
+                                                                const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  gemm_simt_tile<float, true, false>(args[it.x], it.y, it.z);
+}
+
 template <class TAcc>
 void launch(const qlr::GemmArgs& g, cudaStream_t s) {
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN));
@@ -144,6 +159,20 @@ void launch(const qlr::GemmArgs& g, cudaStream_t s) {
 }  // namespace
 
 namespace qlr {
+void gemm_grouped_items(int64_t M, int64_t N, int prob, std::vector<int4>& items) {
+  for (int64_t by = 0; by < (N + BN - 1) / BN; ++by)
+    for (int64_t bx = 0; bx < (M + BM - 1) / BM; ++bx) items.push_back(make_int4(prob, (int)bx, (int)by, 0));
+}
+
+int gemm_simt_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems) {
+  if (nitems <= 0) return QLR_OK;
+  KTimer kt(ctx, QLR_KID_APPLY);
+  gemm_simt_grouped_kernel<<<nitems, NT, 0, ctx->stream>>>(d_args, d_items);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
+
 int gemm_simt(qlr_ctx* ctx, const GemmArgs& g) {
   if (g.M == 0 || g.N == 0) return QLR_OK;
   if (g.N > 65535LL * BN || g.M > (int64_t)INT32_MAX * BM) return QLR_EUNSUPPORTED;

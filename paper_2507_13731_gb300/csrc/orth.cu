@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(128) small_matmul_kernel(const double* __restr
 // The real symmetric W = Yh^T Yh of the plane-stacked Yh = [Y0 Y1 Y2 Y3] (m x 4l) is accumulated
 // in double-FP32: every product a*b is split exactly into hi + lo with an FMA, hi is added with
 // a branch-free two-sum (Knuth) into (S, C), lo goes into C.  The result S + C has a relative
-// error of about 2^-48 of sum |a b|.  Upper 64 x 64 tiles only; row chunks give partial sums
+// error of about 2^-48 of sum |a b|.  Upper 64 x 64 tiles only (on diagonal tiles, the entries on or
+// above the diagonal); row chunks give partial sums
 // that a second kernel adds in FP64 and combines into the quaternion Gram:
 //   G0 = W00 + W11 + W22 + W33,  G1 = W01 - W10 - W23 + W32,
 //   G2 = W02 + W13 - W20 - W31,  G3 = W03 - W12 + W21 - W30   (W_cd = Y_c^T Y_d).
@@ -168,20 +169,21 @@ __device__ __forceinline__ void df_add(float& S, float& C, float a, float b) {
   C = __fadd_rn(C, __fadd_rn(e, lo));
 }
 
-__global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
-                                                               const float* __restrict__ y2, const float* __restrict__ y3,
-                                                               int64_t m, int l, int64_t ld, int64_t rows_per_chunk,
-                                                               double* __restrict__ part) {
+// One 64 x 64 tile (I0, J0) of W over rows [r_begin, r_end): thread (tx, ty) accumulates the
+// entries (I0 + tx + 16 x, J0 + ty + 16 z) into (S, C).  On a diagonal tile (DIAG, I0 == J0) the
+// pairs x > z lie strictly below the diagonal (I - J >= 16 - 15) and are skipped: W is symmetric
+// and its readers take entry (I, J) with I <= J.
+__device__ __forceinline__ const float* plane_of(const float* y0, const float* y1, const float* y2, const float* y3, int c) {
+  return c == 0 ? y0 : (c == 1 ? y1 : (c == 2 ? y2 : y3));
+}
+template <bool DIAG>
+__device__ __forceinline__ void gram_df_tile(const float* y0, const float* y1, const float* y2, const float* y3, int l,
+                                             int64_t ld, int64_t r_begin, int64_t r_end, int I0, int J0,
+                                             float (&S)[4][4], float (&C)[4][4]) {
   __shared__ float Ya[WR][WT];
   __shared__ float Yb[WR][WT];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int2 tile = upper_tri_entry((int)blockIdx.x);
-  const int I0 = tile.x * WT, J0 = tile.y * WT;
   const int L4 = 4 * l;
-  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
-  const int64_t r_end = min(m, r_begin + rows_per_chunk);
-  const float* yp[4] = {y0, y1, y2, y3};
-  float S[4][4], C[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -195,8 +197,8 @@ __global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __res
       float va = 0.f, vb = 0.f;
       if (gr < r_end) {
         const int Ia = I0 + cc, Ib = J0 + cc;
-        if (Ia < L4) va = yp[Ia / l][gr + (int64_t)(Ia % l) * ld];
-        if (Ib < L4) vb = yp[Ib / l][gr + (int64_t)(Ib % l) * ld];
+        if (Ia < L4) va = plane_of(y0, y1, y2, y3, Ia / l)[gr + (int64_t)(Ia % l) * ld];
+        if (Ib < L4) vb = plane_of(y0, y1, y2, y3, Ib / l)[gr + (int64_t)(Ib % l) * ld];
       }
       Ya[rr][cc] = va;
       Yb[rr][cc] = vb;
@@ -210,17 +212,34 @@ __global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __res
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int z = 0; z < 4; ++z) df_add(S[x][z], C[x][z], a[x], b[z]);
+        for (int z = 0; z < 4; ++z)
+          if (!DIAG || x <= z) df_add(S[x][z], C[x][z], a[x], b[z]);
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256) gram_df_partial_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
+                                                               const float* __restrict__ y2, const float* __restrict__ y3,
+                                                               int64_t m, int l, int64_t ld, int64_t rows_per_chunk,
+                                                               double* __restrict__ part) {
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const int2 tile = upper_tri_entry((int)blockIdx.x);
+  const int I0 = tile.x * WT, J0 = tile.y * WT;
+  const int L4 = 4 * l;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r_end = min(m, r_begin + rows_per_chunk);
+  float S[4][4], C[4][4];
+  const bool diag = (tile.x == tile.y);
+  if (diag) gram_df_tile<true>(y0, y1, y2, y3, l, ld, r_begin, r_end, I0, J0, S, C);
+  else gram_df_tile<false>(y0, y1, y2, y3, l, ld, r_begin, r_end, I0, J0, S, C);
   double* P = part + (size_t)blockIdx.y * L4 * L4;
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int z = 0; z < 4; ++z) {
       const int I = I0 + tx + 16 * x, J = J0 + ty + 16 * z;
-      if (I < L4 && J < L4) P[(size_t)J * L4 + I] = (double)S[x][z] + (double)C[x][z];
+      if (I < L4 && J < L4 && !(diag && x > z)) P[(size_t)J * L4 + I] = (double)S[x][z] + (double)C[x][z];
     }
 }
 
@@ -236,7 +255,7 @@ __global__ void gram_df_reduce_kernel(double* __restrict__ part, int nchunks, in
 }
 
 __device__ __forceinline__ double w_at(const double* __restrict__ W, int L4, int I, int J) {
-  if ((I / WT) > (J / WT)) { int t = I; I = J; J = t; }     // only upper tiles were computed
+  if (I > J) { int t = I; I = J; J = t; }     // only entries on or above the diagonal were computed
   return W[(size_t)J * L4 + I];
 }
 
@@ -1404,9 +1423,301 @@ __global__ void fill_identity_kernel(double* __restrict__ X, int l) {
   st_small(X, l, i, j, {i == j ? 1.0 : 0.0, 0.0, 0.0, 0.0});
 }
 
+// ---------------------------------------------------------------------------------------
+// Grouped steps of batch plans: one launch runs one orthonormalisation step for every problem
+// of the plan (item tables map each CTA to its problem and tile).  The small operands are FP32
+// or double-FP32 throughout, so no FP64 instruction runs on this path.
+
+// W tiles of one problem's Gram as (S, C) double-FP32 pairs (one row chunk: the whole m).
+__global__ void __launch_bounds__(256) gram_df_grouped_kernel(const qlr::GramGroupArgs* __restrict__ args,
+                                                               const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const qlr::GramGroupArgs& a = args[it.x];
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const int2 tile = upper_tri_entry(it.y);
+  const int I0 = tile.x * WT, J0 = tile.y * WT;
+  const int l = a.l, L4 = 4 * l;
+  float S[4][4], C[4][4];
+  const bool diag = (tile.x == tile.y);
+  if (diag) gram_df_tile<true>(a.y[0], a.y[1], a.y[2], a.y[3], l, a.ld, 0, a.m, I0, J0, S, C);
+  else gram_df_tile<false>(a.y[0], a.y[1], a.y[2], a.y[3], l, a.ld, 0, a.m, I0, J0, S, C);
+  float2* W = a.W;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int I = I0 + tx + 16 * x, J = J0 + ty + 16 * z;
+      if (I < L4 && J < L4 && !(diag && x > z)) W[(size_t)J * L4 + I] = make_float2(S[x][z], C[x][z]);
+    }
+}
+
+__device__ __forceinline__ d32 wdf_at(const float2* __restrict__ W, int L4, int I, int J) {
+  if (I > J) { int t = I; I = J; J = t; }     // only entries on or above the diagonal were computed
+  const float2 v = W[(size_t)J * L4 + I];
+  return {v.x, v.y};
+}
+
+// The quaternion Gram's upper triangle from W (the sign pattern of gram_df_combine_kernel), in
+// double-FP32: entry (i, j) as 8 floats (high w, x, y, z; low w, x, y, z) at G + 8 (j l + i).
+__global__ void __launch_bounds__(128) gram_df_combine_grouped_kernel(const qlr::GramGroupArgs* __restrict__ args,
+                                                                       const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const qlr::GramGroupArgs& a = args[it.x];
+  const int l = a.l, L4 = 4 * l;
+  const int idx = it.y * 128 + (int)threadIdx.x;
+  if (idx >= l * l) return;
+  const int i = idx % l, j = idx / l;
+  if (i > j) return;
+  d32 w[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) w[c][d] = wdf_at(a.W, L4, c * l + i, d * l + j);
+  d32 g[4];
+  g[0] = d32_add(d32_add(w[0][0], w[1][1]), d32_add(w[2][2], w[3][3]));
+  g[1] = d32_add(d32_add(w[0][1], d32_neg(w[1][0])), d32_add(d32_neg(w[2][3]), w[3][2]));
+  g[2] = d32_add(d32_add(w[0][2], w[1][3]), d32_add(d32_neg(w[2][0]), d32_neg(w[3][1])));
+  g[3] = d32_add(d32_add(w[0][3], d32_neg(w[1][2])), d32_add(w[2][1], d32_neg(w[3][0])));
+  if (i == j) g[1] = g[2] = g[3] = {0.f, 0.f};
+  float4* o = reinterpret_cast<float4*>(a.G + 8 * ((size_t)j * l + i));
+  o[0] = make_float4(g[0].h, g[1].h, g[2].h, g[3].h);
+  o[1] = make_float4(g[0].l, g[1].l, g[2].l, g[3].l);
+}
+
+// s + e += a b for double-FP32 a = ah + al, b = bh + bl: the high product is split exactly by an
+// FMA, its rounded part added into s by a two-sum (Knuth), and every low-order term collected in
+// e (renormalised once per entry, after four products).
+__device__ __forceinline__ void d32_acc(float& s, float& e, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -p);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  const float t = __fadd_rn(s, p);
+  const float v = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(p, v));
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(err, pe));
+}
+__device__ __forceinline__ void d32_renorm(float s, float e, float& h, float& l) {
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// A double-FP32 quaternion in shared memory: high and low parts, components (real, i, j, k) in
+// (x, y, z, w).
+struct DQ {
+  float4 h, l;
+};
+
+// w <- w - conj(a) b (component signs of conj(a) b as in qcmul).
+__device__ __forceinline__ void dq_fms_conj(DQ& w, const DQ& a, const DQ& b) {
+  float s, e;
+  s = w.h.x; e = w.l.x;
+  d32_acc(s, e, -a.h.x, -a.l.x, b.h.x, b.l.x); d32_acc(s, e, -a.h.y, -a.l.y, b.h.y, b.l.y);
+  d32_acc(s, e, -a.h.z, -a.l.z, b.h.z, b.l.z); d32_acc(s, e, -a.h.w, -a.l.w, b.h.w, b.l.w);
+  d32_renorm(s, e, w.h.x, w.l.x);
+  s = w.h.y; e = w.l.y;
+  d32_acc(s, e, -a.h.x, -a.l.x, b.h.y, b.l.y); d32_acc(s, e, a.h.y, a.l.y, b.h.x, b.l.x);
+  d32_acc(s, e, a.h.z, a.l.z, b.h.w, b.l.w); d32_acc(s, e, -a.h.w, -a.l.w, b.h.z, b.l.z);
+  d32_renorm(s, e, w.h.y, w.l.y);
+  s = w.h.z; e = w.l.z;
+  d32_acc(s, e, -a.h.x, -a.l.x, b.h.z, b.l.z); d32_acc(s, e, -a.h.y, -a.l.y, b.h.w, b.l.w);
+  d32_acc(s, e, a.h.z, a.l.z, b.h.x, b.l.x); d32_acc(s, e, a.h.w, a.l.w, b.h.y, b.l.y);
+  d32_renorm(s, e, w.h.z, w.l.z);
+  s = w.h.w; e = w.l.w;
+  d32_acc(s, e, -a.h.x, -a.l.x, b.h.w, b.l.w); d32_acc(s, e, a.h.y, a.l.y, b.h.z, b.l.z);
+  d32_acc(s, e, -a.h.z, -a.l.z, b.h.y, b.l.y); d32_acc(s, e, a.h.w, a.l.w, b.h.x, b.l.x);
+  d32_renorm(s, e, w.h.w, w.l.w);
+}
+
+__device__ __forceinline__ Quat<float> q_of(const float4& v) { return {v.x, v.y, v.z, v.w}; }
+
+// One CTA per problem: the whole quaternion Cholesky factorisation of G (+ shift I) in
+// double-FP32, right-looking over the packed upper triangle in shared memory (column k at offset
+// k (k + 1) / 2), with the rank-1 updates' entries enumerated densely over all threads.  Then,
+// from the factor's high parts, R^{-1} in FP32 (columns are independent: one warp per column
+// solves R x = e_j by column-oriented back substitution) and R Rprev (or R) in FP32.
+constexpr int CG_THREADS = 512;
+
+__global__ void __launch_bounds__(CG_THREADS) chol_df_grouped_kernel(const qlr::CholGroupArgs* __restrict__ args,
+                                                                    int* err) {
+  const qlr::CholGroupArgs& a = args[blockIdx.x];
+  const int l = a.l;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DQ* W = reinterpret_cast<DQ*>(smem_raw);
+  const int ntri = l * (l + 1) / 2;
+  float* rdiag_inv = reinterpret_cast<float*>(W + ntri);   // 1 / r_jj
+  __shared__ float s_trace;
+  __shared__ d32 s_rp;
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = CG_THREADS / 32;
+  auto at = [&](int i, int k) -> DQ& { return W[k * (k + 1) / 2 + i]; };
+  for (int e = t; e < ntri; e += CG_THREADS) {
+    const int2 ik = upper_tri_entry(e);
+    const float4* g = reinterpret_cast<const float4*>(a.G + 8 * ((size_t)ik.y * l + ik.x));
+    W[e].h = g[0];
+    W[e].l = g[1];
+  }
+  __syncthreads();
+  if (a.shift_coef != 0.f) {   // shift s = shift_coef * trace(G) on the diagonal
+    if (warp == 0) {
+      float tr = 0.f;
+      for (int i = lane; i < l; i += 32) tr += at(i, i).h.x;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      if (lane == 0) s_trace = tr;
+    }
+    __syncthreads();
+    const float sh = a.shift_coef * s_trace;
+    for (int i = t; i < l; i += CG_THREADS) {
+      DQ& d = at(i, i);
+      const d32 v = d32_add({d.h.x, d.l.x}, {sh, 0.f});
+      d.h.x = v.h;
+      d.l.x = v.l;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < l; ++j) {
+    if (t == 0) {
+      DQ& dj = at(j, j);
+      d32 d = {dj.h.x, dj.l.x};
+      if (!(d.h > 0.f)) {
+        qlr_set_error(err, QLR_ENOTPD);
+        d = {1e-30f, 0.f};
+      }
+      const d32 rp = d32_rsqrt(d);
+      s_rp = rp;
+      const d32 r = d32_mul(d, rp);
+      dj.h = make_float4(r.h, 0.f, 0.f, 0.f);
+      dj.l = make_float4(r.l, 0.f, 0.f, 0.f);
+      rdiag_inv[j] = 1.f / r.h;
+    }
+    __syncthreads();
+    const d32 rp = s_rp;
+    for (int k = j + 1 + t; k < l; k += CG_THREADS) {   // row j of R
+      DQ& w = at(j, k);
+      d32 v;
+      v = d32_mul({w.h.x, w.l.x}, rp); w.h.x = v.h; w.l.x = v.l;
+      v = d32_mul({w.h.y, w.l.y}, rp); w.h.y = v.h; w.l.y = v.l;
+      v = d32_mul({w.h.z, w.l.z}, rp); w.h.z = v.h; w.l.z = v.l;
+      v = d32_mul({w.h.w, w.l.w}, rp); w.h.w = v.h; w.l.w = v.l;
+    }
+    __syncthreads();
+    const int n = l - j - 1;
+    const int npairs = n * (n + 1) / 2;
+    for (int e = t; e < npairs; e += CG_THREADS) {
+      const int2 ik = upper_tri_entry(e);
+      const int i = j + 1 + ik.x, k = j + 1 + ik.y;
+      dq_fms_conj(at(i, k), at(j, i), at(j, k));
+    }
+    __syncthreads();
+  }
+  const size_t ll = (size_t)l * l;
+  float* Rinv = a.Rinv;
+  if (Rinv) {
+    for (int j = warp; j < l; j += nwarps) {
+      Quat<float> x[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) x[u] = {(lane + 32 * u == j) ? 1.f : 0.f, 0.f, 0.f, 0.f};
+      for (int i = j; i >= 0; --i) {
+        const int src = i & 31, slot = i >> 5;
+        Quat<float> xi = (slot == 0) ? x[0] : (slot == 1 ? x[1] : x[2]);
+        const float ri = rdiag_inv[i];
+        xi.w = __shfl_sync(0xffffffffu, xi.w, src) * ri;
+        xi.x = __shfl_sync(0xffffffffu, xi.x, src) * ri;
+        xi.y = __shfl_sync(0xffffffffu, xi.y, src) * ri;
+        xi.z = __shfl_sync(0xffffffffu, xi.z, src) * ri;
+        if (lane == src) {
+          if (slot == 0) x[0] = xi;
+          else if (slot == 1) x[1] = xi;
+          else x[2] = xi;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int r = lane + 32 * u;
+          if (r < i) {
+            const Quat<float> pr = qmul(q_of(at(r, i).h), xi);
+            x[u].w -= pr.w; x[u].x -= pr.x; x[u].y -= pr.y; x[u].z -= pr.z;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int r = lane + 32 * u;
+        if (r < l) {
+          const bool up = (r <= j);
+          const size_t o = (size_t)j * l + r;
+          Rinv[o] = up ? x[u].w : 0.f;
+          Rinv[ll + o] = up ? x[u].x : 0.f;
+          Rinv[2 * ll + o] = up ? x[u].y : 0.f;
+          Rinv[3 * ll + o] = up ? x[u].z : 0.f;
+        }
+      }
+    }
+  }
+  float* Rout = a.Rout;
+  const float* Rprev = a.Rprev;
+  if (Rout) {
+    for (int e = t; e < (int)ll; e += CG_THREADS) {
+      const int i = e % l, j = e / l;
+      Quat<float> acc = {0.f, 0.f, 0.f, 0.f};
+      if (i <= j) {
+        if (Rprev) {
+          for (int tt = i; tt <= j; ++tt) {
+            const size_t o = (size_t)j * l + tt;
+            const Quat<float> pr = qmul(q_of(at(i, tt).h), Quat<float>{Rprev[o], Rprev[ll + o], Rprev[2 * ll + o], Rprev[3 * ll + o]});
+            acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+          }
+        } else {
+          acc = q_of(at(i, j).h);
+        }
+      }
+      Rout[e] = acc.w; Rout[ll + e] = acc.x; Rout[2 * ll + e] = acc.y; Rout[3 * ll + e] = acc.z;
+    }
+  }
+}
+
 }  // namespace
 
 namespace qlr {
+
+// ---------------------------------------------------------------------------------------
+// grouped steps of batch plans
+
+void gram_grouped_items(int64_t m, int l, int prob, std::vector<int4>& partial, std::vector<int4>& combine) {
+  (void)m;
+  const int nt = (4 * l + WT - 1) / WT;
+  const int ntiles = nt * (nt + 1) / 2;
+  for (int tile = 0; tile < ntiles; ++tile) partial.push_back(make_int4(prob, tile, 0, 0));
+  const int nb = (l * l + 127) / 128;
+  for (int b = 0; b < nb; ++b) combine.push_back(make_int4(prob, b, 0, 0));
+}
+
+int gram_df_grouped(qlr_ctx* ctx, const GramGroupArgs* d_args, const int4* d_partial, int n_partial,
+                    const int4* d_combine, int n_combine) {
+  if (n_partial <= 0) return QLR_OK;
+  KTimer kt(ctx, QLR_KID_GRAM);
+  gram_df_grouped_kernel<<<n_partial, 256, 0, ctx->stream>>>(d_args, d_partial);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  gram_df_combine_grouped_kernel<<<n_combine, 128, 0, ctx->stream>>>(d_args, d_combine);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
+
+size_t chol_df_grouped_smem(int lmax) { return (size_t)lmax * (lmax + 1) / 2 * sizeof(DQ) + (size_t)lmax * 4 + 64; }
+
+int chol_df_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax) {
+  if (count <= 0) return QLR_OK;
+  if (lmax > kBatchMaxL) return QLR_EUNSUPPORTED;
+  const size_t smem = chol_df_grouped_smem(lmax);
+  QLR_CUDA_TRY(cudaFuncSetAttribute(chol_df_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTimer kt(ctx, QLR_KID_CHOL);
+  chol_df_grouped_kernel<<<count, CG_THREADS, smem, ctx->stream>>>(d_args, ctx->d_err);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
 
 static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   const int l = (int)Y.cols;
@@ -1642,7 +1953,7 @@ int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* 
 
 // Q = Y * Rinv (Rinv FP64 small, column-major, l x l)
 static int apply_rinv(qlr_ctx* ctx, const qlr_qmat& Y, const double* Rinv, qlr_qmat& Q, WsArena& ws) {
-  return thin_times_small(ctx, Y, Rinv, (int)Y.cols, (int)Y.cols, Q, ws);
+  return thin_times_small(ctx, Y, Rinv, (int)Y.cols, (int)Y.cols, Q, ws, true);
 }
 
 // Cholesky factor R2 = I + F of a near-identity Gram matrix G and its inverse by series; sets

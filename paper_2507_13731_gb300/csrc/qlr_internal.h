@@ -167,6 +167,7 @@ struct GemmArgs {
   double alpha, beta;
   bool i_contig;      // true when sa_i == 1 (A's row index contiguous in memory)
   bool acc64;         // accumulate in FP64
+  bool b_upper = false;      // B upper triangular: column tile j0 reads K rows [0, j0 + BN) only
   int kid = QLR_KID_APPLY;   // statistics class of the launch
 };
 int gemm_simt(qlr_ctx* ctx, const GemmArgs& g);
@@ -204,6 +205,35 @@ int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Di
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
 
+// Grouped steps of batch plans: one launch runs one step for every problem of a plan, the
+// per-problem arguments and the (problem, tile) items of each launch in device tables built once
+// by the plan.  The small operands are FP32 / double-FP32 (no FP64 instruction on this path).
+constexpr int kBatchMaxL = 80;   // largest l = k + p of a batch plan (one CTA holds its factors)
+//  Gram (orth.cu): W = Yh^T Yh of the plane-stacked Y (m x l, column-major FP32 planes, pitch
+//  ld) as double-FP32 (S, C) pairs, (4l)^2 per problem, then the upper triangle of G = Y^H Y as
+//  double-FP32 quaternions: entry (i, j), i <= j, is 8 floats (high w, x, y, z, low w, x, y, z)
+//  at G + 8 (j l + i).
+struct GramGroupArgs { const float* y[4]; int64_t ld; int64_t m; int l; float2* W; float* G; };
+void gram_grouped_items(int64_t m, int l, int prob, std::vector<int4>& partial, std::vector<int4>& combine);
+int gram_df_grouped(qlr_ctx* ctx, const GramGroupArgs* d_args, const int4* d_partial, int n_partial,
+                    const int4* d_combine, int n_combine);
+//  Cholesky (orth.cu), one CTA per problem: R = chol(G + shift_coef trace(G) I) in double-FP32;
+//  Rinv = R^{-1} and Rout = R Rprev (R when Rprev is null) as FP32 l x l planes (column-major,
+//  zero below the diagonal); either output may be null.
+struct CholGroupArgs { const float* G; const float* Rprev; float* Rout; float* Rinv; int l; float shift_coef; };
+size_t chol_df_grouped_smem(int lmax);
+int chol_df_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax);
+//  Thin x small products (gemm_simt.cu): FP32 GemmArgs (i_contig, no conj), items (problem,
+//  row tile, column tile).
+void gemm_grouped_items(int64_t M, int64_t N, int prob, std::vector<int4>& items);
+int gemm_simt_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems);
+//  Core QSVD (core_svd.cu), one CTA per problem: one-sided Jacobi on R (FP32 l x l planes) with
+//  W and V in shared memory; the k largest sigma in descending order into S, the matching left
+//  vectors into U and right vectors into V (FP32 l x k planes, column-major).
+struct JacobiGroupArgs { const float* R; float* U; float* V; double* S; int l, k; };
+size_t jacobi_grouped_smem(int lmax);
+int jacobi_grouped(qlr_ctx* ctx, const JacobiGroupArgs* d_args, int count, int lmax);
+
 // core QSVD (core_svd.cu)
 int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S, double* Rt, int prec,
               WsArena& ws);
@@ -222,7 +252,9 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
 // utilities (util.cu)
 int convert_qmat(qlr_ctx* ctx, const qlr_qmat& src, qlr_qmat& dst);  // elementwise dtype change
 // C (rows x k) = T (rows x l, column-major) * S (FP64 l x k, column-major planes) (thin.cu)
-int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws);
+// S_upper: S is upper triangular (R^{-1}), so the product skips its zero rows.
+int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws,
+                     bool S_upper = false);
 int zero_qmat(qlr_ctx* ctx, qlr_qmat& dst);
 int small_to_qmat(qlr_ctx* ctx, const double* S, int l, int k, qlr_qmat& dst);  // l x k FP64 small -> qmat
 

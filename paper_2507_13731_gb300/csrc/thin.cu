@@ -16,7 +16,8 @@ __global__ void small_to_f32_kernel(const double* __restrict__ S, float* __restr
 }
 }  // namespace
 
-int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws) {
+int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws,
+                     bool S_upper) {
   // FP32 products: the small factor goes to FP32 once (every CTA of the GEMM would otherwise
   // convert its FP64 tile of S again, on the slow FP64 pipe)
   const bool f32 = (T.dtype != QLR_F64 && C.dtype != QLR_F64);
@@ -43,6 +44,7 @@ int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, in
   g.M = T.rows; g.N = k; g.K = l;
   g.alpha = 1.0; g.beta = 0.0;
   g.acc64 = (T.dtype == QLR_F64 || C.dtype == QLR_F64);
+  g.b_upper = S_upper;
   const int rc = gemm_simt(ctx, g);
   ws.off = mark;
   return rc;
