@@ -143,11 +143,11 @@ int enqueue(qlr_batch* b) {
     for (const StepTables& st : b->steps[i - 1]) {
       QLR_TRY(qlr::gram_df_grouped(mc, st.gram, b->gram_items[par], b->n_gram[par], b->comb_items[par], b->n_comb[par]));
       QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
-      QLR_TRY(qlr::gemm_simt_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
+      QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
   }
   QLR_TRY(qlr::jacobi_grouped(mc, b->jac, b->count, b->lmax));
-  QLR_TRY(qlr::gemm_simt_grouped(mc, b->lift, b->lift_items, b->n_lift));
+  QLR_TRY(qlr::thin_small_grouped(mc, b->lift, b->lift_items, b->n_lift));
   int64_t n = 0;
   for (int kk = 0; kk < QLR_KID_COUNT; ++kk) n += mc->launches[kk];
   b->launches_per_run = n;
@@ -261,7 +261,7 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
       const qlr_batch::Prob& P = b->pr[j];
       const int64_t rows = par == 0 ? P.A.rows : P.A.cols;
       gram_grouped_items(rows, P.l, j, gi, ci);
-      gemm_grouped_items(rows, P.l, j, ai);
+      thin_small_items(rows, P.l, j, ai);
     }
     b->n_gram[par] = (int)gi.size();
     b->n_comb[par] = (int)ci.size();
@@ -327,9 +327,9 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     const float* Vhat = (passes % 2 == 0) ? P.Uh : P.Vh;
     la[j] = thin_small_args(P.Q1, Uhat, P.l, P.k, P.U);
     la[count + j] = thin_small_args(P.Q2, Vhat, P.l, P.k, P.V);
-    gemm_grouped_items(P.A.rows, P.k, j, li);
+    thin_small_items(P.A.rows, P.k, j, li);
   }
-  for (int j = 0; j < count; ++j) gemm_grouped_items(b->pr[j].A.cols, b->pr[j].k, count + j, li);
+  for (int j = 0; j < count; ++j) thin_small_items(b->pr[j].A.cols, b->pr[j].k, count + j, li);
   b->n_lift = (int)li.size();
   tb.add(ja);
   tb.add(la);

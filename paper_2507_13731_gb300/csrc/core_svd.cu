@@ -148,24 +148,19 @@ __device__ int jacobi_sweeps(T* W, T* Vs, int l, int max_sweeps, T tol, T* rlog,
   return sweep;
 }
 
-// Vout != nullptr (W in shared memory and room for V next to it): the rotations are applied to
-// V = I in place as well, and neither the log nor the replay is needed.
+// One CTA: W = R (in shared memory when it fits), the rotations logged for the replay on V.
 template <class T>
 __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R, int l, T* __restrict__ Wout,
                                                      bool w_smem, int max_sweeps, T tol, T* __restrict__ sig_out,
-                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err,
-                                                     T* __restrict__ Vout) {
+                                                     int* __restrict__ sweeps_out, T* __restrict__ rlog, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
   const size_t ll = (size_t)l * l;
-  T* Vs = Vout ? reinterpret_cast<T*>(smem_raw) + 4 * ll : nullptr;
   for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
-  if (Vs)
-    for (size_t e = t; e < 4 * ll; e += JT) Vs[e] = (e < ll && e % (l + 1) == 0) ? (T)1 : (T)0;
   __syncthreads();
   bool converged = false;
-  const int sweep = jacobi_sweeps<T>(W, Vs, l, max_sweeps, tol, rlog, &converged);
+  const int sweep = jacobi_sweeps<T>(W, (T*)nullptr, l, max_sweeps, tol, rlog, &converged);
   if (t == 0) {
     *sweeps_out = sweep;
     if (!converged) qlr_set_error(err, QLR_ENOCONV);
@@ -185,8 +180,6 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
   __syncthreads();
   if (w_smem)
     for (size_t e = t; e < 4 * ll; e += JT) Wout[e] = W[e];
-  if (Vs)
-    for (size_t e = t; e < 4 * ll; e += JT) Vout[e] = Vs[e];
 }
 
 template <class T>
@@ -664,8 +657,7 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   if (!ws.ok) return QLR_ENOMEM;
   const T eps = (sizeof(T) == 4) ? (T)5.9604645e-08 : (T)1.1102230246251565e-16;
   const T tol = (T)8 * eps * (T)sqrt((double)l);   // above the rounding noise of the dot products
-  // many concurrent small problems: one CTA each (the cluster form spends 8 SMs on one problem)
-  const bool blockj = use_block_jacobi(l, sizeof(T)) && !(ctx->small_mode && ll4 * sizeof(T) <= 220 * 1024);
+  const bool blockj = use_block_jacobi(l, sizeof(T));
   if (blockj) {
     const int bw = (l + 2 * JP - 1) / (2 * JP);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
@@ -701,19 +693,16 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   } else {
     const size_t one = ll4 * sizeof(T);
     const bool w_smem = one <= 220 * 1024;
-    // many concurrent small problems: V accumulated in place (no log, no replay launch)
-    const bool vin = ctx->small_mode && 2 * one <= 220 * 1024;
-    const size_t smem = vin ? 2 * one : (w_smem ? one : 0);
+    const size_t smem = w_smem ? one : 0;
     if (smem > 0)
       QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
-      jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err,
-                                                     vin ? V : nullptr);
+      jacobi_kernel<T><<<1, JT, smem, ctx->stream>>>(R, l, W, w_smem, JMAX_SWEEPS, tol, sig, sweeps, rlog, ctx->d_err);
       qlr_count_launch();
     }
     QLR_CUDA_TRY(cudaGetLastError());
-    if (!vin) {
+    {
       KTimer kt(ctx, QLR_KID_JACOBI);
       const size_t rs = (size_t)4 * 4 * l * sizeof(T);
       // static shared memory comes on top of the dynamic size: always opt in

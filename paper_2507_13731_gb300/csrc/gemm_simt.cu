@@ -136,13 +136,6 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(qlr::GemmArgs g) {
   gemm_simt_tile<TAcc, I_CONTIG, CONJ>(g, blockIdx.x, blockIdx.y);
 }
 
-// Many independent products in one launch (batch plans): item (problem, row tile, column tile).
-__global__ void __launch_bounds__(NT) gemm_simt_grouped_kernel(const qlr::GemmArgs* __restrict__ args,
-                                                                const int4* __restrict__ items) {
-  const int4 it = items[blockIdx.x];
-  gemm_simt_tile<float, true, false>(args[it.x], it.y, it.z);
-}
-
 template <class TAcc>
 void launch(const qlr::GemmArgs& g, cudaStream_t s) {
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN));
@@ -159,20 +152,6 @@ void launch(const qlr::GemmArgs& g, cudaStream_t s) {
 }  // namespace
 
 namespace qlr {
-void gemm_grouped_items(int64_t M, int64_t N, int prob, std::vector<int4>& items) {
-  for (int64_t by = 0; by < (N + BN - 1) / BN; ++by)
-    for (int64_t bx = 0; bx < (M + BM - 1) / BM; ++bx) items.push_back(make_int4(prob, (int)bx, (int)by, 0));
-}
-
-int gemm_simt_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems) {
-  if (nitems <= 0) return QLR_OK;
-  KTimer kt(ctx, QLR_KID_APPLY);
-  gemm_simt_grouped_kernel<<<nitems, NT, 0, ctx->stream>>>(d_args, d_items);
-  qlr_count_launch();
-  QLR_CUDA_TRY(cudaGetLastError());
-  return QLR_OK;
-}
-
 int gemm_simt(qlr_ctx* ctx, const GemmArgs& g) {
   if (g.M == 0 || g.N == 0) return QLR_OK;
   if (g.N > 65535LL * BN || g.M > (int64_t)INT32_MAX * BM) return QLR_EUNSUPPORTED;

@@ -720,136 +720,6 @@ __global__ void __launch_bounds__(CC_THREADS, 1) chol_cluster_kernel(const doubl
 }
 
 // ---------------------------------------------------------------------------------------
-// Whole Cholesky factorisation of a small Gram (l <= CS_MAX_L) in one CTA, for many concurrent
-// small problems: the upper triangle packed by columns in shared memory (column k at offset
-// k (k + 1) / 2, rows 0..k, plane-interleaved), right-looking with the rank-1 updates' (row,
-// column) pairs enumerated densely over all threads.  Then either the CB x CB diagonal-block
-// inverses (for the blocked triangular inverse) or, with Rinv != nullptr (l <= CS_INV_MAX_L), the
-// whole inverse by column-oriented back substitution in a second packed triangle.
-constexpr int CS_THREADS = 512;
-constexpr int CS_MAX_L = 96;
-constexpr int CS_INV_MAX_L = 80;
-
-__global__ void __launch_bounds__(CS_THREADS, 1) chol_single_kernel(const double* __restrict__ G, double* __restrict__ R,
-                                                                    double* __restrict__ Dinv_all, int l,
-                                                                    double shift_coef, int* err, const int* run_if,
-                                                                    double* __restrict__ Rinv) {
-  if (run_if && *run_if == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double4* W = reinterpret_cast<double4*>(smem_raw);
-  double* rpv_all = reinterpret_cast<double*>(W + l * (l + 1) / 2);     // 1 / r_jj, l values
-  double4* Xp = reinterpret_cast<double4*>(rpv_all + ((l + 3) / 4) * 4);  // packed inverse (Rinv only)
-  __shared__ double s_shift, s_rp;
-  const int t = threadIdx.x, lane = t % 32, warp = t / 32;
-  const size_t ll = (size_t)l * l;
-  auto at = [&](int i, int k) -> double4& { return W[k * (k + 1) / 2 + i]; };
-  if (warp == 0) {
-    double tr = 0.0;
-    for (int i = lane; i < l; i += 32) tr += G[(size_t)i * l + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    if (lane == 0) s_shift = shift_coef * tr;
-  }
-  __syncthreads();
-  const int ntri = l * (l + 1) / 2;
-  for (int e = t; e < ntri; e += CS_THREADS) {
-    const int2 ik = upper_tri_entry(e);
-    const size_t o = (size_t)ik.y * l + ik.x;
-    double4 q = make_double4(G[o], G[ll + o], G[2 * ll + o], G[3 * ll + o]);
-    if (ik.x == ik.y) q.x += s_shift;
-    W[e] = q;
-  }
-  __syncthreads();
-  for (int j = 0; j < l; ++j) {
-    if (t == 0) {
-      double d = at(j, j).x;
-      if (!(d > 0.0)) {
-        qlr_set_error(err, QLR_ENOTPD);
-        d = 1e-300;
-      }
-      const double rp = rsqrt_newton(d);
-      s_rp = rp;
-      rpv_all[j] = rp;
-      at(j, j) = make_double4(d * rp, 0.0, 0.0, 0.0);
-    }
-    __syncthreads();
-    const double rp = s_rp;
-    for (int k = j + 1 + t; k < l; k += CS_THREADS) {   // row j of R
-      double4& w = at(j, k);
-      w = make_double4(w.x * rp, w.y * rp, w.z * rp, w.w * rp);
-    }
-    __syncthreads();
-    const int n = l - j - 1;
-    const int npairs = n * (n + 1) / 2;
-    for (int e = t; e < npairs; e += CS_THREADS) {
-      const int2 ik = upper_tri_entry(e);
-      const int i = j + 1 + ik.x, k = j + 1 + ik.y;
-      double4& w = at(i, k);
-      w = qcfms(w, at(j, i), at(j, k));
-    }
-    __syncthreads();
-  }
-  for (int e = t; e < (int)ll; e += CS_THREADS) {
-    const int i = e % l, k = e / l;
-    const double4 r = (i <= k) ? at(i, k) : make_double4(0.0, 0.0, 0.0, 0.0);
-    R[e] = r.x; R[ll + e] = r.y; R[2 * ll + e] = r.z; R[3 * ll + e] = r.w;
-  }
-  if (Rinv) {
-    // X = R^{-1}: for i = l-1 .. 0, X[i, i:] = Y[i, i:] / r_ii, then Y[0:i, i:] -= R[0:i, i] X[i, i:]
-    // (Y starts as the identity; row i of X is zero left of the diagonal)
-    auto xt = [&](int i, int k) -> double4& { return Xp[k * (k + 1) / 2 + i]; };
-    for (int e = t; e < ntri; e += CS_THREADS) {
-      const int2 ik = upper_tri_entry(e);
-      Xp[e] = make_double4(ik.x == ik.y ? 1.0 : 0.0, 0.0, 0.0, 0.0);
-    }
-    __syncthreads();
-    for (int i = l - 1; i >= 0; --i) {
-      const int w = l - i;
-      const double rp = rpv_all[i];
-      for (int e = t; e < w; e += CS_THREADS) {
-        double4& x = xt(i, i + e);
-        x = make_double4(x.x * rp, x.y * rp, x.z * rp, x.w * rp);
-      }
-      __syncthreads();
-      for (int e = t; e < i * w; e += CS_THREADS) {   // rows r < i, columns j >= i
-        const int r = e % i, j = i + e / i;
-        const double4 a = at(r, i), b = xt(i, j);
-        const Quat<double> pr = qmul(Quat<double>{a.x, a.y, a.z, a.w}, Quat<double>{b.x, b.y, b.z, b.w});
-        double4& x = xt(r, j);
-        x.x -= pr.w; x.y -= pr.x; x.z -= pr.y; x.w -= pr.z;
-      }
-      __syncthreads();
-    }
-    for (int e = t; e < (int)ll; e += CS_THREADS) {
-      const int i = e % l, k = e / l;
-      const double4 r = (i <= k) ? xt(i, k) : make_double4(0.0, 0.0, 0.0, 0.0);
-      Rinv[e] = r.x; Rinv[ll + e] = r.y; Rinv[2 * ll + e] = r.z; Rinv[3 * ll + e] = r.w;
-    }
-    return;
-  }
-  __shared__ double D[4][CB][CB];
-  __shared__ double X[4][CB][CB];
-  __shared__ double rpv[CB];
-  const int nblk = (l + CB - 1) / CB;
-  for (int J = 0; J < nblk; ++J) {
-    const int j0 = J * CB, b = min(CB, l - j0);
-    for (int e = t; e < CB * CB; e += blockDim.x) {
-      const int i = e % CB, jj = e / CB;
-      const double4 q = (i < b && jj < b && i <= jj) ? at(j0 + i, j0 + jj) : make_double4(0.0, 0.0, 0.0, 0.0);
-      D[0][i][jj] = q.x; D[1][i][jj] = q.y; D[2][i][jj] = q.z; D[3][i][jj] = q.w;
-    }
-    __syncthreads();
-    cc_block_inverse(D, X, rpv, b);
-    double* Dinv = Dinv_all + (size_t)J * 4 * CB * CB;
-    for (int e = t; e < b * b; e += blockDim.x) {
-      const int i = e % b, jj = e / b;
-      for (int cp = 0; cp < 4; ++cp) Dinv[(size_t)cp * b * b + (size_t)jj * b + i] = (i <= jj) ? X[cp][i][jj] : 0.0;
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // The same cluster Cholesky in double-FP32 arithmetic (an unevaluated sum hi + lo of two floats,
 // about 48 significant bits), for Grams of FP32 sketches, which the Gram kernel already forms in
 // double-FP32: the factorisation then matches the Gram's precision, while every step runs on the
@@ -1850,16 +1720,6 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
          const int* run_if, bool df) {
   if (l == 0) return QLR_OK;
   const size_t ll4 = (size_t)4 * l * l;
-  if (ctx->small_mode && l <= CS_MAX_L && Dinv_all != nullptr) {
-    const size_t smem = (size_t)l * (l + 1) / 2 * 32 + (size_t)(l + 3) / 4 * 32;   // + 16.5 KB static: opt in
-    QLR_CUDA_TRY(cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    KTimer kt(ctx, QLR_KID_CHOL);
-    chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, Dinv_all, l, shift_coef, ctx->d_err, run_if,
-                                                             nullptr);
-    qlr_count_launch();
-    QLR_CUDA_TRY(cudaGetLastError());
-    return QLR_OK;
-  }
   const int nc = (l > CB) ? cluster_chol_size(ctx->device, l) : 0;
   if (nc > 0 && Dinv_all != nullptr) {
     cudaLaunchConfig_t cfg = {};
@@ -1908,18 +1768,6 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
     QLR_CUDA_TRY(cudaGetLastError());
   }
   ws.off = mark;
-  return QLR_OK;
-}
-
-// Small problems in throughput mode: factor and invert in one single-CTA launch.
-static int chol_inv_small(qlr_ctx* ctx, int l, const double* G, double* R, double* Rinv, double shift_coef) {
-  const size_t tri = (size_t)l * (l + 1) / 2 * 32;
-  const size_t smem = 2 * tri + (size_t)(l + 3) / 4 * 32;   // + 16.5 KB static: opt in
-  QLR_CUDA_TRY(cudaFuncSetAttribute(chol_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  KTimer kt(ctx, QLR_KID_CHOL);
-  chol_single_kernel<<<1, CS_THREADS, smem, ctx->stream>>>(G, R, nullptr, l, shift_coef, ctx->d_err, nullptr, Rinv);
-  qlr_count_launch();
-  QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
 
@@ -2045,9 +1893,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     qlr_qmat& dst = const_cast<qlr_qmat&>(*seq[s + 1]);
     double* Rcur = (s == 0) ? Rprod : Rs;
     QLR_TRY(gram(ctx, src, G, ws));
-    if (ctx->small_mode && l <= CS_INV_MAX_L) {
-      QLR_TRY(chol_inv_small(ctx, l, G, Rcur, Rinv, (s == 0) ? shift : 0.0));
-    } else if (s == 1 && orth == QLR_ORTH_CHOLQR2 && !(ctx->small_mode && l <= CS_MAX_L)) {
+    if (s == 1 && orth == QLR_ORTH_CHOLQR2) {
       int* use_chol = nullptr;
       QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol));
       QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol, df));     // only if the series test failed

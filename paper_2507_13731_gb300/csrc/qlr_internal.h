@@ -17,9 +17,6 @@ struct qlr_ctx {
   void* ws = nullptr;            // workspace
   size_t ws_bytes = 0;
   int num_sms = 0;
-  // Throughput mode for many concurrent small problems (batch lanes): small factorisations run in
-  // one CTA each instead of spreading one problem over a cluster of SMs.
-  bool small_mode = false;
   // launch statistics
   int64_t launches[QLR_KID_COUNT] = {};
   double ms[QLR_KID_COUNT] = {};
@@ -223,10 +220,10 @@ int gram_df_grouped(qlr_ctx* ctx, const GramGroupArgs* d_args, const int4* d_par
 struct CholGroupArgs { const float* G; const float* Rprev; float* Rout; float* Rinv; int l; float shift_coef; };
 size_t chol_df_grouped_smem(int lmax);
 int chol_df_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax);
-//  Thin x small products (gemm_simt.cu): FP32 GemmArgs (i_contig, no conj), items (problem,
-//  row tile, column tile).
-void gemm_grouped_items(int64_t M, int64_t N, int prob, std::vector<int4>& items);
-int gemm_simt_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems);
+//  Thin x small products (thin.cu): FP32 GemmArgs (A column-major, sa_i == 1, 4 planes; B FP32
+//  column-major; no conj, alpha 1, beta 0), items (problem, row block, column chunk).
+void thin_small_items(int64_t M, int64_t N, int prob, std::vector<int4>& items);
+int thin_small_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems);
 //  Core QSVD (core_svd.cu), one CTA per problem: one-sided Jacobi on R (FP32 l x l planes) with
 //  W and V in shared memory; the k largest sigma in descending order into S, the matching left
 //  vectors into U and right vectors into V (FP32 l x k planes, column-major).

@@ -1,8 +1,9 @@
 // Thin x small products C = T S: T (rows x l) a tall quaternion basis stored column-major, S a
-// small FP64 l x k factor (R^{-1} of a CholeskyQR step, or the core QSVD's singular vectors for
-// the lifts U = Q1 U_hat, V = Q2 V_hat), on the SIMT kernel (FP32, FP64 for FP64 operands).  The
-// tensor-core sketch kernel was measured on this shape (4096 x 110 x 110) and gained nothing:
-// with K = l its CTAs run a dozen pipeline stages each and the 3xTF32 split costs three MMAs.
+// small l x k factor (R^{-1} of a CholeskyQR step, or the core QSVD's singular vectors for the
+// lifts U = Q1 U_hat, V = Q2 V_hat).  FP32 operands run on thin_small_kernel; FP64 operands on
+// the generic SIMT GEMM.  The tensor-core sketch kernel was measured on this shape (4096 x 110 x
+// 110) and gained nothing: with K = l its CTAs run a dozen pipeline stages each and the 3xTF32
+// split costs three MMAs.
 #include <algorithm>
 
 #include "qlr_internal.h"
@@ -14,7 +15,98 @@ __global__ void small_to_f32_kernel(const double* __restrict__ S, float* __restr
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (float)S[e];
 }
+
+// FP32 thin x small product, one row of C per thread: a CTA takes TS_ROWS rows and TS_COLS
+// columns of C, stages S's rows for those columns in shared memory (TS_KC rows at a time, each
+// entry a quaternion broadcast to every thread), and streams T's rows k (four coalesced loads
+// per k) into TS_COLS quaternion accumulators.  With an upper-triangular S (R^{-1}) rows k >=
+// j0 + TS_COLS of the chunk are zero and skipped.
+constexpr int TS_ROWS = 128, TS_COLS = 16, TS_KC = 64;
+
+__device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, int cc) {
+  __shared__ float4 Bs[TS_KC][TS_COLS];
+  const int t = threadIdx.x;
+  const int j0 = cc * TS_COLS;
+  const int N = (int)g.N, K = (int)g.K;
+  const int ncol = min(TS_COLS, N - j0);
+  const int kend = g.b_upper ? min(K, j0 + TS_COLS) : K;
+  const int64_t i = rb * TS_ROWS + t;
+  const bool row_ok = i < g.M;
+  const int64_t lda = g.sa_k, ldb = g.ldb;
+  const float* a0 = static_cast<const float*>(g.a[0]) + i;
+  const float* a1 = static_cast<const float*>(g.a[1]) + i;
+  const float* a2 = static_cast<const float*>(g.a[2]) + i;
+  const float* a3 = static_cast<const float*>(g.a[3]) + i;
+  const float* b0 = static_cast<const float*>(g.b[0]);
+  const float* b1 = static_cast<const float*>(g.b[1]);
+  const float* b2 = static_cast<const float*>(g.b[2]);
+  const float* b3 = static_cast<const float*>(g.b[3]);
+  Quat<float> acc[TS_COLS];
+#pragma unroll
+  for (int jj = 0; jj < TS_COLS; ++jj) acc[jj] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < kend; k0 += TS_KC) {
+    const int kn = min(TS_KC, kend - k0);
+    __syncthreads();
+    for (int e = t; e < kn * TS_COLS; e += TS_ROWS) {
+      const int kk = e % kn, jj = e / kn;   // consecutive threads: consecutive rows of one column
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jj < ncol) {
+        const int64_t o = (int64_t)(k0 + kk) + (int64_t)(j0 + jj) * ldb;
+        v = make_float4(b0[o], b1[o], b2[o], b3[o]);
+      }
+      Bs[kk][jj] = v;
+    }
+    __syncthreads();
+    if (row_ok) {
+#pragma unroll 2
+      for (int kk = 0; kk < kn; ++kk) {
+        const int64_t o = (int64_t)(k0 + kk) * lda;
+        const Quat<float> a = {a0[o], a1[o], a2[o], a3[o]};
+#pragma unroll
+        for (int jj = 0; jj < TS_COLS; ++jj) {
+          const float4 b = Bs[kk][jj];
+          const Quat<float> p = qmul(a, Quat<float>{b.x, b.y, b.z, b.w});
+          acc[jj].w += p.w; acc[jj].x += p.x; acc[jj].y += p.y; acc[jj].z += p.z;
+        }
+      }
+    }
+  }
+  if (!row_ok) return;
+  float* c0 = static_cast<float*>(g.c[0]) + i;
+  float* c1 = static_cast<float*>(g.c[1]) + i;
+  float* c2 = static_cast<float*>(g.c[2]) + i;
+  float* c3 = static_cast<float*>(g.c[3]) + i;
+#pragma unroll
+  for (int jj = 0; jj < TS_COLS; ++jj)
+    if (jj < ncol) {
+      const int64_t o = (int64_t)(j0 + jj) * g.ldc;
+      c0[o] = acc[jj].w; c1[o] = acc[jj].x; c2[o] = acc[jj].y; c3[o] = acc[jj].z;
+    }
+}
+
+__global__ void __launch_bounds__(TS_ROWS) thin_small_kernel(GemmArgs g) { thin_small_tile(g, blockIdx.x, blockIdx.y); }
+
+// Many independent products in one launch (batch plans): item (problem, row block, column chunk).
+__global__ void __launch_bounds__(TS_ROWS) thin_small_grouped_kernel(const GemmArgs* __restrict__ args,
+                                                                    const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  thin_small_tile(args[it.x], it.y, it.z);
+}
 }  // namespace
+
+void thin_small_items(int64_t M, int64_t N, int prob, std::vector<int4>& items) {
+  for (int64_t c = 0; c < (N + TS_COLS - 1) / TS_COLS; ++c)
+    for (int64_t r = 0; r < (M + TS_ROWS - 1) / TS_ROWS; ++r) items.push_back(make_int4(prob, (int)r, (int)c, 0));
+}
+
+int thin_small_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems) {
+  if (nitems <= 0) return QLR_OK;
+  KTimer kt(ctx, QLR_KID_APPLY);
+  thin_small_grouped_kernel<<<nitems, TS_ROWS, 0, ctx->stream>>>(d_args, d_items);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
 
 int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, int k, qlr_qmat& C, WsArena& ws,
                      bool S_upper) {
@@ -45,7 +137,16 @@ int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, in
   g.alpha = 1.0; g.beta = 0.0;
   g.acc64 = (T.dtype == QLR_F64 || C.dtype == QLR_F64);
   g.b_upper = S_upper;
-  const int rc = gemm_simt(ctx, g);
+  int rc = QLR_OK;
+  if (f32 && T.dtype == QLR_F32 && C.dtype == QLR_F32 && T.plane[0] != nullptr && T.rows > 0 && k > 0) {
+    KTimer kt(ctx, g.kid);
+    const dim3 grid((unsigned)((T.rows + TS_ROWS - 1) / TS_ROWS), (unsigned)((k + TS_COLS - 1) / TS_COLS));
+    thin_small_kernel<<<grid, TS_ROWS, 0, ctx->stream>>>(g);
+    qlr_count_launch();
+    rc = (cudaGetLastError() == cudaSuccess) ? QLR_OK : QLR_ECUDA;
+  } else {
+    rc = gemm_simt(ctx, g);
+  }
   ws.off = mark;
   return rc;
 }
