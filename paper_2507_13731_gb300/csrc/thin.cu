@@ -16,20 +16,22 @@ __global__ void small_to_f32_kernel(const double* __restrict__ S, float* __restr
     out[e] = (float)S[e];
 }
 
-// FP32 thin x small product, one row of C per thread: a CTA takes TS_ROWS rows and TS_COLS
-// columns of C, stages S's rows for those columns in shared memory (TS_KC rows at a time, each
-// entry a quaternion broadcast to every thread), and streams T's rows k (four coalesced loads
-// per k) into TS_COLS quaternion accumulators.  With an upper-triangular S (R^{-1}) rows k >=
-// j0 + TS_COLS of the chunk are zero and skipped.
-constexpr int TS_ROWS = 128, TS_COLS = 16, TS_KC = 64;
+// FP32 thin x small product, one row of C per thread: a CTA takes TS_ROWS rows and COLS columns
+// of C, stages S's rows for those columns in shared memory (TS_KC rows at a time, each entry a
+// quaternion broadcast to every thread), and streams T's rows k (four coalesced loads per k) into
+// COLS quaternion accumulators.  With an upper-triangular S (R^{-1}) rows k >= j0 + COLS of the
+// chunk are zero and skipped.  Batches use 16 columns per CTA (many problems fill the GPU); a
+// single product uses 8, for twice the CTAs.
+constexpr int TS_ROWS = 128, TS_COLS = 16, TS_COLS1 = 8, TS_KC = 64;
 
+template <int COLS>
 __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, int cc) {
-  __shared__ float4 Bs[TS_KC][TS_COLS];
+  __shared__ float4 Bs[TS_KC][COLS];
   const int t = threadIdx.x;
-  const int j0 = cc * TS_COLS;
+  const int j0 = cc * COLS;
   const int N = (int)g.N, K = (int)g.K;
-  const int ncol = min(TS_COLS, N - j0);
-  const int kend = g.b_upper ? min(K, j0 + TS_COLS) : K;
+  const int ncol = min(COLS, N - j0);
+  const int kend = g.b_upper ? min(K, j0 + COLS) : K;
   const int64_t i = rb * TS_ROWS + t;
   const bool row_ok = i < g.M;
   const int64_t lda = g.sa_k, ldb = g.ldb;
@@ -41,13 +43,13 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
   const float* b1 = static_cast<const float*>(g.b[1]);
   const float* b2 = static_cast<const float*>(g.b[2]);
   const float* b3 = static_cast<const float*>(g.b[3]);
-  Quat<float> acc[TS_COLS];
+  Quat<float> acc[COLS];
 #pragma unroll
-  for (int jj = 0; jj < TS_COLS; ++jj) acc[jj] = {0.f, 0.f, 0.f, 0.f};
+  for (int jj = 0; jj < COLS; ++jj) acc[jj] = {0.f, 0.f, 0.f, 0.f};
   for (int k0 = 0; k0 < kend; k0 += TS_KC) {
     const int kn = min(TS_KC, kend - k0);
     __syncthreads();
-    for (int e = t; e < kn * TS_COLS; e += TS_ROWS) {
+    for (int e = t; e < kn * COLS; e += TS_ROWS) {
       const int kk = e % kn, jj = e / kn;   // consecutive threads: consecutive rows of one column
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (jj < ncol) {
@@ -63,7 +65,7 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
         const int64_t o = (int64_t)(k0 + kk) * lda;
         const Quat<float> a = {a0[o], a1[o], a2[o], a3[o]};
 #pragma unroll
-        for (int jj = 0; jj < TS_COLS; ++jj) {
+        for (int jj = 0; jj < COLS; ++jj) {
           const float4 b = Bs[kk][jj];
           const Quat<float> p = qmul(a, Quat<float>{b.x, b.y, b.z, b.w});
           acc[jj].w += p.w; acc[jj].x += p.x; acc[jj].y += p.y; acc[jj].z += p.z;
@@ -77,20 +79,22 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
   float* c2 = static_cast<float*>(g.c[2]) + i;
   float* c3 = static_cast<float*>(g.c[3]) + i;
 #pragma unroll
-  for (int jj = 0; jj < TS_COLS; ++jj)
+  for (int jj = 0; jj < COLS; ++jj)
     if (jj < ncol) {
       const int64_t o = (int64_t)(j0 + jj) * g.ldc;
       c0[o] = acc[jj].w; c1[o] = acc[jj].x; c2[o] = acc[jj].y; c3[o] = acc[jj].z;
     }
 }
 
-__global__ void __launch_bounds__(TS_ROWS) thin_small_kernel(GemmArgs g) { thin_small_tile(g, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(TS_ROWS) thin_small_kernel(GemmArgs g) {
+  thin_small_tile<TS_COLS1>(g, blockIdx.x, blockIdx.y);
+}
 
 // Many independent products in one launch (batch plans): item (problem, row block, column chunk).
 __global__ void __launch_bounds__(TS_ROWS) thin_small_grouped_kernel(const GemmArgs* __restrict__ args,
                                                                     const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
-  thin_small_tile(args[it.x], it.y, it.z);
+  thin_small_tile<TS_COLS>(args[it.x], it.y, it.z);
 }
 }  // namespace
 
@@ -140,7 +144,7 @@ int thin_times_small(qlr_ctx* ctx, const qlr_qmat& T, const double* S, int l, in
   int rc = QLR_OK;
   if (f32 && T.dtype == QLR_F32 && C.dtype == QLR_F32 && T.plane[0] != nullptr && T.rows > 0 && k > 0) {
     KTimer kt(ctx, g.kid);
-    const dim3 grid((unsigned)((T.rows + TS_ROWS - 1) / TS_ROWS), (unsigned)((k + TS_COLS - 1) / TS_COLS));
+    const dim3 grid((unsigned)((T.rows + TS_ROWS - 1) / TS_ROWS), (unsigned)((k + TS_COLS1 - 1) / TS_COLS1));
     thin_small_kernel<<<grid, TS_ROWS, 0, ctx->stream>>>(g);
     qlr_count_launch();
     rc = (cudaGetLastError() == cudaSuccess) ? QLR_OK : QLR_ECUDA;
