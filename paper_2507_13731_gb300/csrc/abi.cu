@@ -14,15 +14,16 @@
 #include "qlr_internal.h"
 
 namespace qlr {
-size_t gram_ws_bound(int64_t l) {
+size_t gram_ws_bound(int64_t rows, int64_t l) {
   size_t per = (size_t)32 * l * l;
   size_t cap = std::max<size_t>(per, (size_t)64 << 20);
-  return cap + (size_t)8 * ((l + 31) / 32) * ((l + 31) / 32) + 4096;
+  const size_t tc = (l <= 1024) ? gram_tc_ws(rows, (int)l) : 0;
+  return std::max(cap, tc) + (size_t)8 * ((l + 31) / 32) * ((l + 31) / 32) + 4096;
 }
 
 size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
   return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * (rows + 4) * l * esz + (size_t)16 * l * l +
-         gram_ws_bound(l) + 16 * 256;
+         gram_ws_bound(rows, l) + 16 * 256;
 }
 
 size_t tsvd_ws_bound(int64_t l) { return core_tsvd_ws((int)l) + 16384; }
@@ -450,7 +451,7 @@ int qlr_qgram(qlr_ctx* ctx, const qlr_qmat* Y, double* G) {
   QLR_TRY(check_qmat(Y, QLR_COL_MAJOR, false));
   if (Y->dtype == QLR_BF16) return QLR_EINVAL;
   DeviceGuard g(ctx->device);
-  QLR_TRY(qlr_ensure_ws(ctx, gram_ws_bound(Y->cols)));
+  QLR_TRY(qlr_ensure_ws(ctx, gram_ws_bound(Y->rows, Y->cols)));
   WsArena ws(ctx->ws, ctx->ws_bytes);
   return qlr::gram(ctx, *Y, G, ws);
 }

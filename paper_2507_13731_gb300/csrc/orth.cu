@@ -1630,7 +1630,11 @@ static int gram_df32(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
 }
 
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
-  if (Y.dtype == QLR_F32 && Y.cols > 0 && Y.rows > 0) return gram_df32(ctx, Y, G, ws);
+  if (Y.dtype == QLR_F32 && Y.cols > 0 && Y.rows > 0) {
+    // tensor cores when the workspace holds the slices, else the double-FP32 SIMT Gram
+    if (gram_tc_supported(Y) && ws.cap - ws.off >= gram_tc_ws(Y.rows, (int)Y.cols)) return gram_tc(ctx, Y, G, ws);
+    return gram_df32(ctx, Y, G, ws);
+  }
   const int l = (int)Y.cols;
   const int64_t m = Y.rows;
   if (l == 0) return QLR_OK;

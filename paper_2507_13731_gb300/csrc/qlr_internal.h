@@ -195,6 +195,10 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs);
 
 // orthonormalisation pieces (orth.cu)
 int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
+// FP64-class Gram of FP32 Y on the tensor cores by exact BF16 slicing (gram_tc.cu); G FP64 planes.
+size_t gram_tc_ws(int64_t m, int l);
+bool gram_tc_supported(const qlr_qmat& Y);
+int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
          const int* run_if = nullptr, bool df = false);
 int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr,
@@ -237,7 +241,7 @@ int core_tsvd(qlr_ctx* ctx, int l, const double* R, int k, double* L, double* S,
 size_t core_tsvd_ws(int l);
 
 // workspace bounds (abi.cu)
-size_t gram_ws_bound(int64_t l);
+size_t gram_ws_bound(int64_t rows, int64_t l);
 size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz);
 size_t tsvd_ws_bound(int64_t l);
 

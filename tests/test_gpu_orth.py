@@ -43,6 +43,28 @@ def test_gram(ctx, m, l, dt):
     assert np.all(Q.qnorm(small_to_np(G) - want) <= 64 * m * 2.0 ** -53 * scale)
 
 
+@pytest.mark.parametrize("m,l,seed", [(1, 1, 1), (513, 64, 2), (64, 200, 3), (2048, 17, 4), (4100, 110, 5)])
+def test_gram_fp32_graded_normwise(ctx, m, l, seed):
+    """FP32 Gram (tensor-core exact slicing when it applies) on columns scaled over 12 decades and
+    rows over 6: every entry within 2^-36 sqrt(m) |y_i| |y_j| of the FP64 Gram of the stored data --
+    FP64-class normwise, far below the 2^-24 of an FP32 sum.  Covers one row, chunk boundaries
+    (513 rows), several W tiles (l = 200) and ragged tiles."""
+    from paper_2507_13731_gb300 import qlr
+    rng = np.random.default_rng(seed)
+    Y = synth.gaussian_qmat(seed, m, l)
+    Y = Y * (10.0 ** rng.uniform(-6, 6, size=l))[None, None, :] * (10.0 ** rng.uniform(-3, 3, size=m))[None, :, None]
+    Yd = dev_thin(Y, "f32")
+    G = small(l)
+    qlr.qgram(ctx, Yd, G)
+    assert ctx.sync() == 0
+    Yh = host(Yd)
+    want = Q.qmatmul(Q.qH(Yh), Yh)
+    cn = np.sqrt((Yh ** 2).sum(axis=(0, 1)))
+    Gh = small_to_np(G)
+    assert np.all(Q.qnorm(Gh - want) <= 2.0 ** -36 * np.sqrt(m) * np.outer(cn, cn))
+    assert np.all(Gh[1:, np.arange(l), np.arange(l)] == 0.0)
+
+
 @pytest.mark.parametrize("l", [1, 5, 64, 110])
 def test_chol_matches_unique_qr_factor(ctx, l):
     from paper_2507_13731_gb300 import qlr
