@@ -3,13 +3,13 @@
 // One plan per problem set, and one launch per step for all the problems: every sketch pass is
 // a grouped tensor-core launch over all the problems' output tiles (sketch_tc.cu), preceded by
 // one grouped staging launch of their thin operands; every orthonormalisation step is a grouped
-// Gram launch (with its combine), a grouped double-FP32 Cholesky launch (one CTA per problem,
-// which also forms R^{-1} and the running product of the R factors) and a grouped thin x small
-// product; after the last pass one grouped Jacobi launch computes every core QSVD and one
-// grouped product lifts all U and V.  A run is a few dozen launches, whatever the problem count,
-// and each launch spreads the problems' CTAs over the whole GPU.  The sequence is captured once
-// into a CUDA graph and replayed by every run.  At plan time a small autotuner times the grouped
-// sketch's tile orders and keeps the faster one.
+// tensor-core Gram (slicing, MMA and combine launches, gram_tc.cu), a grouped double-FP32
+// Cholesky launch (one CTA per problem, which also forms R^{-1} and the running product of the R
+// factors) and a grouped thin x small product; after the last pass one grouped Jacobi launch
+// computes every core QSVD and one grouped product lifts all U and V.  A run is a few dozen
+// launches, whatever the problem count, and each launch spreads the problems' CTAs over the whole
+// GPU.  The sequence is captured once into a CUDA graph and replayed by every run.  At plan time a
+// small autotuner times the grouped sketch's tile orders and keeps the faster one.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -21,7 +21,7 @@ namespace {
 
 // One orthonormalisation step of one pass (device tables, one entry per problem).
 struct StepTables {
-  const qlr::GramGroupArgs* gram = nullptr;
+  const void* gram = nullptr;               // tensor-core Gram records
   const qlr::CholGroupArgs* chol = nullptr;
   const qlr::GemmArgs* apply = nullptr;
 };
@@ -32,7 +32,7 @@ struct qlr_batch {
   struct Prob {
     qlr_qmat A, om, U, V, Y, Z, Q1, Q2, T;
     double* S;
-    float2* W;        // Gram tiles (double-FP32 pairs)
+    char* gsc;        // tensor-core Gram scratch (slices, exponents, chunk partials)
     float* G;         // Gram, double-FP32 upper triangle
     float* Rinv;      // R^{-1} of the current step (FP32)
     float* Rp[2];     // running products of the last pass's R factors (FP32)
@@ -50,10 +50,11 @@ struct qlr_batch {
   char* gdev[3] = {nullptr, nullptr, nullptr};
   size_t gbytes[3] = {0, 0, 0};
   std::vector<std::vector<StepTables>> steps;   // [pass - 1][step]
-  const int4* gram_items[2] = {nullptr, nullptr};   // [0]: rows m (odd passes), [1]: rows n
+  const int4* slice_items[2] = {nullptr, nullptr};  // [0]: rows m (odd passes), [1]: rows n
+  const int4* gram_items[2] = {nullptr, nullptr};
   const int4* comb_items[2] = {nullptr, nullptr};
   const int4* apply_items[2] = {nullptr, nullptr};
-  int n_gram[2] = {0, 0}, n_comb[2] = {0, 0}, n_apply[2] = {0, 0};
+  int n_slice[2] = {0, 0}, n_gram[2] = {0, 0}, n_comb[2] = {0, 0}, n_apply[2] = {0, 0};
   const qlr::JacobiGroupArgs* jac = nullptr;
   const qlr::GemmArgs* lift = nullptr;
   const int4* lift_items = nullptr;
@@ -141,7 +142,8 @@ int enqueue(qlr_batch* b) {
     QLR_TRY(qlr::sketch_tc_grouped_run(mc, plan_of(b, i)));
     const int par = (i % 2 == 1) ? 0 : 1;
     for (const StepTables& st : b->steps[i - 1]) {
-      QLR_TRY(qlr::gram_df_grouped(mc, st.gram, b->gram_items[par], b->n_gram[par], b->comb_items[par], b->n_comb[par]));
+      QLR_TRY(qlr::gram_tc_grouped(mc, st.gram, b->slice_items[par], b->n_slice[par], b->gram_items[par], b->n_gram[par],
+                                   b->comb_items[par], b->n_comb[par]));
       QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
       QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
@@ -215,6 +217,7 @@ void release(qlr_batch* b) {
 struct TableBuf {
   std::vector<char> host;
   std::vector<size_t> offs;
+  void add_raw(const std::vector<char>& v) { add(v); }
   template <class T>
   void add(const std::vector<T>& v) {
     const size_t off = rup(host.size());
@@ -225,9 +228,10 @@ struct TableBuf {
 };
 
 // Lays out every problem's buffers from `base` (returns the bytes used) and records the host
-// images of the step tables in tb, in the order batch_create reads them back.
+// images of the step tables in tb, in the order batch_create reads them back; *rc receives the
+// first failure to encode a tensor map (the dry run from a dummy base ignores it).
 size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const qlr_qmat* omega, qlr_qmat* U,
-              double* const* S, qlr_qmat* V, char* base, TableBuf& tb) {
+              double* const* S, qlr_qmat* V, char* base, TableBuf& tb, int* rc) {
   using namespace qlr;
   const int count = b->count, passes = b->passes;
   char* cur = base;
@@ -241,7 +245,7 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     P.Z = thin_at(cur, n, P.l);
     P.Q2 = thin_at(cur, n, P.l);
     P.T = thin_at(cur, std::max(m, n), P.l);
-    P.W = take<float2>(cur, (size_t)16 * P.l * P.l);
+    P.gsc = take<char>(cur, gram_tc_ws(std::max(m, n), P.l));
     P.G = take<float>(cur, (size_t)8 * P.l * P.l);
     P.Rinv = take<float>(cur, (size_t)4 * P.l * P.l);
     P.Rp[0] = take<float>(cur, (size_t)4 * P.l * P.l);
@@ -252,7 +256,7 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
   // items: Gram tiles, combine blocks and product tiles for row count m (odd passes) or n, the
   // problems with the most rows first (their CTAs run longest)
   for (int par = 0; par < 2; ++par) {
-    std::vector<int4> gi, ci, ai;
+    std::vector<int4> si, gi, ci, ai;
     std::vector<int> heavy(count);
     for (int j = 0; j < count; ++j) heavy[j] = j;
     auto rows_of = [&](int j) { return par == 0 ? b->pr[j].A.rows : b->pr[j].A.cols; };
@@ -260,22 +264,25 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     for (int j : heavy) {
       const qlr_batch::Prob& P = b->pr[j];
       const int64_t rows = par == 0 ? P.A.rows : P.A.cols;
-      gram_grouped_items(rows, P.l, j, gi, ci);
+      gram_tc_grouped_items(rows, P.l, j, si, gi, ci);
       thin_small_items(rows, P.l, j, ai);
     }
+    b->n_slice[par] = (int)si.size();
     b->n_gram[par] = (int)gi.size();
     b->n_comb[par] = (int)ci.size();
     b->n_apply[par] = (int)ai.size();
+    tb.add(si);
     tb.add(gi);
     tb.add(ci);
     tb.add(ai);
   }
+  const size_t rec = gram_tc_record_bytes();
   // steps of every pass: Y (odd) or Z (even) -> Q1 or Q2, through T
   for (int i = 1; i <= passes; ++i) {
     const int o = (i >= passes - 1) ? b->orth : b->mid;
     const int ns = orth_steps(o);
     for (int s = 0; s < ns; ++s) {
-      std::vector<GramGroupArgs> ga(count);
+      std::vector<char> ga((size_t)count * rec);
       std::vector<CholGroupArgs> ca(count);
       std::vector<GemmArgs> aa(count);
       for (int j = 0; j < count; ++j) {
@@ -291,9 +298,8 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         if (ns == 3) { seq[2] = &T; seq[3] = &dst; }
         const qlr_qmat& from = *seq[s];
         const qlr_qmat& to = *seq[s + 1];
-        GramGroupArgs& G = ga[j];
-        for (int c = 0; c < 4; ++c) G.y[c] = static_cast<const float*>(from.plane[c]);
-        G.ld = from.ld; G.m = from.rows; G.l = P.l; G.W = P.W; G.G = P.G;
+        const int grc = gram_tc_record(ga.data() + (size_t)j * rec, from, P.gsc, P.G, b->ctx->d_err);
+        if (grc != QLR_OK && *rc == QLR_OK) *rc = grc;
         CholGroupArgs& C = ca[j];
         C.G = P.G;
         C.Rinv = P.Rinv;
@@ -309,7 +315,7 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         aa[j] = thin_small_args(from, P.Rinv, P.l, P.l, to);
         aa[j].b_upper = true;   // R^{-1} is upper triangular
       }
-      tb.add(ga);
+      tb.add_raw(ga);
       tb.add(ca);
       tb.add(aa);
     }
@@ -403,7 +409,8 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   {
     TableBuf dry;
     char* dummy = reinterpret_cast<char*>((uintptr_t)256);
-    bytes = rup(layout(b, A, k, p, omega, U, S, V, dummy, dry));
+    int dry_rc = QLR_OK;
+    bytes = rup(layout(b, A, k, p, omega, U, S, V, dummy, dry, &dry_rc));
     tbytes = rup(dry.host.size());
   }
   const size_t total = bytes + rup(b->gbytes[0]) + rup(b->gbytes[1]) + rup(b->gbytes[2]) + tbytes;
@@ -414,12 +421,12 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
   }
   char* base = static_cast<char*>(b->dev);
   TableBuf tb;
-  layout(b, A, k, p, omega, U, S, V, base, tb);
+  int rc = QLR_OK;
+  layout(b, A, k, p, omega, U, S, V, base, tb, &rc);
   char* cur = base + bytes;
   for (int s = 0; s < 3; ++s) { b->gdev[s] = cur; cur += rup(b->gbytes[s]); }
   char* tdev = cur;
-  int rc = QLR_OK;
-  if (cudaMemsetAsync(b->dev, 0, bytes, ctx->stream) != cudaSuccess) rc = QLR_ECUDA;
+  if (rc == QLR_OK && cudaMemsetAsync(b->dev, 0, bytes, ctx->stream) != cudaSuccess) rc = QLR_ECUDA;
   if (rc == QLR_OK && cudaMemcpyAsync(tdev, tb.host.data(), tb.host.size(), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
     rc = QLR_ECUDA;
   if (rc == QLR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = QLR_ECUDA;   // tb is pageable
@@ -427,6 +434,7 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
     size_t q = 0;
     auto next = [&]() { return tdev + tb.offs[q++]; };
     for (int par = 0; par < 2; ++par) {
+      b->slice_items[par] = reinterpret_cast<const int4*>(next());
       b->gram_items[par] = reinterpret_cast<const int4*>(next());
       b->comb_items[par] = reinterpret_cast<const int4*>(next());
       b->apply_items[par] = reinterpret_cast<const int4*>(next());
@@ -436,7 +444,7 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
       const int ns = orth_steps((i >= passes - 1) ? b->orth : b->mid);
       for (int s = 0; s < ns; ++s) {
         StepTables st;
-        st.gram = reinterpret_cast<const GramGroupArgs*>(next());
+        st.gram = next();
         st.chol = reinterpret_cast<const CholGroupArgs*>(next());
         st.apply = reinterpret_cast<const GemmArgs*>(next());
         b->steps[i - 1].push_back(st);

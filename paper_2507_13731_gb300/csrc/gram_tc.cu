@@ -57,14 +57,26 @@ struct GramTcParams {
   int* err;
 };
 
-// One CTA per column c of Yh (L4p columns, the padding zero).
-__global__ void __launch_bounds__(256) gram_slice_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
-                                                         const float* __restrict__ y2, const float* __restrict__ y3,
-                                                         int64_t m, int l, int64_t ld, int L4p, int64_t mp,
-                                                         __nv_bfloat16* __restrict__ S, int* __restrict__ ex) {
+// A problem of a batch plan: the MMA parameters (tensor maps first, 64-byte aligned) and what the
+// slicing and the combine need.
+struct GramTcProb {
+  GramTcParams tc;
+  const float* y[4];
+  int64_t m, ld, mp;
+  int l, nchunks;
+  __nv_bfloat16* S;
+  int* ex;
+  float* G;             // double-FP32 upper triangle, 8 floats per entry at G + 8 (j l + i)
+};
+
+// Column c of Yh (L4p columns, the padding zero) by one CTA of 256 threads.
+__device__ __forceinline__ void gram_slice_col(const float* __restrict__ y0, const float* __restrict__ y1,
+                                               const float* __restrict__ y2, const float* __restrict__ y3, int64_t m,
+                                               int l, int64_t ld, int L4p, int64_t mp, __nv_bfloat16* __restrict__ S,
+                                               int* __restrict__ ex, const int c) {
   __shared__ float red[8];
   __shared__ int s_e;
-  const int c = blockIdx.x, t = threadIdx.x;
+  const int t = threadIdx.x;
   const float* y = nullptr;
   if (c < 4 * l) {
     const int pl = c / l, j = c % l;
@@ -98,6 +110,13 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const float* __restrict
   }
 }
 
+__global__ void __launch_bounds__(256) gram_slice_kernel(const float* __restrict__ y0, const float* __restrict__ y1,
+                                                         const float* __restrict__ y2, const float* __restrict__ y3,
+                                                         int64_t m, int l, int64_t ld, int L4p, int64_t mp,
+                                                         __nv_bfloat16* __restrict__ S, int* __restrict__ ex) {
+  gram_slice_col(y0, y1, y2, y3, m, l, ld, L4p, mp, S, ex, blockIdx.x);
+}
+
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -115,13 +134,13 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
   e = __fadd_rn(e, err);
 }
 
-__global__ void __launch_bounds__(GTHREADS, 1) gram_tc_kernel(const __grid_constant__ GramTcParams p) {
-  // tile: blockIdx.x enumerates (ab, bb) with bb >= 2 ab (the upper part of W)
-  int tl = blockIdx.x, ab = 0;
+// One tile of W for one chunk of rows: tile index tl enumerates (ab, bb) with bb >= 2 ab (the
+// upper part of W).
+__device__ __forceinline__ void gram_tc_tile(const GramTcParams& p, int tl, const int chunk) {
+  int ab = 0;
   while (ab < p.nA && tl >= max(0, p.nB - 2 * ab)) { tl -= max(0, p.nB - 2 * ab); ++ab; }
   const int bb = 2 * ab + tl;
   const int a0 = ab * GA, b0 = bb * GB;
-  const int chunk = blockIdx.y;
   const int it0 = chunk * (GCHUNK / GK);
   const int it1 = min(p.kiters, it0 + GCHUNK / GK);
   const int nit = it1 - it0;
@@ -260,6 +279,23 @@ __global__ void __launch_bounds__(GTHREADS, 1) gram_tc_kernel(const __grid_const
   }
 }
 
+__global__ void __launch_bounds__(GTHREADS, 1) gram_tc_kernel(const __grid_constant__ GramTcParams p) {
+  gram_tc_tile(p, blockIdx.x, blockIdx.y);
+}
+
+// Batch plans: item (problem, tile, chunk) with that problem's parameters in global memory
+// (tensor maps 64-byte aligned, written before the launch).
+__global__ void __launch_bounds__(GTHREADS, 1) gram_tc_grouped_kernel(const GramTcProb* __restrict__ probs,
+                                                                      const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GramTcParams& p = probs[it.x].tc;
+  if (threadIdx.x == 0) {   // the TMA-issuing thread
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmB) : "memory");
+  }
+  gram_tc_tile(p, it.y, it.z);
+}
+
 // W(I, J) for I <= J: the chunk partials added in double-FP32, scaled by 2^(e_I + e_J - 12).
 __device__ __forceinline__ double w_tc(const float2* __restrict__ part, int nchunks, const int* __restrict__ ex, int L4,
                                        int I, int J) {
@@ -272,6 +308,68 @@ __device__ __forceinline__ double w_tc(const float2* __restrict__ part, int nchu
     e = __fadd_rn(e, v.y);
   }
   return ldexp((double)s + (double)e, ex[I] + ex[J] - 2 * GBITS);
+}
+
+// W(I, J), I <= J, as a scaled double-FP32 pair (s, e).
+__device__ __forceinline__ float2 w_tc_d32(const float2* __restrict__ part, int nchunks, const int* __restrict__ ex,
+                                           int L4, int I, int J) {
+  if (I > J) { const int t = I; I = J; J = t; }
+  const size_t o = (size_t)J * L4 + I, step = (size_t)L4 * L4;
+  float s = 0.f, e = 0.f;
+  for (int c = 0; c < nchunks; ++c) {
+    const float2 v = part[c * step + o];
+    two_sum_acc(s, e, v.x);
+    e = __fadd_rn(e, v.y);
+  }
+  const int k = ex[I] + ex[J] - 2 * GBITS;
+  return make_float2(ldexpf(s, k), ldexpf(e, k));
+}
+
+// Batch plans: item (problem, block of 128 entries); G's upper triangle in double-FP32.
+__global__ void __launch_bounds__(128) gram_tc_combine_grouped_kernel(const GramTcProb* __restrict__ probs,
+                                                                      const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GramTcProb& a = probs[it.x];
+  const int l = a.l, L4 = 4 * l;
+  const int idx = it.y * 128 + (int)threadIdx.x;
+  if (idx >= l * l) return;
+  const int i = idx % l, j = idx / l;
+  if (i > j) return;
+  // component signs of conj(y_i) y_j from the 16 plane products W(c l + i, d l + j)
+  const float sg[4][4][4] = {{{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}},
+                             {{0, -1, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, -1}, {0, 0, 1, 0}},
+                             {{0, 0, -1, 0}, {0, 0, 0, 1}, {1, 0, 0, 0}, {0, -1, 0, 0}},
+                             {{0, 0, 0, -1}, {0, 0, -1, 0}, {0, 1, 0, 0}, {1, 0, 0, 0}}};
+  float gs[4] = {0.f, 0.f, 0.f, 0.f}, ge[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const float2 w = w_tc_d32(a.tc.part, a.nchunks, a.ex, L4, c * l + i, d * l + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (sg[c][d][q] != 0.f) {
+          two_sum_acc(gs[q], ge[q], sg[c][d][q] * w.x);
+          ge[q] = __fadd_rn(ge[q], sg[c][d][q] * w.y);
+        }
+    }
+  float h[4], lo[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = __fadd_rn(gs[q], ge[q]);
+    lo[q] = __fsub_rn(ge[q], __fsub_rn(h[q], gs[q]));
+    if (i == j && q > 0) h[q] = lo[q] = 0.f;
+  }
+  float4* o = reinterpret_cast<float4*>(a.G + 8 * ((size_t)j * l + i));
+  o[0] = make_float4(h[0], h[1], h[2], h[3]);
+  o[1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+__global__ void __launch_bounds__(256) gram_slice_grouped_kernel(const GramTcProb* __restrict__ probs,
+                                                                 const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GramTcProb& a = probs[it.x];
+  gram_slice_col(a.y[0], a.y[1], a.y[2], a.y[3], a.m, a.l, a.ld, a.tc.L4p, a.mp, a.S, a.ex, it.y);
 }
 
 // The quaternion Gram from W (components as in the SIMT Gram's combine), FP64 planes.
@@ -315,13 +413,48 @@ GramTcDims gram_tc_dims(int64_t m, int l) {
   return d;
 }
 
+struct GramTcBufs {
+  __nv_bfloat16* S;
+  int* ex;
+  float2* part;
+};
+size_t rup256(size_t b) { return (b + 255) / 256 * 256; }
+GramTcBufs gram_tc_carve(char* base, const GramTcDims& d) {
+  GramTcBufs b;
+  b.S = reinterpret_cast<__nv_bfloat16*>(base);
+  base += rup256((size_t)GS * d.L4p * d.mp * 2);
+  b.ex = reinterpret_cast<int*>(base);
+  base += rup256((size_t)d.L4p * 4);
+  b.part = reinterpret_cast<float2*>(base);
+  return b;
+}
+
+// Tensor maps and dimensions of one problem (host side).
+bool gram_tc_params(GramTcParams& prm, const GramTcDims& d, const GramTcBufs& bufs, int* err) {
+  memset(&prm, 0, sizeof(prm));
+  const uint64_t cols = (uint64_t)GS * d.L4p;
+  if (!encode_2d(&prm.tmA, bufs.S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GA,
+                 CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !encode_2d(&prm.tmB, bufs.S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GB,
+                 CU_TENSOR_MAP_SWIZZLE_64B))
+    return false;
+  prm.part = bufs.part;
+  prm.L4 = d.L4;
+  prm.nA = d.nA;
+  prm.nB = d.nB;
+  prm.L4p = d.L4p;
+  prm.kiters = d.kiters;
+  prm.err = err;
+  return true;
+}
+
 }  // namespace
 
 namespace qlr {
 
 size_t gram_tc_ws(int64_t m, int l) {
   const GramTcDims d = gram_tc_dims(m, l);
-  return (size_t)GS * d.L4p * d.mp * 2 + (size_t)d.L4p * 4 + (size_t)d.nchunks * d.L4 * d.L4 * 8 + 3 * 256;
+  return rup256((size_t)GS * d.L4p * d.mp * 2) + rup256((size_t)d.L4p * 4) + rup256((size_t)d.nchunks * d.L4 * d.L4 * 8);
 }
 
 bool gram_tc_supported(const qlr_qmat& Y) {
@@ -337,27 +470,17 @@ int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   const int l = (int)Y.cols;
   const GramTcDims d = gram_tc_dims(m, l);
   const size_t mark = ws.off;
-  __nv_bfloat16* S = ws.take<__nv_bfloat16>((size_t)GS * d.L4p * d.mp);
-  int* ex = ws.take<int>((size_t)d.L4p);
-  float2* part = ws.take<float2>((size_t)d.nchunks * d.L4 * d.L4);
+  char* base = ws.take<char>(gram_tc_ws(m, l));
   if (!ws.ok) { ws.off = mark; ws.ok = true; return QLR_ENOMEM; }
+  const GramTcBufs bufs = gram_tc_carve(base, d);
+  __nv_bfloat16* S = bufs.S;
+  int* ex = bufs.ex;
+  float2* part = bufs.part;
   GramTcParams prm;
-  memset(&prm, 0, sizeof(prm));
-  const uint64_t cols = (uint64_t)GS * d.L4p;
-  if (!encode_2d(&prm.tmA, S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GA,
-                 CU_TENSOR_MAP_SWIZZLE_64B) ||
-      !encode_2d(&prm.tmB, S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GB,
-                 CU_TENSOR_MAP_SWIZZLE_64B)) {
+  if (!gram_tc_params(prm, d, bufs, ctx->d_err)) {
     ws.off = mark;
     return QLR_ECUDA;
   }
-  prm.part = part;
-  prm.L4 = d.L4;
-  prm.nA = d.nA;
-  prm.nB = d.nB;
-  prm.L4p = d.L4p;
-  prm.kiters = d.kiters;
-  prm.err = ctx->d_err;
   KTimer kt(ctx, QLR_KID_GRAM);
   gram_slice_kernel<<<d.L4p, 256, 0, ctx->stream>>>(
       static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
@@ -373,6 +496,55 @@ int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   ws.off = mark;   // the buffers are dead once the combine is enqueued (stream order)
+  return QLR_OK;
+}
+
+size_t gram_tc_record_bytes() { return sizeof(GramTcProb); }
+
+int gram_tc_record(void* dst, const qlr_qmat& Y, char* scratch, float* G, int* err) {
+  const int l = (int)Y.cols;
+  const GramTcDims d = gram_tc_dims(Y.rows, l);
+  const GramTcBufs bufs = gram_tc_carve(scratch, d);
+  GramTcProb r;
+  memset(&r, 0, sizeof(r));
+  if (!gram_tc_params(r.tc, d, bufs, err)) return QLR_ECUDA;
+  for (int c = 0; c < 4; ++c) r.y[c] = static_cast<const float*>(Y.plane[c]);
+  r.m = Y.rows;
+  r.ld = Y.ld;
+  r.mp = d.mp;
+  r.l = l;
+  r.nchunks = d.nchunks;
+  r.S = bufs.S;
+  r.ex = bufs.ex;
+  r.G = G;
+  memcpy(dst, &r, sizeof(r));
+  return QLR_OK;
+}
+
+void gram_tc_grouped_items(int64_t m, int l, int prob, std::vector<int4>& slice, std::vector<int4>& mma,
+                           std::vector<int4>& comb) {
+  const GramTcDims d = gram_tc_dims(m, l);
+  for (int c = 0; c < d.L4p; ++c) slice.push_back(make_int4(prob, c, 0, 0));
+  for (int ch = 0; ch < d.nchunks; ++ch)
+    for (int t = 0; t < d.ntiles; ++t) mma.push_back(make_int4(prob, t, ch, 0));
+  for (int b = 0; b < (l * l + 127) / 128; ++b) comb.push_back(make_int4(prob, b, 0, 0));
+}
+
+int gram_tc_grouped(qlr_ctx* ctx, const void* d_probs, const int4* slice, int n_slice, const int4* mma, int n_mma,
+                    const int4* comb, int n_comb) {
+  if (n_slice <= 0) return QLR_OK;
+  const GramTcProb* probs = static_cast<const GramTcProb*>(d_probs);
+  KTimer kt(ctx, QLR_KID_GRAM);
+  gram_slice_grouped_kernel<<<n_slice, 256, 0, ctx->stream>>>(probs, slice);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  QLR_CUDA_TRY(cudaFuncSetAttribute(gram_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GSMEM));
+  gram_tc_grouped_kernel<<<n_mma, GTHREADS, GSMEM, ctx->stream>>>(probs, mma);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  gram_tc_combine_grouped_kernel<<<n_comb, 128, 0, ctx->stream>>>(probs, comb);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
 

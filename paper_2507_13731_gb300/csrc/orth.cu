@@ -1298,62 +1298,6 @@ __global__ void fill_identity_kernel(double* __restrict__ X, int l) {
 // of the plan (item tables map each CTA to its problem and tile).  The small operands are FP32
 // or double-FP32 throughout, so no FP64 instruction runs on this path.
 
-// W tiles of one problem's Gram as (S, C) double-FP32 pairs (one row chunk: the whole m).
-__global__ void __launch_bounds__(256) gram_df_grouped_kernel(const qlr::GramGroupArgs* __restrict__ args,
-                                                               const int4* __restrict__ items) {
-  const int4 it = items[blockIdx.x];
-  const qlr::GramGroupArgs& a = args[it.x];
-  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int2 tile = upper_tri_entry(it.y);
-  const int I0 = tile.x * WT, J0 = tile.y * WT;
-  const int l = a.l, L4 = 4 * l;
-  float S[4][4], C[4][4];
-  const bool diag = (tile.x == tile.y);
-  if (diag) gram_df_tile<true>(a.y[0], a.y[1], a.y[2], a.y[3], l, a.ld, 0, a.m, I0, J0, S, C);
-  else gram_df_tile<false>(a.y[0], a.y[1], a.y[2], a.y[3], l, a.ld, 0, a.m, I0, J0, S, C);
-  float2* W = a.W;
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int z = 0; z < 4; ++z) {
-      const int I = I0 + tx + 16 * x, J = J0 + ty + 16 * z;
-      if (I < L4 && J < L4 && !(diag && x > z)) W[(size_t)J * L4 + I] = make_float2(S[x][z], C[x][z]);
-    }
-}
-
-__device__ __forceinline__ d32 wdf_at(const float2* __restrict__ W, int L4, int I, int J) {
-  if (I > J) { int t = I; I = J; J = t; }     // only entries on or above the diagonal were computed
-  const float2 v = W[(size_t)J * L4 + I];
-  return {v.x, v.y};
-}
-
-// The quaternion Gram's upper triangle from W (the sign pattern of gram_df_combine_kernel), in
-// double-FP32: entry (i, j) as 8 floats (high w, x, y, z; low w, x, y, z) at G + 8 (j l + i).
-__global__ void __launch_bounds__(128) gram_df_combine_grouped_kernel(const qlr::GramGroupArgs* __restrict__ args,
-                                                                       const int4* __restrict__ items) {
-  const int4 it = items[blockIdx.x];
-  const qlr::GramGroupArgs& a = args[it.x];
-  const int l = a.l, L4 = 4 * l;
-  const int idx = it.y * 128 + (int)threadIdx.x;
-  if (idx >= l * l) return;
-  const int i = idx % l, j = idx / l;
-  if (i > j) return;
-  d32 w[4][4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int d = 0; d < 4; ++d) w[c][d] = wdf_at(a.W, L4, c * l + i, d * l + j);
-  d32 g[4];
-  g[0] = d32_add(d32_add(w[0][0], w[1][1]), d32_add(w[2][2], w[3][3]));
-  g[1] = d32_add(d32_add(w[0][1], d32_neg(w[1][0])), d32_add(d32_neg(w[2][3]), w[3][2]));
-  g[2] = d32_add(d32_add(w[0][2], w[1][3]), d32_add(d32_neg(w[2][0]), d32_neg(w[3][1])));
-  g[3] = d32_add(d32_add(w[0][3], d32_neg(w[1][2])), d32_add(w[2][1], d32_neg(w[3][0])));
-  if (i == j) g[1] = g[2] = g[3] = {0.f, 0.f};
-  float4* o = reinterpret_cast<float4*>(a.G + 8 * ((size_t)j * l + i));
-  o[0] = make_float4(g[0].h, g[1].h, g[2].h, g[3].h);
-  o[1] = make_float4(g[0].l, g[1].l, g[2].l, g[3].l);
-}
-
 // s + e += a b for double-FP32 a = ah + al, b = bh + bl: the high product is split exactly by an
 // FMA, its rounded part added into s by a two-sum (Knuth), and every low-order term collected in
 // e (renormalised once per entry, after four products).
@@ -1552,28 +1496,6 @@ namespace qlr {
 
 // ---------------------------------------------------------------------------------------
 // grouped steps of batch plans
-
-void gram_grouped_items(int64_t m, int l, int prob, std::vector<int4>& partial, std::vector<int4>& combine) {
-  (void)m;
-  const int nt = (4 * l + WT - 1) / WT;
-  const int ntiles = nt * (nt + 1) / 2;
-  for (int tile = 0; tile < ntiles; ++tile) partial.push_back(make_int4(prob, tile, 0, 0));
-  const int nb = (l * l + 127) / 128;
-  for (int b = 0; b < nb; ++b) combine.push_back(make_int4(prob, b, 0, 0));
-}
-
-int gram_df_grouped(qlr_ctx* ctx, const GramGroupArgs* d_args, const int4* d_partial, int n_partial,
-                    const int4* d_combine, int n_combine) {
-  if (n_partial <= 0) return QLR_OK;
-  KTimer kt(ctx, QLR_KID_GRAM);
-  gram_df_grouped_kernel<<<n_partial, 256, 0, ctx->stream>>>(d_args, d_partial);
-  qlr_count_launch();
-  QLR_CUDA_TRY(cudaGetLastError());
-  gram_df_combine_grouped_kernel<<<n_combine, 128, 0, ctx->stream>>>(d_args, d_combine);
-  qlr_count_launch();
-  QLR_CUDA_TRY(cudaGetLastError());
-  return QLR_OK;
-}
 
 size_t chol_df_grouped_smem(int lmax) { return (size_t)lmax * (lmax + 1) / 2 * sizeof(DQ) + (size_t)lmax * 4 + 64; }
 

@@ -199,6 +199,15 @@ int gram(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
 size_t gram_tc_ws(int64_t m, int l);
 bool gram_tc_supported(const qlr_qmat& Y);
 int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws);
+// Batch plans (grouped launches): a per-problem record of gram_tc_record_bytes() bytes (64-byte
+// aligned in the device table) holds the tensor maps over the problem's scratch (gram_tc_ws(m, l)
+// bytes) and writes G as a double-FP32 upper triangle (8 floats per entry at G + 8 (j l + i)).
+size_t gram_tc_record_bytes();
+int gram_tc_record(void* dst, const qlr_qmat& Y, char* scratch, float* G, int* err);
+void gram_tc_grouped_items(int64_t m, int l, int prob, std::vector<int4>& slice, std::vector<int4>& mma,
+                           std::vector<int4>& comb);
+int gram_tc_grouped(qlr_ctx* ctx, const void* d_probs, const int4* slice, int n_slice, const int4* mma, int n_mma,
+                    const int4* comb, int n_comb);
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
          const int* run_if = nullptr, bool df = false);
 int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr,
@@ -210,14 +219,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
 // per-problem arguments and the (problem, tile) items of each launch in device tables built once
 // by the plan.  The small operands are FP32 / double-FP32 (no FP64 instruction on this path).
 constexpr int kBatchMaxL = 80;   // largest l = k + p of a batch plan (one CTA holds its factors)
-//  Gram (orth.cu): W = Yh^T Yh of the plane-stacked Y (m x l, column-major FP32 planes, pitch
-//  ld) as double-FP32 (S, C) pairs, (4l)^2 per problem, then the upper triangle of G = Y^H Y as
-//  double-FP32 quaternions: entry (i, j), i <= j, is 8 floats (high w, x, y, z, low w, x, y, z)
-//  at G + 8 (j l + i).
-struct GramGroupArgs { const float* y[4]; int64_t ld; int64_t m; int l; float2* W; float* G; };
-void gram_grouped_items(int64_t m, int l, int prob, std::vector<int4>& partial, std::vector<int4>& combine);
-int gram_df_grouped(qlr_ctx* ctx, const GramGroupArgs* d_args, const int4* d_partial, int n_partial,
-                    const int4* d_combine, int n_combine);
+//  Gram: gram_tc_grouped (below, with the single-problem tensor-core Gram).
 //  Cholesky (orth.cu), one CTA per problem: R = chol(G + shift_coef trace(G) I) in double-FP32;
 //  Rinv = R^{-1} and Rout = R Rprev (R when Rprev is null) as FP32 l x l planes (column-major,
 //  zero below the diagonal); either output may be null.
