@@ -17,7 +17,7 @@
 // The error of W(a, b) is about 2^-45 of max|y_a| max|y_b| m: FP64-class, as the Gram of the
 // double-FP32 SIMT path (orth.cu), at tensor-core throughput.
 //
-// Kernels: gram_slice_kernel (one CTA per column: exponent, then the 8 slices, BF16, column-major
+// Kernels: gram_slice_kernel (one warp per column: exponent, then the 8 slices, BF16, column-major
 // per slice with rows padded to a multiple of 8), gram_tc_kernel (one CTA per (128 x 64 tile of
 // W's upper part, 512-row chunk): TMA of the 8 slices of both operands into a 2-stage ring, 72
 // MMAs of 128 x 64 x 16 per 32-row stage into 8 x 64 TMEM columns, epilogue to double-FP32
@@ -52,7 +52,8 @@ struct GramTcParams {
   CUtensorMap tmB;      // the same array, box {GK, GB}
   float2* part;         // [chunk] L4 x L4 column-major: W(a, b) at b L4 + a, double-FP32 (h, l)
   int L4, nA, nB;       // W order, a-blocks of GA, b-blocks of GB
-  int L4p;              // columns per slice (L4 rounded up to GA)
+  int L4p;              // columns per slice (L4 rounded up to GB; an A tile may run into the
+                        // next slice: those W rows a >= L4 are never stored)
   int kiters;           // GK-row stages over all m rows
   int* err;
 };
@@ -69,14 +70,17 @@ struct GramTcProb {
   float* G;             // double-FP32 upper triangle, 8 floats per entry at G + 8 (j l + i)
 };
 
-// Column c of Yh (L4p columns, the padding zero) by one CTA of 256 threads.
-__device__ __forceinline__ void gram_slice_col(const float* __restrict__ y0, const float* __restrict__ y1,
-                                               const float* __restrict__ y2, const float* __restrict__ y3, int64_t m,
-                                               int l, int64_t ld, int L4p, int64_t mp, __nv_bfloat16* __restrict__ S,
-                                               int* __restrict__ ex, const int c) {
-  __shared__ float red[8];
-  __shared__ int s_e;
-  const int t = threadIdx.x;
+// Columns 8 g .. 8 g + 7 of Yh (L4p columns, the padding zero), one warp per column: the
+// column exponent, then the 8 slices; each lane takes row pairs, stored as BF16 pairs.
+constexpr int SL_COLS = 8;
+
+__device__ __forceinline__ void gram_slice_cols(const float* __restrict__ y0, const float* __restrict__ y1,
+                                                const float* __restrict__ y2, const float* __restrict__ y3, int64_t m,
+                                                int l, int64_t ld, int L4p, int64_t mp, __nv_bfloat16* __restrict__ S,
+                                                int* __restrict__ ex, const int g) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int c = g * SL_COLS + warp;
+  if (c >= L4p) return;
   const float* y = nullptr;
   if (c < 4 * l) {
     const int pl = c / l, j = c % l;
@@ -84,28 +88,21 @@ __device__ __forceinline__ void gram_slice_col(const float* __restrict__ y0, con
   }
   float mx = 0.f;
   if (y)
-    for (int64_t r = t; r < m; r += 256) mx = fmaxf(mx, fabsf(y[r]));
+    for (int64_t r = lane; r < m; r += 32) mx = fmaxf(mx, fabsf(y[r]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (t % 32 == 0) red[t / 32] = mx;
-  __syncthreads();
-  if (t == 0) {
-    float M = 0.f;
-    for (int w = 0; w < 8; ++w) M = fmaxf(M, red[w]);
-    int e = 0;
-    if (M > 0.f) frexpf(M, &e);   // M < 2^e
-    s_e = e;
-    ex[c] = e;
-  }
-  __syncthreads();
-  const int e = s_e;
-  for (int64_t r = t; r < mp; r += 256) {
-    float v = (y && r < m) ? ldexpf(y[r], GBITS - e) : 0.f;   // |v| < 64, exact
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);   // max < 2^e
+  if (lane == 0) ex[c] = e;
+  for (int64_t r = 2 * lane; r < mp; r += 64) {   // mp is even
+    float v0 = (y && r < m) ? ldexpf(y[r], GBITS - e) : 0.f;       // |v| < 64, exact
+    float v1 = (y && r + 1 < m) ? ldexpf(y[r + 1], GBITS - e) : 0.f;
 #pragma unroll
     for (int i = 0; i < GS; ++i) {
-      const float q = truncf(v);                               // |q| <= 63
-      S[((size_t)i * L4p + c) * mp + r] = __float2bfloat16_rn(q);
-      v = (v - q) * 64.f;                                      // exact
+      const float q0 = truncf(v0), q1 = truncf(v1);                // |q| <= 63
+      *reinterpret_cast<__nv_bfloat162*>(S + ((size_t)i * L4p + c) * mp + r) = __floats2bfloat162_rn(q0, q1);
+      v0 = (v0 - q0) * 64.f;                                        // exact
+      v1 = (v1 - q1) * 64.f;
     }
   }
 }
@@ -114,7 +111,7 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const float* __restrict
                                                          const float* __restrict__ y2, const float* __restrict__ y3,
                                                          int64_t m, int l, int64_t ld, int L4p, int64_t mp,
                                                          __nv_bfloat16* __restrict__ S, int* __restrict__ ex) {
-  gram_slice_col(y0, y1, y2, y3, m, l, ld, L4p, mp, S, ex, blockIdx.x);
+  gram_slice_cols(y0, y1, y2, y3, m, l, ld, L4p, mp, S, ex, blockIdx.x);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
@@ -369,30 +366,37 @@ __global__ void __launch_bounds__(256) gram_slice_grouped_kernel(const GramTcPro
                                                                  const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GramTcProb& a = probs[it.x];
-  gram_slice_col(a.y[0], a.y[1], a.y[2], a.y[3], a.m, a.l, a.ld, a.tc.L4p, a.mp, a.S, a.ex, it.y);
+  gram_slice_cols(a.y[0], a.y[1], a.y[2], a.y[3], a.m, a.l, a.ld, a.tc.L4p, a.mp, a.S, a.ex, it.y);
 }
 
-// The quaternion Gram from W (components as in the SIMT Gram's combine), FP64 planes.
-__global__ void gram_tc_combine_kernel(const float2* __restrict__ part, int nchunks, const int* __restrict__ ex, int l,
-                                       double* __restrict__ G) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)l * l) return;
-  const int i = (int)(idx % l), j = (int)(idx / l);
-  if (i > j) return;
-  const int L4 = 4 * l;
-  double w[4][4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int d = 0; d < 4; ++d) w[c][d] = w_tc(part, nchunks, ex, L4, c * l + i, d * l + j);
-  Quat<double> g;
-  g.w = w[0][0] + w[1][1] + w[2][2] + w[3][3];
-  g.x = w[0][1] - w[1][0] - w[2][3] + w[3][2];
-  g.y = w[0][2] + w[1][3] - w[2][0] - w[3][1];
-  g.z = w[0][3] - w[1][2] + w[2][1] - w[3][0];
-  if (i == j) g.x = g.y = g.z = 0.0;
-  st_small(G, l, i, j, g);
-  if (i != j) st_small(G, l, j, i, {g.w, -g.x, -g.y, -g.z});
+// The quaternion Gram from W, FP64 planes: 16 threads per entry (i <= j), thread (c, d) forms
+// W(c l + i, d l + j); component q = c xor d of conj(y_i) y_j takes it with the sign of the
+// Hamilton table (negative for (c, d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)}), and the four
+// threads of each component add their terms by two shuffles.
+__global__ void __launch_bounds__(128) gram_tc_combine_kernel(const float2* __restrict__ part, int nchunks,
+                                                              const int* __restrict__ ex, int l, double* __restrict__ G) {
+  const int e = blockIdx.x * 8 + (int)(threadIdx.x >> 4);
+  const int lane16 = threadIdx.x & 15, c = lane16 >> 2, d = lane16 & 3;
+  const int ntri = l * (l + 1) / 2;
+  // entry e of the column-by-column listing of the upper triangle: j the largest with j (j + 1) / 2 <= e
+  int j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (j > 0 && j * (j + 1) / 2 > e) --j;
+  while ((j + 1) * (j + 2) / 2 <= e) ++j;
+  const int i = e - j * (j + 1) / 2;
+  double v = 0.0;
+  if (e < ntri) {
+    v = w_tc(part, nchunks, ex, 4 * l, c * l + i, d * l + j);
+    if ((0x3950u >> (c * 4 + d)) & 1u) v = -v;
+  }
+  v += __shfl_xor_sync(0xffffffffu, v, 5);
+  v += __shfl_xor_sync(0xffffffffu, v, 10);
+  if (e < ntri && c == 0) {   // thread (0, q) holds component q
+    const int q = d;
+    const size_t ll = (size_t)l * l;
+    const double gq = (i == j && q > 0) ? 0.0 : v;
+    G[q * ll + (size_t)j * l + i] = gq;
+    if (i != j) G[q * ll + (size_t)i * l + j] = (q == 0) ? gq : -gq;
+  }
 }
 
 struct GramTcDims {
@@ -402,8 +406,8 @@ struct GramTcDims {
 GramTcDims gram_tc_dims(int64_t m, int l) {
   GramTcDims d{};
   d.L4 = 4 * l;
-  d.L4p = (d.L4 + GA - 1) / GA * GA;
-  d.nA = d.L4p / GA;
+  d.L4p = (d.L4 + GB - 1) / GB * GB;
+  d.nA = (d.L4 + GA - 1) / GA;
   d.nB = (d.L4 + GB - 1) / GB;
   d.ntiles = 0;
   for (int ab = 0; ab < d.nA; ++ab) d.ntiles += std::max(0, d.nB - 2 * ab);
@@ -482,7 +486,7 @@ int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
     return QLR_ECUDA;
   }
   KTimer kt(ctx, QLR_KID_GRAM);
-  gram_slice_kernel<<<d.L4p, 256, 0, ctx->stream>>>(
+  gram_slice_kernel<<<(d.L4p + SL_COLS - 1) / SL_COLS, 256, 0, ctx->stream>>>(
       static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
       static_cast<const float*>(Y.plane[3]), m, l, Y.ld, d.L4p, d.mp, S, ex);
   qlr_count_launch();
@@ -491,8 +495,8 @@ int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
   gram_tc_kernel<<<dim3((unsigned)d.ntiles, (unsigned)d.nchunks), GTHREADS, GSMEM, ctx->stream>>>(prm);
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
-  const int64_t tot = (int64_t)l * l;
-  gram_tc_combine_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, ctx->stream>>>(part, d.nchunks, ex, l, G);
+  const int64_t ntri = (int64_t)l * (l + 1) / 2;
+  gram_tc_combine_kernel<<<(unsigned)((ntri + 7) / 8), 128, 0, ctx->stream>>>(part, d.nchunks, ex, l, G);
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   ws.off = mark;   // the buffers are dead once the combine is enqueued (stream order)
@@ -524,7 +528,7 @@ int gram_tc_record(void* dst, const qlr_qmat& Y, char* scratch, float* G, int* e
 void gram_tc_grouped_items(int64_t m, int l, int prob, std::vector<int4>& slice, std::vector<int4>& mma,
                            std::vector<int4>& comb) {
   const GramTcDims d = gram_tc_dims(m, l);
-  for (int c = 0; c < d.L4p; ++c) slice.push_back(make_int4(prob, c, 0, 0));
+  for (int g = 0; g < (d.L4p + SL_COLS - 1) / SL_COLS; ++g) slice.push_back(make_int4(prob, g, 0, 0));
   for (int ch = 0; ch < d.nchunks; ++ch)
     for (int t = 0; t < d.ntiles; ++t) mma.push_back(make_int4(prob, t, ch, 0));
   for (int b = 0; b < (l * l + 127) / 128; ++b) comb.push_back(make_int4(prob, b, 0, 0));
