@@ -6,18 +6,21 @@
 // the leading l columns are exactly the quaternion columns of R written in complex form.  A
 // one-sided (Hestenes) Jacobi that only uses right rotations of the form chi(G) for 2 x 2
 // quaternion unitaries G keeps that structure, so it suffices to store and rotate the l leading
-// columns -- equivalently, the quaternion columns of W = R.  For a pair of columns (p, q) with
-// alpha = |w_p|^2, beta = |w_q|^2 and gamma = w_p^H w_q = |gamma| mu (mu a unit quaternion),
-// w_q <- w_q mu* makes the 2 x 2 Gram real, and a real Jacobi rotation then orthogonalises the
-// pair.  At convergence W = U diag(sigma); each quaternion singular value of R is one of the
-// doubled singular values of chi(R).
+// columns -- equivalently, the quaternion columns of the matrix W that is swept.  W = R^H (the
+// same singular values; one-sided Jacobi on the conjugate transpose of a triangular factor needs
+// fewer sweeps).  For a pair of columns (p, q) with alpha = |w_p|^2, beta = |w_q|^2 and
+// gamma = w_p^H w_q = |gamma| mu (mu a unit quaternion), w_q <- w_q mu* makes the 2 x 2 Gram real,
+// and a real Jacobi rotation then orthogonalises the pair.  At convergence W V_W = U_W diag(sigma);
+// each quaternion singular value of R is one of the doubled singular values of chi(R).
 //
-// The right rotations make up V (R V = U diag(sigma)).  The sweep kernel works on W alone (in
-// shared memory when it fits) and logs every rotation (c, s, mu); a second kernel replays the log
-// on V = I.  The rows of V transform independently under right rotations, so the replay runs
-// row-parallel on many SMs.  Both vector sets are orthonormal to the working precision.  Precision: the sweeps run in T (float or double); a final
-// FP64 step evaluates every kept singular value as the two-sided Rayleigh quotient
-// sigma = Re(u^H R v) / (|u| |v|) from the FP64 R, whose error is second order in the vectors'.
+// The right rotations make up V_W, and R = V_W diag(sigma) U_W^H: R's left singular vectors are
+// V_W, its right ones U_W.  The sweep kernel works on W alone (in shared memory when it fits) and
+// logs every rotation (c, s, mu); a second kernel replays the log on V_W = I.  The rows of V_W
+// transform independently under right rotations, so the replay runs row-parallel on many SMs.
+// Both vector sets are orthonormal to the working precision.  Precision: the sweeps run in T
+// (float or double); a final FP64 step evaluates every kept singular value as the two-sided
+// Rayleigh quotient sigma = Re(u^H R v) / (|u| |v|) from the FP64 R, whose error is second order
+// in the vectors'.
 #include <cooperative_groups.h>
 #include <cstdio>
 #include <cstdlib>
@@ -83,6 +86,19 @@ __device__ __forceinline__ void jacobi_rotation(T alpha, T beta, const Quat<T>& 
   const T tt = (zeta >= 0 ? (T)1 : (T)-1) * jrcp(den);
   c = jrsqrt((T)1 + tt * tt);
   s = c * tt;
+}
+
+// Element e (plane-major, column-major planes) of W = R^H, the matrix the sweeps orthogonalise:
+// W(i, j) = conj(R(j, i)).  One-sided Jacobi on R^H rather than R converges in fewer sweeps on
+// the triangular factors of CholeskyQR (Drmac and Veselic's preconditioning); the roles of the
+// vectors swap: R = V_W Sigma U_W^H, so R's left vectors are W's accumulated rotations V_W and its
+// right vectors W's normalised columns U_W.
+template <class S>
+__device__ __forceinline__ S rh_elem(const S* __restrict__ R, int l, size_t ll, size_t e) {
+  const size_t c = e / ll, o = e % ll;
+  const size_t i = o % l, j = o / l;
+  const S v = R[c * ll + i * l + j];
+  return c == 0 ? v : -v;
 }
 
 // Cyclic (round-robin) one-sided Jacobi sweeps by one CTA of JT threads on W (l x l, planes of
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
   T* W = w_smem ? reinterpret_cast<T*>(smem_raw) : Wout;
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
   const size_t ll = (size_t)l * l;
-  for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)R[e];
+  for (size_t e = t; e < 4 * ll; e += JT) W[e] = (T)rh_elem(R, l, ll, e);
   __syncthreads();
   bool converged = false;
   const int sweep = jacobi_sweeps<T>(W, (T*)nullptr, l, max_sweeps, tol, rlog, &converged);
@@ -203,7 +219,7 @@ __global__ void __launch_bounds__(JT) jacobi_grouped_kernel(const qlr::JacobiGro
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
   const float* R = a.R;
   for (size_t e = t; e < 4 * ll; e += JT) {
-    W[e] = R[e];
+    W[e] = rh_elem(R, l, ll, e);
     Vs[e] = (e < ll && e % (l + 1) == 0) ? 1.f : 0.f;
   }
   __syncthreads();
@@ -240,8 +256,8 @@ __global__ void __launch_bounds__(JT) jacobi_grouped_kernel(const qlr::JacobiGro
   for (size_t e = t; e < 4 * lk; e += JT) {
     const int c = (int)(e / lk), r = (int)((e % lk) / l), i = (int)(e % l);
     const size_t src = (size_t)c * ll + (size_t)ord[r] * l + i;
-    U[e] = W[src];
-    V[e] = Vs[src];
+    U[e] = Vs[src];   // R's left vectors: the rotations of W = R^H
+    V[e] = W[src];    // R's right vectors: W's normalised columns
   }
 }
 
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const doubl
   const int sps = jb_stages_per_sweep(bw);
   const int stage_cap = JP * bw;
   const T tol2 = tol * tol;
-  for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)R[e];
+  for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)rh_elem(R, l, ll, e);
   if (p == 0)
     for (int i = t; i < max_sweeps; i += JB_THREADS) flags[i] = 0;
   __threadfence();
@@ -723,7 +739,11 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   const size_t rsm = (size_t)8 * l * sizeof(double);
   // static shared memory comes on top of the dynamic size: always opt in
   QLR_CUDA_TRY(cudaFuncSetAttribute(refine_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-  { KTimer kt(ctx, QLR_KID_REFINE); refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, W, V, order, k, L, S, Rt); qlr_count_launch(); }
+  {   // R's left vectors are the replayed rotations V, its right vectors W's columns (W = R^H)
+    KTimer kt(ctx, QLR_KID_REFINE);
+    refine_kernel<T><<<k, 256, rsm, ctx->stream>>>(R, l, V, W, order, k, L, S, Rt);
+    qlr_count_launch();
+  }
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
 }
