@@ -380,7 +380,80 @@ __global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const doubl
           }
       }
       __syncthreads();
-      const int nlr = (br == 0) ? U - 1 : bw;
+      if (br > 0 && bw <= nwarps) {
+        // cross-block rounds: warp pi keeps column a_pi in registers for all bw local rounds and
+        // only the b column it meets this round goes through shared memory
+        const int pi = warp;
+        const int ga = (pi < bw) ? gcol[pi] : -1;
+        Quat<T> wa[RPL];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int i = lane + 32 * u;
+          wa[u] = (ga >= 0 && i < l) ? Quat<T>{col(0, pi)[i], col(1, pi)[i], col(2, pi)[i], col(3, pi)[i]}
+                                     : Quat<T>{0, 0, 0, 0};
+        }
+        for (int lr = 0; lr < bw; ++lr) {
+          if (pi < bw) {
+            T* lg = rlog + ((size_t)sweep * sps + jb_stage(br, lr, bw)) * stage_cap * REC + ((size_t)p * bw + pi) * REC;
+            const int b = bw + (pi + lr) % bw;
+            const int gb = gcol[b];
+            if (ga < 0 || gb < 0) {
+              if (lane == 0) { lg[0] = (T)-1; lg[1] = (T)-1; lg[2] = (T)1; lg[3] = (T)0; }
+            } else {
+              T* B0 = col(0, b); T* B1 = col(1, b); T* B2 = col(2, b); T* B3 = col(3, b);
+              Quat<T> wq[RPL];
+              T aa = 0, bb2 = 0;
+              Quat<T> g = {0, 0, 0, 0};
+#pragma unroll
+              for (int u = 0; u < RPL; ++u) {
+                const int i = lane + 32 * u;
+                wq[u] = (i < l) ? Quat<T>{B0[i], B1[i], B2[i], B3[i]} : Quat<T>{0, 0, 0, 0};
+                aa += qnorm2(wa[u]);
+                bb2 += qnorm2(wq[u]);
+                const Quat<T> pr = qcmul(wa[u], wq[u]);
+                g.w += pr.w; g.x += pr.x; g.y += pr.y; g.z += pr.z;
+              }
+              aa = warp_sum(aa); bb2 = warp_sum(bb2);
+              g.w = warp_sum(g.w); g.x = warp_sum(g.x); g.y = warp_sum(g.y); g.z = warp_sum(g.z);
+              const T gn2 = qnorm2(g);
+              if (!(gn2 > (tol2 * aa) * bb2)) {
+                if (lane == 0) { lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = (T)1; lg[3] = (T)0; }
+              } else {
+                if (lane == 0) s_rot = 1;
+                Quat<T> mu;
+                T c, sn;
+                jacobi_rotation(aa, bb2, g, gn2, mu, c, sn);
+                if (lane == 0) {
+                  lg[0] = (T)ga; lg[1] = (T)gb; lg[2] = c; lg[3] = sn;
+                  lg[4] = mu.w; lg[5] = mu.x; lg[6] = mu.y; lg[7] = mu.z;
+                }
+#pragma unroll
+                for (int u = 0; u < RPL; ++u) {
+                  const int i = lane + 32 * u;
+                  const Quat<T> q = qmulc(wq[u], mu);
+                  const Quat<T> np = {c * wa[u].w - sn * q.w, c * wa[u].x - sn * q.x, c * wa[u].y - sn * q.y,
+                                      c * wa[u].z - sn * q.z};
+                  if (i < l) {
+                    B0[i] = sn * wa[u].w + c * q.w; B1[i] = sn * wa[u].x + c * q.x;
+                    B2[i] = sn * wa[u].y + c * q.y; B3[i] = sn * wa[u].z + c * q.z;
+                  }
+                  wa[u] = np;
+                }
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (ga >= 0) {
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int i = lane + 32 * u;
+            if (i < l) { col(0, pi)[i] = wa[u].w; col(1, pi)[i] = wa[u].x; col(2, pi)[i] = wa[u].y; col(3, pi)[i] = wa[u].z; }
+          }
+        }
+        __syncthreads();
+      }
+      const int nlr = (br == 0) ? U - 1 : ((bw <= nwarps) ? 0 : bw);
       for (int lr = 0; lr < nlr; ++lr) {
         T* lg_stage = rlog + ((size_t)sweep * sps + jb_stage(br, lr, bw)) * stage_cap * REC;
         for (int pi = warp; pi < bw; pi += nwarps) {
