@@ -11,14 +11,15 @@
 //
 // Per CTA: a 128-row tile of the output (M = m for op N, M = n for op H) and a block of nb <= 128
 // output columns of all four planes (4 nb <= 512 TMEM columns), over a contiguous range of the
-// reduction (split-K).  A's tiles come through TMA into a 2-4 stage shared-memory ring; A is read
+// reduction (stream-K when there are fewer tiles than SMs: every SM takes an equal share of all
+// the tiles' reduction stages).  A's tiles come through TMA into a 2-4 stage shared-memory ring; A is read
 // exactly once per column block.  Op N stages A K-major (TMA swizzled tiles).  Op H reads A along
 // its rows: for BF16 the MMA consumes the MN-major tile directly; for the 4-byte modes the tile is
 // loaded unswizzled and the worker warps transpose it into the K-major swizzled layout (splitting
 // it into hi / lo on the way for 3xTF32).
 // Warp roles: 0 = TMA producer, 1 = MMA issuer (owns TMEM), 2-3 = workers (hi/lo split and/or
-// transpose of A), 4-7 = epilogue (TMEM -> registers -> global, or split-K partial + last-CTA
-// reduction).
+// transpose of A), 4-7 = epilogue (TMEM -> registers -> global, or a stream-K partial + the
+// last piece's reduction).
 //
 // Precision modes: BF16 (kind::f16, A stored BF16, X rounded to BF16), TF32 (kind::tf32, one
 // product on FP32 data), TF32X3 (kind::tf32: A = A_hi + A_lo and X = X_hi + X_lo with
@@ -50,15 +51,14 @@ struct TcParams {
   CUtensorMap tmXlo[4];
   float* y[4];
   int64_t ldy;
-  float* part;              // split-K partial tiles
+  float* part;              // stream-K partial tiles (two slots per CTA)
   unsigned* counters;       // one arrival counter per output tile
   int64_t M;                // output rows
   int l;                    // valid output columns
   int nb;                   // output columns per CTA block
   int ncb;                  // column blocks
   int kiters;               // K stages in total
-  int kper;                 // K stages per split
-  int nsplit;
+  int mtiles;               // row tiles (the stream-K kernel's tile count is mtiles * ncb)
   int c_first;              // 1 for a pure quaternion A (plane 0 absent)
   uint32_t neg_mask;        // bit c*4+d set: negate the (c, d) product
   uint32_t idesc_base;
@@ -76,7 +76,7 @@ struct TcScalars {
   float* part;
   unsigned* counters;
   int64_t M;
-  int l, nb, ncb, kiters, kper, nsplit, c_first, stages;
+  int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
@@ -85,7 +85,7 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   TcScalars v;
   v.y0 = p.y[0]; v.y1 = p.y[1]; v.y2 = p.y[2]; v.y3 = p.y[3];
   v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
-  v.kiters = p.kiters; v.kper = p.kper; v.nsplit = p.nsplit; v.c_first = p.c_first; v.stages = p.stages;
+  v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
   return v;
 }
@@ -119,10 +119,18 @@ template <> struct Cfg<K_TF32X3> {   // 4-byte operands, 32 B swizzle, 8 K-eleme
 };
 
 // ---------------------------------------------------------------------------------------
-// One output tile: column block cb, row tile mt, reduction slice `split` (mtiles row tiles).
+// A contiguous piece of one output tile's reduction: stages [it0, it1).  A tile reduced in
+// nseg > 1 pieces (stream-K) has them from CTAs c0 .. c0 + nseg - 1; piece o writes its partial
+// to slot 2 (c0 + o) + (o == 0 ? b0 : 0) (b0 = 1 when the tile starts inside CTA c0's range, as
+// that CTA's second piece), and the last piece to arrive adds the partials in slot order.
+struct Seg {
+  int it0, it1, slot, nseg, c0, b0;
+  int more;   // another piece follows in this CTA: keep the right to allocate TMEM
+};
+
+// One output tile (column block cb, row tile mt) over the reduction piece sg.
 template <int KIND, int AMODE>
-__device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, const int mt, const int split,
-                                            const int mtiles) {
+__device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, const int mt, const Seg sg) {
   using C = Cfg<KIND>;
   const TcScalars pv = tc_scalars(p);
   constexpr bool X3 = (KIND == K_TF32X3);
@@ -154,8 +162,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t m0 = (int64_t)mt * TBM;
   const int j0 = cb * nb;
-  const int it0 = split * pv.kper;
-  const int it1 = min(pv.kiters, it0 + pv.kper);
+  const int it0 = sg.it0;
+  const int it1 = sg.it1;
   const int nit = it1 - it0;
 
   constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
@@ -181,7 +189,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(pv.tmem_cols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (!sg.more) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -335,8 +343,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     float v[16];
     if (ok && nit > 0) {
       for (int d = 0; d < 4; ++d) {
-        for (int cc = 0; cc < nb; cc += (pv.nsplit == 1 ? 32 : 16)) {
-          if (pv.nsplit == 1) {
+        for (int cc = 0; cc < nb; cc += (sg.nseg == 1 ? 32 : 16)) {
+          if (sg.nseg == 1) {
             // two loads in flight per wait (nb is a multiple of 16)
             uint32_t r0[16], r1[16];
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
@@ -355,19 +363,19 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
           }
           tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc), v);
           {
-            float* P = pv.part + ((size_t)split * mtiles * pv.ncb + tile) * tile_elems + (size_t)d * TBM * nb;
+            float* P = pv.part + (size_t)sg.slot * tile_elems + (size_t)d * TBM * nb;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) P[(size_t)(cc + jj) * TBM + row] = v[jj];
           }
         }
       }
     }
-    if (pv.nsplit > 1) {
+    if (sg.nseg > 1) {
       __threadfence();
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (threadIdx.x == 128) {
         const unsigned old = atomicAdd(&pv.counters[tile], 1u);
-        *last_flag = (old == (unsigned)(pv.nsplit - 1)) ? 1 : 0;
+        *last_flag = (old == (unsigned)(sg.nseg - 1)) ? 1 : 0;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (*last_flag) {
@@ -378,9 +386,9 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
               float acc[16];
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
-              for (int sp = 0; sp < pv.nsplit; ++sp) {
-                const float* P = pv.part + ((size_t)sp * mtiles * pv.ncb + tile) * tile_elems + (size_t)d * TBM * nb +
-                                 (size_t)jc0 * TBM + row;
+              for (int o = 0; o < sg.nseg; ++o) {
+                const int slot = 2 * (sg.c0 + o) + (o == 0 ? sg.b0 : 0);
+                const float* P = pv.part + (size_t)slot * tile_elems + (size_t)d * TBM * nb + (size_t)jc0 * TBM + row;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) acc[jj] += __ldcg(P + (size_t)jj * TBM);   // 16 loads in flight
               }
@@ -404,9 +412,38 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   }
 }
 
+// One CTA per output tile, the whole reduction.
 template <int KIND, int AMODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_constant__ TcParams p) {
-  sketch_tile<KIND, AMODE>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.y);
+  sketch_tile<KIND, AMODE>(p, blockIdx.x, blockIdx.y, Seg{0, p.kiters, 0, 1, 0, 0, 0});
+}
+
+// Stream-K: fewer output tiles than SMs.  The reduction stages of all tiles, taken in tile order,
+// are cut into gridDim.x equal ranges, one per CTA; a range covers the end of one tile and/or the
+// start of the next (gridDim.x > tiles), each piece is reduced as in sketch_tile and the pieces
+// of a tile are added by the last one to finish.
+template <int KIND, int AMODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const __grid_constant__ TcParams p) {
+  const int64_t K = p.kiters, W = (int64_t)p.mtiles * p.ncb * K, G = gridDim.x, c = blockIdx.x;
+  auto start = [&](int64_t cc) { return cc * W / G; };
+  // the CTA whose range holds stage x: the largest cc with start(cc) <= x
+  auto owner = [&](int64_t x) { return ((x + 1) * G + W - 1) / W - 1; };
+  int64_t pos = start(c);
+  const int64_t end = start(c + 1);
+  bool first = true;
+  while (pos < end) {
+    const int64_t t = pos / K;
+    const int it0 = (int)(pos - t * K);
+    const int it1 = (int)min(K, (int64_t)it0 + (end - pos));
+    const int64_t c0 = owner(t * K), c1 = owner((t + 1) * K - 1);
+    const int b0 = (start(c0) < t * K) ? 1 : 0;
+    const int more = (pos + (it1 - it0) < end) ? 1 : 0;
+    const Seg sg{it0, it1, (int)(2 * c + (c == c0 ? b0 : 0)), (int)(c1 - c0 + 1), (int)c0, b0, more};
+    if (!first) __syncthreads();
+    sketch_tile<KIND, AMODE>(p, (int)(t % p.ncb), (int)(t / p.ncb), sg);
+    first = false;
+    pos += it1 - it0;
+  }
 }
 
 // Grouped launch over many problems: CTA b computes the tile items[b] = (problem, row tile,
@@ -425,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const 
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&p.tmXlo[q]) : "memory");
     }
   }
-  sketch_tile<KIND, AMODE>(p, it.z, it.y, 0, 1);
+  sketch_tile<KIND, AMODE>(p, it.z, it.y, Seg{0, p.kiters, 0, 1, 0, 0, 0});
 }
 
 // Persistent grouped form: gridDim.x CTAs (one per SM) walk the item list, CTA b taking items
@@ -765,7 +802,8 @@ int kind_of(int compute) {
 }
 
 struct Plan {
-  int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, nsplit, kper, stages;
+  int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages;
+  int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
   uint32_t tmem_cols;
   size_t smem;
 };
@@ -782,11 +820,11 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
   pl.mtiles = (int)((M + TBM - 1) / TBM);
   pl.kiters = (int)((K + pl.bk - 1) / pl.bk);
-  const int ctas = pl.mtiles * pl.ncb;
-  int ns = std::max(1, num_sms / std::max(1, ctas));
-  ns = std::min(ns, std::max(1, pl.kiters / 8));
-  pl.kper = (pl.kiters + ns - 1) / ns;
-  pl.nsplit = (pl.kiters + pl.kper - 1) / pl.kper;
+  // fewer tiles than SMs: stream-K over every SM, each CTA at least 8 stages (a CTA's range then
+  // covers less than one tile, so at most two pieces)
+  const int64_t tiles = (int64_t)pl.mtiles * pl.ncb;
+  const int64_t g = std::min<int64_t>(num_sms, tiles * pl.kiters / 8);
+  pl.grid_sk = (g > tiles) ? (int)g : 0;
   const int cols = 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const bool x3 = pl.kind == K_TF32X3;
@@ -802,9 +840,14 @@ template <int KIND, int AMODE>
 int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm, int kid) {
   auto kern = sketch_tc_kernel<KIND, AMODE>;
   QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-  dim3 grid((unsigned)pl.ncb, (unsigned)pl.mtiles, (unsigned)pl.nsplit);
   KTimer kt(ctx, kid);
-  kern<<<grid, TC_THREADS, pl.smem, ctx->stream>>>(prm);
+  if (pl.grid_sk > 0) {
+    auto sk = sketch_tc_streamk_kernel<KIND, AMODE>;
+    QLR_CUDA_TRY(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    sk<<<pl.grid_sk, TC_THREADS, pl.smem, ctx->stream>>>(prm);
+  } else {
+    kern<<<dim3((unsigned)pl.ncb, (unsigned)pl.mtiles, 1u), TC_THREADS, pl.smem, ctx->stream>>>(prm);
+  }
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;
@@ -980,8 +1023,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     prm.nb = g.nb;
     prm.ncb = g.ncb;
     prm.kiters = g.kiters;
-    prm.kper = g.kiters;
-    prm.nsplit = 1;
+    prm.mtiles = g.mtiles;
     prm.neg_mask = neg;
     prm.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((base.amode == A_MN ? 1u : 0u) << 15) |
                      ((uint32_t)(g.nb >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
@@ -1070,7 +1112,7 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
 
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
   const int64_t ldo = (rows_in + 7) / 8 * 8;
-  return (size_t)2 * 4 * ldo * l * 4 + (size_t)(num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
+  return (size_t)2 * 4 * ldo * l * 4 + (size_t)2 * (num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
 }
 
 int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws) {
@@ -1091,7 +1133,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   void* xs = ws.take<char>((size_t)4 * ldo * l * xesz);
   void* xlo = (pl.kind == K_TF32X3) ? ws.take<char>((size_t)4 * ldo * l * 4) : nullptr;
   const size_t tile_elems = (size_t)4 * TBM * pl.nb;
-  float* part = pl.nsplit > 1 ? ws.take<float>((size_t)pl.nsplit * pl.mtiles * pl.ncb * tile_elems) : nullptr;
+  float* part = pl.grid_sk > 0 ? ws.take<float>((size_t)2 * pl.grid_sk * tile_elems) : nullptr;
   unsigned* counters = ws.take<unsigned>((size_t)pl.mtiles * pl.ncb);
   if (!ws.ok) return QLR_ENOMEM;
   if (X.dtype == QLR_BF16) {
@@ -1149,8 +1191,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.nb = pl.nb;
   prm.ncb = pl.ncb;
   prm.kiters = pl.kiters;
-  prm.kper = pl.kper;
-  prm.nsplit = pl.nsplit;
+  prm.mtiles = pl.mtiles;
   // sign table: op N: negative for (c,d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)}; op H flips c != 0
   uint32_t neg = 0;
   const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
