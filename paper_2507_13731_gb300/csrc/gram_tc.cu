@@ -17,11 +17,12 @@
 // The error of W(a, b) is about 2^-45 of max|y_a| max|y_b| m: FP64-class, as the Gram of the
 // double-FP32 SIMT path (orth.cu), at tensor-core throughput.
 //
-// Kernels: gram_slice_kernel (one warp per column: exponent, then the 8 slices, BF16, column-major
+// Kernels: gram_slice_kernel (one CTA per column: exponent, then the 8 slices, BF16, column-major
 // per slice with rows padded to a multiple of 8), gram_tc_kernel (one CTA per (128 x 64 tile of
-// W's upper part, 512-row chunk): TMA of the 8 slices of both operands into a 2-stage ring, 72
-// MMAs of 128 x 64 x 16 per 32-row stage into 8 x 64 TMEM columns, epilogue to double-FP32
-// partial tiles), gram_tc_combine_kernel (chunk sums, scaling, the quaternion components of G).
+// W's upper part, 512-row chunk): TMA of the 8 slices of both operands into a 4-stage ring of
+// 16-row stages, 36 MMAs of 128 x 64 x 16 per stage into 8 x 64 TMEM columns, epilogue to
+// double-FP32 partial tiles), gram_tc_combine_kernel (chunk sums, scaling, the quaternion
+// components of G).
 #include <algorithm>
 #include <cstring>
 
@@ -38,10 +39,12 @@ constexpr int GPAIR_MAX = 9;     // slice pairs (i, j), 1-based, with i + j <= 9
 constexpr int NGRP = GPAIR_MAX - 1;   // weights s = i + j - 2 = 0 .. 7
 constexpr int GA = 128;          // W rows per tile (MMA M)
 constexpr int GB = 64;           // W columns per tile (MMA N)
-constexpr int GK = 32;           // rows of Y per pipeline stage (64-byte swizzled BF16 rows)
+constexpr int GK = 16;           // rows of Y per pipeline stage (32-byte swizzled BF16 rows, one MMA K)
 constexpr int GCHUNK = 512;      // rows of Y per CTA (exactness of the TMEM sums)
-constexpr int GSTAGES = 2;
+constexpr int GSTAGES = 4;
 constexpr int GTHREADS = 256;
+constexpr int GSW = GK * 2;           // bytes per K-major row = swizzle span
+constexpr int GMODE = 6;              // descriptor swizzle mode: 32 bytes
 constexpr int A_TILE = GA * GK * 2;   // bytes of one slice's A tile
 constexpr int B_TILE = GB * GK * 2;
 constexpr int STAGE_BYTES = GS * (A_TILE + B_TILE);
@@ -70,31 +73,39 @@ struct GramTcProb {
   float* G;             // double-FP32 upper triangle, 8 floats per entry at G + 8 (j l + i)
 };
 
-// Columns 8 g .. 8 g + 7 of Yh (L4p columns, the padding zero), one warp per column: the
-// column exponent, then the 8 slices; each lane takes row pairs, stored as BF16 pairs.
-constexpr int SL_COLS = 8;
-
+// Columns of Yh (L4p columns, the padding zero) by CTAs of 8 warps, WPC warps per column (8 for
+// one tall problem, 1 for the many short ones of a batch): the column exponent, then the 8
+// slices; each lane takes row pairs, stored as BF16 pairs.
+template <int WPC>
 __device__ __forceinline__ void gram_slice_cols(const float* __restrict__ y0, const float* __restrict__ y1,
                                                 const float* __restrict__ y2, const float* __restrict__ y3, int64_t m,
                                                 int l, int64_t ld, int L4p, int64_t mp, __nv_bfloat16* __restrict__ S,
                                                 int* __restrict__ ex, const int g) {
+  __shared__ float red[8];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int c = g * SL_COLS + warp;
-  if (c >= L4p) return;
+  const int c = g * (8 / WPC) + warp / WPC, sub = warp % WPC;
+  const bool valid = c < L4p;
   const float* y = nullptr;
-  if (c < 4 * l) {
+  if (valid && c < 4 * l) {
     const int pl = c / l, j = c % l;
     y = (pl == 0 ? y0 : pl == 1 ? y1 : pl == 2 ? y2 : y3) + (int64_t)j * ld;
   }
   float mx = 0.f;
   if (y)
-    for (int64_t r = lane; r < m; r += 32) mx = fmaxf(mx, fabsf(y[r]));
+    for (int64_t r = sub * 32 + lane; r < m; r += 32 * WPC) mx = fmaxf(mx, fabsf(y[r]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (WPC > 1) {
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    const int w0 = warp - sub;
+    for (int w = 0; w < WPC; ++w) mx = fmaxf(mx, red[w0 + w]);
+  }
+  if (!valid) return;
   int e = 0;
   if (mx > 0.f) frexpf(mx, &e);   // max < 2^e
-  if (lane == 0) ex[c] = e;
-  for (int64_t r = 2 * lane; r < mp; r += 64) {   // mp is even
+  if (sub == 0 && lane == 0) ex[c] = e;
+  for (int64_t r = 2 * (sub * 32 + lane); r < mp; r += 64 * WPC) {   // mp is even
     float v0 = (y && r < m) ? ldexpf(y[r], GBITS - e) : 0.f;       // |v| < 64, exact
     float v1 = (y && r + 1 < m) ? ldexpf(y[r + 1], GBITS - e) : 0.f;
 #pragma unroll
@@ -111,7 +122,7 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const float* __restrict
                                                          const float* __restrict__ y2, const float* __restrict__ y3,
                                                          int64_t m, int l, int64_t ld, int L4p, int64_t mp,
                                                          __nv_bfloat16* __restrict__ S, int* __restrict__ ex) {
-  gram_slice_cols(y0, y1, y2, y3, m, l, ld, L4p, mp, S, ex, blockIdx.x);
+  gram_slice_cols<8>(y0, y1, y2, y3, m, l, ld, L4p, mp, S, ex, blockIdx.x);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
@@ -215,11 +226,11 @@ __device__ __forceinline__ void gram_tc_tile(const GramTcParams& p, int tl, cons
         for (int ks = 0; ks < GK / 16; ++ks) {
 #pragma unroll
           for (int qi = 0; qi < GS; ++qi) {
-            const uint64_t ad = make_desc(smem_u32(a_tile(s, qi)) + (uint32_t)(ks * 32), 16, 8 * 64, 4);
+            const uint64_t ad = make_desc(smem_u32(a_tile(s, qi)) + (uint32_t)(ks * 32), 16, 8 * GSW, GMODE);
 #pragma unroll
             for (int qj = 0; qj < GS; ++qj) {
               if (qi + qj > GPAIR_MAX - 2) continue;
-              const uint64_t bd = make_desc(smem_u32(b_tile(s, qj)) + (uint32_t)(ks * 32), 16, 8 * 64, 4);
+              const uint64_t bd = make_desc(smem_u32(b_tile(s, qj)) + (uint32_t)(ks * 32), 16, 8 * GSW, GMODE);
               // first product of weight group qi + qj in this chunk: qi == 0, first stage and k-step
               const uint32_t acc = (i > 0 || ks > 0 || qi > 0) ? 1u : 0u;
               umma_bf16(tmem + (uint32_t)((qi + qj) * GB), ad, bd, idesc, acc);
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(256) gram_slice_grouped_kernel(const GramTcPro
                                                                  const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GramTcProb& a = probs[it.x];
-  gram_slice_cols(a.y[0], a.y[1], a.y[2], a.y[3], a.m, a.l, a.ld, a.tc.L4p, a.mp, a.S, a.ex, it.y);
+  gram_slice_cols<1>(a.y[0], a.y[1], a.y[2], a.y[3], a.m, a.l, a.ld, a.tc.L4p, a.mp, a.S, a.ex, it.y);
 }
 
 // The quaternion Gram from W, FP64 planes: 16 threads per entry (i <= j), thread (c, d) forms
@@ -438,9 +449,9 @@ bool gram_tc_params(GramTcParams& prm, const GramTcDims& d, const GramTcBufs& bu
   memset(&prm, 0, sizeof(prm));
   const uint64_t cols = (uint64_t)GS * d.L4p;
   if (!encode_2d(&prm.tmA, bufs.S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GA,
-                 CU_TENSOR_MAP_SWIZZLE_64B) ||
+                 CU_TENSOR_MAP_SWIZZLE_32B) ||
       !encode_2d(&prm.tmB, bufs.S, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (uint64_t)d.mp, cols, (uint64_t)d.mp * 2, GK, GB,
-                 CU_TENSOR_MAP_SWIZZLE_64B))
+                 CU_TENSOR_MAP_SWIZZLE_32B))
     return false;
   prm.part = bufs.part;
   prm.L4 = d.L4;
@@ -486,7 +497,7 @@ int gram_tc(qlr_ctx* ctx, const qlr_qmat& Y, double* G, WsArena& ws) {
     return QLR_ECUDA;
   }
   KTimer kt(ctx, QLR_KID_GRAM);
-  gram_slice_kernel<<<(d.L4p + SL_COLS - 1) / SL_COLS, 256, 0, ctx->stream>>>(
+  gram_slice_kernel<<<d.L4p, 256, 0, ctx->stream>>>(
       static_cast<const float*>(Y.plane[0]), static_cast<const float*>(Y.plane[1]), static_cast<const float*>(Y.plane[2]),
       static_cast<const float*>(Y.plane[3]), m, l, Y.ld, d.L4p, d.mp, S, ex);
   qlr_count_launch();
@@ -528,7 +539,7 @@ int gram_tc_record(void* dst, const qlr_qmat& Y, char* scratch, float* G, int* e
 void gram_tc_grouped_items(int64_t m, int l, int prob, std::vector<int4>& slice, std::vector<int4>& mma,
                            std::vector<int4>& comb) {
   const GramTcDims d = gram_tc_dims(m, l);
-  for (int g = 0; g < (d.L4p + SL_COLS - 1) / SL_COLS; ++g) slice.push_back(make_int4(prob, g, 0, 0));
+  for (int g = 0; g < (d.L4p + 7) / 8; ++g) slice.push_back(make_int4(prob, g, 0, 0));
   for (int ch = 0; ch < d.nchunks; ++ch)
     for (int t = 0; t < d.ntiles; ++t) mma.push_back(make_int4(prob, t, ch, 0));
   for (int b = 0; b < (l * l + 127) / 128; ++b) comb.push_back(make_int4(prob, b, 0, 0));
