@@ -20,7 +20,7 @@
 // Kernels: gram_slice_kernel (one CTA per column: exponent, then the 8 slices, BF16, column-major
 // per slice with rows padded to a multiple of 8), gram_tc_kernel (one CTA per (128 x 64 tile of
 // W's upper part, 512-row chunk): TMA of the 8 slices of both operands into a 4-stage ring of
-// 16-row stages, 36 MMAs of 128 x 64 x 16 per stage into 8 x 64 TMEM columns, epilogue to
+// 16-row stages, 12 MMAs of 128 x (64..256) x 16 per stage into 8 x 64 TMEM columns, epilogue to
 // double-FP32 partial tiles), gram_tc_combine_kernel (chunk sums, scaling, the quaternion
 // components of G).
 #include <algorithm>
@@ -213,8 +213,10 @@ __device__ __forceinline__ void gram_tc_tile(const GramTcParams& p, int tl, cons
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      // BF16 A and B, FP32 D, both K-major, N = GB, M = GA
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GB >> 3) << 17) | ((uint32_t)(GA >> 4) << 24);
+      // BF16 A and B, FP32 D, both K-major, M = GA; N = t GB for t consecutive B slices: the B
+      // slice tiles are adjacent in shared memory, and one MMA of A_i against slices j .. j+t-1
+      // writes pair (i, j + u) to TMEM columns (i + j + u) GB, the accumulator of its weight group
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GA >> 4) << 24);
       bool ok = true;
       for (int i = 0; i < nit && ok; ++i) {
         const int s = i % GSTAGES;
@@ -228,10 +230,11 @@ __device__ __forceinline__ void gram_tc_tile(const GramTcParams& p, int tl, cons
           for (int qi = 0; qi < GS; ++qi) {
             const uint64_t ad = make_desc(smem_u32(a_tile(s, qi)) + (uint32_t)(ks * 32), 16, 8 * GSW, GMODE);
 #pragma unroll
-            for (int qj = 0; qj < GS; ++qj) {
-              if (qi + qj > GPAIR_MAX - 2) continue;
+            for (int qj = 0; qj <= GPAIR_MAX - 2 - qi; qj += 4) {
+              const int t = min(4, GPAIR_MAX - 1 - qi - qj);   // slices qj .. qj + t - 1
               const uint64_t bd = make_desc(smem_u32(b_tile(s, qj)) + (uint32_t)(ks * 32), 16, 8 * GSW, GMODE);
-              // first product of weight group qi + qj in this chunk: qi == 0, first stage and k-step
+              const uint32_t idesc = idesc0 | ((uint32_t)((t * GB) >> 3) << 17);
+              // first products of the weight groups in this chunk: qi == 0, first stage and k-step
               const uint32_t acc = (i > 0 || ks > 0 || qi > 0) ? 1u : 0u;
               umma_bf16(tmem + (uint32_t)((qi + qj) * GB), ad, bd, idesc, acc);
             }
