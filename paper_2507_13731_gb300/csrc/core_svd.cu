@@ -526,11 +526,9 @@ __global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const doubl
             if (i < l) W[c * ll + (size_t)g * l + i] = col(c, lc)[i];
           }
       }
-      __threadfence();
-      cluster.sync();
+      cluster.sync();   // arrive.release / wait.acquire at cluster scope: W's columns visible to all CTAs
     }
     if (t == 0 && s_rot) atomicOr(&flags[sweep], 1);
-    __threadfence();
     cluster.sync();
     converged = (*(volatile int*)&flags[sweep] == 0);
     cluster.sync();
