@@ -80,7 +80,7 @@ extern "C" int qlr_qsketch_noalloc(void* stream, int op, const qlr_qmat* A, cons
   ctx.d_err = err;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QLR_ECUDA;
-  // Fewer split-K slices need fewer partial tiles: shrink the split budget until the scratch fits.
+  // Fewer stream-K CTAs need fewer partial tiles: shrink the CTA budget until the scratch fits.
   int budget = sms;
   while (budget > 1 && qlr::sketch_tc_ws(inner, X->cols, budget) > QLR_NOALLOC_SCRATCH_BYTES) budget /= 2;
   if (qlr::sketch_tc_ws(inner, X->cols, budget) > QLR_NOALLOC_SCRATCH_BYTES) return QLR_ENOMEM;
