@@ -255,7 +255,7 @@ size_t lowrank_ws(int64_t m, int64_t n, int k, int p, int v, int algo, int compu
   b += (size_t)4 * esz * (rows + 4) * l;         // omega conversion
   b += (size_t)32 * L * L * 2 + (size_t)64 * L * k + 8 * k;
   b += cholqr_ws_bound(rows, L, esz) + tsvd_ws_bound(L);
-  b += qlr::sketch_tc_ws(rows, L, 160);           // tensor-core operand staging + split-K partials
+  b += qlr::sketch_tc_ws(rows, L, 160);           // tensor-core operand staging + stream-K partials
   return b + ((size_t)4 << 20);
 }
 

@@ -8,7 +8,7 @@
 // file-scope device array that the CUDA module carries, so the call itself allocates nothing.
 //
 // The scratch array is shared by every call on a device and keeps the last call's contents; the
-// parts that must start at zero (the split-K arrival counters) are cleared on the stream by each
+// parts that must start at zero (the stream-K arrival counters) are cleared on the stream by each
 // call.  Calls that overlap on the GPU (different streams, or another thread's call in flight)
 // race on the array.
 #include <mutex>
