@@ -618,20 +618,38 @@ __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw,
     const int ns = (int)((nst - ch * RCH < (size_t)RCH) ? nst - ch * RCH : (size_t)RCH);
     if (active) {
       for (int st = 0; st < ns; ++st) {
-        for (int k = lane; k < cap; k += 32) {
-          T r[REC];
-          ld_rec(lb + ((size_t)st * cap + k) * REC, r);
-          const T sn = r[3];
-          if (sn == (T)0) continue;
-          const int pp = (int)r[0], qq = (int)r[1];
-          const T c = r[2];
-          const Quat<T> mu = {r[4], r[5], r[6], r[7]};
-          const Quat<T> vp = {vr[pp], vr[l + pp], vr[2 * l + pp], vr[3 * l + pp]};
-          const Quat<T> vq = qmulc(Quat<T>{vr[qq], vr[l + qq], vr[2 * l + qq], vr[3 * l + qq]}, mu);
-          vr[pp] = c * vp.w - sn * vq.w; vr[l + pp] = c * vp.x - sn * vq.x; vr[2 * l + pp] = c * vp.y - sn * vq.y;
-          vr[3 * l + pp] = c * vp.z - sn * vq.z;
-          vr[qq] = sn * vp.w + c * vq.w; vr[l + qq] = sn * vp.x + c * vq.x; vr[2 * l + qq] = sn * vp.y + c * vq.y;
-          vr[3 * l + qq] = sn * vp.z + c * vq.z;
+        // two records per lane and iteration, loaded and applied side by side (a stage's pairs are
+        // disjoint, so the two rotations touch different entries of the row)
+        for (int k0 = 0; k0 < cap; k0 += 64) {
+          T r[2][REC];
+          int pp[2], qq[2];
+          bool on[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = k0 + 32 * h + lane;
+            if (k < cap) ld_rec(lb + ((size_t)st * cap + k) * REC, r[h]);
+            else r[h][3] = (T)0;
+            on[h] = (r[h][3] != (T)0);
+            pp[h] = on[h] ? (int)r[h][0] : 0;
+            qq[h] = on[h] ? (int)r[h][1] : 0;
+          }
+          Quat<T> vp[2], vq[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            vp[h] = {vr[pp[h]], vr[l + pp[h]], vr[2 * l + pp[h]], vr[3 * l + pp[h]]};
+            vq[h] = {vr[qq[h]], vr[l + qq[h]], vr[2 * l + qq[h]], vr[3 * l + qq[h]]};
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            const T c = r[h][2], sn = r[h][3];
+            const Quat<T> q = qmulc(vq[h], Quat<T>{r[h][4], r[h][5], r[h][6], r[h][7]});
+            const int a = pp[h], b = qq[h];
+            vr[a] = c * vp[h].w - sn * q.w; vr[l + a] = c * vp[h].x - sn * q.x; vr[2 * l + a] = c * vp[h].y - sn * q.y;
+            vr[3 * l + a] = c * vp[h].z - sn * q.z;
+            vr[b] = sn * vp[h].w + c * q.w; vr[l + b] = sn * vp[h].x + c * q.x; vr[2 * l + b] = sn * vp[h].y + c * q.y;
+            vr[3 * l + b] = sn * vp[h].z + c * q.z;
+          }
         }
         __syncwarp();
       }
