@@ -60,27 +60,8 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
     }
     __syncthreads();
     if (row_ok) {
-      // T's rows PF at a time: their loads are issued before the products that use them (PF = 4
-      // for 8 columns per CTA; 16 columns already give each load 16 products)
-      constexpr int PF = (COLS <= 8) ? 4 : 1;
-      int kk = 0;
-      for (; kk + PF <= kn; kk += PF) {
-        Quat<float> a[PF];
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          const int64_t o = (int64_t)(k0 + kk + u) * lda;
-          a[u] = {a0[o], a1[o], a2[o], a3[o]};
-        }
-#pragma unroll
-        for (int u = 0; u < PF; ++u)
-#pragma unroll
-          for (int jj = 0; jj < COLS; ++jj) {
-            const float4 b = Bs[kk + u][jj];
-            const Quat<float> p = qmul(a[u], Quat<float>{b.x, b.y, b.z, b.w});
-            acc[jj].w += p.w; acc[jj].x += p.x; acc[jj].y += p.y; acc[jj].z += p.z;
-          }
-      }
-      for (; kk < kn; ++kk) {
+#pragma unroll 2
+      for (int kk = 0; kk < kn; ++kk) {
         const int64_t o = (int64_t)(k0 + kk) * lda;
         const Quat<float> a = {a0[o], a1[o], a2[o], a3[o]};
 #pragma unroll
