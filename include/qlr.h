@@ -63,8 +63,10 @@ extern "C" {
 #define QLR_OP_H 1 /* Y = A^H X   */
 
 /* ---- algorithm / side / orthonormalisation choices ------------------------------------- */
-#define QLR_ALG2 2 /* Algorithm 2 (arbitrary number of passes)              */
-#define QLR_ALG4 4 /* Algorithm 4 (flexible block Krylov, arbitrary views)  */
+#define QLR_ALG1 1 /* Algorithm 1 (classical power scheme, q = passes/2 - 1; passes even)     */
+#define QLR_ALG2 2 /* Algorithm 2 (arbitrary number of passes)                                */
+#define QLR_ALG3 3 /* Algorithm 3 (classical block Krylov, q = passes/2 - 1; passes even)     */
+#define QLR_ALG4 4 /* Algorithm 4 (flexible block Krylov, arbitrary views)                    */
 #define QLR_SIDE_AUTO (-1)
 #define QLR_SIDE_X 0
 #define QLR_SIDE_XH 1
@@ -199,6 +201,11 @@ int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, 
  * qlr_qsvd_lowrank -- rank-k approximation A ~= U diag(S) V^H by Algorithm 2 (algo = QLR_ALG2)
  * or Algorithm 4 (QLR_ALG4, with block width l = k + p) with exactly `passes` passes over A,
  * followed by the truncated QSVD of the last R and the lifts V = Q2 V_hat, U = Q1 U_hat.
+ * QLR_ALG1 and QLR_ALG3 (the classical power scheme and block Krylov method with q power steps,
+ * 2q + 2 passes; `passes` must be even, else QLR_ESHAPE) give, for the same Omega, the result of
+ * Algorithm 2 and Algorithm 4 with that number of passes -- Section 3 shows Algorithm 2 with
+ * v = 2q + 2 is Algorithm 1, and for even v Algorithm 4's stacked basis spans Algorithm 3's Krylov
+ * matrix (Section 5) -- and run those schedules, with a QR after every product.
  * U: m x k, V: n x k, column-major, F32 or F64; S: device FP64 array of k values, descending.
  * The call leaves the result defined up to a right unit-quaternion factor per column pair.
  */

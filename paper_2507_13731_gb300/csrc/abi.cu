@@ -239,7 +239,7 @@ int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
 }
 
 int64_t stacked_width(int algo, int l, int v) {
-  if (algo != QLR_ALG4) return l;
+  if (algo != QLR_ALG4 && algo != QLR_ALG3) return l;
   return (int64_t)((v % 2 == 0) ? v / 2 : (v - 1) / 2) * l;
 }
 
@@ -518,12 +518,31 @@ int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, 
   return QLR_OK;
 }
 
-static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo, const qlr_qmat* omega,
-                        const qlr_opts* opts, qlr_qmat* U, double* S_out, qlr_qmat* V) {
+// Algorithms 1 and 3 take 2q + 2 passes and, for the same Omega, give the results of Algorithm 2
+// and Algorithm 4 with that (even) number of passes (Sections 3 and 5): they run those schedules
+// with a QR after every product, as the classical methods orthonormalise every power step.
+static int canonical_algo(int algo, int passes, const qlr_opts* opts, int& algo_out, qlr_opts& o) {
+  o = opts ? *opts : qlr_opts{QLR_COMPUTE_AUTO, QLR_SIDE_AUTO, QLR_ORTH_CHOLQR2, 0};
+  if (algo == QLR_ALG2 || algo == QLR_ALG4) {
+    algo_out = algo;
+    return QLR_OK;
+  }
+  if (algo != QLR_ALG1 && algo != QLR_ALG3) return QLR_EINVAL;
+  if (passes < 2 || passes % 2 != 0) return QLR_ESHAPE;
+  algo_out = (algo == QLR_ALG1) ? QLR_ALG2 : QLR_ALG4;
+  o.flags |= QLR_FLAG_QR_EVERY_PASS;
+  return QLR_OK;
+}
+
+static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo_in,
+                        const qlr_qmat* omega, const qlr_opts* opts_in, qlr_qmat* U, double* S_out, qlr_qmat* V) {
+  int algo = QLR_ALG2;
+  qlr_opts opts_c;
+  QLR_TRY(canonical_algo(algo_in, passes, opts_in, algo, opts_c));
+  const qlr_opts* opts = &opts_c;
   int compute, side;
   bool autoc;
   QLR_TRY(prepare(ctx, A, k, p, passes, omega, opts, compute, side, autoc));
-  if (algo != QLR_ALG2 && algo != QLR_ALG4) return QLR_EINVAL;
   QLR_TRY(check_qmat(U, QLR_COL_MAJOR, false));
   QLR_TRY(check_qmat(V, QLR_COL_MAJOR, false));
   if (!S_out) return QLR_EINVAL;

@@ -26,7 +26,7 @@ F64, F32, BF16 = 0, 1, 2
 ROW_MAJOR, COL_MAJOR = 0, 1
 COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16 = range(6)
 OP_N, OP_H = 0, 1
-ALG2, ALG4 = 2, 4
+ALG1, ALG2, ALG3, ALG4 = 1, 2, 3, 4
 SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
 ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
 FLAG_QR_EVERY_PASS = 1

@@ -73,6 +73,28 @@ def test_qr_every_pass_flag(ctx, algo, v):
         np.testing.assert_allclose(_proj(host(U)[:, :, :8]), _proj(ref.U[:, :, :8]), atol=1e-8)
 
 
+@pytest.mark.parametrize("algo,q", [("alg1", 0), ("alg1", 1), ("alg1", 2), ("alg3", 1), ("alg3", 2)])
+def test_classical_algorithms_match_oracle(ctx, algo, q):
+    """QLR_ALG1 / QLR_ALG3 with 2q + 2 passes against the oracle's Algorithm 1 (power scheme, a QR
+    after every product) and Algorithm 3 (one QR of the stacked Krylov matrix, full SVD of Q^H X)
+    on the same Omega: singular values to 1e-9, rank-8 subspaces to 1e-8.  An odd pass count is
+    rejected with QLR_ESHAPE."""
+    from paper_2507_13731_gb300 import qlr
+    v = 2 * q + 2
+    P = synth.config_slow_decay(300, 220, 12, 6, v, seed=31 + q)
+    a = qlr.ALG1 if algo == "alg1" else qlr.ALG3
+    U, S, V, Om, Ad = run_gpu(ctx, P, v, a, "f64", qlr.COMPUTE_F64)
+    ref = (al.alg1_classical if algo == "alg1" else al.alg3_block_classical)(P.A, P.k, P.p, q, Om)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-9)
+    np.testing.assert_allclose(_proj(U[:, :, :8]), _proj(ref.U[:, :, :8]), atol=1e-8)
+    np.testing.assert_allclose(_proj(V[:, :, :8]), _proj(ref.V[:, :, :8]), atol=1e-8)
+    Od = dev_thin(Om, "f64")
+    Ub, Vb = qlr.empty_thin(P.m, P.k, torch.float64), qlr.empty_thin(P.n, P.k, torch.float64)
+    Sb = torch.zeros(P.k, dtype=torch.float64, device="cuda")
+    with pytest.raises(qlr.QlrError):
+        qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, v + 1, Od, Ub, Sb, Vb, algo=a, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X)
+
+
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 6])
 def test_alg4_fp64_small(ctx, v):
     from paper_2507_13731_gb300 import qlr
