@@ -496,8 +496,9 @@ def main():
             "metric": METRIC, "value": round(value, 3), "unit": "sketch passes/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"TF32X3": "f32 (3xTF32 tensor-core sketch, FP64 Gram/Cholesky)", "F32": "f32 (SIMT)",
-                      "BF16": "bf16 (FP32 accumulate, FP64 Gram/Cholesky)", "TF32": "tf32"}[args.compute],
+            "dtype": {"TF32X3": "f32 (3xTF32 tensor-core sketch; FP64-class Gram (exact BF16 slices on tensor cores) "
+                                "and Cholesky (double-FP32))", "F32": "f32 (SIMT)",
+                      "BF16": "bf16 (FP32 accumulate; FP64-class Gram and Cholesky)", "TF32": "tf32"}[args.compute],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "passes": list(PASSES), "compute": args.compute,
                        "l2": "inputs larger than L2 (A = %.0f MB)" % (a_bytes / 1e6), "parallelism": f"replicas x{ws}"},
