@@ -70,7 +70,7 @@ extern "C" {
 #define QLR_SIDE_AUTO (-1)
 #define QLR_SIDE_X 0
 #define QLR_SIDE_XH 1
-#define QLR_ORTH_CHOLQR2 0  /* CholeskyQR2, FP64 Gram and Cholesky                    */
+#define QLR_ORTH_CHOLQR2 0  /* CholeskyQR2, FP64-class Gram and Cholesky              */
 #define QLR_ORTH_SCHOLQR3 1 /* shifted CholeskyQR3 (Fukaya et al. 2020) for ill-conditioned input */
 /* opts.flags bit: run opts.orth at every pass, as Algorithms 2 and 4 write it.  Without it, a basis
  * that only feeds the next pass (Algorithm 2's passes 1..v-2, the blocks Algorithm 4 stacks or
@@ -124,7 +124,7 @@ const char* qlr_strerror(int code);
  * the number of launches and the summed event time in milliseconds since the last reset. */
 #define QLR_KID_SKETCH_TC 0   /* tcgen05 sketch product                     */
 #define QLR_KID_SKETCH_SIMT 1 /* SIMT sketch product / thin GEMMs           */
-#define QLR_KID_GRAM 2        /* FP64 Gram (partials + reduction)           */
+#define QLR_KID_GRAM 2        /* FP64-class Gram (slices / partials, combine) */
 #define QLR_KID_CHOL 3        /* quaternion Cholesky                         */
 #define QLR_KID_TRIINV 4      /* triangular inverse                          */
 #define QLR_KID_APPLY 5       /* Q = Y R^{-1}, lifts, projections            */
@@ -150,8 +150,11 @@ int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
 int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute);
 
 /*
- * qlr_qgram -- G = Y^H Y in FP64 (the Gram step of CholeskyQR; the "QR" of Algorithms 1-4,
- * Def. 1 eq. QQR).  Y: m x l column-major F32 or F64.  G: device, FP64, l x l x 4 planes,
+ * qlr_qgram -- G = Y^H Y with FP64-class accuracy (the Gram step of CholeskyQR; the "QR" of
+ * Algorithms 1-4, Def. 1 eq. QQR).  F64 Y: FP64 arithmetic.  F32 Y: on the tensor cores by an
+ * exact splitting of every column into 6-bit BF16 slices below its largest entry (error about
+ * 2^-45 of max|y_i| max|y_j| m), or, when the workspace cannot hold the slices, double-FP32 sums
+ * on the FP32 pipes.  Y: m x l column-major F32 or F64.  G: device, FP64, l x l x 4 planes,
  * column-major (G[c*l*l + j*l + i]), full Hermitian matrix written.
  */
 int qlr_qgram(qlr_ctx* ctx, const qlr_qmat* Y, double* G);
