@@ -1177,16 +1177,23 @@ __global__ void __launch_bounds__(256) tri_inv_blocked_kernel(const double* __re
 // upper triangular and real diagonal; (I + F)^H (I + F) = I + E is equivalent to
 // F = Phi(E - F^H F), Phi(X) = strict upper part of X plus half its (real) diagonal, a fixed point
 // reached by iterating from F = Phi(E) (the error shrinks like |E|^(n+1)).  The inverse is
-// (I + F)^{-1} = I - F + F^2 - ..., evaluated as X <- I - F X.  Each step is a triangular product
-// spread over all SMs in FP64 -- no serial pivots.  Both iterations contract with rate of order
-// |E|, so a step whose predecessor changed no entry by more than SERIES_TOL (far below the FP64
-// resolution of I + F) only copies its input forward.  The init kernel raises `use_chol` when
-// l * max|E_ij| exceeds SERIES_MAX; the blocked Cholesky kernels then run instead (they are
-// predicated on that flag, so no host synchronisation is needed).
+// (I + F)^{-1} = I + D with D = -F - F D (the Neumann series I - F + F^2 - ...), iterated from
+// D = 0.  Each step is a triangular product spread over all SMs -- no serial pivots.  Both
+// iterations contract with rate of order |E|, so a step whose predecessor changed no entry by
+// more than SERIES_TOL (far below the FP64 resolution of I + F) only copies its input forward.
+// The init kernel raises `use_chol` when l * max|E_ij| exceeds SERIES_MAX; the blocked Cholesky
+// kernels then run instead (they are predicated on that flag, so no host synchronisation is
+// needed).
+//
+// Both products, F^H F and F D, are products of two matrices of order |E|, and their sums are
+// subtracted from E (or -F) in FP64.  For FP32 sketches they are accumulated in FP32 (TAcc =
+// float): the absolute error is of order l |E|^2 2^-24 (below 4e-15 at the SERIES_MAX limit,
+// under the 2^-45-class error of the Gram itself), and the steps stop being FP64-bound.  FP64
+// sketches accumulate in FP64.
 constexpr double SERIES_MAX = 5e-3;
 constexpr double SERIES_TOL = 1e-18;
 constexpr int SERIES_ITERS = 6, NEUMANN_ITERS = 7;
-constexpr int SPLIT = 16;   // lanes per entry: FP64 sums as short per-lane chains plus a shuffle tree
+constexpr int SPLIT = 16;   // lanes per entry: sums as short per-lane chains plus a shuffle tree
 
 __global__ void series_init_kernel(const double* __restrict__ G, double* __restrict__ E, double* __restrict__ F, int l,
                                    unsigned long long* __restrict__ emax_bits) {
@@ -1209,21 +1216,30 @@ __global__ void series_decide_kernel(const unsigned long long* __restrict__ emax
   *use_chol = (!(emax * l <= SERIES_MAX)) ? 1 : 0;
 }
 
+template <class TA>
+__device__ __forceinline__ Quat<TA> ld_small_as(const double* M, int l, int i, int j) {
+  const Quat<double> q = ld_small(M, l, i, j);
+  return {(TA)q.w, (TA)q.x, (TA)q.y, (TA)q.z};
+}
+
 // out(i, j) for i <= j with SPLIT threads per entry:
 //   mode 0 (series):  Phi(E - F^H F)(i, j),  (F^H F)_ij = sum_{t <= i} conj(F_ti) F_tj
-//   mode 1 (Neumann): delta_ij - (F X)_ij,     (F X)_ij  = sum_{i <= t <= j} F_it X_tj
-// The largest change against the step's input (F in mode 0, X in mode 1) goes to *delta; when
-// the previous step's change *prev_delta is at most SERIES_TOL the input is copied unchanged.
+//   mode 1 (Neumann): (-F - F D)_ij,          (F D)_ij  = sum_{i <= t <= j} F_it D_tj
+// The largest change against the step's
+// input (F in mode 0, D in mode 1) goes to *delta; when the previous step's change *prev_delta is
+// at most SERIES_TOL the input is copied unchanged.  `add_identity` stores I + out (the last
+// Neumann step writes R2^{-1} = I + D).
+template <class TA>
 __global__ void __launch_bounds__(128) series_step_kernel(const double* __restrict__ E, const double* __restrict__ F,
-                                                           const double* __restrict__ X, double* __restrict__ out, int l,
-                                                           int mode, int nentries,
+                                                           const double* __restrict__ D, double* __restrict__ out, int l,
+                                                           int mode, int nentries, int add_identity,
                                                            const unsigned long long* __restrict__ prev_delta,
                                                            unsigned long long* __restrict__ delta) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ent = gt / SPLIT;
   const int part = (int)(gt % SPLIT);
   const bool valid = ent < nentries;
-  const double* in = (mode == 0) ? F : X;
+  const double* in = (mode == 0) ? F : D;
   int i = 0, j = 0;
   if (valid) {
     const int2 ij = upper_tri_entry((int)ent);
@@ -1231,21 +1247,25 @@ __global__ void __launch_bounds__(128) series_step_kernel(const double* __restri
     j = ij.y;
   }
   if (prev_delta && __longlong_as_double((long long)*prev_delta) <= SERIES_TOL) {
-    if (valid && part == 0) st_small(out, l, i, j, ld_small(in, l, i, j));
+    if (valid && part == 0) {
+      Quat<double> o = ld_small(in, l, i, j);
+      if (add_identity && i == j) o.w += 1.0;
+      st_small(out, l, i, j, o);
+    }
     return;
   }
-  Quat<double> acc = {0, 0, 0, 0};
+  Quat<TA> acc = {0, 0, 0, 0};
   if (valid) {
     if (mode == 0) {
 #pragma unroll 4
       for (int t = part; t <= i; t += SPLIT) {
-        Quat<double> pr = qcmul(ld_small(F, l, t, i), ld_small(F, l, t, j));
+        Quat<TA> pr = qcmul(ld_small_as<TA>(F, l, t, i), ld_small_as<TA>(F, l, t, j));
         acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
       }
     } else {
 #pragma unroll 4
       for (int t = i + part; t <= j; t += SPLIT) {
-        Quat<double> pr = qmul(ld_small(F, l, i, t), ld_small(X, l, t, j));
+        Quat<TA> pr = qmul(ld_small_as<TA>(F, l, i, t), ld_small_as<TA>(D, l, t, j));
         acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
       }
     }
@@ -1261,14 +1281,16 @@ __global__ void __launch_bounds__(128) series_step_kernel(const double* __restri
   if (valid && part == 0) {
     Quat<double> r;
     if (mode == 0) {
-      Quat<double> e = ld_small(E, l, i, j);
-      if (i < j) r = {e.w - acc.w, e.x - acc.x, e.y - acc.y, e.z - acc.z};
-      else r = {0.5 * (e.w - acc.w), 0.0, 0.0, 0.0};
+      const Quat<double> e = ld_small(E, l, i, j);
+      if (i < j) r = {e.w - (double)acc.w, e.x - (double)acc.x, e.y - (double)acc.y, e.z - (double)acc.z};
+      else r = {0.5 * (e.w - (double)acc.w), 0.0, 0.0, 0.0};
     } else {
-      r = {(i == j ? 1.0 : 0.0) - acc.w, -acc.x, -acc.y, -acc.z};
+      const Quat<double> f = ld_small(F, l, i, j);
+      r = {-f.w - (double)acc.w, -f.x - (double)acc.x, -f.y - (double)acc.y, -f.z - (double)acc.z};
     }
     const Quat<double> o = ld_small(in, l, i, j);
     ch = fmax(fmax(fabs(r.w - o.w), fabs(r.x - o.x)), fmax(fabs(r.y - o.y), fabs(r.z - o.z)));
+    if (add_identity && i == j) r.w += 1.0;
     st_small(out, l, i, j, r);
   }
   // warp maximum, one atomic per warp (non-negative doubles order like their bit patterns)
@@ -1285,13 +1307,6 @@ __global__ void series_form_kernel(const double* __restrict__ F, double* __restr
   Quat<double> f = (i <= j) ? ld_small(F, l, i, j) : Quat<double>{0, 0, 0, 0};
   if (i == j) f.w += 1.0;
   st_small(R2, l, i, j, f);
-}
-
-__global__ void fill_identity_kernel(double* __restrict__ X, int l) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)l * l) return;
-  const int i = (int)(idx % l), j = (int)(idx / l);
-  st_small(X, l, i, j, {i == j ? 1.0 : 0.0, 0.0, 0.0, 0.0});
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1733,8 +1748,9 @@ static int apply_rinv(qlr_ctx* ctx, const qlr_qmat& Y, const double* Rinv, qlr_q
 
 // Cholesky factor R2 = I + F of a near-identity Gram matrix G and its inverse by series; sets
 // *use_chol_out to a device flag that is non-zero when G is too far from I for the series.
+// f32acc: accumulate the small products in FP32 (Grams of FP32 sketches).
 static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, double* R2inv, WsArena& ws,
-                         int** use_chol_out) {
+                         int** use_chol_out, bool f32acc) {
   const size_t ll4 = (size_t)4 * l * l;
   double* E = ws.take<double>(ll4);
   double* Fa = ws.take<double>(ll4);
@@ -1755,24 +1771,25 @@ static int series_factor(qlr_ctx* ctx, int l, const double* G, double* R2, doubl
   qlr_count_launch();
   series_decide_kernel<<<1, 1, 0, ctx->stream>>>(emax, l, use_chol);
   qlr_count_launch();
+  auto step = f32acc ? series_step_kernel<float> : series_step_kernel<double>;
   double* Fc = Fa;
   double* Fn = Fb;
   for (int it = 0; it < SERIES_ITERS; ++it) {
-    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, nent, it ? deltas + it - 1 : nullptr,
-                                                     deltas + it);
+    step<<<gst, 128, 0, ctx->stream>>>(E, Fc, nullptr, Fn, l, 0, nent, 0, it ? deltas + it - 1 : nullptr, deltas + it);
     qlr_count_launch();
     std::swap(Fc, Fn);
   }
   series_form_kernel<<<gsq, 128, 0, ctx->stream>>>(Fc, R2, l);
   qlr_count_launch();
-  fill_identity_kernel<<<gsq, 128, 0, ctx->stream>>>(Xa, l);
-  qlr_count_launch();
+  // the Neumann iteration runs on D = X - I from D = 0; its last step writes I + D
+  QLR_CUDA_TRY(cudaMemsetAsync(Xa, 0, ll4 * sizeof(double), ctx->stream));
   double* Xc = Xa;
   double* Xn = Xb;
   unsigned long long* nd = deltas + SERIES_ITERS;
   for (int it = 0; it < NEUMANN_ITERS; ++it) {
-    series_step_kernel<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, (it == NEUMANN_ITERS - 1) ? R2inv : Xn, l, 1, nent,
-                                                     it ? nd + it - 1 : nullptr, nd + it);
+    const bool last = (it == NEUMANN_ITERS - 1);
+    step<<<gst, 128, 0, ctx->stream>>>(nullptr, Fc, Xc, last ? R2inv : Xn, l, 1, nent, last ? 1 : 0,
+                                       it ? nd + it - 1 : nullptr, nd + it);
     qlr_count_launch();
     std::swap(Xc, Xn);
   }
@@ -1822,7 +1839,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
     QLR_TRY(gram(ctx, src, G, ws));
     if (s == 1 && orth == QLR_ORTH_CHOLQR2) {
       int* use_chol = nullptr;
-      QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol));
+      QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol, df));
       QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol, df));     // only if the series test failed
       QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, use_chol));
     } else {
