@@ -22,8 +22,9 @@ size_t gram_ws_bound(int64_t rows, int64_t l) {
 }
 
 size_t cholqr_ws_bound(int64_t rows, int64_t l, size_t esz) {
+  // + the double-FP32 copies of R and the diagonal-block inverses (FP32 sketches)
   return (size_t)12 * 32 * l * l + (size_t)8 * l * l + (size_t)4 * (rows + 4) * l * esz + (size_t)16 * l * l +
-         gram_ws_bound(rows, l) + 16 * 256;
+         gram_ws_bound(rows, l) + (size_t)32 * l * l + (size_t)8 * 1024 * ((l + 15) / 16) + 17 * 256;
 }
 
 size_t tsvd_ws_bound(int64_t l) { return core_tsvd_ws((int)l) + 16384; }

@@ -1362,6 +1362,131 @@ __device__ __forceinline__ void dq_fms_conj(DQ& w, const DQ& a, const DQ& b) {
 
 __device__ __forceinline__ Quat<float> q_of(const float4& v) { return {v.x, v.y, v.z, v.w}; }
 
+// s + e += a b for double-FP32 quaternions a = ah + al, b = bh + bl (Hamilton product, eq. 1),
+// components (real, i, j, k) at indices 0..3.
+__device__ __forceinline__ void dq_mul_acc(float (&s)[4], float (&e)[4], const float (&ah)[4], const float (&al)[4],
+                                           const float (&bh)[4], const float (&bl)[4]) {
+  d32_acc(s[0], e[0], ah[0], al[0], bh[0], bl[0]); d32_acc(s[0], e[0], -ah[1], -al[1], bh[1], bl[1]);
+  d32_acc(s[0], e[0], -ah[2], -al[2], bh[2], bl[2]); d32_acc(s[0], e[0], -ah[3], -al[3], bh[3], bl[3]);
+  d32_acc(s[1], e[1], ah[0], al[0], bh[1], bl[1]); d32_acc(s[1], e[1], ah[1], al[1], bh[0], bl[0]);
+  d32_acc(s[1], e[1], ah[2], al[2], bh[3], bl[3]); d32_acc(s[1], e[1], -ah[3], -al[3], bh[2], bl[2]);
+  d32_acc(s[2], e[2], ah[0], al[0], bh[2], bl[2]); d32_acc(s[2], e[2], -ah[1], -al[1], bh[3], bl[3]);
+  d32_acc(s[2], e[2], ah[2], al[2], bh[0], bl[0]); d32_acc(s[2], e[2], ah[3], al[3], bh[1], bl[1]);
+  d32_acc(s[3], e[3], ah[0], al[0], bh[3], bl[3]); d32_acc(s[3], e[3], ah[1], al[1], bh[2], bl[2]);
+  d32_acc(s[3], e[3], -ah[2], -al[2], bh[1], bl[1]); d32_acc(s[3], e[3], ah[3], al[3], bh[0], bl[0]);
+}
+
+// Renormalise the four (s, e) sums and add them over the 16 lanes of a half-warp (all 32 lanes
+// of the warp take part in the shuffles).
+__device__ __forceinline__ void dq_halfwarp_sum(const float (&s)[4], const float (&e)[4], d32 (&v)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) d32_renorm(s[c], e[c], v[c].h, v[c].l);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const d32 w = {__shfl_xor_sync(0xffffffffu, v[c].h, o), __shfl_xor_sync(0xffffffffu, v[c].l, o)};
+      v[c] = d32_add(v[c], w);
+    }
+  }
+}
+
+// FP64 values split into double-FP32 pairs: hi = fl32(x), lo = fl32(x - hi), for two arrays in
+// one launch (a triangular factor and its diagonal-block inverses).
+__global__ void split_d32_kernel(const double* __restrict__ a, float* __restrict__ ah, float* __restrict__ al, int64_t na,
+                                 const double* __restrict__ b, float* __restrict__ bh, float* __restrict__ bl, int64_t nb,
+                                 const int* run_if) {
+  if (run_if && *run_if == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (i < na) ? a[i] : b[i - na];
+    const float h = __double2float_rn(x);
+    const float lo = __double2float_rn(x - (double)h);
+    if (i < na) { ah[i] = h; al[i] = lo; } else { bh[i - na] = h; bl[i - na] = lo; }
+  }
+}
+
+// Double-FP32 form of tri_inv_blocked_kernel (same block back substitution, same lane layout) for
+// the factors of FP32 sketches' Grams, whose Cholesky already ran in double-FP32: R and the
+// diagonal-block inverses come as high/low FP32 planes, every product is an exact FMA product
+// summed by two-sums, so no FP64 instruction issues in the loops (the FP64 form is bound by the
+// FP64 pipe's few DFMA per clock per SM).
+__global__ void __launch_bounds__(256) tri_inv_blocked_df_kernel(const float* __restrict__ Rh, const float* __restrict__ Rl,
+                                                                  const float* __restrict__ Dh, const float* __restrict__ Dl,
+                                                                  double* __restrict__ X, int l, const int* run_if) {
+  if (run_if && *run_if == 0) return;
+  extern __shared__ float xsf[];          // 8 * l: high parts of the four planes of x, then low parts
+  float* xh = xsf;
+  float* xl = xsf + 4 * l;
+  __shared__ float th[4][CB], tl[4][CB];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const size_t ll = (size_t)l * l;
+  const int J = j / CB;
+  const int r = t >> 4, ch = t & 15;      // 16 rows x 16 lanes = 256 threads
+  for (int i = t; i < 4 * l; i += blockDim.x) xh[i] = xl[i] = 0.f;
+  __syncthreads();
+  {   // x_J = Dinv_J[:, j - J*CB]
+    const int bJ = min(CB, l - J * CB), jj = j - J * CB;
+    const size_t base = (size_t)J * 4 * CB * CB;
+    const size_t bb = (size_t)bJ * bJ;
+    if (t < bJ && t <= jj) {
+      const size_t o = base + (size_t)jj * bJ + t;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        xh[c * l + J * CB + t] = Dh[o + c * bb];
+        xl[c * l + J * CB + t] = Dl[o + c * bb];
+      }
+    }
+  }
+  __syncthreads();
+  for (int I = J - 1; I >= 0; --I) {
+    const int i0 = I * CB, q0 = (I + 1) * CB;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = q0 + ch; q <= j; q += 16) {
+      const size_t o = (size_t)q * l + i0 + r;
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        ah[c] = Rh[c * ll + o]; al[c] = Rl[c * ll + o];
+        bh[c] = xh[c * l + q]; bl[c] = xl[c * l + q];
+      }
+      dq_mul_acc(s, e, ah, al, bh, bl);
+    }
+    d32 v[4];
+    dq_halfwarp_sum(s, e, v);
+    if (ch == 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { th[c][r] = v[c].h; tl[c][r] = v[c].l; }
+    }
+    __syncthreads();
+    // x_I[r] = -sum_{q >= r} Dinv_I[r][q] T[q]: lane (r, q)
+    {
+      const size_t base = (size_t)I * 4 * CB * CB;
+      const size_t bb = (size_t)CB * CB;
+      const int q = ch;
+      float s2[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+      if (q >= r) {
+        const size_t o = base + (size_t)q * CB + r;
+        float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          ah[c] = Dh[o + c * bb]; al[c] = Dl[o + c * bb];
+          bh[c] = th[c][q]; bl[c] = tl[c][q];
+        }
+        dq_mul_acc(s2, e2, ah, al, bh, bl);
+      }
+      d32 w[4];
+      dq_halfwarp_sum(s2, e2, w);
+      if (ch == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { xh[c * l + i0 + r] = -w[c].h; xl[c * l + i0 + r] = -w[c].l; }
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < l; i += blockDim.x)
+    for (int c = 0; c < 4; ++c) X[c * ll + (size_t)j * l + i] = (double)xh[c * l + i] + (double)xl[c * l + i];
+}
+
 // One CTA per problem: the whole quaternion Cholesky factorisation of G (+ shift I) in
 // double-FP32, right-looking over the packed upper triangle in shared memory (column k at offset
 // k (k + 1) / 2), with the rank-1 updates' entries enumerated densely over all threads.  Then,
@@ -1713,11 +1838,26 @@ int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_coef, WsA
   return QLR_OK;
 }
 
-int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all, const int* run_if) {
+int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all, const int* run_if,
+            float* d32buf) {
   if (l == 0) return QLR_OK;
   KTimer kt(ctx, QLR_KID_TRIINV);
   const size_t smem = (size_t)4 * l * sizeof(double);
-  if (Dinv_all) {
+  if (Dinv_all && d32buf) {
+    const int64_t nr = (int64_t)4 * l * l;
+    const int64_t nd = (int64_t)((l + CB - 1) / CB) * 4 * CB * CB;
+    float* Rh = d32buf;
+    float* Rl = Rh + nr;
+    float* Dh = Rl + nr;
+    float* Dl = Dh + nd;
+    const unsigned gs = (unsigned)std::min<int64_t>((nr + nd + 255) / 256, 1024);
+    split_d32_kernel<<<gs, 256, 0, ctx->stream>>>(R, Rh, Rl, nr, Dinv_all, Dh, Dl, nd, run_if);
+    qlr_count_launch();
+    // 8 l floats: the same bytes as the FP64 form's 4 l doubles
+    QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_blocked_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tri_inv_blocked_df_kernel<<<l, 256, smem, ctx->stream>>>(Rh, Rl, Dh, Dl, Rinv, l, run_if);
+    qlr_count_launch();
+  } else if (Dinv_all) {
     // static shared memory comes on top of the dynamic size: always opt in
     QLR_CUDA_TRY(cudaFuncSetAttribute(tri_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tri_inv_blocked_kernel<<<l, 256, smem, ctx->stream>>>(R, Dinv_all, Rinv, l, run_if);
@@ -1811,6 +1951,9 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
   double* P2 = ws.take<double>(ll4);
   double* Rinv = ws.take<double>(ll4);
   double* Dinv_all = ws.take<double>((size_t)((l + CB - 1) / CB) * 4 * CB * CB);
+  // double-FP32 copies of R and Dinv for the triangular inverse of FP32 sketches' factors
+  float* d32buf = (Y.dtype == QLR_F32) ? ws.take<float>(2 * ((size_t)4 * l * l + (size_t)((l + CB - 1) / CB) * 4 * CB * CB))
+                                       : nullptr;
   const int64_t tld = (m + 3) / 4 * 4;   // 16-byte multiple pitch (tensor-core thin products)
   char* tbuf = ws.take<char>((size_t)4 * tld * l * esz);
   if (!ws.ok) return QLR_ENOMEM;
@@ -1841,10 +1984,10 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
       int* use_chol = nullptr;
       QLR_TRY(series_factor(ctx, l, G, Rcur, Rinv, ws, &use_chol, df));
       QLR_TRY(chol(ctx, l, G, Rcur, 0.0, ws, Dinv_all, use_chol, df));     // only if the series test failed
-      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, use_chol));
+      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, use_chol, d32buf));
     } else {
       QLR_TRY(chol(ctx, l, G, Rcur, (s == 0) ? shift : 0.0, ws, Dinv_all, nullptr, df));
-      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all));
+      QLR_TRY(tri_inv(ctx, l, Rcur, Rinv, Dinv_all, nullptr, d32buf));
     }
     QLR_TRY(apply_rinv(ctx, src, Rinv, dst, ws));
     if (s > 0) {   // R_total <- R_s * R_total

@@ -210,8 +210,10 @@ int gram_tc_grouped(qlr_ctx* ctx, const void* d_probs, const int4* slice, int n_
                     const int4* comb, int n_comb);
 int chol(qlr_ctx* ctx, int l, const double* G, double* R, double shift_rel, WsArena& ws, double* Dinv_all = nullptr,
          const int* run_if = nullptr, bool df = false);
+// d32buf (2 (4 l^2 + ceil(l/16) 4 16^2) floats, or null): run the double-FP32 form of the blocked
+// inverse (factors of FP32 sketches' Grams); null runs it in FP64.
 int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Dinv_all = nullptr,
-            const int* run_if = nullptr);
+            const int* run_if = nullptr, float* d32buf = nullptr);
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
 
