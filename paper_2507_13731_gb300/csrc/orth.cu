@@ -1,7 +1,8 @@
 // Orthonormalisation of thin quaternion sketches: the "QR" step after every pass of
 // Algorithms 1-4 (Def. 1, eq. QQR).  CholeskyQR2: G = Y^H Y and R1 = chol(G) in FP64-class
 // arithmetic (FP64 for FP64 sketches; for FP32 sketches the tensor-core Gram of gram_tc.cu and a
-// double-FP32 Cholesky), Q' = Y R1^{-1}, then once more on Q'; R = R2 R1.  Shifted CholeskyQR3 (Fukaya, Kannan,
+// double-FP32 Cholesky and triangular inverse), Q' = Y R1^{-1}, then once more on Q' (where Q'^H Q'
+// is close to I, the second factor and its inverse come from a series); R = R2 R1.  Shifted CholeskyQR3 (Fukaya, Kannan,
 // Nakatsukasa, Zhang and Yamamoto, SISC 2020) adds s I to the first Gram matrix so the
 // Cholesky factorisation exists for ill-conditioned input (Algorithm 4's stacked basis).
 #include <cooperative_groups.h>
