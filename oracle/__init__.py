@@ -17,9 +17,11 @@ The oracle is plain, slow and written to be checked against the paper by eye:
                     theorems bound.
 * ``bounds``      -- the expected-error bounds of Lemma 1, Theorem 3 (eqs. mn11/mn12),
                     Lemma 4 / Corollary 5 and Theorem 6.
+* ``completion``  -- quaternion matrix completion by the alternating updates of Section 7
+                    (eqs. Step1 and Step2) around a rank-k approximation.
 
 Every floating-point step runs in float64.  Where a function is only checked against itself
 it says "parity unpinned" in its docstring; all functions here are pinned by the tests in
 ``tests/test_oracle_*.py``.
 """
-from . import quaternion, qr, qsvd, algorithms, norms, bounds  # noqa: F401
+from . import quaternion, qr, qsvd, algorithms, norms, bounds, completion  # noqa: F401

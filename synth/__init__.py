@@ -30,7 +30,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 _CHUNK = 1 << 22
 
 # stream tags (one independent stream per use)
-TAG_LEFT, TAG_RIGHT, TAG_PHASE_U, TAG_PHASE_V, TAG_NOISE, TAG_OMEGA, TAG_SIZES, TAG_FIELD = range(1, 9)
+TAG_LEFT, TAG_RIGHT, TAG_PHASE_U, TAG_PHASE_V, TAG_NOISE, TAG_OMEGA, TAG_SIZES, TAG_FIELD, TAG_MASK = range(1, 10)
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -85,7 +85,7 @@ def gaussian_qmat(seed: int, rows: int, cols: int, real_only: bool = False) -> n
     """Gaussian quaternion matrix (Def. 2): four iid N(0,1) planes, plane-major column-major fill.
 
     With real_only=True only plane 0 is drawn (the real-Gaussian test matrix the experiments
-    of Section 7 use); the other planes are zero.
+    of Section 8 use); the other planes are zero.
     """
     nplanes = 1 if real_only else 4
     g = gaussian(seed, nplanes * rows * cols).reshape(nplanes, cols, rows).transpose(0, 2, 1)
@@ -323,3 +323,27 @@ def batched_problems(count: int = 512, seed: int = 1238, mmin: int = 64, mmax: i
         out.append(Problem(f"batch{i}", A, r, ell - r, v, omega_for(s, n, ell), pure=True,
                            extra={"rank": r}))
     return out
+
+
+def completion_problem(m: int, n: int, rank: int, missing: float = 0.7, seed: int = 1239, noise: float = 0.0,
+                       k: Optional[int] = None, p: int = 10, v: int = 2) -> Problem:
+    """Matrix-completion input (Section 7): M, a pure quaternion matrix of exact rank `rank`
+    (a real Gaussian m x rank matrix times a pure Gaussian quaternion rank x n matrix, scaled to
+    unit RMS over the i, j, k planes) plus iid N(0, noise^2) on the i, j, k planes, and a 0/1
+    observation mask (uint8, m x n, 1 = observed) that removes each entry independently with
+    probability `missing` (a uniform below `missing` removes it).  Stands in for the paper's
+    colour images with 70 % of the pixels removed uniformly at random (Section 8).  k defaults to
+    `rank`; Omega is n x (k + p).  The mask is in extra["mask"]."""
+    k = rank if k is None else k
+    B = gaussian(stream_seed(seed, TAG_LEFT), m * rank).reshape(rank, m).T
+    C = gaussian(stream_seed(seed, TAG_RIGHT), 3 * rank * n).reshape(3, n, rank).transpose(0, 2, 1)
+    A = np.zeros((4, m, n))
+    for c in range(3):
+        A[c + 1] = B @ C[c]
+    A /= math.sqrt(float((A[1:] ** 2).mean()))
+    if noise > 0.0:
+        A[1:] += noise * gaussian(stream_seed(seed, TAG_NOISE), 3 * m * n).reshape(3, n, m).transpose(0, 2, 1)
+    u = uniform(stream_seed(seed, TAG_MASK), m * n).reshape(m, n)
+    mask = (u >= missing).astype(np.uint8)
+    return Problem(f"complete{m}x{n}r{rank}", A, k, p, v, omega_for(seed, n, k + p), pure=True,
+                   extra={"mask": mask, "rank": rank, "missing": missing})
