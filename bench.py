@@ -226,6 +226,75 @@ def batched_leg(dev, steps=5):
             "device_error": rc}
 
 
+COMPLETE_M = COMPLETE_N = 4096
+COMPLETE_K, COMPLETE_P, COMPLETE_ITERS = 30, 10, 20
+COMPLETE_WORKLOAD = ("matrix completion: 4096x4096 pure quaternion matrix of rank 30 plus N(0,(1e-2)^2) noise on the "
+                     "i,j,k planes, FP32 planes, 70% of the entries removed uniformly at random, k=30, p=10, "
+                     "Algorithm 2 with v=2 per iteration, 20 alternating updates from P_Omega(M) (the paper's colour "
+                     "images with 70% of the pixels removed, R=30, two passes, scaled up)")
+
+
+def completion_problem():
+    import synth
+    return synth.completion_problem(COMPLETE_M, COMPLETE_N, COMPLETE_K, missing=0.7, seed=1240, noise=1e-2,
+                                    k=COMPLETE_K, p=COMPLETE_P)
+
+
+def completion_leg(dev, steps=5):
+    """Matrix completion (Section 7): one qlr_qcomplete call of COMPLETE_ITERS alternating updates
+    (after one warm-up call), the masked update kernel alone (`steps` launches; M and C together
+    exceed L2) and the completed matrix's error on the removed entries."""
+    import numpy as np
+    import torch
+
+    from paper_2507_13731_gb300 import qlr
+    P = completion_problem()
+    m, n, k = P.m, P.n, P.k
+    ctx = qlr.Context(dev.index or 0)
+    mask = torch.from_numpy(P.extra["mask"]).to(dev)
+    Md = torch.from_numpy(np.ascontiguousarray(P.A[1:])).float().to(dev)
+    Cd = torch.empty(4, m, n, dtype=torch.float32, device=dev)
+    Ud, Vd = qlr.empty_thin(m, k, device=dev), qlr.empty_thin(n, k, device=dev)
+    Sd = torch.zeros(k, dtype=torch.float64, device=dev)
+    Od = qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev))
+    qlr.complete(ctx, Md, mask, k, P.p, 2, 1, Od, Cd, Ud, Sd, Vd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qlr.complete(ctx, Md, mask, k, P.p, 2, COMPLETE_ITERS, Od, Cd, Ud, Sd, Vd)
+    e1.record()
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    rc = ctx.sync()
+    miss = P.extra["mask"] == 0
+    C = Cd.cpu().double().numpy()
+    err = float(np.sqrt(((C - P.A)[:, miss] ** 2).sum() / (P.A[:, miss] ** 2).sum()))
+    for _ in range(3):
+        qlr.complete_update(ctx, Md, mask, Cd, Ud, Sd, Vd, k)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        qlr.complete_update(ctx, Md, mask, Cd, Ud, Sd, Vd, k)
+    e1.record()
+    torch.cuda.synchronize()
+    up_ms = e0.elapsed_time(e1) / steps
+    rc = rc or ctx.sync()
+    ctx.close()
+    flops = 32.0 * m * n * k
+    obs = float(P.extra["mask"].mean())
+    nbytes = m * n * (1 + 16 + 12 * obs)           # mask, C written, M read at observed entries
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ach = flops / (up_ms / 1e3) / 1e12
+    return {"workload": COMPLETE_WORKLOAD, "iters": COMPLETE_ITERS, "ms_total": round(total_ms, 3),
+            "ms_per_iter": round(total_ms / COMPLETE_ITERS, 3), "unobserved_rel_err": round(err, 6),
+            "update_kernel": {"ms": round(up_ms, 4), "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
+                              "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                              "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                              "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                              "hbm_gbs": round(nbytes / (up_ms / 1e3) / 1e9, 1)},
+            "device_error": rc}
+
+
 def max_over_ranks(x: float, ws: int, device=None) -> float:
     """The largest of the ranks' values (the whole job is as slow as its slowest replica)."""
     if ws <= 1:
@@ -317,6 +386,38 @@ def batch_driver(args):
     return 0 if rc == 0 else 1
 
 
+def complete_driver(args):
+    """--only complete: the completion workload's masked update kernel, `warmup + steps` launches."""
+    import numpy as np
+    import torch
+
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    P = completion_problem()
+    m, n, k = P.m, P.n, P.k
+    ctx = qlr.Context(0)
+    mask = torch.from_numpy(P.extra["mask"]).cuda()
+    Md = torch.from_numpy(np.ascontiguousarray(P.A[1:])).float().cuda()
+    Cd = torch.empty(4, m, n, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    Ud = qlr.to_thin(torch.from_numpy(rng.standard_normal((4, m, k))).float().cuda())
+    Vd = qlr.to_thin(torch.from_numpy(rng.standard_normal((4, n, k))).float().cuda())
+    Sd = torch.ones(k, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        qlr.complete_update(ctx, Md, mask, Cd, Ud, Sd, Vd, k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        qlr.complete_update(ctx, Md, mask, Cd, Ud, Sd, Vd, k)
+    e1.record()
+    torch.cuda.synchronize()
+    rc = ctx.sync()
+    print(json.dumps({"only": "complete", "ms_per_call": e0.elapsed_time(e1) / args.steps, "device_error": rc}),
+          flush=True)
+    ctx.close()
+    return 0 if rc == 0 else 1
+
+
 def profile_driver(args):
     """Small driver for ncu captures: the bench workload's A and Omega, then `warmup + steps`
     calls of one sketch pass (--only sketch --op N|H) or one QSVD with --passes v (--only qsvd).
@@ -326,6 +427,8 @@ def profile_driver(args):
 
     if args.only == "batch":
         return batch_driver(args)
+    if args.only == "complete":
+        return complete_driver(args)
 
     import synth
     from paper_2507_13731_gb300 import build, qlr
@@ -371,7 +474,8 @@ def main():
     ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
-    ap.add_argument("--only", choices=["sketch", "qsvd", "batch"], default=None,
+    ap.add_argument("--no-completion", action="store_true", help="skip the matrix-completion leg")
+    ap.add_argument("--only", choices=["sketch", "qsvd", "batch", "complete"], default=None,
                     help="profiling driver: time only sketch passes, single QSVDs or batch runs (for ncu captures)")
     ap.add_argument("--op", choices=["N", "H"], default="N")
     ap.add_argument("--passes", type=int, default=4)
@@ -488,6 +592,12 @@ def main():
         batched = None
         if ws == 1 and not args.no_batched:
             batched = batched_leg(dev)
+        completion = None
+        if ws == 1 and not args.no_completion:
+            try:
+                completion = completion_leg(dev)
+            except Exception as e:                 # reported, never fatal to the headline line
+                completion = {"error": f"{type(e).__name__}: {e}"}
         if ws == 1 and not args.no_cpu_baseline:
             val, secs, thr = cpu_oracle_sample(P)
             cpu = {"value": round(val, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
@@ -510,6 +620,7 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
             "batched": batched,
+            "completion": completion,
             "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in stats.items() if n},
             "clocks": clk,
             "device_error": rc,

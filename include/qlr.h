@@ -132,7 +132,8 @@ const char* qlr_strerror(int code);
 #define QLR_KID_REFINE 7      /* core QSVD FP64 evaluation + ranking         */
 #define QLR_KID_MISC 8        /* conversions, operand staging, small products */
 #define QLR_KID_SERIES 9      /* CholeskyQR2 second step by series (factor and inverse) */
-#define QLR_KID_COUNT 10
+#define QLR_KID_COMPLETE 10   /* matrix completion: masked low-rank update   */
+#define QLR_KID_COUNT 11
 int qlr_set_timing(qlr_ctx* ctx, int enable);
 int qlr_reset_stats(qlr_ctx* ctx);
 int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
@@ -281,6 +282,38 @@ int qlr_batch_destroy(qlr_batch* b);
  */
 int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start,
                       int iters, double* out);
+
+/*
+ * qlr_qcomplete_update -- the masked update of quaternion matrix completion (Section 7, eq. Step2):
+ * C = mask .* M + (1 - mask) .* (U diag(S) V^H), mask the 0/1 pattern of observed entries.
+ * M, C: m x n row-major, one dtype (F32 or F64); M may be pure (plane[0] == NULL: zero real part);
+ * C needs all four planes and may be M itself (in place: only observed entries of M are read,
+ * each by the thread that writes it).  mask: device uint8, m x n row-major with row stride
+ * mask_ld >= n, non-zero = observed.  U: m x k and V: n x k column-major in the dtype of C (only
+ * their first k columns are read); S: device FP64, k values.  k = 0 (U, S, V may be NULL) writes
+ * the starting point P_Omega(M), zero at the unobserved entries.  The rank-k product is formed
+ * tile by tile in registers (FP32 for F32, FP64 for F64) and never stored.
+ * Errors: QLR_EINVAL (null pointers, layouts, dtypes), QLR_ESHAPE (sizes, k < 0),
+ * QLR_EUNSUPPORTED (more than 65535 * 32 rows).
+ */
+int qlr_qcomplete_update(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t mask_ld, const qlr_qmat* U,
+                         const double* S, const qlr_qmat* V, int k, qlr_qmat* C);
+
+/*
+ * qlr_qcomplete -- quaternion matrix completion by alternating updates (Section 7, eqs. Step1 and
+ * Step2): C = P_Omega(M), then `iters` times X = U diag(S) V^H, the rank-k approximation of C by
+ * qlr_qsvd_lowrank(C, k, p, passes, algo, omega, opts), and C = mask .* M + (1 - mask) .* X.
+ * Arguments as qlr_qcomplete_update and qlr_qsvd_lowrank, with C in the role of A (row-major; a
+ * row pitch that is a multiple of 16 bytes lets the sketches run on the tensor cores) and U, V in
+ * C's dtype.  The paper starts from no stated C; this call starts from P_Omega(M).  The same omega
+ * serves every iteration.  On return C holds the last update and U, S, V the factors of the last
+ * X.  The Gaussian smoothing the paper applies to images after each iteration is image
+ * post-processing outside the operator and is not applied.
+ * Errors: as the two calls; QLR_ESHAPE for iters < 1.
+ */
+int qlr_qcomplete(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t mask_ld, int k, int p, int passes,
+                  int algo, int iters, const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* C, qlr_qmat* U,
+                  double* S, qlr_qmat* V);
 
 /*
  * qlr_qsketch_noalloc -- the tensor-core sketch product of qlr_qsketch (same op, operands, layouts

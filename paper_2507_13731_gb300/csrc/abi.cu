@@ -591,6 +591,64 @@ int qlr_qblock_krylov(qlr_ctx* ctx, const qlr_qmat* A, int k, int b, int passes,
   return lowrank_impl(ctx, A, k, b - k, passes, QLR_ALG4, omega, opts, U, S, V);
 }
 
+// Checks of the masked completion update's operands (k = 0: U, S, V unused).
+static int complete_args(const qlr_qmat* M, const uint8_t* mask, int64_t mask_ld, const qlr_qmat* U, const double* S,
+                         const qlr_qmat* V, int k, const qlr_qmat* C, qlr::CompleteArgs& a) {
+  QLR_TRY(check_qmat(M, QLR_ROW_MAJOR, true));
+  QLR_TRY(check_qmat(C, QLR_ROW_MAJOR, false));
+  if (M->dtype != C->dtype || (C->dtype != QLR_F32 && C->dtype != QLR_F64)) return QLR_EINVAL;
+  if (M->rows != C->rows || M->cols != C->cols || k < 0) return QLR_ESHAPE;
+  if (!mask && C->rows > 0 && C->cols > 0) return QLR_EINVAL;
+  if (mask_ld < std::max<int64_t>(1, C->cols)) return QLR_ESHAPE;
+  a = qlr::CompleteArgs{};
+  if (k > 0) {
+    QLR_TRY(check_qmat(U, QLR_COL_MAJOR, false));
+    QLR_TRY(check_qmat(V, QLR_COL_MAJOR, false));
+    if (!S) return QLR_EINVAL;
+    if (U->dtype != C->dtype || V->dtype != C->dtype) return QLR_EINVAL;
+    if (U->rows != C->rows || V->rows != C->cols || U->cols < k || V->cols < k) return QLR_ESHAPE;
+    for (int c = 0; c < 4; ++c) { a.U[c] = U->plane[c]; a.V[c] = V->plane[c]; }
+    a.ldu = U->ld;
+    a.ldv = V->ld;
+    a.S = S;
+  }
+  for (int c = 0; c < 4; ++c) { a.M[c] = M->plane[c]; a.C[c] = C->plane[c]; }
+  a.ldm = M->ld;
+  a.ldc = C->ld;
+  a.mask = mask;
+  a.ldk = mask_ld;
+  a.m = C->rows;
+  a.n = C->cols;
+  a.k = k;
+  return QLR_OK;
+}
+
+int qlr_qcomplete_update(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t mask_ld, const qlr_qmat* U,
+                         const double* S, const qlr_qmat* V, int k, qlr_qmat* C) {
+  if (!ctx) return QLR_EINVAL;
+  qlr::CompleteArgs a;
+  QLR_TRY(complete_args(M, mask, mask_ld, U, S, V, k, C, a));
+  DeviceGuard g(ctx->device);
+  return qlr::complete_update(ctx, a, C->dtype);
+}
+
+int qlr_qcomplete(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t mask_ld, int k, int p, int passes,
+                  int algo, int iters, const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* C, qlr_qmat* U,
+                  double* S, qlr_qmat* V) {
+  if (!ctx) return QLR_EINVAL;
+  if (iters < 1 || k < 1) return QLR_ESHAPE;
+  qlr::CompleteArgs start, update;
+  QLR_TRY(complete_args(M, mask, mask_ld, nullptr, nullptr, nullptr, 0, C, start));
+  QLR_TRY(complete_args(M, mask, mask_ld, U, S, V, k, C, update));
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr::complete_update(ctx, start, C->dtype));                        // C = P_Omega(M)
+  for (int it = 0; it < iters; ++it) {
+    QLR_TRY(lowrank_impl(ctx, C, k, p, passes, algo, omega, opts, U, S, V));   // eq. Step1
+    QLR_TRY(qlr::complete_update(ctx, update, C->dtype));                     // eq. Step2
+  }
+  return QLR_OK;
+}
+
 int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
                              const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V) {
   if (!ctx || count < 0 || (count > 0 && (!A || !k || !p || !omega || !U || !S || !V))) return QLR_EINVAL;

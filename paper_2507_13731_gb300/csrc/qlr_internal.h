@@ -217,6 +217,25 @@ int tri_inv(qlr_ctx* ctx, int l, const double* R, double* Rinv, const double* Di
 int small_matmul(qlr_ctx* ctx, int l, const double* A, const double* B, double* C);  // C = A B (upper-tri A, B)
 int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, WsArena& ws);
 
+// Masked update of matrix completion (complete.cu, Section 7 eq. Step2):
+// C = mask .* M + (1 - mask) .* U diag(S) V^H, entries in the dtype of C (F32 or F64).
+struct CompleteArgs {
+  const void* M[4];      // row-major m x n; M[0] null for a pure M
+  int64_t ldm;
+  const uint8_t* mask;   // row-major m x n, non-zero = observed
+  int64_t ldk;
+  const void* U[4];      // column-major m x k
+  int64_t ldu;
+  const double* S;       // k values
+  const void* V[4];      // column-major n x k
+  int64_t ldv;
+  void* C[4];            // row-major m x n (may alias M)
+  int64_t ldc;
+  int64_t m, n;
+  int k;
+};
+int complete_update(qlr_ctx* ctx, const CompleteArgs& a, int dtype);
+
 // Grouped steps of batch plans: one launch runs one step for every problem of a plan, the
 // per-problem arguments and the (problem, tile) items of each launch in device tables built once
 // by the plan.  The small operands are FP32 / double-FP32 (no FP64 instruction on this path).

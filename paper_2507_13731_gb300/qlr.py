@@ -33,7 +33,8 @@ FLAG_QR_EVERY_PASS = 1
 FLAG_NO_GRAPH = 2
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
-KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series"]
+KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series",
+             "complete"]
 
 
 class QlrError(RuntimeError):
@@ -90,6 +91,8 @@ def lib():
             "qlr_qsvd_lowrank_batched": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
                                              ctypes.POINTER(P), Q]),
             "qlr_residual_norm": (I, [P, Q, Q, I, Q, I, ctypes.POINTER(D)]),
+            "qlr_qcomplete_update": (I, [P, Q, P, I64, Q, P, Q, I, Q]),
+            "qlr_qcomplete": (I, [P, Q, P, I64, I, I, I, I, I, Q, O, Q, Q, P, Q]),
             "qlr_set_timing": (I, [P, I]),
             "qlr_reset_stats": (I, [P]),
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
@@ -292,6 +295,39 @@ def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE
                                    ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
            "qlr_qblock_krylov")
     return U, S, V
+
+
+def _mask(mask: torch.Tensor, rows: int, cols: int):
+    """Device uint8 observation mask (rows x cols, row-major, unit column stride): pointer, row stride."""
+    if mask.dtype != torch.uint8 or mask.dim() != 2 or tuple(mask.shape) != (rows, cols):
+        raise ValueError("the mask is a (rows, cols) uint8 tensor")
+    if cols > 1 and mask.stride(1) != 1:
+        raise ValueError("the mask must be row-major with a unit column stride")
+    return ctypes.c_void_p(mask.data_ptr()), max(mask.stride(0) if rows > 1 else cols, cols, 1)
+
+
+def complete_update(ctx: Context, M, mask, C, U=None, S=None, V=None, k: int = 0):
+    """C = mask .* M + (1 - mask) .* U[:, :k] diag(S) V[:, :k]^H (eq. Step2); k = 0 gives P_Omega(M)."""
+    m, c = _A(M), _A(C)
+    mp, ml = _mask(mask, C.shape[1], C.shape[2])
+    u = ctypes.byref(_T(U)) if U is not None else None
+    v = ctypes.byref(_T(V)) if V is not None else None
+    sp = ctypes.c_void_p(S.data_ptr()) if S is not None else None
+    _check(lib().qlr_qcomplete_update(ctx.h, ctypes.byref(m), mp, ml, u, sp, v, k, ctypes.byref(c)),
+           "qlr_qcomplete_update")
+    return C
+
+
+def complete(ctx: Context, M, mask, k, p, passes, iters, omega, C, U, S, V, algo=ALG2, compute=COMPUTE_AUTO,
+             side=SIDE_AUTO, orth=ORTH_CHOLQR2):
+    """Matrix completion by alternating updates (eqs. Step1, Step2) from C = P_Omega(M)."""
+    m, c, om, u, v = _A(M), _A(C), _T(omega), _T(U), _T(V)
+    mp, ml = _mask(mask, C.shape[1], C.shape[2])
+    o = _opts(compute, side, orth)
+    _check(lib().qlr_qcomplete(ctx.h, ctypes.byref(m), mp, ml, k, p, passes, algo, iters, ctypes.byref(om),
+                               ctypes.byref(o), ctypes.byref(c), ctypes.byref(u), ctypes.c_void_p(S.data_ptr()),
+                               ctypes.byref(v)), "qlr_qcomplete")
+    return C, U, S, V
 
 
 def qsvd_lowrank_batched(ctx: Context, As: Sequence[torch.Tensor], ks: Sequence[int], ps: Sequence[int], passes: int,

@@ -1,0 +1,136 @@
+"""Quaternion matrix completion (Section 7, eqs. Step1 and Step2) on the GPU against the oracle.
+
+- The masked update kernel, element by element: observed entries are M's stored values exactly,
+  unobserved ones the rank-k product within the rounding bound of its arithmetic (FP64 / FP32),
+  over ragged tiles, several rank chunks, pure and full M, a padded mask and C in place of M.
+- The whole completion loop against `oracle.completion.complete` on the same Omega: FP64 storage
+  to 1e-9 (C) and 1e-10 (sigma), FP32 storage with 3xTF32 sketches to 1e-4.
+- Recovery of a rank-5 matrix from half of its entries, as the oracle recovers it.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import completion as oc
+from tests._qutil import TORCH_DT, dev_rowmajor, dev_thin, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    c = qlr.Context(0)
+    yield c
+    c.close()
+
+
+def _qabs(X):
+    return np.sqrt((X * X).sum(axis=0))
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("m,n,k,pure,pad,inplace", [(77, 131, 7, False, 0, False), (300, 65, 33, True, 5, False),
+                                                   (1, 1, 1, False, 0, False), (33, 64, 0, True, 3, False),
+                                                   (64, 200, 20, False, 16, True)])
+def test_update_kernel_elementwise(ctx, dt, m, n, k, pure, pad, inplace):
+    from paper_2507_13731_gb300 import qlr
+    rng = np.random.default_rng(m * 1000 + n + k)
+    M = rng.standard_normal((4, m, n))
+    if pure:
+        M[0] = 0.0
+    kk = max(k, 1)
+    U = rng.standard_normal((4, m, kk))
+    V = rng.standard_normal((4, n, kk))
+    S = np.sort(rng.random(kk) * 3.0)[::-1].copy()
+    mask = (rng.random((m, n)) < 0.4).astype(np.uint8)
+    Md = dev_rowmajor(M, dt, pure=pure and not inplace)
+    Ud, Vd = dev_thin(U, dt), dev_thin(V, dt)
+    Sd = torch.from_numpy(S).cuda()
+    mbuf = torch.zeros(m, n + pad, dtype=torch.uint8, device="cuda")
+    mbuf[:, :n] = torch.from_numpy(mask).cuda()
+    maskd = mbuf[:, :n]
+    Cd = Md if inplace else torch.full((4, m, n), float("nan"), dtype=TORCH_DT[dt], device="cuda")
+    Mh = host(Md)                          # the stored (rounded) values
+    Uh, Vh = host(Ud), host(Vd)
+    qlr.complete_update(ctx, Md, maskd, Cd, Ud, Sd, Vd, k)
+    assert ctx.sync() == 0
+    C = host(Cd)
+    obs = mask == 1
+    assert np.array_equal(C[:, obs], Mh[:, obs])
+    if k == 0:
+        assert np.array_equal(C[:, ~obs], np.zeros((4, int((~obs).sum()))))
+        return
+    X = oc.low_rank_product(Uh[:, :, :k], S[:k], Vh[:, :, :k])
+    bound = (_qabs(Uh[:, :, :k]) * S[None, :k]) @ _qabs(Vh[:, :, :k]).T     # sum_r |u_ir| s_r |v_jr|
+    c = 1e-14 if dt == "f64" else 2e-7 * (k + 4)
+    err = np.abs(C - X).max(axis=0)
+    assert np.all(err[~obs] <= c * bound[~obs] + 1e-300)
+
+
+def test_update_rejects_bad_arguments(ctx):
+    from paper_2507_13731_gb300 import qlr
+    M = torch.zeros(4, 8, 6, device="cuda")
+    C = torch.zeros(4, 8, 6, device="cuda")
+    mask = torch.ones(8, 6, dtype=torch.uint8, device="cuda")
+    with pytest.raises(qlr.QlrError) as e:
+        qlr.complete_update(ctx, M, mask, C.double())
+    assert e.value.code == qlr.EINVAL
+    U = qlr.empty_thin(7, 2)
+    V = qlr.empty_thin(6, 2)
+    S = torch.ones(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(qlr.QlrError) as e:
+        qlr.complete_update(ctx, M, mask, C, U, S, V, 2)
+    assert e.value.code == qlr.ESHAPE
+    om = qlr.empty_thin(6, 4)
+    with pytest.raises(qlr.QlrError) as e:
+        qlr.complete(ctx, M, mask, 2, 2, 2, 0, om, C, qlr.empty_thin(8, 2), S, V)
+    assert e.value.code == qlr.ESHAPE
+
+
+def _run(ctx, P, dt, compute, iters, v):
+    from paper_2507_13731_gb300 import qlr
+    mask = torch.from_numpy(P.extra["mask"]).cuda()
+    Md = dev_rowmajor(P.A, dt, pure=True)
+    tdt = TORCH_DT[dt]
+    Cd = torch.empty(4, P.m, P.n, dtype=tdt, device="cuda")
+    Ud, Vd = qlr.empty_thin(P.m, P.k, tdt), qlr.empty_thin(P.n, P.k, tdt)
+    Sd = torch.zeros(P.k, dtype=torch.float64, device="cuda")
+    Od = dev_thin(P.Omega, "f64" if dt == "f64" else "f32")
+    qlr.complete(ctx, Md, mask, P.k, P.p, v, iters, Od, Cd, Ud, Sd, Vd, compute=compute, side=qlr.SIDE_X)
+    assert ctx.sync() == 0
+    return host(Cd), Sd.cpu().numpy(), host(Md)
+
+
+def test_completion_fp64_matches_oracle(ctx):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.completion_problem(120, 90, 5, missing=0.5, seed=31, noise=1e-3, p=5)
+    C, S, _ = _run(ctx, P, "f64", qlr.COMPUTE_F64, 3, 2)
+    Cw, _, Sw, _, _ = oc.complete(P.A, P.extra["mask"], P.k, P.p, 2, 3, P.Omega, side="X")
+    np.testing.assert_allclose(S, Sw, rtol=1e-10)
+    assert np.abs(C - Cw).max() <= 1e-9 * np.abs(P.A).max()
+
+
+def test_completion_fp32_tensor_core_matches_oracle(ctx):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.completion_problem(256, 192, 8, missing=0.7, seed=32, noise=1e-3, p=8)
+    C, S, Mh = _run(ctx, P, "f32", qlr.COMPUTE_TF32X3, 5, 2)
+    obs = P.extra["mask"] == 1
+    assert np.array_equal(C[:, obs], Mh[:, obs])
+    Cw, _, Sw, _, _ = oc.complete(P.A, P.extra["mask"], P.k, P.p, 2, 5, P.Omega, side="X")
+    np.testing.assert_allclose(S, Sw, rtol=1e-4)
+    assert np.abs(C - Cw).max() <= 1e-4 * np.abs(P.A).max()
+
+
+def test_completion_recovers_rank5_from_half_the_entries(ctx):
+    from paper_2507_13731_gb300 import qlr
+    P = synth.completion_problem(256, 256, 5, missing=0.5, seed=21, p=5)
+    miss = P.extra["mask"] == 0
+    C, _, _ = _run(ctx, P, "f32", qlr.COMPUTE_AUTO, 40, 4)
+    ref = np.sqrt((P.A[:, miss] ** 2).sum())
+    err = np.sqrt(((C - P.A)[:, miss] ** 2).sum()) / ref
+    Cw, _, _, _, _ = oc.complete(P.A, P.extra["mask"], P.k, P.p, 4, 40, P.Omega, side="X")
+    err_w = np.sqrt(((Cw - P.A)[:, miss] ** 2).sum()) / ref
+    assert err < 1e-3 and err <= 10 * err_w + 1e-4
