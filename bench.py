@@ -295,6 +295,53 @@ def completion_leg(dev, steps=5):
             "device_error": rc}
 
 
+SWEEP_SIZES = tuple(range(500, 4001, 500))
+SWEEP_CASES = (("alg2", 2), ("alg2", 3), ("alg1", 4), ("alg1", 6))
+SWEEP_WORKLOAD = ("random low-rank example: A = B C with Gaussian quaternion B (m x 50) and C (50 x n), m = n = "
+                  "500..4000 step 500, FP32 planes, k = 50, p = 10, Algorithm 2 with v = 2, 3 and Algorithm 1 with "
+                  "q = 1, 2 (v = 4, 6)")
+
+
+def lowrank_sweep_leg(dev, reps=3):
+    """The random low-rank example of the experiments (Section 8): per size and algorithm the mean
+    time of `reps` qlr_qsvd_lowrank calls (after one warm-up call) and the relative Frobenius error
+    ||A - U S V^H||_F / ||A||_F (U S V^H formed by qlr_qcomplete_update with no observed entry)."""
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import qlr
+    ctx = qlr.Context(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for m in SWEEP_SIZES:
+        P = synth.random_lowrank_problem(m, m, 50)
+        A = torch.from_numpy(P.A).float().to(dev).contiguous()
+        om = qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev))
+        U, V = qlr.empty_thin(m, P.k, device=dev), qlr.empty_thin(m, P.k, device=dev)
+        S = torch.zeros(P.k, dtype=torch.float64, device=dev)
+        X = torch.empty_like(A)
+        none = torch.zeros(m, m, dtype=torch.uint8, device=dev)
+        nrm = float(torch.linalg.vector_norm(A.double()))
+        ent = {"m": m, "n": m}
+        for algo, v in SWEEP_CASES:
+            a = qlr.ALG1 if algo == "alg1" else qlr.ALG2
+            for _ in range(reps + 1):
+                if _ == 1:
+                    e0.record()
+                qlr.qsvd_lowrank(ctx, A, P.k, P.p, v, om, U, S, V, algo=a, side=qlr.SIDE_X)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            qlr.complete_update(ctx, A, none, X, U, S, V, P.k)
+            err = float(torch.linalg.vector_norm((A - X).double())) / nrm
+            name = f"alg2_v{v}" if algo == "alg2" else f"alg1_q{v // 2 - 1}"
+            ent[name] = {"ms": round(ms, 3), "rel_err": float(f"{err:.3e}")}
+        rows.append(ent)
+    rc = ctx.sync()
+    ctx.close()
+    return {"workload": SWEEP_WORKLOAD, "results": rows, "device_error": rc}
+
+
 def max_over_ranks(x: float, ws: int, device=None) -> float:
     """The largest of the ranks' values (the whole job is as slow as its slowest replica)."""
     if ws <= 1:
@@ -475,6 +522,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
     ap.add_argument("--no-completion", action="store_true", help="skip the matrix-completion leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the random low-rank size sweep")
     ap.add_argument("--only", choices=["sketch", "qsvd", "batch", "complete"], default=None,
                     help="profiling driver: time only sketch passes, single QSVDs or batch runs (for ncu captures)")
     ap.add_argument("--op", choices=["N", "H"], default="N")
@@ -598,6 +646,12 @@ def main():
                 completion = completion_leg(dev)
             except Exception as e:                 # reported, never fatal to the headline line
                 completion = {"error": f"{type(e).__name__}: {e}"}
+        sweep = None
+        if ws == 1 and not args.no_sweep:
+            try:
+                sweep = lowrank_sweep_leg(dev)
+            except Exception as e:                 # reported, never fatal to the headline line
+                sweep = {"error": f"{type(e).__name__}: {e}"}
         if ws == 1 and not args.no_cpu_baseline:
             val, secs, thr = cpu_oracle_sample(P)
             cpu = {"value": round(val, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
@@ -621,6 +675,7 @@ def main():
             "gpu_launches": gpu_launches,
             "batched": batched,
             "completion": completion,
+            "lowrank_sweep": sweep,
             "kernels": {k: {"launches": n, "ms": round(ms, 3)} for k, (n, ms) in stats.items() if n},
             "clocks": clk,
             "device_error": rc,

@@ -347,3 +347,14 @@ def completion_problem(m: int, n: int, rank: int, missing: float = 0.7, seed: in
     mask = (u >= missing).astype(np.uint8)
     return Problem(f"complete{m}x{n}r{rank}", A, k, p, v, omega_for(seed, n, k + p), pure=True,
                    extra={"mask": mask, "rank": rank, "missing": missing})
+
+
+def random_lowrank_problem(m: int, n: int, rank: int = 50, seed: int = 1241, p: int = 10, v: int = 2) -> Problem:
+    """The random low-rank example of the experiments (Section 8): A = B C with B (m x rank) and
+    C (rank x n) Gaussian quaternion matrices (Def. 2), so A has rank `rank`; k = rank, Omega is
+    n x (rank + p).  The paper runs m = n = 500, 1000, ..., 4000 with rank 50 and does not state p."""
+    B = gaussian_qmat(stream_seed(seed, TAG_LEFT, m, n), m, rank)
+    C = gaussian_qmat(stream_seed(seed, TAG_RIGHT, m, n), rank, n)
+    A = _qmm(B, C)
+    return Problem(f"randlr{m}x{n}r{rank}", A, rank, p, v, omega_for(stream_seed(seed, m, n), n, rank + p),
+                   extra={"rank": rank})

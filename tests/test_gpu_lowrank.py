@@ -95,6 +95,23 @@ def test_classical_algorithms_match_oracle(ctx, algo, q):
         qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, v + 1, Od, Ub, Sb, Vb, algo=a, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X)
 
 
+@pytest.mark.parametrize("algo,v", [("alg2", 2), ("alg2", 3), ("alg1", 4), ("alg1", 6)])
+def test_random_lowrank_example(ctx, algo, v):
+    """The random low-rank example (Section 8): A = B C of exact rank 50, m = n = 500, FP32 planes
+    with 3xTF32 sketches; Algorithm 2 with two and three passes and Algorithm 1 with q = 1, 2
+    against the oracle on the same Omega (sigma to 1e-4), and the rank-50 approximation
+    reproduces A to FP32 rounding (Frobenius relative error below 1e-5)."""
+    from paper_2507_13731_gb300 import qlr
+    P = synth.random_lowrank_problem(500, 500, 50, v=v)
+    a = qlr.ALG1 if algo == "alg1" else qlr.ALG2
+    U, S, V, Om, _ = run_gpu(ctx, P, v, a, "f32", qlr.COMPUTE_TF32X3)
+    ref = (al.alg1_classical(P.A, P.k, P.p, v // 2 - 1, Om) if algo == "alg1"
+           else al.alg2_arbitrary_pass(P.A, P.k, P.p, v, Om))
+    np.testing.assert_allclose(S, ref.S, rtol=1e-4)
+    X = Q.qmatmul(U * S[None, None, :], Q.qH(V))
+    assert Q.qfro(X - P.A) <= 1e-5 * Q.qfro(P.A)
+
+
 @pytest.mark.parametrize("v", [2, 3, 4, 5, 6])
 def test_alg4_fp64_small(ctx, v):
     from paper_2507_13731_gb300 import qlr
