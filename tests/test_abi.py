@@ -45,6 +45,10 @@ def test_host_only_calls(libpath):
     # null-pointer arguments are rejected before any device work
     assert L.qlr_qsketch(None, 0, None, None, None, 0) == qlr.EINVAL
     assert L.qlr_create(None, 0, None) == qlr.EINVAL
+    assert L.qlr_qcomplete_update(None, None, None, 1, None, None, None, 0, None) == qlr.EINVAL
+    assert L.qlr_qcomplete(None, None, None, 1, 1, 0, 2, qlr.ALG2, 1, None, None, None, None, None, None) == qlr.EINVAL
+    kid_count = int(re.search(r"#define QLR_KID_COUNT (\d+)", open(HEADER).read()).group(1))
+    assert len(qlr.KID_NAMES) == kid_count
 
 
 def test_descriptor_layouts_on_cpu_tensors():
