@@ -18,6 +18,9 @@
  *  - Calls are asynchronous on the context's stream.  Host-side validation errors are returned
  *    immediately.  Device-side conditions (Cholesky breakdown, Jacobi non-convergence, bounded
  *    waits) are recorded in a device error word; qlr_sync() waits for the stream and returns it.
+ *  - A context is not thread-safe: its calls share one workspace, error word and launch
+ *    statistics, so calls on one context must not overlap across host threads.  Use one context
+ *    per host thread (each on its own stream).
  *  - Every function returns QLR_OK (0) or one of the QLR_E* codes below.
  */
 #ifndef QLR_H
