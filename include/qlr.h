@@ -319,6 +319,15 @@ int qlr_qcomplete(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t 
                   double* S, qlr_qmat* V);
 
 /*
+ * qlr_selftest_wait_timeout -- failure-detection self test (the paper has no counterpart):
+ * launches one CTA that waits on an mbarrier nothing arrives at, through the bounded wait the
+ * tensor-core pipelines use.  The wait gives up after its limit (1.5 s), records QLR_ETIMEOUT in
+ * the context's device error word and the kernel returns: qlr_sync then returns QLR_ETIMEOUT
+ * once, and later calls on the context run normally.  Nothing faults or traps.
+ */
+int qlr_selftest_wait_timeout(qlr_ctx* ctx);
+
+/*
  * qlr_qsketch_noalloc -- the tensor-core sketch product of qlr_qsketch (same op, operands, layouts
  * and results, compute QLR_COMPUTE_TF32, QLR_COMPUTE_TF32X3 or QLR_COMPUTE_BF16) for callers that
  * cannot allocate device memory.  The paper has no counterpart; this is a deployment convenience.

@@ -649,6 +649,12 @@ int qlr_qcomplete(qlr_ctx* ctx, const qlr_qmat* M, const uint8_t* mask, int64_t 
   return QLR_OK;
 }
 
+int qlr_selftest_wait_timeout(qlr_ctx* ctx) {
+  if (!ctx) return QLR_EINVAL;
+  DeviceGuard g(ctx->device);
+  return qlr::selftest_wait_timeout(ctx);
+}
+
 int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
                              const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V) {
   if (!ctx || count < 0 || (count > 0 && (!A || !k || !p || !omega || !U || !S || !V))) return QLR_EINVAL;

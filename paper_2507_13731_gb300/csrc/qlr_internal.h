@@ -235,6 +235,8 @@ struct CompleteArgs {
   int k;
 };
 int complete_update(qlr_ctx* ctx, const CompleteArgs& a, int dtype);
+// Failure-detection self test (selftest.cu): a bounded mbarrier wait that times out.
+int selftest_wait_timeout(qlr_ctx* ctx);
 
 // Grouped steps of batch plans: one launch runs one step for every problem of a plan, the
 // per-problem arguments and the (problem, tile) items of each launch in device tables built once

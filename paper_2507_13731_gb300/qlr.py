@@ -93,6 +93,7 @@ def lib():
             "qlr_residual_norm": (I, [P, Q, Q, I, Q, I, ctypes.POINTER(D)]),
             "qlr_qcomplete_update": (I, [P, Q, P, I64, Q, P, Q, I, Q]),
             "qlr_qcomplete": (I, [P, Q, P, I64, I, I, I, I, I, Q, O, Q, Q, P, Q]),
+            "qlr_selftest_wait_timeout": (I, [P]),
             "qlr_set_timing": (I, [P, I]),
             "qlr_reset_stats": (I, [P]),
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
@@ -295,6 +296,12 @@ def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE
                                    ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
            "qlr_qblock_krylov")
     return U, S, V
+
+
+def selftest_wait_timeout(ctx: Context) -> None:
+    """Launch the failure-detection self test: a bounded device wait that times out, after which
+    ctx.sync() returns ETIMEOUT once."""
+    _check(lib().qlr_selftest_wait_timeout(ctx.h), "qlr_selftest_wait_timeout")
 
 
 def _mask(mask: torch.Tensor, rows: int, cols: int):
