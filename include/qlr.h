@@ -149,6 +149,8 @@ int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
  * A: row-major, dtype F64 / F32 / BF16 (pure allowed).  X: column-major, 4 planes; its dtype
  * must be F64 for COMPUTE_F64, F32 for F32 / TF32 / TF32X3, F32 or BF16 for BF16 (F32 input is
  * rounded to BF16 on the device).  Y: column-major, F64 (COMPUTE_F64) or F32.  A is read once.
+ * Degenerate sizes: an empty Y (no rows or no columns) launches nothing; an empty inner
+ * dimension (n = 0 for op N, m = 0 for op H) writes Y = 0.
  * Errors: QLR_EINVAL (null/dtype/layout), QLR_ESHAPE (size mismatch), QLR_EUNSUPPORTED.
  */
 int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute);

@@ -440,6 +440,8 @@ int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_
   if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
   if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && A->dtype != QLR_F32) return QLR_EINVAL;
   DeviceGuard g(ctx->device);
+  if (outer == 0 || X->cols == 0) return QLR_OK;                        // Y is empty
+  if (inner == 0) return qlr::zero_qmat(ctx, *Y);                       // empty sums: Y = 0
   if (compute >= QLR_COMPUTE_TF32) QLR_TRY(qlr_ensure_ws(ctx, qlr::sketch_tc_ws(X->rows, X->cols, ctx->num_sms)));
   WsArena ws(ctx->ws, ctx->ws_bytes);
   Sched S{};
