@@ -5,7 +5,11 @@ Workload (one "step"): the FP32 arbitrary-pass range finder workload -- a 4096 x
 matrix with FP32 planes, sigma_i = 1/i and Haar-like singular vectors, k = 100, p = 10 -- run
 through Algorithm 2 with each pass budget v in {2, 3, 4, 6, 8}: 23 sketch passes with their
 orthonormalisations, five core QSVDs and lifts.  Metric: sketch passes per second (whole job);
-A-read TB/s and the per-v rank-k QSVD times go in extra keys.
+A-read TB/s and the per-v rank-k QSVD times go in extra keys.  On one GPU the line also carries
+`batched` (512 uneven BF16 problems as one batch plan against the plain FP32 per-problem loop),
+`completion` (matrix completion's alternating updates on a 4096 x 4096 matrix with 70 % of the
+entries removed, and the masked update kernel's roofline) and `lowrank_sweep` (the random rank-50
+example at m = n = 500..4000); --no-batched / --no-completion / --no-sweep skip them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
