@@ -64,3 +64,17 @@ def test_descriptor_layouts_on_cpu_tensors():
     P = torch.zeros(3, 4, 6, dtype=torch.bfloat16)
     d = qlr.qmat(P)
     assert d.plane[0] is None and d.dtype == qlr.BF16
+
+
+def test_mask_descriptor_on_cpu_tensors():
+    import torch
+    from paper_2507_13731_gb300 import qlr
+    buf = torch.zeros(6, 10, dtype=torch.uint8)
+    _, ld = qlr._mask(buf[:, :7], 6, 7)
+    assert ld == 10                                   # padded rows keep their stride
+    with pytest.raises(ValueError):
+        qlr._mask(torch.zeros(6, 7), 6, 7)            # not uint8
+    with pytest.raises(ValueError):
+        qlr._mask(buf[:, :7], 7, 6)                   # wrong shape
+    with pytest.raises(ValueError):
+        qlr._mask(buf.t()[:7, :6], 7, 6)              # column-major
