@@ -62,3 +62,24 @@ def test_bounds_decrease_with_passes():
         assert max(r, c) < prev
         prev = max(r, c)
         assert t == pytest.approx(bounds.power_bound(s, K, P, v - 1))
+
+
+def _golden_constants():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "bound_constants.json")
+    return json.load(open(path))["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_constants(), ids=lambda c: f"k{c['k']}p{c['p']}")
+def test_bound_constants_match_hand_worked_values(case):
+    """The constants a (of sigma_{k+1}) and b (of the tail sum) against values worked by hand from
+    Lemma 1 at (k, p) where a is an integer: tail (1) gives a + b, tail (3, 4) gives 3a + 5b, so a
+    mistyped 4p+2, 2p+2 or 4k+4p+2 changes one of the two."""
+    k, p, a, b = case["k"], case["p"], case["a"], case["b"]
+    head = np.arange(k + 5, 5, -1, dtype=np.float64)[:k]           # any k leading values
+    one = np.concatenate([head, [1.0]])
+    pyth = np.concatenate([head, [3.0, 4.0]])
+    assert bounds.power_bound(one, k, p, 1) == pytest.approx(a + b, rel=1e-14)
+    assert bounds.power_bound(pyth, k, p, 1) == pytest.approx(3 * a + 5 * b, rel=1e-14)
+    assert bounds.lemma1(one, k, p, 0) == pytest.approx(a + b, rel=1e-14)
