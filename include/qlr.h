@@ -60,6 +60,10 @@ extern "C" {
 #define QLR_COMPUTE_TF32 3   /* tcgen05 kind::tf32, one product (FP32 storage)                  */
 #define QLR_COMPUTE_TF32X3 4 /* tcgen05 kind::tf32, hi/lo split of both operands, three products */
 #define QLR_COMPUTE_BF16 5   /* tcgen05 kind::f16 with BF16 operands (BF16 storage of A)         */
+/* FP32 storage, algorithm calls only: the products whose result only feeds a later basis or
+ * Krylov block (Algorithm 2's passes 1..v-1, Algorithm 4's views before the final pass) run one
+ * TF32 product; the last pass, which forms the returned R, runs 3xTF32. */
+#define QLR_COMPUTE_TF32_MIXED 6
 
 /* ---- sketch operator ------------------------------------------------------------------- */
 #define QLR_OP_N 0 /* Y = A X     */
@@ -141,6 +145,22 @@ int qlr_set_timing(qlr_ctx* ctx, int enable);
 int qlr_reset_stats(qlr_ctx* ctx);
 int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
 
+/* ---- throughput probes (no paper counterpart: the roofline denominators) ---------------
+ * qlr_peak_probe runs one probe kernel on `device` (on a stream of its own, synchronously) and
+ * returns the floating-point operations it executed and its CUDA-event time:
+ *   QLR_PEAK_TF32_MMA / QLR_PEAK_BF16_MMA: one CTA per SM issues `iters` rounds of 8 tcgen05 MMAs
+ *     (M = 128, N = 256, K = 8 kind::tf32 / K = 16 kind::f16 with BF16 operands) on operands
+ *     staged once in shared memory; iters <= 400000 (the kernel's bounded wait must not expire);
+ *   QLR_PEAK_FP32_FMA / QLR_PEAK_FP64_FMA: 8 CTAs of 256 threads per SM, each thread `iters`
+ *     rounds of 8 independent fused multiply-adds.
+ * Dense peak = flops / ms.  Errors: QLR_EINVAL (kind, iters, null outputs), QLR_ECUDA,
+ * QLR_ETIMEOUT (the MMA probe's bounded wait gave up). */
+#define QLR_PEAK_TF32_MMA 0
+#define QLR_PEAK_BF16_MMA 1
+#define QLR_PEAK_FP32_FMA 2
+#define QLR_PEAK_FP64_FMA 3
+int qlr_peak_probe(int kind, int device, int64_t iters, double* flops, float* ms);
+
 /*
  * qlr_qsketch -- one sketch pass (the products X Q2 / X^H Q1 of Algorithm 2 and Algorithm 4,
  * and the Hamilton product of eq. (1), Section 2, summed over the inner index).
@@ -220,6 +240,21 @@ int qlr_qrangefinder(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, 
  */
 int qlr_qsvd_lowrank(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo,
                      const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* S, qlr_qmat* V);
+
+/*
+ * qlr_qbasis -- the orthonormal bases and the last R factor of a qlr_qsvd_lowrank call, before its
+ * truncated QSVD: Algorithm 2 (and 1) return the last Q1, Q2 and R as qlr_qrangefinder does;
+ * Algorithm 4 (and 3) return Q1 = QR(K1) (even v: the range basis of width L = (v/2) l) with
+ * [Q2, R2] = QR(X^H Q1), or Q2 = QR(K2) (odd v: L = ((v-1)/2) l) with [Q1, R1] = QR(X Q2) (Section
+ * 5, Algorithm 4).  These are the bases whose projection errors ||X - Q1 Q1^H X||_2 and
+ * ||X - X Q2 Q2^H||_2 Lemma 1, Theorem 3, eqs. (mn11)/(mn12) and Theorem 6 bound (measure them with
+ * qlr_residual_norm).  Arguments as qlr_qsvd_lowrank; Q1: rows_fwd x L and Q2: rows_bwd x L
+ * column-major in the thin dtype (F64 for COMPUTE_F64, else F32), with rows_fwd = m, rows_bwd = n
+ * on side X and swapped on side X^H; R: device FP64 L x L x 4 (R2 for even v, R1 for odd v);
+ * side_used (host, may be NULL).  L = l for Algorithms 1 and 2.  Same errors as qlr_qsvd_lowrank.
+ */
+int qlr_qbasis(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo, const qlr_qmat* omega,
+               const qlr_opts* opts, qlr_qmat* Q1, qlr_qmat* Q2, double* R, int* side_used);
 
 /*
  * qlr_qblock_krylov -- Algorithm 4 (flexible block Krylov, Section 5) with block size b >= k:
@@ -337,15 +372,20 @@ int qlr_selftest_wait_timeout(qlr_ctx* ctx);
  * so latency-critical serving loops keep it out of their steady state, and some host applications
  * give all device memory to their own pool allocator and forbid other allocations; neither can
  * create a qlr context (which allocates its error word and workspace).
- * No context: the call runs on `stream` (a cudaStream_t, NULL = legacy default stream) of the
- * current device and takes all scratch memory from one fixed 32 MiB device array compiled into the
- * library (every GPU that loads it keeps those 32 MiB until the process exits).  It calls no
- * cudaMalloc / cudaFree.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress), so make the first call on each device before any stream capture.
+ * No context: the call runs on `stream` (a cudaStream_t, NULL = legacy default stream) on that
+ * stream's device (made current for the call, the caller's current device restored on return) and
+ * takes all scratch memory from one fixed 32 MiB device array compiled into the library (every GPU
+ * that loads it keeps those 32 MiB until the process exits).  It calls no cudaMalloc / cudaFree.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress, with the
+ * device current) and keeps it for the life of the process, so make the first call on each device
+ * before any stream capture, and do not call this entry point on a device after a cudaDeviceReset
+ * of it (the kept address would be stale).  The stream-K schedule uses as many CTAs as the array's
+ * partial-tile space allows (up to one per SM).
  * The array is shared by all calls on a device and keeps the previous call's contents; each call
  * clears the parts that must start at zero.  Calls that overlap on the GPU (other streams or
  * threads) race on the array: serialise them.  `err` (device int, may be NULL) receives
  * QLR_ETIMEOUT if a bounded device wait gives up.
+ * Degenerate sizes as qlr_qsketch: an empty Y launches nothing; an empty inner dimension writes Y = 0.
  * Errors: QLR_EINVAL / QLR_ESHAPE as qlr_qsketch; QLR_EUNSUPPORTED for a row pitch of A that is not
  * a multiple of 16 bytes; QLR_ENOMEM when the operands need more scratch than the 32 MiB array
  * (the staged thin operand alone needs 32 bytes per quaternion entry of X for TF32X3, 8 for BF16).

@@ -71,6 +71,10 @@ int resolve_compute(int compute, int a_dtype) {
 
 bool valid_compute(int c) { return c >= QLR_COMPUTE_F64 && c <= QLR_COMPUTE_BF16; }
 
+// Mixed mode: the products that only feed later bases run one TF32 product, the last pass 3xTF32.
+int final_compute(int c) { return c == QLR_COMPUTE_TF32_MIXED ? QLR_COMPUTE_TF32X3 : c; }
+int mid_compute(int c) { return c == QLR_COMPUTE_TF32_MIXED ? QLR_COMPUTE_TF32 : c; }
+
 // Thin-matrix dtype used by the scheduler for a compute mode.
 int thin_dtype(int compute) { return compute == QLR_COMPUTE_F64 ? QLR_F64 : QLR_F32; }
 
@@ -79,11 +83,20 @@ struct Sched {
   qlr_ctx* ctx;
   WsArena* ws;
   const qlr_qmat* A;
-  int compute;
+  int compute;      // arithmetic of the products that form the returned R (the last pass)
+  int compute_mid;  // arithmetic of the products that only feed a later basis or Krylov block
   int tdt;          // thin dtype
   int op_fwd, op_bwd;
   int64_t rows_fwd, rows_bwd;   // X is rows_fwd x rows_bwd
   bool allow_simt_fallback = false;
+
+  // a product whose result only feeds a later basis (mixed mode: one TF32 product)
+  int sketch_mid(int op, const qlr_qmat& B, qlr_qmat& Y) {
+    if (compute_mid == compute) return sketch(op, B, Y);
+    Sched s2 = *this;
+    s2.compute = compute_mid;
+    return s2.sketch(op, B, Y);
+  }
 
   int sketch(int op, const qlr_qmat& B, qlr_qmat& Y) {
     if (compute == QLR_COMPUTE_F64 || compute == QLR_COMPUTE_F32) {
@@ -101,7 +114,7 @@ struct Sched {
     if (!qlr::sketch_tc_supported(op, *A, B, compute)) {
       if (!allow_simt_fallback) return QLR_EUNSUPPORTED;
       Sched s2 = *this;                 // documented AUTO behaviour: SIMT FP32 for unsupported shapes
-      s2.compute = QLR_COMPUTE_F32;
+      s2.compute = s2.compute_mid = QLR_COMPUTE_F32;
       return s2.sketch(op, B, Y);
     }
     return qlr::sketch_tc(ctx, op, *A, B, Y, compute, *ws);
@@ -140,9 +153,11 @@ int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr
   if (l > std::min(A->rows, A->cols)) return QLR_ESHAPE;
   auto_compute = (opts == nullptr || opts->compute == QLR_COMPUTE_AUTO);
   compute = resolve_compute(opts ? opts->compute : QLR_COMPUTE_AUTO, A->dtype);
-  if (!valid_compute(compute)) return QLR_EINVAL;
+  if (!valid_compute(compute) && compute != QLR_COMPUTE_TF32_MIXED) return QLR_EINVAL;
   if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
-  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && A->dtype != QLR_F32) return QLR_EINVAL;
+  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3 || compute == QLR_COMPUTE_TF32_MIXED) &&
+      A->dtype != QLR_F32)
+    return QLR_EINVAL;
   side = opts ? opts->side : QLR_SIDE_AUTO;
   if (side == QLR_SIDE_AUTO) side = (passes % 2 == 0 && A->cols > A->rows) ? QLR_SIDE_XH : QLR_SIDE_X;
   if (side != QLR_SIDE_X && side != QLR_SIDE_XH) return QLR_EINVAL;
@@ -153,7 +168,8 @@ int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr
 }
 
 void init_sched(Sched& S, qlr_ctx* ctx, WsArena* ws, const qlr_qmat* A, int compute, int side) {
-  S.ctx = ctx; S.ws = ws; S.A = A; S.compute = compute; S.tdt = thin_dtype(compute);
+  S.ctx = ctx; S.ws = ws; S.A = A; S.compute = final_compute(compute); S.compute_mid = mid_compute(compute);
+  S.tdt = thin_dtype(compute);
   S.op_fwd = (side == QLR_SIDE_X) ? QLR_OP_N : QLR_OP_H;
   S.op_bwd = (side == QLR_SIDE_X) ? QLR_OP_H : QLR_OP_N;
   S.rows_fwd = (side == QLR_SIDE_X) ? A->rows : A->cols;
@@ -182,10 +198,10 @@ int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
   const qlr_qmat* q2 = &om;
   for (int i = 1; i <= v; ++i) {
     if (i % 2 == 1) {
-      QLR_TRY(S.sketch(S.op_fwd, *q2, Y));                          // X Q2
+      QLR_TRY(i == v ? S.sketch(S.op_fwd, *q2, Y) : S.sketch_mid(S.op_fwd, *q2, Y));   // X Q2
       QLR_TRY(qlr::cholqr(S.ctx, Y, Q1, i == v ? R : nullptr, i >= v - 1 ? orth : orth_mid, *S.ws));   // [Q1, R1] = QR(.)
     } else {
-      QLR_TRY(S.sketch(S.op_bwd, Q1, Z));                           // X^H Q1
+      QLR_TRY(i == v ? S.sketch(S.op_bwd, Q1, Z) : S.sketch_mid(S.op_bwd, Q1, Z));     // X^H Q1
       QLR_TRY(qlr::cholqr(S.ctx, Z, Q2, i == v ? R : nullptr, i >= v - 1 ? orth : orth_mid, *S.ws));   // [Q2, R2] = QR(.)
       q2 = &Q2;
     }
@@ -193,48 +209,95 @@ int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
   return QLR_OK;
 }
 
+// Block classical Gram-Schmidt of the newest block of a stack against the blocks before it:
+// the slot (columns [c0, c0 + l) of K) becomes Y - B (B^H Y), B = K's columns [0, c0), run twice
+// ("twice is enough").  B^H Y is the off-diagonal block of the FP64-class Gram of K's first
+// c0 + l columns; the product B (B^H Y) accumulates in FP32.  The span of the stack is unchanged.
+int deflate_block(Sched& S, qlr_qmat& K, int64_t c0, int l) {
+  if (c0 == 0) return QLR_OK;
+  const int64_t w = c0 + l;
+  const size_t mark = S.ws->off;
+  double* G = S.ws->take<double>((size_t)4 * w * w);
+  if (!S.ws->ok) return QLR_ENOMEM;
+  const qlr_qmat KB = col_slice(K, 0, w);
+  const qlr_qmat slot = col_slice(K, c0, l);
+  for (int round = 0; round < 2; ++round) {
+    QLR_TRY(qlr::gram(S.ctx, KB, G, *S.ws));
+    qlr::GemmArgs g{};
+    for (int c = 0; c < 4; ++c) {
+      g.a[c] = K.plane[c];                          // B(i, t) at plane + i + t ld
+      g.b[c] = G + (size_t)c * w * w + (size_t)c0 * w;   // (B^H Y)(t, j) = G(t, c0 + j)
+      g.c[c] = slot.plane[c];
+    }
+    g.sa_i = 1; g.sa_k = K.ld; g.i_contig = true; g.conj_a = false; g.a_dtype = K.dtype;
+    g.ldb = w; g.b_dtype = QLR_F64;
+    g.ldc = K.ld; g.c_dtype = K.dtype;
+    g.M = K.rows; g.N = l; g.K = c0;
+    g.alpha = -1.0; g.beta = 1.0; g.acc64 = (K.dtype == QLR_F64);
+    g.kid = QLR_KID_APPLY;
+    QLR_TRY(qlr::gemm_simt(S.ctx, g));
+  }
+  S.ws->off = mark;
+  return QLR_OK;
+}
+
+// One Krylov block of Algorithm 4: slot j of the stack K receives QR(sketch of `in`), first
+// deflated against the stack's earlier blocks.  In exact arithmetic the deflation changes the
+// blocks that feed later views but not the span of [K_1 ... K_j] (every block's span grows by
+// the same new directions), so QR(K) -- hence Q1 / Q2, R, U, S, V -- is unchanged; in floating
+// point it keeps the new directions of each view, which in the plain stack sit below the FP32
+// rounding of the dominant ones.
+int krylov_block(Sched& S, int op, const qlr_qmat& in, qlr_qmat& K, int j, int l, qlr_qmat& tmp, int orth_mid) {
+  qlr_qmat slot = col_slice(K, (int64_t)j * l, l);
+  QLR_TRY(S.sketch_mid(op, in, slot));
+  QLR_TRY(deflate_block(S, K, (int64_t)j * l, l));
+  QLR_TRY(qlr::cholqr(S.ctx, slot, tmp, nullptr, orth_mid, *S.ws));
+  const size_t esz = qlr_dtype_size(K.dtype);
+  for (int c = 0; c < 4; ++c)
+    QLR_CUDA_TRY(cudaMemcpy2DAsync(slot.plane[c], K.ld * esz, tmp.plane[c], tmp.ld * esz, K.rows * esz, l,
+                                   cudaMemcpyDeviceToDevice, S.ctx->stream));
+  return QLR_OK;
+}
+
 // Algorithm 4.  On return Q1 (rows_fwd x L), Q2 (rows_bwd x L), R (L x L) with L the stacked width.
-// The per-view blocks are stacked into K (re-orthonormalised as a whole) or only feed the next view.
+// The per-view blocks of each side are kept in a stack (K1: range side, K2: co-range side), each
+// new block deflated against the blocks before it; the stack Algorithm 4 names (K1 for even v, K2
+// for odd v) then gets its QR, the other only serves the deflation.
 int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth, int orth_mid) {
   const int s = (v - 1) / 2;
   const bool even = (v % 2 == 0);
-  const int nblk = even ? v / 2 : (v - 1) / 2;
-  const int64_t Lw = (int64_t)nblk * l;
-  qlr_qmat K = S.thin(even ? S.rows_fwd : S.rows_bwd, Lw);
-  qlr_qmat Y = S.thin(S.rows_fwd, l), Z = S.thin(S.rows_bwd, l);
-  qlr_qmat q1cur = S.thin(S.rows_fwd, l), q2cur = S.thin(S.rows_bwd, l);
+  const int n1 = even ? v / 2 : s, n2 = s;          // blocks on the range / co-range side
+  qlr_qmat K1 = S.thin(S.rows_fwd, (int64_t)std::max(n1, 1) * l);
+  qlr_qmat K2 = S.thin(S.rows_bwd, (int64_t)std::max(n2, 1) * l);
+  qlr_qmat t1 = S.thin(S.rows_fwd, l), t2 = S.thin(S.rows_bwd, l);
   if (!S.ws->ok) return QLR_ENOMEM;
   const qlr_qmat* q2prev = &om;                 // Q2_0 = Omega
+  qlr_qmat q2j{};
   for (int j = 1; j <= s; ++j) {
-    if (2 * j - 1 < v) {                        // odd view: range side
-      qlr_qmat dst = even ? col_slice(K, (int64_t)(j - 1) * l, l) : q1cur;
-      QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
-      QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth_mid, *S.ws));
-      q1cur = dst;
+    if (2 * j - 1 < v) {                        // odd view: Q1_j = QR(X Q2_{j-1})
+      QLR_TRY(krylov_block(S, S.op_fwd, *q2prev, K1, j - 1, l, t1, orth_mid));
     }
-    if (2 * j < v) {
-      qlr_qmat dst = even ? q2cur : col_slice(K, (int64_t)(j - 1) * l, l);
-      QLR_TRY(S.sketch(S.op_bwd, q1cur, Z));
-      QLR_TRY(qlr::cholqr(S.ctx, Z, dst, nullptr, orth_mid, *S.ws));
-      q2cur = dst;
-      q2prev = &q2cur;
+    if (2 * j < v) {                            // even view: Q2_j = QR(X^H Q1_j)
+      const qlr_qmat q1j = col_slice(K1, (int64_t)(j - 1) * l, l);
+      QLR_TRY(krylov_block(S, S.op_bwd, q1j, K2, j - 1, l, t2, orth_mid));
+      q2j = col_slice(K2, (int64_t)(j - 1) * l, l);
+      q2prev = &q2j;
     }
   }
+  const int64_t Lw = (int64_t)(even ? n1 : n2) * l;
   if (even) {
-    qlr_qmat dst = col_slice(K, (int64_t)s * l, l);
-    QLR_TRY(S.sketch(S.op_fwd, *q2prev, Y));
-    QLR_TRY(qlr::cholqr(S.ctx, Y, dst, nullptr, orth_mid, *S.ws));
-    QLR_TRY(qlr::cholqr(S.ctx, K, Q1, nullptr, QLR_ORTH_SCHOLQR3, *S.ws));   // [Q1, ~] = QR(K1)
+    QLR_TRY(krylov_block(S, S.op_fwd, *q2prev, K1, s, l, t1, orth_mid));          // Q1_{s+1}
+    QLR_TRY(qlr::cholqr(S.ctx, K1, Q1, nullptr, orth, *S.ws));                     // [Q1, ~] = QR(K1)
     qlr_qmat W = S.thin(S.rows_bwd, Lw);
     if (!S.ws->ok) return QLR_ENOMEM;
-    QLR_TRY(S.sketch(S.op_bwd, Q1, W));                                       // X^H Q1
-    QLR_TRY(qlr::cholqr(S.ctx, W, Q2, R, orth, *S.ws));                        // [Q2, R2]
+    QLR_TRY(S.sketch(S.op_bwd, Q1, W));                                             // X^H Q1
+    QLR_TRY(qlr::cholqr(S.ctx, W, Q2, R, orth, *S.ws));                             // [Q2, R2]
   } else {
-    QLR_TRY(qlr::cholqr(S.ctx, K, Q2, nullptr, QLR_ORTH_SCHOLQR3, *S.ws));   // [Q2, ~] = QR(K2)
+    QLR_TRY(qlr::cholqr(S.ctx, K2, Q2, nullptr, orth, *S.ws));                     // [Q2, ~] = QR(K2)
     qlr_qmat W = S.thin(S.rows_fwd, Lw);
     if (!S.ws->ok) return QLR_ENOMEM;
-    QLR_TRY(S.sketch(S.op_fwd, Q2, W));                                       // X Q2
-    QLR_TRY(qlr::cholqr(S.ctx, W, Q1, R, orth, *S.ws));                        // [Q1, R1]
+    QLR_TRY(S.sketch(S.op_fwd, Q2, W));                                             // X Q2
+    QLR_TRY(qlr::cholqr(S.ctx, W, Q1, R, orth, *S.ws));                             // [Q1, R1]
   }
   return QLR_OK;
 }
@@ -254,7 +317,7 @@ size_t lowrank_ws(int64_t m, int64_t n, int k, int p, int v, int algo, int compu
   b += (size_t)4 * esz * (rows + 4) * L * 3;     // K, W, Q1/Q2 (stacked)
   b += (size_t)4 * esz * (m + n + 8) * L;        // Q1, Q2 when not caller-provided
   b += (size_t)4 * esz * (rows + 4) * l;         // omega conversion
-  b += (size_t)32 * L * L * 2 + (size_t)64 * L * k + 8 * k;
+  b += (size_t)32 * L * L * 3 + (size_t)64 * L * k + 8 * k;   // + the Gram of a deflated stack
   b += cholqr_ws_bound(rows, L, esz) + tsvd_ws_bound(L);
   b += qlr::sketch_tc_ws(rows, L, 160);           // tensor-core operand staging + stream-K partials
   return b + ((size_t)4 << 20);
@@ -579,6 +642,40 @@ static int lowrank_impl(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passe
   qlr_qmat* VX = (side == QLR_SIDE_X) ? V : U;
   QLR_TRY(qlr::thin_times_small(ctx, Q1, Uhat, (int)L, k, *UX, ws));   // U = Q1 U_hat
   QLR_TRY(qlr::thin_times_small(ctx, Q2, Vhat, (int)L, k, *VX, ws));   // V = Q2 V_hat
+  return QLR_OK;
+}
+
+int qlr_qbasis(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, int algo_in, const qlr_qmat* omega,
+               const qlr_opts* opts_in, qlr_qmat* Q1, qlr_qmat* Q2, double* R, int* side_used) {
+  int algo = QLR_ALG2;
+  qlr_opts opts_c;
+  QLR_TRY(canonical_algo(algo_in, passes, opts_in, algo, opts_c));
+  const qlr_opts* opts = &opts_c;
+  int compute, side;
+  bool autoc;
+  QLR_TRY(prepare(ctx, A, k, p, passes, omega, opts, compute, side, autoc));
+  QLR_TRY(check_qmat(Q1, QLR_COL_MAJOR, false));
+  QLR_TRY(check_qmat(Q2, QLR_COL_MAJOR, false));
+  if (!R) return QLR_EINVAL;
+  const int l = k + p;
+  const int64_t L = stacked_width(algo, l, passes);
+  if (L > std::min(A->rows, A->cols)) return QLR_ESHAPE;
+  const int tdt = thin_dtype(compute);
+  const int64_t rf = (side == QLR_SIDE_X) ? A->rows : A->cols, rb = (side == QLR_SIDE_X) ? A->cols : A->rows;
+  if (Q1->rows != rf || Q1->cols != L || Q2->rows != rb || Q2->cols != L) return QLR_ESHAPE;
+  if (Q1->dtype != tdt || Q2->dtype != tdt) return QLR_EINVAL;
+  const int orth = opts->orth;
+  DeviceGuard g(ctx->device);
+  QLR_TRY(qlr_ensure_ws(ctx, lowrank_ws(A->rows, A->cols, k, p, passes, algo, compute)));
+  WsArena ws(ctx->ws, ctx->ws_bytes);
+  Sched S{};
+  init_sched(S, ctx, &ws, A, compute, side);
+  S.allow_simt_fallback = autoc;
+  qlr_qmat om;
+  QLR_TRY(omega_in(S, omega, om));
+  if (algo == QLR_ALG2) QLR_TRY(run_alg2(S, l, passes, om, *Q1, *Q2, R, orth, mid_orth(opts, orth)));
+  else QLR_TRY(run_alg4(S, l, passes, om, *Q1, *Q2, R, orth, mid_orth(opts, orth)));
+  if (side_used) *side_used = side;
   return QLR_OK;
 }
 

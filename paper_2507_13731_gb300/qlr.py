@@ -24,13 +24,15 @@ LIB_PATH = os.path.join(_PKG, "libqlr.so")
 OK, EINVAL, ESHAPE, ENOTPD, ENOCONV, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
 F64, F32, BF16 = 0, 1, 2
 ROW_MAJOR, COL_MAJOR = 0, 1
-COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16 = range(6)
+COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16, COMPUTE_TF32_MIXED = range(7)
+COMPUTE_MIXED = COMPUTE_TF32_MIXED
 OP_N, OP_H = 0, 1
 ALG1, ALG2, ALG3, ALG4 = 1, 2, 3, 4
 SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
 ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
 FLAG_QR_EVERY_PASS = 1
 FLAG_NO_GRAPH = 2
+PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_FP32_FMA, PEAK_FP64_FMA = range(4)
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series",
@@ -88,6 +90,7 @@ def lib():
             "qlr_qrangefinder": (I, [P, Q, I, I, I, Q, O, Q, Q, P, ctypes.POINTER(I)]),
             "qlr_qsvd_lowrank": (I, [P, Q, I, I, I, I, Q, O, Q, P, Q]),
             "qlr_qblock_krylov": (I, [P, Q, I, I, I, Q, O, Q, P, Q]),
+            "qlr_qbasis": (I, [P, Q, I, I, I, I, Q, O, Q, Q, P, ctypes.POINTER(I)]),
             "qlr_qsvd_lowrank_batched": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
                                              ctypes.POINTER(P), Q]),
             "qlr_residual_norm": (I, [P, Q, Q, I, Q, I, ctypes.POINTER(D)]),
@@ -98,6 +101,7 @@ def lib():
             "qlr_reset_stats": (I, [P]),
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
             "qlr_qsketch_noalloc": (I, [P, I, Q, Q, Q, I, P]),
+            "qlr_peak_probe": (I, [I, I, I64, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)]),
             "qlr_batch_create": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
                                      ctypes.POINTER(P), Q, ctypes.POINTER(P)]),
             "qlr_batch_run": (I, [P]),
@@ -231,12 +235,18 @@ def qsketch(ctx: Context, op: int, A: torch.Tensor, X: torch.Tensor, Y: torch.Te
 def qsketch_noalloc(op: int, A: torch.Tensor, X: torch.Tensor, Y: torch.Tensor, compute: int,
                     stream: Optional[torch.cuda.Stream] = None, err: Optional[torch.Tensor] = None):
     """qlr_qsketch_noalloc: the tensor-core sketch product without a context and without any
-    device allocation (scratch comes from the library's fixed device array); see include/qlr.h."""
+    device allocation (scratch comes from the library's fixed device array); see include/qlr.h.
+    A, X, Y (and err) must be on one CUDA device; the call runs on that device's `stream`
+    (default: its current stream)."""
+    devs = {t.device for t in (A, X, Y) + ((err,) if err is not None else ())}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError("A, X, Y and err must be on one CUDA device")
     a, x, y = _A(A), _T(X), _T(Y)
-    s = stream if stream is not None else torch.cuda.current_stream(A.device)
-    ep = ctypes.c_void_p(err.data_ptr()) if err is not None else ctypes.c_void_p()
-    _check(lib().qlr_qsketch_noalloc(ctypes.c_void_p(s.cuda_stream), op, ctypes.byref(a), ctypes.byref(x),
-                                     ctypes.byref(y), compute, ep), "qlr_qsketch_noalloc")
+    with torch.cuda.device(A.device):
+        s = stream if stream is not None else torch.cuda.current_stream(A.device)
+        ep = ctypes.c_void_p(err.data_ptr()) if err is not None else ctypes.c_void_p()
+        _check(lib().qlr_qsketch_noalloc(ctypes.c_void_p(s.cuda_stream), op, ctypes.byref(a), ctypes.byref(x),
+                                         ctypes.byref(y), compute, ep), "qlr_qsketch_noalloc")
     return Y
 
 
@@ -286,6 +296,27 @@ def qsvd_lowrank(ctx: Context, A, k, p, passes, omega, U, S, V, algo=ALG2, compu
                                   ctypes.byref(u), ctypes.c_void_p(S.data_ptr()), ctypes.byref(v)),
            "qlr_qsvd_lowrank")
     return U, S, V
+
+
+def qbasis(ctx: Context, A, k, p, passes, omega, Q1, Q2, R, algo=ALG2, compute=COMPUTE_AUTO, side=SIDE_AUTO,
+           orth=ORTH_CHOLQR2, qr_every_pass=False) -> int:
+    """qlr_qbasis: the final bases Q1, Q2 and R of qsvd_lowrank's schedule (Q1: rows_fwd x L,
+    Q2: rows_bwd x L, R: FP64 (4, L, L) storage); returns the side used."""
+    a, om, q1, q2 = _A(A), _T(omega), _T(Q1), _T(Q2)
+    o = _opts(compute, side, orth, qr_every_pass)
+    used = ctypes.c_int(-1)
+    _check(lib().qlr_qbasis(ctx.h, ctypes.byref(a), k, p, passes, algo, ctypes.byref(om), ctypes.byref(o),
+                            ctypes.byref(q1), ctypes.byref(q2), ctypes.c_void_p(R.data_ptr()), ctypes.byref(used)),
+           "qlr_qbasis")
+    return used.value
+
+
+def stacked_width(algo: int, l: int, passes: int) -> int:
+    """Width L of the bases qbasis returns: l for Algorithms 1 and 2; the stacked Krylov width of
+    Algorithms 3 and 4 ((v/2) l for even v, ((v-1)/2) l for odd v)."""
+    if algo in (ALG3, ALG4):
+        return (passes // 2 if passes % 2 == 0 else (passes - 1) // 2) * l
+    return l
 
 
 def qblock_krylov(ctx: Context, A, k, b, passes, omega, U, S, V, compute=COMPUTE_AUTO, side=SIDE_AUTO,
@@ -396,6 +427,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def peak_probe(kind: int, device: int = 0, iters: int = 1000):
+    """qlr_peak_probe: (flops executed, milliseconds) of one throughput probe kernel."""
+    f, t = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _check(lib().qlr_peak_probe(kind, device, iters, ctypes.byref(f), ctypes.byref(t)), "qlr_peak_probe")
+    return f.value, t.value
+
+
+def measure_peak(kind: int, device: int = 0, target_ms: float = 40.0, reps: int = 3) -> float:
+    """Dense peak in TFLOP/s of one probe: calibrate the iteration count on a short run so one
+    launch takes about target_ms, then the best of `reps` launches."""
+    cap = 400000 if kind in (PEAK_TF32_MMA, PEAK_BF16_MMA) else 1 << 40
+    iters = 2000 if kind in (PEAK_TF32_MMA, PEAK_BF16_MMA) else 20000
+    f, ms = peak_probe(kind, device, iters)
+    iters = int(min(cap, max(1, iters * target_ms / max(ms, 1e-3))))
+    best = 0.0
+    for _ in range(reps):
+        f, ms = peak_probe(kind, device, iters)
+        best = max(best, f / (ms * 1e-3) / 1e12)
+    return best
 
 
 def empty_rowmajor(rows: int, cols: int, planes: int = 4, dtype=torch.bfloat16, device="cuda") -> torch.Tensor:

@@ -201,3 +201,46 @@ def test_residual_norm_matches_oracle(ctx):
     w1, w2 = norms.range_error(P.A, ref.Q1), norms.corange_error(P.A, ref.Q2)
     assert w1 * (1 - 1e-3) <= e1 <= w1 * (1 + 1e-10)
     assert w2 * (1 - 1e-3) <= e2 <= w2 * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 6, 7])
+def test_alg4_basis_spans_oracle_krylov_space(ctx, v):
+    """qlr_qbasis with Algorithm 4 (FP64): the stacked basis (Q1 = QR(K1) for even v, Q2 = QR(K2)
+    for odd v, each new Krylov block deflated against the earlier ones on the GPU) spans the
+    oracle's stacked Krylov space, so the projectors, the singular values of R and the defining
+    relation (X^H Q1 = Q2 R2 / X Q2 = Q1 R1) agree with the oracle's Algorithm 4."""
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_slow_decay(240, 180, 8, 4, v, seed=40 + v)
+    l = P.k + P.p
+    L = qlr.stacked_width(qlr.ALG4, l, v)
+    Ad = dev_rowmajor(P.A, "f64")
+    Od = dev_thin(P.Omega, "f64")
+    Q1, Q2 = qlr.empty_thin(P.m, L, torch.float64), qlr.empty_thin(P.n, L, torch.float64)
+    R = small(L)
+    side = qlr.qbasis(ctx, Ad, P.k, P.p, v, Od, Q1, Q2, R, algo=qlr.ALG4, compute=qlr.COMPUTE_F64,
+                      side=qlr.SIDE_X)
+    assert ctx.sync() == 0 and side == qlr.SIDE_X
+    ref = al.alg4_block_flexible(P.A, P.k, P.p, v, P.Omega)
+    q1, q2, r = host(Q1), host(Q2), small_to_np(R)
+    for q, rq in ((q1, ref.Q1), (q2, ref.Q2)):
+        np.testing.assert_allclose(Q.qmatmul(Q.qH(q), q), Q.qeye(L), atol=1e-12)
+        np.testing.assert_allclose(_proj(q), _proj(rq), atol=1e-9)
+    np.testing.assert_allclose(singular_values(r), singular_values(ref.R), rtol=1e-9, atol=1e-12)
+    lhs = Q.qmatmul(P.A, q2) if v % 2 else Q.qmatmul(Q.qH(P.A), q1)
+    rhs = Q.qmatmul(q1, r) if v % 2 else Q.qmatmul(q2, r)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-9 * np.abs(P.A).max() * P.m)
+
+
+@pytest.mark.parametrize("compute", ["TF32X3", "F32"])
+def test_alg4_fp32_colour_field(ctx, compute):
+    """Algorithm 4 with FP32 storage on a colour field (the config-4 construction at 1200 x 600,
+    k = 30, b = 40, v = 6): the top-k singular values within the FP32 tolerance 1e-4 of the FP64
+    oracle's on the unrounded A.  The field's leading singular value is ~10x the next, so the
+    plain stack of Krylov blocks is numerically rank-deficient at FP32 (the oracle pin
+    test_alg4_fp32_rounding_floor_on_colour_field shows 2e-4..2e-3 from FP32 rounding alone); the
+    GPU deflates each new block against the earlier ones, which keeps the new directions."""
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config_colour(1200, 600, 30, 40, 6, seed=1237)
+    U, S, V, Om, _ = run_gpu(ctx, P, 6, qlr.ALG4, "f32", getattr(qlr, "COMPUTE_" + compute))
+    ref = al.alg4_block_flexible(P.A, P.k, P.p, 6, Om)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-4)
