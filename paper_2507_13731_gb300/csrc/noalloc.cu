@@ -24,8 +24,11 @@ namespace {
 std::mutex g_mu;
 void* g_scratch_addr[QLR_NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device (looked up once per device; the
-// name g_qlr_noalloc_scratch is only a host-side handle and must never be passed to a kernel).
+// Device address of the scratch array on the current device, looked up once per device with that
+// device current (the name g_qlr_noalloc_scratch is only a host-side handle and must never be
+// passed to a kernel).  The cached address belongs to the device's primary context: after a
+// cudaDeviceReset of that device it is stale, so a process that resets a device must not call
+// this entry point on it again.
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= QLR_NOALLOC_MAX_DEVICES) return QLR_EUNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -40,6 +43,20 @@ int scratch_address(int dev, void** out) {
   *out = g_scratch_addr[dev];
   return QLR_OK;
 }
+
+// Makes `dev` current for the call and restores the caller's device on exit.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); ok = false; prev = -1; }
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 int check_qmat_na(const qlr_qmat* q, int layout, bool allow_pure) {
   if (!q) return QLR_EINVAL;
@@ -65,25 +82,36 @@ extern "C" int qlr_qsketch_noalloc(void* stream, int op, const qlr_qmat* A, cons
   if (Y->dtype != QLR_F32 || !(X->dtype == QLR_F32 || (compute == QLR_COMPUTE_BF16 && X->dtype == QLR_BF16)))
     return QLR_EINVAL;
   if ((compute == QLR_COMPUTE_BF16) != (A->dtype == QLR_BF16) || A->dtype == QLR_F64) return QLR_EINVAL;
-  if (!qlr::sketch_tc_supported(op, *A, *X, compute)) return QLR_EUNSUPPORTED;
 
+  // The stream's device runs the call (the legacy default stream means the current device).
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return QLR_ECUDA;
-  void* scratch = nullptr;
-  const int rc = scratch_address(dev, &scratch);
-  if (rc != QLR_OK) return rc;
+  if (cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &dev) != cudaSuccess) {
+    cudaGetLastError();
+    return QLR_ECUDA;
+  }
+  DeviceScope scope(dev);
+  if (!scope.ok) return QLR_ECUDA;
 
   // A context on the stack: no device allocation, no launch statistics timing.
   qlr_ctx ctx;
   ctx.device = dev;
   ctx.stream = static_cast<cudaStream_t>(stream);
   ctx.d_err = err;
+  if (outer == 0 || X->cols == 0) return QLR_OK;                 // Y is empty
+  if (inner == 0) return qlr::zero_qmat(&ctx, *Y);               // empty sums: Y = 0 (a memset)
+  if (!qlr::sketch_tc_supported(op, *A, *X, compute)) return QLR_EUNSUPPORTED;
+
+  void* scratch = nullptr;
+  const int rc = scratch_address(dev, &scratch);
+  if (rc != QLR_OK) return rc;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QLR_ECUDA;
-  // Fewer stream-K CTAs need fewer partial tiles: shrink the CTA budget until the scratch fits.
+  // Stream-K partial tiles take scratch in proportion to the CTA budget: use the largest budget
+  // whose plan fits the array (the need grows with the budget, so the first fit from the top).
+  const int l = (int)X->cols;
   int budget = sms;
-  while (budget > 1 && qlr::sketch_tc_ws(inner, X->cols, budget) > QLR_NOALLOC_SCRATCH_BYTES) budget /= 2;
-  if (qlr::sketch_tc_ws(inner, X->cols, budget) > QLR_NOALLOC_SCRATCH_BYTES) return QLR_ENOMEM;
+  while (budget > 1 && qlr::sketch_tc_need(op, outer, inner, l, compute, budget) > QLR_NOALLOC_SCRATCH_BYTES) --budget;
+  if (qlr::sketch_tc_need(op, outer, inner, l, compute, budget) > QLR_NOALLOC_SCRATCH_BYTES) return QLR_ENOMEM;
   ctx.num_sms = budget;
   ctx.ws = scratch;
   ctx.ws_bytes = QLR_NOALLOC_SCRATCH_BYTES;

@@ -172,6 +172,9 @@ int gemm_simt(qlr_ctx* ctx, const GemmArgs& g);
 // tcgen05 sketch products (see sketch_tc.cu)
 int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws);
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms);
+// Exact scratch bytes sketch_tc takes for this product with a budget of num_sms stream-K CTAs
+// (staged thin operand, stream-K partial tiles, arrival counters; 256-byte aligned slices).
+size_t sketch_tc_need(int op, int64_t M, int64_t K, int l, int compute, int num_sms);
 bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compute);
 
 // Grouped tensor-core sketch over many problems (one launch for the staging of every X and one

@@ -418,10 +418,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
   sketch_tile<KIND, AMODE>(p, blockIdx.x, blockIdx.y, Seg{0, p.kiters, 0, 1, 0, 0, 0});
 }
 
-// Stream-K: fewer output tiles than SMs.  The reduction stages of all tiles, taken in tile order,
-// are cut into gridDim.x equal ranges, one per CTA; a range covers the end of one tile and/or the
-// start of the next (gridDim.x > tiles), each piece is reduced as in sketch_tile and the pieces
-// of a tile are added by the last one to finish.
+// Stream-K: the reduction stages of all tiles, taken in tile order, are cut into gridDim.x equal
+// ranges, one per CTA.  A range may start inside one tile (its tail piece), run through whole
+// tiles, and end inside another (its head piece); each piece is reduced as in sketch_tile, a
+// whole tile writes its output directly, and the pieces of a split tile are added by the last one
+// to finish.  A CTA writes at most two partial tiles: slot 2c for its tail piece, slot 2c + 1 for a
+// head piece that is not its first piece.
 template <int KIND, int AMODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const __grid_constant__ TcParams p) {
   const int64_t K = p.kiters, W = (int64_t)p.mtiles * p.ncb * K, G = gridDim.x, c = blockIdx.x;
@@ -820,11 +822,15 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
   pl.mtiles = (int)((M + TBM - 1) / TBM);
   pl.kiters = (int)((K + pl.bk - 1) / pl.bk);
-  // fewer tiles than SMs: stream-K over every SM, each CTA at least 8 stages (a CTA's range then
-  // covers less than one tile, so at most two pieces)
+  // Stream-K over every SM (each CTA at least 8 stages) when the tiles do not fill whole waves:
+  // fewer tiles than SMs, or a last wave that would leave SMs idle (e.g. 157 row tiles on 152
+  // SMs would take two full tile times).  A CTA's range then holds at most two partial pieces
+  // (the tail of one tile and the head of another) around any number of whole tiles.
   const int64_t tiles = (int64_t)pl.mtiles * pl.ncb;
   const int64_t g = std::min<int64_t>(num_sms, tiles * pl.kiters / 8);
-  pl.grid_sk = (g > tiles) ? (int)g : 0;
+  if (g > tiles) pl.grid_sk = (int)g;
+  else if (tiles > num_sms && tiles % num_sms != 0 && g == num_sms) pl.grid_sk = num_sms;
+  else pl.grid_sk = 0;
   const int cols = 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const bool x3 = pl.kind == K_TF32X3;
@@ -1113,6 +1119,16 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
   const int64_t ldo = (rows_in + 7) / 8 * 8;
   return (size_t)2 * 4 * ldo * l * 4 + (size_t)2 * (num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
+}
+
+size_t sketch_tc_need(int op, int64_t M, int64_t K, int l, int compute, int num_sms) {
+  const Plan pl = make_plan(compute, op, M, K, l, num_sms);
+  const int64_t ldo = (K + 7) / 8 * 8;
+  const size_t xesz = (pl.kind == K_BF16) ? 2 : 4;
+  size_t b = align256((size_t)4 * ldo * l * xesz);
+  if (pl.kind == K_TF32X3) b += align256((size_t)4 * ldo * l * 4);
+  if (pl.grid_sk > 0) b += align256((size_t)2 * pl.grid_sk * 4 * TBM * pl.nb * sizeof(float));
+  return b + align256((size_t)pl.mtiles * pl.ncb * sizeof(unsigned));
 }
 
 int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qmat& Y, int compute, WsArena& ws) {
