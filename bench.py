@@ -1,17 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the pass-efficient randomized quaternion QSVD on GB300 (one JSON line).
 
-Workload (one "step"): the FP32 arbitrary-pass range finder workload -- a 4096 x 4096 quaternion
-matrix with FP32 planes, sigma_i = 1/i and Haar-like singular vectors, k = 100, p = 10 -- run
-through Algorithm 2 with each pass budget v in {2, 3, 4, 6, 8}: 23 sketch passes with their
-orthonormalisations, five core QSVDs and lifts.  Metric: sketch passes per second (whole job);
-A-read TB/s and the per-v rank-k QSVD times go in extra keys.  On one GPU the line also carries
-`batched` (512 uneven BF16 problems as one batch plan against the plain FP32 per-problem loop),
-`completion` (matrix completion's alternating updates on a 4096 x 4096 matrix with 70 % of the
-entries removed, and the masked update kernel's roofline) and `lowrank_sweep` (the random rank-50
-example at m = n = 500..4000); --no-batched / --no-completion / --no-sweep skip them.
+Headline workload (one "step"): the pass-efficient block Krylov workload -- a 20000 x 10000 pure
+quaternion colour field (FP32 planes; per colour plane a sum of 64 random 2-D cosines, min-max
+scaled to [0, 1], plus uniform noise of amplitude 0.05) -- through Algorithm 4 with k = 50, block
+size b = 60 and v = 6 views: six sketch passes (five of 60 columns, the last of 180), the deflated
+Krylov stack and its QR, the core QSVD of the 180 x 180 factor and the lifts.  Metric: sketch passes
+per second (whole job); extra keys: A-read TB/s, ms per QSVD and the result's error against the FP64
+oracle (the oracle's values on the same seeded input are stored in tests/golden/fullsize_oracle.json
+by tests/golden/make_fullsize_golden.py): the largest relative error of the top-k singular values
+and the projection errors ||A - Q1 Q1^H A||_2, ||A - A Q2 Q2^H||_2 of the call's final bases
+(estimated on the GPU by qlr_residual_norm, outside the timed region).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+On one GPU the line also carries
+  `peaks`       the measured dense rates of this GPU's tensor and CUDA cores (the roofline
+                denominators other than HBM and BF16, which MEASURED_PEAKS.json holds);
+  `mixed_precision` the 16384 x 8192 exponential-decay workload (k = 200, p = 20, v = 4, Algorithm 2)
+                with BF16 storage against the same call in 3xTF32 and in plain FP32 (SIMT), each
+                with its time and its error against the oracle, plus the BF16 sketch's roofline;
+  `pass_sweep`  the 4096 x 4096 slow-decay workload through Algorithm 2 at v in {2, 3, 4, 6, 8};
+  `batched`, `completion`, `lowrank_sweep` as named (--no-batched / --no-completion / --no-sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--compute MODE]
 
 N > 1 runs under torchrun: every rank runs its own replica (weak scaling, no collective on the
 data path); rank 0 prints the line with the max-over-ranks time.
@@ -31,11 +41,21 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "sketch passes/s & A-read TB/s; rank-k QSVD time at stated error, BF16/batched vs FP32"
+# headline: the block Krylov workload
+HM, HN, HK, HB, HV = 20000, 10000, 50, 60, 6
+WORKLOAD = ("pure quaternion colour field 20000x10000 (64 random 2-D cosines per colour plane, min-max scaled, "
+            "+U[-0.05,0.05] noise), FP32 planes, Algorithm 4, k=50, b=60, v=6 (5 passes of 60 columns + 1 of 180)")
+# the mixed-precision workload
+C3 = dict(m=16384, n=8192, k=200, p=20, v=4)
+C3_WORKLOAD = "exp-decay 16384x8192 quaternion, sigma_i=exp(-i/50), Haar-like vectors, k=200, p=20, Algorithm 2, v=4"
+# the pass sweep
 M = N = 4096
 K_RANK, P_OVER = 100, 10
 PASSES = (2, 3, 4, 6, 8)
-METRIC = "sketch passes/s & A-read TB/s; rank-k QSVD time at stated error, BF16/batched vs FP32"
-WORKLOAD = "slow-decay 4096x4096 quaternion, FP32 planes, sigma_i=1/i, k=100, p=10, Algorithm 2 at v in {2,3,4,6,8}"
+C2_WORKLOAD = "slow-decay 4096x4096 quaternion, FP32 planes, sigma_i=1/i, k=100, p=10, Algorithm 2 at v in {2,3,4,6,8}"
+# probe-measured peaks of this run (filled by peaks_leg)
+_MEASURED = {}
 
 
 def _peaks():
@@ -43,6 +63,13 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _golden():
+    try:
+        return json.load(open(os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")))
+    except Exception:
+        return {}
 
 
 class ClockSampler:
@@ -91,60 +118,73 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_work(kid: str, compute: str):
-    """(flops, bytes, bound, peak, unit, peak_note) per launch of a kernel class at this workload.
-    Flops count 32 m n l per quaternion sketch (the Hamilton product, no split overhead)."""
+# ------------------------------------------------------------------------------------------
+# roofline arithmetic (host logic, tested on CPU)
+def sketch_work(m: int, n: int, widths, pure: bool, esz: int):
+    """Algorithmic work of sketch passes over an m x n quaternion A: flops 32 m n l per pass (24 for a
+    pure A: its real plane is zero), bytes = A read once per pass (4 or 3 planes of esz bytes)."""
+    planes = 3 if pure else 4
+    flops = sum((8.0 * planes) * m * n * l for l in widths)
+    nbytes = float(len(widths)) * planes * m * n * esz
+    return flops, nbytes
+
+
+def peak_for(compute: str):
+    """(peak, unit, products per algorithmic flop, source note) of a sketch's arithmetic."""
     pk, src = _peaks()
-    l = K_RANK + P_OVER
-    sk_flops, sk_bytes = 32.0 * M * N * l, 4.0 * M * N * 4
-    tf32 = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
-    if kid == "sketch_tc":
-        if compute == "BF16":
-            return sk_flops, sk_bytes / 2, "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s", \
-                f"bf16 sustained ({src})"
-        return sk_flops, sk_bytes, "tensor", tf32, "TFLOP/s", f"tf32 = bf16 sustained ({src}) x 1.1/2.25 nominal"
-    fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12          # unit counts x max SM clock
-    fp64 = 1.25                                         # nominal dense FP64 of the part
-    if kid == "sketch_simt":
-        return sk_flops, sk_bytes, "alu", fp32_simt, "TFLOP/s", "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    if kid == "gram":
-        return 32.0 * M * l * (l + 1) / 2, 16.0 * M * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
-    if kid == "chol":
-        return 32.0 * l ** 3 / 6, 32.0 * l * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
-    if kid == "tri_inv":
-        return 32.0 * l ** 3 / 6, 32.0 * l * l, "alu", fp64, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
-    if kid == "jacobi":
-        return 8 * 56.0 * l ** 3 / 2, 32.0 * l * l, "alu", fp32_simt, "TFLOP/s", "FP32 SIMT peak (one CTA can reach 1/152 of it)"
-    return None
+    if compute == "BF16":
+        return pk.get("bf16_tflops", 1900.0), "TFLOP/s", 1, f"bf16 burst ({src}, MEASURED_PEAKS.json)"
+    if compute in ("TF32", "TF32X3", "MIXED"):
+        if "tf32_mma" in _MEASURED:
+            return _MEASURED["tf32_mma"], "TFLOP/s", 3 if compute == "TF32X3" else 1, \
+                "tf32 tcgen05 MMA loop measured in this run (qlr_peak_probe)"
+        return pk.get("bf16_tflops", 1900.0) * 0.5, "TFLOP/s", 3 if compute == "TF32X3" else 1, \
+            f"tf32 = bf16 burst ({src}) x 1/2 nominal ratio (probe not run)"
+    if compute == "F32":
+        if "fp32_fma" in _MEASURED:
+            return _MEASURED["fp32_fma"], "TFLOP/s", 1, "FP32 FMA loop measured in this run (qlr_peak_probe)"
+        return 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s", 1, "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal)"
+    return None, None, 1, None
 
 
-def roofline(stats, compute, steps):
-    live = {k: v for k, v in stats.items() if v[0] > 0}
-    dom = max(live, key=lambda k: live[k][1])
-    n, ms = live[dom]
-    w = algorithmic_work(dom, compute)
-    out = {"kernel": dom, "launches": n, "avg_ms": ms / n}
-    if w is None:
-        out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
-        return out
-    flops, nbytes, bound, peak, unit, note = w
-    sec = ms / n / 1e3
-    if bound == "hbm":
+def sketch_roofline(flops: float, nbytes: float, ms: float, launches: int, compute: str, traffic=None):
+    """Roofline object of the sketch launches of a timed region: achieved = algorithmic work of all
+    launches / their summed CUDA-event time; bound = the roof the work meets first."""
+    pk, src = _peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    peak, unit, products, note = peak_for(compute)
+    sec = ms / 1e3
+    t_hbm = nbytes / (hbm * 1e9)
+    t_ops = flops * products / (peak * 1e12) if peak else 0.0
+    out = {"kernel": "sketch_tc" if compute != "F32" else "sketch_simt", "launches": launches,
+           "avg_ms": round(ms / max(launches, 1), 5), "algorithmic_flops_per_launch": flops / max(launches, 1),
+           "algorithmic_bytes_per_launch": nbytes / max(launches, 1), "traffic": traffic}
+    if t_hbm >= t_ops:
         ach = nbytes / sec / 1e9
+        out.update({"bound": "hbm", "achieved": round(ach, 2), "peak": round(hbm, 1), "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "peak_source": f"HBM copy ({src}, MEASURED_PEAKS.json)"})
     else:
         ach = flops / sec / 1e12
-    traffic = None
+        out.update({"bound": "alu" if compute == "F32" else "tensor", "achieved": round(ach, 3),
+                    "peak": round(peak, 2), "unit": unit, "frac": round(ach / peak, 4), "peak_source": note})
+    out["hbm_gbs"] = round(nbytes / sec / 1e9, 1)
+    if products > 1:
+        out["products_per_flop"] = products
+        out["frac_of_own_ceiling"] = round(out["frac"] * products, 4) if out["bound"] != "hbm" else None
+    return out
+
+
+def traffic_for(key: str):
+    """DRAM bytes per launch from profiles/traffic.json, only while the kernel's source is the one
+    the counters were taken on."""
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get(dom)
+        ent = tr.get(key)
         if ent and ent.get("source_sha") == _source_sha(ent.get("source", "")):
-            traffic = ent.get("dram_bytes_per_launch")
+            return ent.get("dram_bytes_per_launch")
     except Exception:
         pass
-    out.update({"bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3), "unit": unit,
-                "frac": round(ach / peak, 4), "traffic": traffic, "peak_source": note,
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes})
-    return out
+    return None
 
 
 def _source_sha(rel):
@@ -153,15 +193,163 @@ def _source_sha(rel):
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if rel and os.path.exists(p) else None
 
 
-def cpu_oracle_sample(P, passes=2):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: Algorithm 2 with v=2 on
-    the full matrix.  Returns (passes/s, seconds, threads)."""
-    from oracle import algorithms as al
+def sigma_rel_err(S, ref) -> float:
+    import numpy as np
+    S, ref = np.asarray(S, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(S[:len(ref)] - ref) / ref))
+
+
+# ------------------------------------------------------------------------------------------
+def colour_problem():
+    import synth
+    return synth.config4()
+
+
+def errors_vs_oracle(ctx, A, P, S, algo, v, compute, golden, side=0, iters=30, nvec=8):
+    """The result's error statement: sigma relative error against the oracle's, and the projection
+    errors of the call's final bases (qlr_qbasis, then qlr_residual_norm) beside the oracle's."""
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import qlr
+    out = {}
+    if golden and "sigma" in golden:
+        out["sigma_rel_err"] = float(f"{sigma_rel_err(S, golden['sigma']):.3e}")
+    l = P.k + P.p
+    L = qlr.stacked_width(algo, l, v)
+    om = qlr.to_thin(torch.from_numpy(P.Omega).float().to(A.device))
+    Q1, Q2 = qlr.empty_thin(P.m, L, device=A.device), qlr.empty_thin(P.n, L, device=A.device)
+    R = torch.zeros(4, L, L, dtype=torch.float64, device=A.device)
+    qlr.qbasis(ctx, A, P.k, P.p, v, om, Q1, Q2, R, algo=algo, compute=compute, side=qlr.SIDE_X)
+    start = qlr.to_thin(torch.from_numpy(synth.gaussian_qmat(4242, P.n, nvec)).float().to(A.device))
+    e1 = qlr.residual_norm(ctx, A, Q1, qlr.SIDE_X, start, iters=iters)
+    e2 = qlr.residual_norm(ctx, A, Q2, qlr.SIDE_XH, start, iters=iters)
+    out["range_err"] = float(f"{e1:.6e}")
+    out["corange_err"] = float(f"{e2:.6e}")
+    if golden and "range_err" in golden:
+        out["oracle_range_err"] = golden["range_err"]
+        out["oracle_corange_err"] = golden["corange_err"]
+        out["range_err_rel_diff"] = float(f"{abs(e1 - golden['range_err']) / golden['range_err']:.3e}")
+        out["corange_err_rel_diff"] = float(f"{abs(e2 - golden['corange_err']) / golden['corange_err']:.3e}")
+    out["estimator"] = f"block power iteration, {nvec} vectors, {iters} steps (a lower bound converging to the norm)"
+    return out
+
+
+def peaks_leg(dev):
+    """Dense rates of this GPU measured by the library's probe kernels (qlr_peak_probe)."""
+    from paper_2507_13731_gb300 import qlr
+    d = dev.index or 0
+    out = {}
+    for name, kind in (("tf32_mma", qlr.PEAK_TF32_MMA), ("bf16_mma", qlr.PEAK_BF16_MMA),
+                       ("fp32_fma", qlr.PEAK_FP32_FMA), ("fp64_fma", qlr.PEAK_FP64_FMA)):
+        try:
+            out[name] = round(qlr.measure_peak(kind, d), 2)
+        except Exception as e:                     # reported, never fatal to the headline line
+            out[name] = None
+            out[name + "_error"] = f"{type(e).__name__}: {e}"
+    _MEASURED.update({k: v for k, v in out.items() if isinstance(v, float)})
+    out["unit"] = "TFLOP/s"
+    out["how"] = ("tcgen05 MMA loop, M=128 N=256 (K=8 tf32 / 16 bf16) from shared memory, one CTA per SM; "
+                  "FMA loops, 8 independent chains per thread, 8 CTAs of 256 threads per SM; best of 3 ~40 ms launches")
+    return out
+
+
+def cpu_oracle_sample(P):
+    """The FP64 oracle, as it stands, on a bounded sample of the headline workload: one view of
+    Algorithm 4 (Y = X Omega and the QR of Y) on the full matrix.  Returns (passes/s, s, threads)."""
+    from oracle import quaternion as Q
+    from oracle.qr import qr
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     t0 = time.perf_counter()
-    al.alg2_arbitrary_pass(P.A, P.k, P.p, passes, P.Omega)
+    qr(Q.qmatmul(P.A, P.Omega))
     dt = time.perf_counter() - t0
-    return passes / dt, dt, threads
+    return 1.0 / dt, dt, threads
+
+
+def mixed_precision_leg(dev, golden, reps=3):
+    """The 16384 x 8192 workload (Algorithm 2, v = 4) with BF16 storage against the same call in
+    3xTF32 and in plain FP32 (SIMT) on FP32 storage: time per QSVD, error against the oracle and
+    the sketch's roofline in each arithmetic."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config3()
+    ctx = qlr.Context(dev.index or 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    om = qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev))
+    U, V = qlr.empty_thin(P.m, P.k, device=dev), qlr.empty_thin(P.n, P.k, device=dev)
+    S = torch.zeros(P.k, dtype=torch.float64, device=dev)
+    gold = golden.get("c3", {}).get("v4")
+    out = {"workload": C3_WORKLOAD}
+    Af = torch.from_numpy(P.A).float().to(dev).contiguous()
+    Ab = Af.to(torch.bfloat16).contiguous()
+    for mode, Ad in (("BF16", Ab), ("TF32X3", Af), ("F32", Af)):
+        comp = getattr(qlr, "COMPUTE_" + mode)
+        n = 1 if mode == "F32" else reps
+        qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, 4, om, U, S, V, compute=comp, side=qlr.SIDE_X)
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        e0.record()
+        for _ in range(n):
+            qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, 4, om, U, S, V, compute=comp, side=qlr.SIDE_X)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.set_timing(False)
+        ms = e0.elapsed_time(e1) / n
+        st = ctx.stats()
+        ent = {"ms_per_qsvd": round(ms, 3)}
+        ent.update(errors_vs_oracle(ctx, Ad, P, S.cpu().numpy(), qlr.ALG2, 4, comp, gold))
+        kid = "sketch_simt" if mode == "F32" else "sketch_tc"
+        nl, kms = st[kid]
+        if nl:
+            fl, nb = sketch_work(P.m, P.n, [P.k + P.p] * 4 * n, False, 2 if mode == "BF16" else 4)
+            ent["sketch"] = sketch_roofline(fl, nb, kms, nl, mode,
+                                            traffic_for("sketch_tc_bf16_c3") if mode == "BF16" else None)
+        ent["kernels_ms_per_qsvd"] = {k: round(t / n, 3) for k, (c, t) in st.items() if c}
+        out[mode] = ent
+    rc = ctx.sync()
+    out["bf16_speedup_vs_fp32_simt"] = round(out["F32"]["ms_per_qsvd"] / out["BF16"]["ms_per_qsvd"], 2)
+    out["tf32x3_speedup_vs_fp32_simt"] = round(out["F32"]["ms_per_qsvd"] / out["TF32X3"]["ms_per_qsvd"], 2)
+    out["tolerance"] = {"BF16": 2e-2, "TF32X3": 1e-4, "F32": 1e-4}
+    out["device_error"] = rc
+    ctx.close()
+    return out
+
+
+def pass_sweep_leg(dev, golden, compute="TF32X3", reps=3):
+    """The 4096 x 4096 slow-decay workload through Algorithm 2 at each pass budget: ms per QSVD and
+    the singular values' error against the oracle."""
+    import torch
+
+    import synth
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config2(2)
+    ctx = qlr.Context(dev.index or 0)
+    A = torch.from_numpy(P.A).float().to(dev).contiguous()
+    om = qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev))
+    U, V = qlr.empty_thin(M, K_RANK, device=dev), qlr.empty_thin(N, K_RANK, device=dev)
+    S = torch.zeros(K_RANK, dtype=torch.float64, device=dev)
+    comp = getattr(qlr, "COMPUTE_" + compute)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": C2_WORKLOAD, "compute": compute}
+    for v in PASSES:
+        qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, v, om, U, S, V, compute=comp, side=qlr.SIDE_X)
+        e0.record()
+        for _ in range(reps):
+            qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, v, om, U, S, V, compute=comp, side=qlr.SIDE_X)
+        e1.record()
+        torch.cuda.synchronize()
+        ent = {"ms_per_qsvd": round(e0.elapsed_time(e1) / reps, 3)}
+        gold = golden.get("c2", {}).get(f"v{v}")
+        if gold:
+            ent["sigma_rel_err"] = float(f"{sigma_rel_err(S.cpu().numpy(), gold['sigma']):.3e}")
+        out[f"v{v}"] = ent
+    out["device_error"] = ctx.sync()
+    ctx.close()
+    return out
 
 
 BATCH_WORKLOAD = ("512 pure quaternion matrices, m ~ U{64..1024}, n ~ U{64..768}, rank r ~ U{8..64} plus "
@@ -169,9 +357,9 @@ BATCH_WORKLOAD = ("512 pure quaternion matrices, m ~ U{64..1024}, n ~ U{64..768}
 
 
 def batched_leg(dev, steps=5):
-    """The batched workload: one batch plan (grouped tensor-core sketch per pass, per-problem
-    orthonormalisation lanes, CUDA graph, tile-order autotuner) against the plain FP32 comparator,
-    a loop of per-problem calls with FP32 storage and the FP32 SIMT sketch."""
+    """The batched workload: one batch plan (grouped tensor-core sketch per pass, grouped
+    orthonormalisation and core QSVD launches, CUDA graph, autotuner) against the plain FP32
+    comparator, a loop of per-problem calls with FP32 storage and the FP32 SIMT sketch."""
     import numpy as np
     import torch
 
@@ -287,13 +475,12 @@ def completion_leg(dev, steps=5):
     flops = 32.0 * m * n * k
     obs = float(P.extra["mask"].mean())
     nbytes = m * n * (1 + 16 + 12 * obs)           # mask, C written, M read at observed entries
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    peak, unit, _, note = peak_for("F32")
     ach = flops / (up_ms / 1e3) / 1e12
     return {"workload": COMPLETE_WORKLOAD, "iters": COMPLETE_ITERS, "ms_total": round(total_ms, 3),
             "ms_per_iter": round(total_ms / COMPLETE_ITERS, 3), "unobserved_rel_err": round(err, 6),
             "update_kernel": {"ms": round(up_ms, 4), "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-                              "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                              "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                              "unit": "TFLOP/s", "frac": round(ach / peak, 4), "peak_source": note,
                               "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                               "hbm_gbs": round(nbytes / (up_ms / 1e3) / 1e9, 1)},
             "device_error": rc}
@@ -375,11 +562,11 @@ def dist_setup():
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only), each step one view
+    of Algorithm 4 on the headline matrix."""
     if rank != 0:
         return
-    import synth
-    P = synth.config2(2)
+    P = colour_problem()
     for _ in range(args.warmup):
         cpu_oracle_sample(P)
     t0 = time.perf_counter()
@@ -387,17 +574,80 @@ def run_reference(args, ws, rank):
     for _ in range(args.steps):
         _, _, thr = cpu_oracle_sample(P)
     dt = time.perf_counter() - t0
-    value = 2 * args.steps / dt
+    value = args.steps / dt
+    sample = "one view of Algorithm 4 per step: Y = X Omega (60 columns) and the Householder QR of Y, full 20000x10000 matrix"
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "sketch passes/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "Algorithm 2, v=2, full 4096x4096 matrix per step"},
+            "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": round(value, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
-                             "sample": "Algorithm 2 with v=2 on the full 4096x4096 matrix per step"},
+                             "sample": sample},
             "e2e": {"value": round(value, 5), "unit": "sketch passes/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+def profile_driver(args):
+    """Small driver for ncu captures and probes: the named workload's A and Omega, then
+    `warmup + steps` calls of one sketch pass (--only sketch --op N|H --ell L) or one QSVD
+    (--only qsvd), or a batch plan (--only batch), or the completion update (--only complete), or
+    the peak probes (--only peaks).  Prints one JSON line with the mean CUDA-event time."""
+    import numpy as np
+    import torch
+
+    if args.only == "batch":
+        return batch_driver(args)
+    if args.only == "complete":
+        return complete_driver(args)
+    import synth
+    from paper_2507_13731_gb300 import build, qlr
+    build.build()
+    if args.only == "peaks":
+        print(json.dumps({"only": "peaks", "peaks": peaks_leg(torch.device("cuda", 0))}), flush=True)
+        return 0
+    compute = getattr(qlr, "COMPUTE_" + args.compute)
+    a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
+    if args.config == "c4":
+        P, algo, v = colour_problem(), qlr.ALG4, HV
+        A = torch.from_numpy(np.ascontiguousarray(P.A[1:])).to(a_dt).cuda().contiguous()
+    elif args.config == "c3":
+        P, algo, v = synth.config3(), qlr.ALG2, 4
+        A = torch.from_numpy(P.A).to(a_dt).cuda().contiguous()
+    else:
+        P, algo, v = synth.config2(args.passes), qlr.ALG2, args.passes
+        A = torch.from_numpy(P.A).to(a_dt).cuda().contiguous()
+    m, n = P.m, P.n
+    ell = args.ell or (P.k + P.p)
+    ctx = qlr.Context(0)
+    U, V = qlr.empty_thin(m, P.k), qlr.empty_thin(n, P.k)
+    S = torch.zeros(P.k, dtype=torch.float64, device="cuda")
+    om = qlr.to_thin(torch.from_numpy(P.Omega).float().cuda())
+    op = qlr.OP_N if args.op == "N" else qlr.OP_H
+    X = qlr.to_thin(torch.randn(4, n if op == qlr.OP_N else m, ell).cuda())
+    Y = qlr.empty_thin(m if op == qlr.OP_N else n, ell)
+
+    def call():
+        if args.only == "sketch":
+            qlr.qsketch(ctx, op, A, X, Y, compute)
+        else:
+            qlr.qsvd_lowrank(ctx, A, P.k, P.p, v, om, U, S, V, algo=algo, compute=compute, side=qlr.SIDE_X)
+
+    for _ in range(args.warmup):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    rc = ctx.sync()
+    print(json.dumps({"only": args.only, "config": args.config, "op": args.op, "ell": ell, "passes": v,
+                      "compute": args.compute, "ms_per_call": e0.elapsed_time(e1) / args.steps,
+                      "device_error": rc}), flush=True)
+    ctx.close()
+    return 0 if rc == 0 else 1
 
 
 def batch_driver(args):
@@ -469,67 +719,23 @@ def complete_driver(args):
     return 0 if rc == 0 else 1
 
 
-def profile_driver(args):
-    """Small driver for ncu captures: the bench workload's A and Omega, then `warmup + steps`
-    calls of one sketch pass (--only sketch --op N|H) or one QSVD with --passes v (--only qsvd).
-    Prints one JSON line with the mean CUDA-event time of the timed calls."""
-    import numpy as np
-    import torch
-
-    if args.only == "batch":
-        return batch_driver(args)
-    if args.only == "complete":
-        return complete_driver(args)
-
-    import synth
-    from paper_2507_13731_gb300 import build, qlr
-    build.build()
-    P = synth.config2(args.passes)
-    compute = getattr(qlr, "COMPUTE_" + args.compute)
-    a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
-    A = torch.from_numpy(P.A).to(a_dt).cuda().contiguous()
-    om = qlr.to_thin(torch.from_numpy(P.Omega).float().cuda())
-    ctx = qlr.Context(0)
-    U, V = qlr.empty_thin(M, K_RANK), qlr.empty_thin(N, K_RANK)
-    S = torch.zeros(K_RANK, dtype=torch.float64, device="cuda")
-    Y = qlr.empty_thin(M, K_RANK + P_OVER)
-    op = qlr.OP_N if args.op == "N" else qlr.OP_H
-
-    def call():
-        if args.only == "sketch":
-            qlr.qsketch(ctx, op, A, om, Y, compute)
-        else:
-            qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, args.passes, om, U, S, V, compute=compute, side=qlr.SIDE_X)
-
-    for _ in range(args.warmup):
-        call()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        call()
-    e1.record()
-    torch.cuda.synchronize()
-    rc = ctx.sync()
-    print(json.dumps({"only": args.only, "op": args.op, "passes": args.passes, "compute": args.compute,
-                      "ms_per_call": e0.elapsed_time(e1) / args.steps, "device_error": rc}), flush=True)
-    ctx.close()
-    return 0 if rc == 0 else 1
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32"])
+    ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32", "MIXED"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
     ap.add_argument("--no-completion", action="store_true", help="skip the matrix-completion leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the random low-rank size sweep")
-    ap.add_argument("--only", choices=["sketch", "qsvd", "batch", "complete"], default=None,
-                    help="profiling driver: time only sketch passes, single QSVDs or batch runs (for ncu captures)")
+    ap.add_argument("--no-legs", action="store_true", help="headline only (no peaks / mixed / sweeps / batched)")
+    ap.add_argument("--only", choices=["sketch", "qsvd", "batch", "complete", "peaks"], default=None,
+                    help="profiling driver: time only sketch passes, single QSVDs, batch runs or probes")
+    ap.add_argument("--config", choices=["c2", "c3", "c4"], default="c4")
     ap.add_argument("--op", choices=["N", "H"], default="N")
+    ap.add_argument("--ell", type=int, default=0)
     ap.add_argument("--passes", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -546,34 +752,28 @@ def main():
     import numpy as np
     import torch
 
-    import synth
     from paper_2507_13731_gb300 import build, qlr
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    P = synth.config2(4)
+    golden = _golden()
+    legs = ws == 1 and not args.no_legs
+    peaks = peaks_leg(dev) if legs else None
+    P = colour_problem()
     compute = getattr(qlr, "COMPUTE_" + args.compute)
-    a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
-    A_host = torch.from_numpy(P.A).to(a_dt).contiguous().pin_memory()
+    A_host = torch.from_numpy(np.ascontiguousarray(P.A[1:])).float().contiguous().pin_memory()
     Om_host = torch.from_numpy(np.ascontiguousarray(P.Omega.transpose(0, 2, 1))).float().contiguous().pin_memory()
     A = A_host.to(dev, non_blocking=True)
     om_store = Om_host.to(dev, non_blocking=True)
     om = om_store.transpose(1, 2)                                    # column-major n x l view
-    U = qlr.empty_thin(M, K_RANK, device=dev)
-    V = qlr.empty_thin(N, K_RANK, device=dev)
-    S = torch.zeros(len(PASSES), K_RANK, dtype=torch.float64, device=dev)
+    U = qlr.empty_thin(HM, HK, device=dev)
+    V = qlr.empty_thin(HN, HK, device=dev)
+    S = torch.zeros(HK, dtype=torch.float64, device=dev)
     ctx = qlr.Context(local)
-    ctx.reserve(max(qlr.workspace_size(M, N, K_RANK, P_OVER, v, qlr.ALG2, compute) for v in PASSES))
-    qsvd_ms = {v: [] for v in PASSES}
-    ev = {v: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for v in PASSES}
+    ctx.reserve(qlr.workspace_size(HM, HN, HK, HB - HK, HV, qlr.ALG4, compute))
 
-    def step(record=False):
-        for i, v in enumerate(PASSES):
-            if record:
-                ev[v][0].record()
-            qlr.qsvd_lowrank(ctx, A, K_RANK, P_OVER, v, om, U, S[i], V, compute=compute, side=qlr.SIDE_X)
-            if record:
-                ev[v][1].record()
+    def step():
+        qlr.qsvd_lowrank(ctx, A, HK, HB - HK, HV, om, U, S, V, algo=qlr.ALG4, compute=compute, side=qlr.SIDE_X)
 
     for _ in range(args.warmup):
         step()
@@ -595,11 +795,9 @@ def main():
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0e.record()
     for s in range(args.steps):
-        step(record=(s == args.steps - 1))
+        step()
     t1e.record()
     torch.cuda.synchronize()
-    for v in PASSES:
-        qsvd_ms[v].append(ev[v][0].elapsed_time(ev[v][1]))
     barrier()
     clk = clocks.stop()
     ctx.set_timing(False)
@@ -607,16 +805,18 @@ def main():
     stats = ctx.stats()
     rc = ctx.sync()
     elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
-    passes_per_step = sum(PASSES)
+    widths = [HB] * (HV - 1) + [HB * (HV // 2)]
+    passes_per_step = len(widths)
     value = whole_job_rate(passes_per_step * args.steps, ws, elapsed_ms)
     a_bytes = A.numel() * A.element_size()
     tbs = ws * passes_per_step * args.steps * a_bytes / (elapsed_ms / 1e3) / 1e12
     gpu_launches = sum(n for n, _ in stats.values())
+    S_gpu = S.cpu().numpy()
 
     # end to end through the C ABI with host buffers: H2D of A and Omega, D2H of U, S, V per step
-    U_h = torch.empty(4, K_RANK, M, dtype=torch.float32).pin_memory()
-    V_h = torch.empty(4, K_RANK, N, dtype=torch.float32).pin_memory()
-    S_h = torch.empty(len(PASSES), K_RANK, dtype=torch.float64).pin_memory()
+    U_h = torch.empty(4, HK, HM, dtype=torch.float32).pin_memory()
+    V_h = torch.empty(4, HK, HN, dtype=torch.float32).pin_memory()
+    S_h = torch.empty(HK, dtype=torch.float64).pin_memory()
     e2e_steps = max(2, min(args.steps, 3))
     barrier()
     torch.cuda.synchronize()
@@ -639,44 +839,68 @@ def main():
 
     line = None
     if rank == 0:
-        roof = roofline(stats, args.compute, args.steps)
-        cpu = None
-        batched = None
-        if ws == 1 and not args.no_batched:
-            batched = batched_leg(dev)
-        completion = None
-        if ws == 1 and not args.no_completion:
-            try:
-                completion = completion_leg(dev)
-            except Exception as e:                 # reported, never fatal to the headline line
-                completion = {"error": f"{type(e).__name__}: {e}"}
-        sweep = None
-        if ws == 1 and not args.no_sweep:
-            try:
-                sweep = lowrank_sweep_leg(dev)
-            except Exception as e:                 # reported, never fatal to the headline line
-                sweep = {"error": f"{type(e).__name__}: {e}"}
+        flops, nbytes = sketch_work(HM, HN, widths * args.steps, True, 4)
+        kid = "sketch_simt" if args.compute == "F32" else "sketch_tc"
+        nl, kms = stats[kid]
+        roof = sketch_roofline(flops, nbytes, kms, nl, args.compute,
+                               traffic_for(f"sketch_tc_{args.compute.lower()}_c4"))
+        dom = max(stats, key=lambda k: stats[k][1])
+        roof["dominant_class"] = dom
+        roof["class_share"] = round(kms / max(sum(t for _, t in stats.values()), 1e-9), 4)
+        errs = errors_vs_oracle(ctx, A, P, S_gpu, qlr.ALG4, HV, compute, golden.get("c4", {}).get("v6"))
+        cpu = mixed = sweep2 = batched = completion = sweep = None
+        if legs:
+            for name, fn in (("mixed", lambda: mixed_precision_leg(dev, golden)),
+                             ("sweep2", lambda: pass_sweep_leg(dev, golden)),
+                             ("batched", None if args.no_batched else lambda: batched_leg(dev)),
+                             ("completion", None if args.no_completion else lambda: completion_leg(dev)),
+                             ("sweep", None if args.no_sweep else lambda: lowrank_sweep_leg(dev))):
+                if fn is None:
+                    continue
+                try:
+                    res = fn()
+                except Exception as e:                 # reported, never fatal to the headline line
+                    res = {"error": f"{type(e).__name__}: {e}"}
+                if name == "mixed":
+                    mixed = res
+                elif name == "sweep2":
+                    sweep2 = res
+                elif name == "batched":
+                    batched = res
+                elif name == "completion":
+                    completion = res
+                else:
+                    sweep = res
         if ws == 1 and not args.no_cpu_baseline:
             val, secs, thr = cpu_oracle_sample(P)
             cpu = {"value": round(val, 5), "unit": "sketch passes/s", "cores": thr, "kind": "oracle",
-                   "sample": f"Algorithm 2 with v=2 on the full 4096x4096 matrix ({secs:.1f} s)"}
+                   "sample": f"one view of Algorithm 4 on the full matrix: Y = X Omega (60 columns) and the "
+                             f"Householder QR of Y ({secs:.1f} s)"}
+        dtypes = {"TF32X3": "f32 (3xTF32 tensor-core sketch, FP32 accumulation; FP64-class Gram and Cholesky)",
+                  "MIXED": "f32/tf32 (TF32 sketches for the Krylov blocks, 3xTF32 for the final pass; FP64-class "
+                           "Gram and Cholesky)",
+                  "F32": "f32 (SIMT)", "TF32": "tf32", "BF16": "bf16"}
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "sketch passes/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"TF32X3": "f32 (3xTF32 tensor-core sketch; FP64-class Gram (exact BF16 slices on tensor cores) "
-                                "and Cholesky (double-FP32))", "F32": "f32 (SIMT)",
-                      "BF16": "bf16 (FP32 accumulate; FP64-class Gram and Cholesky)", "TF32": "tf32"}[args.compute],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "passes": list(PASSES), "compute": args.compute,
-                       "l2": "inputs larger than L2 (A = %.0f MB)" % (a_bytes / 1e6), "parallelism": f"replicas x{ws}"},
+            "dtype": dtypes[args.compute], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "compute": args.compute, "passes_per_step": passes_per_step,
+                       "pass_widths": widths,
+                       "l2": "inputs larger than L2 (A = %.0f MB > 129 MB L2)" % (a_bytes / 1e6),
+                       "parallelism": f"replicas x{ws}"},
             "a_read_tbs": round(tbs, 4),
-            "qsvd_ms": {str(v): round(statistics.mean(qsvd_ms[v]), 3) for v in PASSES},
+            "qsvd_ms": round(elapsed_ms / args.steps, 3),
+            "error_vs_oracle": errs,
+            "tolerance": {"sigma_rel": 1e-4},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": "sketch passes/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
+            "peaks": peaks,
+            "mixed_precision": mixed,
+            "pass_sweep": sweep2,
             "batched": batched,
             "completion": completion,
             "lowrank_sweep": sweep,

@@ -65,6 +65,8 @@ struct TcParams {
   uint32_t tmem_cols;
   int stages;
   int* err;
+  int flush;                // K stages per accumulation chunk (0: the whole piece in one chunk)
+  int nbuf;                 // TMEM chunk accumulators (2: the MMA fills one while the other drains)
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -79,6 +81,7 @@ struct TcScalars {
   int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
+  int flush, nbuf;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
 };
 __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
@@ -87,6 +90,7 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
   v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
+  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf;
   return v;
 }
 
@@ -154,10 +158,17 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   uint64_t* full = bars;
   uint64_t* empty = bars + MAX_STAGES;
   uint64_t* ready = bars + 2 * MAX_STAGES;
-  uint64_t* tmem_full = bars + 3 * MAX_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAX_STAGES + 1);
+  uint64_t* tmem_full = bars + 3 * MAX_STAGES;        // [2] a chunk accumulator is complete
+  uint64_t* tmem_empty = bars + 3 * MAX_STAGES + 2;   // [2] a chunk accumulator has been drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAX_STAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* last_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  // Accumulation chunks: the tensor cores' FP32 accumulation does not round to nearest, and on
+  // data of one sign its error grows with the number of MMAs added into one accumulator (~1 ulp
+  // each).  With pv.flush > 0 the piece is reduced in chunks of pv.flush stages, each started from
+  // zero in TMEM, and the epilogue adds the chunks in FP32 with round-to-nearest.
+  const int F = pv.flush > 0 ? pv.flush : (1 << 30);
+  const int NBUF = pv.nbuf;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t m0 = (int64_t)mt * TBM;
@@ -179,7 +190,10 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
       mbar_init(&empty[s], 1);
       mbar_init(&ready[s], 64);
     }
-    mbar_init(tmem_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tmem_full[b], 1);
+      mbar_init(&tmem_empty[b], 128);
+    }
     *abort_flag = 0;
     *last_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -236,7 +250,19 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
+      int chunk = 0;
       for (int i = 0; i < nit && ok; ++i) {
+        const int ic = i % F;                      // stage within the accumulation chunk
+        if (i > 0 && ic == 0) {                    // chunk boundary: hand the finished chunk over
+          umma_commit(&tmem_full[chunk % NBUF]);
+          ++chunk;
+          if (chunk >= NBUF) {                     // its buffer must have been drained first
+            ok = mbar_wait(&tmem_empty[chunk % NBUF], (uint32_t)((chunk / NBUF) - 1) & 1u, abort_flag, pv.err);
+            if (!ok) break;
+            tc_fence_after();
+          }
+        }
+        const uint32_t abase = tmem + (uint32_t)((chunk % NBUF) * 4 * nb);
         const int s = i % STAGES;
         const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
         ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, pv.err);
@@ -262,8 +288,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
               const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
               const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
               const uint32_t idesc = pv.idesc_base | (((pv.neg_mask >> (c * 4 + d)) & 1u) << 14);
-              const uint32_t dt = tmem + (uint32_t)(d * nb);
-              const uint32_t acc = (i > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
+              const uint32_t dt = abase + (uint32_t)(d * nb);
+              const uint32_t acc = (ic > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
               umma<KIND>(dt, ad, bd, idesc, acc);
               if (X3) {
                 const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
@@ -275,7 +301,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
         }
         umma_commit(&empty[s]);   // frees the stage once these MMAs have read it
       }
-      umma_commit(tmem_full);     // accumulator complete (also fires after an abort)
+      umma_commit(&tmem_full[chunk % NBUF]);   // last chunk complete (also fires after an abort)
     }
   } else if (warp < 4) {
     // ---------------- workers: hi/lo split (3xTF32) and/or transpose of A ----------------
@@ -336,39 +362,57 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row = q * 32 + lane;
     const int64_t grow = m0 + row;
-    const bool ok = mbar_wait(tmem_full, 0, abort_flag, pv.err) && !*abort_flag;
-    tc_fence_after();
     const int tile = mt * pv.ncb + cb;
     const size_t tile_elems = (size_t)4 * TBM * nb;
-    float v[16];
-    if (ok && nit > 0) {
+    const int nchunks = (nit > 0) ? (nit + F - 1) / F : 1;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      const int b = ch % NBUF;
+      ok = mbar_wait(&tmem_full[b], (uint32_t)(ch / NBUF) & 1u, abort_flag, pv.err) && !*abort_flag;
+      tc_fence_after();
+      if (!ok || nit == 0) break;
+      const bool first = (ch == 0);
+      const uint32_t abase = tmem + (uint32_t)(b * 4 * nb);
       for (int d = 0; d < 4; ++d) {
-        for (int cc = 0; cc < nb; cc += (sg.nseg == 1 ? 32 : 16)) {
-          if (sg.nseg == 1) {
-            // two loads in flight per wait (nb is a multiple of 16)
-            uint32_t r0[16], r1[16];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
-            tmem_ld16_issue(ta, r0);
-            if (cc + 16 < nb) tmem_ld16_issue(ta + 16, r1);
-            tmem_wait_ld();
-            if (grow < pv.M) {
-              float* yd = pv.y(d) + grow;
+        // the output plane d of this tile: Y itself (a whole tile) or this piece's partial slot
+        float* dst;
+        int64_t stride;
+        bool valid_row;
+        if (sg.nseg == 1) {
+          dst = pv.y(d) + grow;
+          stride = pv.ldy;
+          valid_row = grow < pv.M;
+        } else {
+          dst = pv.part + (size_t)sg.slot * tile_elems + (size_t)d * TBM * nb + row;
+          stride = TBM;
+          valid_row = true;
+        }
+        for (int cc = 0; cc < nb; cc += 32) {
+          // two TMEM loads in flight per wait (nb is a multiple of 16)
+          uint32_t r0[16], r1[16];
+          const uint32_t ta = abase + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
+          tmem_ld16_issue(ta, r0);
+          if (cc + 16 < nb) tmem_ld16_issue(ta + 16, r1);
+          tmem_wait_ld();
+          if (!valid_row) continue;
+          float old[32];
+          if (!first) {
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj) {
-                const int j = j0 + cc + jj;
-                if (j < pv.l && cc + jj < nb) yd[(int64_t)j * pv.ldy] = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
-              }
+            for (int jj = 0; jj < 32; ++jj) {
+              const bool in = (cc + jj < nb) && (sg.nseg > 1 || j0 + cc + jj < pv.l);
+              old[jj] = in ? dst[(int64_t)(cc + jj) * stride + (sg.nseg == 1 ? (int64_t)j0 * stride : 0)] : 0.f;
             }
-            continue;
           }
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc), v);
-          {
-            float* P = pv.part + (size_t)sg.slot * tile_elems + (size_t)d * TBM * nb;
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) P[(size_t)(cc + jj) * TBM + row] = v[jj];
+          for (int jj = 0; jj < 32; ++jj) {
+            const bool in = (cc + jj < nb) && (sg.nseg > 1 || j0 + cc + jj < pv.l);
+            const float v = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
+            if (in) dst[(int64_t)(cc + jj) * stride + (sg.nseg == 1 ? (int64_t)j0 * stride : 0)] = first ? v : old[jj] + v;
           }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&tmem_empty[b]);   // this chunk's accumulator may be overwritten
     }
     if (sg.nseg > 1) {
       __threadfence();
@@ -806,9 +850,19 @@ int kind_of(int compute) {
 struct Plan {
   int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages;
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
+  int flush, nbuf;               // accumulation chunks (stages per chunk, TMEM buffers)
   uint32_t tmem_cols;
   size_t smem;
 };
+
+// 3xTF32 (the FP32-accurate mode) adds at most this many stages into one TMEM accumulator before
+// the epilogue takes the chunk over (a stage adds 3 MMAs per input plane into each output plane):
+// the accumulation's rounding error on one-signed data then stays near 32 x 12 MMA additions
+// instead of growing with the reduction length (~0.5 ulp per addition was measured on GB300).
+// Column blocks are at most 64 wide in this mode so that two chunk accumulators fit in TMEM and
+// the epilogue drains one while the MMAs fill the other.
+constexpr int X3_FLUSH_STAGES = 32;
+constexpr int X3_MAX_NB = 64;
 
 Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   Plan pl{};
@@ -818,7 +872,8 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   pl.sw = pl.kind == K_TF32X3 ? 32 : 64;
   pl.bk = pl.sw / pl.esz;
   const int lp = (l + 15) / 16 * 16;
-  pl.ncb = (lp + 127) / 128;
+  const int max_nb = (pl.kind == K_TF32X3) ? X3_MAX_NB : 128;
+  pl.ncb = (lp + max_nb - 1) / max_nb;
   pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
   pl.mtiles = (int)((M + TBM - 1) / TBM);
   pl.kiters = (int)((K + pl.bk - 1) / pl.bk);
@@ -831,7 +886,9 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   if (g > tiles) pl.grid_sk = (int)g;
   else if (tiles > num_sms && tiles % num_sms != 0 && g == num_sms) pl.grid_sk = num_sms;
   else pl.grid_sk = 0;
-  const int cols = 4 * pl.nb;
+  pl.flush = (pl.kind == K_TF32X3) ? X3_FLUSH_STAGES : 0;
+  pl.nbuf = (pl.flush > 0 && 8 * pl.nb <= 512) ? 2 : 1;
+  const int cols = pl.nbuf * 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const bool x3 = pl.kind == K_TF32X3;
   const size_t stage = (size_t)4 * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
@@ -1220,6 +1277,8 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.tmem_cols = pl.tmem_cols;
   prm.stages = pl.stages;
   prm.err = ctx->d_err;
+  prm.flush = pl.flush;
+  prm.nbuf = pl.nbuf;
   int rc;
   const bool h = (op != QLR_OP_N);
   const int kid = QLR_KID_SKETCH_TC;

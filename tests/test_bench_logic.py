@@ -1,39 +1,54 @@
-"""Host logic of bench.py on CPU: the roofline object's arithmetic and the traffic figure's
-provenance check."""
+"""Host logic of bench.py on CPU: the algorithmic work of sketch passes, the roofline object's
+arithmetic and bound, the traffic figure's provenance check and the error statement."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
 
 
-def test_roofline_of_the_dominant_class():
-    stats = {"sketch_tc": (10, 3.2), "jacobi": (5, 2.0), "gram": (0, 0.0)}
-    r = bench.roofline(stats, "TF32X3", 1)
-    assert r["kernel"] == "sketch_tc" and r["launches"] == 10
-    flops = 32.0 * bench.M * bench.N * (bench.K_RANK + bench.P_OVER)
-    assert r["algorithmic_flops_per_launch"] == flops
-    assert r["achieved"] == pytest.approx(flops / 0.32e-3 / 1e12, rel=1e-3)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
+def test_sketch_work_counts_hamilton_flops_and_planes():
+    f, b = bench.sketch_work(100, 80, [10, 30], pure=False, esz=4)
+    assert f == 32.0 * 100 * 80 * 40 and b == 2 * 4 * 100 * 80 * 4
+    f, b = bench.sketch_work(100, 80, [10], pure=True, esz=2)
+    assert f == 24.0 * 100 * 80 * 10 and b == 3 * 100 * 80 * 2
+
+
+def test_roofline_bound_and_fraction():
+    pk, _ = bench._peaks()
+    # narrow BF16 passes: A's bytes take longer than the flops at the BF16 rate -> HBM bound
+    f, b = bench.sketch_work(20000, 10000, [8] * 4, pure=True, esz=2)
+    r = bench.sketch_roofline(f, b, 4.0, 4, "BF16")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(b / 4e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / pk["hbm_gbs"], rel=1e-3)
+    # wide 3xTF32 passes: three products per flop -> tensor bound, with the ceiling at a third
+    f, b = bench.sketch_work(4096, 4096, [110] * 10, pure=False, esz=4)
+    r = bench.sketch_roofline(f, b, 3.2, 10, "TF32X3")
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
-
-
-def test_bf16_sketch_counts_half_the_bytes():
-    f32 = bench.algorithmic_work("sketch_tc", "TF32X3")
-    bf16 = bench.algorithmic_work("sketch_tc", "BF16")
-    assert bf16[1] == f32[1] / 2 and bf16[0] == f32[0]
+    assert r["achieved"] == pytest.approx(f / 3.2e-3 / 1e12, rel=1e-3)
+    assert r["frac_of_own_ceiling"] == pytest.approx(3 * r["frac"], rel=1e-3)
+    assert r["algorithmic_flops_per_launch"] == pytest.approx(f / 10)
 
 
 def test_traffic_only_for_the_measured_source():
-    tr = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    ent = tr["sketch_tc"]
-    r = bench.roofline({"sketch_tc": (1, 1.0)}, "TF32X3", 1)
-    if bench._source_sha(ent["source"]) == ent["source_sha"]:
-        assert r["traffic"] == ent["dram_bytes_per_launch"]
-    else:
-        assert r["traffic"] is None
+    path = os.path.join(bench.ROOT, "profiles", "traffic.json")
+    tr = json.load(open(path)) if os.path.exists(path) else {}
+    for key, ent in tr.items():
+        if bench._source_sha(ent["source"]) == ent["source_sha"]:
+            assert bench.traffic_for(key) == ent["dram_bytes_per_launch"]
+        else:
+            assert bench.traffic_for(key) is None
+    assert bench.traffic_for("no_such_kernel") is None
     assert bench._source_sha("no/such/file.cu") is None
+
+
+def test_sigma_error_statement():
+    ref = np.array([4.0, 2.0, 1.0])
+    assert bench.sigma_rel_err([4.0, 2.0, 1.0], ref) == 0.0
+    assert bench.sigma_rel_err([4.0, 2.002, 0.999, 7.0], ref) == pytest.approx(1e-3)
 
 
 def test_whole_job_rate_and_single_rank_max():

@@ -69,15 +69,15 @@ def test_config3_bf16_full_size():
     c.close()
 
 
-@pytest.mark.parametrize("compute,tol", [("TF32X3", 1e-3), ("TF32", 2e-2)])
+@pytest.mark.parametrize("compute,tol", [("TF32X3", 1e-4), ("TF32_MIXED", 1e-4), ("TF32", 2e-2)])
 def test_config4_block_krylov_full_size(ctx, compute, tol):
-    """20000 x 10000 pure quaternion colour field, Algorithm 4 with k = 50, b = 60, v = 6.
-
-    FP32 tolerance 1e-3 rather than 1e-4: the colour field's DC singular value is 9x the next, so
-    the three Krylov blocks stacked by Algorithm 4 are nearly dependent and FP32 rounding of the
-    sketches and bases alone moves the singular values by ~7e-4 -- the oracle itself shows the same
-    shift when only those are rounded (tests/test_oracle_algorithms.py::
-    test_alg4_fp32_rounding_floor_on_colour_field), while the FP64 path matches to 1e-10."""
+    """20000 x 10000 pure quaternion colour field, Algorithm 4 with k = 50, b = 60, v = 6: the top-k
+    singular values within the FP32 tolerance 1e-4 of the FP64 oracle's on the unrounded A in
+    3xTF32 and in the mixed mode (one TF32 product for the Krylov blocks, 3xTF32 for the final
+    pass), 2e-2 with single-product TF32 throughout.  The field's leading singular value is ~9x
+    the next, so the plain stack of Krylov blocks is numerically rank-deficient in FP32 (the oracle
+    pin test_alg4_fp32_rounding_floor_on_colour_field); the GPU deflates each new block against the
+    earlier ones, which keeps the directions the stack adds (same span in exact arithmetic)."""
     from paper_2507_13731_gb300 import qlr
     P = _config4()
     U, S, V, _ = _run(ctx, P, 6, "f32", getattr(qlr, "COMPUTE_" + compute), algo=qlr.ALG4,

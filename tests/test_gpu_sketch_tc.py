@@ -91,3 +91,32 @@ def test_tc_unsupported_alignment_is_reported(ctx):
     with pytest.raises(qlr.QlrError) as e:
         qlr.qsketch(ctx, qlr.OP_N, A, X, Y, qlr.COMPUTE_TF32X3)
     assert e.value.code == qlr.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("op", ["N", "H"])
+def test_tf32x3_long_one_signed_reduction(ctx, op):
+    """3xTF32 on data of one sign with a long reduction (K = 20000) and one output tile per SM (no
+    stream-K split): the tensor cores' FP32 accumulation does not round to nearest, so adding all
+    7500 MMAs of an output's reduction into one accumulator drifts by ~0.5 ulp per addition (about
+    3e-4 relative here, all of one sign); the kernel reduces in chunks of 32 stages added in
+    round-to-nearest FP32, which keeps every sampled entry within 2.5e-5 of the FP64 oracle product
+    relative to sum_k |a_ik| |x_kj|."""
+    from paper_2507_13731_gb300 import qlr
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    M, K, l = sms * 128, 20000, 64
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.rand(3, M, K, device="cuda", generator=g) if op == "N" else \
+        torch.rand(3, K, M, device="cuda", generator=g)             # pure, entries in [0, 1)
+    X = qlr.to_thin(torch.rand(4, K, l, device="cuda", generator=g))
+    Y = qlr.empty_thin(M, l)
+    qlr.qsketch(ctx, qlr.OP_N if op == "N" else qlr.OP_H, A, X, Y, qlr.COMPUTE_TF32X3)
+    assert ctx.sync() == 0
+    rows = torch.from_numpy(np.random.default_rng(3).choice(M, 48, replace=False)).cuda()
+    Ar = A[:, rows, :] if op == "N" else A[:, :, rows].transpose(1, 2)
+    Ah = np.concatenate([np.zeros((1, 48, K)), Ar.double().cpu().numpy()])
+    Aop = Ah if op == "N" else Q.qconj(Ah)
+    Xh = host(X)
+    want = Q.qmatmul(Aop, Xh)
+    scale = Q.qnorm(Aop) @ Q.qnorm(Xh)
+    err = Q.qnorm(host(Y)[:, rows.cpu().numpy(), :] - want)
+    assert float((err / scale).max()) < 2.5e-5, float((err / scale).max())
