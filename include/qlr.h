@@ -161,6 +161,26 @@ int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
 #define QLR_PEAK_FP64_FMA 3
 int qlr_peak_probe(int kind, int device, int64_t iters, double* flops, float* ms);
 
+/* ---- the Gaussian test matrix from a seed (Def. 2) ---------------------------------------
+ * Def. 2's test matrix Omega has four independent standard normal components per entry; the
+ * paper fixes no generator.  These calls reproduce, from a seed, the Omega that this library's
+ * tests and benchmarks give both the GPU path and the FP64 oracle: a counter-based SplitMix64
+ * (draw t of the stream with seed s is SplitMix64's finaliser applied to s + (t + 1) *
+ * 0x9E3779B97F4A7C15) and the Box-Muller transform (normals 2p, 2p + 1 from uniforms u, w = the
+ * top 53 bits of draws 2p, 2p + 1 times 2^-53: r cos(2 pi w), r sin(2 pi w), r = sqrt(-2 ln(1 - u))),
+ * entry (c, i, j) of a rows x cols matrix being normal number c rows cols + j rows + i.
+ * qlr_splitmix64 -- draw `counter` of the stream with seed `seed` (derives stream seeds: the test
+ *   matrix of a workload with base seed b is drawn with seed qlr_splitmix64(b, 6)).
+ * qlr_gaussian_qmat_host -- fills `out` (host, 4 planes of rows x cols doubles, column-major, plane c
+ *   at out + c rows cols) with the Gaussian quaternion matrix of stream `seed`; real_only != 0 draws
+ *   plane 0 only (the real Gaussian matrix of the experiments, Section 8) and zeroes the others.
+ *   No device work.  QLR_EINVAL for a null out or negative sizes.
+ * qlr_fill_omega -- the same matrix written into the device matrix `omega` (column-major, F64 or
+ *   F32, 4 planes) on the context's stream; synchronises the stream (host-to-device copies). */
+uint64_t qlr_splitmix64(uint64_t seed, uint64_t counter);
+int qlr_gaussian_qmat_host(uint64_t seed, int64_t rows, int64_t cols, int real_only, double* out);
+int qlr_fill_omega(qlr_ctx* ctx, uint64_t seed, int real_only, qlr_qmat* omega);
+
 /*
  * qlr_qsketch -- one sketch pass (the products X Q2 / X^H Q1 of Algorithm 2 and Algorithm 4,
  * and the Hamilton product of eq. (1), Section 2, summed over the inner index).

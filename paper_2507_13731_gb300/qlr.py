@@ -102,6 +102,9 @@ def lib():
             "qlr_stats": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
             "qlr_qsketch_noalloc": (I, [P, I, Q, Q, Q, I, P]),
             "qlr_peak_probe": (I, [I, I, I64, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_float)]),
+            "qlr_splitmix64": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
+            "qlr_gaussian_qmat_host": (I, [ctypes.c_uint64, I64, I64, I, P]),
+            "qlr_fill_omega": (I, [P, ctypes.c_uint64, I, Q]),
             "qlr_batch_create": (I, [P, I, Q, ctypes.POINTER(I), ctypes.POINTER(I), I, Q, O, Q,
                                      ctypes.POINTER(P), Q, ctypes.POINTER(P)]),
             "qlr_batch_run": (I, [P]),
@@ -427,6 +430,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def gaussian_qmat_host(seed: int, rows: int, cols: int, real_only: bool = False):
+    """qlr_gaussian_qmat_host: the seeded Gaussian quaternion matrix (Def. 2) as a (4, rows, cols)
+    float64 CPU tensor (column-major planes, as the library fills them)."""
+    out = torch.zeros(4, cols, rows, dtype=torch.float64)
+    _check(lib().qlr_gaussian_qmat_host(seed & 0xFFFFFFFFFFFFFFFF, rows, cols, 1 if real_only else 0,
+                                        ctypes.c_void_p(out.data_ptr())), "qlr_gaussian_qmat_host")
+    return out.transpose(1, 2)
+
+
+def fill_omega(ctx: Context, seed: int, omega: torch.Tensor, real_only: bool = False) -> torch.Tensor:
+    """qlr_fill_omega: write the seeded Gaussian test matrix into the column-major device tensor omega."""
+    om = _T(omega)
+    _check(lib().qlr_fill_omega(ctx.h, seed & 0xFFFFFFFFFFFFFFFF, 1 if real_only else 0, ctypes.byref(om)),
+           "qlr_fill_omega")
+    return omega
+
+
+def splitmix64(seed: int, counter: int) -> int:
+    return int(lib().qlr_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, counter))
 
 
 def peak_probe(kind: int, device: int = 0, iters: int = 1000):

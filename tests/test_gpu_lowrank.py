@@ -244,3 +244,24 @@ def test_alg4_fp32_colour_field(ctx, compute):
     U, S, V, Om, _ = run_gpu(ctx, P, 6, qlr.ALG4, "f32", getattr(qlr, "COMPUTE_" + compute))
     ref = al.alg4_block_flexible(P.A, P.k, P.p, 6, Om)
     np.testing.assert_allclose(S, ref.S, rtol=1e-4)
+
+
+def test_seeded_omega_on_the_device(ctx):
+    """qlr_fill_omega writes the seeded Gaussian test matrix (Def. 2) into a device matrix: the
+    same Omega as the input module's, so a C caller that only has the seed runs the oracle's
+    problem (config 1, FP64: singular values to 1e-10)."""
+    from paper_2507_13731_gb300 import qlr
+    P = synth.config1()
+    Od = qlr.empty_thin(P.n, P.ell, torch.float64)
+    qlr.fill_omega(ctx, qlr.splitmix64(1234, synth.TAG_OMEGA), Od)
+    np.testing.assert_allclose(host(Od), P.Omega, rtol=1e-13, atol=1e-13)
+    O32 = qlr.empty_thin(P.n, P.ell, torch.float32)
+    qlr.fill_omega(ctx, qlr.splitmix64(1234, synth.TAG_OMEGA), O32)
+    np.testing.assert_allclose(host(O32), P.Omega.astype(np.float32), rtol=1e-7, atol=1e-7)
+    Ad = dev_rowmajor(P.A, "f64")
+    U, V = qlr.empty_thin(P.m, P.k, torch.float64), qlr.empty_thin(P.n, P.k, torch.float64)
+    S = torch.zeros(P.k, dtype=torch.float64, device="cuda")
+    qlr.qsvd_lowrank(ctx, Ad, P.k, P.p, P.v, Od, U, S, V, compute=qlr.COMPUTE_F64, side=qlr.SIDE_X)
+    assert ctx.sync() == 0
+    ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, P.v, P.Omega)
+    np.testing.assert_allclose(S.cpu().numpy(), ref.S, rtol=1e-10)
