@@ -5,7 +5,9 @@ Headline workload (one "step"): the pass-efficient block Krylov workload -- a 20
 quaternion colour field (FP32 planes; per colour plane a sum of 64 random 2-D cosines, min-max
 scaled to [0, 1], plus uniform noise of amplitude 0.05) -- through Algorithm 4 with k = 50, block
 size b = 60 and v = 6 views: six sketch passes (five of 60 columns, the last of 180), the deflated
-Krylov stack and its QR, the core QSVD of the 180 x 180 factor and the lifts.  Metric: sketch passes
+Krylov stack and its QR, the core QSVD of the 180 x 180 factor and the lifts, in the mixed mode
+(one TF32 product for the Krylov blocks, 3xTF32 for the final pass; --compute picks another
+arithmetic).  Metric: sketch passes
 per second (whole job); extra keys: A-read TB/s, ms per QSVD and the result's error against the FP64
 oracle (the oracle's values on the same seeded input are stored in tests/golden/fullsize_oracle.json
 by tests/golden/make_fullsize_golden.py): the largest relative error of the top-k singular values
@@ -609,7 +611,13 @@ def profile_driver(args):
         return 0
     compute = getattr(qlr, "COMPUTE_" + args.compute)
     a_dt = torch.bfloat16 if args.compute == "BF16" else torch.float32
-    if args.config == "c4":
+    if args.m and args.n:          # a uniform pure matrix of the given size (small profiling cases)
+        P, algo, v = synth.config_colour(max(args.m, 256), max(args.n, 256), HK, HB, HV), qlr.ALG4, HV
+        g = torch.Generator(device="cuda").manual_seed(5)
+        A = torch.rand(3, args.m, args.n, device="cuda", generator=g).to(a_dt).contiguous()
+        P.A = P.A[:, :args.m, :args.n]
+        P.Omega = P.Omega[:, :args.n, :]
+    elif args.config == "c4":
         P, algo, v = colour_problem(), qlr.ALG4, HV
         A = torch.from_numpy(np.ascontiguousarray(P.A[1:])).to(a_dt).cuda().contiguous()
     elif args.config == "c3":
@@ -725,7 +733,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--compute", default="TF32X3", choices=["TF32X3", "F32", "BF16", "TF32", "MIXED"])
+    ap.add_argument("--compute", default="MIXED", choices=["TF32X3", "F32", "BF16", "TF32", "MIXED", "TF32_MIXED"],
+                    help="headline arithmetic: MIXED = TF32 Krylov blocks + 3xTF32 final pass (default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
     ap.add_argument("--no-completion", action="store_true", help="skip the matrix-completion leg")
@@ -736,9 +745,13 @@ def main():
     ap.add_argument("--config", choices=["c2", "c3", "c4"], default="c4")
     ap.add_argument("--op", choices=["N", "H"], default="N")
     ap.add_argument("--ell", type=int, default=0)
+    ap.add_argument("--m", type=int, default=0, help="profiling driver: rows of a uniform pure A (with --n)")
+    ap.add_argument("--n", type=int, default=0, help="profiling driver: columns of a uniform pure A (with --m)")
     ap.add_argument("--passes", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.compute == "TF32_MIXED":
+        args.compute = "MIXED"
     if args.only:
         return profile_driver(args)
     ws, rank, local = dist_setup()

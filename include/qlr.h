@@ -337,8 +337,10 @@ int qlr_batch_destroy(qlr_batch* b);
  * ||A - Q Q^H A||_2 (side == QLR_SIDE_X, Q m x l) or ||A - A Q Q^H||_2 (side == QLR_SIDE_XH,
  * Q n x l) -- the errors bounded by Lemma 1, Theorem 3 and eqs. (mn11)/(mn12) -- by `iters`
  * steps of block power iteration with `nvec` vectors started from `start` (column-major F32/F64,
- * n x nvec for side X, m x nvec for side X^H).  *out (host) receives the estimate (a lower
- * bound that converges to the norm).  Synchronises the stream.
+ * n x nvec for side X, m x nvec for side X^H).  *out (host) receives the estimate: the largest,
+ * over the steps, Rayleigh-Ritz value ||E x||_2 = sqrt(lambda_max(Y^H Y)) of the residual operator
+ * E on the step's orthonormal block x (Y = E x), a lower bound that converges to the norm.
+ * Synchronises the stream.
  */
 int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start,
                       int iters, double* out);

@@ -262,7 +262,10 @@ int krylov_block(Sched& S, int op, const qlr_qmat& in, qlr_qmat& K, int j, int l
 // Algorithm 4.  On return Q1 (rows_fwd x L), Q2 (rows_bwd x L), R (L x L) with L the stacked width.
 // The per-view blocks of each side are kept in a stack (K1: range side, K2: co-range side), each
 // new block deflated against the blocks before it; the stack Algorithm 4 names (K1 for even v, K2
-// for odd v) then gets its QR, the other only serves the deflation.
+// for odd v) then gets its QR, the other only serves the deflation.  That QR's R is discarded, but
+// its Q is the final basis (it forms the last product and the lifts), so it gets opts.orth; the
+// deflated stack is well conditioned, so CholeskyQR2 suffices where the plain stack needed the
+// shifted CholeskyQR3.
 int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth, int orth_mid) {
   const int s = (v - 1) / 2;
   const bool even = (v % 2 == 0);
@@ -767,6 +770,50 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
   return QLR_OK;
 }
 
+// Largest eigenvalue of an n x n quaternion Hermitian matrix G (four column-major FP64 planes,
+// host) by power iteration with Rayleigh quotients; n is the handful of vectors of a block.
+static double herm_lmax(const std::vector<double>& g, int64_t n) {
+  const size_t nn = (size_t)n * n;
+  std::vector<double> x((size_t)4 * n), y((size_t)4 * n);
+  for (int64_t i = 0; i < n; ++i) {     // a start with components along every direction
+    x[i] = 1.0;
+    x[n + i] = 0.25 + 0.125 * (double)(i % 5);
+    x[2 * n + i] = -0.5 + 0.0625 * (double)(i % 7);
+    x[3 * n + i] = 0.375 - 0.03125 * (double)(i % 3);
+  }
+  double lam = 0.0;
+  for (int it = 0; it < 5000; ++it) {
+    double xx = 0.0, xy = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double acc[4] = {0, 0, 0, 0};
+      for (int64_t j = 0; j < n; ++j) {   // y_i = sum_j G_ij x_j (Hamilton product, eq. 1)
+        const size_t o = (size_t)j * n + i;
+        const double a0 = g[o], a1 = g[nn + o], a2 = g[2 * nn + o], a3 = g[3 * nn + o];
+        const double b0 = x[j], b1 = x[n + j], b2 = x[2 * n + j], b3 = x[3 * n + j];
+        acc[0] += a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3;
+        acc[1] += a0 * b1 + a1 * b0 + a2 * b3 - a3 * b2;
+        acc[2] += a0 * b2 - a1 * b3 + a2 * b0 + a3 * b1;
+        acc[3] += a0 * b3 + a1 * b2 - a2 * b1 + a3 * b0;
+      }
+      for (int c = 0; c < 4; ++c) {
+        y[(size_t)c * n + i] = acc[c];
+        xx += x[(size_t)c * n + i] * x[(size_t)c * n + i];
+        xy += x[(size_t)c * n + i] * acc[c];       // Re(x^H y)
+      }
+    }
+    const double lnew = xx > 0.0 ? xy / xx : 0.0;
+    double yy = 0.0;
+    for (double v : y) yy += v * v;
+    if (!(yy > 0.0)) return lnew;
+    const double inv = 1.0 / std::sqrt(yy);
+    for (size_t e = 0; e < y.size(); ++e) x[e] = y[e] * inv;
+    const bool done = it > 8 && std::fabs(lnew - lam) <= 1e-15 * std::fabs(lnew);
+    lam = lnew;
+    if (done) break;
+  }
+  return lam;
+}
+
 int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int side, const qlr_qmat* start, int iters,
                       double* out) {
   if (!ctx || !out) return QLR_EINVAL;
@@ -817,7 +864,8 @@ int qlr_residual_norm(qlr_ctx* ctx, const qlr_qmat* A, const qlr_qmat* Q, int si
     std::vector<double> hg((size_t)4 * nv * nv);
     QLR_CUDA_TRY(cudaMemcpyAsync(hg.data(), norms, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     QLR_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    for (int64_t j = 0; j < nv; ++j) best = std::max(best, std::sqrt(std::max(0.0, hg[(size_t)j * nv + j])));
+    // Rayleigh-Ritz: ||E x_block||_2 = sqrt(lambda_max(Y^H Y)) for the orthonormal block x
+    best = std::max(best, std::sqrt(std::max(0.0, herm_lmax(hg, nv))));
     QLR_TRY(S.sketch(QLR_OP_H, y, x));         // x = A^H y (= E^H y for side X)
     if (side == QLR_SIDE_XH) QLR_TRY(project(x));
   }

@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(128) jacobi_replay_kernel(int l, const T* __re
 // the rotation log: P x BW records (p, q, c, s, mu), disjoint columns, identity-padded, so the
 // replay can apply a whole stage in parallel.
 constexpr int JP = 8;                 // cluster size
-constexpr int JB_THREADS = 256;
+constexpr int JB_THREADS = 256;      // threads of a cluster CTA (FP64, or at most 8 pairs per local round)
+constexpr int JB_THREADS_WIDE = 384; // FP32 with 9..16 pairs per local round: one warp per pair up to 12
 constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4)
 
 // Stage index of local round lr in block round br: block round 0 runs the full round-robin over
@@ -323,8 +324,8 @@ __host__ __device__ __forceinline__ int jb_stage(int br, int lr, int bw) { retur
 
 // Rows per lane RPL: the two columns of a pair stay in registers between the dot products and
 // the rotation (l <= 32 RPL).
-template <class T, int RPL>
-__global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
+template <class T, int RPL, int NT>
+__global__ void __launch_bounds__(NT, 1) jacobi_block_kernel(const double* __restrict__ R, int l, int bw,
                                                                    T* __restrict__ W, int max_sweeps, T tol,
                                                                    T* __restrict__ rlog, int* __restrict__ flags,
                                                                    int* __restrict__ sweeps_out, T* __restrict__ sig_out,
@@ -333,16 +334,16 @@ __global__ void __launch_bounds__(JB_THREADS, 1) jacobi_block_kernel(const doubl
   T* S = reinterpret_cast<T*>(smem_raw);          // [4][2 bw][l]: plane, local column, row
   cg::cluster_group cluster = cg::this_cluster();
   const int p = (int)cluster.block_rank();
-  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JB_THREADS / 32;
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = NT / 32;
   const size_t ll = (size_t)l * l;
   const int NB = 2 * JP;
   const int U = 2 * bw;
   const int sps = jb_stages_per_sweep(bw);
   const int stage_cap = JP * bw;
   const T tol2 = tol * tol;
-  for (size_t e = (size_t)p * JB_THREADS + t; e < 4 * ll; e += (size_t)JP * JB_THREADS) W[e] = (T)rh_elem(R, l, ll, e);
+  for (size_t e = (size_t)p * NT + t; e < 4 * ll; e += (size_t)JP * NT) W[e] = (T)rh_elem(R, l, ll, e);
   if (p == 0)
-    for (int i = t; i < max_sweeps; i += JB_THREADS) flags[i] = 0;
+    for (int i = t; i < max_sweeps; i += NT) flags[i] = 0;
   __threadfence();
   cluster.sync();
   int sweep = 0;
@@ -766,11 +767,18 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   if (blockj) {
     const int bw = (l + 2 * JP - 1) / (2 * JP);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
-    auto kern = (l <= 128) ? jacobi_block_kernel<T, 4> : jacobi_block_kernel<T, 8>;
+    // FP32 sweeps with more than 8 pairs per local round: a warp for every pair (up to 12), so a
+    // local round is one pair rotation deep (the register budget of 384 threads still holds the
+    // kernel's working set without spilling)
+    const bool wide = sizeof(T) == 4 && bw > JB_THREADS / 32;
+    auto kern = (l <= 128) ? jacobi_block_kernel<T, 4, JB_THREADS> : jacobi_block_kernel<T, 8, JB_THREADS>;
+    if constexpr (sizeof(T) == 4) {
+      if (wide) kern = (l <= 128) ? jacobi_block_kernel<T, 4, JB_THREADS_WIDE> : jacobi_block_kernel<T, 8, JB_THREADS_WIDE>;
+    }
     QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(JP, 1, 1);
-    cfg.blockDim = dim3(JB_THREADS, 1, 1);
+    cfg.blockDim = dim3(wide ? JB_THREADS_WIDE : JB_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];

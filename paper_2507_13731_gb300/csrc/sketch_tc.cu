@@ -111,16 +111,96 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
         : "memory");
   }
 }
-template <int KIND> struct Cfg;
-template <> struct Cfg<K_BF16> {     // 2-byte operands, 64 B swizzle, 32 K-elements per stage
+// Stage geometry.  WIDE (K-major A, column blocks of at most 64): 128-byte rows per stage (128 B
+// swizzle), so every TMA row fetch of A moves 128 contiguous bytes; otherwise 64-byte rows.
+template <int KIND, bool WIDE = false> struct Cfg;
+template <> struct Cfg<K_BF16, false> {     // 2-byte operands, 64 B swizzle, 32 K-elements per stage
   static constexpr int ESZ = 2, SW = 64, BK = 32, MMA_K = 16, MODE = 4;
 };
-template <> struct Cfg<K_TF32> {     // 4-byte operands, 64 B swizzle, 16 K-elements per stage
+template <> struct Cfg<K_BF16, true> {      // 2-byte operands, 128 B swizzle, 64 K-elements per stage
+  static constexpr int ESZ = 2, SW = 128, BK = 64, MMA_K = 16, MODE = 2;
+};
+template <> struct Cfg<K_TF32, false> {     // 4-byte operands, 64 B swizzle, 16 K-elements per stage
   static constexpr int ESZ = 4, SW = 64, BK = 16, MMA_K = 8, MODE = 4;
 };
-template <> struct Cfg<K_TF32X3> {   // 4-byte operands, 32 B swizzle, 8 K-elements per stage
+template <> struct Cfg<K_TF32, true> {      // 4-byte operands, 128 B swizzle, 32 K-elements per stage
+  static constexpr int ESZ = 4, SW = 128, BK = 32, MMA_K = 8, MODE = 2;
+};
+template <> struct Cfg<K_TF32X3, false> {   // 4-byte operands, 32 B swizzle, 8 K-elements per stage
   static constexpr int ESZ = 4, SW = 32, BK = 8, MMA_K = 8, MODE = 6;
 };
+template <> struct Cfg<K_TF32X3, true> : Cfg<K_TF32X3, false> {};
+
+// ---------------------------------------------------------------------------------------
+// MMA issue.  The shared-memory descriptors of stage 0's operand tiles are built once; stage s
+// and K step ks only move the start address, whose field holds (address >> 4) in the low 14 bits
+// of the descriptor, so they are plain 64-bit additions.  A stage is then issued as a fully
+// unrolled run of tcgen05.mma with no per-MMA address arithmetic: with 64-column blocks an MMA
+// takes ~32 tensor-pipe cycles, so the issuing thread must spend only a few instructions on each.
+struct StageDescs {
+  uint64_t a[4], alo[4], x[4], xlo[4];
+  uint64_t sstep;                 // one stage, in descriptor address units (16 bytes)
+};
+
+template <int KIND, int AMODE, bool WIDE = false>
+__device__ __forceinline__ StageDescs make_stage_descs(uint32_t sbase, int stage_bytes, int hi_off, int a_bytes,
+                                                       int a_set, int x_bytes) {
+  using C = Cfg<KIND, WIDE>;
+  StageDescs D;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t ah = sbase + (uint32_t)(hi_off + c * a_bytes), al = ah + (uint32_t)(4 * a_bytes);
+    if (AMODE == A_MN) {   // MN-major: LBO = stride between MN atoms, SBO = stride between 8-row K groups
+      D.a[c] = make_desc(ah, C::BK * C::SW, 8 * C::SW, C::MODE);
+      D.alo[c] = make_desc(al, C::BK * C::SW, 8 * C::SW, C::MODE);
+    } else {
+      D.a[c] = make_desc(ah, 16, 8 * C::SW, C::MODE);
+      D.alo[c] = make_desc(al, 16, 8 * C::SW, C::MODE);
+    }
+    const uint32_t xh = sbase + (uint32_t)(a_set + c * x_bytes), xl = xh + (uint32_t)(4 * x_bytes);
+    D.x[c] = make_desc(xh, 16, 8 * C::SW, C::MODE);
+    D.xlo[c] = make_desc(xl, 16, 8 * C::SW, C::MODE);
+  }
+  D.sstep = (uint64_t)(stage_bytes >> 4);
+  return D;
+}
+
+// All MMAs of stage s into the accumulator at TMEM column abase (output plane d at abase + d nb):
+// per K step and input plane c, one MMA per output plane d of A_c against X_{c xor d} (three for
+// 3xTF32: hi hi, lo hi, hi lo), the sign of the Hamilton product in the negate-B bit.  `fresh`:
+// the first stage of an accumulation chunk (its first MMA overwrites the accumulator).
+template <int KIND, int AMODE, bool WIDE = false>
+__device__ __forceinline__ void issue_stage(const StageDescs& D, int s, uint32_t abase, int nb, int c_first,
+                                            uint32_t idesc_base, uint32_t neg_mask, bool fresh) {
+  using C = Cfg<KIND, WIDE>;
+  constexpr bool X3 = (KIND == K_TF32X3);
+  constexpr int KSTEPS = C::BK / C::MMA_K;
+  constexpr uint64_t KA = (AMODE == A_MN) ? (uint64_t)((C::MMA_K * C::SW) >> 4) : (uint64_t)((C::MMA_K * C::ESZ) >> 4);
+  constexpr uint64_t KB = (uint64_t)((C::MMA_K * C::ESZ) >> 4);
+  const uint64_t so = (uint64_t)s * D.sstep;
+#pragma unroll
+  for (int ks = 0; ks < KSTEPS; ++ks) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (c < c_first) continue;
+      const uint64_t ad = D.a[c] + so + ks * KA;
+      const uint64_t adlo = D.alo[c] + so + ks * KA;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const int q = c ^ d;
+        const uint64_t bd = D.x[q] + so + ks * KB;
+        const uint32_t idesc = idesc_base | (((neg_mask >> (c * 4 + d)) & 1u) << 14);
+        const uint32_t dt = abase + (uint32_t)(d * nb);
+        const uint32_t acc = (!fresh || ks > 0 || c > c_first) ? 1u : 0u;
+        umma<KIND>(dt, ad, bd, idesc, acc);
+        if (X3) {
+          umma<KIND>(dt, adlo, bd, idesc, 1u);
+          umma<KIND>(dt, ad, D.xlo[q] + so + ks * KB, idesc, 1u);
+        }
+      }
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // A contiguous piece of one output tile's reduction: stages [it0, it1).  A tile reduced in
@@ -133,9 +213,9 @@ struct Seg {
 };
 
 // One output tile (column block cb, row tile mt) over the reduction piece sg.
-template <int KIND, int AMODE>
+template <int KIND, int AMODE, bool WIDE = false>
 __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, const int mt, const Seg sg) {
-  using C = Cfg<KIND>;
+  using C = Cfg<KIND, WIDE>;
   const TcScalars pv = tc_scalars(p);
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
@@ -251,6 +331,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     if (lane == 0) {
       bool ok = true;
       int chunk = 0;
+      const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF, A_BYTES, A_SET, X_BYTES);
       for (int i = 0; i < nit && ok; ++i) {
         const int ic = i % F;                      // stage within the accumulation chunk
         if (i > 0 && ic == 0) {                    // chunk boundary: hand the finished chunk over
@@ -268,37 +349,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
         ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, pv.err);
         if (!ok) break;
         tc_fence_after();
-#pragma unroll
-        for (int ks = 0; ks < KSTEPS; ++ks) {
-          for (int c = pv.c_first; c < 4; ++c) {
-            uint64_t ad, adlo = 0;
-            if (MN) {
-              // MN-major: LBO = stride between MN atoms, SBO = stride between 8-row K groups
-              const uint32_t off = (uint32_t)(ks * C::MMA_K * C::SW);
-              ad = make_desc(smem_u32(a_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
-              if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
-            } else {
-              const uint32_t off = (uint32_t)(ks * C::MMA_K * C::ESZ);
-              ad = make_desc(smem_u32(a_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
-              if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
-            }
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-              const int q = c ^ d;
-              const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
-              const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-              const uint32_t idesc = pv.idesc_base | (((pv.neg_mask >> (c * 4 + d)) & 1u) << 14);
-              const uint32_t dt = abase + (uint32_t)(d * nb);
-              const uint32_t acc = (ic > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
-              umma<KIND>(dt, ad, bd, idesc, acc);
-              if (X3) {
-                const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-                umma<KIND>(dt, adlo, bd, idesc, 1u);
-                umma<KIND>(dt, ad, bdlo, idesc, 1u);
-              }
-            }
-          }
-        }
+        issue_stage<KIND, AMODE, WIDE>(D, s, abase, nb, pv.c_first, pv.idesc_base, pv.neg_mask, ic == 0);
         umma_commit(&empty[s]);   // frees the stage once these MMAs have read it
       }
       umma_commit(&tmem_full[chunk % NBUF]);   // last chunk complete (also fires after an abort)
@@ -457,9 +508,9 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
 }
 
 // One CTA per output tile, the whole reduction.
-template <int KIND, int AMODE>
+template <int KIND, int AMODE, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_constant__ TcParams p) {
-  sketch_tile<KIND, AMODE>(p, blockIdx.x, blockIdx.y, Seg{0, p.kiters, 0, 1, 0, 0, 0});
+  sketch_tile<KIND, AMODE, WIDE>(p, blockIdx.x, blockIdx.y, Seg{0, p.kiters, 0, 1, 0, 0, 0});
 }
 
 // Stream-K: the reduction stages of all tiles, taken in tile order, are cut into gridDim.x equal
@@ -468,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
 // whole tile writes its output directly, and the pieces of a split tile are added by the last one
 // to finish.  A CTA writes at most two partial tiles: slot 2c for its tail piece, slot 2c + 1 for a
 // head piece that is not its first piece.
-template <int KIND, int AMODE>
+template <int KIND, int AMODE, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const __grid_constant__ TcParams p) {
   const int64_t K = p.kiters, W = (int64_t)p.mtiles * p.ncb * K, G = gridDim.x, c = blockIdx.x;
   auto start = [&](int64_t cc) { return cc * W / G; };
@@ -486,7 +537,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const 
     const int more = (pos + (it1 - it0) < end) ? 1 : 0;
     const Seg sg{it0, it1, (int)(2 * c + (c == c0 ? b0 : 0)), (int)(c1 - c0 + 1), (int)c0, b0, more};
     if (!first) __syncthreads();
-    sketch_tile<KIND, AMODE>(p, (int)(t % p.ncb), (int)(t / p.ncb), sg);
+    sketch_tile<KIND, AMODE, WIDE>(p, (int)(t % p.ncb), (int)(t / p.ncb), sg);
     first = false;
     pos += it1 - it0;
   }
@@ -635,6 +686,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int g = 0;
       bool ok = true;
+      const StageDescs D = make_stage_descs<KIND, AMODE>(smem_u32(smem), stage_bytes, HI_OFF, A_BYTES, A_SET, X_BYTES);
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
         const TcParams& p = probs[it.x];
@@ -652,36 +704,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, err);
           if (!ok) break;
           tc_fence_after();
-#pragma unroll
-          for (int ks = 0; ks < KSTEPS; ++ks) {
-            for (int c = pv.c_first; c < 4; ++c) {
-              uint64_t ad, adlo = 0;
-              if (MN) {
-                const uint32_t off = (uint32_t)(ks * C::MMA_K * C::SW);
-                ad = make_desc(smem_u32(a_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
-                if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, C::BK * C::SW, 8 * C::SW, C::MODE);
-              } else {
-                const uint32_t off = (uint32_t)(ks * C::MMA_K * C::ESZ);
-                ad = make_desc(smem_u32(a_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
-                if (X3) adlo = make_desc(smem_u32(alo_plane(s, c)) + off, 16, 8 * C::SW, C::MODE);
-              }
-#pragma unroll
-              for (int d = 0; d < 4; ++d) {
-                const int q = c ^ d;
-                const uint32_t boff = (uint32_t)(ks * C::MMA_K * C::ESZ);
-                const uint64_t bd = make_desc(smem_u32(x_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-                const uint32_t idesc = pv.idesc_base | (((pv.neg_mask >> (c * 4 + d)) & 1u) << 14);
-                const uint32_t dt = acc_base + (uint32_t)(d * pv.nb);
-                const uint32_t acc = (i > 0 || ks > 0 || c > pv.c_first) ? 1u : 0u;
-                umma<KIND>(dt, ad, bd, idesc, acc);
-                if (X3) {
-                  const uint64_t bdlo = make_desc(smem_u32(xlo_plane(s, q)) + boff, 16, 8 * C::SW, C::MODE);
-                  umma<KIND>(dt, adlo, bd, idesc, 1u);
-                  umma<KIND>(dt, ad, bdlo, idesc, 1u);
-                }
-              }
-            }
-          }
+          issue_stage<KIND, AMODE>(D, s, acc_base, pv.nb, pv.c_first, pv.idesc_base, pv.neg_mask, i == 0);
           umma_commit(&empty[s]);
         }
         umma_commit(&acc_full[a]);   // accumulator of item t complete (also after an abort)
@@ -750,7 +773,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- epilogue ----------------
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    float v[16];
     for (int t = 0; t < my_items; ++t) {
       const int4 it = items[blockIdx.x + t * gridDim.x];
       const TcParams& p = probs[it.x];
@@ -851,6 +873,7 @@ struct Plan {
   int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages;
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
   int flush, nbuf;               // accumulation chunks (stages per chunk, TMEM buffers)
+  bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
   uint32_t tmem_cols;
   size_t smem;
 };
@@ -864,17 +887,18 @@ struct Plan {
 constexpr int X3_FLUSH_STAGES = 32;
 constexpr int X3_MAX_NB = 64;
 
-Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
+Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true) {
   Plan pl{};
   pl.kind = kind_of(compute);
   pl.amode = (op == QLR_OP_N) ? A_K : (pl.kind == K_BF16 ? A_MN : A_T);
   pl.esz = pl.kind == K_BF16 ? 2 : 4;
-  pl.sw = pl.kind == K_TF32X3 ? 32 : 64;
-  pl.bk = pl.sw / pl.esz;
   const int lp = (l + 15) / 16 * 16;
   const int max_nb = (pl.kind == K_TF32X3) ? X3_MAX_NB : 128;
   pl.ncb = (lp + max_nb - 1) / max_nb;
   pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
+  pl.wide = allow_wide && (pl.amode == A_K) && (pl.kind != K_TF32X3) && (pl.nb <= 64);
+  pl.sw = pl.kind == K_TF32X3 ? 32 : (pl.wide ? 128 : 64);
+  pl.bk = pl.sw / pl.esz;
   pl.mtiles = (int)((M + TBM - 1) / TBM);
   pl.kiters = (int)((K + pl.bk - 1) / pl.bk);
   // Stream-K over every SM (each CTA at least 8 stages) when the tiles do not fill whole waves:
@@ -899,13 +923,16 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms) {
   return pl;
 }
 
-template <int KIND, int AMODE>
+template <int KIND, int AMODE, bool WIDE = false>
 int launch_kernel(qlr_ctx* ctx, const Plan& pl, const TcParams& prm, int kid) {
-  auto kern = sketch_tc_kernel<KIND, AMODE>;
+  if constexpr (AMODE == A_K && KIND != K_TF32X3 && !WIDE) {
+    if (pl.wide) return launch_kernel<KIND, AMODE, true>(ctx, pl, prm, kid);
+  }
+  auto kern = sketch_tc_kernel<KIND, AMODE, WIDE>;
   QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   KTimer kt(ctx, kid);
   if (pl.grid_sk > 0) {
-    auto sk = sketch_tc_streamk_kernel<KIND, AMODE>;
+    auto sk = sketch_tc_streamk_kernel<KIND, AMODE, WIDE>;
     QLR_CUDA_TRY(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
     sk<<<pl.grid_sk, TC_THREADS, pl.smem, ctx->stream>>>(prm);
   } else {
@@ -990,7 +1017,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_qmat* X, int compute) {
-  const Plan base = make_plan(compute, op, 1, 1, 16, 1);
+  const Plan base = make_plan(compute, op, 1, 1, 16, 1, false);
   const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
   size_t b = align256((size_t)count * sizeof(TcParams)) + align256((size_t)count * sizeof(StageArg));
   size_t items = 0;
@@ -1006,7 +1033,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
                            int compute, int variant, char* dev, size_t bytes, GroupedSketch& gs) {
   const int order = variant & 1;
   if (count <= 0) return QLR_EINVAL;
-  const Plan base = make_plan(compute, op, 1, 1, 16, 1);
+  const Plan base = make_plan(compute, op, 1, 1, 16, 1, false);
   const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
   const bool x3 = base.kind == K_TF32X3;
   std::vector<GDims> dims(count);
@@ -1229,7 +1256,8 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   TcParams prm;
   memset(&prm, 0, sizeof(prm));
   const CUtensorMapDataType dt = (pl.kind == K_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const CUtensorMapSwizzle sw = (pl.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUtensorMapSwizzle sw = (pl.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B
+                                : (pl.sw == 64) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   const int esz = pl.esz;
   prm.c_first = (A.plane[0] == nullptr) ? 1 : 0;
   for (int c = prm.c_first; c < 4; ++c) {

@@ -75,3 +75,29 @@ def test_core_tsvd_repeated_values(ctx):
     np.testing.assert_allclose(Sd.cpu().numpy(), sig, rtol=1e-12)
     L, Rt = small_to_np(Ld), small_to_np(Rtd)
     np.testing.assert_allclose(Q.qmatmul(L * Sd.cpu().numpy(), Q.qH(Rt)), R, atol=1e-12)
+
+
+def test_fp32_sweeps_match_fp64_core(ctx):
+    """The core QSVD of the FP32 modes (FP32 one-sided Jacobi sweeps, then the kept triplets
+    re-evaluated in FP64 as Rayleigh quotients of the FP64 R) against the FP64 core on the same R:
+    l = 110, sigma_i = 1/i, k = 100 (the 4096 x 4096 workload's core).  Bounds: the singular values
+    to 1e-6 relative (the refinement's error is second order in the vectors' angles, ~u32 / relgap
+    with relative gaps >= 0.005 here); the rank-k projectors of both vector sets to 5e-4 entrywise
+    (sin of the subspace angle <= eps / relgap_k with eps ~ 4 sqrt(l) u32 and relgap_k =
+    (sigma_100 - sigma_101) / sigma_100 ~ 0.0099)."""
+    import torch
+    from paper_2507_13731_gb300 import qlr
+    l, k = 110, 100
+    sig = 1.0 / np.arange(1, l + 1)
+    R = _upper_r(l, sig, 113)
+    out = {}
+    for prec in (qlr.F64, qlr.F32):
+        Ld, Rtd = small(l, k), small(l, k)
+        Sd = torch.zeros(k, dtype=torch.float64, device="cuda")
+        qlr.qtsvd(ctx, np_to_small(R), k, Ld, Sd, Rtd, prec)
+        assert ctx.sync() == 0
+        out[prec] = (small_to_np(Ld), Sd.cpu().numpy(), small_to_np(Rtd))
+    (L64, S64, R64), (L32, S32, R32) = out[qlr.F64], out[qlr.F32]
+    np.testing.assert_allclose(S32, S64, rtol=1e-6)
+    assert float(np.abs(_proj(R32) - _proj(R64)).max()) <= 5e-4
+    assert float(np.abs(_proj(L32) - _proj(L64)).max()) <= 5e-4
