@@ -176,6 +176,15 @@ def sketch_roofline(flops: float, nbytes: float, ms: float, launches: int, compu
     return out
 
 
+def sketch_classes(compute: str, widths):
+    """(statistics class, arithmetic, pass widths) of the sketch launches of one step: the mixed
+    mode runs the Krylov blocks in TF32 and the last pass in 3xTF32 (a class of its own)."""
+    if compute == "MIXED":
+        return [("sketch_tc", "TF32", list(widths[:-1])), ("sketch_x3", "TF32X3", [widths[-1]])]
+    kid = {"F32": "sketch_simt", "TF32X3": "sketch_x3"}.get(compute, "sketch_tc")
+    return [(kid, compute, list(widths))]
+
+
 def traffic_for(key: str):
     """DRAM bytes per launch from profiles/traffic.json, only while the kernel's source is the one
     the counters were taken on."""
@@ -304,7 +313,7 @@ def mixed_precision_leg(dev, golden, reps=3):
         st = ctx.stats()
         ent = {"ms_per_qsvd": round(ms, 3)}
         ent.update(errors_vs_oracle(ctx, Ad, P, S.cpu().numpy(), qlr.ALG2, 4, comp, gold))
-        kid = "sketch_simt" if mode == "F32" else "sketch_tc"
+        kid = {"F32": "sketch_simt", "TF32X3": "sketch_x3"}.get(mode, "sketch_tc")
         nl, kms = st[kid]
         if nl:
             fl, nb = sketch_work(P.m, P.n, [P.k + P.p] * 4 * n, False, 2 if mode == "BF16" else 4)
@@ -424,8 +433,8 @@ COMPLETE_M = COMPLETE_N = 4096
 COMPLETE_K, COMPLETE_P, COMPLETE_ITERS = 30, 10, 20
 COMPLETE_WORKLOAD = ("matrix completion: 4096x4096 pure quaternion matrix of rank 30 plus N(0,(1e-2)^2) noise on the "
                      "i,j,k planes, FP32 planes, 70% of the entries removed uniformly at random, k=30, p=10, "
-                     "Algorithm 2 with v=2 per iteration, 20 alternating updates from P_Omega(M) (the paper's colour "
-                     "images with 70% of the pixels removed, R=30, two passes, scaled up)")
+                     "Algorithm 2 with v=4 (and v=2) per update, 20 alternating updates from P_Omega(M) (the paper's "
+                     "colour images with 70% of the pixels removed, R=30, scaled up)")
 
 
 def completion_problem():
@@ -434,10 +443,11 @@ def completion_problem():
                                     k=COMPLETE_K, p=COMPLETE_P)
 
 
-def completion_leg(dev, steps=5):
+def completion_leg(dev, golden, steps=5):
     """Matrix completion (Section 7): one qlr_qcomplete call of COMPLETE_ITERS alternating updates
-    (after one warm-up call), the masked update kernel alone (`steps` launches; M and C together
-    exceed L2) and the completed matrix's error on the removed entries."""
+    per pass budget (after one warm-up call), the error on the removed entries beside the oracle's
+    (stored values; with two passes per update the oracle itself stalls, with four it converges),
+    and the masked update kernel alone (`steps` launches; M and C together exceed L2)."""
     import numpy as np
     import torch
 
@@ -451,18 +461,29 @@ def completion_leg(dev, steps=5):
     Ud, Vd = qlr.empty_thin(m, k, device=dev), qlr.empty_thin(n, k, device=dev)
     Sd = torch.zeros(k, dtype=torch.float64, device=dev)
     Od = qlr.to_thin(torch.from_numpy(P.Omega).float().to(dev))
-    qlr.complete(ctx, Md, mask, k, P.p, 2, 1, Od, Cd, Ud, Sd, Vd)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    qlr.complete(ctx, Md, mask, k, P.p, 2, COMPLETE_ITERS, Od, Cd, Ud, Sd, Vd)
-    e1.record()
-    torch.cuda.synchronize()
-    total_ms = e0.elapsed_time(e1)
-    rc = ctx.sync()
     miss = P.extra["mask"] == 0
-    C = Cd.cpu().double().numpy()
-    err = float(np.sqrt(((C - P.A)[:, miss] ** 2).sum() / (P.A[:, miss] ** 2).sum()))
+    ref = float(np.sqrt((P.A[:, miss] ** 2).sum()))
+    out = {"workload": COMPLETE_WORKLOAD, "iters": COMPLETE_ITERS}
+    rc = 0
+    for v in (4, 2):
+        qlr.complete(ctx, Md, mask, k, P.p, v, 1, Od, Cd, Ud, Sd, Vd)
+        torch.cuda.synchronize()
+        e0.record()
+        qlr.complete(ctx, Md, mask, k, P.p, v, COMPLETE_ITERS, Od, Cd, Ud, Sd, Vd)
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms = e0.elapsed_time(e1)
+        rc = rc or ctx.sync()
+        C = Cd.cpu().double().numpy()
+        err = float(np.sqrt(((C - P.A)[:, miss] ** 2).sum())) / ref
+        ent = {"ms_total": round(total_ms, 3), "ms_per_iter": round(total_ms / COMPLETE_ITERS, 3),
+               "unobserved_rel_err": round(err, 6)}
+        gold = golden.get("completion", {}).get(f"v{v}")
+        if gold:
+            ent["oracle_unobserved_rel_err"] = round(gold["unobserved_rel_err"], 6)
+            ent["sigma_rel_err"] = float(f"{sigma_rel_err(Sd.cpu().numpy(), gold['sigma']):.3e}")
+        out[f"v{v}"] = ent
     for _ in range(3):
         qlr.complete_update(ctx, Md, mask, Cd, Ud, Sd, Vd, k)
     torch.cuda.synchronize()
@@ -479,13 +500,12 @@ def completion_leg(dev, steps=5):
     nbytes = m * n * (1 + 16 + 12 * obs)           # mask, C written, M read at observed entries
     peak, unit, _, note = peak_for("F32")
     ach = flops / (up_ms / 1e3) / 1e12
-    return {"workload": COMPLETE_WORKLOAD, "iters": COMPLETE_ITERS, "ms_total": round(total_ms, 3),
-            "ms_per_iter": round(total_ms / COMPLETE_ITERS, 3), "unobserved_rel_err": round(err, 6),
-            "update_kernel": {"ms": round(up_ms, 4), "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-                              "unit": "TFLOP/s", "frac": round(ach / peak, 4), "peak_source": note,
-                              "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
-                              "hbm_gbs": round(nbytes / (up_ms / 1e3) / 1e9, 1)},
-            "device_error": rc}
+    out["update_kernel"] = {"ms": round(up_ms, 4), "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
+                            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "peak_source": note,
+                            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                            "hbm_gbs": round(nbytes / (up_ms / 1e3) / 1e9, 1)}
+    out["device_error"] = rc
+    return out
 
 
 SWEEP_SIZES = tuple(range(500, 4001, 500))
@@ -852,21 +872,26 @@ def main():
 
     line = None
     if rank == 0:
-        flops, nbytes = sketch_work(HM, HN, widths * args.steps, True, 4)
-        kid = "sketch_simt" if args.compute == "F32" else "sketch_tc"
-        nl, kms = stats[kid]
-        roof = sketch_roofline(flops, nbytes, kms, nl, args.compute,
-                               traffic_for(f"sketch_tc_{args.compute.lower()}_c4"))
-        dom = max(stats, key=lambda k: stats[k][1])
-        roof["dominant_class"] = dom
-        roof["class_share"] = round(kms / max(sum(t for _, t in stats.values()), 1e-9), 4)
+        total_ms = max(sum(t for _, t in stats.values()), 1e-9)
+        roofs = []
+        for kid, comp, ws_ in sketch_classes(args.compute, widths):
+            nl, kms = stats[kid]
+            if not nl:
+                continue
+            flops, nbytes = sketch_work(HM, HN, ws_ * args.steps, True, 4)
+            r = sketch_roofline(flops, nbytes, kms, nl, comp, traffic_for(f"{kid}_{comp.lower()}_c4"))
+            r.update({"class": kid, "compute": comp, "pass_widths": ws_, "class_share": round(kms / total_ms, 4)})
+            roofs.append(r)
+        roof = dict(max(roofs, key=lambda r: r["class_share"]))   # the sketch class with most time
+        roof["dominant_class"] = max(stats, key=lambda k: stats[k][1])
+        roof["sketch_classes"] = roofs
         errs = errors_vs_oracle(ctx, A, P, S_gpu, qlr.ALG4, HV, compute, golden.get("c4", {}).get("v6"))
         cpu = mixed = sweep2 = batched = completion = sweep = None
         if legs:
             for name, fn in (("mixed", lambda: mixed_precision_leg(dev, golden)),
                              ("sweep2", lambda: pass_sweep_leg(dev, golden)),
                              ("batched", None if args.no_batched else lambda: batched_leg(dev)),
-                             ("completion", None if args.no_completion else lambda: completion_leg(dev)),
+                             ("completion", None if args.no_completion else lambda: completion_leg(dev, golden)),
                              ("sweep", None if args.no_sweep else lambda: lowrank_sweep_leg(dev))):
                 if fn is None:
                     continue

@@ -140,7 +140,8 @@ const char* qlr_strerror(int code);
 #define QLR_KID_MISC 8        /* conversions, operand staging, small products */
 #define QLR_KID_SERIES 9      /* CholeskyQR2 second step by series (factor and inverse) */
 #define QLR_KID_COMPLETE 10   /* matrix completion: masked low-rank update   */
-#define QLR_KID_COUNT 11
+#define QLR_KID_SKETCH_X3 11  /* tcgen05 sketch product in 3xTF32 (class 0 holds BF16 / TF32) */
+#define QLR_KID_COUNT 12
 int qlr_set_timing(qlr_ctx* ctx, int enable);
 int qlr_reset_stats(qlr_ctx* ctx);
 int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);

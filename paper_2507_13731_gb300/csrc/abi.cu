@@ -263,9 +263,9 @@ int krylov_block(Sched& S, int op, const qlr_qmat& in, qlr_qmat& K, int j, int l
 // The per-view blocks of each side are kept in a stack (K1: range side, K2: co-range side), each
 // new block deflated against the blocks before it; the stack Algorithm 4 names (K1 for even v, K2
 // for odd v) then gets its QR, the other only serves the deflation.  That QR's R is discarded, but
-// its Q is the final basis (it forms the last product and the lifts), so it gets opts.orth; the
-// deflated stack is well conditioned, so CholeskyQR2 suffices where the plain stack needed the
-// shifted CholeskyQR3.
+// its Q is the final basis (it forms the last product and the lifts), so it must be orthonormal to
+// working precision; the deflated stack is already well conditioned, so one plain CholeskyQR step
+// does that (the plain stack needed the shifted CholeskyQR3).
 int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat& Q2, double* R, int orth, int orth_mid) {
   const int s = (v - 1) / 2;
   const bool even = (v % 2 == 0);
@@ -288,15 +288,18 @@ int run_alg4(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
     }
   }
   const int64_t Lw = (int64_t)(even ? n1 : n2) * l;
+  // the deflated stack is orthonormal up to rounding (condition number ~1): one plain CholeskyQR
+  // step makes its Q orthonormal to working precision
+  const int korth = (orth == QLR_ORTH_SCHOLQR3) ? orth : qlr::ORTH_ONE;
   if (even) {
     QLR_TRY(krylov_block(S, S.op_fwd, *q2prev, K1, s, l, t1, orth_mid));          // Q1_{s+1}
-    QLR_TRY(qlr::cholqr(S.ctx, K1, Q1, nullptr, orth, *S.ws));                     // [Q1, ~] = QR(K1)
+    QLR_TRY(qlr::cholqr(S.ctx, K1, Q1, nullptr, korth, *S.ws));                    // [Q1, ~] = QR(K1)
     qlr_qmat W = S.thin(S.rows_bwd, Lw);
     if (!S.ws->ok) return QLR_ENOMEM;
     QLR_TRY(S.sketch(S.op_bwd, Q1, W));                                             // X^H Q1
     QLR_TRY(qlr::cholqr(S.ctx, W, Q2, R, orth, *S.ws));                             // [Q2, R2]
   } else {
-    QLR_TRY(qlr::cholqr(S.ctx, K2, Q2, nullptr, orth, *S.ws));                     // [Q2, ~] = QR(K2)
+    QLR_TRY(qlr::cholqr(S.ctx, K2, Q2, nullptr, korth, *S.ws));                    // [Q2, ~] = QR(K2)
     qlr_qmat W = S.thin(S.rows_fwd, Lw);
     if (!S.ws->ok) return QLR_ENOMEM;
     QLR_TRY(S.sketch(S.op_fwd, Q2, W));                                             // X Q2

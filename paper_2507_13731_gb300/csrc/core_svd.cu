@@ -24,6 +24,8 @@
 #include <cooperative_groups.h>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
+#include <vector>
 
 #include "qlr_internal.h"
 
@@ -310,7 +312,8 @@ __global__ void __launch_bounds__(128) jacobi_replay_kernel(int l, const T* __re
 // barrier ends the round.  W stays in global memory (L2).  Every local round is one "stage" of
 // the rotation log: P x BW records (p, q, c, s, mu), disjoint columns, identity-padded, so the
 // replay can apply a whole stage in parallel.
-constexpr int JP = 8;                 // cluster size
+constexpr int JP = 8;                 // portable cluster size (16 when the GPU can co-schedule it)
+constexpr int JP_MAX = 16;
 constexpr int JB_THREADS = 256;      // threads of a cluster CTA (FP64, or at most 8 pairs per local round)
 constexpr int JB_THREADS_WIDE = 384; // FP32 with 9..16 pairs per local round: one warp per pair up to 12
 constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4)
@@ -318,7 +321,7 @@ constexpr int REC = 8;                // floats per log record: p, q, c, s, mu(4
 // Stage index of local round lr in block round br: block round 0 runs the full round-robin over
 // the 2 bw columns of its block pair (U - 1 rounds, covering the pairs inside each block); later
 // block rounds only pair columns across the two blocks (bw rounds: a_i with b_{(i + lr) mod bw}).
-__host__ __device__ __forceinline__ int jb_stages_per_sweep(int bw) { return (2 * bw - 1) + (2 * JP - 2) * bw; }
+__host__ __device__ __forceinline__ int jb_stages_per_sweep(int bw, int jp) { return (2 * bw - 1) + (2 * jp - 2) * bw; }
 __host__ __device__ __forceinline__ int jb_stage(int br, int lr, int bw) { return br == 0 ? lr : (2 * bw - 1) + (br - 1) * bw + lr; }
 
 
@@ -336,12 +339,13 @@ __global__ void __launch_bounds__(NT, 1) jacobi_block_kernel(const double* __res
   const int p = (int)cluster.block_rank();
   const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = NT / 32;
   const size_t ll = (size_t)l * l;
-  const int NB = 2 * JP;
+  const int JPR = (int)gridDim.x;                 // cluster size: one cluster of JPR CTAs
+  const int NB = 2 * JPR;
   const int U = 2 * bw;
-  const int sps = jb_stages_per_sweep(bw);
-  const int stage_cap = JP * bw;
+  const int sps = jb_stages_per_sweep(bw, JPR);
+  const int stage_cap = JPR * bw;
   const T tol2 = tol * tol;
-  for (size_t e = (size_t)p * NT + t; e < 4 * ll; e += (size_t)JP * NT) W[e] = (T)rh_elem(R, l, ll, e);
+  for (size_t e = (size_t)p * NT + t; e < 4 * ll; e += (size_t)JPR * NT) W[e] = (T)rh_elem(R, l, ll, e);
   if (p == 0)
     for (int i = t; i < max_sweeps; i += NT) flags[i] = 0;
   __threadfence();
@@ -538,7 +542,7 @@ __global__ void __launch_bounds__(NT, 1) jacobi_block_kernel(const double* __res
     *sweeps_out = sweep;
     if (!converged) qlr_set_error(err, QLR_ENOCONV);
   }
-  for (int j = p * nwarps + warp; j < l; j += JP * nwarps) {
+  for (int j = p * nwarps + warp; j < l; j += JPR * nwarps) {
     T a = 0;
     for (int i = lane; i < l; i += 32) a += qnorm2(ldw(W, l, i, j));
     a = sqrt(warp_sum(a));
@@ -575,16 +579,16 @@ __device__ __forceinline__ void ld_rec<float>(const float* r, float (&v)[REC]) {
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
-size_t jb_replay_smem(int l, int bw, size_t esz) {
-  return (size_t)2 * RCH * JP * bw * REC * esz + (size_t)4 * 4 * l * esz;
+size_t jb_replay_smem(int l, int bw, int jp, size_t esz) {
+  return (size_t)2 * RCH * jp * bw * REC * esz + (size_t)4 * 4 * l * esz;
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw, const T* __restrict__ rlog,
+__global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw, int jp, const T* __restrict__ rlog,
                                                                    const int* __restrict__ nsweeps, T* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int cap = JP * bw;
+  const int cap = jp * bw;
   const size_t stage_elems = (size_t)cap * REC;
   T* logbuf = reinterpret_cast<T*>(smem_raw);                    // [2][RCH][cap][REC]
   T* vr = logbuf + 2 * RCH * stage_elems + (size_t)warp * 4 * l;  // this warp's row of V, 4 planes
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(128) jacobi_block_replay_kernel(int l, int bw,
       vr[j] = (j == row) ? (T)1 : (T)0;
       vr[l + j] = vr[2 * l + j] = vr[3 * l + j] = (T)0;
     }
-  const size_t nst = (size_t)(*nsweeps) * jb_stages_per_sweep(bw);
+  const size_t nst = (size_t)(*nsweeps) * jb_stages_per_sweep(bw, jp);
   const size_t nchunks = (nst + RCH - 1) / RCH;
   auto stage_chunk = [&](size_t ch) {
     const size_t s0 = ch * RCH;
@@ -743,11 +747,50 @@ static bool use_block_jacobi(int l, size_t esz) {
 }
 
 size_t jacobi_log_floats(int l) {
-  const int bw = (l + 2 * JP - 1) / (2 * JP);
-  const size_t blk = (size_t)JMAX_SWEEPS * jb_stages_per_sweep(bw) * JP * bw * REC + REC;
+  size_t blk = 0;
+  for (int jp : {JP, JP_MAX}) {
+    const int bw = (l + 2 * jp - 1) / (2 * jp);
+    blk = std::max(blk, (size_t)JMAX_SWEEPS * jb_stages_per_sweep(bw, jp) * jp * bw * REC + REC);
+  }
   const int lp = l + (l & 1);
   const size_t one = (size_t)JMAX_SWEEPS * (lp - 1) * (lp / 2) * 6 + 6;
   return blk > one ? blk : one;
+}
+
+// Cluster size of the block Jacobi for this l: 16 when the device allows the non-portable size
+// and can co-schedule 16 CTAs of the kernel, else 8 (decided once per device and l).
+template <class T>
+static int block_jacobi_cluster(int device, int l) {
+  static std::mutex mu;
+  static std::vector<std::pair<int64_t, int>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const int64_t key = ((int64_t)device << 32) | (uint32_t)l;
+  for (const auto& e : cache)
+    if (e.first == key) return e.second;
+  int pick = JP;
+  const int bw = (l + 2 * JP_MAX - 1) / (2 * JP_MAX);
+  auto kern = (l <= 128) ? jacobi_block_kernel<T, 4, JB_THREADS> : jacobi_block_kernel<T, 8, JB_THREADS>;
+  const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
+  if (bw <= JB_THREADS / 32 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(JP_MAX, 1, 1);
+    cfg.blockDim = dim3(JB_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = JP_MAX;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0) pick = JP_MAX;
+  }
+  cudaGetLastError();
+  cache.emplace_back(key, pick);
+  return pick;
 }
 
 template <class T>
@@ -765,7 +808,10 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
   const T tol = (T)8 * eps * (T)sqrt((double)l);   // above the rounding noise of the dot products
   const bool blockj = use_block_jacobi(l, sizeof(T));
   if (blockj) {
-    const int bw = (l + 2 * JP - 1) / (2 * JP);
+    // FP32 sweeps spread over a 16-CTA cluster where the GPU can co-schedule one (the sweeps are
+    // bound by the FMA issue of the cluster's SMs), else over 8 CTAs
+    const int jp = (sizeof(T) == 4) ? block_jacobi_cluster<T>(ctx->device, l) : JP;
+    const int bw = (l + 2 * jp - 1) / (2 * jp);
     const size_t smem = (size_t)4 * l * 2 * bw * sizeof(T);
     // FP32 sweeps with more than 8 pairs per local round: a warp for every pair (up to 12), so a
     // local round is one pair rotation deep (the register budget of 384 threads still holds the
@@ -777,13 +823,14 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     }
     QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(JP, 1, 1);
+    if (jp > JP) QLR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cfg.gridDim = dim3(jp, 1, 1);
     cfg.blockDim = dim3(wide ? JB_THREADS_WIDE : JB_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = JP;
+    attr[0].val.clusterDim.x = jp;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -796,10 +843,10 @@ static int core_tsvd_t(qlr_ctx* ctx, int l, const double* R, int k, double* L, d
     }
     {
       KTimer kt(ctx, QLR_KID_JACOBI);
-      const size_t rs = jb_replay_smem(l, bw, sizeof(T));
+      const size_t rs = jb_replay_smem(l, bw, jp, sizeof(T));
       // static shared memory comes on top of the dynamic size: always opt in
       QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_block_replay_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
-      jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, rlog, sweeps, V);
+      jacobi_block_replay_kernel<T><<<(l + 3) / 4, 128, rs, ctx->stream>>>(l, bw, jp, rlog, sweeps, V);
       qlr_count_launch();
       QLR_CUDA_TRY(cudaGetLastError());
     }

@@ -1964,7 +1964,7 @@ int cholqr(qlr_ctx* ctx, const qlr_qmat& Y, qlr_qmat& Q, double* R, int orth, Ws
   for (int c = 0; c < 4; ++c) T.plane[c] = tbuf + (size_t)c * tld * l * esz;
 
   // CholeskyQR2: Y -> T -> Q.  Shifted CholeskyQR3: Y -> Q -> T -> Q.  Span only: Y -> Q (shifted).
-  const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : (orth == ORTH_SPAN) ? 1 : 2;
+  const int steps = (orth == QLR_ORTH_SCHOLQR3) ? 3 : (orth == ORTH_SPAN || orth == ORTH_ONE) ? 1 : 2;
   // FP32 sketches: the Gram is double-FP32, and the Cholesky runs in the same arithmetic
   const bool df = (Y.dtype == QLR_F32);
   const qlr_qmat* seq1[2] = {&Y, &Q};

@@ -149,9 +149,11 @@ __device__ __forceinline__ void st_small(double* M, int l, int i, int j, const Q
 // launchers implemented in the .cu files (all asynchronous on ctx->stream)
 namespace qlr {
 
-// Internal orthonormalisation mode of cholqr(): one shifted CholeskyQR step, for bases of which
-// only the column space is used.
+// Internal orthonormalisation modes of cholqr(): one shifted CholeskyQR step, for bases of which
+// only the column space is used; one plain CholeskyQR step, for a well-conditioned input (a
+// deflated Krylov stack) whose Q must be orthonormal to working precision.
 constexpr int ORTH_SPAN = 16;
+constexpr int ORTH_ONE = 17;
 
 // SIMT generic quaternion GEMM  C = alpha * op(A) * B + beta * C
 //   A element (i, k) at A.plane[c] + i*sa_i + k*sa_k, conj_a applies A -> conj(A) elementwise.

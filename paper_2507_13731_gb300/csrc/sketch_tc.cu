@@ -67,6 +67,7 @@ struct TcParams {
   int* err;
   int flush;                // K stages per accumulation chunk (0: the whole piece in one chunk)
   int nbuf;                 // TMEM chunk accumulators (2: the MMA fills one while the other drains)
+  int ttotal;               // 1: the chunks' running sum is kept in TMEM columns [4 nb, 8 nb)
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -81,7 +82,7 @@ struct TcScalars {
   int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
-  int flush, nbuf;
+  int flush, nbuf, ttotal;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
 };
 __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
@@ -90,7 +91,7 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
   v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
-  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf;
+  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal;
   return v;
 }
 
@@ -246,7 +247,9 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   // Accumulation chunks: the tensor cores' FP32 accumulation does not round to nearest, and on
   // data of one sign its error grows with the number of MMAs added into one accumulator (~1 ulp
   // each).  With pv.flush > 0 the piece is reduced in chunks of pv.flush stages, each started from
-  // zero in TMEM, and the epilogue adds the chunks in FP32 with round-to-nearest.
+  // zero in TMEM, and the epilogue adds the chunks in FP32 with round-to-nearest: into a running
+  // sum kept in TMEM (pv.ttotal; the MMAs wait while a chunk is read out), or into the output in
+  // global memory (the MMAs fill the other of two chunk buffers meanwhile).
   const int F = pv.flush > 0 ? pv.flush : (1 << 30);
   const int NBUF = pv.nbuf;
 
@@ -423,7 +426,11 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
       tc_fence_after();
       if (!ok || nit == 0) break;
       const bool first = (ch == 0);
+      const bool last = (ch == nchunks - 1);
       const uint32_t abase = tmem + (uint32_t)(b * 4 * nb);
+      const uint32_t tbase = tmem + (uint32_t)(4 * nb);   // running sum (pv.ttotal)
+      const bool to_total = pv.ttotal && !last;             // this chunk only updates the TMEM sum
+      const bool add_total = pv.ttotal && !first;           // the TMEM sum enters this chunk's values
       for (int d = 0; d < 4; ++d) {
         // the output plane d of this tile: Y itself (a whole tile) or this piece's partial slot
         float* dst;
@@ -440,14 +447,31 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
         }
         for (int cc = 0; cc < nb; cc += 32) {
           // two TMEM loads in flight per wait (nb is a multiple of 16)
-          uint32_t r0[16], r1[16];
-          const uint32_t ta = abase + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
-          tmem_ld16_issue(ta, r0);
-          if (cc + 16 < nb) tmem_ld16_issue(ta + 16, r1);
+          uint32_t r0[16], r1[16], s0[16], s1[16];
+          const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(d * nb + cc);
+          tmem_ld16_issue(abase + lane_off, r0);
+          if (cc + 16 < nb) tmem_ld16_issue(abase + lane_off + 16, r1);
+          if (add_total) {
+            tmem_ld16_issue(tbase + lane_off, s0);
+            if (cc + 16 < nb) tmem_ld16_issue(tbase + lane_off + 16, s1);
+          }
           tmem_wait_ld();
+          if (add_total) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              r0[jj] = __float_as_uint(__uint_as_float(s0[jj]) + __uint_as_float(r0[jj]));
+              r1[jj] = __float_as_uint(__uint_as_float(s1[jj]) + __uint_as_float(r1[jj]));
+            }
+          }
+          if (to_total) {
+            tmem_st16(tbase + lane_off, r0);
+            if (cc + 16 < nb) tmem_st16(tbase + lane_off + 16, r1);
+            continue;
+          }
           if (!valid_row) continue;
+          const bool accumulate = !first && !pv.ttotal;     // global running sum
           float old[32];
-          if (!first) {
+          if (accumulate) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
               const bool in = (cc + jj < nb) && (sg.nseg > 1 || j0 + cc + jj < pv.l);
@@ -458,10 +482,11 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
           for (int jj = 0; jj < 32; ++jj) {
             const bool in = (cc + jj < nb) && (sg.nseg > 1 || j0 + cc + jj < pv.l);
             const float v = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
-            if (in) dst[(int64_t)(cc + jj) * stride + (sg.nseg == 1 ? (int64_t)j0 * stride : 0)] = first ? v : old[jj] + v;
+            if (in) dst[(int64_t)(cc + jj) * stride + (sg.nseg == 1 ? (int64_t)j0 * stride : 0)] = accumulate ? old[jj] + v : v;
           }
         }
       }
+      if (to_total) tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&tmem_empty[b]);   // this chunk's accumulator may be overwritten
     }
@@ -872,7 +897,7 @@ int kind_of(int compute) {
 struct Plan {
   int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages;
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
-  int flush, nbuf;               // accumulation chunks (stages per chunk, TMEM buffers)
+  int flush, nbuf, ttotal;       // accumulation chunks (stages per chunk, TMEM buffers, TMEM sum)
   bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
   uint32_t tmem_cols;
   size_t smem;
@@ -911,8 +936,11 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   else if (tiles > num_sms && tiles % num_sms != 0 && g == num_sms) pl.grid_sk = num_sms;
   else pl.grid_sk = 0;
   pl.flush = (pl.kind == K_TF32X3) ? X3_FLUSH_STAGES : 0;
-  pl.nbuf = (pl.flush > 0 && 8 * pl.nb <= 512) ? 2 : 1;
-  const int cols = pl.nbuf * 4 * pl.nb;
+  // chunk sums in TMEM next to the chunk accumulator when both fit (column blocks <= 64), else in
+  // the output with two chunk buffers
+  pl.ttotal = (pl.flush > 0 && 8 * pl.nb <= 512) ? 1 : 0;
+  pl.nbuf = (pl.flush > 0 && !pl.ttotal && 8 * pl.nb <= 512) ? 2 : 1;
+  const int cols = (pl.ttotal ? 2 : pl.nbuf) * 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const bool x3 = pl.kind == K_TF32X3;
   const size_t stage = (size_t)4 * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
@@ -1307,9 +1335,10 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.err = ctx->d_err;
   prm.flush = pl.flush;
   prm.nbuf = pl.nbuf;
+  prm.ttotal = pl.ttotal;
   int rc;
   const bool h = (op != QLR_OP_N);
-  const int kid = QLR_KID_SKETCH_TC;
+  const int kid = (pl.kind == K_TF32X3) ? QLR_KID_SKETCH_X3 : QLR_KID_SKETCH_TC;
   if (pl.kind == K_BF16) rc = h ? launch_kernel<K_BF16, A_MN>(ctx, pl, prm, kid) : launch_kernel<K_BF16, A_K>(ctx, pl, prm, kid);
   else if (pl.kind == K_TF32) rc = h ? launch_kernel<K_TF32, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32, A_K>(ctx, pl, prm, kid);
   else rc = h ? launch_kernel<K_TF32X3, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32X3, A_K>(ctx, pl, prm, kid);

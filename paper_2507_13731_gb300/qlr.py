@@ -36,7 +36,7 @@ PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_FP32_FMA, PEAK_FP64_FMA = range(4)
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series",
-             "complete"]
+             "complete", "sketch_x3"]
 
 
 class QlrError(RuntimeError):

@@ -7,7 +7,7 @@ values and the two projection errors the error bounds of Section 4 govern -- the
 ||A - Q1 Q1^H A||_2 and the co-range error ||A - A Q2 Q2^H||_2 (Lemma 1, Theorem 3, eqs.
 (mn11)/(mn12); Theorem 6 for Algorithm 4) -- with Q1, Q2 the oracle's final bases.
 
-  python tests/golden/make_fullsize_golden.py [c2] [c3] [c4]    (default: all; tens of minutes)
+  python tests/golden/make_fullsize_golden.py [c2] [c3] [c4] [completion]   (default: all; about an hour)
 """
 from __future__ import annotations
 
@@ -16,12 +16,15 @@ import os
 import sys
 import time
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 from oracle import algorithms as al  # noqa: E402
+from oracle import completion as oc  # noqa: E402
 from oracle import norms  # noqa: E402
 
 OUT = os.path.join(HERE, "fullsize_oracle.json")
@@ -68,15 +71,34 @@ def c4():
     return out
 
 
+def completion():
+    """Matrix completion (Section 7) at the benchmark's parameters: 4096 x 4096 rank-30 pure matrix
+    plus noise 1e-2, 70 % removed, k = 30, p = 10, 20 alternating updates with 2 and 4 passes per
+    update: the relative error on the removed entries and the last update's singular values."""
+    P = synth.completion_problem(4096, 4096, 30, missing=0.7, seed=1240, noise=1e-2, k=30, p=10)
+    miss = P.extra["mask"] == 0
+    ref = float(np.sqrt((P.A[:, miss] ** 2).sum()))
+    out = {"workload": "completion_problem(4096, 4096, 30, missing=0.7, seed=1240, noise=1e-2, k=30, p=10), "
+                       "20 updates, Algorithm 2, side X"}
+    for v in (2, 4):
+        t = time.time()
+        C, _, S, _, _ = oc.complete(P.A, P.extra["mask"], P.k, P.p, v, 20, P.Omega, side="X")
+        err = float(np.sqrt(((C - P.A)[:, miss] ** 2).sum())) / ref
+        out[f"v{v}"] = {"unobserved_rel_err": err, "sigma": [float(x) for x in S],
+                        "oracle_seconds": round(time.time() - t, 1)}
+        print("completion v", v, err, flush=True)
+    return out
+
+
 def main():
-    which = sys.argv[1:] or ["c2", "c3", "c4"]
+    which = sys.argv[1:] or ["c2", "c3", "c4", "completion"]
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     data["citation"] = ("FP64 oracle results (oracle/algorithms.py Algorithms 2 and 4, oracle/norms.py spectral "
                         "norms by Lanczos on the complex adjoint) on the seeded full-size workloads of synth/, written "
                         "by tests/golden/make_fullsize_golden.py; Omega is each workload's seeded Gaussian test "
                         "matrix (Def. 2), side X.")
     for name in which:
-        data[name] = {"c2": c2, "c3": c3, "c4": c4}[name]()
+        data[name] = {"c2": c2, "c3": c3, "c4": c4, "completion": completion}[name]()
         json.dump(data, open(OUT, "w"), indent=1)
     print("wrote", OUT)
 

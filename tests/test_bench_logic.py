@@ -54,3 +54,11 @@ def test_sigma_error_statement():
 def test_whole_job_rate_and_single_rank_max():
     assert bench.whole_job_rate(115, 2, 1000.0) == pytest.approx(230.0)
     assert bench.max_over_ranks(7.0, 1) == 7.0
+
+
+def test_sketch_classes_of_the_mixed_mode():
+    w = [60, 60, 60, 60, 60, 180]
+    assert bench.sketch_classes("MIXED", w) == [("sketch_tc", "TF32", w[:-1]), ("sketch_x3", "TF32X3", [180])]
+    assert bench.sketch_classes("TF32X3", w) == [("sketch_x3", "TF32X3", w)]
+    assert bench.sketch_classes("BF16", w) == [("sketch_tc", "BF16", w)]
+    assert bench.sketch_classes("F32", w) == [("sketch_simt", "F32", w)]
