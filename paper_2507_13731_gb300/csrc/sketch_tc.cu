@@ -847,45 +847,53 @@ struct StageArg {
   void* out_lo;
 };
 
-__global__ void stage_x_grouped_kernel(const StageArg* __restrict__ args, int mode) {
+// One CTA per (column range, problem): columns j = blockIdx.x, blockIdx.x + gridDim.x, ... of all
+// four planes, rows across the threads (coalesced on both sides, no 64-bit division per entry).
+template <int MODE>
+__global__ void __launch_bounds__(256) stage_x_grouped_kernel(const StageArg* __restrict__ args) {
   const StageArg a = args[blockIdx.y];
-  const int64_t per = a.rows * a.cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * per; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / per);
-    const int64_t r = e % per, i = r % a.rows, j = r / a.rows;
-    const float v = a.x[c][i + j * a.ldx];
-    const size_t o = (size_t)c * a.ldo * a.cols + (size_t)j * a.ldo + i;
-    if (mode == K_BF16) {
-      static_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(v);
-    } else if (mode == K_TF32) {
-      static_cast<float*>(a.out)[o] = v;
-    } else {
-      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-      static_cast<float*>(a.out)[o] = h;
-      static_cast<float*>(a.out_lo)[o] = v - h;
+  const int rows = (int)a.rows, cols = (int)a.cols;
+  for (int j = blockIdx.x; j < cols; j += gridDim.x)
+    for (int c = 0; c < 4; ++c) {
+      const float* src = a.x[c] + (int64_t)j * a.ldx;
+      const size_t o0 = (size_t)c * a.ldo * a.cols + (size_t)j * a.ldo;
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const float v = src[i];
+        if (MODE == K_BF16) {
+          static_cast<__nv_bfloat16*>(a.out)[o0 + i] = __float2bfloat16_rn(v);
+        } else if (MODE == K_TF32) {
+          static_cast<float*>(a.out)[o0 + i] = v;
+        } else {
+          const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+          static_cast<float*>(a.out)[o0 + i] = h;
+          static_cast<float*>(a.out_lo)[o0 + i] = v - h;
+        }
+      }
     }
-  }
 }
 
 // Operand staging: X (F32, column-major) -> BF16 copy, plain FP32 copy, or hi / lo FP32 pair.
-__global__ void stage_x_kernel(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ x2,
-                               const float* __restrict__ x3, int64_t ldx, int64_t rows, int64_t cols, int mode,
-                               void* __restrict__ out, void* __restrict__ out_lo, int64_t ldo) {
-  const float* xs[4] = {x0, x1, x2, x3};
-  const int64_t per = rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * per; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / per);
-    const int64_t r = e % per, i = r % rows, j = r / rows;
-    const float v = xs[c][i + j * ldx];
-    const size_t o = (size_t)c * ldo * cols + (size_t)j * ldo + i;
+// Grid (row chunks of 2048, columns, planes): each thread stages 8 rows of one column of one plane.
+constexpr int STAGE_ROWS = 2048;
+__global__ void __launch_bounds__(256) stage_x_kernel(const float* __restrict__ x0, const float* __restrict__ x1,
+                                                      const float* __restrict__ x2, const float* __restrict__ x3,
+                                                      int64_t ldx, int64_t rows, int64_t cols, int mode,
+                                                      void* __restrict__ out, void* __restrict__ out_lo, int64_t ldo) {
+  const int c = blockIdx.z, j = blockIdx.y;
+  const float* src = (c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : x3) + (int64_t)j * ldx;
+  const size_t o0 = (size_t)c * ldo * cols + (size_t)j * ldo;
+  const int64_t r0 = (int64_t)blockIdx.x * STAGE_ROWS;
+  const int64_t r1 = min(rows, r0 + STAGE_ROWS);
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const float v = src[i];
     if (mode == K_BF16) {
-      static_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
+      static_cast<__nv_bfloat16*>(out)[o0 + i] = __float2bfloat16_rn(v);
     } else if (mode == K_TF32) {
-      static_cast<float*>(out)[o] = v;
+      static_cast<float*>(out)[o0 + i] = v;
     } else {
       const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-      static_cast<float*>(out)[o] = h;
-      static_cast<float*>(out_lo)[o] = v - h;
+      static_cast<float*>(out)[o0 + i] = h;
+      static_cast<float*>(out_lo)[o0 + i] = v - h;
     }
   }
 }
@@ -1156,7 +1164,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     sa.ldo = g.ldo;
     sa.out = xs;
     sa.out_lo = xlo;
-    max_stage_blocks = std::max<int>(max_stage_blocks, (int)std::min<int64_t>((4 * g.K * g.l + 255) / 256, 64));
+    max_stage_blocks = std::max<int>(max_stage_blocks, std::min<int>(g.l, 128));   // one CTA per column
     for (int mt = 0; mt < g.mtiles; ++mt)
       for (int cb = 0; cb < g.ncb; ++cb) hi.push_back(make_int4(i, mt, cb, 0));
   }
@@ -1217,8 +1225,11 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
   if (gs.nitems == 0) return QLR_OK;
   {
     KTimer kt(ctx, QLR_KID_MISC);
-    stage_x_grouped_kernel<<<dim3((unsigned)gs.stage_grid_x, (unsigned)gs.count), 256, 0, ctx->stream>>>(
-        static_cast<const StageArg*>(gs.d_stage), gs.kind);
+    const dim3 grid((unsigned)gs.stage_grid_x, (unsigned)gs.count);
+    const StageArg* sa = static_cast<const StageArg*>(gs.d_stage);
+    if (gs.kind == K_BF16) stage_x_grouped_kernel<K_BF16><<<grid, 256, 0, ctx->stream>>>(sa);
+    else if (gs.kind == K_TF32) stage_x_grouped_kernel<K_TF32><<<grid, 256, 0, ctx->stream>>>(sa);
+    else stage_x_grouped_kernel<K_TF32X3><<<grid, 256, 0, ctx->stream>>>(sa);
     qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
@@ -1270,10 +1281,10 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
     for (int c = 0; c < 4; ++c) dst.plane[c] = static_cast<char*>(xs) + (size_t)c * ldo * l * 2;
     QLR_TRY(convert_qmat(ctx, X, dst));
   } else {
-    int64_t tot = 4 * K * (int64_t)l;
-    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8192);
+    if (l > 65535) return QLR_EUNSUPPORTED;
+    const dim3 grid((unsigned)((K + STAGE_ROWS - 1) / STAGE_ROWS), (unsigned)l, 4u);
     KTimer kt(ctx, QLR_KID_MISC);
-    stage_x_kernel<<<blocks, 256, 0, ctx->stream>>>(
+    stage_x_kernel<<<grid, 256, 0, ctx->stream>>>(
         static_cast<const float*>(X.plane[0]), static_cast<const float*>(X.plane[1]),
         static_cast<const float*>(X.plane[2]), static_cast<const float*>(X.plane[3]), X.ld, K, l, pl.kind, xs, xlo, ldo);
     qlr_count_launch();
