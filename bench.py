@@ -708,7 +708,23 @@ def batch_driver(args):
     e1.record()
     torch.cuda.synchronize()
     rc = ctx.sync()
-    print(json.dumps({"only": "batch", "ms_per_run": e0.elapsed_time(e1) / args.steps, "info": b.info(),
+    graph_ms = e0.elapsed_time(e1) / args.steps
+    info = b.info()
+    b.close()
+    # the same plan run eagerly, each kernel class timed with events on the context stream
+    b = qlr.Batch(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs, graph=False)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    for _ in range(args.steps):
+        b.run()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    rc = rc or ctx.sync()
+    per_run = {k: [round(n / args.steps, 1), round(ms / args.steps, 4)] for k, (n, ms) in st.items() if n}
+    print(json.dumps({"only": "batch", "ms_per_run": graph_ms, "info": info, "eager_classes_launches_ms": per_run,
                       "device_error": rc}), flush=True)
     b.close()
     ctx.close()

@@ -303,7 +303,8 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  * for every problem, else QLR_EUNSUPPORTED; compute AUTO means BF16 for BF16 A and 3xTF32 for
  * FP32 A; side must be AUTO or X).  Every step runs as one grouped launch over all the problems:
  * each sketch pass is one grouped tensor-core launch over every output tile (plus one grouped
- * staging launch); each CholeskyQR step is a grouped Gram (double-FP32), a grouped Cholesky
+ * staging launch); each CholeskyQR step is a grouped Gram (FP64-class on the tensor cores; FP32
+ * in the last step of CholeskyQR2, whose input is already nearly orthonormal), a grouped Cholesky
  * (double-FP32, one CTA per problem, also forming R^{-1} and the running product of the R
  * factors in FP32) and a grouped thin x small product; the core QSVDs (FP32 one-sided Jacobi,
  * sigma from the converged column norms) and the lifts are one launch each.  At creation the plan allocates its
@@ -313,7 +314,9 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  * QLR_FLAG_NO_GRAPH.  The pointers in A, omega, U, S, V are baked into the plan: later runs read
  * and write the same buffers.
  * qlr_batch_run -- enqueues one run on the context stream (asynchronous; errors of the device
- * side show in qlr_sync).  qlr_batch_info -- plan facts.  qlr_batch_destroy -- synchronises and
+ * side show in qlr_sync).  A plan made with QLR_FLAG_NO_GRAPH runs its launches eagerly; then,
+ * with timing enabled on the context (qlr_set_timing), each kernel class of the run is counted
+ * and timed in the context's statistics (a graph replay is not broken down).  qlr_batch_info -- plan facts.  qlr_batch_destroy -- synchronises and
  * frees the plan (b may be NULL).
  */
 typedef struct qlr_batch qlr_batch;

@@ -21,7 +21,8 @@ namespace {
 
 // One orthonormalisation step of one pass (device tables, one entry per problem).
 struct StepTables {
-  const void* gram = nullptr;               // tensor-core Gram records
+  const void* gram = nullptr;               // tensor-core Gram records (FP64-class steps)
+  const qlr::GramF32Args* gram32 = nullptr; // FP32 Gram arguments (last step of a QR)
   const qlr::CholGroupArgs* chol = nullptr;
   const qlr::GemmArgs* apply = nullptr;
 };
@@ -41,7 +42,7 @@ struct qlr_batch {
     int k, p, l;
   };
   qlr_ctx* ctx = nullptr;
-  qlr_ctx main_ctx;                         // issues the launches, untimed: on ctx->stream, or
+  qlr_ctx main_ctx;                         // issues the launches (timed only in eager runs): on ctx->stream, or
                                             // on cap_stream while the graph is captured
   cudaStream_t cap_stream = nullptr;        // capture needs a stream other than the legacy default
   int count = 0, passes = 0, compute = 0, orth = 0, mid = 0, lmax = 0;
@@ -55,6 +56,8 @@ struct qlr_batch {
   const int4* comb_items[2] = {nullptr, nullptr};
   const int4* apply_items[2] = {nullptr, nullptr};
   int n_slice[2] = {0, 0}, n_gram[2] = {0, 0}, n_comb[2] = {0, 0}, n_apply[2] = {0, 0};
+  const int4* gf_items = nullptr;           // FP32 Gram tiles (independent of the row count)
+  int n_gf = 0;
   const qlr::JacobiGroupArgs* jac = nullptr;
   const qlr::GemmArgs* lift = nullptr;
   const int4* lift_items = nullptr;
@@ -129,6 +132,13 @@ qlr::GemmArgs thin_small_args(const qlr_qmat& T, const float* S, int l, int k, c
 
 int orth_steps(int orth) { return orth == QLR_ORTH_SCHOLQR3 ? 3 : (orth == qlr::ORTH_SPAN ? 1 : 2); }
 
+// The last step of CholeskyQR2 (and of shifted CholeskyQR3) factors the Gram of a basis whose
+// previous, unshifted step left it nearly orthonormal: its Gram is formed in FP32.  Every other
+// step (a sketch's first step, the step after a shifted one) keeps the FP64-class Gram.
+bool fp32_gram_step(int orth, int s) {
+  return (orth == QLR_ORTH_CHOLQR2 && s == 1) || (orth == QLR_ORTH_SCHOLQR3 && s == 2);
+}
+
 const qlr::GroupedSketch& plan_of(const qlr_batch* b, int pass) {
   return pass == 1 ? b->gs[0] : (pass % 2 == 0 ? b->gs[1] : b->gs[2]);
 }
@@ -142,8 +152,11 @@ int enqueue(qlr_batch* b) {
     QLR_TRY(qlr::sketch_tc_grouped_run(mc, plan_of(b, i)));
     const int par = (i % 2 == 1) ? 0 : 1;
     for (const StepTables& st : b->steps[i - 1]) {
-      QLR_TRY(qlr::gram_tc_grouped(mc, st.gram, b->slice_items[par], b->n_slice[par], b->gram_items[par], b->n_gram[par],
-                                   b->comb_items[par], b->n_comb[par]));
+      if (st.gram32)
+        QLR_TRY(qlr::gram_f32_grouped(mc, st.gram32, b->gf_items, b->n_gf));
+      else
+        QLR_TRY(qlr::gram_tc_grouped(mc, st.gram, b->slice_items[par], b->n_slice[par], b->gram_items[par],
+                                     b->n_gram[par], b->comb_items[par], b->n_comb[par]));
       QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
       QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
@@ -276,13 +289,21 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     tb.add(ci);
     tb.add(ai);
   }
+  {
+    std::vector<int4> gf;
+    for (int j = 0; j < count; ++j) gram_f32_items(b->pr[j].l, j, gf);
+    b->n_gf = (int)gf.size();
+    tb.add(gf);
+  }
   const size_t rec = gram_tc_record_bytes();
   // steps of every pass: Y (odd) or Z (even) -> Q1 or Q2, through T
   for (int i = 1; i <= passes; ++i) {
     const int o = (i >= passes - 1) ? b->orth : b->mid;
     const int ns = orth_steps(o);
     for (int s = 0; s < ns; ++s) {
-      std::vector<char> ga((size_t)count * rec);
+      const bool g32 = fp32_gram_step(o, s);
+      std::vector<char> ga(g32 ? 0 : (size_t)count * rec);
+      std::vector<GramF32Args> gfa(g32 ? count : 0);
       std::vector<CholGroupArgs> ca(count);
       std::vector<GemmArgs> aa(count);
       for (int j = 0; j < count; ++j) {
@@ -298,8 +319,17 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         if (ns == 3) { seq[2] = &T; seq[3] = &dst; }
         const qlr_qmat& from = *seq[s];
         const qlr_qmat& to = *seq[s + 1];
-        const int grc = gram_tc_record(ga.data() + (size_t)j * rec, from, P.gsc, P.G, b->ctx->d_err);
-        if (grc != QLR_OK && *rc == QLR_OK) *rc = grc;
+        if (g32) {
+          GramF32Args& G = gfa[j];
+          for (int c = 0; c < 4; ++c) G.y[c] = static_cast<const float*>(from.plane[c]);
+          G.ld = from.ld;
+          G.m = from.rows;
+          G.l = P.l;
+          G.G = P.G;
+        } else {
+          const int grc = gram_tc_record(ga.data() + (size_t)j * rec, from, P.gsc, P.G, b->ctx->d_err);
+          if (grc != QLR_OK && *rc == QLR_OK) *rc = grc;
+        }
         CholGroupArgs& C = ca[j];
         C.G = P.G;
         C.Rinv = P.Rinv;
@@ -315,7 +345,8 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         aa[j] = thin_small_args(from, P.Rinv, P.l, P.l, to);
         aa[j].b_upper = true;   // R^{-1} is upper triangular
       }
-      tb.add_raw(ga);
+      if (g32) tb.add(gfa);
+      else tb.add_raw(ga);
       tb.add(ca);
       tb.add(aa);
     }
@@ -337,6 +368,8 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
   }
   for (int j = 0; j < count; ++j) thin_small_items(b->pr[j].A.cols, b->pr[j].k, count + j, li);
   b->n_lift = (int)li.size();
+  // the largest cores first: CTAs are dispatched in order as SMs free up (longest job first)
+  std::stable_sort(ja.begin(), ja.end(), [](const JacobiGroupArgs& x, const JacobiGroupArgs& y) { return x.l > y.l; });
   tb.add(ja);
   tb.add(la);
   tb.add(li);
@@ -439,12 +472,15 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
       b->comb_items[par] = reinterpret_cast<const int4*>(next());
       b->apply_items[par] = reinterpret_cast<const int4*>(next());
     }
+    b->gf_items = reinterpret_cast<const int4*>(next());
     b->steps.resize(passes);
     for (int i = 1; i <= passes; ++i) {
       const int ns = orth_steps((i >= passes - 1) ? b->orth : b->mid);
+      const int o = (i >= passes - 1) ? b->orth : b->mid;
       for (int s = 0; s < ns; ++s) {
         StepTables st;
-        st.gram = next();
+        if (fp32_gram_step(o, s)) st.gram32 = reinterpret_cast<const GramF32Args*>(next());
+        else st.gram = next();
         st.chol = reinterpret_cast<const CholGroupArgs*>(next());
         st.apply = reinterpret_cast<const GemmArgs*>(next());
         b->steps[i - 1].push_back(st);
@@ -504,7 +540,17 @@ extern "C" int qlr_batch_run(qlr_batch* b) {
     QLR_CUDA_TRY(cudaGraphLaunch(b->exec, b->ctx->stream));
     return QLR_OK;
   }
-  return enqueue(b);
+  // eager run: with timing enabled on the caller's context, every kernel class of the run is
+  // bracketed by events and counted there (a graph replay is one launch and is not broken down)
+  qlr_ctx* c = b->ctx;
+  b->main_ctx.timing = c->timing;
+  const int rc = enqueue(b);
+  b->main_ctx.timing = false;
+  for (auto& pe : b->main_ctx.ev_pending) c->ev_pending.push_back(pe);
+  b->main_ctx.ev_pending.clear();
+  if (c->timing)
+    for (int kk = 0; kk < QLR_KID_COUNT; ++kk) c->launches[kk] += b->main_ctx.launches[kk];
+  return rc;
 }
 
 extern "C" int qlr_batch_info(const qlr_batch* b, qlr_batch_stats* st) {

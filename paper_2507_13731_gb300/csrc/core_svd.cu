@@ -203,45 +203,123 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const double* __restrict__ R
 template <class T>
 __device__ __forceinline__ T rank_key(T x) { return isnan(x) ? -INFINITY : x; }
 
-// Batch plans: one CTA per problem, W = R and V = I in shared memory (FP32).  After the sweeps
+// Batch plans: one CTA per problem, W = R^H and V = I in shared memory (FP32, each quaternion
+// stored as one float4).  A column pair is handled by a group of g lanes (8 for l <= 48, 16 up to
+// 80), each lane holding up to JG_RMAX rows of both columns in registers between the dot products
+// and the rotation, so a warp works on 32 / g pairs at once and no lane idles on a short column;
+// the group's dot products are reduced with log2(g) shuffle steps.  After the sweeps
 // sigma_j = |w_j| and u_j = w_j / sigma_j; the k largest sigma (descending, ties by column) go to
 // S and their u, v columns to U, V.  Without the FP64 Rayleigh step of the single-problem path:
 // the plan's sketches and bases are BF16 / FP32, and the column norms carry the FP32 accuracy of
 // the rotated columns.
-__global__ void __launch_bounds__(JT) jacobi_grouped_kernel(const qlr::JacobiGroupArgs* __restrict__ args,
-                                                            int max_sweeps, int* err) {
+constexpr int JG_THREADS = 640;   // 40 groups of 16 lanes: every pair of a round at once (l <= 80)
+constexpr int JG_RMAX = 6;        // rows per lane: l <= 8 * 6 (groups of 8), l <= 16 * 5 (of 16)
+
+__device__ __forceinline__ Quat<float> q_of4(const float4 v) { return {v.x, v.y, v.z, v.w}; }
+__device__ __forceinline__ float4 f4_of(const Quat<float>& q) { return make_float4(q.w, q.x, q.y, q.z); }
+
+__global__ void __launch_bounds__(JG_THREADS) jacobi_grouped_kernel(const qlr::JacobiGroupArgs* __restrict__ args,
+                                                                   int max_sweeps, int* err) {
   const qlr::JacobiGroupArgs& a = args[blockIdx.x];
   const int l = a.l, k = a.k;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t ll = (size_t)l * l;
-  float* W = reinterpret_cast<float*>(smem_raw);
-  float* Vs = W + 4 * ll;
-  float* sig = Vs + 4 * ll;
+  float4* W = reinterpret_cast<float4*>(smem_raw);   // W(i, j) at W[j l + i]
+  float4* Vs = W + ll;
+  float* sig = reinterpret_cast<float*>(Vs + ll);
   int* ord = reinterpret_cast<int*>(sig + l);
-  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JT / 32;
+  __shared__ int s_rot;
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = JG_THREADS / 32;
   const float* R = a.R;
-  for (size_t e = t; e < 4 * ll; e += JT) {
-    W[e] = rh_elem(R, l, ll, e);
-    Vs[e] = (e < ll && e % (l + 1) == 0) ? 1.f : 0.f;
+  for (size_t e = t; e < ll; e += JG_THREADS) {   // W(i, j) = conj(R(j, i))
+    const size_t i = e % l, j = e / l, src = i * l + j;
+    W[e] = make_float4(R[src], -R[ll + src], -R[2 * ll + src], -R[3 * ll + src]);
+    Vs[e] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   const float tol = 8.f * 5.9604645e-08f * sqrtf((float)l);   // above the rounding noise of the dot products
-  bool converged = false;
-  jacobi_sweeps<float>(W, Vs, l, max_sweeps, tol, nullptr, &converged);
+  const int g = (l <= 8 * JG_RMAX) ? 8 : 16;
+  const int grp = t / g, sub = t % g, ngroups = JG_THREADS / g;
+  const int lp = l + (l & 1), npairs = lp / 2;
+  bool converged = (l < 2);
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (t == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < lp - 1; ++r) {
+      for (int base = 0; base < npairs; base += ngroups) {
+        const int pi = base + grp;
+        int p = 0, q = 0;
+        bool valid = pi < npairs;
+        if (valid) {
+          rr_pair(lp, r, pi, p, q);
+          valid = p < l && q < l;
+        }
+        Quat<float> wp[JG_RMAX], wq[JG_RMAX];
+        float al = 0.f, be = 0.f;
+        Quat<float> ga = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < JG_RMAX; ++u) {
+          const int i = sub + u * g;
+          if (valid && i < l) {
+            wp[u] = q_of4(W[(size_t)p * l + i]);
+            wq[u] = q_of4(W[(size_t)q * l + i]);
+            al += qnorm2(wp[u]);
+            be += qnorm2(wq[u]);
+            const Quat<float> pr = qcmul(wp[u], wq[u]);
+            ga.w += pr.w; ga.x += pr.x; ga.y += pr.y; ga.z += pr.z;
+          }
+        }
+        for (int o = g / 2; o > 0; o >>= 1) {   // within the group (every lane of the warp takes part)
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.w += __shfl_xor_sync(0xffffffffu, ga.w, o);
+          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+          ga.z += __shfl_xor_sync(0xffffffffu, ga.z, o);
+        }
+        const float gn2 = qnorm2(ga);
+        if (valid && gn2 > (tol * tol * al) * be) {
+          if (sub == 0) s_rot = 1;
+          Quat<float> mu;
+          float c, s;
+          jacobi_rotation(al, be, ga, gn2, mu, c, s);
+#pragma unroll
+          for (int u = 0; u < JG_RMAX; ++u) {
+            const int i = sub + u * g;
+            if (i < l) {
+              const Quat<float> wqm = qmulc(wq[u], mu);   // w_q mu*
+              W[(size_t)p * l + i] = make_float4(c * wp[u].w - s * wqm.w, c * wp[u].x - s * wqm.x,
+                                                 c * wp[u].y - s * wqm.y, c * wp[u].z - s * wqm.z);
+              W[(size_t)q * l + i] = make_float4(s * wp[u].w + c * wqm.w, s * wp[u].x + c * wqm.x,
+                                                 s * wp[u].y + c * wqm.y, s * wp[u].z + c * wqm.z);
+              const Quat<float> vp = q_of4(Vs[(size_t)p * l + i]), vq = qmulc(q_of4(Vs[(size_t)q * l + i]), mu);
+              Vs[(size_t)p * l + i] = make_float4(c * vp.w - s * vq.w, c * vp.x - s * vq.x, c * vp.y - s * vq.y,
+                                                  c * vp.z - s * vq.z);
+              Vs[(size_t)q * l + i] = make_float4(s * vp.w + c * vq.w, s * vp.x + c * vq.x, s * vp.y + c * vq.y,
+                                                  s * vp.z + c * vq.z);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    converged = (s_rot == 0);
+    __syncthreads();
+  }
   if (t == 0 && !converged) qlr_set_error(err, QLR_ENOCONV);
   for (int j = warp; j < l; j += nwarps) {
     float s2 = 0.f;
-    for (int i = lane; i < l; i += 32) s2 += qnorm2(ldw(W, l, i, j));
+    for (int i = lane; i < l; i += 32) s2 += qnorm2(q_of4(W[(size_t)j * l + i]));
     s2 = sqrtf(warp_sum(s2));
     if (lane == 0) sig[j] = s2;
     const float inv = s2 > 0.f ? 1.f / s2 : 0.f;
     for (int i = lane; i < l; i += 32) {
-      const Quat<float> w = ldw(W, l, i, j);
-      stw(W, l, i, j, {w.w * inv, w.x * inv, w.y * inv, w.z * inv});
+      const float4 w = W[(size_t)j * l + i];
+      W[(size_t)j * l + i] = make_float4(w.x * inv, w.y * inv, w.z * inv, w.w * inv);
     }
   }
   __syncthreads();
-  for (int j = t; j < l; j += JT) {
+  for (int j = t; j < l; j += JG_THREADS) {
     const float sj = rank_key(sig[j]);
     int rank = 0;
     for (int i = 0; i < l; ++i) {
@@ -251,15 +329,16 @@ __global__ void __launch_bounds__(JT) jacobi_grouped_kernel(const qlr::JacobiGro
     ord[rank] = j;
   }
   __syncthreads();
-  for (int r = t; r < k; r += JT) a.S[r] = (double)sig[ord[r]];
+  for (int r = t; r < k; r += JG_THREADS) a.S[r] = (double)sig[ord[r]];
   const size_t lk = (size_t)l * k;
   float* U = a.U;
   float* V = a.V;
-  for (size_t e = t; e < 4 * lk; e += JT) {
-    const int c = (int)(e / lk), r = (int)((e % lk) / l), i = (int)(e % l);
-    const size_t src = (size_t)c * ll + (size_t)ord[r] * l + i;
-    U[e] = Vs[src];   // R's left vectors: the rotations of W = R^H
-    V[e] = W[src];    // R's right vectors: W's normalised columns
+  for (size_t e = t; e < lk; e += JG_THREADS) {
+    const int r = (int)(e / l), i = (int)(e % l);
+    const size_t src = (size_t)ord[r] * l + i;
+    const float4 u = Vs[src], v = W[src];   // R's left vectors: the rotations of W = R^H; right: W's columns
+    U[e] = u.x; U[lk + e] = u.y; U[2 * lk + e] = u.z; U[3 * lk + e] = u.w;
+    V[e] = v.x; V[lk + e] = v.y; V[2 * lk + e] = v.z; V[3 * lk + e] = v.w;
   }
 }
 
@@ -900,7 +979,7 @@ int jacobi_grouped(qlr_ctx* ctx, const JacobiGroupArgs* d_args, int count, int l
   const size_t smem = jacobi_grouped_smem(lmax);
   QLR_CUDA_TRY(cudaFuncSetAttribute(jacobi_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   KTimer kt(ctx, QLR_KID_JACOBI);
-  jacobi_grouped_kernel<<<count, JT, smem, ctx->stream>>>(d_args, JMAX_SWEEPS, ctx->d_err);
+  jacobi_grouped_kernel<<<count, JG_THREADS, smem, ctx->stream>>>(d_args, JMAX_SWEEPS, ctx->d_err);
   qlr_count_launch();
   QLR_CUDA_TRY(cudaGetLastError());
   return QLR_OK;

@@ -186,7 +186,7 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 // the tile list (else one CTA per tile).
 struct GroupedSketch {
   int kind = 0, amode = 0, count = 0, nitems = 0, stage_grid_x = 0;
-  int persistent = 0, grid = 0, nb_max = 0, nacc = 1, stages = 0;
+  int persistent = 0, grid = 0, nb_max = 0, stages = 0, apl = 4;
   uint32_t tmem_cols = 0;
   size_t smem = 0;
   void* d_probs = nullptr;
@@ -247,7 +247,13 @@ int selftest_wait_timeout(qlr_ctx* ctx);
 // per-problem arguments and the (problem, tile) items of each launch in device tables built once
 // by the plan.  The small operands are FP32 / double-FP32 (no FP64 instruction on this path).
 constexpr int kBatchMaxL = 80;   // largest l = k + p of a batch plan (one CTA holds its factors)
-//  Gram: gram_tc_grouped (below, with the single-problem tensor-core Gram).
+//  Gram: gram_tc_grouped (below, with the single-problem tensor-core Gram), FP64-class; and, for
+//  the last step of CholeskyQR2 / shifted CholeskyQR3 (a nearly orthonormal input), the FP32 Gram
+//  gram_f32_grouped (gram_f32.cu): Y FP32 column-major planes, G in the same double-FP32 upper
+//  layout, items (problem, tile I, tile J >= I) of 16 x 16 entries.
+struct GramF32Args { const float* y[4]; int64_t ld, m; int l; float* G; };
+void gram_f32_items(int l, int prob, std::vector<int4>& items);
+int gram_f32_grouped(qlr_ctx* ctx, const GramF32Args* d_args, const int4* d_items, int nitems);
 //  Cholesky (orth.cu), one CTA per problem: R = chol(G + shift_coef trace(G) I) in double-FP32;
 //  Rinv = R^{-1} and Rout = R Rprev (R when Rprev is null) as FP32 l x l planes (column-major,
 //  zero below the diagonal); either output may be null.

@@ -40,7 +40,8 @@ using namespace qlr_tc;
 
 constexpr int TC_THREADS = 256;
 constexpr int TBM = 128;          // output rows per CTA (MMA M)
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGES = 4;    // pipeline stages of the per-tile kernels
+constexpr int PMAX_STAGES = 8;   // pipeline stages of the persistent grouped kernel
 
 enum Kind { K_BF16 = 0, K_TF32 = 1, K_TF32X3 = 2 };
 enum AMode { A_K = 0, A_MN = 1, A_T = 2 };   // K-major TMA, MN-major descriptors, transposed by workers
@@ -589,14 +590,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const 
 
 // Persistent grouped form: gridDim.x CTAs (one per SM) walk the item list, CTA b taking items
 // b, b + gridDim.x, ...  The TMA ring, the worker and MMA stage counters run on across items, and
-// the accumulator is double-buffered in TMEM when two fit (nacc = 2): the epilogue drains item t
-// while the MMA warp already accumulates item t + 1 and the producer streams A for the next ones.
-// Shared-memory stages are laid out for the widest column block (nb_max); every problem's tiles
-// use its own nb <= nb_max.
+// the accumulators alternate between the two ends of the CTA's 512 TMEM columns: item t (4 nb_t
+// columns) sits at column 0 when t is even and ends at column 512 when t is odd, so the epilogue
+// drains item t while the MMA warp already accumulates item t + 1 (and the producer streams A for
+// the next ones) unless the two items' columns overlap (nb_t + nb_t+1 > 128); only then does the
+// MMA warp wait for item t's epilogue.  Shared-memory stages are laid out for the widest column
+// block (nb_max); every problem's tiles use its own nb <= nb_max.
 template <int KIND, int AMODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     sketch_tc_persistent_kernel(const TcParams* __restrict__ probs, const int4* __restrict__ items, int nitems,
-                                int nb_max, int nacc, int stages, uint32_t tmem_cols, int* err) {
+                                int nb_max, int stages, int apl, uint32_t tmem_cols, int* err) {
   using C = Cfg<KIND>;
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
@@ -612,28 +615,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int X_BYTES = nb_max * C::SW;
-  const int A_SET = 4 * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
+  // apl A planes per stage: 3 when every problem is pure quaternion (plane 0 absent; BF16 / TF32
+  // loaded as is), else 4; plane c is stored at slot c - (4 - apl)
+  const int c0 = 4 - apl;
+  const int A_SET = apl * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
   const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint64_t* full = bars;
-  uint64_t* empty = bars + MAX_STAGES;
-  uint64_t* ready = bars + 2 * MAX_STAGES;
-  uint64_t* acc_full = bars + 3 * MAX_STAGES;        // [2]
-  uint64_t* acc_empty = bars + 3 * MAX_STAGES + 2;   // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * MAX_STAGES + 4);
+  uint64_t* empty = bars + PMAX_STAGES;
+  uint64_t* ready = bars + 2 * PMAX_STAGES;
+  uint64_t* acc_full = bars + 3 * PMAX_STAGES;        // [2]
+  uint64_t* acc_empty = bars + 3 * PMAX_STAGES + 2;   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * PMAX_STAGES + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int my_items = (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
   auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + c * A_BYTES; };
-  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + c * A_BYTES; };
+  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - c0) * A_BYTES; };
   auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + 4 * A_BYTES + c * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
   auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < MAX_STAGES; ++s) {
+    for (int s = 0; s < PMAX_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
       mbar_init(&ready[s], 64);
@@ -711,18 +717,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int g = 0;
       bool ok = true;
-      const StageDescs D = make_stage_descs<KIND, AMODE>(smem_u32(smem), stage_bytes, HI_OFF, A_BYTES, A_SET, X_BYTES);
+      const StageDescs D =
+          make_stage_descs<KIND, AMODE>(smem_u32(smem), stage_bytes, HI_OFF - c0 * A_BYTES, A_BYTES, A_SET, X_BYTES);
+      int prev_nb = 0;
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
         const TcParams& p = probs[it.x];
         const TcScalars pv = tc_scalars(p);
-        const int a = t % nacc;
-        if (t >= nacc) {
-          ok = mbar_wait(&acc_empty[a], (uint32_t)((t / nacc) - 1) & 1u, abort_flag, err);
+        const int a = t & 1;
+        if (t >= 2) {   // item t - 2 (same end of TMEM) drained
+          ok = mbar_wait(&acc_empty[a], (uint32_t)((t >> 1) - 1) & 1u, abort_flag, err);
           if (!ok) break;
-          tc_fence_after();
         }
-        const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
+        if (t >= 1 && 4 * (pv.nb + prev_nb) > (int)tmem_cols) {   // overlaps item t - 1: wait for its drain
+          ok = mbar_wait(&acc_empty[a ^ 1], (uint32_t)((t - 1) >> 1) & 1u, abort_flag, err);
+          if (!ok) break;
+        }
+        if (t >= 1) tc_fence_after();
+        prev_nb = pv.nb;
+        const uint32_t acc_base = tmem + (a ? tmem_cols - (uint32_t)(4 * pv.nb) : 0u);
         for (int i = 0; i < pv.kiters; ++i, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -802,13 +815,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int4 it = items[blockIdx.x + t * gridDim.x];
       const TcParams& p = probs[it.x];
       const TcScalars pv = tc_scalars(p);
-      const int a = t % nacc;
-      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(t / nacc) & 1u, abort_flag, err) && !*abort_flag;
+      const int a = t & 1;
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)(t >> 1) & 1u, abort_flag, err) && !*abort_flag;
       tc_fence_after();
       if (!ok) break;
       const int64_t grow = (int64_t)it.y * TBM + row;
       const int j0 = it.z * pv.nb;
-      const uint32_t acc_base = tmem + (uint32_t)(a * 4 * nb_max);
+      const uint32_t acc_base = tmem + (a ? tmem_cols - (uint32_t)(4 * pv.nb) : 0u);
       for (int d = 0; d < 4; ++d) {
         for (int cc = 0; cc < pv.nb; cc += 32) {
           uint32_t r0[16], r1[16];
@@ -1088,6 +1101,14 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
   const int stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
   if (stages < 2) return QLR_EUNSUPPORTED;
+  // persistent form: only the A planes some problem has (3 when all are pure quaternion, for the
+  // modes that load A as is), and a deeper ring
+  bool all_pure = true;
+  for (int i = 0; i < count; ++i) all_pure = all_pure && (A[i].plane[0] == nullptr);
+  const int apl = (all_pure && !x3 && base.amode != A_T) ? 3 : 4;
+  const size_t pstage = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
+                        (size_t)4 * max_nb * base.sw * (x3 ? 2 : 1);
+  const int pstages = (int)std::min<size_t>(PMAX_STAGES, budget / pstage);
   const int cols = 4 * max_nb;
   const uint32_t tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
 
@@ -1182,15 +1203,15 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   gs.nitems = (int)hi.size();
   gs.persistent = (variant >> 1) & 1;
   gs.nb_max = max_nb;
-  gs.nacc = (2 * 4 * max_nb <= 512) ? 2 : 1;
-  gs.stages = stages;
-  {
-    const int pc = gs.nacc * 4 * max_nb;
+  gs.stages = gs.persistent ? pstages : stages;
+  gs.apl = apl;
+  {   // two accumulators of the widest block when they fit in fewer columns, else all 512
+    const int pc = 2 * 4 * max_nb;
     gs.tmem_cols = pc <= 32 ? 32 : pc <= 64 ? 64 : pc <= 128 ? 128 : pc <= 256 ? 256 : 512;
   }
   gs.grid = std::min(gs.nitems, ctx->num_sms > 0 ? ctx->num_sms : 148);
   gs.stage_grid_x = max_stage_blocks;
-  gs.smem = stages * stage + 1024 + 256;
+  gs.smem = gs.persistent ? pstages * pstage + 1024 + 256 : stages * stage + 1024 + 256;
   gs.d_probs = d_probs;
   gs.d_items = d_items;
   gs.d_stage = d_stage;
@@ -1205,7 +1226,7 @@ int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
     QLR_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
     KTimer kt(ctx, QLR_KID_SKETCH_TC);
     pk<<<(unsigned)gs.grid, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items,
-                                                               gs.nitems, gs.nb_max, gs.nacc, gs.stages, gs.tmem_cols,
+                                                               gs.nitems, gs.nb_max, gs.stages, gs.apl, gs.tmem_cols,
                                                                ctx->d_err);
     qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());

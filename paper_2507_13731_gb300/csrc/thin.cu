@@ -18,15 +18,25 @@ __global__ void small_to_f32_kernel(const double* __restrict__ S, float* __restr
 
 // FP32 thin x small product, one row of C per thread: a CTA takes TS_ROWS rows and COLS columns
 // of C, stages S's rows for those columns in shared memory (TS_KC rows at a time, each entry a
-// quaternion broadcast to every thread), and streams T's rows k (four coalesced loads per k) into
-// COLS quaternion accumulators.  With an upper-triangular S (R^{-1}) rows k >= j0 + COLS of the
-// chunk are zero and skipped.  Batches use 16 columns per CTA (many problems fill the GPU); a
-// single product uses 8, for twice the CTAs.
+// quaternion broadcast to every thread), and streams T's rows k into COLS quaternion
+// accumulators, a few rows k at a time (the coalesced loads of the next 4 (16 columns: 2) rows
+// are in flight while the quaternion multiply-adds of the current ones run; each multiply-add is
+// 16 FMAs into the accumulator).  With an upper-triangular S (R^{-1}) rows k >= j0 + COLS of the chunk are zero
+// and skipped.  Batches use 16 columns per CTA (many problems fill the GPU); a single product
+// uses 8, for twice the CTAs.
 constexpr int TS_ROWS = 128, TS_COLS = 16, TS_COLS1 = 8, TS_KC = 64;
+
+// acc += a * b (Hamilton product, Section 2 eq. 1), as 16 FMAs
+__device__ __forceinline__ void qfma(Quat<float>& acc, const Quat<float>& a, const float4& b) {
+  acc.w = fmaf(a.w, b.x, acc.w); acc.w = fmaf(-a.x, b.y, acc.w); acc.w = fmaf(-a.y, b.z, acc.w); acc.w = fmaf(-a.z, b.w, acc.w);
+  acc.x = fmaf(a.w, b.y, acc.x); acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.w, acc.x); acc.x = fmaf(-a.z, b.z, acc.x);
+  acc.y = fmaf(a.w, b.z, acc.y); acc.y = fmaf(-a.x, b.w, acc.y); acc.y = fmaf(a.y, b.x, acc.y); acc.y = fmaf(a.z, b.y, acc.y);
+  acc.z = fmaf(a.w, b.w, acc.z); acc.z = fmaf(a.x, b.z, acc.z); acc.z = fmaf(-a.y, b.y, acc.z); acc.z = fmaf(a.z, b.x, acc.z);
+}
 
 template <int COLS>
 __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, int cc) {
-  __shared__ float4 Bs[TS_KC][COLS];
+  __shared__ float4 Bs[TS_KC][COLS + 1];   // padded rows: conflict-free staging
   const int t = threadIdx.x;
   const int j0 = cc * COLS;
   const int N = (int)g.N, K = (int)g.K;
@@ -35,10 +45,10 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
   const int64_t i = rb * TS_ROWS + t;
   const bool row_ok = i < g.M;
   const int64_t lda = g.sa_k, ldb = g.ldb;
-  const float* a0 = static_cast<const float*>(g.a[0]) + i;
-  const float* a1 = static_cast<const float*>(g.a[1]) + i;
-  const float* a2 = static_cast<const float*>(g.a[2]) + i;
-  const float* a3 = static_cast<const float*>(g.a[3]) + i;
+  const float* __restrict__ a0 = static_cast<const float*>(g.a[0]) + i;
+  const float* __restrict__ a1 = static_cast<const float*>(g.a[1]) + i;
+  const float* __restrict__ a2 = static_cast<const float*>(g.a[2]) + i;
+  const float* __restrict__ a3 = static_cast<const float*>(g.a[3]) + i;
   const float* b0 = static_cast<const float*>(g.b[0]);
   const float* b1 = static_cast<const float*>(g.b[1]);
   const float* b2 = static_cast<const float*>(g.b[2]);
@@ -60,16 +70,33 @@ __device__ __forceinline__ void thin_small_tile(const GemmArgs& g, int64_t rb, i
     }
     __syncthreads();
     if (row_ok) {
-#pragma unroll 2
-      for (int kk = 0; kk < kn; ++kk) {
+      // software pipeline: the loads of the next U rows are issued before the multiply-adds of
+      // the current ones
+      constexpr int U = (COLS > 8) ? 2 : 4;   // rows k per batch of loads (register budget)
+      const int kfull = kn / U * U;
+      Quat<float> cur[U], nxt[U];
+      auto load = [&](Quat<float>* a, int kb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t o = (int64_t)(k0 + kb + u) * lda;
+          a[u] = {a0[o], a1[o], a2[o], a3[o]};
+        }
+      };
+      if (kfull > 0) load(cur, 0);
+      for (int kk = 0; kk < kfull; kk += U) {
+        if (kk + U < kfull) load(nxt, kk + U);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int jj = 0; jj < COLS; ++jj) qfma(acc[jj], cur[u], Bs[kk + u][jj]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+      }
+      for (int kk = kfull; kk < kn; ++kk) {
         const int64_t o = (int64_t)(k0 + kk) * lda;
         const Quat<float> a = {a0[o], a1[o], a2[o], a3[o]};
 #pragma unroll
-        for (int jj = 0; jj < COLS; ++jj) {
-          const float4 b = Bs[kk][jj];
-          const Quat<float> p = qmul(a, Quat<float>{b.x, b.y, b.z, b.w});
-          acc[jj].w += p.w; acc[jj].x += p.x; acc[jj].y += p.y; acc[jj].z += p.z;
-        }
+        for (int jj = 0; jj < COLS; ++jj) qfma(acc[jj], a, Bs[kk][jj]);
       }
     }
   }
@@ -91,7 +118,7 @@ __global__ void __launch_bounds__(TS_ROWS) thin_small_kernel(GemmArgs g) {
 }
 
 // Many independent products in one launch (batch plans): item (problem, row block, column chunk).
-__global__ void __launch_bounds__(TS_ROWS) thin_small_grouped_kernel(const GemmArgs* __restrict__ args,
+__global__ void __launch_bounds__(TS_ROWS, 4) thin_small_grouped_kernel(const GemmArgs* __restrict__ args,
                                                                     const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   thin_small_tile<TS_COLS>(args[it.x], it.y, it.z);
