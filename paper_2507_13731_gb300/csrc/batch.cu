@@ -37,6 +37,7 @@ struct qlr_batch {
     float* G;         // Gram, double-FP32 upper triangle
     float* Rinv;      // R^{-1} of the current step (FP32)
     float* Rp[2];     // running products of the last pass's R factors (FP32)
+    float* Sinv[2];   // inverse last factors of passes v - 1 ([0]) and v ([1]), carried (see layout)
     float* Uh;        // core QSVD: left vectors (l x k)
     float* Vh;        // core QSVD: right vectors (l x k)
     int k, p, l;
@@ -158,7 +159,7 @@ int enqueue(qlr_batch* b) {
         QLR_TRY(qlr::gram_tc_grouped(mc, st.gram, b->slice_items[par], b->n_slice[par], b->gram_items[par],
                                      b->n_gram[par], b->comb_items[par], b->n_comb[par]));
       QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
-      QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
+      if (st.apply) QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
   }
   QLR_TRY(qlr::jacobi_grouped(mc, b->jac, b->count, b->lmax));
@@ -263,6 +264,8 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     P.Rinv = take<float>(cur, (size_t)4 * P.l * P.l);
     P.Rp[0] = take<float>(cur, (size_t)4 * P.l * P.l);
     P.Rp[1] = take<float>(cur, (size_t)4 * P.l * P.l);
+    P.Sinv[0] = take<float>(cur, (size_t)4 * P.l * P.l);
+    P.Sinv[1] = take<float>(cur, (size_t)4 * P.l * P.l);
     P.Uh = take<float>(cur, (size_t)4 * P.l * P.k);
     P.Vh = take<float>(cur, (size_t)4 * P.l * P.k);
   }
@@ -296,11 +299,20 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
     tb.add(gf);
   }
   const size_t rec = gram_tc_record_bytes();
-  // steps of every pass: Y (odd) or Z (even) -> Q1 or Q2, through T
+  // steps of every pass: Y (odd) or Z (even) -> Q1 or Q2, through T.
+  // The last two passes carry their last CholeskyQR factor S instead of applying it: their basis
+  // buffer keeps B = Q S (the previous step's output) and S^{-1} is kept in Sinv.  The last pass
+  // then sketches with B_{v-1} = Q_{v-1} S_{v-1}, so its own factorisation B_v R' of that sketch
+  // gives the core factor R = R' S_{v-1}^{-1} (the chain's first Rprev), and the lifts take
+  // Q_v U_hat = B_v (S_v^{-1} U_hat), Q_{v-1} V_hat = B_{v-1} (S_{v-1}^{-1} V_hat) (the factors
+  // applied to the core's vectors in the Jacobi launch).  The same factorisations in exact
+  // arithmetic, without two thin x small products per run.
   for (int i = 1; i <= passes; ++i) {
     const int o = (i >= passes - 1) ? b->orth : b->mid;
     const int ns = orth_steps(o);
+    const bool carry = (i >= passes - 1);
     for (int s = 0; s < ns; ++s) {
+      const bool no_apply = carry && (s == ns - 1);
       const bool g32 = fp32_gram_step(o, s);
       std::vector<char> ga(g32 ? 0 : (size_t)count * rec);
       std::vector<GramF32Args> gfa(g32 ? count : 0);
@@ -313,12 +325,16 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         qlr_qmat T = P.T;
         T.rows = dst.rows;
         T.ld = dst.ld;
-        // 1 step: src -> dst; 2: src -> T -> dst; 3: src -> dst -> T -> dst
+        // 1 step: src -> dst; 2: src -> T -> dst; 3: src -> dst -> T -> dst; carried (the last
+        // step factors only): 2: src -> dst, 3: src -> T -> dst
         const qlr_qmat* seq[4] = {&src, &dst, nullptr, nullptr};
-        if (ns == 2) { seq[1] = &T; seq[2] = &dst; }
-        if (ns == 3) { seq[2] = &T; seq[3] = &dst; }
+        if (carry) {
+          if (ns == 3) { seq[1] = &T; seq[2] = &dst; }
+        } else {
+          if (ns == 2) { seq[1] = &T; seq[2] = &dst; }
+          if (ns == 3) { seq[2] = &T; seq[3] = &dst; }
+        }
         const qlr_qmat& from = *seq[s];
-        const qlr_qmat& to = *seq[s + 1];
         if (g32) {
           GramF32Args& G = gfa[j];
           for (int c = 0; c < 4; ++c) G.y[c] = static_cast<const float*>(from.plane[c]);
@@ -332,19 +348,22 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
         }
         CholGroupArgs& C = ca[j];
         C.G = P.G;
-        C.Rinv = P.Rinv;
+        C.Rinv = no_apply ? P.Sinv[i == passes ? 1 : 0] : P.Rinv;
         C.l = P.l;
         // shifted first step (span steps, shifted CholeskyQR3): s = 11 (m l + l (l + 1)) u trace(G),
         // u = 2^-48 for the double-FP32 Gram and Cholesky
         const bool shifted = (s == 0) && (o == QLR_ORTH_SCHOLQR3 || o == ORTH_SPAN);
         C.shift_coef = shifted ? (float)(11.0 * ((double)from.rows * P.l + (double)P.l * (P.l + 1)) * 3.552713678800501e-15)
                                : 0.f;
-        // the last pass keeps R = R_s ... R_0 for the core QSVD
+        // the last pass keeps R = R_s ... R_0 S_{v-1}^{-1} for the core QSVD
         C.Rout = (i == passes) ? P.Rp[s % 2] : nullptr;
-        C.Rprev = (i == passes && s > 0) ? P.Rp[(s - 1) % 2] : nullptr;
-        aa[j] = thin_small_args(from, P.Rinv, P.l, P.l, to);
-        aa[j].b_upper = true;   // R^{-1} is upper triangular
+        C.Rprev = (i == passes) ? (s > 0 ? P.Rp[(s - 1) % 2] : P.Sinv[0]) : nullptr;
+        if (!no_apply) {
+          aa[j] = thin_small_args(from, P.Rinv, P.l, P.l, *seq[s + 1]);
+          aa[j].b_upper = true;   // R^{-1} is upper triangular
+        }
       }
+      if (no_apply) aa.clear();
       if (g32) tb.add(gfa);
       else tb.add_raw(ga);
       tb.add(ca);
@@ -359,7 +378,7 @@ size_t layout(qlr_batch* b, const qlr_qmat* A, const int* k, const int* p, const
   std::vector<int4> li;
   for (int j = 0; j < count; ++j) {
     qlr_batch::Prob& P = b->pr[j];
-    ja[j] = {P.Rp[(nlast - 1) % 2], P.Uh, P.Vh, P.S, P.l, P.k};
+    ja[j] = {P.Rp[(nlast - 1) % 2], P.Uh, P.Vh, P.S, P.l, P.k, P.Sinv[1], P.Sinv[0]};
     const float* Uhat = (passes % 2 == 0) ? P.Vh : P.Uh;
     const float* Vhat = (passes % 2 == 0) ? P.Uh : P.Vh;
     la[j] = thin_small_args(P.Q1, Uhat, P.l, P.k, P.U);
@@ -483,6 +502,7 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
         else st.gram = next();
         st.chol = reinterpret_cast<const CholGroupArgs*>(next());
         st.apply = reinterpret_cast<const GemmArgs*>(next());
+        if (i >= passes - 1 && s == ns - 1) st.apply = nullptr;   // carried factor (see layout)
         b->steps[i - 1].push_back(st);
       }
     }

@@ -209,7 +209,9 @@ __device__ __forceinline__ T rank_key(T x) { return isnan(x) ? -INFINITY : x; }
 // and the rotation, so a warp works on 32 / g pairs at once and no lane idles on a short column;
 // the group's dot products are reduced with log2(g) shuffle steps.  After the sweeps
 // sigma_j = |w_j| and u_j = w_j / sigma_j; the k largest sigma (descending, ties by column) go to
-// S and their u, v columns to U, V.  Without the FP64 Rayleigh step of the single-problem path:
+// S and their u, v columns to U, V (times the upper-triangular Lleft, Lright when given: the
+// carried inverse factors of the plan's last two passes).  Without the FP64 Rayleigh step of the
+// single-problem path:
 // the plan's sketches and bases are BF16 / FP32, and the column norms carry the FP32 accuracy of
 // the rotated columns.
 constexpr int JG_THREADS = 640;   // 40 groups of 16 lanes: every pair of a round at once (l <= 80)
@@ -333,12 +335,31 @@ __global__ void __launch_bounds__(JG_THREADS) jacobi_grouped_kernel(const qlr::J
   const size_t lk = (size_t)l * k;
   float* U = a.U;
   float* V = a.V;
+  const float* Ll = a.Lleft;
+  const float* Lr = a.Lright;
   for (size_t e = t; e < lk; e += JG_THREADS) {
     const int r = (int)(e / l), i = (int)(e % l);
-    const size_t src = (size_t)ord[r] * l + i;
-    const float4 u = Vs[src], v = W[src];   // R's left vectors: the rotations of W = R^H; right: W's columns
-    U[e] = u.x; U[lk + e] = u.y; U[2 * lk + e] = u.z; U[3 * lk + e] = u.w;
-    V[e] = v.x; V[lk + e] = v.y; V[2 * lk + e] = v.z; V[3 * lk + e] = v.w;
+    const size_t col = (size_t)ord[r] * l;
+    // R's left vectors: the rotations of W = R^H; right: W's normalised columns
+    Quat<float> u = q_of4(Vs[col + i]), v = q_of4(W[col + i]);
+    if (Ll) {
+      u = {0.f, 0.f, 0.f, 0.f};
+      for (int tt = i; tt < l; ++tt) {
+        const size_t o = (size_t)tt * l + i;
+        const Quat<float> pr = qmul(Quat<float>{Ll[o], Ll[ll + o], Ll[2 * ll + o], Ll[3 * ll + o]}, q_of4(Vs[col + tt]));
+        u.w += pr.w; u.x += pr.x; u.y += pr.y; u.z += pr.z;
+      }
+    }
+    if (Lr) {
+      v = {0.f, 0.f, 0.f, 0.f};
+      for (int tt = i; tt < l; ++tt) {
+        const size_t o = (size_t)tt * l + i;
+        const Quat<float> pr = qmul(Quat<float>{Lr[o], Lr[ll + o], Lr[2 * ll + o], Lr[3 * ll + o]}, q_of4(W[col + tt]));
+        v.w += pr.w; v.x += pr.x; v.y += pr.y; v.z += pr.z;
+      }
+    }
+    U[e] = u.w; U[lk + e] = u.x; U[2 * lk + e] = u.y; U[3 * lk + e] = u.z;
+    V[e] = v.w; V[lk + e] = v.x; V[2 * lk + e] = v.y; V[3 * lk + e] = v.z;
   }
 }
 

@@ -266,8 +266,9 @@ void thin_small_items(int64_t M, int64_t N, int prob, std::vector<int4>& items);
 int thin_small_grouped(qlr_ctx* ctx, const GemmArgs* d_args, const int4* d_items, int nitems);
 //  Core QSVD (core_svd.cu), one CTA per problem: one-sided Jacobi on R (FP32 l x l planes) with
 //  W and V in shared memory; the k largest sigma in descending order into S, the matching left
-//  vectors into U and right vectors into V (FP32 l x k planes, column-major).
-struct JacobiGroupArgs { const float* R; float* U; float* V; double* S; int l, k; };
+//  vectors into U and right vectors into V (FP32 l x k planes, column-major), multiplied on the
+//  left by the upper-triangular Lleft / Lright (FP32 l x l planes) when those are set.
+struct JacobiGroupArgs { const float* R; float* U; float* V; double* S; int l, k; const float* Lleft; const float* Lright; };
 size_t jacobi_grouped_smem(int lmax);
 int jacobi_grouped(qlr_ctx* ctx, const JacobiGroupArgs* d_args, int count, int lmax);
 
