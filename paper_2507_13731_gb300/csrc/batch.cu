@@ -158,7 +158,8 @@ int enqueue(qlr_batch* b) {
       else
         QLR_TRY(qlr::gram_tc_grouped(mc, st.gram, b->slice_items[par], b->n_slice[par], b->gram_items[par],
                                      b->n_gram[par], b->comb_items[par], b->n_comb[par]));
-      QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
+      if (st.gram32) QLR_TRY(qlr::chol_f32_grouped(mc, st.chol, b->count, b->lmax));
+      else QLR_TRY(qlr::chol_df_grouped(mc, st.chol, b->count, b->lmax));
       if (st.apply) QLR_TRY(qlr::thin_small_grouped(mc, st.apply, b->apply_items[par], b->n_apply[par]));
     }
   }

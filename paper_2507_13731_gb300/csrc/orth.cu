@@ -1632,6 +1632,137 @@ __global__ void __launch_bounds__(CG_THREADS) chol_df_grouped_kernel(const qlr::
   }
 }
 
+// The same grouped factorisation in plain FP32 (a packed upper triangle of float4 quaternions),
+// for the Gram of the last CholeskyQR2 step, which is formed in FP32 (its input is already nearly
+// orthonormal, so its factor is well conditioned): a quarter of the shared memory and a fraction
+// of the instructions of the double-FP32 form, 256 threads, several problems per SM.
+constexpr int CF_THREADS = 256;
+
+__global__ void __launch_bounds__(CF_THREADS) chol_f32_grouped_kernel(const qlr::CholGroupArgs* __restrict__ args,
+                                                                     int* err) {
+  const qlr::CholGroupArgs& a = args[blockIdx.x];
+  const int l = a.l;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* W = reinterpret_cast<float4*>(smem_raw);
+  const int ntri = l * (l + 1) / 2;
+  float* rdiag_inv = reinterpret_cast<float*>(W + ntri);
+  __shared__ float s_rp;
+  const int t = threadIdx.x, lane = t % 32, warp = t / 32, nwarps = CF_THREADS / 32;
+  auto at = [&](int i, int k) -> float4& { return W[k * (k + 1) / 2 + i]; };
+  for (int e = t; e < ntri; e += CF_THREADS) {
+    const int2 ik = upper_tri_entry(e);
+    W[e] = *reinterpret_cast<const float4*>(a.G + 8 * ((size_t)ik.y * l + ik.x));
+  }
+  __syncthreads();
+  if (a.shift_coef != 0.f) {   // shift s = shift_coef * trace(G) on the diagonal
+    if (warp == 0) {
+      float tr = 0.f;
+      for (int i = lane; i < l; i += 32) tr += at(i, i).x;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      if (lane == 0) s_rp = tr;
+    }
+    __syncthreads();
+    const float sh = a.shift_coef * s_rp;
+    __syncthreads();
+    for (int i = t; i < l; i += CF_THREADS) at(i, i).x += sh;
+    __syncthreads();
+  }
+  for (int j = 0; j < l; ++j) {
+    if (t == 0) {
+      float d = at(j, j).x;
+      if (!(d > 0.f)) {
+        qlr_set_error(err, QLR_ENOTPD);
+        d = 1e-30f;
+      }
+      const float r = sqrtf(d);
+      at(j, j) = make_float4(r, 0.f, 0.f, 0.f);
+      s_rp = 1.f / r;
+      rdiag_inv[j] = 1.f / r;
+    }
+    __syncthreads();
+    const float rp = s_rp;
+    for (int k = j + 1 + t; k < l; k += CF_THREADS) {   // row j of R
+      float4& w = at(j, k);
+      w.x *= rp; w.y *= rp; w.z *= rp; w.w *= rp;
+    }
+    __syncthreads();
+    const int n = l - j - 1;
+    const int npairs = n * (n + 1) / 2;
+    for (int e = t; e < npairs; e += CF_THREADS) {
+      const int2 ik = upper_tri_entry(e);
+      const int i = j + 1 + ik.x, k = j + 1 + ik.y;
+      const Quat<float> pr = qcmul(q_of(at(j, i)), q_of(at(j, k)));
+      float4& w = at(i, k);
+      w.x -= pr.w; w.y -= pr.x; w.z -= pr.y; w.w -= pr.z;
+    }
+    __syncthreads();
+  }
+  const size_t ll = (size_t)l * l;
+  float* Rinv = a.Rinv;
+  if (Rinv) {
+    for (int j = warp; j < l; j += nwarps) {
+      Quat<float> x[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) x[u] = {(lane + 32 * u == j) ? 1.f : 0.f, 0.f, 0.f, 0.f};
+      for (int i = j; i >= 0; --i) {
+        const int src = i & 31, slot = i >> 5;
+        Quat<float> xi = (slot == 0) ? x[0] : (slot == 1 ? x[1] : x[2]);
+        const float ri = rdiag_inv[i];
+        xi.w = __shfl_sync(0xffffffffu, xi.w, src) * ri;
+        xi.x = __shfl_sync(0xffffffffu, xi.x, src) * ri;
+        xi.y = __shfl_sync(0xffffffffu, xi.y, src) * ri;
+        xi.z = __shfl_sync(0xffffffffu, xi.z, src) * ri;
+        if (lane == src) {
+          if (slot == 0) x[0] = xi;
+          else if (slot == 1) x[1] = xi;
+          else x[2] = xi;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int r = lane + 32 * u;
+          if (r < i) {
+            const Quat<float> pr = qmul(q_of(at(r, i)), xi);
+            x[u].w -= pr.w; x[u].x -= pr.x; x[u].y -= pr.y; x[u].z -= pr.z;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int r = lane + 32 * u;
+        if (r < l) {
+          const bool up = (r <= j);
+          const size_t o = (size_t)j * l + r;
+          Rinv[o] = up ? x[u].w : 0.f;
+          Rinv[ll + o] = up ? x[u].x : 0.f;
+          Rinv[2 * ll + o] = up ? x[u].y : 0.f;
+          Rinv[3 * ll + o] = up ? x[u].z : 0.f;
+        }
+      }
+    }
+  }
+  float* Rout = a.Rout;
+  const float* Rprev = a.Rprev;
+  if (Rout) {
+    for (int e = t; e < (int)ll; e += CF_THREADS) {
+      const int i = e % l, j = e / l;
+      Quat<float> acc = {0.f, 0.f, 0.f, 0.f};
+      if (i <= j) {
+        if (Rprev) {
+          for (int tt = i; tt <= j; ++tt) {
+            const size_t o = (size_t)j * l + tt;
+            const Quat<float> pr = qmul(q_of(at(i, tt)), Quat<float>{Rprev[o], Rprev[ll + o], Rprev[2 * ll + o], Rprev[3 * ll + o]});
+            acc.w += pr.w; acc.x += pr.x; acc.y += pr.y; acc.z += pr.z;
+          }
+        } else {
+          acc = q_of(at(i, j));
+        }
+      }
+      Rout[e] = acc.w; Rout[ll + e] = acc.x; Rout[2 * ll + e] = acc.y; Rout[3 * ll + e] = acc.z;
+    }
+  }
+}
+
 }  // namespace
 
 namespace qlr {
@@ -1640,6 +1771,20 @@ namespace qlr {
 // grouped steps of batch plans
 
 size_t chol_df_grouped_smem(int lmax) { return (size_t)lmax * (lmax + 1) / 2 * sizeof(DQ) + (size_t)lmax * 4 + 64; }
+
+size_t chol_f32_grouped_smem(int lmax) { return (size_t)lmax * (lmax + 1) / 2 * sizeof(float4) + (size_t)lmax * 4 + 64; }
+
+int chol_f32_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax) {
+  if (count <= 0) return QLR_OK;
+  if (lmax > kBatchMaxL) return QLR_EUNSUPPORTED;
+  const size_t smem = chol_f32_grouped_smem(lmax);
+  QLR_CUDA_TRY(cudaFuncSetAttribute(chol_f32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KTimer kt(ctx, QLR_KID_CHOL);
+  chol_f32_grouped_kernel<<<count, CF_THREADS, smem, ctx->stream>>>(d_args, ctx->d_err);
+  qlr_count_launch();
+  QLR_CUDA_TRY(cudaGetLastError());
+  return QLR_OK;
+}
 
 int chol_df_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax) {
   if (count <= 0) return QLR_OK;

@@ -260,6 +260,8 @@ int gram_f32_grouped(qlr_ctx* ctx, const GramF32Args* d_args, const int4* d_item
 struct CholGroupArgs { const float* G; const float* Rprev; float* Rout; float* Rinv; int l; float shift_coef; };
 size_t chol_df_grouped_smem(int lmax);
 int chol_df_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax);
+//  The same in plain FP32 (G's high parts only), for the steps whose Gram is formed in FP32.
+int chol_f32_grouped(qlr_ctx* ctx, const CholGroupArgs* d_args, int count, int lmax);
 //  Thin x small products (thin.cu): FP32 GemmArgs (A column-major, sa_i == 1, 4 planes; B FP32
 //  column-major; no conj, alpha 1, beta 0), items (problem, row block, column chunk).
 void thin_small_items(int64_t M, int64_t N, int prob, std::vector<int4>& items);
