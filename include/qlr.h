@@ -308,8 +308,9 @@ int qlr_qsvd_lowrank_batched(qlr_ctx* ctx, int count, const qlr_qmat* A, const i
  * (double-FP32, one CTA per problem, also forming R^{-1} and the running product of the R
  * factors in FP32) and a grouped thin x small product; the core QSVDs (FP32 one-sided Jacobi,
  * sigma from the converged column norms) and the lifts are one launch each.  At creation the plan allocates its
- * device memory (cudaMalloc), times four variants of the grouped sketch (tile order x one CTA per
- * tile or persistent CTAs) and keeps the fastest (the autotuner), runs the whole sequence once
+ * device memory (cudaMalloc), times the variants of the grouped sketch (tile order x one CTA per
+ * tile or persistent CTAs x, for persistent CTAs, the tile shape: K elements per stage and the
+ * widest column block) and keeps the fastest (the autotuner), runs the whole sequence once
  * (its results are valid), and captures it into a CUDA graph unless opts.flags has
  * QLR_FLAG_NO_GRAPH.  The pointers in A, omega, U, S, V are baked into the plan: later runs read
  * and write the same buffers.
@@ -323,11 +324,18 @@ typedef struct qlr_batch qlr_batch;
 typedef struct {
   int32_t lanes;           /* streams a run uses (1: every step is one grouped launch) */
   int32_t graph;           /* 1 when runs replay the captured CUDA graph               */
-  int32_t tile_order;      /* grouped sketch variant chosen: bit 0 tiles with the longest reduction
-                              first (else problem order), bit 1 persistent CTAs (else one per tile) */
+  int32_t tile_order;      /* grouped sketch variant chosen (0..15): bit 0 tiles with the longest
+                              reduction first (else problem order), bit 1 persistent CTAs (else one
+                              per tile), bit 2 128-byte stage rows (persistent, BF16/TF32 K-major
+                              A), bit 3 column blocks of at most 64 (else 128)                   */
   int32_t sketch_launches; /* grouped launches per run (staging + sketch per pass)     */
-  float tune_ms[4];        /* autotuner: N + H sketch time of each variant (ms)       */
+  float tune_ms[16];       /* autotuner: N + H sketch time of each variant (ms; 0 when the variant
+                              is not timed: tile shapes apply to the persistent form only) */
   int64_t launches_per_run;/* kernels launched per run (all streams)                  */
+  int32_t stage_k;         /* chosen shape of the first pass's sketch: K elements per stage, */
+  int32_t col_block_max;   /*   widest column block (MMA N; the MMA M is 128 rows),        */
+  int32_t ring_stages;     /*   pipeline stages                                            */
+  int32_t reserved;
 } qlr_batch_stats;
 int qlr_batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const int* p, int passes,
                      const qlr_qmat* omega, const qlr_opts* opts, qlr_qmat* U, double* const* S, qlr_qmat* V,

@@ -19,6 +19,8 @@
 
 namespace {
 
+constexpr int kBatchVariants = 16;   // grouped sketch variants (see autotune)
+
 // One orthonormalisation step of one pass (device tables, one entry per problem).
 struct StepTables {
   const void* gram = nullptr;               // tensor-core Gram records (FP64-class steps)
@@ -66,8 +68,9 @@ struct qlr_batch {
   void* dev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int order = 1;                            // chosen grouped-sketch variant (bit 0 order, bit 1 persistent)
-  float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
+  int order = 1;                            // chosen grouped-sketch variant (bit 0 order, bit 1 persistent,
+                                            // bit 2 128-byte stage rows, bit 3 column blocks <= 64)
+  float tune_ms[kBatchVariants] = {};
   int64_t launches_per_run = 0;
 };
 
@@ -187,15 +190,25 @@ int plan_sketches(qlr_batch* b, int order) {
   return QLR_OK;
 }
 
+// Whether the autotuner times variant v: the tile shapes (bits 2, 3) only apply to the persistent
+// schedule, and 128-byte stage rows not to 3xTF32 (its stages are 32-byte rows).
+bool tuned_variant(int v, int compute) {
+  if (!((v >> 1) & 1) && (v & 12)) return false;
+  if (compute == QLR_COMPUTE_TF32X3 && ((v >> 2) & 1)) return false;
+  return true;
+}
+
 // Autotuner: time the grouped sketch variants -- tile order (problem order / longest reduction
-// first) x schedule (one CTA per tile / one persistent CTA per SM) -- on passes N and H, best of
-// three after a warm-up, and keep the fastest.
+// first) x schedule (one CTA per tile / one persistent CTA per SM) x, for the persistent schedule,
+// tile shape (K elements per stage: 64-byte or 128-byte rows; column blocks of at most 128 or 64)
+// -- on passes N and H, best of three after a warm-up, and keep the fastest.
 int autotune(qlr_batch* b) {
   cudaEvent_t e0, e1;
   QLR_CUDA_TRY(cudaEventCreate(&e0));
   QLR_CUDA_TRY(cudaEventCreate(&e1));
   int rc = QLR_OK;
-  for (int order = 0; order < 4 && rc == QLR_OK; ++order) {
+  for (int order = 0; order < kBatchVariants && rc == QLR_OK; ++order) {
+    if (!tuned_variant(order, b->compute)) continue;
     rc = plan_sketches(b, order);
     if (rc != QLR_OK) break;
     float best = 1e30f;
@@ -214,7 +227,10 @@ int autotune(qlr_batch* b) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   QLR_TRY(rc);
-  b->order = (int)(std::min_element(b->tune_ms, b->tune_ms + 4) - b->tune_ms);
+  int best = -1;
+  for (int v = 0; v < kBatchVariants; ++v)
+    if (tuned_variant(v, b->compute) && (best < 0 || b->tune_ms[v] < b->tune_ms[best])) best = v;
+  b->order = best;
   return plan_sketches(b, b->order);
 }
 
@@ -511,10 +527,12 @@ int batch_create(qlr_ctx* ctx, int count, const qlr_qmat* A, const int* k, const
     b->lift = reinterpret_cast<const GemmArgs*>(next());
     b->lift_items = reinterpret_cast<const int4*>(next());
   }
-  // QLR_BATCH_VARIANT=0..3 in the environment fixes the grouped sketch variant (no tuning)
+  // QLR_BATCH_VARIANT=0..15 in the environment fixes the grouped sketch variant (no tuning)
   const char* force = std::getenv("QLR_BATCH_VARIANT");
-  if (rc == QLR_OK && force && force[0] >= '0' && force[0] <= '3' && force[1] == 0) {
-    b->order = force[0] - '0';
+  char* fend = nullptr;
+  const long fv = force ? std::strtol(force, &fend, 10) : -1;
+  if (rc == QLR_OK && force && fend != force && *fend == 0 && fv >= 0 && fv < kBatchVariants) {
+    b->order = (int)fv;
     rc = plan_sketches(b, b->order);
   } else if (rc == QLR_OK) {
     rc = tune ? autotune(b) : plan_sketches(b, b->order);
@@ -579,7 +597,11 @@ extern "C" int qlr_batch_info(const qlr_batch* b, qlr_batch_stats* st) {
   st->lanes = 1;
   st->graph = b->exec ? 1 : 0;
   st->tile_order = b->order;
-  for (int i = 0; i < 4; ++i) st->tune_ms[i] = b->tune_ms[i];
+  for (int i = 0; i < kBatchVariants; ++i) st->tune_ms[i] = b->tune_ms[i];
+  const qlr::GroupedSketch& g = b->gs[0];   // the first pass's plan (op N)
+  st->stage_k = g.stage_k;
+  st->col_block_max = g.nb_max;
+  st->ring_stages = g.stages;
   st->sketch_launches = 2 * b->passes;
   st->launches_per_run = b->launches_per_run;
   return QLR_OK;

@@ -183,10 +183,11 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 // for every output tile).  The plan lives in caller-provided device memory (`dev`, sized by
 // sketch_tc_grouped_bytes) and is reused by every run.  `variant` bit 0: schedule the tiles with
 // the longest reduction first (else in problem order); bit 1: one persistent CTA per SM walking
-// the tile list (else one CTA per tile).
+// the tile list (else one CTA per tile); bit 2 (persistent, K-major A, BF16 / TF32): 128-byte
+// stage rows (else 64); bit 3: column blocks of at most 64 (else 128).
 struct GroupedSketch {
   int kind = 0, amode = 0, count = 0, nitems = 0, stage_grid_x = 0;
-  int persistent = 0, grid = 0, nb_max = 0, stages = 0, apl = 4;
+  int persistent = 0, grid = 0, nb_max = 0, stages = 0, apl = 4, wide = 0, stage_k = 0;
   uint32_t tmem_cols = 0;
   size_t smem = 0;
   void* d_probs = nullptr;

@@ -596,11 +596,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const 
 // the next ones) unless the two items' columns overlap (nb_t + nb_t+1 > 128); only then does the
 // MMA warp wait for item t's epilogue.  Shared-memory stages are laid out for the widest column
 // block (nb_max); every problem's tiles use its own nb <= nb_max.
-template <int KIND, int AMODE>
+template <int KIND, int AMODE, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     sketch_tc_persistent_kernel(const TcParams* __restrict__ probs, const int4* __restrict__ items, int nitems,
                                 int nb_max, int stages, int apl, uint32_t tmem_cols, int* err) {
-  using C = Cfg<KIND>;
+  using C = Cfg<KIND, WIDE>;
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
   constexpr bool TR = (AMODE == A_T);
@@ -717,8 +717,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int g = 0;
       bool ok = true;
-      const StageDescs D =
-          make_stage_descs<KIND, AMODE>(smem_u32(smem), stage_bytes, HI_OFF - c0 * A_BYTES, A_BYTES, A_SET, X_BYTES);
+      const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF - c0 * A_BYTES,
+                                                               A_BYTES, A_SET, X_BYTES);
       int prev_nb = 0;
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, err);
           if (!ok) break;
           tc_fence_after();
-          issue_stage<KIND, AMODE>(D, s, acc_base, pv.nb, pv.c_first, pv.idesc_base, pv.neg_mask, i == 0);
+          issue_stage<KIND, AMODE, WIDE>(D, s, acc_base, pv.nb, pv.c_first, pv.idesc_base, pv.neg_mask, i == 0);
           umma_commit(&empty[s]);
         }
         umma_commit(&acc_full[a]);   // accumulator of item t complete (also after an abort)
@@ -1049,13 +1049,13 @@ struct GDims {
   int l, nb, ncb, mtiles, kiters;
   int64_t ldo;
 };
-GDims gdims(int op, const qlr_qmat& A, const qlr_qmat& X, const Plan& base) {
+GDims gdims(int op, const qlr_qmat& A, const qlr_qmat& X, const Plan& base, int ncap) {
   GDims g{};
   g.M = (op == QLR_OP_N) ? A.rows : A.cols;
   g.K = (op == QLR_OP_N) ? A.cols : A.rows;
   g.l = (int)X.cols;
   const int lp = (g.l + 15) / 16 * 16;
-  g.ncb = (lp + 127) / 128;
+  g.ncb = (lp + ncap - 1) / ncap;
   g.nb = ((lp + g.ncb - 1) / g.ncb + 15) / 16 * 16;
   g.mtiles = (int)((g.M + TBM - 1) / TBM);
   g.kiters = (int)((g.K + base.bk - 1) / base.bk);
@@ -1071,7 +1071,7 @@ size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_q
   size_t b = align256((size_t)count * sizeof(TcParams)) + align256((size_t)count * sizeof(StageArg));
   size_t items = 0;
   for (int i = 0; i < count; ++i) {
-    const GDims g = gdims(op, A[i], X[i], base);
+    const GDims g = gdims(op, A[i], X[i], base, 64);   // the narrowest column blocks: the most items
     items += (size_t)g.mtiles * g.ncb;
     b += align256((size_t)4 * g.ldo * g.l * xesz) * (base.kind == K_TF32X3 ? 2 : 1);
   }
@@ -1081,15 +1081,23 @@ size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_q
 int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, const qlr_qmat* X, const qlr_qmat* Y,
                            int compute, int variant, char* dev, size_t bytes, GroupedSketch& gs) {
   const int order = variant & 1;
+  const bool persistent = (variant >> 1) & 1;
   if (count <= 0) return QLR_EINVAL;
-  const Plan base = make_plan(compute, op, 1, 1, 16, 1, false);
+  Plan base = make_plan(compute, op, 1, 1, 16, 1, false);
+  // tile shape: 128-byte stage rows (twice the K elements per stage) for the persistent form of
+  // a K-major A, and column blocks of at most 128 or 64
+  if (persistent && ((variant >> 2) & 1) && base.amode == A_K && base.kind != K_TF32X3) {
+    base.sw = 128;
+    base.bk = base.sw / base.esz;
+  }
+  const int ncap = ((variant >> 3) & 1) ? 64 : 128;
   const size_t xesz = (base.kind == K_BF16) ? 2 : 4;
   const bool x3 = base.kind == K_TF32X3;
   std::vector<GDims> dims(count);
   int max_nb = 16;
   for (int i = 0; i < count; ++i) {
     if (!sketch_tc_supported(op, A[i], X[i], compute)) return QLR_EUNSUPPORTED;
-    dims[i] = gdims(op, A[i], X[i], base);
+    dims[i] = gdims(op, A[i], X[i], base, ncap);
     const GDims& g = dims[i];
     if (g.M <= 0 || g.K <= 0 || g.l <= 0) return QLR_ESHAPE;
     if (X[i].dtype != QLR_F32 || X[i].layout != QLR_COL_MAJOR || X[i].rows != g.K) return QLR_EINVAL;
@@ -1126,7 +1134,8 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   std::vector<int4> hi;
   hi.reserve(nitems);
   const CUtensorMapDataType dt = (base.kind == K_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const CUtensorMapSwizzle sw = (base.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUtensorMapSwizzle sw = (base.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B
+                                : (base.sw == 64) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   uint32_t neg = 0;
   const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
   for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
@@ -1201,7 +1210,9 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   gs.amode = base.amode;
   gs.count = count;
   gs.nitems = (int)hi.size();
-  gs.persistent = (variant >> 1) & 1;
+  gs.persistent = persistent ? 1 : 0;
+  gs.wide = base.sw == 128 ? 1 : 0;
+  gs.stage_k = base.bk;
   gs.nb_max = max_nb;
   gs.stages = gs.persistent ? pstages : stages;
   gs.apl = apl;
@@ -1222,7 +1233,9 @@ namespace {
 template <int KIND, int AMODE>
 int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
   if (gs.persistent) {
-    auto pk = sketch_tc_persistent_kernel<KIND, AMODE>;
+    auto pk = sketch_tc_persistent_kernel<KIND, AMODE, false>;
+    if constexpr (AMODE == A_K && KIND != K_TF32X3)
+      if (gs.wide) pk = sketch_tc_persistent_kernel<KIND, AMODE, true>;
     QLR_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
     KTimer kt(ctx, QLR_KID_SKETCH_TC);
     pk<<<(unsigned)gs.grid, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items,

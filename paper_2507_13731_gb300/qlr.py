@@ -57,8 +57,9 @@ class OptsC(ctypes.Structure):
 
 class BatchStatsC(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("graph", ctypes.c_int32), ("tile_order", ctypes.c_int32),
-                ("sketch_launches", ctypes.c_int32), ("tune_ms", ctypes.c_float * 4),
-                ("launches_per_run", ctypes.c_int64)]
+                ("sketch_launches", ctypes.c_int32), ("tune_ms", ctypes.c_float * 16),
+                ("launches_per_run", ctypes.c_int64), ("stage_k", ctypes.c_int32),
+                ("col_block_max", ctypes.c_int32), ("ring_stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -418,7 +419,8 @@ class Batch:
         _check(lib().qlr_batch_info(self.h, ctypes.byref(st)), "qlr_batch_info")
         return {"lanes": st.lanes, "graph": bool(st.graph), "tile_order": st.tile_order,
                 "sketch_launches": st.sketch_launches, "tune_ms": list(st.tune_ms),
-                "launches_per_run": st.launches_per_run}
+                "launches_per_run": st.launches_per_run, "stage_k": st.stage_k,
+                "col_block_max": st.col_block_max, "ring_stages": st.ring_stages}
 
     def close(self) -> None:
         if self.h:

@@ -72,8 +72,12 @@ def test_batch_plan_graph_replay(ctx):
     assert ctx.sync() == 0
     first = [s.clone() for s in Ss]
     info = b.info()
-    assert info["graph"] and info["sketch_launches"] == 6 and info["tile_order"] in (0, 1, 2, 3)
-    assert min(info["tune_ms"]) > 0 and info["launches_per_run"] > 6
+    assert info["graph"] and info["sketch_launches"] == 6 and 0 <= info["tile_order"] < 16
+    timed = [v for v in range(16) if info["tune_ms"][v] > 0]
+    # every schedule x order, and for the persistent one every tile shape (BF16: 2 + 8 variants)
+    assert len(timed) == 10 and info["tune_ms"][info["tile_order"]] == min(info["tune_ms"][v] for v in timed)
+    assert info["stage_k"] in (32, 64) and info["col_block_max"] % 16 == 0 and info["ring_stages"] >= 2
+    assert info["launches_per_run"] > 6
     for _ in range(2):
         for s in Ss:
             s.zero_()
@@ -88,11 +92,12 @@ def test_batch_plan_graph_replay(ctx):
     b.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 6, 7, 10, 11, 14, 15])
 def test_batch_sketch_variants(ctx, monkeypatch, variant):
-    """Every grouped sketch variant (tile order x one CTA per tile / persistent CTAs, fixed
+    """Every grouped sketch variant (tile order x one CTA per tile / persistent CTAs x, for the
+    persistent CTAs, 64- or 128-byte stage rows and column blocks of at most 128 or 64; fixed
     through QLR_BATCH_VARIANT) gives the oracle's sigma; 80 problems give the persistent CTAs
-    several tiles each and exercise the double-buffered accumulator."""
+    several tiles each and exercise the alternating accumulators."""
     from paper_2507_13731_gb300 import qlr
     monkeypatch.setenv("QLR_BATCH_VARIANT", str(variant))
     probs = synth.batched_problems(count=80, seed=45, mmax=900, nmax=600, rmax=40)
