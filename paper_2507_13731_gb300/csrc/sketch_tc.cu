@@ -40,8 +40,8 @@ using namespace qlr_tc;
 
 constexpr int TC_THREADS = 256;
 constexpr int TBM = 128;          // output rows per CTA (MMA M)
-constexpr int MAX_STAGES = 4;    // pipeline stages of the per-tile kernels
-constexpr int PMAX_STAGES = 8;   // pipeline stages of the persistent grouped kernel
+constexpr int MAX_STAGES = 8;    // pipeline stages (as many as fit in shared memory, at most 8)
+constexpr int PMAX_STAGES = MAX_STAGES;
 
 enum Kind { K_BF16 = 0, K_TF32 = 1, K_TF32X3 = 2 };
 enum AMode { A_K = 0, A_MN = 1, A_T = 2 };   // K-major TMA, MN-major descriptors, transposed by workers
@@ -69,6 +69,7 @@ struct TcParams {
   int flush;                // K stages per accumulation chunk (0: the whole piece in one chunk)
   int nbuf;                 // TMEM chunk accumulators (2: the MMA fills one while the other drains)
   int ttotal;               // 1: the chunks' running sum is kept in TMEM columns [4 nb, 8 nb)
+  int apl;                  // A planes per stage: 3 for a pure quaternion A (plane 0 absent), else 4
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -83,7 +84,7 @@ struct TcScalars {
   int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
-  int flush, nbuf, ttotal;
+  int flush, nbuf, ttotal, apl;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
 };
 __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
@@ -92,7 +93,7 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
   v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
-  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal;
+  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal; v.apl = p.apl == 3 ? 3 : 4;
   return v;
 }
 
@@ -146,12 +147,14 @@ struct StageDescs {
 
 template <int KIND, int AMODE, bool WIDE = false>
 __device__ __forceinline__ StageDescs make_stage_descs(uint32_t sbase, int stage_bytes, int hi_off, int a_bytes,
-                                                       int a_set, int x_bytes) {
+                                                       int a_set, int x_bytes, int apl) {
   using C = Cfg<KIND, WIDE>;
   StageDescs D;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const uint32_t ah = sbase + (uint32_t)(hi_off + c * a_bytes), al = ah + (uint32_t)(4 * a_bytes);
+    // plane c of the hi (and lo) set at slot c - (4 - apl): hi_off is the set's offset minus
+    // (4 - apl) planes; the slots of absent planes are never used
+    const uint32_t ah = sbase + (uint32_t)(hi_off + c * a_bytes), al = ah + (uint32_t)(apl * a_bytes);
     if (AMODE == A_MN) {   // MN-major: LBO = stride between MN atoms, SBO = stride between 8-row K groups
       D.a[c] = make_desc(ah, C::BK * C::SW, 8 * C::SW, C::MODE);
       D.alo[c] = make_desc(al, C::BK * C::SW, 8 * C::SW, C::MODE);
@@ -234,7 +237,10 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nb = pv.nb;
   const int X_BYTES = nb * C::SW;
-  const int A_SET = 4 * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));   // [raw][hi][lo]
+  // A sets [raw][hi][lo] of APL planes each: plane c at slot c - (4 - APL) (APL = 3 for a pure
+  // quaternion A, whose plane 0 is absent)
+  const int APL = pv.apl, C0 = 4 - APL;
+  const int A_SET = APL * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
   const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint64_t* full = bars;
@@ -261,10 +267,10 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   const int it1 = sg.it1;
   const int nit = it1 - it0;
 
-  constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
-  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + c * A_BYTES; };
-  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + c * A_BYTES; };
-  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + 4 * A_BYTES + c * A_BYTES; };
+  const int HI_OFF = TR ? APL * A_BYTES : 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - C0) * A_BYTES; };
+  auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - C0) * A_BYTES; };
+  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (APL + c - C0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
   auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
 
@@ -335,7 +341,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     if (lane == 0) {
       bool ok = true;
       int chunk = 0;
-      const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF, A_BYTES, A_SET, X_BYTES);
+      const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF - C0 * A_BYTES,
+                                                               A_BYTES, A_SET, X_BYTES, APL);
       for (int i = 0; i < nit && ok; ++i) {
         const int ic = i % F;                      // stage within the accumulation chunk
         if (i > 0 && ic == 0) {                    // chunk boundary: hand the finished chunk over
@@ -615,8 +622,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int X_BYTES = nb_max * C::SW;
-  // apl A planes per stage: 3 when every problem is pure quaternion (plane 0 absent; BF16 / TF32
-  // loaded as is), else 4; plane c is stored at slot c - (4 - apl)
+  // apl A planes per set: 3 when every problem is pure quaternion (plane 0 absent), else 4; plane
+  // c is stored at slot c - (4 - apl)
   const int c0 = 4 - apl;
   const int A_SET = apl * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
   const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
@@ -631,10 +638,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int my_items = (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  constexpr int HI_OFF = TR ? 4 * A_BYTES : 0;
-  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + c * A_BYTES; };
+  const int HI_OFF = TR ? apl * A_BYTES : 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - c0) * A_BYTES; };
   auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - c0) * A_BYTES; };
-  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + 4 * A_BYTES + c * A_BYTES; };
+  auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (apl + c - c0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
   auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
 
@@ -718,7 +725,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0;
       bool ok = true;
       const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF - c0 * A_BYTES,
-                                                               A_BYTES, A_SET, X_BYTES);
+                                                               A_BYTES, A_SET, X_BYTES, apl);
       int prev_nb = 0;
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
@@ -916,7 +923,7 @@ int kind_of(int compute) {
 }
 
 struct Plan {
-  int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages;
+  int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages, apl;
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
   int flush, nbuf, ttotal;       // accumulation chunks (stages per chunk, TMEM buffers, TMEM sum)
   bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
@@ -933,8 +940,9 @@ struct Plan {
 constexpr int X3_FLUSH_STAGES = 32;
 constexpr int X3_MAX_NB = 64;
 
-Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true) {
+Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true, int apl = 4) {
   Plan pl{};
+  pl.apl = apl;
   pl.kind = kind_of(compute);
   pl.amode = (op == QLR_OP_N) ? A_K : (pl.kind == K_BF16 ? A_MN : A_T);
   pl.esz = pl.kind == K_BF16 ? 2 : 4;
@@ -964,7 +972,7 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   const int cols = (pl.ttotal ? 2 : pl.nbuf) * 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   const bool x3 = pl.kind == K_TF32X3;
-  const size_t stage = (size_t)4 * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
+  const size_t stage = (size_t)apl * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
                        (size_t)4 * pl.nb * pl.sw * (x3 ? 2 : 1);
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
   pl.stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
@@ -1104,19 +1112,17 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     if (Y[i].dtype != QLR_F32 || Y[i].layout != QLR_COL_MAJOR || Y[i].rows != g.M || Y[i].cols != g.l) return QLR_ESHAPE;
     max_nb = std::max(max_nb, g.nb);
   }
-  const size_t stage = (size_t)4 * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
+  // only the A planes some problem has (3 when all are pure quaternion)
+  bool all_pure = true;
+  for (int i = 0; i < count; ++i) all_pure = all_pure && (A[i].plane[0] == nullptr);
+  const int apl = all_pure ? 3 : 4;
+  const size_t stage = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
                        (size_t)4 * max_nb * base.sw * (x3 ? 2 : 1);
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
   const int stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
   if (stages < 2) return QLR_EUNSUPPORTED;
-  // persistent form: only the A planes some problem has (3 when all are pure quaternion, for the
-  // modes that load A as is), and a deeper ring
-  bool all_pure = true;
-  for (int i = 0; i < count; ++i) all_pure = all_pure && (A[i].plane[0] == nullptr);
-  const int apl = (all_pure && !x3 && base.amode != A_T) ? 3 : 4;
-  const size_t pstage = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
-                        (size_t)4 * max_nb * base.sw * (x3 ? 2 : 1);
-  const int pstages = (int)std::min<size_t>(PMAX_STAGES, budget / pstage);
+  const size_t pstage = stage;
+  const int pstages = stages;
   const int cols = 4 * max_nb;
   const uint32_t tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
 
@@ -1151,6 +1157,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     char* xlo = x3 ? take((size_t)4 * g.ldo * g.l * 4) : nullptr;
     if ((size_t)(cur - dev) > bytes) return QLR_ENOMEM;
     prm.c_first = (a.plane[0] == nullptr) ? 1 : 0;
+    prm.apl = apl;
     for (int c = prm.c_first; c < 4; ++c) {
       bool ok;
       if (op == QLR_OP_N)
@@ -1297,7 +1304,8 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   if (M == 0 || l == 0) return QLR_OK;
   if (K == 0) return zero_qmat(ctx, Y);
   if (X.dtype != QLR_F32 && !(compute == QLR_COMPUTE_BF16 && X.dtype == QLR_BF16)) return QLR_EINVAL;
-  const Plan pl = make_plan(compute, op, M, K, l, ctx->num_sms > 0 ? ctx->num_sms : 148);
+  const Plan pl = make_plan(compute, op, M, K, l, ctx->num_sms > 0 ? ctx->num_sms : 148, true,
+                            A.plane[0] == nullptr ? 3 : 4);
   if (pl.stages < 2) return QLR_EUNSUPPORTED;
   size_t mark = ws.off;
   // stage the thin operand with a 16-byte aligned column pitch
@@ -1333,6 +1341,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
                                 : (pl.sw == 64) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   const int esz = pl.esz;
   prm.c_first = (A.plane[0] == nullptr) ? 1 : 0;
+  prm.apl = pl.apl;
   for (int c = prm.c_first; c < 4; ++c) {
     bool ok;
     if (op == QLR_OP_N)   // K-major: inner = n (reduction), outer = m (output rows); box {BK, 128}
