@@ -671,8 +671,18 @@ def profile_driver(args):
     e1.record()
     torch.cuda.synchronize()
     rc = ctx.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same calls again with every kernel class bracketed by events (launches ms per call)
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    for _ in range(args.steps):
+        call()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    rc = rc or ctx.sync()
+    classes = {k: [round(nl / args.steps, 1), round(t / args.steps, 4)] for k, (nl, t) in st.items() if nl}
     print(json.dumps({"only": args.only, "config": args.config, "op": args.op, "ell": ell, "passes": v,
-                      "compute": args.compute, "ms_per_call": e0.elapsed_time(e1) / args.steps,
+                      "compute": args.compute, "ms_per_call": ms, "classes_launches_ms": classes,
                       "device_error": rc}), flush=True)
     ctx.close()
     return 0 if rc == 0 else 1
