@@ -187,7 +187,7 @@ bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compu
 // stage rows (else 64); bit 3: column blocks of at most 64 (else 128).
 struct GroupedSketch {
   int kind = 0, amode = 0, count = 0, nitems = 0, stage_grid_x = 0;
-  int persistent = 0, grid = 0, nb_max = 0, stages = 0, apl = 4, wide = 0, stage_k = 0;
+  int persistent = 0, grid = 0, nb_max = 0, stages = 0, apl = 4, wide = 0, stage_k = 0, fd = 0;
   uint32_t tmem_cols = 0;
   size_t smem = 0;
   void* d_probs = nullptr;

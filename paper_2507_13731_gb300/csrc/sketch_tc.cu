@@ -70,6 +70,7 @@ struct TcParams {
   int nbuf;                 // TMEM chunk accumulators (2: the MMA fills one while the other drains)
   int ttotal;               // 1: the chunks' running sum is kept in TMEM columns [4 nb, 8 nb)
   int apl;                  // A planes per stage: 3 for a pure quaternion A (plane 0 absent), else 4
+  int fd;                   // 1: fused output planes (one MMA per input plane, N = 4 nb; see issue_stage)
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -84,7 +85,7 @@ struct TcScalars {
   int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
-  int flush, nbuf, ttotal, apl;
+  int flush, nbuf, ttotal, apl, fd;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
 };
 __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
@@ -93,7 +94,7 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   v.ldy = p.ldy; v.part = p.part; v.counters = p.counters; v.M = p.M; v.l = p.l; v.nb = p.nb; v.ncb = p.ncb;
   v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
-  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal; v.apl = p.apl == 3 ? 3 : 4;
+  v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal; v.apl = p.apl == 3 ? 3 : 4; v.fd = p.fd;
   return v;
 }
 
@@ -147,7 +148,7 @@ struct StageDescs {
 
 template <int KIND, int AMODE, bool WIDE = false>
 __device__ __forceinline__ StageDescs make_stage_descs(uint32_t sbase, int stage_bytes, int hi_off, int a_bytes,
-                                                       int a_set, int x_bytes, int apl) {
+                                                       int a_set, int x_bytes, int apl, int nxp) {
   using C = Cfg<KIND, WIDE>;
   StageDescs D;
 #pragma unroll
@@ -162,7 +163,8 @@ __device__ __forceinline__ StageDescs make_stage_descs(uint32_t sbase, int stage
       D.a[c] = make_desc(ah, 16, 8 * C::SW, C::MODE);
       D.alo[c] = make_desc(al, 16, 8 * C::SW, C::MODE);
     }
-    const uint32_t xh = sbase + (uint32_t)(a_set + c * x_bytes), xl = xh + (uint32_t)(4 * x_bytes);
+    // X tile c of the hi (and lo) set: nxp tiles of x_bytes each
+    const uint32_t xh = sbase + (uint32_t)(a_set + c * x_bytes), xl = xh + (uint32_t)(nxp * x_bytes);
     D.x[c] = make_desc(xh, 16, 8 * C::SW, C::MODE);
     D.xlo[c] = make_desc(xl, 16, 8 * C::SW, C::MODE);
   }
@@ -170,19 +172,42 @@ __device__ __forceinline__ StageDescs make_stage_descs(uint32_t sbase, int stage
   return D;
 }
 
-// All MMAs of stage s into the accumulator at TMEM column abase (output plane d at abase + d nb):
-// per K step and input plane c, one MMA per output plane d of A_c against X_{c xor d} (three for
-// 3xTF32: hi hi, lo hi, hi lo), the sign of the Hamilton product in the negate-B bit.  `fresh`:
-// the first stage of an accumulation chunk (its first MMA overwrites the accumulator).
+// All MMAs of stage s into the accumulator at TMEM column abase (output plane d at abase + d nb).
+// Plain form: per K step and input plane c, one MMA per output plane d of A_c against X_{c xor d}
+// (three for 3xTF32: hi hi, lo hi, hi lo), the sign of the Hamilton product in the negate-B bit.
+// Fused form (fd): per K step and input plane c, one MMA of N = 4 nb of A_c against the staged
+// operand X~_c whose rows d nb + j hold sign(c, d) X_{c xor d}(:, j) -- all four output planes in
+// one instruction.  A tcgen05 MMA of M = 128 takes about the same time for every N up to ~100
+// (measured on GB300: ~53 cycles for N = 32..96, then ~N / 2), so the fused form issues a quarter
+// of the MMAs at four times the width.  `fresh`: the first stage of an accumulation chunk (its
+// first MMA overwrites the accumulator).
 template <int KIND, int AMODE, bool WIDE = false>
 __device__ __forceinline__ void issue_stage(const StageDescs& D, int s, uint32_t abase, int nb, int c_first,
-                                            uint32_t idesc_base, uint32_t neg_mask, bool fresh) {
+                                            uint32_t idesc_base, uint32_t neg_mask, bool fresh, int fd, int c0) {
   using C = Cfg<KIND, WIDE>;
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr int KSTEPS = C::BK / C::MMA_K;
   constexpr uint64_t KA = (AMODE == A_MN) ? (uint64_t)((C::MMA_K * C::SW) >> 4) : (uint64_t)((C::MMA_K * C::ESZ) >> 4);
   constexpr uint64_t KB = (uint64_t)((C::MMA_K * C::ESZ) >> 4);
   const uint64_t so = (uint64_t)s * D.sstep;
+  if (fd) {
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < c_first) continue;
+        const uint64_t ad = D.a[c] + so + ks * KA;
+        const uint64_t bd = D.x[c - c0] + so + ks * KB;
+        const uint32_t acc = (!fresh || ks > 0 || c > c_first) ? 1u : 0u;
+        umma<KIND>(abase, ad, bd, idesc_base, acc);
+        if (X3) {
+          umma<KIND>(abase, D.alo[c] + so + ks * KA, bd, idesc_base, 1u);
+          umma<KIND>(abase, ad, D.xlo[c - c0] + so + ks * KB, idesc_base, 1u);
+        }
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int ks = 0; ks < KSTEPS; ++ks) {
 #pragma unroll
@@ -236,12 +261,14 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nb = pv.nb;
-  const int X_BYTES = nb * C::SW;
+  const bool FD = pv.fd != 0;
+  const int X_BYTES = (FD ? 4 * nb : nb) * C::SW;       // one X tile: nb rows, or 4 nb fused rows
   // A sets [raw][hi][lo] of APL planes each: plane c at slot c - (4 - APL) (APL = 3 for a pure
   // quaternion A, whose plane 0 is absent)
   const int APL = pv.apl, C0 = 4 - APL;
   const int A_SET = APL * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
-  const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
+  const int NXP = FD ? APL : 4;                          // X tiles per set (per input plane when fused)
+  const int stage_bytes = A_SET + NXP * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + MAX_STAGES;
@@ -272,7 +299,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - C0) * A_BYTES; };
   auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (APL + c - C0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
-  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
+  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + (NXP + q) * X_BYTES; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < MAX_STAGES; ++s) {
@@ -303,7 +330,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + 4 * X_BYTES * (X3 ? 2 : 1));
+      const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + (FD ? 4 - pv.c_first : 4) * X_BYTES * (X3 ? 2 : 1));
       int issued = 0;
       for (int i = 0; i < nit; ++i) {
         const int s = i % STAGES;
@@ -322,9 +349,16 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
             tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
           }
         }
-        for (int q = 0; q < 4; ++q) {
-          tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
-          if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+        if (FD) {   // X~_c, rows [cb 4 nb, (cb + 1) 4 nb)
+          for (int c = pv.c_first; c < 4; ++c) {
+            tma_load_2d(smem_u32(x_plane(s, c - C0)), &p.tmX[c], k0, 4 * j0, &full[s]);
+            if (X3) tma_load_2d(smem_u32(xlo_plane(s, c - C0)), &p.tmXlo[c], k0, 4 * j0, &full[s]);
+          }
+        } else {
+          for (int q = 0; q < 4; ++q) {
+            tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
+            if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+          }
         }
         ++issued;
       }
@@ -342,7 +376,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
       bool ok = true;
       int chunk = 0;
       const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF - C0 * A_BYTES,
-                                                               A_BYTES, A_SET, X_BYTES, APL);
+                                                               A_BYTES, A_SET, X_BYTES, APL, NXP);
       for (int i = 0; i < nit && ok; ++i) {
         const int ic = i % F;                      // stage within the accumulation chunk
         if (i > 0 && ic == 0) {                    // chunk boundary: hand the finished chunk over
@@ -360,7 +394,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
         ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, pv.err);
         if (!ok) break;
         tc_fence_after();
-        issue_stage<KIND, AMODE, WIDE>(D, s, abase, nb, pv.c_first, pv.idesc_base, pv.neg_mask, ic == 0);
+        issue_stage<KIND, AMODE, WIDE>(D, s, abase, nb, pv.c_first, pv.idesc_base, pv.neg_mask, ic == 0, pv.fd, C0);
         umma_commit(&empty[s]);   // frees the stage once these MMAs have read it
       }
       umma_commit(&tmem_full[chunk % NBUF]);   // last chunk complete (also fires after an abort)
@@ -606,7 +640,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_grouped_kernel(const 
 template <int KIND, int AMODE, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     sketch_tc_persistent_kernel(const TcParams* __restrict__ probs, const int4* __restrict__ items, int nitems,
-                                int nb_max, int stages, int apl, uint32_t tmem_cols, int* err) {
+                                int nb_max, int stages, int apl, int fd, uint32_t tmem_cols, int* err) {
   using C = Cfg<KIND, WIDE>;
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
@@ -621,12 +655,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int X_BYTES = nb_max * C::SW;
+  const int X_BYTES = (fd ? 4 * nb_max : nb_max) * C::SW;   // one X tile (4 nb_max fused rows when fd)
   // apl A planes per set: 3 when every problem is pure quaternion (plane 0 absent), else 4; plane
   // c is stored at slot c - (4 - apl)
   const int c0 = 4 - apl;
   const int A_SET = apl * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
-  const int stage_bytes = A_SET + 4 * X_BYTES * (X3 ? 2 : 1);
+  const int NXP = fd ? apl : 4;
+  const int stage_bytes = A_SET + NXP * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + PMAX_STAGES;
@@ -643,7 +678,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - c0) * A_BYTES; };
   auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (apl + c - c0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
-  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + 4 * X_BYTES + q * X_BYTES; };
+  auto xlo_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + (NXP + q) * X_BYTES; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < PMAX_STAGES; ++s) {
@@ -687,7 +722,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const int64_t m0 = (int64_t)it.y * TBM;
         const int j0 = it.z * pv.nb;
-        const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + 4 * pv.nb * C::SW * (X3 ? 2 : 1));
+        const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES +
+                                       (fd ? (4 - pv.c_first) * 4 * pv.nb : 4 * pv.nb) * C::SW * (X3 ? 2 : 1));
         for (int i = 0; i < pv.kiters; ++i, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -705,9 +741,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
             }
           }
-          for (int q = 0; q < 4; ++q) {
-            tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
-            if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+          if (fd) {   // X~_c, rows [cb 4 nb, (cb + 1) 4 nb)
+            for (int c = pv.c_first; c < 4; ++c) {
+              tma_load_2d(smem_u32(x_plane(s, c - c0)), &p.tmX[c], k0, 4 * j0, &full[s]);
+              if (X3) tma_load_2d(smem_u32(xlo_plane(s, c - c0)), &p.tmXlo[c], k0, 4 * j0, &full[s]);
+            }
+          } else {
+            for (int q = 0; q < 4; ++q) {
+              tma_load_2d(smem_u32(x_plane(s, q)), &p.tmX[q], k0, j0, &full[s]);
+              if (X3) tma_load_2d(smem_u32(xlo_plane(s, q)), &p.tmXlo[q], k0, j0, &full[s]);
+            }
           }
         }
       }
@@ -725,7 +768,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0;
       bool ok = true;
       const StageDescs D = make_stage_descs<KIND, AMODE, WIDE>(smem_u32(smem), stage_bytes, HI_OFF - c0 * A_BYTES,
-                                                               A_BYTES, A_SET, X_BYTES, apl);
+                                                               A_BYTES, A_SET, X_BYTES, apl, NXP);
       int prev_nb = 0;
       for (int t = 0; t < my_items && ok; ++t) {
         const int4 it = items[blockIdx.x + t * gridDim.x];
@@ -749,7 +792,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = mbar_wait(WORKERS ? &ready[s] : &full[s], ph, abort_flag, err);
           if (!ok) break;
           tc_fence_after();
-          issue_stage<KIND, AMODE, WIDE>(D, s, acc_base, pv.nb, pv.c_first, pv.idesc_base, pv.neg_mask, i == 0);
+          issue_stage<KIND, AMODE, WIDE>(D, s, acc_base, pv.nb, pv.c_first, pv.idesc_base, pv.neg_mask, i == 0, fd, c0);
           umma_commit(&empty[s]);
         }
         umma_commit(&acc_full[a]);   // accumulator of item t complete (also after an abort)
@@ -859,63 +902,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// Grouped operand staging: problem blockIdx.y's X (FP32, column-major) into its staged buffer.
+// Operand staging: the thin operand X (FP32, column-major) into the layout the sketch's TMA reads,
+// as rows (one per operand column) of K elements at pitch ldo, converted to the MMA type (BF16,
+// TF32, or the 3xTF32 hi / lo pair).  Plain layout: row q cols + j = X_q(:, j).  Fused layout
+// (fd): per input plane c >= c0 and column block cb, 4 nb rows, row (c - c0) ncb 4 nb + cb 4 nb
+// + d nb + j = sign(c, d) X_{c xor d}(:, cb nb + j) (zero past the last column), so one MMA of
+// N = 4 nb forms every output plane (issue_stage).
 struct StageArg {
   const float* x[4];
-  int64_t ldx, rows, cols, ldo;
+  int64_t ldx, rows, cols, ldo;   // rows: K (the reduction), cols: l
   void* out;
   void* out_lo;
+  int fd, nb, ncb, c0;
+  uint32_t neg;                   // bit c*4+d: sign(c, d) = -1
+  int nrows;                      // staged rows: 4 cols, or (4 - c0) ncb 4 nb
 };
 
-// One CTA per (column range, problem): columns j = blockIdx.x, blockIdx.x + gridDim.x, ... of all
-// four planes, rows across the threads (coalesced on both sides, no 64-bit division per entry).
+template <int MODE>
+__device__ __forceinline__ void stage_row(const StageArg& a, int r, int64_t k0, int64_t k1, int t, int nt) {
+  int q, j;
+  float sg = 1.f;
+  bool valid = true;
+  if (!a.fd) {
+    q = r / (int)a.cols;
+    j = r % (int)a.cols;
+  } else {
+    const int per = a.ncb * 4 * a.nb;
+    const int c = a.c0 + r / per, rr = r % per;
+    const int d = (rr % (4 * a.nb)) / a.nb;
+    j = (rr / (4 * a.nb)) * a.nb + rr % a.nb;
+    q = c ^ d;
+    sg = ((a.neg >> (c * 4 + d)) & 1u) ? -1.f : 1.f;
+    valid = j < a.cols;
+  }
+  const float* src = a.x[q] + (int64_t)(valid ? j : 0) * a.ldx;
+  const size_t o0 = (size_t)r * a.ldo;
+  for (int64_t i = k0 + t; i < k1; i += nt) {
+    const float v = valid ? sg * src[i] : 0.f;
+    if (MODE == K_BF16) {
+      static_cast<__nv_bfloat16*>(a.out)[o0 + i] = __float2bfloat16_rn(v);
+    } else if (MODE == K_TF32) {
+      static_cast<float*>(a.out)[o0 + i] = v;
+    } else {
+      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      static_cast<float*>(a.out)[o0 + i] = h;
+      static_cast<float*>(a.out_lo)[o0 + i] = v - h;
+    }
+  }
+}
+
+// Grouped: problem blockIdx.y; a warp per staged row, the rows over the grid's x blocks.
 template <int MODE>
 __global__ void __launch_bounds__(256) stage_x_grouped_kernel(const StageArg* __restrict__ args) {
   const StageArg a = args[blockIdx.y];
-  const int rows = (int)a.rows, cols = (int)a.cols;
-  for (int j = blockIdx.x; j < cols; j += gridDim.x)
-    for (int c = 0; c < 4; ++c) {
-      const float* src = a.x[c] + (int64_t)j * a.ldx;
-      const size_t o0 = (size_t)c * a.ldo * a.cols + (size_t)j * a.ldo;
-      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        const float v = src[i];
-        if (MODE == K_BF16) {
-          static_cast<__nv_bfloat16*>(a.out)[o0 + i] = __float2bfloat16_rn(v);
-        } else if (MODE == K_TF32) {
-          static_cast<float*>(a.out)[o0 + i] = v;
-        } else {
-          const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-          static_cast<float*>(a.out)[o0 + i] = h;
-          static_cast<float*>(a.out_lo)[o0 + i] = v - h;
-        }
-      }
-    }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int r = blockIdx.x * 8 + warp; r < a.nrows; r += gridDim.x * 8) stage_row<MODE>(a, r, 0, a.rows, lane, 32);
 }
 
-// Operand staging: X (F32, column-major) -> BF16 copy, plain FP32 copy, or hi / lo FP32 pair.
-// Grid (row chunks of 2048, columns, planes): each thread stages 8 rows of one column of one plane.
+// One problem: grid (reduction chunks of STAGE_ROWS, staged rows).
 constexpr int STAGE_ROWS = 2048;
-__global__ void __launch_bounds__(256) stage_x_kernel(const float* __restrict__ x0, const float* __restrict__ x1,
-                                                      const float* __restrict__ x2, const float* __restrict__ x3,
-                                                      int64_t ldx, int64_t rows, int64_t cols, int mode,
-                                                      void* __restrict__ out, void* __restrict__ out_lo, int64_t ldo) {
-  const int c = blockIdx.z, j = blockIdx.y;
-  const float* src = (c == 0 ? x0 : c == 1 ? x1 : c == 2 ? x2 : x3) + (int64_t)j * ldx;
-  const size_t o0 = (size_t)c * ldo * cols + (size_t)j * ldo;
-  const int64_t r0 = (int64_t)blockIdx.x * STAGE_ROWS;
-  const int64_t r1 = min(rows, r0 + STAGE_ROWS);
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    const float v = src[i];
-    if (mode == K_BF16) {
-      static_cast<__nv_bfloat16*>(out)[o0 + i] = __float2bfloat16_rn(v);
-    } else if (mode == K_TF32) {
-      static_cast<float*>(out)[o0 + i] = v;
-    } else {
-      const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-      static_cast<float*>(out)[o0 + i] = h;
-      static_cast<float*>(out_lo)[o0 + i] = v - h;
-    }
-  }
+template <int MODE>
+__global__ void __launch_bounds__(256) stage_x_kernel(const StageArg a) {
+  const int64_t k0 = (int64_t)blockIdx.x * STAGE_ROWS;
+  stage_row<MODE>(a, (int)blockIdx.y, k0, min(a.rows, k0 + STAGE_ROWS), threadIdx.x, blockDim.x);
+}
+
+// Staged X bytes of one problem (hi set; the 3xTF32 lo set is as large again).
+size_t staged_x_bytes(bool fd, int apl, int64_t ldo, int l, int nb, int ncb, size_t esz) {
+  return fd ? (size_t)apl * ncb * 4 * nb * ldo * esz : (size_t)4 * l * ldo * esz;
+}
+
+uint32_t neg_table(int op) {
+  // op N: negative for (c,d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)}; op H flips every c != 0
+  uint32_t neg = 0;
+  const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
+  for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
+  if (op == QLR_OP_H) neg ^= 0xFFF0u;
+  return neg;
 }
 
 int kind_of(int compute) {
@@ -924,6 +987,7 @@ int kind_of(int compute) {
 
 struct Plan {
   int kind, amode, sw, bk, esz, nb, ncb, mtiles, kiters, stages, apl;
+  bool fd;                       // fused output planes (N = 4 nb per MMA; column blocks <= 64)
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
   int flush, nbuf, ttotal;       // accumulation chunks (stages per chunk, TMEM buffers, TMEM sum)
   bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
@@ -943,7 +1007,8 @@ struct Plan {
 constexpr int X3_FLUSH_STAGES = 32;
 constexpr int X3_MAX_NB = 128;
 
-Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true, int apl = 4) {
+Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true, int apl = 4,
+               bool allow_fd = true) {
   Plan pl{};
   pl.apl = apl;
   pl.kind = kind_of(compute);
@@ -953,7 +1018,18 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   const int max_nb = (pl.kind == K_TF32X3) ? X3_MAX_NB : 128;
   pl.ncb = (lp + max_nb - 1) / max_nb;
   pl.nb = ((lp + pl.ncb - 1) / pl.ncb + 15) / 16 * 16;
+  // fused output planes when one MMA of N = 4 nb fits (nb <= 64): a quarter of the MMAs, but a
+  // fused X set (4 - c0) times larger; kept only while the ring still holds 3 stages (with two, the
+  // transposed-A form lost more to exposed loads than it gained: 1.16 against 0.87 ms at
+  // 20000 x 10000 x 60, TF32 op H)
+  const bool x3 = pl.kind == K_TF32X3;
+  const size_t budget = (size_t)227 * 1024 - 1024 - 256;
+  const int sw0 = x3 ? 32 : 64;
+  const size_t aset = (size_t)apl * TBM * sw0 * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0));
+  pl.fd = allow_fd && pl.nb <= 64 && budget / (aset + (size_t)apl * 4 * pl.nb * sw0 * (x3 ? 2 : 1)) >= 3;
   pl.wide = allow_wide && (pl.amode == A_K) && (pl.kind != K_TF32X3) && (pl.nb <= 64);
+  if (pl.wide && pl.fd)   // 128-byte rows double the stage: only with 2+ stages
+    pl.wide = budget / (2 * (aset + (size_t)apl * 4 * pl.nb * sw0)) >= 2;
   pl.sw = pl.kind == K_TF32X3 ? 32 : (pl.wide ? 128 : 64);
   pl.bk = pl.sw / pl.esz;
   pl.mtiles = (int)((M + TBM - 1) / TBM);
@@ -974,10 +1050,8 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   pl.nbuf = (pl.flush > 0 && !pl.ttotal && 8 * pl.nb <= 512) ? 2 : 1;
   const int cols = (pl.ttotal ? 2 : pl.nbuf) * 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
-  const bool x3 = pl.kind == K_TF32X3;
   const size_t stage = (size_t)apl * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
-                       (size_t)4 * pl.nb * pl.sw * (x3 ? 2 : 1);
-  const size_t budget = (size_t)227 * 1024 - 1024 - 256;
+                       (size_t)(pl.fd ? apl : 1) * 4 * pl.nb * pl.sw * (x3 ? 2 : 1);
   pl.stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
   pl.smem = pl.stages * stage + 1024 + 256;
   return pl;
@@ -1083,8 +1157,12 @@ size_t sketch_tc_grouped_bytes(int op, int count, const qlr_qmat* A, const qlr_q
   size_t items = 0;
   for (int i = 0; i < count; ++i) {
     const GDims g = gdims(op, A[i], X[i], base, 64);   // the narrowest column blocks: the most items
+    const GDims g2 = gdims(op, A[i], X[i], base, 128);
     items += (size_t)g.mtiles * g.ncb;
-    b += align256((size_t)4 * g.ldo * g.l * xesz) * (base.kind == K_TF32X3 ? 2 : 1);
+    const size_t xb = std::max({staged_x_bytes(false, 4, g.ldo, g.l, g.nb, g.ncb, xesz),
+                                staged_x_bytes(true, 4, g.ldo, g.l, g.nb, g.ncb, xesz),
+                                staged_x_bytes(true, 4, g2.ldo, g2.l, g2.nb, g2.ncb, xesz)});
+    b += align256(xb) * (base.kind == K_TF32X3 ? 2 : 1);
   }
   return b + align256(items * sizeof(int4)) + 4096;
 }
@@ -1119,9 +1197,16 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   bool all_pure = true;
   for (int i = 0; i < count; ++i) all_pure = all_pure && (A[i].plane[0] == nullptr);
   const int apl = all_pure ? 3 : 4;
-  const size_t stage = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0)) +
-                       (size_t)4 * max_nb * base.sw * (x3 ? 2 : 1);
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
+  const size_t aset = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0));
+  auto xset = [&](bool f) { return (size_t)(f ? apl : 1) * 4 * max_nb * base.sw * (x3 ? 2 : 1); };
+  // fused output planes for every problem when N = 4 nb <= 256 and the ring keeps 3 stages; with
+  // 128-byte rows that leave fewer than 2 stages, 64-byte rows instead
+  bool fd = max_nb <= 64 && budget / (aset + xset(true)) >= 3;
+  if (base.sw == 128 && budget / (aset + xset(fd)) < 2) {
+    return sketch_tc_grouped_plan(ctx, op, count, A, X, Y, compute, variant & ~4, dev, bytes, gs);
+  }
+  const size_t stage = aset + xset(fd);
   const int stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
   if (stages < 2) return QLR_EUNSUPPORTED;
   const size_t pstage = stage;
@@ -1145,10 +1230,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   const CUtensorMapDataType dt = (base.kind == K_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const CUtensorMapSwizzle sw = (base.sw == 32) ? CU_TENSOR_MAP_SWIZZLE_32B
                                 : (base.sw == 64) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
-  uint32_t neg = 0;
-  const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
-  for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
-  if (op == QLR_OP_H) neg ^= 0xFFF0u;
+  const uint32_t neg = neg_table(op);
   const uint32_t fmt = (base.kind == K_BF16) ? 1u : 2u;
   int max_stage_blocks = 1;
   for (int i = 0; i < count; ++i) {
@@ -1156,11 +1238,13 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     const qlr_qmat& a = A[i];
     TcParams& prm = hp[i];
     memset(&prm, 0, sizeof(prm));
-    char* xs = take((size_t)4 * g.ldo * g.l * xesz);
-    char* xlo = x3 ? take((size_t)4 * g.ldo * g.l * 4) : nullptr;
+    const size_t xb = staged_x_bytes(fd, apl, g.ldo, g.l, g.nb, g.ncb, xesz);
+    char* xs = take(xb);
+    char* xlo = x3 ? take(xb) : nullptr;
     if ((size_t)(cur - dev) > bytes) return QLR_ENOMEM;
     prm.c_first = (a.plane[0] == nullptr) ? 1 : 0;
     prm.apl = apl;
+    prm.fd = fd ? 1 : 0;
     for (int c = prm.c_first; c < 4; ++c) {
       bool ok;
       if (op == QLR_OP_N)
@@ -1174,13 +1258,26 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
                        (uint32_t)base.bk, CU_TENSOR_MAP_SWIZZLE_NONE);
       if (!ok) return QLR_ECUDA;
     }
-    for (int q = 0; q < 4; ++q) {
-      if (!encode_2d(&prm.tmX[q], xs + (size_t)q * g.ldo * g.l * xesz, dt, (uint64_t)g.K, (uint64_t)g.l,
-                     (uint64_t)g.ldo * xesz, (uint32_t)base.bk, (uint32_t)g.nb, sw))
-        return QLR_ECUDA;
-      if (xlo && !encode_2d(&prm.tmXlo[q], xlo + (size_t)q * g.ldo * g.l * 4, dt, (uint64_t)g.K, (uint64_t)g.l,
-                            (uint64_t)g.ldo * 4, (uint32_t)base.bk, (uint32_t)g.nb, sw))
-        return QLR_ECUDA;
+    if (fd) {   // X~_c of input plane c >= c0: ncb 4 nb rows, boxes of 4 nb rows
+      const int64_t fr = (int64_t)g.ncb * 4 * g.nb;
+      for (int c = 4 - apl; c < 4; ++c) {
+        const size_t off = (size_t)(c - (4 - apl)) * fr * g.ldo;
+        if (!encode_2d(&prm.tmX[c], xs + off * xesz, dt, (uint64_t)g.K, (uint64_t)fr, (uint64_t)g.ldo * xesz,
+                       (uint32_t)base.bk, (uint32_t)(4 * g.nb), sw))
+          return QLR_ECUDA;
+        if (xlo && !encode_2d(&prm.tmXlo[c], xlo + off * 4, dt, (uint64_t)g.K, (uint64_t)fr, (uint64_t)g.ldo * 4,
+                              (uint32_t)base.bk, (uint32_t)(4 * g.nb), sw))
+          return QLR_ECUDA;
+      }
+    } else {
+      for (int q = 0; q < 4; ++q) {
+        if (!encode_2d(&prm.tmX[q], xs + (size_t)q * g.ldo * g.l * xesz, dt, (uint64_t)g.K, (uint64_t)g.l,
+                       (uint64_t)g.ldo * xesz, (uint32_t)base.bk, (uint32_t)g.nb, sw))
+          return QLR_ECUDA;
+        if (xlo && !encode_2d(&prm.tmXlo[q], xlo + (size_t)q * g.ldo * g.l * 4, dt, (uint64_t)g.K, (uint64_t)g.l,
+                              (uint64_t)g.ldo * 4, (uint32_t)base.bk, (uint32_t)g.nb, sw))
+          return QLR_ECUDA;
+      }
     }
     for (int c = 0; c < 4; ++c) prm.y[c] = static_cast<float*>(Y[i].plane[c]);
     prm.ldy = Y[i].ld;
@@ -1192,7 +1289,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     prm.mtiles = g.mtiles;
     prm.neg_mask = neg;
     prm.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((base.amode == A_MN ? 1u : 0u) << 15) |
-                     ((uint32_t)(g.nb >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+                     ((uint32_t)((fd ? 4 * g.nb : g.nb) >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
     prm.tmem_cols = tmem_cols;
     prm.stages = stages;
     prm.err = ctx->d_err;
@@ -1204,7 +1301,13 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
     sa.ldo = g.ldo;
     sa.out = xs;
     sa.out_lo = xlo;
-    max_stage_blocks = std::max<int>(max_stage_blocks, std::min<int>(g.l, 128));   // one CTA per column
+    sa.fd = fd ? 1 : 0;
+    sa.nb = g.nb;
+    sa.ncb = g.ncb;
+    sa.c0 = 4 - apl;
+    sa.neg = neg;
+    sa.nrows = fd ? apl * g.ncb * 4 * g.nb : 4 * g.l;
+    max_stage_blocks = std::max<int>(max_stage_blocks, std::min<int>((sa.nrows + 7) / 8, 64));   // 8 rows per CTA
     for (int mt = 0; mt < g.mtiles; ++mt)
       for (int cb = 0; cb < g.ncb; ++cb) hi.push_back(make_int4(i, mt, cb, 0));
   }
@@ -1226,6 +1329,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   gs.nb_max = max_nb;
   gs.stages = gs.persistent ? pstages : stages;
   gs.apl = apl;
+  gs.fd = fd ? 1 : 0;
   {   // two accumulators of the widest block when they fit in fewer columns, else all 512
     const int pc = 2 * 4 * max_nb;
     gs.tmem_cols = pc <= 32 ? 32 : pc <= 64 ? 64 : pc <= 128 ? 128 : pc <= 256 ? 256 : 512;
@@ -1249,7 +1353,7 @@ int launch_grouped(qlr_ctx* ctx, const GroupedSketch& gs) {
     QLR_CUDA_TRY(cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs.smem));
     KTimer kt(ctx, QLR_KID_SKETCH_TC);
     pk<<<(unsigned)gs.grid, TC_THREADS, gs.smem, ctx->stream>>>(static_cast<const TcParams*>(gs.d_probs), gs.d_items,
-                                                               gs.nitems, gs.nb_max, gs.stages, gs.apl, gs.tmem_cols,
+                                                               gs.nitems, gs.nb_max, gs.stages, gs.apl, gs.fd, gs.tmem_cols,
                                                                ctx->d_err);
     qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
@@ -1289,11 +1393,12 @@ size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
 }
 
 size_t sketch_tc_need(int op, int64_t M, int64_t K, int l, int compute, int num_sms) {
-  const Plan pl = make_plan(compute, op, M, K, l, num_sms);
+  const Plan pl = make_plan(compute, op, M, K, l, num_sms);   // a full quaternion A: the largest staging
   const int64_t ldo = (K + 7) / 8 * 8;
   const size_t xesz = (pl.kind == K_BF16) ? 2 : 4;
-  size_t b = align256((size_t)4 * ldo * l * xesz);
-  if (pl.kind == K_TF32X3) b += align256((size_t)4 * ldo * l * 4);
+  const size_t xb = staged_x_bytes(pl.fd, 4, ldo, l, pl.nb, pl.ncb, xesz);
+  size_t b = align256(xb);
+  if (pl.kind == K_TF32X3) b += align256(xb);
   if (pl.grid_sk > 0) b += align256((size_t)2 * pl.grid_sk * 4 * TBM * pl.nb * sizeof(float));
   return b + align256((size_t)pl.mtiles * pl.ncb * sizeof(unsigned));
 }
@@ -1308,14 +1413,15 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   if (K == 0) return zero_qmat(ctx, Y);
   if (X.dtype != QLR_F32 && !(compute == QLR_COMPUTE_BF16 && X.dtype == QLR_BF16)) return QLR_EINVAL;
   const Plan pl = make_plan(compute, op, M, K, l, ctx->num_sms > 0 ? ctx->num_sms : 148, true,
-                            A.plane[0] == nullptr ? 3 : 4);
+                            A.plane[0] == nullptr ? 3 : 4, X.dtype == QLR_F32);
   if (pl.stages < 2) return QLR_EUNSUPPORTED;
   size_t mark = ws.off;
   // stage the thin operand with a 16-byte aligned column pitch
   const int64_t ldo = (K + 7) / 8 * 8;
   const size_t xesz = (pl.kind == K_BF16) ? 2 : 4;
-  void* xs = ws.take<char>((size_t)4 * ldo * l * xesz);
-  void* xlo = (pl.kind == K_TF32X3) ? ws.take<char>((size_t)4 * ldo * l * 4) : nullptr;
+  const size_t xb = staged_x_bytes(pl.fd, pl.apl, ldo, l, pl.nb, pl.ncb, xesz);
+  void* xs = ws.take<char>(xb);
+  void* xlo = (pl.kind == K_TF32X3) ? ws.take<char>(xb) : nullptr;
   const size_t tile_elems = (size_t)4 * TBM * pl.nb;
   float* part = pl.grid_sk > 0 ? ws.take<float>((size_t)2 * pl.grid_sk * tile_elems) : nullptr;
   unsigned* counters = ws.take<unsigned>((size_t)pl.mtiles * pl.ncb);
@@ -1326,12 +1432,26 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
     for (int c = 0; c < 4; ++c) dst.plane[c] = static_cast<char*>(xs) + (size_t)c * ldo * l * 2;
     QLR_TRY(convert_qmat(ctx, X, dst));
   } else {
-    if (l > 65535) return QLR_EUNSUPPORTED;
-    const dim3 grid((unsigned)((K + STAGE_ROWS - 1) / STAGE_ROWS), (unsigned)l, 4u);
+    StageArg sa{};
+    for (int c = 0; c < 4; ++c) sa.x[c] = static_cast<const float*>(X.plane[c]);
+    sa.ldx = X.ld;
+    sa.rows = K;
+    sa.cols = l;
+    sa.ldo = ldo;
+    sa.out = xs;
+    sa.out_lo = xlo;
+    sa.fd = pl.fd ? 1 : 0;
+    sa.nb = pl.nb;
+    sa.ncb = pl.ncb;
+    sa.c0 = 4 - pl.apl;
+    sa.neg = neg_table(op);
+    sa.nrows = pl.fd ? pl.apl * pl.ncb * 4 * pl.nb : 4 * l;
+    if (sa.nrows > 65535) return QLR_EUNSUPPORTED;
+    const dim3 grid((unsigned)((K + STAGE_ROWS - 1) / STAGE_ROWS), (unsigned)sa.nrows);
     KTimer kt(ctx, QLR_KID_MISC);
-    stage_x_kernel<<<grid, 256, 0, ctx->stream>>>(
-        static_cast<const float*>(X.plane[0]), static_cast<const float*>(X.plane[1]),
-        static_cast<const float*>(X.plane[2]), static_cast<const float*>(X.plane[3]), X.ld, K, l, pl.kind, xs, xlo, ldo);
+    if (pl.kind == K_BF16) stage_x_kernel<K_BF16><<<grid, 256, 0, ctx->stream>>>(sa);
+    else if (pl.kind == K_TF32) stage_x_kernel<K_TF32><<<grid, 256, 0, ctx->stream>>>(sa);
+    else stage_x_kernel<K_TF32X3><<<grid, 256, 0, ctx->stream>>>(sa);
     qlr_count_launch();
     QLR_CUDA_TRY(cudaGetLastError());
   }
@@ -1358,7 +1478,17 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
                      (uint32_t)pl.bk, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!ok) { ws.off = mark; return QLR_ECUDA; }
   }
-  for (int q = 0; q < 4; ++q) {
+  if (pl.fd) {   // X~_c of input plane c >= c_first: ncb 4 nb rows, boxes of 4 nb rows
+    const int64_t fr = (int64_t)pl.ncb * 4 * pl.nb;
+    for (int c = 4 - pl.apl; c < 4; ++c) {
+      const size_t off = (size_t)(c - (4 - pl.apl)) * fr * ldo;
+      if (!encode_2d(&prm.tmX[c], static_cast<const char*>(xs) + off * xesz, dt, (uint64_t)K, (uint64_t)fr,
+                     (uint64_t)ldo * xesz, (uint32_t)pl.bk, (uint32_t)(4 * pl.nb), sw)) { ws.off = mark; return QLR_ECUDA; }
+      if (xlo && !encode_2d(&prm.tmXlo[c], static_cast<const char*>(xlo) + off * 4, dt, (uint64_t)K, (uint64_t)fr,
+                            (uint64_t)ldo * 4, (uint32_t)pl.bk, (uint32_t)(4 * pl.nb), sw)) { ws.off = mark; return QLR_ECUDA; }
+    }
+  }
+  for (int q = 0; q < 4 && !pl.fd; ++q) {
     const char* base = static_cast<const char*>(xs) + (size_t)q * ldo * l * xesz;
     if (!encode_2d(&prm.tmX[q], base, dt, (uint64_t)K, (uint64_t)l, (uint64_t)ldo * xesz, (uint32_t)pl.bk,
                    (uint32_t)pl.nb, sw)) { ws.off = mark; return QLR_ECUDA; }
@@ -1378,15 +1508,11 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.ncb = pl.ncb;
   prm.kiters = pl.kiters;
   prm.mtiles = pl.mtiles;
-  // sign table: op N: negative for (c,d) in {(1,0),(2,0),(3,0),(1,2),(2,3),(3,1)}; op H flips c != 0
-  uint32_t neg = 0;
-  const int negN[6][2] = {{1, 0}, {2, 0}, {3, 0}, {1, 2}, {2, 3}, {3, 1}};
-  for (auto& e : negN) neg |= 1u << (e[0] * 4 + e[1]);
-  if (op == QLR_OP_H) neg ^= 0xFFF0u;   // flip every (c != 0, d) entry
-  prm.neg_mask = neg;
+  prm.neg_mask = neg_table(op);
+  prm.fd = pl.fd ? 1 : 0;
   const uint32_t fmt = (pl.kind == K_BF16) ? 1u : 2u;
   prm.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((pl.amode == A_MN ? 1u : 0u) << 15) |
-                   ((uint32_t)(pl.nb >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+                   ((uint32_t)((pl.fd ? 4 * pl.nb : pl.nb) >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
   prm.tmem_cols = pl.tmem_cols;
   prm.stages = pl.stages;
   prm.err = ctx->d_err;
