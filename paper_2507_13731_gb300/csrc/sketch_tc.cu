@@ -1027,6 +1027,17 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   const int sw0 = x3 ? 32 : 64;
   const size_t aset = (size_t)apl * TBM * sw0 * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0));
   pl.fd = allow_fd && pl.nb <= 64 && budget / (aset + (size_t)apl * 4 * pl.nb * sw0 * (x3 ? 2 : 1)) >= 3;
+  if (allow_fd && !pl.fd && x3 && pl.amode == A_K && pl.ncb >= 2) {
+    // 3xTF32 over several column blocks anyway: fused planes in blocks of <= 64 (one more read of
+    // A, but a quarter of the MMAs and the chunk sums kept in TMEM): 5.27 against 6.02 ms at
+    // 20000 x 10000 x 180, op N
+    const int ncb = (lp + 63) / 64, nb = ((lp + ncb - 1) / ncb + 15) / 16 * 16;
+    if (budget / (aset + (size_t)apl * 4 * nb * sw0 * 2) >= 3) {
+      pl.ncb = ncb;
+      pl.nb = nb;
+      pl.fd = true;
+    }
+  }
   pl.wide = allow_wide && (pl.amode == A_K) && (pl.kind != K_TF32X3) && (pl.nb <= 64);
   if (pl.wide && pl.fd)   // 128-byte rows double the stage: only with 2+ stages
     pl.wide = budget / (2 * (aset + (size_t)apl * 4 * pl.nb * sw0)) >= 2;
@@ -1389,7 +1400,10 @@ int sketch_tc_grouped_run(qlr_ctx* ctx, const GroupedSketch& gs) {
 
 size_t sketch_tc_ws(int64_t rows_in, int64_t l, int num_sms) {
   const int64_t ldo = (rows_in + 7) / 8 * 8;
-  return (size_t)2 * 4 * ldo * l * 4 + (size_t)2 * (num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
+  // staged X (hi and lo sets, 4-byte elements): 4 planes of l rows, or per input plane the fused
+  // rows (4 nb per column block, at most 4 (l + 64) in all)
+  const int64_t rows = std::max<int64_t>(l, 4 * (l + 64));
+  return (size_t)2 * 4 * ldo * rows * 4 + (size_t)2 * (num_sms + 8) * 4 * TBM * 128 * 4 + 65536 + 4096;
 }
 
 size_t sketch_tc_need(int op, int64_t M, int64_t K, int l, int compute, int num_sms) {
