@@ -252,7 +252,8 @@ def peaks_leg(dev):
     d = dev.index or 0
     out = {}
     for name, kind in (("tf32_mma", qlr.PEAK_TF32_MMA), ("bf16_mma", qlr.PEAK_BF16_MMA),
-                       ("fp32_fma", qlr.PEAK_FP32_FMA), ("fp64_fma", qlr.PEAK_FP64_FMA)):
+                       ("fp32_fma", qlr.PEAK_FP32_FMA), ("fp64_fma", qlr.PEAK_FP64_FMA),
+                       ("tf32_mma_n64", qlr.PEAK_TF32_MMA_N64), ("bf16_mma_n64", qlr.PEAK_BF16_MMA_N64)):
         try:
             out[name] = round(qlr.measure_peak(kind, d), 2)
         except Exception as e:                     # reported, never fatal to the headline line
@@ -260,8 +261,9 @@ def peaks_leg(dev):
             out[name + "_error"] = f"{type(e).__name__}: {e}"
     _MEASURED.update({k: v for k, v in out.items() if isinstance(v, float)})
     out["unit"] = "TFLOP/s"
-    out["how"] = ("tcgen05 MMA loop, M=128 N=256 (K=8 tf32 / 16 bf16) from shared memory, one CTA per SM; "
-                  "FMA loops, 8 independent chains per thread, 8 CTAs of 256 threads per SM; best of 3 ~40 ms launches")
+    out["how"] = ("tcgen05 MMA loop, M=128 N=256 (K=8 tf32 / 16 bf16) from shared memory, one CTA per SM (the _n64 "
+                  "entries: the same loop with N=64); FMA loops, 8 independent chains per thread, 8 CTAs of 256 threads "
+                  "per SM; best of 3 ~40 ms launches")
     return out
 
 

@@ -153,13 +153,17 @@ int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
  *     (M = 128, N = 256, K = 8 kind::tf32 / K = 16 kind::f16 with BF16 operands) on operands
  *     staged once in shared memory; iters <= 400000 (the kernel's bounded wait must not expire);
  *   QLR_PEAK_FP32_FMA / QLR_PEAK_FP64_FMA: 8 CTAs of 256 threads per SM, each thread `iters`
- *     rounds of 8 independent fused multiply-adds.
+ *     rounds of 8 independent fused multiply-adds;
+ *   QLR_PEAK_TF32_MMA_N64 / QLR_PEAK_BF16_MMA_N64: the MMA loops with N = 64 (the width of a thin
+ *     sketch's MMAs; an MMA of M = 128 takes about as long for N = 64 as for N ~ 100).
  * Dense peak = flops / ms.  Errors: QLR_EINVAL (kind, iters, null outputs), QLR_ECUDA,
  * QLR_ETIMEOUT (the MMA probe's bounded wait gave up). */
 #define QLR_PEAK_TF32_MMA 0
 #define QLR_PEAK_BF16_MMA 1
 #define QLR_PEAK_FP32_FMA 2
 #define QLR_PEAK_FP64_FMA 3
+#define QLR_PEAK_TF32_MMA_N64 4   /* the MMA loops with N = 64 (thin sketches' MMA width) */
+#define QLR_PEAK_BF16_MMA_N64 5
 int qlr_peak_probe(int kind, int device, int64_t iters, double* flops, float* ms);
 
 /* ---- the Gaussian test matrix from a seed (Def. 2) ---------------------------------------

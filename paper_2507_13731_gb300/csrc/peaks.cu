@@ -20,8 +20,10 @@ constexpr int PM = 128, PN = 256;
 constexpr int MMAS_PER_ROUND = 8;
 
 // KIND 0: kind::tf32 (K = 8 per MMA); KIND 1: kind::f16 with BF16 operands (K = 16 per MMA).
-// Both operands use 32-byte rows (one K step), the 32-byte swizzled K-major layout.
-template <int KIND>
+// Both operands use 32-byte rows (one K step), the 32-byte swizzled K-major layout.  N = PN
+// (256: the dense rate) or 64 (the rate of the narrow MMAs of thin sketches: an MMA of M = 128
+// takes about the same time for every N up to ~100).
+template <int KIND, int NN = PN>
 __global__ void __launch_bounds__(128, 1) mma_peak_kernel(int64_t rounds, int* err, float* sink) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(128, 1) mma_peak_kernel(int64_t rounds, int* e
     const uint64_t ad = make_desc(smem_u32(a), 16, 8 * 32, 6);
     const uint64_t bd = make_desc(smem_u32(b), 16, 8 * 32, 6);
     const uint32_t fmt = (KIND == 0) ? 2u : 1u;
-    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(PN >> 3) << 17) | ((uint32_t)(PM >> 4) << 24);
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(PM >> 4) << 24);
     for (int64_t r = 0; r < rounds; ++r) {
 #pragma unroll
       for (int j = 0; j < MMAS_PER_ROUND; ++j) {
@@ -104,8 +106,10 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int64_t iters, T x, T y, 
 }  // namespace
 
 extern "C" int qlr_peak_probe(int kind, int device, int64_t iters, double* flops, float* ms) {
-  if (!flops || !ms || iters < 1 || kind < QLR_PEAK_TF32_MMA || kind > QLR_PEAK_FP64_FMA) return QLR_EINVAL;
-  if ((kind == QLR_PEAK_TF32_MMA || kind == QLR_PEAK_BF16_MMA) && iters > 400000) return QLR_EINVAL;
+  if (!flops || !ms || iters < 1 || kind < QLR_PEAK_TF32_MMA || kind > QLR_PEAK_BF16_MMA_N64) return QLR_EINVAL;
+  const bool mma = kind == QLR_PEAK_TF32_MMA || kind == QLR_PEAK_BF16_MMA || kind == QLR_PEAK_TF32_MMA_N64 ||
+                   kind == QLR_PEAK_BF16_MMA_N64;
+  if (mma && iters > 400000) return QLR_EINVAL;
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); return QLR_ECUDA; }
   if (prev != device && cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return QLR_ECUDA; }
@@ -127,16 +131,18 @@ extern "C" int qlr_peak_probe(int kind, int device, int64_t iters, double* flops
     char* sink = static_cast<char*>(scratch) + 256;
     double f = 0.0;
     cudaEventRecord(e0, st);
-    if (kind == QLR_PEAK_TF32_MMA || kind == QLR_PEAK_BF16_MMA) {
+    if (mma) {
       const size_t smem = (size_t)(PM + PN) * 32 + 64 + 1024;
-      auto kern = (kind == QLR_PEAK_TF32_MMA) ? mma_peak_kernel<0> : mma_peak_kernel<1>;
+      const bool tf32 = kind == QLR_PEAK_TF32_MMA || kind == QLR_PEAK_TF32_MMA_N64;
+      const bool n64 = kind == QLR_PEAK_TF32_MMA_N64 || kind == QLR_PEAK_BF16_MMA_N64;
+      auto kern = tf32 ? (n64 ? mma_peak_kernel<0, 64> : mma_peak_kernel<0>) : (n64 ? mma_peak_kernel<1, 64> : mma_peak_kernel<1>);
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         rc = QLR_ECUDA;
         break;
       }
       kern<<<sms, 128, smem, st>>>(iters, err, reinterpret_cast<float*>(sink));
-      const double k = (kind == QLR_PEAK_TF32_MMA) ? 8.0 : 16.0;
-      f = (double)sms * (double)iters * MMAS_PER_ROUND * 2.0 * PM * PN * k;
+      const double k = tf32 ? 8.0 : 16.0;
+      f = (double)sms * (double)iters * MMAS_PER_ROUND * 2.0 * PM * (n64 ? 64 : PN) * k;
     } else {
       const int blocks = sms * 8;
       if (kind == QLR_PEAK_FP32_FMA)

@@ -32,7 +32,7 @@ SIDE_AUTO, SIDE_X, SIDE_XH = -1, 0, 1
 ORTH_CHOLQR2, ORTH_SCHOLQR3 = 0, 1
 FLAG_QR_EVERY_PASS = 1
 FLAG_NO_GRAPH = 2
-PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_FP32_FMA, PEAK_FP64_FMA = range(4)
+PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_N64, PEAK_BF16_MMA_N64 = range(6)
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series",
@@ -465,8 +465,9 @@ def peak_probe(kind: int, device: int = 0, iters: int = 1000):
 def measure_peak(kind: int, device: int = 0, target_ms: float = 40.0, reps: int = 3) -> float:
     """Dense peak in TFLOP/s of one probe: calibrate the iteration count on a short run so one
     launch takes about target_ms, then the best of `reps` launches."""
-    cap = 400000 if kind in (PEAK_TF32_MMA, PEAK_BF16_MMA) else 1 << 40
-    iters = 2000 if kind in (PEAK_TF32_MMA, PEAK_BF16_MMA) else 20000
+    mma = kind in (PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_TF32_MMA_N64, PEAK_BF16_MMA_N64)
+    cap = 400000 if mma else 1 << 40
+    iters = 2000 if mma else 20000
     f, ms = peak_probe(kind, device, iters)
     iters = int(min(cap, max(1, iters * target_ms / max(ms, 1e-3))))
     best = 0.0
