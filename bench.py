@@ -659,7 +659,9 @@ def profile_driver(args):
     Y = qlr.empty_thin(m if op == qlr.OP_N else n, ell)
 
     def call():
-        if args.only == "sketch":
+        if args.only == "sketch" and args.noalloc:
+            qlr.qsketch_noalloc(op, A, X, Y, compute)
+        elif args.only == "sketch":
             qlr.qsketch(ctx, op, A, X, Y, compute)
         else:
             qlr.qsvd_lowrank(ctx, A, P.k, P.p, v, om, U, S, V, algo=algo, compute=compute, side=qlr.SIDE_X)
@@ -684,7 +686,8 @@ def profile_driver(args):
     rc = rc or ctx.sync()
     classes = {k: [round(nl / args.steps, 1), round(t / args.steps, 4)] for k, (nl, t) in st.items() if nl}
     print(json.dumps({"only": args.only, "config": args.config, "op": args.op, "ell": ell, "passes": v,
-                      "compute": args.compute, "ms_per_call": ms, "classes_launches_ms": classes,
+                      "compute": args.compute, "noalloc": bool(args.noalloc), "ms_per_call": ms,
+                      "classes_launches_ms": classes,
                       "device_error": rc}), flush=True)
     ctx.close()
     return 0 if rc == 0 else 1
@@ -796,6 +799,8 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="profiling driver: rows of a uniform pure A (with --n)")
     ap.add_argument("--n", type=int, default=0, help="profiling driver: columns of a uniform pure A (with --m)")
     ap.add_argument("--passes", type=int, default=4)
+    ap.add_argument("--noalloc", action="store_true",
+                    help="profiling driver, --only sketch: time the allocation-free entry point instead")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.compute == "TF32_MIXED":

@@ -412,8 +412,9 @@ int qlr_selftest_wait_timeout(qlr_ctx* ctx);
  * create a qlr context (which allocates its error word and workspace).
  * No context: the call runs on `stream` (a cudaStream_t, NULL = legacy default stream) on that
  * stream's device (made current for the call, the caller's current device restored on return) and
- * takes all scratch memory from one fixed 32 MiB device array compiled into the library (every GPU
- * that loads it keeps those 32 MiB until the process exits).  It calls no cudaMalloc / cudaFree.
+ * takes all scratch memory from one fixed 128 MiB device array compiled into the library (every GPU
+ * that loads it keeps those 128 MiB until the process exits; the size leaves room for the staged
+ * operand and the stream-K partial tiles of every SM at l up to ~128 and K up to ~20000).  It calls no cudaMalloc / cudaFree.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress, with the
  * device current) and keeps it for the life of the process, so make the first call on each device
  * before any stream capture, and do not call this entry point on a device after a cudaDeviceReset
@@ -425,7 +426,7 @@ int qlr_selftest_wait_timeout(qlr_ctx* ctx);
  * QLR_ETIMEOUT if a bounded device wait gives up.
  * Degenerate sizes as qlr_qsketch: an empty Y launches nothing; an empty inner dimension writes Y = 0.
  * Errors: QLR_EINVAL / QLR_ESHAPE as qlr_qsketch; QLR_EUNSUPPORTED for a row pitch of A that is not
- * a multiple of 16 bytes; QLR_ENOMEM when the operands need more scratch than the 32 MiB array
+ * a multiple of 16 bytes; QLR_ENOMEM when the operands need more scratch than the 128 MiB array
  * (the staged thin operand alone needs 32 bytes per quaternion entry of X for TF32X3, 8 for BF16).
  */
 int qlr_qsketch_noalloc(void* stream, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_qmat* Y, int compute,

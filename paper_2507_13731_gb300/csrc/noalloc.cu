@@ -15,7 +15,7 @@
 
 #include "qlr_internal.h"
 
-#define QLR_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define QLR_NOALLOC_SCRATCH_BYTES (128u << 20)
 #define QLR_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) unsigned char g_qlr_noalloc_scratch[QLR_NOALLOC_SCRATCH_BYTES];

@@ -101,7 +101,7 @@ def test_noalloc_degenerate_sizes():
 def test_noalloc_rejects_oversized_operands():
     from paper_2507_13731_gb300 import build, qlr
     build.build()
-    A = torch.zeros(4, 64, 200000, device="cuda")        # staged X would need > 32 MiB
+    A = torch.zeros(4, 64, 200000, device="cuda")        # staged X would need > 128 MiB
     X = qlr.empty_thin(200000, 64)
     Y = qlr.empty_thin(64, 64)
     with pytest.raises(qlr.QlrError) as e:
