@@ -34,7 +34,9 @@ def _tol(mode, K):
 
 SHAPES = [(256, 192, 15, False), (300, 264, 37, False), (129, 1000, 5, False), (1000, 128, 112, False),
           (77, 40, 128, True), (200, 120, 220, False), (513, 1024, 64, False), (16, 8, 1, False),
-          (640, 2048, 110, True)]
+          (640, 2048, 110, True),
+          # pure, l = 180: 3xTF32 op N runs the fused output planes over three 64-column blocks
+          (300, 504, 180, True)]
 
 
 @pytest.mark.parametrize("m,n,l,pure", SHAPES)
