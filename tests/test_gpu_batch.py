@@ -147,3 +147,28 @@ def test_batch_plan_rejects_unaligned_pitch(ctx):
     for i, P in enumerate(probs):
         ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, 3, P.Omega)
         np.testing.assert_allclose(Ss[i].cpu().numpy(), ref.S, rtol=2e-2)
+
+
+@pytest.mark.parametrize("variant", [2, 10, 15])
+def test_batch_mixed_pure_and_full_quaternion(ctx, monkeypatch, variant):
+    """A batch whose problems are partly full quaternion (a real plane present): the grouped
+    sketch then stages all four A planes for every problem, in the plain and the fused-plane
+    forms (variants 10 and 15: column blocks <= 64, one MMA per input plane); sigma against the
+    oracle on the same matrices."""
+    from paper_2507_13731_gb300 import qlr
+    monkeypatch.setenv("QLR_BATCH_VARIANT", str(variant))
+    probs = synth.batched_problems(count=40, seed=47, mmax=700, nmax=500, rmax=40)
+    rng = np.random.default_rng(7)
+    for i, P in enumerate(probs):
+        if i % 2 == 0:   # a real plane at the noise level: the problem is no longer pure
+            P.A[0] = 1e-3 * rng.standard_normal(P.A[0].shape)
+            P.pure = False
+    As, Os, Us, Vs, Ss = _buffers(probs, torch.bfloat16)
+    b = qlr.Batch(ctx, As, [P.k for P in probs], [P.p for P in probs], 3, Os, Us, Ss, Vs, graph=False)
+    assert ctx.sync() == 0 and b.info()["tile_order"] == variant
+    for i in (0, 1, 20, 39):
+        P = probs[i]
+        ref = al.alg2_arbitrary_pass(P.A, P.k, P.p, 3, P.Omega)
+        np.testing.assert_allclose(Ss[i].cpu().numpy(), ref.S, rtol=2e-2, err_msg=f"problem {i}")
+        assert _orth_err(Us[i]) < 1e-4 and _orth_err(Vs[i]) < 1e-4
+    b.close()
