@@ -266,7 +266,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   // A sets [raw][hi][lo] of APL planes each: plane c at slot c - (4 - APL) (APL = 3 for a pure
   // quaternion A, whose plane 0 is absent)
   const int APL = pv.apl, C0 = 4 - APL;
-  const int A_SET = APL * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
+  const int A_SET = APL * A_BYTES * (X3 ? 2 : 1);   // [hi][lo]; a transposed A lands raw in [hi]
   const int NXP = FD ? APL : 4;                          // X tiles per set (per input plane when fused)
   const int stage_bytes = A_SET + NXP * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
@@ -294,8 +294,8 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   const int it1 = sg.it1;
   const int nit = it1 - it0;
 
-  const int HI_OFF = TR ? APL * A_BYTES : 0;
-  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - C0) * A_BYTES; };
+  const int HI_OFF = 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - C0) * A_BYTES; };   // = a_plane
   auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - C0) * A_BYTES; };
   auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (APL + c - C0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
@@ -412,16 +412,25 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
           uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
           if (TR) {
             // raw[k][r] (k < BK, r < 128) -> row r of the K-major tile, 16-byte chunk cch holding
-            // k = 4 cch .. 4 cch + 3, stored at chunk position cch ^ swizzle(r)
+            // k = 4 cch .. 4 cch + 3, stored at chunk position cch ^ swizzle(r).  In place: the
+            // workers read the whole raw plane into registers, meet at a named barrier, then write.
             const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_plane(s, c));
-            for (int e = st; e < TBM * CH; e += 64) {
-              const int r = e % TBM, cch = e / TBM;
+            constexpr int NPER = TBM * CH / 64;
+            uint4 vv[NPER];
+#pragma unroll
+            for (int q = 0; q < NPER; ++q) {
+              const int e = st + 64 * q, r = e % TBM, cch = e / TBM;
+              vv[q].x = raw[(4 * cch + 0) * TBM + r];
+              vv[q].y = raw[(4 * cch + 1) * TBM + r];
+              vv[q].z = raw[(4 * cch + 2) * TBM + r];
+              vv[q].w = raw[(4 * cch + 3) * TBM + r];
+            }
+            asm volatile("bar.sync 2, 64;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < NPER; ++q) {
+              const int e = st + 64 * q, r = e % TBM, cch = e / TBM;
               const int sw = (CH == 2) ? ((r >> 2) & 1) : (CH == 4) ? ((r >> 1) & 3) : (r & 7);
-              uint4 v;
-              v.x = raw[(4 * cch + 0) * TBM + r];
-              v.y = raw[(4 * cch + 1) * TBM + r];
-              v.z = raw[(4 * cch + 2) * TBM + r];
-              v.w = raw[(4 * cch + 3) * TBM + r];
+              const uint4 v = vv[q];
               const int o = r * CH + (cch ^ sw);
               if (X3) {
                 uint4 h, rr;
@@ -659,7 +668,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // apl A planes per set: 3 when every problem is pure quaternion (plane 0 absent), else 4; plane
   // c is stored at slot c - (4 - apl)
   const int c0 = 4 - apl;
-  const int A_SET = apl * A_BYTES * ((X3 ? 2 : 1) + (TR ? 1 : 0));
+  const int A_SET = apl * A_BYTES * (X3 ? 2 : 1);   // [hi][lo]; a transposed A lands raw in [hi]
   const int NXP = fd ? apl : 4;
   const int stage_bytes = A_SET + NXP * X_BYTES * (X3 ? 2 : 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * stage_bytes);
@@ -673,8 +682,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int my_items = (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int HI_OFF = TR ? apl * A_BYTES : 0;
-  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - c0) * A_BYTES; };
+  const int HI_OFF = 0;
+  auto raw_plane = [&](int s, int c) { return smem + s * stage_bytes + (c - c0) * A_BYTES; };   // = a_plane
   auto a_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (c - c0) * A_BYTES; };
   auto alo_plane = [&](int s, int c) { return smem + s * stage_bytes + HI_OFF + (apl + c - c0) * A_BYTES; };
   auto x_plane = [&](int s, int q) { return smem + s * stage_bytes + A_SET + q * X_BYTES; };
@@ -815,16 +824,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int c = pv.c_first; c < 4; ++c) {
             uint4* hi = reinterpret_cast<uint4*>(a_plane(s, c));
             uint4* lo = reinterpret_cast<uint4*>(alo_plane(s, c));
-            if (TR) {
+            if (TR) {   // in place, as in sketch_tile
               const uint32_t* raw = reinterpret_cast<const uint32_t*>(raw_plane(s, c));
-              for (int e = st; e < TBM * CH; e += 64) {
-                const int r = e % TBM, cch = e / TBM;
+              constexpr int NPER = TBM * CH / 64;
+              uint4 vv[NPER];
+#pragma unroll
+              for (int q = 0; q < NPER; ++q) {
+                const int e = st + 64 * q, r = e % TBM, cch = e / TBM;
+                vv[q].x = raw[(4 * cch + 0) * TBM + r];
+                vv[q].y = raw[(4 * cch + 1) * TBM + r];
+                vv[q].z = raw[(4 * cch + 2) * TBM + r];
+                vv[q].w = raw[(4 * cch + 3) * TBM + r];
+              }
+              asm volatile("bar.sync 2, 64;" ::: "memory");
+#pragma unroll
+              for (int q = 0; q < NPER; ++q) {
+                const int e = st + 64 * q, r = e % TBM, cch = e / TBM;
                 const int sw = (CH == 2) ? ((r >> 2) & 1) : (CH == 4) ? ((r >> 1) & 3) : (r & 7);
-                uint4 v;
-                v.x = raw[(4 * cch + 0) * TBM + r];
-                v.y = raw[(4 * cch + 1) * TBM + r];
-                v.z = raw[(4 * cch + 2) * TBM + r];
-                v.w = raw[(4 * cch + 3) * TBM + r];
+                const uint4 v = vv[q];
                 const int o = r * CH + (cch ^ sw);
                 if (X3) {
                   uint4 h, rr;
@@ -1025,9 +1042,9 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   const bool x3 = pl.kind == K_TF32X3;
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
   const int sw0 = x3 ? 32 : 64;
-  const size_t aset = (size_t)apl * TBM * sw0 * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0));
+  const size_t aset = (size_t)apl * TBM * sw0 * (x3 ? 2 : 1);
   pl.fd = allow_fd && pl.nb <= 64 && budget / (aset + (size_t)apl * 4 * pl.nb * sw0 * (x3 ? 2 : 1)) >= 3;
-  if (allow_fd && !pl.fd && x3 && pl.amode == A_K && pl.ncb >= 2) {
+  if (allow_fd && !pl.fd && x3 && pl.ncb >= 2) {
     // 3xTF32 over several column blocks anyway: fused planes in blocks of <= 64 (one more read of
     // A, but a quarter of the MMAs and the chunk sums kept in TMEM): 5.27 against 6.02 ms at
     // 20000 x 10000 x 180, op N
@@ -1061,7 +1078,7 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   pl.nbuf = (pl.flush > 0 && !pl.ttotal && 8 * pl.nb <= 512) ? 2 : 1;
   const int cols = (pl.ttotal ? 2 : pl.nbuf) * 4 * pl.nb;
   pl.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
-  const size_t stage = (size_t)apl * TBM * pl.sw * ((x3 ? 2 : 1) + (pl.amode == A_T ? 1 : 0)) +
+  const size_t stage = (size_t)apl * TBM * pl.sw * (x3 ? 2 : 1) +
                        (size_t)(pl.fd ? apl : 1) * 4 * pl.nb * pl.sw * (x3 ? 2 : 1);
   pl.stages = (int)std::min<size_t>(MAX_STAGES, budget / stage);
   pl.smem = pl.stages * stage + 1024 + 256;
@@ -1209,7 +1226,7 @@ int sketch_tc_grouped_plan(qlr_ctx* ctx, int op, int count, const qlr_qmat* A, c
   for (int i = 0; i < count; ++i) all_pure = all_pure && (A[i].plane[0] == nullptr);
   const int apl = all_pure ? 3 : 4;
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
-  const size_t aset = (size_t)apl * TBM * base.sw * ((x3 ? 2 : 1) + (base.amode == A_T ? 1 : 0));
+  const size_t aset = (size_t)apl * TBM * base.sw * (x3 ? 2 : 1);
   auto xset = [&](bool f) { return (size_t)(f ? apl : 1) * 4 * max_nb * base.sw * (x3 ? 2 : 1); };
   // fused output planes for every problem when N = 4 nb <= 256 and the ring keeps 3 stages; with
   // 128-byte rows that leave fewer than 2 stages, 64-byte rows instead
