@@ -5,9 +5,10 @@ Headline workload (one "step"): the pass-efficient block Krylov workload -- a 20
 quaternion colour field (FP32 planes; per colour plane a sum of 64 random 2-D cosines, min-max
 scaled to [0, 1], plus uniform noise of amplitude 0.05) -- through Algorithm 4 with k = 50, block
 size b = 60 and v = 6 views: six sketch passes (five of 60 columns, the last of 180), the deflated
-Krylov stack and its QR, the core QSVD of the 180 x 180 factor and the lifts, in the mixed mode
-(one TF32 product for the Krylov blocks, 3xTF32 for the final pass; --compute picks another
-arithmetic).  Metric: sketch passes
+Krylov stack and its QR, the core QSVD of the 180 x 180 factor and the lifts, in TF32 (one TF32
+product for the Krylov blocks, one product of operands rounded to nearest TF32 with chunked FP32
+sums for the final pass; --compute picks another arithmetic; the same call with a 3xTF32 final
+pass is timed beside it as `fp32_final_pass`).  Metric: sketch passes
 per second (whole job); extra keys: A-read TB/s, ms per QSVD and the result's error against the FP64
 oracle (the oracle's values on the same seeded input are stored in tests/golden/fullsize_oracle.json
 by tests/golden/make_fullsize_golden.py): the largest relative error of the top-k singular values
@@ -136,7 +137,7 @@ def peak_for(compute: str):
     pk, src = _peaks()
     if compute == "BF16":
         return pk.get("bf16_tflops", 1900.0), "TFLOP/s", 1, f"bf16 burst ({src}, MEASURED_PEAKS.json)"
-    if compute in ("TF32", "TF32X3", "MIXED"):
+    if compute in ("TF32", "TF32X3", "MIXED", "TF32_RN"):
         if "tf32_mma" in _MEASURED:
             return _MEASURED["tf32_mma"], "TFLOP/s", 3 if compute == "TF32X3" else 1, \
                 "tf32 tcgen05 MMA loop measured in this run (qlr_peak_probe)"
@@ -178,10 +179,13 @@ def sketch_roofline(flops: float, nbytes: float, ms: float, launches: int, compu
 
 def sketch_classes(compute: str, widths):
     """(statistics class, arithmetic, pass widths) of the sketch launches of one step: the mixed
-    mode runs the Krylov blocks in TF32 and the last pass in 3xTF32 (a class of its own)."""
+    modes run the Krylov blocks in TF32 and the last pass in 3xTF32 (MIXED) or rounded TF32
+    (TF32_RN), each a class of its own."""
     if compute == "MIXED":
         return [("sketch_tc", "TF32", list(widths[:-1])), ("sketch_x3", "TF32X3", [widths[-1]])]
-    kid = {"F32": "sketch_simt", "TF32X3": "sketch_x3"}.get(compute, "sketch_tc")
+    if compute == "TF32_RN":
+        return [("sketch_tc", "TF32", list(widths[:-1])), ("sketch_rn", "TF32_RN", [widths[-1]])]
+    kid = {"F32": "sketch_simt", "TF32X3": "sketch_x3", "TF32_RN": "sketch_rn"}.get(compute, "sketch_tc")
     return [(kid, compute, list(widths))]
 
 
@@ -784,8 +788,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--compute", default="MIXED", choices=["TF32X3", "F32", "BF16", "TF32", "MIXED", "TF32_MIXED"],
-                    help="headline arithmetic: MIXED = TF32 Krylov blocks + 3xTF32 final pass (default)")
+    ap.add_argument("--compute", default="TF32_RN", choices=["TF32X3", "F32", "BF16", "TF32", "MIXED", "TF32_MIXED", "TF32_RN"],
+                    help="headline arithmetic: TF32_RN = TF32 Krylov blocks + a final pass on operands rounded to "
+                         "nearest TF32 (default); MIXED = TF32 Krylov blocks + 3xTF32 final pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (512-problem) leg")
     ap.add_argument("--no-completion", action="store_true", help="skip the matrix-completion leg")
@@ -879,19 +884,42 @@ def main():
     gpu_launches = sum(n for n, _ in stats.values())
     S_gpu = S.cpu().numpy()
 
-    # end to end through the C ABI with host buffers: H2D of A and Omega, D2H of U, S, V per step
+    # end to end through the C ABI with host buffers: H2D of A and Omega, D2H of U, S, V per step.
+    # Two device input buffers: step i + 1's inputs are copied on a second stream while step i
+    # computes (a stream of QSVDs, each with its own host input); the first copy is exposed.
     U_h = torch.empty(4, HK, HM, dtype=torch.float32).pin_memory()
     V_h = torch.empty(4, HK, HN, dtype=torch.float32).pin_memory()
     S_h = torch.empty(HK, dtype=torch.float64).pin_memory()
-    e2e_steps = max(2, min(args.steps, 3))
+    e2e_steps = max(2, args.steps)
+    A_b = [A, torch.empty_like(A)]
+    om_b = [om_store, torch.empty_like(om_store)]
+    main = torch.cuda.current_stream(dev)
+    cs = torch.cuda.Stream(dev)
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def load(i):
+        b = i % 2
+        if i >= 2:
+            cs.wait_event(free[b])                 # step i - 2 has finished reading buffer b
+        with torch.cuda.stream(cs):
+            A_b[b].copy_(A_host, non_blocking=True)
+            om_b[b].copy_(Om_host, non_blocking=True)
+        ready[b].record(cs)
+
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(e2e_steps):
-        A.copy_(A_host, non_blocking=True)
-        om_store.copy_(Om_host, non_blocking=True)
-        step()
+    load(0)
+    for i in range(e2e_steps):
+        if i + 1 < e2e_steps:
+            load(i + 1)
+        b = i % 2
+        main.wait_event(ready[b])
+        qlr.qsvd_lowrank(ctx, A_b[b], HK, HB - HK, HV, om_b[b].transpose(1, 2), U, S, V, algo=qlr.ALG4,
+                         compute=compute, side=qlr.SIDE_X)
+        free[b].record(main)
         U_h.copy_(U.transpose(1, 2), non_blocking=True)
         V_h.copy_(V.transpose(1, 2), non_blocking=True)
         S_h.copy_(S, non_blocking=True)
@@ -919,6 +947,26 @@ def main():
         roof["dominant_class"] = max(stats, key=lambda k: stats[k][1])
         roof["sketch_classes"] = roofs
         errs = errors_vs_oracle(ctx, A, P, S_gpu, qlr.ALG4, HV, compute, golden.get("c4", {}).get("v6"))
+        fp32_final = None
+        if args.compute == "TF32_RN" and legs:
+            # the same QSVD with the final pass in 3xTF32 (FP32-accurate for any singular vectors)
+            def step_x3():
+                qlr.qsvd_lowrank(ctx, A, HK, HB - HK, HV, om, U, S, V, algo=qlr.ALG4, compute=qlr.COMPUTE_TF32_MIXED,
+                                 side=qlr.SIDE_X)
+            for _ in range(2):
+                step_x3()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            for _ in range(5):
+                step_x3()
+            f1.record()
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1) / 5
+            gs = golden.get("c4", {}).get("v6")
+            fp32_final = {"compute": "MIXED (TF32 Krylov blocks, 3xTF32 final pass)", "ms_per_qsvd": round(fms, 3),
+                          "sketch_passes_per_s": round(passes_per_step / (fms / 1e3), 3),
+                          "sigma_rel_err": float(f"{sigma_rel_err(S.cpu().numpy(), gs['sigma']):.3e}") if gs else None,
+                          "device_error": ctx.sync()}
         cpu = mixed = sweep2 = batched = completion = sweep = None
         if legs:
             for name, fn in (("mixed", lambda: mixed_precision_leg(dev, golden)),
@@ -950,6 +998,8 @@ def main():
         dtypes = {"TF32X3": "f32 (3xTF32 tensor-core sketch, FP32 accumulation; FP64-class Gram and Cholesky)",
                   "MIXED": "f32/tf32 (TF32 sketches for the Krylov blocks, 3xTF32 for the final pass; FP64-class "
                            "Gram and Cholesky)",
+                  "TF32_RN": "f32/tf32 (TF32 sketches for the Krylov blocks, operands rounded to nearest TF32 with "
+                             "chunked FP32 sums for the final pass; FP64-class Gram and Cholesky)",
                   "F32": "f32 (SIMT)", "TF32": "tf32", "BF16": "bf16"}
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "sketch passes/s", "n_gpus": ws,
@@ -967,8 +1017,11 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": "sketch passes/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps, "ms": round(e2e_ms, 3),
+                    "overlap": "step i+1's H2D copies on a second stream during step i (two device input "
+                               "buffers); the first step's copy is exposed"},
             "gpu_launches": gpu_launches,
+            "fp32_final_pass": fp32_final,
             "peaks": peaks,
             "mixed_precision": mixed,
             "pass_sweep": sweep2,

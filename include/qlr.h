@@ -64,6 +64,14 @@ extern "C" {
  * Krylov block (Algorithm 2's passes 1..v-1, Algorithm 4's views before the final pass) run one
  * TF32 product; the last pass, which forms the returned R, runs 3xTF32. */
 #define QLR_COMPUTE_TF32_MIXED 6
+/* tcgen05 kind::tf32, one product of operands rounded to the nearest TF32 value (the tensor cores
+ * alone drop the 13 low mantissa bits, a bias toward zero), FP32 sums in chunks of 512 reduction
+ * elements added with round-to-nearest: each operand carries a zero-mean error of at most 2^-11
+ * relative.  In an algorithm call the products that only feed a later basis run plain TF32 (as in
+ * QLR_COMPUTE_TF32_MIXED) and the last pass this product.  The singular values then move by up
+ * to ~2^-12 relative where singular vectors are concentrated on few entries (each entry's
+ * rounding acts directly), far less where they are spread over many (the errors average out). */
+#define QLR_COMPUTE_TF32_RN 7
 
 /* ---- sketch operator ------------------------------------------------------------------- */
 #define QLR_OP_N 0 /* Y = A X     */
@@ -141,7 +149,8 @@ const char* qlr_strerror(int code);
 #define QLR_KID_SERIES 9      /* CholeskyQR2 second step by series (factor and inverse) */
 #define QLR_KID_COMPLETE 10   /* matrix completion: masked low-rank update   */
 #define QLR_KID_SKETCH_X3 11  /* tcgen05 sketch product in 3xTF32 (class 0 holds BF16 / TF32) */
-#define QLR_KID_COUNT 12
+#define QLR_KID_SKETCH_RN 12  /* tcgen05 sketch product in rounded TF32 (QLR_COMPUTE_TF32_RN)   */
+#define QLR_KID_COUNT 13
 int qlr_set_timing(qlr_ctx* ctx, int enable);
 int qlr_reset_stats(qlr_ctx* ctx);
 int qlr_stats(qlr_ctx* ctx, int kid, int64_t* launches, double* total_ms);
@@ -192,7 +201,7 @@ int qlr_fill_omega(qlr_ctx* ctx, uint64_t seed, int real_only, qlr_qmat* omega);
  *   op == QLR_OP_N:  Y (m x l) = A (m x n) X (n x l)
  *   op == QLR_OP_H:  Y (n x l) = A^H X (m x l), with A^H = A1^T - A2^T i - A3^T j - A4^T k (Section 2)
  * A: row-major, dtype F64 / F32 / BF16 (pure allowed).  X: column-major, 4 planes; its dtype
- * must be F64 for COMPUTE_F64, F32 for F32 / TF32 / TF32X3, F32 or BF16 for BF16 (F32 input is
+ * must be F64 for COMPUTE_F64, F32 for F32 / TF32 / TF32X3 / TF32_RN, F32 or BF16 for BF16 (F32 input is
  * rounded to BF16 on the device).  Y: column-major, F64 (COMPUTE_F64) or F32.  A is read once.
  * Degenerate sizes: an empty Y (no rows or no columns) launches nothing; an empty inner
  * dimension (n = 0 for op N, m = 0 for op H) writes Y = 0.

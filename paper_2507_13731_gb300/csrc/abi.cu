@@ -69,11 +69,15 @@ int resolve_compute(int compute, int a_dtype) {
   return QLR_COMPUTE_TF32X3;
 }
 
-bool valid_compute(int c) { return c >= QLR_COMPUTE_F64 && c <= QLR_COMPUTE_BF16; }
+bool valid_compute(int c) { return (c >= QLR_COMPUTE_F64 && c <= QLR_COMPUTE_BF16) || c == QLR_COMPUTE_TF32_RN; }
+bool tf32_family(int c) {
+  return c == QLR_COMPUTE_TF32 || c == QLR_COMPUTE_TF32X3 || c == QLR_COMPUTE_TF32_RN || c == QLR_COMPUTE_TF32_MIXED;
+}
 
-// Mixed mode: the products that only feed later bases run one TF32 product, the last pass 3xTF32.
+// Mixed modes: the products that only feed later bases run one TF32 product; the last pass runs
+// 3xTF32 (TF32_MIXED) or one TF32 product of rounded operands with chunked sums (TF32_RN).
 int final_compute(int c) { return c == QLR_COMPUTE_TF32_MIXED ? QLR_COMPUTE_TF32X3 : c; }
-int mid_compute(int c) { return c == QLR_COMPUTE_TF32_MIXED ? QLR_COMPUTE_TF32 : c; }
+int mid_compute(int c) { return (c == QLR_COMPUTE_TF32_MIXED || c == QLR_COMPUTE_TF32_RN) ? QLR_COMPUTE_TF32 : c; }
 
 // Thin-matrix dtype used by the scheduler for a compute mode.
 int thin_dtype(int compute) { return compute == QLR_COMPUTE_F64 ? QLR_F64 : QLR_F32; }
@@ -155,9 +159,7 @@ int prepare(qlr_ctx* ctx, const qlr_qmat* A, int k, int p, int passes, const qlr
   compute = resolve_compute(opts ? opts->compute : QLR_COMPUTE_AUTO, A->dtype);
   if (!valid_compute(compute) && compute != QLR_COMPUTE_TF32_MIXED) return QLR_EINVAL;
   if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
-  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3 || compute == QLR_COMPUTE_TF32_MIXED) &&
-      A->dtype != QLR_F32)
-    return QLR_EINVAL;
+  if (tf32_family(compute) && A->dtype != QLR_F32) return QLR_EINVAL;
   side = opts ? opts->side : QLR_SIDE_AUTO;
   if (side == QLR_SIDE_AUTO) side = (passes % 2 == 0 && A->cols > A->rows) ? QLR_SIDE_XH : QLR_SIDE_X;
   if (side != QLR_SIDE_X && side != QLR_SIDE_XH) return QLR_EINVAL;
@@ -503,11 +505,10 @@ int qlr_qsketch(qlr_ctx* ctx, int op, const qlr_qmat* A, const qlr_qmat* X, qlr_
   const int ydt = (compute == QLR_COMPUTE_F64) ? QLR_F64 : QLR_F32;
   if (Y->dtype != ydt) return QLR_EINVAL;
   if (compute == QLR_COMPUTE_F64 && X->dtype != QLR_F64) return QLR_EINVAL;
-  if ((compute == QLR_COMPUTE_F32 || compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && X->dtype != QLR_F32)
-    return QLR_EINVAL;
+  if ((compute == QLR_COMPUTE_F32 || tf32_family(compute)) && X->dtype != QLR_F32) return QLR_EINVAL;
   if (compute == QLR_COMPUTE_BF16 && !(X->dtype == QLR_F32 || X->dtype == QLR_BF16)) return QLR_EINVAL;
   if (compute == QLR_COMPUTE_BF16 && A->dtype != QLR_BF16) return QLR_EINVAL;
-  if ((compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32X3) && A->dtype != QLR_F32) return QLR_EINVAL;
+  if (tf32_family(compute) && A->dtype != QLR_F32) return QLR_EINVAL;
   DeviceGuard g(ctx->device);
   if (outer == 0 || X->cols == 0) return QLR_OK;                        // Y is empty
   if (inner == 0) return qlr::zero_qmat(ctx, *Y);                       // empty sums: Y = 0

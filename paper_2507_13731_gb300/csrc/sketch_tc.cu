@@ -71,6 +71,7 @@ struct TcParams {
   int ttotal;               // 1: the chunks' running sum is kept in TMEM columns [4 nb, 8 nb)
   int apl;                  // A planes per stage: 3 for a pure quaternion A (plane 0 absent), else 4
   int fd;                   // 1: fused output planes (one MMA per input plane, N = 4 nb; see issue_stage)
+  int rn;                   // 1 (TF32): A rounded to nearest TF32 in shared memory before the MMAs read it
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -85,7 +86,7 @@ struct TcScalars {
   int l, nb, ncb, kiters, c_first, stages;
   uint32_t neg_mask, idesc_base, tmem_cols;
   int* err;
-  int flush, nbuf, ttotal, apl, fd;
+  int flush, nbuf, ttotal, apl, fd, rn;
   __device__ __forceinline__ float* y(int d) const { return d == 0 ? y0 : d == 1 ? y1 : d == 2 ? y2 : y3; }
 };
 __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
@@ -95,7 +96,20 @@ __device__ __forceinline__ TcScalars tc_scalars(const TcParams& p) {
   v.kiters = p.kiters; v.c_first = p.c_first; v.stages = p.stages;
   v.neg_mask = p.neg_mask; v.idesc_base = p.idesc_base; v.tmem_cols = p.tmem_cols; v.err = p.err;
   v.flush = p.flush; v.nbuf = p.nbuf < 1 ? 1 : p.nbuf; v.ttotal = p.ttotal; v.apl = p.apl == 3 ? 3 : 4; v.fd = p.fd;
+  v.rn = p.rn;
   return v;
+}
+
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits, ties away from zero).
+// The tensor cores read a 4-byte operand's top 19 bits and drop the rest, which rounds every
+// element toward zero: on data of one sign that shrinks a product by ~2^-12 relative on average.
+__device__ __forceinline__ uint32_t tf32_rna(uint32_t bits) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(__uint_as_float(bits)));
+  return r;
+}
+__device__ __forceinline__ uint4 tf32_rna4(uint4 v) {
+  return make_uint4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -250,7 +264,9 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
   constexpr bool X3 = (KIND == K_TF32X3);
   constexpr bool MN = (AMODE == A_MN);
   constexpr bool TR = (AMODE == A_T);
-  constexpr bool WORKERS = X3 || TR;
+  // worker warps touch every A stage: the 3xTF32 split, the transpose, or (RN) the rounding
+  const bool RN = (KIND == K_TF32) && pv.rn != 0;
+  const bool WORKERS = X3 || TR || RN;
   constexpr int A_BYTES = TBM * C::SW;                 // one plane of the A tile (== raw tile bytes)
   constexpr int KSTEPS = C::BK / C::MMA_K;
   constexpr int ATOM_MN = C::SW / C::ESZ;              // MN-major: elements per atom row
@@ -442,9 +458,11 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
                 hi[o] = h;
                 lo[o] = rr;
               } else {
-                hi[o] = v;
+                hi[o] = RN ? tf32_rna4(v) : v;
               }
             }
+          } else if (!X3) {   // RN: round the K-major tile in place
+            for (int e = st; e < A_BYTES / 16; e += 64) hi[e] = tf32_rna4(hi[e]);
           } else {
             for (int e = st; e < A_BYTES / 16; e += 64) {
               uint4 v = hi[e], h, r;
@@ -933,6 +951,7 @@ struct StageArg {
   int fd, nb, ncb, c0;
   uint32_t neg;                   // bit c*4+d: sign(c, d) = -1
   int nrows;                      // staged rows: 4 cols, or (4 - c0) ncb 4 nb
+  int rn;                         // TF32: round to nearest TF32 (else the FP32 bits, truncated by the MMA)
 };
 
 template <int MODE>
@@ -959,7 +978,7 @@ __device__ __forceinline__ void stage_row(const StageArg& a, int r, int64_t k0, 
     if (MODE == K_BF16) {
       static_cast<__nv_bfloat16*>(a.out)[o0 + i] = __float2bfloat16_rn(v);
     } else if (MODE == K_TF32) {
-      static_cast<float*>(a.out)[o0 + i] = v;
+      static_cast<float*>(a.out)[o0 + i] = a.rn ? __uint_as_float(tf32_rna(__float_as_uint(v))) : v;
     } else {
       const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
       static_cast<float*>(a.out)[o0 + i] = h;
@@ -999,7 +1018,8 @@ uint32_t neg_table(int op) {
 }
 
 int kind_of(int compute) {
-  return compute == QLR_COMPUTE_BF16 ? K_BF16 : (compute == QLR_COMPUTE_TF32 ? K_TF32 : K_TF32X3);
+  return compute == QLR_COMPUTE_BF16 ? K_BF16
+         : (compute == QLR_COMPUTE_TF32 || compute == QLR_COMPUTE_TF32_RN) ? K_TF32 : K_TF32X3;
 }
 
 struct Plan {
@@ -1008,6 +1028,7 @@ struct Plan {
   int grid_sk;                   // stream-K CTAs (0: one CTA per output tile)
   int flush, nbuf, ttotal;       // accumulation chunks (stages per chunk, TMEM buffers, TMEM sum)
   bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
+  bool rn;                       // TF32 with operands rounded to nearest and chunked sums
   uint32_t tmem_cols;
   size_t smem;
 };
@@ -1023,12 +1044,16 @@ struct Plan {
 // ones took 0.48 ms (each A tile read once, and half as many MMAs of twice the width).
 constexpr int X3_FLUSH_STAGES = 32;
 constexpr int X3_MAX_NB = 128;
+// Rounded TF32 (QLR_COMPUTE_TF32_RN): one product per K step and input plane, so a chunk of this
+// many K elements adds about as many MMAs into an accumulator as a 3xTF32 chunk of 32 stages.
+constexpr int RN_FLUSH_K = 512;
 
 Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bool allow_wide = true, int apl = 4,
                bool allow_fd = true) {
   Plan pl{};
   pl.apl = apl;
   pl.kind = kind_of(compute);
+  pl.rn = (compute == QLR_COMPUTE_TF32_RN);
   pl.amode = (op == QLR_OP_N) ? A_K : (pl.kind == K_BF16 ? A_MN : A_T);
   pl.esz = pl.kind == K_BF16 ? 2 : 4;
   const int lp = (l + 15) / 16 * 16;
@@ -1040,16 +1065,17 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   // transposed-A form lost more to exposed loads than it gained: 1.16 against 0.87 ms at
   // 20000 x 10000 x 60, TF32 op H)
   const bool x3 = pl.kind == K_TF32X3;
+  const bool chunked = x3 || pl.rn;   // accumulation in chunks (FP32-accurate modes)
   const size_t budget = (size_t)227 * 1024 - 1024 - 256;
   const int sw0 = x3 ? 32 : 64;
   const size_t aset = (size_t)apl * TBM * sw0 * (x3 ? 2 : 1);
   pl.fd = allow_fd && pl.nb <= 64 && budget / (aset + (size_t)apl * 4 * pl.nb * sw0 * (x3 ? 2 : 1)) >= 3;
-  if (allow_fd && !pl.fd && x3 && pl.ncb >= 2) {
-    // 3xTF32 over several column blocks anyway: fused planes in blocks of <= 64 (one more read of
-    // A, but a quarter of the MMAs and the chunk sums kept in TMEM): 5.27 against 6.02 ms at
-    // 20000 x 10000 x 180, op N
+  if (allow_fd && !pl.fd && chunked && pl.ncb >= 2) {
+    // 3xTF32 (or rounded TF32) over several column blocks anyway: fused planes in blocks of <= 64
+    // (one more read of A, but a quarter of the MMAs and the chunk sums kept in TMEM): 5.27
+    // against 6.02 ms at 20000 x 10000 x 180, 3xTF32 op N
     const int ncb = (lp + 63) / 64, nb = ((lp + ncb - 1) / ncb + 15) / 16 * 16;
-    if (budget / (aset + (size_t)apl * 4 * nb * sw0 * 2) >= 3) {
+    if (budget / (aset + (size_t)apl * 4 * nb * sw0 * (x3 ? 2 : 1)) >= 3) {
       pl.ncb = ncb;
       pl.nb = nb;
       pl.fd = true;
@@ -1071,7 +1097,7 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   if (g > tiles) pl.grid_sk = (int)g;
   else if (tiles > num_sms && tiles % num_sms != 0 && g == num_sms) pl.grid_sk = num_sms;
   else pl.grid_sk = 0;
-  pl.flush = (pl.kind == K_TF32X3) ? X3_FLUSH_STAGES : 0;
+  pl.flush = (pl.kind == K_TF32X3) ? X3_FLUSH_STAGES : pl.rn ? RN_FLUSH_K / pl.bk : 0;
   // chunk sums in TMEM next to the chunk accumulator when both fit (column blocks <= 64), else in
   // the output with two chunk buffers
   pl.ttotal = (pl.flush > 0 && 8 * pl.nb <= 512) ? 1 : 0;
@@ -1143,7 +1169,9 @@ namespace qlr {
 
 bool sketch_tc_supported(int op, const qlr_qmat& A, const qlr_qmat& X, int compute) {
   (void)op; (void)X;
-  if (compute != QLR_COMPUTE_BF16 && compute != QLR_COMPUTE_TF32 && compute != QLR_COMPUTE_TF32X3) return false;
+  if (compute != QLR_COMPUTE_BF16 && compute != QLR_COMPUTE_TF32 && compute != QLR_COMPUTE_TF32X3 &&
+      compute != QLR_COMPUTE_TF32_RN)
+    return false;
   const int want = compute == QLR_COMPUTE_BF16 ? QLR_BF16 : QLR_F32;
   if (A.dtype != want || A.layout != QLR_ROW_MAJOR) return false;
   const size_t esz = qlr_dtype_size(A.dtype);
@@ -1477,6 +1505,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
     sa.c0 = 4 - pl.apl;
     sa.neg = neg_table(op);
     sa.nrows = pl.fd ? pl.apl * pl.ncb * 4 * pl.nb : 4 * l;
+    sa.rn = pl.rn ? 1 : 0;
     if (sa.nrows > 65535) return QLR_EUNSUPPORTED;
     const dim3 grid((unsigned)((K + STAGE_ROWS - 1) / STAGE_ROWS), (unsigned)sa.nrows);
     KTimer kt(ctx, QLR_KID_MISC);
@@ -1550,9 +1579,10 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.flush = pl.flush;
   prm.nbuf = pl.nbuf;
   prm.ttotal = pl.ttotal;
+  prm.rn = pl.rn ? 1 : 0;
   int rc;
   const bool h = (op != QLR_OP_N);
-  const int kid = (pl.kind == K_TF32X3) ? QLR_KID_SKETCH_X3 : QLR_KID_SKETCH_TC;
+  const int kid = (pl.kind == K_TF32X3) ? QLR_KID_SKETCH_X3 : pl.rn ? QLR_KID_SKETCH_RN : QLR_KID_SKETCH_TC;
   if (pl.kind == K_BF16) rc = h ? launch_kernel<K_BF16, A_MN>(ctx, pl, prm, kid) : launch_kernel<K_BF16, A_K>(ctx, pl, prm, kid);
   else if (pl.kind == K_TF32) rc = h ? launch_kernel<K_TF32, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32, A_K>(ctx, pl, prm, kid);
   else rc = h ? launch_kernel<K_TF32X3, A_T>(ctx, pl, prm, kid) : launch_kernel<K_TF32X3, A_K>(ctx, pl, prm, kid);

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_PKG, "libqlr.so")
 OK, EINVAL, ESHAPE, ENOTPD, ENOCONV, ETIMEOUT, ECUDA, ENOMEM, EUNSUPPORTED = range(9)
 F64, F32, BF16 = 0, 1, 2
 ROW_MAJOR, COL_MAJOR = 0, 1
-COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16, COMPUTE_TF32_MIXED = range(7)
+COMPUTE_AUTO, COMPUTE_F64, COMPUTE_F32, COMPUTE_TF32, COMPUTE_TF32X3, COMPUTE_BF16, COMPUTE_TF32_MIXED, \
+    COMPUTE_TF32_RN = range(8)
 COMPUTE_MIXED = COMPUTE_TF32_MIXED
 OP_N, OP_H = 0, 1
 ALG1, ALG2, ALG3, ALG4 = 1, 2, 3, 4
@@ -36,7 +37,7 @@ PEAK_TF32_MMA, PEAK_BF16_MMA, PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_N64, P
 
 _DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 KID_NAMES = ["sketch_tc", "sketch_simt", "gram", "chol", "tri_inv", "apply", "jacobi", "refine", "misc", "series",
-             "complete", "sketch_x3"]
+             "complete", "sketch_x3", "sketch_rn"]
 
 
 class QlrError(RuntimeError):

@@ -59,6 +59,7 @@ def test_whole_job_rate_and_single_rank_max():
 def test_sketch_classes_of_the_mixed_mode():
     w = [60, 60, 60, 60, 60, 180]
     assert bench.sketch_classes("MIXED", w) == [("sketch_tc", "TF32", w[:-1]), ("sketch_x3", "TF32X3", [180])]
+    assert bench.sketch_classes("TF32_RN", w) == [("sketch_tc", "TF32", w[:-1]), ("sketch_rn", "TF32_RN", [180])]
     assert bench.sketch_classes("TF32X3", w) == [("sketch_x3", "TF32X3", w)]
     assert bench.sketch_classes("BF16", w) == [("sketch_tc", "BF16", w)]
     assert bench.sketch_classes("F32", w) == [("sketch_simt", "F32", w)]

@@ -124,13 +124,21 @@ def test_alg4_fp64_small(ctx, v):
     assert abs(err_gpu - err_ref) <= 1e-8 * err_ref
 
 
+@pytest.mark.parametrize("compute,tol", [("F32", 1e-4), ("TF32_MIXED", 1e-4), ("TF32_RN", 1e-3)])
 @pytest.mark.parametrize("v", [2, 3, 4])
-def test_fp32_slow_decay(ctx, v):
+def test_fp32_slow_decay(ctx, v, compute, tol):
+    """Algorithm 2 with FP32 storage: plain FP32 (SIMT) and the mixed mode (TF32 products for the
+    passes that only feed the next basis, 3xTF32 for the last pass) within the FP32 tolerance 1e-4
+    of the oracle's singular values; the rounded-TF32 mode (the last pass one product of operands
+    rounded to nearest TF32: op N for odd v, op H for even v) within 1e-3.  This matrix's singular
+    vectors are concentrated on few entries (a unit-quaternion diagonal and 8 reflectors per side),
+    so the rounding of those entries (2^-12 relative) moves sigma_1 at first order: a CPU model of
+    the same arithmetic gives 2e-4..4e-4, where 3xTF32 gives 4e-5."""
     from paper_2507_13731_gb300 import qlr
     P = synth.config_slow_decay(1024, 768, 40, 10, v, seed=22)
-    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG2, "f32", qlr.COMPUTE_F32)
+    U, S, V, Om, _ = run_gpu(ctx, P, v, qlr.ALG2, "f32", getattr(qlr, "COMPUTE_" + compute))
     ref = al.alg2_arbitrary_pass(P.A, 40, 10, v, Om)
-    np.testing.assert_allclose(S, ref.S, rtol=1e-4)
+    np.testing.assert_allclose(S, ref.S, rtol=tol)
 
 
 @pytest.mark.parametrize("v", [2, 3])
@@ -231,7 +239,7 @@ def test_alg4_basis_spans_oracle_krylov_space(ctx, v):
     np.testing.assert_allclose(lhs, rhs, atol=1e-9 * np.abs(P.A).max() * P.m)
 
 
-@pytest.mark.parametrize("compute", ["TF32X3", "F32"])
+@pytest.mark.parametrize("compute", ["TF32X3", "F32", "TF32_MIXED", "TF32_RN"])
 def test_alg4_fp32_colour_field(ctx, compute):
     """Algorithm 4 with FP32 storage on a colour field (the config-4 construction at 1200 x 600,
     k = 30, b = 40, v = 6): the top-k singular values within the FP32 tolerance 1e-4 of the FP64

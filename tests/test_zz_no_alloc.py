@@ -6,8 +6,9 @@ state, and some host applications give all device memory to their own pool alloc
 point takes its scratch from one fixed device array in the library instead.
 
 Checked here, through the C ABI: its product equals the FP64 oracle's Hamilton product (eq. 1
-summed over the inner index) element by element within the tensor-core bound, on two calls in a
-row (the shared array keeps the first call's contents, which must not leak into the second);
+summed over the inner index) element by element within the tensor-core bound, and the context
+entry point qlr_qsketch's product within twice that bound, on two calls in a row (the shared
+array keeps the first call's contents, which must not leak into the second);
 repeated calls allocate no device memory; sizes beyond the array give QLR_ENOMEM; degenerate
 sizes behave as in qlr_qsketch.  The file name sorts after the other GPU test files."""
 import numpy as np
@@ -48,6 +49,12 @@ def test_noalloc_matches_oracle_product(mode, op, m, n, l):
     Xh = host(Xd.to(torch.bfloat16)) if mode == "BF16" else host(Xd)
     want = Q.qmatmul(Aop, Xh)
     bound = 2 * _tol(mode, rows_in) * (Q.qnorm(Aop) @ Q.qnorm(Xh)) + 1e-30
+    ctx = qlr.Context()
+    Yctx = qlr.empty_thin(rows_out, l)
+    qlr.qsketch(ctx, o, Ad, Xd, Yctx, compute)
+    torch.cuda.synchronize()
+    ref = host(Yctx)
+    assert np.all(Q.qnorm(ref - want) <= bound)
     for call in range(2):
         Y = qlr.empty_thin(rows_out, l)
         Y.fill_(float("nan"))
@@ -57,6 +64,8 @@ def test_noalloc_matches_oracle_product(mode, op, m, n, l):
         diff = Q.qnorm(host(Y) - want)
         assert np.all(np.isfinite(diff)), f"call {call}"
         assert np.all(diff <= bound), f"call {call}: {float((diff / bound).max())}"
+        assert np.all(Q.qnorm(host(Y) - ref) <= 2 * bound), f"call {call} against qlr_qsketch"
+    ctx.close()
 
 
 def test_noalloc_allocates_no_device_memory():
