@@ -72,6 +72,7 @@ struct TcParams {
   int apl;                  // A planes per stage: 3 for a pure quaternion A (plane 0 absent), else 4
   int fd;                   // 1: fused output planes (one MMA per input plane, N = 4 nb; see issue_stage)
   int rn;                   // 1 (TF32): A rounded to nearest TF32 in shared memory before the MMAs read it
+  int cgroup;               // stream-K in column-block groups (gridDim.x a multiple of ncb)
 };
 
 // The scalar part of TcParams, copied into registers once: with the parameters in global memory
@@ -248,12 +249,15 @@ __device__ __forceinline__ void issue_stage(const StageDescs& D, int s, uint32_t
 
 // ---------------------------------------------------------------------------------------
 // A contiguous piece of one output tile's reduction: stages [it0, it1).  A tile reduced in
-// nseg > 1 pieces (stream-K) has them from CTAs c0 .. c0 + nseg - 1; piece o writes its partial
-// to slot 2 (c0 + o) + (o == 0 ? b0 : 0) (b0 = 1 when the tile starts inside CTA c0's range, as
-// that CTA's second piece), and the last piece to arrive adds the partials in slot order.
+// nseg > 1 pieces (stream-K) has them from CTAs c0 .. c0 + nseg - 1 of its group; piece o writes
+// its partial to slot 2 ((c0 + o) cs + coff) + (o == 0 ? b0 : 0) (b0 = 1 when the tile starts
+// inside CTA c0's range, as that CTA's second piece), and the last piece to arrive adds the
+// partials in slot order.  A group is every CTA (cs = 1, coff = 0), or, with column-block groups,
+// the CTAs coff, coff + cs, coff + 2 cs, ... of one column block (cs = the number of blocks).
 struct Seg {
   int it0, it1, slot, nseg, c0, b0;
   int more;   // another piece follows in this CTA: keep the right to allocate TMEM
+  int cs = 1, coff = 0;
 };
 
 // One output tile (column block cb, row tile mt) over the reduction piece sg.
@@ -576,7 +580,7 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
 #pragma unroll
               for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
               for (int o = 0; o < sg.nseg; ++o) {
-                const int slot = 2 * (sg.c0 + o) + (o == 0 ? sg.b0 : 0);
+                const int slot = 2 * ((sg.c0 + o) * sg.cs + sg.coff) + (o == 0 ? sg.b0 : 0);
                 const float* P = pv.part + (size_t)slot * tile_elems + (size_t)d * TBM * nb + (size_t)jc0 * TBM + row;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) acc[jj] += __ldcg(P + (size_t)jj * TBM);   // 16 loads in flight
@@ -613,9 +617,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(const __grid_c
 // whole tile writes its output directly, and the pieces of a split tile are added by the last one
 // to finish.  A CTA writes at most two partial tiles: slot 2c for its tail piece, slot 2c + 1 for a
 // head piece that is not its first piece.
+// Column-block groups (p.cgroup, gridDim.x a multiple of ncb): CTA c works on column block
+// c mod ncb only, and the CTAs of each block split that block's row tiles' stages the same way,
+// so CTAs c, c + 1, ..., c + ncb - 1 read the same A stages at about the same time: A comes from
+// DRAM once and from L2 for the other blocks (with one list over all blocks, the CTAs reading a
+// given A stage for different blocks are a tile's length apart in time and A is re-read from
+// DRAM once per block).
 template <int KIND, int AMODE, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const __grid_constant__ TcParams p) {
-  const int64_t K = p.kiters, W = (int64_t)p.mtiles * p.ncb * K, G = gridDim.x, c = blockIdx.x;
+  const int NG = (p.cgroup && p.ncb > 1) ? p.ncb : 1;             // CTAs per group step
+  const int cbg = (int)(blockIdx.x % NG);                         // this CTA's block (groups)
+  const int64_t K = p.kiters, W = (int64_t)p.mtiles * (p.ncb / NG) * K, G = gridDim.x / NG, c = blockIdx.x / NG;
   auto start = [&](int64_t cc) { return cc * W / G; };
   // the CTA whose range holds stage x: the largest cc with start(cc) <= x
   auto owner = [&](int64_t x) { return ((x + 1) * G + W - 1) / W - 1; };
@@ -629,9 +641,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_streamk_kernel(const 
     const int64_t c0 = owner(t * K), c1 = owner((t + 1) * K - 1);
     const int b0 = (start(c0) < t * K) ? 1 : 0;
     const int more = (pos + (it1 - it0) < end) ? 1 : 0;
-    const Seg sg{it0, it1, (int)(2 * c + (c == c0 ? b0 : 0)), (int)(c1 - c0 + 1), (int)c0, b0, more};
+    const Seg sg{it0, it1, (int)(2 * (c * NG + cbg) + (c == c0 ? b0 : 0)), (int)(c1 - c0 + 1), (int)c0, b0, more,
+                 NG, cbg};
     if (!first) __syncthreads();
-    sketch_tile<KIND, AMODE, WIDE>(p, (int)(t % p.ncb), (int)(t / p.ncb), sg);
+    if (NG > 1) sketch_tile<KIND, AMODE, WIDE>(p, cbg, (int)t, sg);
+    else sketch_tile<KIND, AMODE, WIDE>(p, (int)(t % p.ncb), (int)(t / p.ncb), sg);
     first = false;
     pos += it1 - it0;
   }
@@ -1029,6 +1043,7 @@ struct Plan {
   int flush, nbuf, ttotal;       // accumulation chunks (stages per chunk, TMEM buffers, TMEM sum)
   bool wide;                     // 128-byte stage rows (Cfg<KIND, true>)
   bool rn;                       // TF32 with operands rounded to nearest and chunked sums
+  bool cgroup;                   // stream-K CTAs in column-block groups (grid_sk a multiple of ncb)
   uint32_t tmem_cols;
   size_t smem;
 };
@@ -1097,6 +1112,12 @@ Plan make_plan(int compute, int op, int64_t M, int64_t K, int l, int num_sms, bo
   if (g > tiles) pl.grid_sk = (int)g;
   else if (tiles > num_sms && tiles % num_sms != 0 && g == num_sms) pl.grid_sk = num_sms;
   else pl.grid_sk = 0;
+  // several column blocks: the stream-K CTAs in groups of one CTA per block (a whole number of
+  // groups), so the blocks' CTAs read each A stage together
+  if (pl.grid_sk > 0 && pl.ncb > 1 && pl.grid_sk >= 2 * pl.ncb) {
+    pl.grid_sk -= pl.grid_sk % pl.ncb;
+    pl.cgroup = true;
+  }
   pl.flush = (pl.kind == K_TF32X3) ? X3_FLUSH_STAGES : pl.rn ? RN_FLUSH_K / pl.bk : 0;
   // chunk sums in TMEM next to the chunk accumulator when both fit (column blocks <= 64), else in
   // the output with two chunk buffers
@@ -1580,6 +1601,7 @@ int sketch_tc(qlr_ctx* ctx, int op, const qlr_qmat& A, const qlr_qmat& X, qlr_qm
   prm.nbuf = pl.nbuf;
   prm.ttotal = pl.ttotal;
   prm.rn = pl.rn ? 1 : 0;
+  prm.cgroup = pl.cgroup ? 1 : 0;
   int rc;
   const bool h = (op != QLR_OP_N);
   const int kid = (pl.kind == K_TF32X3) ? QLR_KID_SKETCH_X3 : pl.rn ? QLR_KID_SKETCH_RN : QLR_KID_SKETCH_TC;
