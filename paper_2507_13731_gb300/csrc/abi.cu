@@ -212,9 +212,12 @@ int run_alg2(Sched& S, int l, int v, const qlr_qmat& om, qlr_qmat& Q1, qlr_qmat&
 }
 
 // Block classical Gram-Schmidt of the newest block of a stack against the blocks before it:
-// the slot (columns [c0, c0 + l) of K) becomes Y - B (B^H Y), B = K's columns [0, c0), run twice
-// ("twice is enough").  B^H Y is the off-diagonal block of the FP64-class Gram of K's first
-// c0 + l columns; the product B (B^H Y) accumulates in FP32.  The span of the stack is unchanged.
+// the slot (columns [c0, c0 + l) of K) becomes Y - B (B^H Y), B = K's columns [0, c0), once.
+// B^H Y is the off-diagonal block of the FP64-class Gram of K's first c0 + l columns; the
+// product B (B^H Y) accumulates in FP32.  The span of the stack is unchanged.  One pass suffices
+// here: the coefficients are FP64-class and B is orthonormal to FP32 rounding, so what a second
+// pass would remove (the FP32 rounding of Y along B) leaves the stack's condition number within
+// ~1e-5 of 1, and the stack gets its own QR at the end.
 int deflate_block(Sched& S, qlr_qmat& K, int64_t c0, int l) {
   if (c0 == 0) return QLR_OK;
   const int64_t w = c0 + l;
@@ -223,7 +226,7 @@ int deflate_block(Sched& S, qlr_qmat& K, int64_t c0, int l) {
   if (!S.ws->ok) return QLR_ENOMEM;
   const qlr_qmat KB = col_slice(K, 0, w);
   const qlr_qmat slot = col_slice(K, c0, l);
-  for (int round = 0; round < 2; ++round) {
+  {
     QLR_TRY(qlr::gram(S.ctx, KB, G, *S.ws));
     qlr::GemmArgs g{};
     for (int c = 0; c < 4; ++c) {
