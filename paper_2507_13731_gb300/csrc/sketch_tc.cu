@@ -351,6 +351,12 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       const uint32_t tx = (uint32_t)((4 - pv.c_first) * A_BYTES + (FD ? 4 - pv.c_first : 4) * X_BYTES * (X3 ? 2 : 1));
+      // One column block: every A stage is read once, while the staged thin operand is read by
+      // every row tile, so A is loaded evict-first and the operand evict-last (it then stays in
+      // L2 while A streams through).  Several blocks share A stages through L2 (column-block
+      // groups), so their loads keep the default priority.
+      const bool hint = (pv.ncb == 1);
+      const uint64_t pol_a = l2_evict_first_policy(), pol_x = l2_evict_last_policy();
       int issued = 0;
       for (int i = 0; i < nit; ++i) {
         const int s = i % STAGES;
@@ -363,15 +369,18 @@ __device__ __forceinline__ void sketch_tile(const TcParams& p, const int cb, con
 #pragma unroll
             for (int a = 0; a < NATOM; ++a)
               tma_load_2d(smem_u32(a_plane(s, c) + a * C::BK * C::SW), &p.tmA[c], (int)m0 + a * ATOM_MN, k0, &full[s]);
-          } else if (TR) {
-            tma_load_2d(smem_u32(raw_plane(s, c)), &p.tmA[c], (int)m0, k0, &full[s]);   // [BK][128] unswizzled
+          } else if (TR) {   // [BK][128] unswizzled
+            if (hint) tma_load_2d_hint(smem_u32(raw_plane(s, c)), &p.tmA[c], (int)m0, k0, &full[s], pol_a);
+            else tma_load_2d(smem_u32(raw_plane(s, c)), &p.tmA[c], (int)m0, k0, &full[s]);
           } else {
-            tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
+            if (hint) tma_load_2d_hint(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s], pol_a);
+            else tma_load_2d(smem_u32(a_plane(s, c)), &p.tmA[c], k0, (int)m0, &full[s]);
           }
         }
         if (FD) {   // X~_c, rows [cb 4 nb, (cb + 1) 4 nb)
           for (int c = pv.c_first; c < 4; ++c) {
-            tma_load_2d(smem_u32(x_plane(s, c - C0)), &p.tmX[c], k0, 4 * j0, &full[s]);
+            if (hint) tma_load_2d_hint(smem_u32(x_plane(s, c - C0)), &p.tmX[c], k0, 4 * j0, &full[s], pol_x);
+            else tma_load_2d(smem_u32(x_plane(s, c - C0)), &p.tmX[c], k0, 4 * j0, &full[s]);
             if (X3) tma_load_2d(smem_u32(xlo_plane(s, c - C0)), &p.tmXlo[c], k0, 4 * j0, &full[s]);
           }
         } else {
