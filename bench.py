@@ -910,23 +910,29 @@ def main():
                     om_b[b].copy_(Om_host, non_blocking=True)
             ready[b][c].record(st)
 
+    def e2e_run(nsteps):
+        load(0)
+        for i in range(nsteps):
+            if i + 1 < nsteps:
+                load(i + 1)
+            b = i % 2
+            for ev in ready[b]:
+                main.wait_event(ev)
+            qlr.qsvd_lowrank(ctx, A_b[b], HK, HB - HK, HV, om_b[b].transpose(1, 2), U, S, V, algo=qlr.ALG4,
+                             compute=compute, side=qlr.SIDE_X)
+            free[b].record(main)
+            U_h.copy_(U.transpose(1, 2), non_blocking=True)
+            V_h.copy_(V.transpose(1, 2), non_blocking=True)
+            S_h.copy_(S, non_blocking=True)
+
+    e2e_run(2)                                     # untimed: first use of the streams and buffers
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    load(0)
-    for i in range(e2e_steps):
-        if i + 1 < e2e_steps:
-            load(i + 1)
-        b = i % 2
-        for ev in ready[b]:
-            main.wait_event(ev)
-        qlr.qsvd_lowrank(ctx, A_b[b], HK, HB - HK, HV, om_b[b].transpose(1, 2), U, S, V, algo=qlr.ALG4,
-                         compute=compute, side=qlr.SIDE_X)
-        free[b].record(main)
-        U_h.copy_(U.transpose(1, 2), non_blocking=True)
-        V_h.copy_(V.transpose(1, 2), non_blocking=True)
-        S_h.copy_(S, non_blocking=True)
+    for st in cs:
+        st.wait_event(e0)                          # the first copies start inside the timed region
+    e2e_run(e2e_steps)
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
