@@ -11,20 +11,24 @@
 //
 // Per CTA: a 128-row tile of the output (M = m for op N, M = n for op H) and a block of nb <= 128
 // output columns of all four planes (4 nb <= 512 TMEM columns), over a contiguous range of the
-// reduction (stream-K when there are fewer tiles than SMs: every SM takes an equal share of all
-// the tiles' reduction stages).  A's tiles come through TMA into a 2-4 stage shared-memory ring; A is read
-// exactly once per column block.  Op N stages A K-major (TMA swizzled tiles).  Op H reads A along
+// reduction (stream-K when the tiles do not fill whole waves: every SM takes an equal share of
+// the tiles' reduction stages; with several column blocks, one CTA per block in each group, so the
+// blocks read every A stage together and A comes from DRAM about once).  A's tiles come through
+// TMA into a 2-8 stage shared-memory ring.  Op N stages A K-major (TMA swizzled tiles).  Op H reads A along
 // its rows: for BF16 the MMA consumes the MN-major tile directly; for the 4-byte modes the tile is
 // loaded unswizzled and the worker warps transpose it into the K-major swizzled layout (splitting
 // it into hi / lo on the way for 3xTF32).
-// Warp roles: 0 = TMA producer, 1 = MMA issuer (owns TMEM), 2-3 = workers (hi/lo split and/or
-// transpose of A), 4-7 = epilogue (TMEM -> registers -> global, or a stream-K partial + the
-// last piece's reduction).
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (owns TMEM), 2-3 = workers (hi/lo split,
+// rounding and/or transpose of A), 4-7 = epilogue (TMEM -> registers -> global, or a stream-K
+// partial + the last piece's reduction).
 //
 // Precision modes: BF16 (kind::f16, A stored BF16, X rounded to BF16), TF32 (kind::tf32, one
-// product on FP32 data), TF32X3 (kind::tf32: A = A_hi + A_lo and X = X_hi + X_lo with
-// A_hi = A with its 13 low mantissa bits cleared, three products A_hi X_hi + A_lo X_hi + A_hi X_lo).
-// Accumulation is FP32 in TMEM throughout.
+// product on FP32 data, which the tensor cores truncate to TF32), rounded TF32 (one product, A and
+// X rounded to the nearest TF32 value first: by the staging kernel for X, by the worker warps in
+// shared memory for A), TF32X3 (kind::tf32: A = A_hi + A_lo and X = X_hi + X_lo with A_hi = A
+// with its 13 low mantissa bits cleared, three products A_hi X_hi + A_lo X_hi + A_hi X_lo).
+// Accumulation is FP32 in TMEM throughout; the FP32-accurate modes (TF32X3, rounded TF32) add it
+// in chunks summed with round-to-nearest.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
