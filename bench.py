@@ -22,6 +22,8 @@ On one GPU the line also carries
                 with BF16 storage against the same call in 3xTF32 and in plain FP32 (SIMT), each
                 with its time and its error against the oracle, plus the BF16 sketch's roofline;
   `pass_sweep`  the 4096 x 4096 slow-decay workload through Algorithm 2 at v in {2, 3, 4, 6, 8};
+  `library_reference` cuBLAS (torch.matmul) on the materialised real expansion of the headline's
+                narrow pass, FP32 and TF32 (a library reference, not this library's path);
   `batched`, `completion`, `lowrank_sweep` as named (--no-batched / --no-completion / --no-sweep).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--compute MODE]
@@ -268,6 +270,65 @@ def peaks_leg(dev):
     out["how"] = ("tcgen05 MMA loop, M=128 N=256 (K=8 tf32 / 16 bf16) from shared memory, one CTA per SM (the _n64 "
                   "entries: the same loop with N=64); FMA loops, 8 independent chains per thread, 8 CTAs of 256 threads "
                   "per SM; best of 3 ~40 ms launches")
+    return out
+
+
+# the Hamilton product's sign table: s(c, d) = -1 for these (input plane c, output plane d) of op N;
+# op H flips every c != 0
+_NEG_N = {(1, 0), (2, 0), (3, 0), (1, 2), (2, 3), (3, 1)}
+
+
+def _hamilton_sign(c: int, d: int, op: str) -> float:
+    s = -1.0 if (c, d) in _NEG_N else 1.0
+    return -s if (op == "H" and c != 0) else s
+
+
+def library_leg(ctx, A, ell=HB, reps=5):
+    """A library reference for the headline's narrow sketch pass (pure A, l = 60): cuBLAS through
+    torch.matmul on the materialised real expansion of the Hamilton product, FP32 (TF32 off) and
+    TF32 -- op N as Y_d = sum_c s(c, d) A_c X_(c xor d) (one batched product over the planes and a
+    sum), op H as Z = [A_1; A_2; A_3]^T F(Y) (one product on the stacked planes).  Checked against
+    this library's 3xTF32 product; not this library's path."""
+    import torch
+
+    from paper_2507_13731_gb300 import qlr
+    dev = A.device
+    m, n = A.shape[1], A.shape[2]
+    g = torch.Generator(device=dev).manual_seed(7)
+    out = {"workload": f"pure {m}x{n} FP32 planes, l = {ell}", "reps": reps}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for op in ("N", "H"):
+            rows_in, rows_out = (n, m) if op == "N" else (m, n)
+            Xp = torch.randn(4, rows_in, ell, device=dev, generator=g)
+            # E (op N) or F (op H): per input plane c = 1..3, the four output planes' blocks
+            Ex = torch.stack([torch.cat([_hamilton_sign(c, d, op) * Xp[c ^ d] for d in range(4)], dim=1)
+                              for c in (1, 2, 3)])                               # (3, rows_in, 4 l)
+            if op == "N":
+                call = lambda: torch.matmul(A, Ex).sum(0)                        # (rows_out, 4 l)
+            else:
+                A2 = A.reshape(3 * m, n)
+                Ef = Ex.reshape(3 * m, 4 * ell)
+                call = lambda: torch.matmul(A2.t(), Ef)
+            ref = qlr.empty_thin(rows_out, ell, device=dev)
+            qlr.qsketch(ctx, qlr.OP_N if op == "N" else qlr.OP_H, A, qlr.to_thin(Xp), ref, qlr.COMPUTE_TF32X3)
+            for mode, tf32 in (("fp32", False), ("tf32", True)):
+                torch.backends.cuda.matmul.allow_tf32 = tf32
+                for _ in range(2):
+                    Y = call()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    Y = call()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                got = Y.reshape(rows_out, 4, ell).permute(1, 0, 2)
+                err = float((got - ref).abs().max() / ref.abs().max())
+                out[f"op{op}_{mode}"] = {"ms": round(ms, 4), "a_read_tbs": round(3 * m * n * 4 / (ms / 1e3) / 1e12, 3),
+                                         "max_rel_diff_vs_3xtf32": float(f"{err:.2e}")}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
     return out
 
 
@@ -988,9 +1049,10 @@ def main():
                           "sketch_passes_per_s": round(passes_per_step / (fms / 1e3), 3),
                           "sigma_rel_err": float(f"{sigma_rel_err(S.cpu().numpy(), gs['sigma']):.3e}") if gs else None,
                           "device_error": ctx.sync()}
-        cpu = mixed = sweep2 = batched = completion = sweep = None
+        cpu = mixed = sweep2 = batched = completion = sweep = library = None
         if legs:
-            for name, fn in (("mixed", lambda: mixed_precision_leg(dev, golden)),
+            for name, fn in (("library", lambda: library_leg(ctx, A)),
+                             ("mixed", lambda: mixed_precision_leg(dev, golden)),
                              ("sweep2", lambda: pass_sweep_leg(dev, golden)),
                              ("batched", None if args.no_batched else lambda: batched_leg(dev)),
                              ("completion", None if args.no_completion else lambda: completion_leg(dev, golden)),
@@ -1001,7 +1063,9 @@ def main():
                     res = fn()
                 except Exception as e:                 # reported, never fatal to the headline line
                     res = {"error": f"{type(e).__name__}: {e}"}
-                if name == "mixed":
+                if name == "library":
+                    library = res
+                elif name == "mixed":
                     mixed = res
                 elif name == "sweep2":
                     sweep2 = res
@@ -1044,6 +1108,7 @@ def main():
                                "input buffers); the first step's copy is exposed"},
             "gpu_launches": gpu_launches,
             "fp32_final_pass": fp32_final,
+            "library_reference": library,
             "peaks": peaks,
             "mixed_precision": mixed,
             "pass_sweep": sweep2,
