@@ -283,6 +283,26 @@ def _hamilton_sign(c: int, d: int, op: str) -> float:
     return -s if (op == "H" and c != 0) else s
 
 
+def real_expansion(Xp, op: str):
+    """The thin operand's side of the Hamilton product as a real matrix, for a pure A (planes
+    1..3): per input plane c, the four output planes' blocks s(c, d) X_(c xor d) side by side.
+    Xp: (4, rows, l) -> (3, rows, 4 l)."""
+    import torch
+    return torch.stack([torch.cat([_hamilton_sign(c, d, op) * Xp[c ^ d] for d in range(4)], dim=1)
+                        for c in (1, 2, 3)])
+
+
+def expansion_product(A, Ex, op: str):
+    """The sketch product of a pure A (3, m, n) through the real expansion: op N as the batched
+    product over the planes summed, op H as one product on the stacked planes.  Returns the four
+    output planes side by side, (rows_out, 4 l)."""
+    import torch
+    if op == "N":
+        return torch.matmul(A, Ex).sum(0)
+    m, n = A.shape[1], A.shape[2]
+    return torch.matmul(A.reshape(3 * m, n).t(), Ex.reshape(3 * m, Ex.shape[2]))
+
+
 def library_leg(ctx, A, ell=HB, reps=5):
     """A library reference for the headline's narrow sketch pass (pure A, l = 60): cuBLAS through
     torch.matmul on the materialised real expansion of the Hamilton product, FP32 (TF32 off) and
@@ -301,15 +321,8 @@ def library_leg(ctx, A, ell=HB, reps=5):
         for op in ("N", "H"):
             rows_in, rows_out = (n, m) if op == "N" else (m, n)
             Xp = torch.randn(4, rows_in, ell, device=dev, generator=g)
-            # E (op N) or F (op H): per input plane c = 1..3, the four output planes' blocks
-            Ex = torch.stack([torch.cat([_hamilton_sign(c, d, op) * Xp[c ^ d] for d in range(4)], dim=1)
-                              for c in (1, 2, 3)])                               # (3, rows_in, 4 l)
-            if op == "N":
-                call = lambda: torch.matmul(A, Ex).sum(0)                        # (rows_out, 4 l)
-            else:
-                A2 = A.reshape(3 * m, n)
-                Ef = Ex.reshape(3 * m, 4 * ell)
-                call = lambda: torch.matmul(A2.t(), Ef)
+            Ex = real_expansion(Xp, op)                                          # E (op N) or F (op H)
+            call = lambda: expansion_product(A, Ex, op)                          # (rows_out, 4 l)
             ref = qlr.empty_thin(rows_out, ell, device=dev)
             qlr.qsketch(ctx, qlr.OP_N if op == "N" else qlr.OP_H, A, qlr.to_thin(Xp), ref, qlr.COMPUTE_TF32X3)
             for mode, tf32 in (("fp32", False), ("tf32", True)):

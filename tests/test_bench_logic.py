@@ -63,3 +63,22 @@ def test_sketch_classes_of_the_mixed_mode():
     assert bench.sketch_classes("TF32X3", w) == [("sketch_x3", "TF32X3", w)]
     assert bench.sketch_classes("BF16", w) == [("sketch_tc", "BF16", w)]
     assert bench.sketch_classes("F32", w) == [("sketch_simt", "F32", w)]
+
+
+@pytest.mark.parametrize("op", ["N", "H"])
+def test_library_reference_expansion_is_the_hamilton_product(op):
+    """The cuBLAS reference leg computes the sketch through the real expansion of the Hamilton
+    product; on CPU tensors it must equal the oracle's quaternion product of a pure A (eq. 1
+    summed over the inner index; op H with A^H of Section 2)."""
+    torch = pytest.importorskip("torch")
+    from oracle import quaternion as Q
+    m, n, l = 9, 7, 4
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, m, n))
+    Afull = np.concatenate([np.zeros((1, m, n)), A])
+    X = rng.standard_normal((4, n if op == "N" else m, l))
+    got = bench.expansion_product(torch.from_numpy(A), bench.real_expansion(torch.from_numpy(X), op), op)
+    rows = m if op == "N" else n
+    got = got.reshape(rows, 4, l).permute(1, 0, 2).numpy()
+    want = Q.qmatmul(Afull if op == "N" else Q.qH(Afull), X)
+    np.testing.assert_allclose(got, want, atol=1e-12)
